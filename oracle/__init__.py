@@ -1,0 +1,214 @@
+"""Oracle: plain, slow FP64 CPU implementation of the method (test infrastructure only).
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package. The CUDA library shares no code with it. Fields are numpy float64 arrays of
+shape (nz, ny, nx) (x fastest); the vertical coefficient ``v`` is an (ny, nx) array of
+omega^2 lambda^2 / hz^2 per column. Each wrapper names the passage of the paper it follows; the C
+source (``tpmg_oracle.c``) holds the arithmetic.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tpmg_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_D = ctypes.c_double
+_I = ctypes.c_int
+_P = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle into oracle/liboracle.so with the host gcc (no -march flags)."""
+    srcs = [_SRC] + [os.path.join(_HERE, s) for s in ("nn_oracle.c",) if os.path.exists(os.path.join(_HERE, s))]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", _LIB] + srcs + ["-lm"]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        for name, args, res in [
+            ("orc_apply_A", [_I, _I, _I, _D, _D, _P, _P, _P], None),
+            ("orc_line_solve", [_I, _I, _I, _D, _D, _P, _P, _P], None),
+            ("orc_residual", [_I, _I, _I, _D, _D, _P, _P, _P, _P], None),
+            ("orc_smooth", [_I, _I, _I, _D, _D, _P, _D, _P, _P, _P], None),
+            ("orc_restrict", [_I, _I, _I, _P, _P], None),
+            ("orc_prolongate_add", [_I, _I, _I, _P, _P], None),
+            ("orc_coarsen_v", [_I, _I, _P, _P], None),
+            ("orc_vcycle", [_I, _I, _I, _I, _D, _D, _P, _I, _I, _I, _D, _P, _P], _I),
+            ("orc_mg_solve", [_I, _I, _I, _I, _D, _D, _P, _I, _I, _I, _D, _D, _I, _P, _P, _P, _P], _I),
+            ("orc_cg_solve", [_I, _I, _I, _D, _D, _P, _D, _I, _P, _P, _P, _P], _I),
+            ("orc_ir_solve", [_I, _I, _I, _I, _D, _D, _P, _I, _I, _I, _D, _D, _I, _P, _P, _P, _P], _I),
+        ]:
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _vcol(v, nx, ny) -> np.ndarray:
+    v = np.asarray(v, dtype=np.float64)
+    if v.ndim == 0:
+        v = np.full((ny, nx), float(v))
+    assert v.shape == (ny, nx), v.shape
+    return np.ascontiguousarray(v)
+
+
+def coefficients(omega2, hx, hy, hz, lambda2):
+    """Discrete coefficients of the flat-box operator (Sec. 2.1.1): cx = omega^2/hx^2,
+    cy = omega^2/hy^2 and v = omega^2 lambda^2/hz^2 (per column when lambda^2 is a field)."""
+    return omega2 / hx ** 2, omega2 / hy ** 2, omega2 * np.asarray(lambda2, dtype=np.float64) / hz ** 2
+
+
+def problem_coefficients(p):
+    """coefficients() for a workloads.Problem."""
+    return coefficients(p.omega2, p.hx, p.hy, p.hz, p.lambda2_field())
+
+
+def apply_A(x, cx, cy, v):
+    """y = A x, Sec. 2.1.1 (flat-box entries of Eq. (6)) with periodic x/y and Neumann z ends."""
+    x = _f64(x)
+    nz, ny, nx = x.shape
+    v = _vcol(v, nx, ny)
+    y = np.empty_like(x)
+    _load().orc_apply_A(nx, ny, nz, cx, cy, _ptr(v), _ptr(x), _ptr(y))
+    return y
+
+
+def line_solve(b, cx, cy, v):
+    """x = M^{-1} b, vertical line relaxation by the Thomas algorithm (Sec. 2.2)."""
+    b = _f64(b)
+    nz, ny, nx = b.shape
+    v = _vcol(v, nx, ny)
+    x = np.empty_like(b)
+    _load().orc_line_solve(nx, ny, nz, cx, cy, _ptr(v), _ptr(b), _ptr(x))
+    return x
+
+
+def residual(u, f, cx, cy, v):
+    """r = f - A u (Residual kernel, Sec. 3.1)."""
+    u, f = _f64(u), _f64(f)
+    nz, ny, nx = u.shape
+    v = _vcol(v, nx, ny)
+    r = np.empty_like(u)
+    _load().orc_residual(nx, ny, nz, cx, cy, _ptr(v), _ptr(u), _ptr(f), _ptr(r))
+    return r
+
+
+def smooth(u, f, cx, cy, v, rho):
+    """u + rho M^{-1}(f - A u), Eq. (11) "MultigridSmoother"."""
+    u, f = _f64(u), _f64(f)
+    nz, ny, nx = u.shape
+    v = _vcol(v, nx, ny)
+    out = np.empty_like(u)
+    _load().orc_smooth(nx, ny, nz, cx, cy, _ptr(v), rho, _ptr(u), _ptr(f), _ptr(out))
+    return out
+
+
+def restrict(rf):
+    """Cell-average restriction, horizontal only (Sec. 2.2)."""
+    rf = _f64(rf)
+    nz, nyf, nxf = rf.shape
+    fc = np.empty((nz, nyf // 2, nxf // 2))
+    _load().orc_restrict(nxf, nyf, nz, _ptr(rf), _ptr(fc))
+    return fc
+
+
+def prolongate_add(uc, uf):
+    """uf + P uc, horizontal bilinear interpolation of cell-centred data (Sec. 2.2)."""
+    uc = _f64(uc)
+    out = _f64(uf).copy()
+    nz, nyc, nxc = uc.shape
+    assert out.shape == (nz, 2 * nyc, 2 * nxc)
+    _load().orc_prolongate_add(nxc, nyc, nz, _ptr(uc), _ptr(out))
+    return out
+
+
+def coarsen_v(vf):
+    """Coarse-level vertical coefficient: average of the 2x2 children."""
+    vf = _f64(vf)
+    nyf, nxf = vf.shape
+    vc = np.empty((nyf // 2, nxf // 2))
+    _load().orc_coarsen_v(nxf, nyf, _ptr(vf), _ptr(vc))
+    return vc
+
+
+def vcycle(u, f, cx, cy, v, nlevels, nu_pre=2, nu_post=2, n_coarse=2, rho=0.8):
+    """One V-cycle of Algorithm 1 (generalised to nu_pre/nu_post smoothing steps)."""
+    u = _f64(u).copy()
+    f = _f64(f)
+    nz, ny, nx = u.shape
+    v = _vcol(v, nx, ny)
+    rc = _load().orc_vcycle(nx, ny, nz, nlevels, cx, cy, _ptr(v), nu_pre, nu_post, n_coarse,
+                            rho, _ptr(f), _ptr(u))
+    if rc != 0:
+        raise ValueError("bad multigrid arguments")
+    return u
+
+
+def mg_solve(f, cx, cy, v, nlevels, tol=1e-6, max_iter=100, u0=None, nu_pre=2, nu_post=2,
+             n_coarse=2, rho=0.8):
+    """V-cycles until ||r||/||r0|| < tol, Eq. (10). Returns (u, iters, history, converged)."""
+    f = _f64(f)
+    nz, ny, nx = f.shape
+    v = _vcol(v, nx, ny)
+    u = np.zeros_like(f) if u0 is None else _f64(u0).copy()
+    hist = np.zeros(max_iter + 1)
+    conv = ctypes.c_int(0)
+    it = _load().orc_mg_solve(nx, ny, nz, nlevels, cx, cy, _ptr(v), nu_pre, nu_post, n_coarse,
+                              rho, tol, max_iter, _ptr(f), _ptr(u), _ptr(hist),
+                              ctypes.byref(conv))
+    if it < 0:
+        raise ValueError("bad multigrid arguments")
+    return u, it, hist[: it + 1], bool(conv.value)
+
+
+def cg_solve(f, cx, cy, v, tol=1e-6, max_iter=1000, u0=None):
+    """Line-preconditioned CG (Sec. 2.2). Returns (u, iters, history, converged)."""
+    f = _f64(f)
+    nz, ny, nx = f.shape
+    v = _vcol(v, nx, ny)
+    u = np.zeros_like(f) if u0 is None else _f64(u0).copy()
+    hist = np.zeros(max_iter + 1)
+    conv = ctypes.c_int(0)
+    it = _load().orc_cg_solve(nx, ny, nz, cx, cy, _ptr(v), tol, max_iter, _ptr(f), _ptr(u),
+                              _ptr(hist), ctypes.byref(conv))
+    return u, it, hist[: it + 1], bool(conv.value)
+
+
+def ir_solve(f, cx, cy, v, nlevels, tol=1e-6, max_iter=100, u0=None, nu_pre=2, nu_post=2,
+             n_coarse=2, rho=0.8):
+    """Iterative refinement with one V-cycle per correction. Returns (u, iters, hist, conv)."""
+    f = _f64(f)
+    nz, ny, nx = f.shape
+    v = _vcol(v, nx, ny)
+    u = np.zeros_like(f) if u0 is None else _f64(u0).copy()
+    hist = np.zeros(max_iter + 1)
+    conv = ctypes.c_int(0)
+    it = _load().orc_ir_solve(nx, ny, nz, nlevels, cx, cy, _ptr(v), nu_pre, nu_post, n_coarse,
+                              rho, tol, max_iter, _ptr(f), _ptr(u), _ptr(hist),
+                              ctypes.byref(conv))
+    if it < 0:
+        raise ValueError("bad multigrid arguments")
+    return u, it, hist[: it + 1], bool(conv.value)
