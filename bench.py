@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark: multigrid solve time to a 1e-6 relative residual on the mid-size problem of the
+paper's family (512 x 512 x 128 cells, lambda^2(x, y) varying, N(0,1) right-hand side, 7-level
+V(2,2) tensor-product multigrid with vertical line smoothing), FP64-accurate arithmetic.
+
+One step = one complete solve from a zero initial guess (every kernel of the multigrid path:
+Smooth with fused residual norm, Residual, RestrictSmooth, Prolongate, the device-side
+convergence test), inputs resident in HBM. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank solves its own copy of the problem:
+the path has no data-parallel exchange, so ranks are independent replicas ("replicas only").
+`--impl reference` times the oracle (plain FP64 C, test infrastructure) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1402_3545_gb300 import workloads  # noqa: E402
+
+METRIC = "MG solve ms to 1e-6 rel. residual & % of HBM peak, FP64 vs mixed/learned"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="time the solves only (no kernel timing, e2e, variants or CPU baseline): "
+                         "the command the ncu launch-list profile runs")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": HBM_FALLBACK_GBS, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def oracle_counts():
+    path = os.path.join(ROOT, "tests", "golden", "oracle_counts.txt")
+    out = {}
+    if os.path.exists(path):
+        for line in open(path):
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v = line.split(None, 1)
+            out[k] = float(v)
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_sample(p, f, iters_hint):
+    """The oracle as it stands, on the host: one V-cycle and one residual on the full grid; the
+    solve estimate is t_res + iters * (t_cycle + t_res) with the oracle's own iteration count."""
+    import oracle
+    cx, cy, v = oracle.problem_coefficients(p)
+    u = np.zeros_like(f)
+    t0 = time.perf_counter()
+    r = oracle.residual(u, f, cx, cy, v)
+    t_res = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.vcycle(u, f, cx, cy, v, p.nlevels)
+    t_cycle = time.perf_counter() - t0
+    del r
+    counts = oracle_counts()
+    iters = int(counts.get("mid_iters", iters_hint))
+    est_ms = 1e3 * (t_res + iters * (t_cycle + t_res))
+    return est_ms, {"t_cycle_s": round(t_cycle, 3), "t_residual_s": round(t_res, 3), "oracle_iters": iters}
+
+
+def run_reference(args, rank, world):
+    p = workloads.mid()
+    f = p.rhs()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    vals, info = [], None
+    for s in range(args.warmup + args.steps):
+        est, info = cpu_baseline_sample(p, f, 6)
+        if s >= args.warmup:
+            vals.append(est)
+    value = float(np.mean(vals))
+    sample = (f"one oracle V(2,2) cycle + one residual on the full {p.nx}x{p.ny}x{p.nz} grid per step, "
+              f"scaled to a full solve with the oracle's iteration count ({info['oracle_iters']})")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 3),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": p.name, "nx": p.nx, "ny": p.ny, "nz": p.nz, "levels": p.nlevels,
+                       "solver": "V(2,2), rho 0.8, 2 coarse steps", "tol": 1e-6},
+            "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": sample, **info},
+            "e2e": {"value": round(value, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_1402_3545_gb300 import tpmg
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = workloads.mid()
+    f = p.rhs()
+    n = p.n
+    op = tpmg.Operator.from_problem(p)
+    prec = tpmg.DW
+    prm = tpmg.default_params(prec=prec, tol=1e-6, max_iter=100)
+    tpmg.op_reserve(op.op, prec)
+    fd = torch.from_numpy(f).to(dev)
+    u = torch.zeros_like(fd)
+    stream = torch.cuda.current_stream()
+
+    def solve():
+        u.zero_()
+        return tpmg.mg_solve(op.op, prm, fd, u, n)
+
+    for _ in range(max(args.warmup, 3)):
+        res = solve()
+    assert res["converged"], res
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    smi_index = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
+    sampler = ClockSampler(smi_index)
+    sampler.start()
+    time.sleep(0.3)
+    k0 = tpmg.kernel_launches()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        res = solve()
+        iters.append(res["iters"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = tpmg.kernel_launches() - k0
+    clocks = sampler.stop()
+    elapsed = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    ms_per_step = elapsed / args.steps
+    value = elapsed / (args.steps * world)  # ms per solve over all replicas' solves
+    if args.solve_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": round(value, 4), "unit": "ms", "iters": iters[-1],
+                              "gpu_launches": int(launches), "solve_only": True}), flush=True)
+        op.close()
+        return
+
+    # dominant kernel: the finest-level Smooth (4 of the 5 fine-level sweeps of each cycle)
+    t_smooth = tpmg.time_kernel(op.op, prec, tpmg.K_SMOOTH, reps=20)
+    peaks, peak_kind = measured_peaks()
+    bytes_smooth = 3 * 8 * n  # read u, f; write u' (8-byte values)
+    achieved = bytes_smooth / (t_smooth * 1e-3) / 1e9
+    kernel_ms = {name: round(tpmg.time_kernel(op.op, prec, kid, reps=10), 4) for name, kid in [
+        ("residual", tpmg.K_RESIDUAL), ("restrict_smooth", tpmg.K_RESTRICT_SMOOTH),
+        ("prolongate", tpmg.K_PROLONGATE), ("cg_spmv", tpmg.K_CG_SPMV), ("cg_tridiag", tpmg.K_CG_TRIDIAG)]}
+    kernel_ms["smooth"] = round(t_smooth, 4)
+    n_smooth = 4 * iters[-1] + 1
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+                "kernel": "k_smooth<PolDW> (finest level)", "peak_source": peak_kind,
+                "bytes_per_launch": bytes_smooth, "ms_per_launch": round(t_smooth, 4),
+                "share_of_solve": round(n_smooth * t_smooth / ms_per_step, 3)}
+
+    # end to end through the public API with host buffers: H2D of f, solve, D2H of u each step
+    f_h = torch.from_numpy(f).pin_memory()
+    u_h = torch.empty_like(f_h).pin_memory()
+    for _ in range(2):
+        fd.copy_(f_h, non_blocking=True)
+        solve()
+        u_h.copy_(u, non_blocking=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        fd.copy_(f_h, non_blocking=True)
+        solve()
+        u_h.copy_(u, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+
+    # the other precisions on the same problem (one solve each, after a warm-up solve)
+    variants = {}
+    for name, vprec, tol in [("f64_native", tpmg.F64, 1e-6), ("mixed_fp32_inner", tpmg.MIXED, 1e-6),
+                             ("mixed_fp32_inner_1e-10", tpmg.MIXED, 1e-10)]:
+        vp = tpmg.default_params(prec=vprec, tol=tol, max_iter=100)
+        for _ in range(2):
+            u.zero_()
+            r = tpmg.mg_solve(op.op, vp, fd, u, n)
+        variants[name] = {"ms": round(r["ms"], 3), "iters": r["iters"], "rel_res": r["rel_res"]}
+    u.zero_()
+    r = tpmg.cg_solve(op.op, tpmg.default_params(prec=tpmg.DW, tol=1e-6, max_iter=5000), fd, u, n)
+    variants["cg_dw"] = {"ms": round(r["ms"], 3), "iters": r["iters"], "rel_res": r["rel_res"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, info = cpu_baseline_sample(p, f, iters[-1])
+        cpu = {"value": round(est, 3), "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": (f"one oracle V(2,2) cycle + one residual on the full {p.nx}x{p.ny}x{p.nz} grid, "
+                          f"scaled to a full solve with the oracle's iteration count"), **info}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "dw (FP64 storage, double-word fp32 pair arithmetic)", "data": "synthetic",
+                "config": {"workload": p.name, "nx": p.nx, "ny": p.ny, "nz": p.nz, "levels": op.L,
+                           "solver": "V(2,2), rho 0.8, 2 coarse steps", "tol": 1e-6, "precision": "DW",
+                           "parallelism": f"replicas{world}",
+                           "l2": "inputs larger than L2 (268 MB per FP64 field > 129 MB)"},
+                "iters": iters[-1], "roofline": roofline, "kernel_ms": kernel_ms, "variants": variants,
+                "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": 8 * n,
+                        "d2h_bytes_per_step": 8 * n},
+                "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches)}
+        print(json.dumps(line), flush=True)
+    op.close()
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    run_ours(args, rank, world, dist)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

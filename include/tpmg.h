@@ -1,0 +1,200 @@
+/*
+ * tpmg.h -- C ABI of the GB300 tensor-product multigrid / line-preconditioned CG library for the
+ * strongly vertically anisotropic elliptic problem of Mueller, Scheichl & Vainikko, "Petascale
+ * elliptic solvers for anisotropic PDEs on GPU clusters" (arXiv:1402.3545).
+ *
+ * Problem (Sec. 2.1.1, flat-box form of Eq. (6) "TridiagonalPDE"):
+ *   -omega^2 (d_xx u + d_yy u + lambda^2(x,y) d_zz u) + u = f
+ * on an nx x ny x nz cell-centred grid, periodic in x and y, homogeneous Neumann at the bottom and
+ * top (Sec. 2.1). The discrete operator is the 7-point stencil
+ *   (A u)_ijk = (1 + 2cx + 2cy + v_ij n_k) u_ijk - cx (u_{i-1,j,k} + u_{i+1,j,k})
+ *               - cy (u_{i,j-1,k} + u_{i,j+1,k}) - v_ij (u_{i,j,k-1} + u_{i,j,k+1})
+ * with cx = omega^2/hx^2, cy = omega^2/hy^2, v_ij = omega^2 lambda_ij^2/hz^2, n_k the number of
+ * vertical neighbours of cell k (2 inside, 1 at a Neumann end) and the missing neighbours dropped.
+ *
+ * Conventions shared by every entry point:
+ *  - Fields are device arrays of nz*ny*nx values, x fastest: element (i,j,k) at (k*ny + j)*nx + i
+ *    (x-contiguous like Eq. (13) "MemoryMapSingleGPU"; k outermost so horizontal planes are
+ *    contiguous). The caller owns them; they must not overlap unless an entry point says so.
+ *  - Multigrid levels are numbered as in Sec. 2.2: 1 = coarsest ... L = finest. Level l has
+ *    nx/2^(L-l) x ny/2^(L-l) x nz cells, cx and cy divided by 4^(L-l), and v averaged over the
+ *    2x2 children of each coarse column.
+ *  - Element type of a field argument by precision: TPMG_F64 and TPMG_DW: double; TPMG_F32:
+ *    float; TPMG_MIXED (solvers only): double. TPMG_DW computes in double-word ("float-float")
+ *    arithmetic on the FP32 units (about 2^-47 relative accuracy per operation) and converts at the
+ *    boundary through library-owned workspace; TPMG_F64 computes in native FP64.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Every entry point is stream
+ *    ordered; only the solvers and tpmg_op_reserve synchronise (solvers: once per iteration, to
+ *    read the convergence flag).
+ *  - Errors are returned as a tpmg_status, never thrown; nothing aborts the process. A failed
+ *    CUDA call yields TPMG_ERR_CUDA and tpmg_last_error() describes it.
+ *  - Workspace (coarse levels, ping-pong buffers, precision-conversion buffers, partial sums) is
+ *    owned by the operator, allocated with cudaMalloc on the first call that needs it (or by
+ *    tpmg_op_reserve) and freed by tpmg_destroy_operator. Call tpmg_op_reserve before capturing
+ *    library calls into a CUDA graph.
+ *  - One operator must not be used by two host threads or two streams at the same time.
+ */
+#ifndef TPMG_H
+#define TPMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TPMG_OK = 0,
+    TPMG_ERR_ARG = 1,           /* invalid argument (sizes, level, precision, NULL pointer) */
+    TPMG_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    TPMG_ERR_OOM = 3,           /* workspace allocation failed */
+    TPMG_ERR_NOT_CONVERGED = 4, /* max_iter reached; u holds the last iterate */
+    TPMG_ERR_NONFINITE = 5,     /* NaN or Inf met in a norm or dot product; u holds the last iterate */
+    TPMG_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+    TPMG_ERR_NN_REJECTED = 7    /* the learned preconditioner stage was rejected (fallback used) */
+} tpmg_status;
+
+typedef enum {
+    TPMG_F64 = 0,  /* FP64 storage, native FP64 arithmetic */
+    TPMG_F32 = 1,  /* FP32 storage and arithmetic */
+    TPMG_DW = 2,   /* FP64 storage at the interface, double-word (float-float) arithmetic inside */
+    TPMG_MIXED = 3 /* solvers: FP64-accurate outer residual and correction (double-word), FP32
+                      inner V-cycles (iterative refinement) */
+} tpmg_precision;
+
+typedef struct tpmg_grid tpmg_grid; /* opaque, library owned */
+typedef struct tpmg_op tpmg_op;     /* opaque, library owned */
+
+/* Grid of nx x ny x nz cells with `nlevels` multigrid levels (0 = halve nx and ny while both stay
+ * even and the smaller one exceeds 8). nx and ny must be divisible by 2^(nlevels-1);
+ * 1 <= nz <= 256; nlevels <= 16. Sec. 2.2 (horizontal-only semicoarsening, nz fixed). */
+tpmg_status tpmg_create_grid(int nx, int ny, int nz, int nlevels, tpmg_grid** out);
+tpmg_status tpmg_destroy_grid(tpmg_grid* g);
+/* Number of levels, and the horizontal size of `level` (1 = coarsest). */
+int tpmg_grid_nlevels(const tpmg_grid* g);
+tpmg_status tpmg_grid_level_size(const tpmg_grid* g, int level, int* nx, int* ny);
+
+/* Operator -omega2 (Lap_h + lambda^2 d_zz) + I on grid g with mesh widths hx, hy, hz
+ * (Sec. 2.1.1). lambda2_col is a HOST array of ny*nx values lambda^2 per column (index j*nx + i),
+ * copied at creation; when NULL the constant `lambda2` is used. Builds the per-level coefficients
+ * on the current CUDA device (the operator is bound to that device). The grid may be destroyed
+ * afterwards. */
+tpmg_status tpmg_create_operator(const tpmg_grid* g, double omega2, double hx, double hy, double hz,
+                                 double lambda2, const double* lambda2_col, tpmg_op** out);
+tpmg_status tpmg_destroy_operator(tpmg_op* op);
+/* Allocates now the workspace a solver in precision `prec` needs (see the conventions above). */
+tpmg_status tpmg_op_reserve(tpmg_op* op, tpmg_precision prec);
+/* Discrete coefficients of `level`: cx, cy and the HOST copy of v (ny_l*nx_l values), any NULL. */
+tpmg_status tpmg_op_level_coefficients(const tpmg_op* op, int level, double* cx, double* cy,
+                                       double* v_host);
+
+/* ---------------------------------------------------------------- single applications
+ * Each applies one kernel of the method on `level` (1..L). x, y, b, u, f, r, u_out are device
+ * fields of that level in the element type of `prec` (TPMG_F64, TPMG_F32 or TPMG_DW). */
+
+/* y = A x, Eq. (9) "SpMVPrec" (SpMV). x and y must not overlap. */
+tpmg_status tpmg_apply_A(tpmg_op* op, int level, tpmg_precision prec, const void* x, void* y,
+                         void* stream);
+/* x = M^{-1} b with M the vertical line relaxation (block diagonal of the column blocks A_T of
+ * Eq. (6)), one Thomas solve per column: Eq. (9) (Preconditioner), Sec. 2.2. */
+tpmg_status tpmg_line_solve(tpmg_op* op, int level, tpmg_precision prec, const void* b, void* x,
+                            void* stream);
+/* u_out = u + rho M^{-1}(f - A u): one block-Jacobi smoothing step, Eq. (11)
+ * "MultigridSmoother". If norm_out (a DEVICE double) is not NULL it receives ||f - A u||_2. */
+tpmg_status tpmg_smooth(tpmg_op* op, int level, tpmg_precision prec, double rho, const void* u,
+                        const void* f, void* u_out, double* norm_out, void* stream);
+/* r = f - A u (kernel "Residual", Sec. 3.1); optional ||r||_2 into the DEVICE double norm_out. */
+tpmg_status tpmg_residual(tpmg_op* op, int level, tpmg_precision prec, const void* u,
+                          const void* f, void* r, double* norm_out, void* stream);
+/* Fused restriction and first smoothing step on coarse level `level` (< L) (kernel
+ * "RestrictSmooth", Algorithm 1): f_c = R r_f (cell average of the 2x2 children of the residual
+ * r_f of level+1), u_c = rho M_c^{-1} f_c. */
+tpmg_status tpmg_restrict_smooth(tpmg_op* op, int level, tpmg_precision prec, double rho,
+                                 const void* r_fine, void* f_c, void* u_c, void* stream);
+/* u_f += P u_c on fine level `level` (> 1), P the cell-centred bilinear interpolation from level-1
+ * (kernel "Prolongate", Sec. 2.2). */
+tpmg_status tpmg_prolongate(tpmg_op* op, int level, tpmg_precision prec, const void* u_c, void* u_f,
+                            void* stream);
+/* Fused CG kernels on the finest level (Sec. 3.1, "Conjugate Gradient"):
+ * spmv:    u += alpha p; p = z + beta p; q = A z + beta q; *sigma_out = <p, q>
+ * tridiag: r -= alpha q; z = M^{-1} r; *rr_out = <r, r>; *rz_out = <r, z>
+ * The scalar outputs are DEVICE doubles. u, p, z, q, r are fields of the finest level; in TPMG_DW
+ * the fields are double and converted in and out around the fused kernel. */
+tpmg_status tpmg_cg_fused_spmv(tpmg_op* op, tpmg_precision prec, double alpha, double beta, void* u,
+                               void* p, const void* z, void* q, double* sigma_out, void* stream);
+tpmg_status tpmg_cg_fused_tridiag(tpmg_op* op, tpmg_precision prec, double alpha, void* r,
+                                  const void* q, void* z, double* rr_out, double* rz_out,
+                                  void* stream);
+
+/* ---------------------------------------------------------------- solvers */
+typedef struct {
+    int nu_pre;      /* pre-smoothing steps per level (>= 1); the first one on coarse levels is the
+                        fused RestrictSmooth */
+    int nu_post;     /* post-smoothing steps per level (>= 0) */
+    int n_coarse;    /* smoothing steps on the coarsest level (>= 1), Sec. 2.2 last paragraph */
+    int max_iter;    /* V-cycles or CG iterations */
+    double rho;      /* relaxation of the block-Jacobi smoother, Eq. (11) */
+    double tol;      /* stop when ||f - A u|| / ||f - A u_0|| < tol, Eq. (10) */
+    tpmg_precision prec;
+    int use_graph;   /* 1: replay each iteration from a CUDA graph (default), 0: plain launches */
+} tpmg_params;
+
+typedef struct {
+    int iters;          /* V-cycles (or CG iterations) done */
+    int converged;      /* 1 if the tolerance was met */
+    double rel_res;     /* final ||r||/||r0|| as the solver measured it */
+    double r0;          /* ||f - A u_0|| */
+    double* history;    /* caller's HOST array of history_len doubles, or NULL: relative residual
+                           before the first and after each iteration */
+    int history_len;
+    double ms;          /* device time of the solve in milliseconds (CUDA events on `stream`) */
+} tpmg_info;
+
+/* V(2,2), 2 coarse steps, rho 0.8, tol 1e-6, max_iter 100, TPMG_DW, graphs on. */
+void tpmg_default_params(tpmg_params* p);
+
+/* Multigrid solve (Sec. 2.2, Algorithm 1 with nu_pre/nu_post smoothing steps): V-cycles from the
+ * initial guess in u until Eq. (10) holds. f and u are finest-level device fields (double for
+ * TPMG_F64, TPMG_DW and TPMG_MIXED, float for TPMG_F32). TPMG_MIXED runs iterative refinement:
+ * r = f - A u in double-word arithmetic (stored FP32), one FP32 V-cycle for A e = r from e = 0,
+ * u += e in double-word arithmetic. Returns TPMG_OK, TPMG_ERR_NOT_CONVERGED or
+ * TPMG_ERR_NONFINITE (u then holds the last iterate), or an argument/CUDA error. */
+tpmg_status tpmg_mg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, void* u,
+                          tpmg_info* info, void* stream);
+/* One V-cycle from u (in place), for testing a cycle against a reference. */
+tpmg_status tpmg_vcycle(tpmg_op* op, const tpmg_params* prm, const void* f, void* u, void* stream);
+/* Line-preconditioned CG (Sec. 2.2) with the fused kernels of Sec. 3.1. prec: TPMG_F64, TPMG_F32
+ * or TPMG_DW (TPMG_MIXED is rejected). Same return values as tpmg_mg_solve. */
+tpmg_status tpmg_cg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, void* u,
+                          tpmg_info* info, void* stream);
+
+/* ---------------------------------------------------------------- profiling */
+typedef enum {
+    TPMG_K_SMOOTH = 0,          /* finest level Smooth */
+    TPMG_K_RESIDUAL = 1,        /* finest level Residual */
+    TPMG_K_APPLY_A = 2,         /* finest level y = A x */
+    TPMG_K_LINE_SOLVE = 3,      /* finest level x = M^{-1} b */
+    TPMG_K_RESTRICT_SMOOTH = 4, /* level L-1 RestrictSmooth from level L */
+    TPMG_K_PROLONGATE = 5,      /* level L-1 -> L Prolongate */
+    TPMG_K_CG_SPMV = 6,         /* fused CG SpMV on the finest level */
+    TPMG_K_CG_TRIDIAG = 7,      /* fused CG Tridiag on the finest level */
+    TPMG_K_COUNT = 8
+} tpmg_kernel;
+/* Launches kernel `k` of precision `prec` (TPMG_F64, TPMG_F32 or TPMG_DW) `reps` times on the
+ * operator's own workspace buffers of that precision (whatever they hold, e.g. after a solve) and
+ * writes the mean duration of one launch in ms (CUDA events on `stream`) to *ms. Synchronises
+ * `stream`. Allocates the workspace of `prec` if needed. */
+tpmg_status tpmg_time_kernel(tpmg_op* op, tpmg_precision prec, tpmg_kernel k, int reps, double* ms,
+                             void* stream);
+/* Number of kernel launches this library has issued since the process started (a graph replay
+ * counts every kernel node it contains). */
+unsigned long long tpmg_kernel_launches(void);
+
+const char* tpmg_status_string(tpmg_status s);
+/* Message of the last error in the calling thread ("" if none). */
+const char* tpmg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPMG_H */

@@ -28,9 +28,15 @@ def build(force: bool = False) -> str:
     """Compile the C oracle into oracle/liboracle.so with the host gcc (no -march flags)."""
     srcs = [_SRC] + [os.path.join(_HERE, s) for s in ("nn_oracle.c",) if os.path.exists(os.path.join(_HERE, s))]
     newest = max(os.path.getmtime(s) for s in srcs)
+    import platform
+    stamp = _LIB + ".host"
+    if not os.path.exists(stamp) or open(stamp).read() != platform.machine():
+        force = True  # built on another host architecture
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", _LIB] + srcs + ["-lm"]
         subprocess.run(cmd, check=True)
+        with open(stamp, "w") as fh:
+            fh.write(platform.machine())
     return _LIB
 
 

@@ -1,0 +1,1134 @@
+// api.cu -- the C ABI of include/tpmg.h: grid and operator objects, operator-owned workspace, the
+// single-application entry points and the solvers (multigrid V-cycle, mixed-precision iterative
+// refinement, fused line-preconditioned CG).
+//
+// Solver control lives on the device: the finalize kernels compute the norms, CG's alpha/beta and
+// the convergence decision of Eq. (10) and raise a `done` flag that makes every later kernel of the
+// iteration return at once. One iteration is captured into a CUDA graph and replayed; the host
+// reads the flag once per iteration (one 64-byte device-to-host copy).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "tpmg.h"
+
+using namespace tpmg;
+
+static constexpr int MAXL = 16;
+static constexpr int MAX_NZ = 256;
+static constexpr double DW_KAPPA_MAX = 4000.0;
+
+static thread_local std::string g_err;
+
+static tpmg_status set_err(tpmg_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return set_err(TPMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+#define TRY(expr)                                                                                 \
+    do {                                                                                          \
+        tpmg_status s_ = (expr);                                                                  \
+        if (s_ != TPMG_OK) return s_;                                                             \
+    } while (0)
+
+struct tpmg_grid {
+    int nx, ny, nz, L;
+    int lnx[MAXL + 1], lny[MAXL + 1];
+};
+
+// the device buffers of one precision's multigrid hierarchy (level index 1..L)
+struct Hier {
+    bool ready = false;
+    void* u[MAXL + 1] = {};
+    void* ub[MAXL + 1] = {};
+    void* f[MAXL + 1] = {};
+    void* r[MAXL + 1] = {};
+};
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void*> key;
+    unsigned long long nkernels = 0;  // kernel nodes captured into the graph
+};
+
+struct tpmg_op {
+    tpmg_grid g;
+    int device = 0;
+    double omega2 = 0, hx = 0, hy = 0, hz = 0;
+    double cx[MAXL + 1], cy[MAXL + 1];
+    std::vector<double> v_host[MAXL + 1];
+    double* v64[MAXL + 1] = {};
+    float* v32[MAXL + 1] = {};
+    float2* vdw[MAXL + 1] = {};
+    Hier hier[3];  // by policy id (F64, F32, DW)
+    void* finv[3][MAXL + 1] = {};  // Thomas factors 1/m_k per policy and level
+    void* fw[3][MAXL + 1] = {};    // Thomas factors v/m_k
+    int percol[MAXL + 1] = {};     // 1 if lambda^2 varies over the level (factors per cell)
+    double kappa_M[MAXL + 1] = {}; // condition number of the level's column blocks
+    int lsw_dw = 1;                // the double-word solver uses native FP64 below this level
+    bool fac_ready[3] = {false, false, false};
+    void* cgbuf[3][4] = {};  // r, z, p, q per policy
+    void* io[4] = {};        // DW conversion buffers for single applications (finest-level size)
+    double* partials = nullptr;
+    int max_parts = 0;
+    Scalars* sc = nullptr;
+    Scalars* sc_host = nullptr;  // pinned
+    double* history = nullptr;
+    int history_cap = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    GraphCache graphs[8];
+};
+
+// ---------------------------------------------------------------- helpers
+static size_t lvl_cells(const tpmg_op* op, int l) {
+    return (size_t)op->g.lnx[l] * op->g.lny[l] * op->g.nz;
+}
+template <class P>
+static const typename P::S* vptr(const tpmg_op* op, int l);
+template <>
+const double* vptr<PolF64>(const tpmg_op* op, int l) { return op->v64[l]; }
+template <>
+const float* vptr<PolF32>(const tpmg_op* op, int l) { return op->v32[l]; }
+template <>
+const float2* vptr<PolDW>(const tpmg_op* op, int l) { return op->vdw[l]; }
+
+template <class P>
+static Lv<P> level_view(const tpmg_op* op, int l) {
+    Lv<P> L;
+    L.nx = op->g.lnx[l];
+    L.ny = op->g.lny[l];
+    L.nz = op->g.nz;
+    L.cx = op->cx[l];
+    L.cy = op->cy[l];
+    L.v = vptr<P>(op, l);
+    L.finv = (const typename P::S*)op->finv[P::id][l];
+    L.fw = (const typename P::S*)op->fw[P::id][l];
+    L.fac_percol = op->percol[l];
+    return L;
+}
+
+static tpmg_status dalloc(void** p, size_t bytes) {
+    if (*p) return TPMG_OK;
+    cudaError_t e = cudaMalloc(p, bytes < 256 ? 256 : bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return set_err(TPMG_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    cudaMemset(*p, 0, bytes < 256 ? 256 : bytes);  // defined contents for profiling runs
+    return TPMG_OK;
+}
+static void dfree(void*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+static size_t elem_bytes(int pid) { return pid == 1 ? 4 : 8; }
+
+static tpmg_status ensure_common(tpmg_op* op) {
+    if (!op->partials) {
+        op->max_parts = max_partials(op->g.nx, op->g.ny);
+        TRY(dalloc((void**)&op->partials, sizeof(double) * 2 * (size_t)op->max_parts));
+    }
+    if (!op->sc) TRY(dalloc((void**)&op->sc, sizeof(Scalars)));
+    if (!op->sc_host) CK(cudaMallocHost((void**)&op->sc_host, sizeof(Scalars)));
+    return TPMG_OK;
+}
+
+static void invalidate_graphs(tpmg_op* op) {
+    for (auto& gc : op->graphs) {
+        if (gc.exec) cudaGraphExecDestroy(gc.exec);
+        gc.exec = nullptr;
+        gc.key.clear();
+    }
+}
+
+static tpmg_status ensure_history(tpmg_op* op, int n) {
+    if (n <= op->history_cap) return TPMG_OK;
+    if (op->history) {
+        cudaFree(op->history);
+        op->history = nullptr;
+        invalidate_graphs(op);
+    }
+    int cap = n < 1024 ? 1024 : n;
+    TRY(dalloc((void**)&op->history, sizeof(double) * cap));
+    op->history_cap = cap;
+    return TPMG_OK;
+}
+
+// Thomas factors of every level in precision pid, computed once (they depend on the operator only)
+static tpmg_status ensure_factors(tpmg_op* op, int pid) {
+    if (op->fac_ready[pid]) return TPMG_OK;
+    const size_t eb = elem_bytes(pid);
+    for (int l = 1; l <= op->g.L; ++l) {
+        size_t nvals = op->percol[l] ? lvl_cells(op, l) : (size_t)op->g.nz;
+        TRY(dalloc(&op->finv[pid][l], nvals * eb));
+        TRY(dalloc(&op->fw[pid][l], nvals * eb));
+        switch (pid) {
+            case 0: launch_factors<PolF64>(level_view<PolF64>(op, l), (double*)op->finv[0][l], (double*)op->fw[0][l], op->percol[l], 0); break;
+            case 1: launch_factors<PolF32>(level_view<PolF32>(op, l), (float*)op->finv[1][l], (float*)op->fw[1][l], op->percol[l], 0); break;
+            default: launch_factors<PolDW>(level_view<PolDW>(op, l), (float2*)op->finv[2][l], (float2*)op->fw[2][l], op->percol[l], 0); break;
+        }
+    }
+    CK(cudaDeviceSynchronize());
+    op->fac_ready[pid] = true;
+    return TPMG_OK;
+}
+
+// hierarchy of precision pid; the finest level's u and f are allocated only when `own_fine`
+// (DW: internal copies of the caller's FP64 fields; mixed inner FP32 cycle: e and r).
+static tpmg_status ensure_hier(tpmg_op* op, int pid, bool own_fine) {
+    TRY(ensure_factors(op, pid));
+    Hier& h = op->hier[pid];
+    const size_t eb = elem_bytes(pid);
+    const int L = op->g.L;
+    for (int l = 1; l <= L; ++l) {
+        size_t bytes = lvl_cells(op, l) * eb;
+        TRY(dalloc(&h.ub[l], bytes));
+        TRY(dalloc(&h.r[l], bytes));
+        if (l < L || own_fine) {
+            TRY(dalloc(&h.u[l], bytes));
+            TRY(dalloc(&h.f[l], bytes));
+        }
+    }
+    h.ready = true;
+    return ensure_common(op);
+}
+
+static tpmg_status ensure_io(tpmg_op* op) {
+    size_t bytes = lvl_cells(op, op->g.L) * sizeof(float2);
+    for (int t = 0; t < 4; ++t) TRY(dalloc(&op->io[t], bytes));
+    return ensure_common(op);
+}
+
+static tpmg_status ensure_cg(tpmg_op* op, int pid) {
+    size_t bytes = lvl_cells(op, op->g.L) * elem_bytes(pid);
+    for (int t = 0; t < 4; ++t) TRY(dalloc(&op->cgbuf[pid][t], bytes));
+    if (pid == 2) TRY(ensure_hier(op, 2, true));  // DW fine u, f copies live in the DW hierarchy
+    return ensure_common(op);
+}
+
+static tpmg_status check_level(const tpmg_op* op, int level) {
+    if (!op) return set_err(TPMG_ERR_ARG, "NULL operator");
+    if (level < 1 || level > op->g.L) return set_err(TPMG_ERR_ARG, "level out of range");
+    return TPMG_OK;
+}
+static int pid_of(tpmg_precision p) { return p == TPMG_F64 ? 0 : (p == TPMG_F32 ? 1 : 2); }
+
+// ---------------------------------------------------------------- the V-cycle (Algorithm 1)
+// Host-side orchestration of one cycle. Levels >= lsw run in policy PF, the coarser ones in PC
+// (the double-word solver runs its coarsest, ill-conditioned levels in native FP64; every other
+// solver uses one policy, lsw = 1). The finest level's first smoothing step is done by the caller
+// (the solver fuses the convergence norm into it); `rest` continues from there.
+template <class PF, class PC>
+struct Cycle {
+    typedef typename PF::S SF;
+    typedef typename PC::S SC;
+    tpmg_op* op;
+    const tpmg_params* prm;
+    cudaStream_t s;
+    const int* done;
+    int lsw;
+    void* u[MAXL + 1];
+    void* ub[MAXL + 1];
+    void* f[MAXL + 1];
+    void* r[MAXL + 1];
+
+    Cycle(tpmg_op* o, const tpmg_params* p, cudaStream_t st, const int* d, int lsw_)
+        : op(o), prm(p), s(st), done(d), lsw(lsw_) {
+        for (int l = 0; l <= MAXL; ++l) {
+            Hier& h = op->hier[l >= lsw ? PF::id : PC::id];
+            u[l] = h.u[l];
+            ub[l] = h.ub[l];
+            f[l] = h.f[l];
+            r[l] = h.r[l];
+        }
+    }
+    bool hi(int l) const { return l >= lsw; }
+    void smooth(int l, void*& cur, void*& oth, double* parts) {
+        if (hi(l))
+            launch_smooth<PF>(level_view<PF>(op, l), prm->rho, (const SF*)cur, (const SF*)f[l], (SF*)oth, parts, done, s);
+        else
+            launch_smooth<PC>(level_view<PC>(op, l), prm->rho, (const SC*)cur, (const SC*)f[l], (SC*)oth, parts, done, s);
+        void* t = cur;
+        cur = oth;
+        oth = t;
+    }
+    void residual(int l, const void* cur) {
+        if (hi(l))
+            launch_residual<PF, PF>(level_view<PF>(op, l), (const SF*)cur, (const SF*)f[l], (SF*)r[l], nullptr, done, s);
+        else
+            launch_residual<PC, PC>(level_view<PC>(op, l), (const SC*)cur, (const SC*)f[l], (SC*)r[l], nullptr, done, s);
+    }
+    // coarse level l from the residual of level l+1
+    void restrict_smooth(int l, void* cur) {
+        if (hi(l))
+            launch_restrict_smooth<PF, PF>(level_view<PF>(op, l), prm->rho, (const SF*)r[l + 1], (SF*)f[l], (SF*)cur, done, s);
+        else if (hi(l + 1))
+            launch_restrict_smooth<PF, PC>(level_view<PC>(op, l), prm->rho, (const SF*)r[l + 1], (SC*)f[l], (SC*)cur, done, s);
+        else
+            launch_restrict_smooth<PC, PC>(level_view<PC>(op, l), prm->rho, (const SC*)r[l + 1], (SC*)f[l], (SC*)cur, done, s);
+    }
+    // fine level l += P (level l-1)
+    void prolongate(int l, const void* uc, void* cur) {
+        const int nxc = op->g.lnx[l - 1], nyc = op->g.lny[l - 1], nz = op->g.nz;
+        if (hi(l - 1))
+            launch_prolongate<PF, PF>(nxc, nyc, nz, (const SF*)uc, (SF*)cur, done, s);
+        else if (hi(l))
+            launch_prolongate<PC, PF>(nxc, nyc, nz, (const SC*)uc, (SF*)cur, done, s);
+        else
+            launch_prolongate<PC, PC>(nxc, nyc, nz, (const SC*)uc, (SC*)cur, done, s);
+    }
+    // coarse level l: RestrictSmooth from level l+1's residual, then the rest of the cycle
+    void* coarse(int l) {
+        void* cur = u[l];
+        void* oth = ub[l];
+        restrict_smooth(l, cur);
+        if (l == 1) {
+            for (int t = 1; t < prm->n_coarse; ++t) smooth(l, cur, oth, nullptr);
+            return cur;
+        }
+        for (int t = 1; t < prm->nu_pre; ++t) smooth(l, cur, oth, nullptr);
+        residual(l, cur);
+        void* uc = coarse(l - 1);
+        prolongate(l, uc, cur);
+        for (int t = 0; t < prm->nu_post; ++t) smooth(l, cur, oth, nullptr);
+        return cur;
+    }
+    // finest level after its first smoothing step
+    void rest(void*& cur, void*& oth) {
+        const int L = op->g.L;
+        if (L == 1) {
+            for (int t = 1; t < prm->n_coarse; ++t) smooth(L, cur, oth, nullptr);
+            return;
+        }
+        for (int t = 1; t < prm->nu_pre; ++t) smooth(L, cur, oth, nullptr);
+        residual(L, cur);
+        void* uc = coarse(L - 1);
+        prolongate(L, uc, cur);
+        for (int t = 0; t < prm->nu_post; ++t) smooth(L, cur, oth, nullptr);
+    }
+};
+
+// ---------------------------------------------------------------- graph replay of one iteration
+template <class F>
+static tpmg_status run_iteration(tpmg_op* op, int slot, const std::vector<const void*>& key, bool use_graph,
+                                 cudaStream_t s, F&& body) {
+    if (!use_graph) {
+        body(s);
+        CK(cudaGetLastError());
+        return TPMG_OK;
+    }
+    GraphCache& gc = op->graphs[slot];
+    if (!gc.exec || gc.key != key) {
+        if (gc.exec) cudaGraphExecDestroy(gc.exec);
+        gc.exec = nullptr;
+        CK(cudaStreamBeginCapture(op->cap_stream, cudaStreamCaptureModeRelaxed));
+        const unsigned long long c0 = launch_counter();
+        body(op->cap_stream);
+        gc.nkernels = launch_counter() - c0;
+        launch_counter() = c0;  // captured launches run only when the graph is replayed
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(op->cap_stream, &graph);
+        if (e != cudaSuccess) return set_err(TPMG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&gc.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            gc.exec = nullptr;
+            return set_err(TPMG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        }
+        gc.key = key;
+    }
+    CK(cudaGraphLaunch(gc.exec, s));
+    launch_counter() += gc.nkernels;
+    return TPMG_OK;
+}
+
+static tpmg_status read_scalars(tpmg_op* op, cudaStream_t s) {
+    CK(cudaMemcpyAsync(op->sc_host, op->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return TPMG_OK;
+}
+
+static tpmg_status finish_info(tpmg_op* op, tpmg_info* info, cudaStream_t s) {
+    const Scalars& h = *op->sc_host;
+    if (info) {
+        info->iters = h.iters;
+        info->converged = h.converged;
+        info->rel_res = h.rel;
+        info->r0 = h.r0;
+        if (info->history && info->history_len > 0) {
+            int n = h.iters + 1 < info->history_len ? h.iters + 1 : info->history_len;
+            CK(cudaMemcpyAsync(info->history, op->history, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        }
+        CK(cudaEventSynchronize(op->ev1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, op->ev0, op->ev1));
+        info->ms = ms;
+        CK(cudaStreamSynchronize(s));
+    }
+    if (h.nonfinite) return set_err(TPMG_ERR_NONFINITE, "non-finite norm or dot product");
+    if (!h.converged) return set_err(TPMG_ERR_NOT_CONVERGED, "max_iter reached");
+    return TPMG_OK;
+}
+
+static tpmg_status check_params(const tpmg_op* op, const tpmg_params* p) {
+    if (!op || !p) return set_err(TPMG_ERR_ARG, "NULL operator or params");
+    if (p->nu_pre < 1 || p->nu_post < 0 || p->n_coarse < 1 || p->max_iter < 0)
+        return set_err(TPMG_ERR_ARG, "nu_pre >= 1, nu_post >= 0, n_coarse >= 1, max_iter >= 0 required");
+    if (!(p->rho > 0.0) || !(p->tol >= 0.0)) return set_err(TPMG_ERR_ARG, "rho > 0 and tol >= 0 required");
+    return TPMG_OK;
+}
+
+// multigrid solve on finest-level buffers A (iterate) and fL (rhs); levels >= lsw in PF, the
+// coarser ones in PC
+template <class PF, class PC>
+static tpmg_status mg_loop(tpmg_op* op, const tpmg_params* prm, typename PF::S* A, typename PF::S* fL,
+                           int lsw, cudaStream_t s) {
+    typedef typename PF::S S;
+    const int L = op->g.L;
+    const int* done = &op->sc->done;
+    S* B = (S*)op->hier[PF::id].ub[L];
+    const size_t nfine = lvl_cells(op, L);
+    Lv<PF> LL = level_view<PF>(op, L);
+    launch_scalars_init(op->sc, prm->tol, prm->max_iter, s);
+    const int nparts = launch_smooth<PF>(LL, prm->rho, A, fL, B, op->partials, done, s);
+    launch_finalize_norm(op->partials, nparts, FIN_MG_INIT, op->sc, op->history, nullptr, s);
+    CK(cudaGetLastError());
+    TRY(read_scalars(op, s));
+    auto body = [&](cudaStream_t st) {
+        Cycle<PF, PC> c2(op, prm, st, done, lsw);
+        c2.u[L] = A;
+        c2.f[L] = fL;
+        void* cur = B;
+        void* oth = A;
+        c2.rest(cur, oth);
+        if (cur != (void*)A) launch_copy<PF>(nfine, (const S*)cur, A, done, st);
+        const int np = launch_smooth<PF>(LL, prm->rho, A, fL, B, op->partials, done, st);
+        launch_finalize_norm(op->partials, np, FIN_MG_CYCLE, op->sc, op->history, nullptr, st);
+    };
+    std::vector<const void*> key = {A, fL, B, op->history, (const void*)(size_t)prm->nu_pre,
+                                    (const void*)(size_t)prm->nu_post, (const void*)(size_t)prm->n_coarse,
+                                    (const void*)(size_t)(prm->rho * 1e12), (const void*)(size_t)lsw};
+    int guard = 0;
+    while (!op->sc_host->done && guard++ <= prm->max_iter + 1) {
+        TRY(run_iteration(op, PF::id, key, prm->use_graph != 0, s, body));
+        TRY(read_scalars(op, s));
+    }
+    return TPMG_OK;
+}
+
+// mixed precision: u, f in DW (finest level of the DW hierarchy), FP32 inner hierarchy
+static tpmg_status mixed_loop(tpmg_op* op, const tpmg_params* prm, float2* uD, const float2* fD,
+                              cudaStream_t s) {
+    const int L = op->g.L;
+    const int* done = &op->sc->done;
+    Hier& h32 = op->hier[1];
+    float* e = (float*)h32.u[L];
+    float* eb = (float*)h32.ub[L];
+    float* r32 = (float*)h32.f[L];
+    const size_t nfine = lvl_cells(op, L);
+    Lv<PolDW> LD = level_view<PolDW>(op, L);
+    Lv<PolF32> L32 = level_view<PolF32>(op, L);
+    const int nparts = sweep_shape(LD.nx, LD.ny, LD.nz, sizeof(dw), false).nblocks();
+    launch_scalars_init(op->sc, prm->tol, prm->max_iter, s);
+    launch_residual<PolDW, PolF32>(LD, uD, fD, r32, op->partials, done, s);
+    launch_finalize_norm(op->partials, nparts, FIN_MG_INIT, op->sc, op->history, nullptr, s);
+    CK(cudaGetLastError());
+    TRY(read_scalars(op, s));
+    auto body = [&](cudaStream_t st) {
+        Cycle<PolF32, PolF32> c(op, prm, st, done, 1);
+        void* cur = e;
+        void* oth = eb;
+        // first smoothing step from e = 0: e = rho M^{-1} r
+        launch_line_solve<PolF32>(L32, r32, e, prm->rho, done, st);
+        c.rest(cur, oth);
+        launch_correct<PolDW>(nfine, uD, (const float*)cur, done, st);
+        launch_residual<PolDW, PolF32>(LD, uD, fD, r32, op->partials, done, st);
+        launch_finalize_norm(op->partials, nparts, FIN_MG_CYCLE, op->sc, op->history, nullptr, st);
+    };
+    std::vector<const void*> key = {uD, fD, e, op->history, (const void*)(size_t)prm->nu_pre,
+                                    (const void*)(size_t)prm->nu_post, (const void*)(size_t)prm->n_coarse,
+                                    (const void*)(size_t)(prm->rho * 1e12)};
+    int guard = 0;
+    while (!op->sc_host->done && guard++ <= prm->max_iter + 1) {
+        TRY(run_iteration(op, 3, key, prm->use_graph != 0, s, body));
+        TRY(read_scalars(op, s));
+    }
+    return TPMG_OK;
+}
+
+template <class P>
+static tpmg_status cg_loop(tpmg_op* op, const tpmg_params* prm, typename P::S* u, const typename P::S* f,
+                           cudaStream_t s) {
+    typedef typename P::S S;
+    const int pid = P::id;
+    S* r = (S*)op->cgbuf[pid][0];
+    S* z = (S*)op->cgbuf[pid][1];
+    S* p = (S*)op->cgbuf[pid][2];
+    S* q = (S*)op->cgbuf[pid][3];
+    const int L = op->g.L;
+    const size_t n = lvl_cells(op, L);
+    Lv<P> LL = level_view<P>(op, L);
+    const int nb_spmv = sweep_shape(LL.nx, LL.ny, LL.nz, sizeof(typename P::R), false).nblocks();
+    const int nb_tri = sweep_shape(LL.nx, LL.ny, LL.nz, sizeof(typename P::R), true).nblocks();
+    launch_scalars_init(op->sc, prm->tol, prm->max_iter, s);
+    launch_residual<P, P>(LL, u, f, r, nullptr, nullptr, s);
+    CK(cudaMemsetAsync(p, 0, n * sizeof(S), s));
+    CK(cudaMemsetAsync(q, 0, n * sizeof(S), s));
+    launch_cg_tridiag<P>(LL, op->sc, r, q, z, op->partials, s);
+    launch_cg_beta(op->partials, nb_tri, 1, op->sc, op->history, s);
+    CK(cudaGetLastError());
+    TRY(read_scalars(op, s));
+    auto body = [&](cudaStream_t st) {
+        launch_cg_spmv<P>(LL, op->sc, u, p, z, q, op->partials, st);
+        launch_cg_alpha(op->partials, nb_spmv, op->sc, st);
+        launch_cg_tridiag<P>(LL, op->sc, r, q, z, op->partials, st);
+        launch_cg_beta(op->partials, nb_tri, 0, op->sc, op->history, st);
+    };
+    std::vector<const void*> key = {u, f, r, op->history};
+    int guard = 0;
+    while (!op->sc_host->done && guard++ <= prm->max_iter + 1) {
+        TRY(run_iteration(op, 4 + pid, key, prm->use_graph != 0, s, body));
+        TRY(read_scalars(op, s));
+    }
+    launch_cg_finish<P>(n, op->sc, u, p, s);
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+// ================================================================ C ABI
+extern "C" {
+
+const char* tpmg_status_string(tpmg_status s) {
+    switch (s) {
+        case TPMG_OK: return "ok";
+        case TPMG_ERR_ARG: return "invalid argument";
+        case TPMG_ERR_CUDA: return "CUDA error";
+        case TPMG_ERR_OOM: return "out of device memory";
+        case TPMG_ERR_NOT_CONVERGED: return "not converged";
+        case TPMG_ERR_NONFINITE: return "non-finite value";
+        case TPMG_ERR_TIMEOUT: return "device wait timed out";
+        case TPMG_ERR_NN_REJECTED: return "learned stage rejected";
+    }
+    return "unknown status";
+}
+
+const char* tpmg_last_error(void) { return g_err.c_str(); }
+
+tpmg_status tpmg_create_grid(int nx, int ny, int nz, int nlevels, tpmg_grid** out) {
+    if (!out) return set_err(TPMG_ERR_ARG, "NULL output pointer");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || nz > MAX_NZ) return set_err(TPMG_ERR_ARG, "need nx, ny >= 1 and 1 <= nz <= 256");
+    if (nlevels < 0 || nlevels > MAXL) return set_err(TPMG_ERR_ARG, "nlevels must be in [0, 16]");
+    int L = nlevels;
+    if (L == 0) {
+        L = 1;
+        int a = nx, b = ny;
+        while (a % 2 == 0 && b % 2 == 0 && (a < b ? a : b) > 8 && L < MAXL) {
+            a /= 2;
+            b /= 2;
+            ++L;
+        }
+    }
+    const int div = 1 << (L - 1);
+    if (nx % div != 0 || ny % div != 0) return set_err(TPMG_ERR_ARG, "nx and ny must be divisible by 2^(nlevels-1)");
+    tpmg_grid* g = new tpmg_grid();
+    g->nx = nx;
+    g->ny = ny;
+    g->nz = nz;
+    g->L = L;
+    for (int l = 0; l <= MAXL; ++l) g->lnx[l] = g->lny[l] = 0;
+    for (int l = L; l >= 1; --l) {
+        g->lnx[l] = nx >> (L - l);
+        g->lny[l] = ny >> (L - l);
+    }
+    *out = g;
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_destroy_grid(tpmg_grid* g) {
+    delete g;
+    return TPMG_OK;
+}
+
+int tpmg_grid_nlevels(const tpmg_grid* g) { return g ? g->L : 0; }
+
+tpmg_status tpmg_grid_level_size(const tpmg_grid* g, int level, int* nx, int* ny) {
+    if (!g || level < 1 || level > g->L) return set_err(TPMG_ERR_ARG, "bad grid or level");
+    if (nx) *nx = g->lnx[level];
+    if (ny) *ny = g->lny[level];
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_create_operator(const tpmg_grid* g, double omega2, double hx, double hy, double hz,
+                                 double lambda2, const double* lambda2_col, tpmg_op** out) {
+    if (!g || !out) return set_err(TPMG_ERR_ARG, "NULL grid or output pointer");
+    *out = nullptr;
+    if (!(omega2 >= 0.0) || !(hx > 0.0) || !(hy > 0.0) || !(hz > 0.0))
+        return set_err(TPMG_ERR_ARG, "omega2 >= 0 and positive mesh widths required");
+    tpmg_op* op = new tpmg_op();
+    op->g = *g;
+    op->omega2 = omega2;
+    op->hx = hx;
+    op->hy = hy;
+    op->hz = hz;
+    cudaGetDevice(&op->device);
+    const int L = g->L;
+    // finest-level coefficients (Sec. 2.1.1): cx = omega^2/hx^2, cy = omega^2/hy^2,
+    // v_ij = omega^2 lambda_ij^2 / hz^2; coarse levels: h doubles (cx, cy / 4), v averaged
+    op->cx[L] = omega2 / (hx * hx);
+    op->cy[L] = omega2 / (hy * hy);
+    for (int l = L - 1; l >= 1; --l) {
+        op->cx[l] = op->cx[l + 1] / 4.0;
+        op->cy[l] = op->cy[l + 1] / 4.0;
+    }
+    const size_t ncol = (size_t)g->nx * g->ny;
+    std::vector<double> vf(ncol);
+    for (size_t c = 0; c < ncol; ++c) {
+        double lam = lambda2_col ? lambda2_col[c] : lambda2;
+        if (!(lam >= 0.0)) {
+            delete op;
+            return set_err(TPMG_ERR_ARG, "lambda^2 must be non-negative and finite");
+        }
+        vf[c] = omega2 * lam / (hz * hz);
+    }
+    tpmg_status st = TPMG_OK;
+    auto fail = [&](tpmg_status s2) {
+        tpmg_destroy_operator(op);
+        return s2;
+    };
+    for (int l = L; l >= 1; --l) {
+        size_t nc = (size_t)g->lnx[l] * g->lny[l];
+        if ((st = dalloc((void**)&op->v64[l], nc * sizeof(double))) != TPMG_OK) return fail(st);
+        if ((st = dalloc((void**)&op->v32[l], nc * sizeof(float))) != TPMG_OK) return fail(st);
+        if ((st = dalloc((void**)&op->vdw[l], nc * sizeof(float2))) != TPMG_OK) return fail(st);
+        if (l == L) {
+            if (cudaMemcpy(op->v64[l], vf.data(), nc * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(set_err(TPMG_ERR_CUDA, "copy of lambda^2 failed"));
+        } else {
+            launch_coarsen_v_f64(g->lnx[l + 1], g->lny[l + 1], op->v64[l + 1], op->v64[l], 0);
+        }
+        launch_f64_to_f32(nc, op->v64[l], op->v32[l], 0);
+        launch_f64_to_dw(nc, op->v64[l], op->vdw[l], 0);
+        op->v_host[l].resize(nc);
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(set_err(TPMG_ERR_CUDA, "operator setup kernels failed"));
+    for (int l = 1; l <= L; ++l) {
+        cudaMemcpy(op->v_host[l].data(), op->v64[l], op->v_host[l].size() * sizeof(double), cudaMemcpyDeviceToHost);
+        const std::vector<double>& vh = op->v_host[l];
+        op->percol[l] = 0;
+        double vmax = 0.0;
+        for (size_t c = 0; c < vh.size(); ++c) {
+            if (vh[c] != vh[0]) op->percol[l] = 1;
+            vmax = vh[c] > vmax ? vh[c] : vmax;
+        }
+        // kappa(M) = (largest/smallest eigenvalue) of the column block: D - v L_N with L_N the
+        // Neumann 1-D Laplacian, whose spectrum lies in [0, 4): kappa < 1 + 4 v / (1 + 2cx + 2cy)
+        op->kappa_M[l] = 1.0 + 4.0 * vmax / (1.0 + 2.0 * op->cx[l] + 2.0 * op->cy[l]);
+    }
+    // Double-word arithmetic (unit roundoff ~2^-48) loses log2(kappa(M)) bits in the line solves;
+    // levels with kappa(M) > DW_KAPPA_MAX (all coarse and small) run in native FP64 instead, which
+    // keeps every smoother application within 1e-10 of an FP64 computation.
+    op->lsw_dw = L + 1;
+    for (int l = L; l >= 1 && op->kappa_M[l] <= DW_KAPPA_MAX; --l) op->lsw_dw = l;
+    if (cudaStreamCreateWithFlags(&op->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&op->ev0) != cudaSuccess || cudaEventCreate(&op->ev1) != cudaSuccess)
+        return fail(set_err(TPMG_ERR_CUDA, "stream/event creation failed"));
+    *out = op;
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_destroy_operator(tpmg_op* op) {
+    if (!op) return TPMG_OK;
+    cudaDeviceSynchronize();
+    invalidate_graphs(op);
+    for (int l = 0; l <= MAXL; ++l) {
+        dfree((void*&)op->v64[l]);
+        dfree((void*&)op->v32[l]);
+        dfree((void*&)op->vdw[l]);
+        for (int p = 0; p < 3; ++p) {
+            dfree(op->finv[p][l]);
+            dfree(op->fw[p][l]);
+            dfree(op->hier[p].u[l]);
+            dfree(op->hier[p].ub[l]);
+            dfree(op->hier[p].f[l]);
+            dfree(op->hier[p].r[l]);
+        }
+    }
+    for (int p = 0; p < 3; ++p)
+        for (int t = 0; t < 4; ++t) dfree(op->cgbuf[p][t]);
+    for (int t = 0; t < 4; ++t) dfree(op->io[t]);
+    dfree((void*&)op->partials);
+    dfree((void*&)op->sc);
+    dfree((void*&)op->history);
+    if (op->sc_host) cudaFreeHost(op->sc_host);
+    if (op->cap_stream) cudaStreamDestroy(op->cap_stream);
+    if (op->ev0) cudaEventDestroy(op->ev0);
+    if (op->ev1) cudaEventDestroy(op->ev1);
+    delete op;
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_op_reserve(tpmg_op* op, tpmg_precision prec) {
+    if (!op) return set_err(TPMG_ERR_ARG, "NULL operator");
+    switch (prec) {
+        case TPMG_F64: TRY(ensure_hier(op, 0, false)); TRY(ensure_cg(op, 0)); break;
+        case TPMG_F32: TRY(ensure_hier(op, 1, false)); TRY(ensure_cg(op, 1)); break;
+        case TPMG_DW: TRY(ensure_hier(op, 2, true)); TRY(ensure_cg(op, 2)); TRY(ensure_io(op)); break;
+        case TPMG_MIXED: TRY(ensure_hier(op, 2, true)); TRY(ensure_hier(op, 1, true)); break;
+        default: return set_err(TPMG_ERR_ARG, "unknown precision");
+    }
+    TRY(ensure_history(op, 1024));
+    CK(cudaDeviceSynchronize());
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_op_level_coefficients(const tpmg_op* op, int level, double* cx, double* cy, double* v_host) {
+    TRY(check_level(op, level));
+    if (cx) *cx = op->cx[level];
+    if (cy) *cy = op->cy[level];
+    if (v_host) memcpy(v_host, op->v_host[level].data(), op->v_host[level].size() * sizeof(double));
+    return TPMG_OK;
+}
+
+// ---------------------------------------------------------------- single applications
+#define DISPATCH_PREC(prec, ...)                                                                 \
+    switch (prec) {                                                                              \
+        case TPMG_F64: { typedef PolF64 P; __VA_ARGS__; } break;                                 \
+        case TPMG_F32: { typedef PolF32 P; __VA_ARGS__; } break;                                 \
+        case TPMG_DW:  { typedef PolDW P; __VA_ARGS__; } break;                                  \
+        default: return set_err(TPMG_ERR_ARG, "precision must be TPMG_F64, TPMG_F32 or TPMG_DW"); \
+    }
+
+}  // extern "C"
+
+// For TPMG_DW the caller's double fields are converted into the io buffers around the kernel.
+struct DWIO {
+    tpmg_op* op;
+    cudaStream_t s;
+    float2* in(int slot, const void* x, size_t n) {
+        launch_f64_to_dw(n, (const double*)x, (float2*)op->io[slot], s);
+        return (float2*)op->io[slot];
+    }
+    float2* buf(int slot) { return (float2*)op->io[slot]; }
+    void out(int slot, void* y, size_t n) { launch_dw_to_f64(n, (const float2*)op->io[slot], (double*)y, s); }
+};
+
+template <class P>
+static typename P::S* in_ptr(tpmg_op* op, cudaStream_t s, int slot, const void* x, size_t n) {
+    if (P::id == 2) return (typename P::S*)DWIO{op, s}.in(slot, x, n);
+    return (typename P::S*)x;
+}
+template <class P>
+static typename P::S* out_ptr(tpmg_op* op, int slot, void* y) {
+    if (P::id == 2) return (typename P::S*)op->io[slot];
+    return (typename P::S*)y;
+}
+template <class P>
+static void out_back(tpmg_op* op, cudaStream_t s, int slot, void* y, size_t n) {
+    if (P::id == 2) DWIO{op, s}.out(slot, y, n);
+}
+
+static tpmg_status prep_unit(tpmg_op* op, tpmg_precision prec) {
+    if (prec == TPMG_DW) TRY(ensure_io(op));
+    if (prec == TPMG_F64 || prec == TPMG_F32 || prec == TPMG_DW) TRY(ensure_factors(op, pid_of(prec)));
+    return ensure_common(op);
+}
+
+extern "C" {
+
+tpmg_status tpmg_apply_A(tpmg_op* op, int level, tpmg_precision prec, const void* x, void* y, void* stream) {
+    TRY(check_level(op, level));
+    if (prec == TPMG_DW && level < op->lsw_dw) prec = TPMG_F64;  // see DW_KAPPA_MAX
+    if (!x || !y) return set_err(TPMG_ERR_ARG, "NULL field");
+    TRY(prep_unit(op, prec));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = lvl_cells(op, level);
+    DISPATCH_PREC(prec, {
+        auto* xi = in_ptr<P>(op, s, 0, x, n);
+        auto* yo = out_ptr<P>(op, 1, y);
+        launch_apply_A<P>(level_view<P>(op, level), xi, yo, s);
+        out_back<P>(op, s, 1, y, n);
+    });
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_line_solve(tpmg_op* op, int level, tpmg_precision prec, const void* b, void* x, void* stream) {
+    TRY(check_level(op, level));
+    if (prec == TPMG_DW && level < op->lsw_dw) prec = TPMG_F64;  // see DW_KAPPA_MAX
+    if (!x || !b) return set_err(TPMG_ERR_ARG, "NULL field");
+    TRY(prep_unit(op, prec));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = lvl_cells(op, level);
+    DISPATCH_PREC(prec, {
+        auto* bi = in_ptr<P>(op, s, 0, b, n);
+        auto* xo = out_ptr<P>(op, 1, x);
+        launch_line_solve<P>(level_view<P>(op, level), bi, xo, 1.0, nullptr, s);
+        out_back<P>(op, s, 1, x, n);
+    });
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_smooth(tpmg_op* op, int level, tpmg_precision prec, double rho, const void* u,
+                        const void* f, void* u_out, double* norm_out, void* stream) {
+    TRY(check_level(op, level));
+    if (prec == TPMG_DW && level < op->lsw_dw) prec = TPMG_F64;  // see DW_KAPPA_MAX
+    if (!u || !f || !u_out) return set_err(TPMG_ERR_ARG, "NULL field");
+    TRY(prep_unit(op, prec));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = lvl_cells(op, level);
+    DISPATCH_PREC(prec, {
+        Lv<P> LL = level_view<P>(op, level);
+        auto* ui = in_ptr<P>(op, s, 0, u, n);
+        auto* fi = in_ptr<P>(op, s, 1, f, n);
+        auto* uo = out_ptr<P>(op, 2, u_out);
+        const int np = launch_smooth<P>(LL, rho, ui, fi, uo, norm_out ? op->partials : nullptr, nullptr, s);
+        if (norm_out) launch_finalize_norm(op->partials, np, FIN_STORE, op->sc, nullptr, norm_out, s);
+        out_back<P>(op, s, 2, u_out, n);
+    });
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_residual(tpmg_op* op, int level, tpmg_precision prec, const void* u, const void* f,
+                          void* r, double* norm_out, void* stream) {
+    TRY(check_level(op, level));
+    if (prec == TPMG_DW && level < op->lsw_dw) prec = TPMG_F64;  // see DW_KAPPA_MAX
+    if (!u || !f || !r) return set_err(TPMG_ERR_ARG, "NULL field");
+    TRY(prep_unit(op, prec));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = lvl_cells(op, level);
+    DISPATCH_PREC(prec, {
+        Lv<P> LL = level_view<P>(op, level);
+        auto* ui = in_ptr<P>(op, s, 0, u, n);
+        auto* fi = in_ptr<P>(op, s, 1, f, n);
+        auto* ro = out_ptr<P>(op, 2, r);
+        launch_residual<P, P>(LL, ui, fi, ro, norm_out ? op->partials : nullptr, nullptr, s);
+        if (norm_out)
+            launch_finalize_norm(op->partials, sweep_shape(LL.nx, LL.ny, LL.nz, sizeof(typename P::R), false).nblocks(),
+                                 FIN_STORE, op->sc, nullptr, norm_out, s);
+        out_back<P>(op, s, 2, r, n);
+    });
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_restrict_smooth(tpmg_op* op, int level, tpmg_precision prec, double rho, const void* r_fine,
+                                 void* f_c, void* u_c, void* stream) {
+    TRY(check_level(op, level));
+    if (prec == TPMG_DW && level < op->lsw_dw) prec = TPMG_F64;  // see DW_KAPPA_MAX
+    if (level >= op->g.L) return set_err(TPMG_ERR_ARG, "restrict_smooth needs a coarse level < L");
+    if (!r_fine || !f_c || !u_c) return set_err(TPMG_ERR_ARG, "NULL field");
+    TRY(prep_unit(op, prec));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nc = lvl_cells(op, level), nf = lvl_cells(op, level + 1);
+    DISPATCH_PREC(prec, {
+        auto* ri = in_ptr<P>(op, s, 0, r_fine, nf);
+        auto* fo = out_ptr<P>(op, 1, f_c);
+        auto* uo = out_ptr<P>(op, 2, u_c);
+        launch_restrict_smooth<P, P>(level_view<P>(op, level), rho, ri, fo, uo, nullptr, s);
+        out_back<P>(op, s, 1, f_c, nc);
+        out_back<P>(op, s, 2, u_c, nc);
+    });
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_prolongate(tpmg_op* op, int level, tpmg_precision prec, const void* u_c, void* u_f, void* stream) {
+    TRY(check_level(op, level));
+    if (prec == TPMG_DW && level - 1 < op->lsw_dw) prec = TPMG_F64;
+    if (level <= 1) return set_err(TPMG_ERR_ARG, "prolongate needs a fine level > 1");
+    if (!u_c || !u_f) return set_err(TPMG_ERR_ARG, "NULL field");
+    TRY(prep_unit(op, prec));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nc = lvl_cells(op, level - 1), nf = lvl_cells(op, level);
+    DISPATCH_PREC(prec, {
+        auto* ci = in_ptr<P>(op, s, 0, u_c, nc);
+        auto* fio = in_ptr<P>(op, s, 1, u_f, nf);
+        launch_prolongate<P, P>(op->g.lnx[level - 1], op->g.lny[level - 1], op->g.nz, ci, fio, nullptr, s);
+        out_back<P>(op, s, 1, u_f, nf);
+    });
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_cg_fused_spmv(tpmg_op* op, tpmg_precision prec, double alpha, double beta, void* u, void* p,
+                               const void* z, void* q, double* sigma_out, void* stream) {
+    if (!op) return set_err(TPMG_ERR_ARG, "NULL operator");
+    if (prec == TPMG_DW && op->lsw_dw > op->g.L) prec = TPMG_F64;
+    if (!u || !p || !z || !q || !sigma_out) return set_err(TPMG_ERR_ARG, "NULL argument");
+    TRY(prep_unit(op, prec));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = op->g.L;
+    const size_t n = lvl_cells(op, L);
+    launch_set_ab(op->sc, alpha, beta, s);
+    DISPATCH_PREC(prec, {
+        Lv<P> LL = level_view<P>(op, L);
+        auto* ui = in_ptr<P>(op, s, 0, u, n);
+        auto* pi = in_ptr<P>(op, s, 1, p, n);
+        auto* zi = in_ptr<P>(op, s, 2, z, n);
+        auto* qi = in_ptr<P>(op, s, 3, q, n);
+        launch_cg_spmv<P>(LL, op->sc, ui, pi, zi, qi, op->partials, s);
+        launch_finalize_norm(op->partials, sweep_shape(LL.nx, LL.ny, LL.nz, sizeof(typename P::R), false).nblocks(),
+                             FIN_SUM, op->sc, nullptr, sigma_out, s);
+        out_back<P>(op, s, 0, u, n);
+        out_back<P>(op, s, 1, p, n);
+        out_back<P>(op, s, 3, q, n);
+    });
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_cg_fused_tridiag(tpmg_op* op, tpmg_precision prec, double alpha, void* r, const void* q, void* z,
+                                  double* rr_out, double* rz_out, void* stream) {
+    if (!op) return set_err(TPMG_ERR_ARG, "NULL operator");
+    if (prec == TPMG_DW && op->lsw_dw > op->g.L) prec = TPMG_F64;
+    if (!r || !q || !z || !rr_out || !rz_out) return set_err(TPMG_ERR_ARG, "NULL argument");
+    TRY(prep_unit(op, prec));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = op->g.L;
+    const size_t n = lvl_cells(op, L);
+    launch_set_ab(op->sc, alpha, 0.0, s);
+    DISPATCH_PREC(prec, {
+        Lv<P> LL = level_view<P>(op, L);
+        auto* ri = in_ptr<P>(op, s, 0, r, n);
+        auto* qi = in_ptr<P>(op, s, 1, q, n);
+        auto* zo = out_ptr<P>(op, 2, z);
+        launch_cg_tridiag<P>(LL, op->sc, ri, qi, zo, op->partials, s);
+        const int nb = sweep_shape(LL.nx, LL.ny, LL.nz, sizeof(typename P::R), true).nblocks();
+        launch_finalize_norm(op->partials, nb, FIN_SUM, op->sc, nullptr, rr_out, s);
+        launch_finalize_norm(op->partials + nb, nb, FIN_SUM, op->sc, nullptr, rz_out, s);
+        out_back<P>(op, s, 0, r, n);
+        out_back<P>(op, s, 2, z, n);
+    });
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+// ---------------------------------------------------------------- solvers
+void tpmg_default_params(tpmg_params* p) {
+    if (!p) return;
+    p->nu_pre = 2;
+    p->nu_post = 2;
+    p->n_coarse = 2;
+    p->max_iter = 100;
+    p->rho = 0.8;
+    p->tol = 1e-6;
+    p->prec = TPMG_DW;
+    p->use_graph = 1;
+}
+
+tpmg_status tpmg_mg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, void* u, tpmg_info* info,
+                          void* stream) {
+    TRY(check_params(op, prm));
+    if (!f || !u) return set_err(TPMG_ERR_ARG, "NULL field");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = op->g.L;
+    const size_t n = lvl_cells(op, L);
+    TRY(ensure_history(op, prm->max_iter + 2));
+    tpmg_precision prec = prm->prec;
+    if (prec == TPMG_DW && op->lsw_dw > L) prec = TPMG_F64;  // no level where double-word suffices
+    switch (prec) {
+        case TPMG_F64:
+            TRY(ensure_hier(op, 0, false));
+            CK(cudaEventRecord(op->ev0, s));
+            TRY((mg_loop<PolF64, PolF64>(op, prm, (double*)u, (double*)f, 1, s)));
+            break;
+        case TPMG_F32:
+            TRY(ensure_hier(op, 1, false));
+            CK(cudaEventRecord(op->ev0, s));
+            TRY((mg_loop<PolF32, PolF32>(op, prm, (float*)u, (float*)f, 1, s)));
+            break;
+        case TPMG_DW: {
+            TRY(ensure_hier(op, 2, true));
+            TRY(ensure_hier(op, 0, false));
+            float2* uD = (float2*)op->hier[2].u[L];
+            float2* fD = (float2*)op->hier[2].f[L];
+            CK(cudaEventRecord(op->ev0, s));
+            launch_f64_to_dw(n, (const double*)u, uD, s);
+            launch_f64_to_dw(n, (const double*)f, fD, s);
+            TRY((mg_loop<PolDW, PolF64>(op, prm, uD, fD, op->lsw_dw, s)));
+            launch_dw_to_f64(n, uD, (double*)u, s);
+            break;
+        }
+        case TPMG_MIXED: {
+            TRY(ensure_hier(op, 2, true));
+            TRY(ensure_hier(op, 1, true));
+            float2* uD = (float2*)op->hier[2].u[L];
+            float2* fD = (float2*)op->hier[2].f[L];
+            CK(cudaEventRecord(op->ev0, s));
+            launch_f64_to_dw(n, (const double*)u, uD, s);
+            launch_f64_to_dw(n, (const double*)f, fD, s);
+            TRY(mixed_loop(op, prm, uD, fD, s));
+            launch_dw_to_f64(n, uD, (double*)u, s);
+            break;
+        }
+        default: return set_err(TPMG_ERR_ARG, "unknown precision");
+    }
+    CK(cudaEventRecord(op->ev1, s));
+    CK(cudaGetLastError());
+    return finish_info(op, info, s);
+}
+
+tpmg_status tpmg_vcycle(tpmg_op* op, const tpmg_params* prm, const void* f, void* u, void* stream) {
+    TRY(check_params(op, prm));
+    if (!f || !u) return set_err(TPMG_ERR_ARG, "NULL field");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = op->g.L;
+    const size_t n = lvl_cells(op, L);
+    auto one = [&](auto tagF, auto tagC, auto* A, auto* fL, int lsw) -> tpmg_status {
+        typedef decltype(tagF) PF;
+        typedef decltype(tagC) PC;
+        typedef typename PF::S S;
+        Cycle<PF, PC> c(op, prm, s, nullptr, lsw);
+        c.u[L] = A;
+        c.f[L] = fL;
+        S* B = (S*)op->hier[PF::id].ub[L];
+        launch_smooth<PF>(level_view<PF>(op, L), prm->rho, A, fL, B, nullptr, nullptr, s);
+        void* cur = B;
+        void* oth = A;
+        c.rest(cur, oth);
+        if (cur != (void*)A) launch_copy<PF>(n, (const S*)cur, A, nullptr, s);
+        return TPMG_OK;
+    };
+    tpmg_precision prec = prm->prec;
+    if (prec == TPMG_DW && op->lsw_dw > L) prec = TPMG_F64;
+    switch (prec) {
+        case TPMG_F64:
+            TRY(ensure_hier(op, 0, false));
+            TRY(one(PolF64(), PolF64(), (double*)u, (double*)f, 1));
+            break;
+        case TPMG_F32:
+            TRY(ensure_hier(op, 1, false));
+            TRY(one(PolF32(), PolF32(), (float*)u, (float*)f, 1));
+            break;
+        case TPMG_DW: {
+            TRY(ensure_hier(op, 2, true));
+            TRY(ensure_hier(op, 0, false));
+            float2* uD = (float2*)op->hier[2].u[L];
+            float2* fD = (float2*)op->hier[2].f[L];
+            launch_f64_to_dw(n, (const double*)u, uD, s);
+            launch_f64_to_dw(n, (const double*)f, fD, s);
+            TRY(one(PolDW(), PolF64(), uD, fD, op->lsw_dw));
+            launch_dw_to_f64(n, uD, (double*)u, s);
+            break;
+        }
+        default: return set_err(TPMG_ERR_ARG, "tpmg_vcycle: precision must be TPMG_F64, TPMG_F32 or TPMG_DW");
+    }
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+unsigned long long tpmg_kernel_launches(void) { return launch_counter(); }
+
+tpmg_status tpmg_time_kernel(tpmg_op* op, tpmg_precision prec, tpmg_kernel k, int reps, double* ms,
+                             void* stream) {
+    if (!op || !ms || reps < 1) return set_err(TPMG_ERR_ARG, "NULL operator/output or reps < 1");
+    if (prec != TPMG_F64 && prec != TPMG_F32 && prec != TPMG_DW)
+        return set_err(TPMG_ERR_ARG, "precision must be TPMG_F64, TPMG_F32 or TPMG_DW");
+    const int pid = pid_of(prec), L = op->g.L;
+    if ((k == TPMG_K_RESTRICT_SMOOTH || k == TPMG_K_PROLONGATE) && L < 2)
+        return set_err(TPMG_ERR_ARG, "transfer kernels need two levels");
+    TRY(ensure_hier(op, pid, true));
+    TRY(ensure_cg(op, pid));
+    TRY(ensure_history(op, 16));
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_scalars_init(op->sc, 0.0, 1, s);
+    const size_t n = lvl_cells(op, L);
+    auto run = [&](auto tag) {
+        typedef decltype(tag) P;
+        typedef typename P::S S;
+        Hier& h = op->hier[pid];
+        S* a = (S*)h.u[L];
+        S* f = (S*)h.f[L];
+        S* b = (S*)h.ub[L];
+        S* r = (S*)h.r[L];
+        S** cg = (S**)op->cgbuf[pid];
+        Lv<P> LL = level_view<P>(op, L);
+        switch (k) {
+            case TPMG_K_SMOOTH: launch_smooth<P>(LL, 0.8, a, f, b, op->partials, nullptr, s); break;
+            case TPMG_K_RESIDUAL: launch_residual<P, P>(LL, a, f, r, op->partials, nullptr, s); break;
+            case TPMG_K_APPLY_A: launch_apply_A<P>(LL, a, b, s); break;
+            case TPMG_K_LINE_SOLVE: launch_line_solve<P>(LL, f, b, 1.0, nullptr, s); break;
+            case TPMG_K_RESTRICT_SMOOTH:
+                launch_restrict_smooth<P, P>(level_view<P>(op, L - 1), 0.8, r, (S*)h.f[L - 1], (S*)h.u[L - 1], nullptr, s);
+                break;
+            case TPMG_K_PROLONGATE:
+                launch_prolongate<P, P>(op->g.lnx[L - 1], op->g.lny[L - 1], op->g.nz, (S*)h.u[L - 1], a, nullptr, s);
+                break;
+            case TPMG_K_CG_SPMV: launch_cg_spmv<P>(LL, op->sc, cg[0], cg[2], cg[1], cg[3], op->partials, s); break;
+            case TPMG_K_CG_TRIDIAG: launch_cg_tridiag<P>(LL, op->sc, cg[0], cg[3], cg[1], op->partials, s); break;
+            default: break;
+        }
+        (void)n;
+    };
+    if (k < 0 || k >= TPMG_K_COUNT) return set_err(TPMG_ERR_ARG, "unknown kernel id");
+    auto once = [&]() {
+        if (pid == 0) run(PolF64());
+        else if (pid == 1) run(PolF32());
+        else run(PolDW());
+    };
+    once();  // warm-up
+    CK(cudaEventRecord(op->ev0, s));
+    for (int t = 0; t < reps; ++t) once();
+    CK(cudaEventRecord(op->ev1, s));
+    CK(cudaEventSynchronize(op->ev1));
+    CK(cudaGetLastError());
+    float t_ms = 0;
+    CK(cudaEventElapsedTime(&t_ms, op->ev0, op->ev1));
+    *ms = t_ms / reps;
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_cg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, void* u, tpmg_info* info,
+                          void* stream) {
+    TRY(check_params(op, prm));
+    if (!f || !u) return set_err(TPMG_ERR_ARG, "NULL field");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = op->g.L;
+    const size_t n = lvl_cells(op, L);
+    TRY(ensure_history(op, prm->max_iter + 2));
+    tpmg_precision prec = prm->prec;
+    if (prec == TPMG_DW && op->lsw_dw > L) prec = TPMG_F64;
+    switch (prec) {
+        case TPMG_F64:
+            TRY(ensure_cg(op, 0));
+            CK(cudaEventRecord(op->ev0, s));
+            TRY(cg_loop<PolF64>(op, prm, (double*)u, (const double*)f, s));
+            break;
+        case TPMG_F32:
+            TRY(ensure_cg(op, 1));
+            CK(cudaEventRecord(op->ev0, s));
+            TRY(cg_loop<PolF32>(op, prm, (float*)u, (const float*)f, s));
+            break;
+        case TPMG_DW: {
+            TRY(ensure_cg(op, 2));
+            float2* uD = (float2*)op->hier[2].u[L];
+            float2* fD = (float2*)op->hier[2].f[L];
+            CK(cudaEventRecord(op->ev0, s));
+            launch_f64_to_dw(n, (const double*)u, uD, s);
+            launch_f64_to_dw(n, (const double*)f, fD, s);
+            TRY(cg_loop<PolDW>(op, prm, uD, fD, s));
+            launch_dw_to_f64(n, uD, (double*)u, s);
+            break;
+        }
+        default: return set_err(TPMG_ERR_ARG, "tpmg_cg_solve: precision must be TPMG_F64, TPMG_F32 or TPMG_DW");
+    }
+    CK(cudaEventRecord(op->ev1, s));
+    CK(cudaGetLastError());
+    return finish_info(op, info, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,174 @@
+// arith.cuh -- arithmetic policies of the GB300 kernels.
+//
+// Three policies share one kernel source:
+//   F64 : storage double, arithmetic double (native FP64; 1/72 of the FP32 rate on GB300).
+//   F32 : storage float,  arithmetic float.
+//   DW  : storage float2 {hi, lo}, arithmetic on double-word numbers (hi + lo, |lo| <= ulp(hi)/2)
+//         built from error-free transformations on the FP32 units, giving about 2^-47 relative
+//         accuracy per operation at a fraction of the cost of native FP64 on this part.
+//         The algorithms are the published ones: TwoSum (Knuth, TAOCP vol. 2), Fast2Sum (Dekker
+//         1971), TwoProd via FMA, and the double-word products of Joldes, Muller and Popescu,
+//         "Tight and rigorous error bounds for basic building blocks of double-word arithmetic",
+//         ACM TOMS 44(2), 2017 (DWTimesFP3 and DWTimesDW2). The sum is the "sloppy" double-word
+//         sum (TwoSum of the high parts plus the low parts, renormalised): its error is bounded by
+//         a few units of 2^-48 times |a| + |b|, the absolute accuracy a stencil sum needs.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tpmg {
+
+struct dw {
+    float hi, lo;
+};
+
+// ---------------------------------------------------------------- error-free transformations
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ dw dw_add(dw a, dw b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    dw z;
+    fast_two_sum(s, e, z.hi, z.lo);
+    return z;
+}
+__device__ __forceinline__ dw dw_neg(dw a) { return dw{-a.hi, -a.lo}; }
+__device__ __forceinline__ dw dw_sub(dw a, dw b) { return dw_add(a, dw_neg(b)); }
+
+// DWTimesFP3: double-word times float, with FMA.
+__device__ __forceinline__ dw dw_mul_f(dw a, float b) {
+    float ch = __fmul_rn(a.hi, b);
+    float cl1 = __fmaf_rn(a.hi, b, -ch);
+    float cl3 = __fmaf_rn(a.lo, b, cl1);
+    dw z;
+    fast_two_sum(ch, cl3, z.hi, z.lo);
+    return z;
+}
+// DWTimesDW2: double-word times double-word, with FMA.
+__device__ __forceinline__ dw dw_mul(dw a, dw b) {
+    float ch = __fmul_rn(a.hi, b.hi);
+    float cl1 = __fmaf_rn(a.hi, b.hi, -ch);
+    float tl = __fmul_rn(a.hi, b.lo);
+    float cl2 = __fmaf_rn(a.lo, b.hi, tl);
+    float cl3 = __fadd_rn(cl1, cl2);
+    dw z;
+    fast_two_sum(ch, cl3, z.hi, z.lo);
+    return z;
+}
+// 1/a: correctly rounded float reciprocal of the high part refined by one Newton step evaluated
+// in double-word arithmetic: y = y0 + y0 (1 - a y0). Relative error about 2^-47.
+__device__ __forceinline__ dw dw_rcp(dw a) {
+    float y0 = __frcp_rn(a.hi);
+    dw t = dw_mul_f(a, y0);                     // a*y0 = 1 - delta
+    float e = __fsub_rn(__fsub_rn(1.0f, t.hi), t.lo);  // 1 - t.hi is exact (Sterbenz)
+    dw z;
+    fast_two_sum(y0, __fmul_rn(y0, e), z.hi, z.lo);
+    return z;
+}
+
+// ---------------------------------------------------------------- policy traits
+// Each policy provides: storage type S, arithmetic type R, load/store, cst (from a double
+// constant), to_d, to_f/from_f (to and from float, for the mixed-precision hand-over), add, sub,
+// mul, fma, rcp, and acc_dot (accumulate a*b into a per-thread partial sum, read with acc_get).
+
+struct PolF64 {
+    typedef double S;
+    typedef double R;
+    static constexpr int id = 0;
+    __device__ __forceinline__ static R ld(const S* p, size_t i) { return __ldg(p + i); }
+    __device__ __forceinline__ static R ld_plain(const S* p, size_t i) { return p[i]; }
+    __device__ __forceinline__ static void st(S* p, size_t i, R x) { p[i] = x; }
+    __device__ __forceinline__ static R cst(double x) { return x; }
+    __device__ __forceinline__ static double to_d(R x) { return x; }
+    __device__ __forceinline__ static R zero() { return 0.0; }
+    __device__ __forceinline__ static R add(R a, R b) { return a + b; }
+    __device__ __forceinline__ static R sub(R a, R b) { return a - b; }
+    __device__ __forceinline__ static R mul(R a, R b) { return a * b; }
+    // a*b + c
+    __device__ __forceinline__ static R fma(R a, R b, R c) { return ::fma(a, b, c); }
+    __device__ __forceinline__ static R rcp(R a) { return 1.0 / a; }
+    // per-thread partial sum type for dot products and norms
+    typedef double Acc;
+    __device__ __forceinline__ static void acc_dot(Acc& s, Acc& c, R a, R b) { s = ::fma(a, b, s); }
+    __device__ __forceinline__ static double acc_get(Acc s, Acc c) { return s; }
+    __device__ __forceinline__ static float to_f(R x) { return __double2float_rn(x); }
+    __device__ __forceinline__ static R from_f(float x) { return (double)x; }
+};
+
+struct PolF32 {
+    typedef float S;
+    typedef float R;
+    static constexpr int id = 1;
+    __device__ __forceinline__ static R ld(const S* p, size_t i) { return __ldg(p + i); }
+    __device__ __forceinline__ static R ld_plain(const S* p, size_t i) { return p[i]; }
+    __device__ __forceinline__ static void st(S* p, size_t i, R x) { p[i] = x; }
+    __device__ __forceinline__ static R cst(double x) { return (float)x; }
+    __device__ __forceinline__ static double to_d(R x) { return (double)x; }
+    __device__ __forceinline__ static R zero() { return 0.0f; }
+    __device__ __forceinline__ static R add(R a, R b) { return a + b; }
+    __device__ __forceinline__ static R sub(R a, R b) { return a - b; }
+    __device__ __forceinline__ static R mul(R a, R b) { return a * b; }
+    __device__ __forceinline__ static R fma(R a, R b, R c) { return fmaf(a, b, c); }
+    __device__ __forceinline__ static R rcp(R a) { return __frcp_rn(a); }
+    // Kahan-compensated float partial sums (the FP32 pipe is the fast one on this part)
+    typedef float Acc;
+    __device__ __forceinline__ static void acc_dot(Acc& s, Acc& c, R a, R b) {
+        float y = __fsub_rn(__fmul_rn(a, b), c);
+        float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ static double acc_get(Acc s, Acc c) { return (double)s - (double)c; }
+    __device__ __forceinline__ static float to_f(R x) { return x; }
+    __device__ __forceinline__ static R from_f(float x) { return x; }
+};
+
+struct PolDW {
+    typedef float2 S;
+    typedef dw R;
+    static constexpr int id = 2;
+    __device__ __forceinline__ static R ld(const S* p, size_t i) {
+        float2 v = __ldg(p + i);
+        return dw{v.x, v.y};
+    }
+    __device__ __forceinline__ static R ld_plain(const S* p, size_t i) {
+        float2 v = p[i];
+        return dw{v.x, v.y};
+    }
+    __device__ __forceinline__ static void st(S* p, size_t i, R x) { p[i] = make_float2(x.hi, x.lo); }
+    __device__ __forceinline__ static R cst(double x) {
+        float h = __double2float_rn(x);
+        return dw{h, __double2float_rn(x - (double)h)};
+    }
+    __device__ __forceinline__ static double to_d(R x) { return (double)x.hi + (double)x.lo; }
+    __device__ __forceinline__ static R zero() { return dw{0.0f, 0.0f}; }
+    __device__ __forceinline__ static R add(R a, R b) { return dw_add(a, b); }
+    __device__ __forceinline__ static R sub(R a, R b) { return dw_sub(a, b); }
+    __device__ __forceinline__ static R mul(R a, R b) { return dw_mul(a, b); }
+    __device__ __forceinline__ static R fma(R a, R b, R c) { return dw_add(dw_mul(a, b), c); }
+    __device__ __forceinline__ static R rcp(R a) { return dw_rcp(a); }
+    // Kahan-compensated float partial sums of hi*hi + 2 hi*lo (relative accuracy ~1e-7 per
+    // column sum, ample for a convergence test; block and grid stages run in FP64)
+    typedef float Acc;
+    __device__ __forceinline__ static void acc_dot(Acc& s, Acc& c, R a, R b) {
+        float x = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, __fmul_rn(a.hi, b.hi)));
+        float y = __fsub_rn(x, c);
+        float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ static double acc_get(Acc s, Acc c) { return (double)s - (double)c; }
+    __device__ __forceinline__ static float to_f(R x) { return __fadd_rn(x.hi, x.lo); }
+    __device__ __forceinline__ static R from_f(float x) { return dw{x, 0.0f}; }
+};
+
+}  // namespace tpmg

@@ -1,0 +1,161 @@
+// k_cg.cu -- the two fused kernels of the line-preconditioned CG iteration (Sec. 3.1, kernel list
+// "Conjugate Gradient"), with the BLAS-1 updates and the dot products folded into the sweeps.
+//
+// Fused SpMV (iteration j, scalars of iteration j-1):
+//   u <- u + alpha_{j-1} p ; p <- z + beta_{j-1} p ; q <- A z + beta_{j-1} q ; sigma = <p, q>
+// which uses A p_j = A z_j + beta_{j-1} A p_{j-1}, so the stencil is applied to z and the
+// solution update lags one iteration behind (finished by k_cg_finish).
+// Fused Tridiag:
+//   r <- r - alpha_j q ; z <- M^{-1} r ; <r, r> ; <r, z>
+// One thread owns one vertical column; the sums are reduced per block and summed in a fixed order
+// by the finalize kernels (k_util.cu), which also compute alpha and beta on the device.
+#include "kernels.cuh"
+
+namespace tpmg {
+
+static constexpr int TX = 32;
+__device__ __forceinline__ int wrapc(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+template <class P>
+__global__ void __launch_bounds__(256) k_cg_spmv(Lv<P> L, const Scalars* __restrict__ sc,
+                                                 typename P::S* __restrict__ u,
+                                                 typename P::S* __restrict__ p,
+                                                 const typename P::S* __restrict__ z,
+                                                 typename P::S* __restrict__ q, double* partials) {
+    typedef typename P::R R;
+    if (*(volatile const int*)&sc->done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool act = i < L.nx && j < L.ny;
+    typename P::Acc acc = 0, cmp = 0;
+    if (act) {
+        const size_t pl = (size_t)L.nx * L.ny, c = (size_t)j * L.nx + i;
+        const size_t cw = (size_t)j * L.nx + wrapc(i - 1, L.nx), ce = (size_t)j * L.nx + wrapc(i + 1, L.nx);
+        const size_t cs = (size_t)wrapc(j - 1, L.ny) * L.nx + i, cn = (size_t)wrapc(j + 1, L.ny) * L.nx + i;
+        const R alpha = P::cst(sc->alpha), beta = P::cst(sc->beta);
+        const R cx = P::cst(L.cx), cy = P::cst(L.cy), vv = P::ld(L.v, c);
+        const R dh = P::cst(1.0 + 2.0 * L.cx + 2.0 * L.cy);
+        const R dh1 = P::add(dh, vv), dh2 = P::add(dh1, vv);
+        R zm = P::zero(), zc = P::ld(z, c);
+        for (int k = 0; k < L.nz; ++k) {
+            const size_t b = (size_t)k * pl, id = b + c;
+            R zp = (k + 1 < L.nz) ? P::ld(z, b + pl + c) : P::zero();
+            R hx = P::add(P::ld(z, b + cw), P::ld(z, b + ce));
+            R hy = P::add(P::ld(z, b + cs), P::ld(z, b + cn));
+            R diag = (L.nz == 1) ? dh : ((k == 0 || k == L.nz - 1) ? dh1 : dh2);
+            R az = P::mul(diag, zc);
+            az = P::sub(az, P::mul(cx, hx));
+            az = P::sub(az, P::mul(cy, hy));
+            az = P::sub(az, P::mul(vv, P::add(zm, zp)));
+            R pold = P::ld_plain(p, id);
+            P::st(u, id, P::add(P::ld_plain(u, id), P::mul(alpha, pold)));
+            R pn = P::add(zc, P::mul(beta, pold));
+            R qn = P::add(az, P::mul(beta, P::ld_plain(q, id)));
+            P::st(p, id, pn);
+            P::st(q, id, qn);
+            P::acc_dot(acc, cmp, pn, qn);
+            zm = zc;
+            zc = zp;
+        }
+    }
+    double s = block_sum(P::acc_get(acc, cmp));
+    if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+template <class P>
+__global__ void __launch_bounds__(256) k_cg_tridiag(Lv<P> L, const Scalars* __restrict__ sc,
+                                                    typename P::S* __restrict__ r,
+                                                    const typename P::S* __restrict__ q,
+                                                    typename P::S* __restrict__ z, double* partials) {
+    typedef typename P::R R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (*(volatile const int*)&sc->done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool act = i < L.nx && j < L.ny;
+    typename P::Acc arr = 0, crr = 0, arz = 0, crz = 0;
+    if (act) {
+        const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+        R* dp = reinterpret_cast<R*>(smem_raw);
+        R* w = dp + (size_t)L.nz * nt;
+        const size_t pl = (size_t)L.nx * L.ny, c = (size_t)j * L.nx + i;
+        const R alpha = P::cst(sc->alpha);
+        const R vv = P::ld(L.v, c), vv2 = P::mul(vv, vv);
+        const R dh = P::cst(1.0 + 2.0 * L.cx + 2.0 * L.cy);
+        const R dh1 = P::add(dh, vv), dh2 = P::add(dh1, vv);
+        R inv_prev = P::zero(), d_prev = P::zero();
+        for (int k = 0; k < L.nz; ++k) {
+            const size_t id = (size_t)k * pl + c;
+            R rn = P::sub(P::ld_plain(r, id), P::mul(alpha, P::ld(q, id)));
+            P::st(r, id, rn);
+            P::acc_dot(arr, crr, rn, rn);
+            R diag = (L.nz == 1) ? dh : ((k == 0 || k == L.nz - 1) ? dh1 : dh2);
+            R m = (k == 0) ? diag : P::sub(diag, P::mul(vv2, inv_prev));
+            R inv = P::rcp(m);
+            R d = P::mul(P::add(rn, P::mul(vv, d_prev)), inv);
+            dp[(size_t)k * nt + tid] = d;
+            w[(size_t)k * nt + tid] = P::mul(vv, inv);
+            inv_prev = inv;
+            d_prev = d;
+        }
+        R xn = P::zero();
+        for (int k = L.nz - 1; k >= 0; --k) {
+            const size_t id = (size_t)k * pl + c;
+            xn = P::add(dp[(size_t)k * nt + tid], P::mul(w[(size_t)k * nt + tid], xn));
+            P::st(z, id, xn);
+            P::acc_dot(arz, crz, P::ld_plain(r, id), xn);
+        }
+    }
+    double s1 = block_sum(P::acc_get(arr, crr));
+    double s2 = block_sum(P::acc_get(arz, crz));
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const int b = blockIdx.y * gridDim.x + blockIdx.x, nb = gridDim.x * gridDim.y;
+        partials[b] = s1;
+        partials[nb + b] = s2;
+    }
+}
+
+// u <- u + alpha p : the lagged solution update after the last iteration.
+template <class P>
+__global__ void k_cg_finish(size_t n, const Scalars* __restrict__ sc, typename P::S* __restrict__ u,
+                            const typename P::S* __restrict__ p) {
+    const typename P::R alpha = P::cst(sc->alpha);
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        P::st(u, t, P::add(P::ld_plain(u, t), P::mul(alpha, P::ld(p, t))));
+}
+
+template <class P>
+void launch_cg_spmv(const Lv<P>& L, const Scalars* sc, typename P::S* u, typename P::S* p,
+                    const typename P::S* z, typename P::S* q, double* partials, cudaStream_t s) {
+    Shape sh = sweep_shape(L.nx, L.ny, L.nz, sizeof(typename P::R), false);
+    k_cg_spmv<P><<<sh.grid, sh.block, 0, s>>>(L, sc, u, p, z, q, partials);
+    note_launch();
+}
+template <class P>
+void launch_cg_tridiag(const Lv<P>& L, const Scalars* sc, typename P::S* r, const typename P::S* q,
+                       typename P::S* z, double* partials, cudaStream_t s) {
+    Shape sh = sweep_shape(L.nx, L.ny, L.nz, sizeof(typename P::R), true);
+    if (sh.smem > 32 * 1024)
+        cudaFuncSetAttribute(k_cg_tridiag<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+    k_cg_tridiag<P><<<sh.grid, sh.block, sh.smem, s>>>(L, sc, r, q, z, partials);
+    note_launch();
+}
+template <class P>
+void launch_cg_finish(size_t n, const Scalars* sc, typename P::S* u, const typename P::S* p,
+                      cudaStream_t s) {
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_cg_finish<P><<<(unsigned)blocks, 256, 0, s>>>(n, sc, u, p);
+    note_launch();
+}
+
+#define TPMG_CG_INST(P)                                                                             \
+    template void launch_cg_spmv<P>(const Lv<P>&, const Scalars*, P::S*, P::S*, const P::S*, P::S*, \
+                                    double*, cudaStream_t);                                        \
+    template void launch_cg_tridiag<P>(const Lv<P>&, const Scalars*, P::S*, const P::S*, P::S*,     \
+                                       double*, cudaStream_t);                                     \
+    template void launch_cg_finish<P>(size_t, const Scalars*, P::S*, const P::S*, cudaStream_t);
+
+TPMG_CG_INST(PolF64)
+TPMG_CG_INST(PolF32)
+TPMG_CG_INST(PolDW)
+
+}  // namespace tpmg

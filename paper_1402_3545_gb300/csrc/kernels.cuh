@@ -1,0 +1,137 @@
+// kernels.cuh -- internal declarations shared by the kernel translation units and the C-ABI layer.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "arith.cuh"
+
+namespace tpmg {
+
+// Sum of x over a block whose size is a multiple of 32, valid in thread 0. Warp shuffles, then
+// the warp sums in a fixed order: the result is deterministic.
+__device__ __forceinline__ double block_sum(double x) {
+    __shared__ double wsum[32];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nw = (blockDim.x * blockDim.y) >> 5;
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    __syncthreads();
+    if ((tid & 31) == 0) wsum[tid >> 5] = x;
+    __syncthreads();
+    double s = 0.0;
+    if (tid == 0)
+        for (int w = 0; w < nw; ++w) s += wsum[w];
+    return s;
+}
+
+// One multigrid level as the kernels see it: an nx x ny x nz box, x fastest, with horizontal
+// couplings cx = omega^2/hx^2, cy = omega^2/hy^2 (scaled by 1/4 per coarsening) and one vertical
+// coefficient v_ij = omega^2 lambda_ij^2 / hz^2 per column (stored in the policy's storage type).
+//
+// The Thomas factors of the level's column blocks, 1/m_k and w_k = v/m_k with
+// m_0 = D_0, m_k = D_k - v^2/m_{k-1}, depend only on the operator, so they are computed once per
+// level (k_factors) and read by the sweeps: fac_percol = 1 stores them per cell (index k*plane+c,
+// lambda^2 varying over the level); 0 stores one shared table of nz entries (lambda^2 constant).
+template <class P>
+struct Lv {
+    int nx, ny, nz;
+    double cx, cy;
+    const typename P::S* v;
+    const typename P::S* finv;
+    const typename P::S* fw;
+    int fac_percol;
+};
+
+// Device-resident solver scalars (one struct per running solve). All solver control decisions
+// are taken on the device by the finalize kernels so a whole iteration can be replayed from a
+// CUDA graph without host round trips; kernels return immediately once `done` is set.
+struct Scalars {
+    double r0;      // norm of the initial residual
+    double rel;     // latest relative residual
+    double tol;
+    double alpha, beta, kappa;  // CG: step, direction update, <r,z>
+    double last_norm;
+    int iters, max_iter, done, converged, nonfinite, pad;
+};
+
+// process-wide count of kernel launches issued by the library (k_util.cu)
+unsigned long long& launch_counter();
+inline void note_launch() { ++launch_counter(); }
+
+// launch shape of the column-sweep kernels: 32 consecutive x columns per warp row
+struct Shape {
+    dim3 grid, block;
+    size_t smem;
+    int nblocks() const { return (int)(grid.x * grid.y); }
+};
+
+// Thomas stack: two values (forward-eliminated rhs and w_k = v/m_k) per level per thread.
+Shape sweep_shape(int nx, int ny, int nz, int bytes_per_value, bool stack);
+int max_partials(int nx, int ny);
+
+// ---------------------------------------------------------------- launchers (k_sweep.cu)
+// Thomas factors of level L into finv/fw (per cell when percol, else a table of nz entries).
+template <class P>
+void launch_factors(const Lv<P>& L, typename P::S* finv, typename P::S* fw, int percol, cudaStream_t s);
+// Plane-pipelined Smooth for levels with nx % 32 == 0; returns false if the level does not fit.
+template <class P>
+bool launch_smooth_pp(const Lv<P>& L, double rho, const typename P::S* u, const typename P::S* f,
+                      typename P::S* uo, double* partials, const int* done, cudaStream_t s, int* nparts);
+
+// ---------------------------------------------------------------- launchers (k_mg.cu)
+template <class P>
+void launch_apply_A(const Lv<P>& L, const typename P::S* x, typename P::S* y, cudaStream_t s);
+// x = scale * M^{-1} b (scale = 1: the line solve; scale = rho: a smoothing step from zero)
+template <class P>
+void launch_line_solve(const Lv<P>& L, const typename P::S* b, typename P::S* x, double scale, const int* done,
+                       cudaStream_t s);
+// returns the number of blocks (partial sums written when partials != NULL)
+template <class P>
+int launch_smooth(const Lv<P>& L, double rho, const typename P::S* u, const typename P::S* f,
+                   typename P::S* uo, double* partials, const int* done, cudaStream_t s);
+// residual with the output in policy PO's storage (PO = P, or PolF32 for the mixed hand-over)
+template <class P, class PO>
+void launch_residual(const Lv<P>& L, const typename P::S* u, const typename P::S* f,
+                     typename PO::S* r, double* partials, const int* done, cudaStream_t s);
+// fine level in policy PF (its residual r_f), coarse level in P
+template <class PF, class P>
+void launch_restrict_smooth(const Lv<P>& Lc, double rho, const typename PF::S* rf,
+                            typename P::S* fc, typename P::S* uc, const int* done, cudaStream_t s);
+// coarse level in P, fine level in PF
+template <class P, class PF>
+void launch_prolongate(int nxc, int nyc, int nz, const typename P::S* uc, typename PF::S* uf,
+                       const int* done, cudaStream_t s);
+// u += e (e in FP32), the mixed-precision correction
+template <class P>
+void launch_correct(size_t n, typename P::S* u, const float* e, const int* done, cudaStream_t s);
+
+// ---------------------------------------------------------------- launchers (k_cg.cu)
+template <class P>
+void launch_cg_spmv(const Lv<P>& L, const Scalars* sc, typename P::S* u, typename P::S* p,
+                    const typename P::S* z, typename P::S* q, double* partials, cudaStream_t s);
+template <class P>
+void launch_cg_tridiag(const Lv<P>& L, const Scalars* sc, typename P::S* r, const typename P::S* q,
+                       typename P::S* z, double* partials, cudaStream_t s);
+template <class P>
+void launch_cg_finish(size_t n, const Scalars* sc, typename P::S* u, const typename P::S* p,
+                      cudaStream_t s);
+
+// ---------------------------------------------------------------- scalar kernels (k_util.cu)
+// modes of finalize_norm
+enum { FIN_STORE = 0, FIN_MG_INIT = 1, FIN_MG_CYCLE = 2, FIN_SUM = 3 };
+void launch_finalize_norm(const double* partials, int nparts, int mode, Scalars* sc,
+                          double* history, double* out, cudaStream_t s);
+void launch_cg_alpha(const double* partials, int nparts, Scalars* sc, cudaStream_t s);
+void launch_cg_beta(const double* partials, int nparts, int init, Scalars* sc, double* history,
+                    cudaStream_t s);
+void launch_scalars_init(Scalars* sc, double tol, int max_iter, cudaStream_t s);
+void launch_set_ab(Scalars* sc, double alpha, double beta, cudaStream_t s);
+// dst = src (n elements of P's storage) unless *done is set
+template <class P>
+void launch_copy(size_t n, const typename P::S* src, typename P::S* dst, const int* done, cudaStream_t s);
+void launch_f64_to_dw(size_t n, const double* x, float2* y, cudaStream_t s);
+void launch_dw_to_f64(size_t n, const float2* x, double* y, cudaStream_t s);
+void launch_f64_to_f32(size_t n, const double* x, float* y, cudaStream_t s);
+void launch_f32_to_f64(size_t n, const float* x, double* y, cudaStream_t s);
+void launch_coarsen_v_f64(int nxf, int nyf, const double* vf, double* vc, cudaStream_t s);
+
+}  // namespace tpmg

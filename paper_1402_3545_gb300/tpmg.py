@@ -1,0 +1,327 @@
+"""Thin ctypes binding of the C ABI in include/tpmg.h (libtpmg.so, built in-tree).
+
+Each function here has the name of the C entry point without its ``tpmg_`` prefix and only
+marshals arguments: torch CUDA tensors become device pointers, the current torch stream becomes
+the cudaStream_t, and a non-OK status becomes a ``TpmgError``. Every computation runs in the CUDA
+library; there is no CPU fallback -- importing this module without the built library raises.
+
+Fields are contiguous CUDA tensors of shape (nz, ny, nx): float64 for F64, DW and MIXED, float32
+for F32. Levels are numbered 1 (coarsest) .. L (finest) as in the paper's Sec. 2.2.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtpmg.so")
+
+F64, F32, DW, MIXED = 0, 1, 2, 3
+PREC = {"f64": F64, "f32": F32, "dw": DW, "mixed": MIXED}
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
+          4: "not converged", 5: "non-finite value", 6: "device wait timed out",
+          7: "learned stage rejected"}
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_NONFINITE, ERR_TIMEOUT, ERR_NN_REJECTED = range(8)
+
+
+class TpmgError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({msg})")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("n_coarse", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("rho", ctypes.c_double), ("tol", ctypes.c_double),
+                ("prec", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("r0", ctypes.c_double), ("history", ctypes.POINTER(ctypes.c_double)),
+                ("history_len", ctypes.c_int), ("ms", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+_SIGNATURES = {
+    "tpmg_create_grid": [_I, _I, _I, _I, ctypes.POINTER(_P)],
+    "tpmg_destroy_grid": [_P],
+    "tpmg_grid_nlevels": [_P],
+    "tpmg_grid_level_size": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "tpmg_create_operator": [_P, _D, _D, _D, _D, _D, _P, ctypes.POINTER(_P)],
+    "tpmg_destroy_operator": [_P],
+    "tpmg_op_reserve": [_P, _I],
+    "tpmg_op_level_coefficients": [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), _P],
+    "tpmg_apply_A": [_P, _I, _I, _P, _P, _P],
+    "tpmg_line_solve": [_P, _I, _I, _P, _P, _P],
+    "tpmg_smooth": [_P, _I, _I, _D, _P, _P, _P, _P, _P],
+    "tpmg_residual": [_P, _I, _I, _P, _P, _P, _P, _P],
+    "tpmg_restrict_smooth": [_P, _I, _I, _D, _P, _P, _P, _P],
+    "tpmg_prolongate": [_P, _I, _I, _P, _P, _P],
+    "tpmg_cg_fused_spmv": [_P, _I, _D, _D, _P, _P, _P, _P, _P, _P],
+    "tpmg_cg_fused_tridiag": [_P, _I, _D, _P, _P, _P, _P, _P, _P],
+    "tpmg_default_params": [ctypes.POINTER(Params)],
+    "tpmg_mg_solve": [_P, ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Info), _P],
+    "tpmg_vcycle": [_P, ctypes.POINTER(Params), _P, _P, _P],
+    "tpmg_cg_solve": [_P, ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Info), _P],
+    "tpmg_time_kernel": [_P, _I, _I, _I, ctypes.POINTER(_D), _P],
+    "tpmg_kernel_launches": [],
+    "tpmg_status_string": [_I],
+    "tpmg_last_error": [],
+}
+
+K_SMOOTH, K_RESIDUAL, K_APPLY_A, K_LINE_SOLVE, K_RESTRICT_SMOOTH, K_PROLONGATE, K_CG_SPMV, K_CG_TRIDIAG = range(8)
+
+
+def load():
+    """Loads libtpmg.so (raises if it has not been built: there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (nvcc, sm_103a)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = _I
+        lib.tpmg_status_string.restype = ctypes.c_char_p
+        lib.tpmg_last_error.restype = ctypes.c_char_p
+        lib.tpmg_grid_nlevels.restype = _I
+        lib.tpmg_default_params.restype = None
+        lib.tpmg_kernel_launches.restype = ctypes.c_ulonglong
+        _lib = lib
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGNATURES)
+
+
+def _check(status: int, where: str, allow=()):
+    if status != OK and status not in allow:
+        raise TpmgError(status, where, load().tpmg_last_error().decode())
+    return status
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _dtype(prec: int):
+    return torch.float32 if prec == F32 else torch.float64
+
+
+def _field(t: torch.Tensor, prec: int, numel: int, name: str) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != _dtype(prec):
+        raise TypeError(f"{name} must be {_dtype(prec)} for precision {prec}, got {t.dtype}")
+    if not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{name} must be contiguous with {numel} elements")
+    return t.data_ptr()
+
+
+def _scalar_out(t) -> int | None:
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.numel() >= 1):
+        raise TypeError("scalar outputs are CUDA float64 tensors")
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------- grid and operator
+def create_grid(nx: int, ny: int, nz: int, nlevels: int = 0) -> int:
+    h = _P()
+    _check(load().tpmg_create_grid(nx, ny, nz, nlevels, ctypes.byref(h)), "create_grid")
+    return h.value
+
+
+def destroy_grid(g: int) -> None:
+    load().tpmg_destroy_grid(g)
+
+
+def grid_nlevels(g: int) -> int:
+    return load().tpmg_grid_nlevels(g)
+
+
+def grid_level_size(g: int, level: int) -> tuple[int, int]:
+    nx, ny = _I(), _I()
+    _check(load().tpmg_grid_level_size(g, level, ctypes.byref(nx), ctypes.byref(ny)), "grid_level_size")
+    return nx.value, ny.value
+
+
+def create_operator(g: int, omega2: float, hx: float, hy: float, hz: float, lambda2=1.0):
+    """lambda2: a scalar, or a host array of shape (ny, nx) (lambda^2 per column)."""
+    import numpy as np
+    h = _P()
+    col = None
+    lam = 0.0
+    if np.ndim(lambda2) == 0:
+        lam = float(lambda2)
+    else:
+        col = np.ascontiguousarray(lambda2, dtype=np.float64)
+    ptr = col.ctypes.data_as(_P) if col is not None else None
+    _check(load().tpmg_create_operator(g, omega2, hx, hy, hz, lam, ptr, ctypes.byref(h)), "create_operator")
+    return h.value
+
+
+def destroy_operator(op: int) -> None:
+    load().tpmg_destroy_operator(op)
+
+
+def op_reserve(op: int, prec: int) -> None:
+    _check(load().tpmg_op_reserve(op, prec), "op_reserve")
+
+
+def op_level_coefficients(op: int, level: int, ncol: int):
+    import numpy as np
+    cx, cy = _D(), _D()
+    v = np.empty(ncol)
+    _check(load().tpmg_op_level_coefficients(op, level, ctypes.byref(cx), ctypes.byref(cy),
+                                             v.ctypes.data_as(_P)), "op_level_coefficients")
+    return cx.value, cy.value, v
+
+
+# ---------------------------------------------------------------- single applications
+def apply_A(op, level, prec, x, y, n, stream=None):
+    _check(load().tpmg_apply_A(op, level, prec, _field(x, prec, n, "x"), _field(y, prec, n, "y"),
+                               _stream(stream)), "apply_A")
+
+
+def line_solve(op, level, prec, b, x, n, stream=None):
+    _check(load().tpmg_line_solve(op, level, prec, _field(b, prec, n, "b"), _field(x, prec, n, "x"),
+                                  _stream(stream)), "line_solve")
+
+
+def smooth(op, level, prec, rho, u, f, u_out, n, norm_out=None, stream=None):
+    _check(load().tpmg_smooth(op, level, prec, rho, _field(u, prec, n, "u"), _field(f, prec, n, "f"),
+                              _field(u_out, prec, n, "u_out"), _scalar_out(norm_out), _stream(stream)),
+           "smooth")
+
+
+def residual(op, level, prec, u, f, r, n, norm_out=None, stream=None):
+    _check(load().tpmg_residual(op, level, prec, _field(u, prec, n, "u"), _field(f, prec, n, "f"),
+                                _field(r, prec, n, "r"), _scalar_out(norm_out), _stream(stream)), "residual")
+
+
+def restrict_smooth(op, level, prec, rho, r_fine, f_c, u_c, n_fine, n_coarse, stream=None):
+    _check(load().tpmg_restrict_smooth(op, level, prec, rho, _field(r_fine, prec, n_fine, "r_fine"),
+                                       _field(f_c, prec, n_coarse, "f_c"), _field(u_c, prec, n_coarse, "u_c"),
+                                       _stream(stream)), "restrict_smooth")
+
+
+def prolongate(op, level, prec, u_c, u_f, n_coarse, n_fine, stream=None):
+    _check(load().tpmg_prolongate(op, level, prec, _field(u_c, prec, n_coarse, "u_c"),
+                                  _field(u_f, prec, n_fine, "u_f"), _stream(stream)), "prolongate")
+
+
+def cg_fused_spmv(op, prec, alpha, beta, u, p, z, q, sigma_out, n, stream=None):
+    _check(load().tpmg_cg_fused_spmv(op, prec, alpha, beta, _field(u, prec, n, "u"), _field(p, prec, n, "p"),
+                                     _field(z, prec, n, "z"), _field(q, prec, n, "q"), _scalar_out(sigma_out),
+                                     _stream(stream)), "cg_fused_spmv")
+
+
+def cg_fused_tridiag(op, prec, alpha, r, q, z, rr_out, rz_out, n, stream=None):
+    _check(load().tpmg_cg_fused_tridiag(op, prec, alpha, _field(r, prec, n, "r"), _field(q, prec, n, "q"),
+                                        _field(z, prec, n, "z"), _scalar_out(rr_out), _scalar_out(rz_out),
+                                        _stream(stream)), "cg_fused_tridiag")
+
+
+# ---------------------------------------------------------------- solvers
+def default_params(**kw) -> Params:
+    p = Params()
+    load().tpmg_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "prec" and isinstance(v, str):
+            v = PREC[v]
+        setattr(p, k, v)
+    return p
+
+
+def _solve(fn_name, op, params, f, u, n, history_len, stream, allow):
+    prec = params.prec
+    hist = (ctypes.c_double * max(history_len, 1))()
+    info = Info()
+    info.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+    info.history_len = history_len
+    status = getattr(load(), fn_name)(op, ctypes.byref(params), _field(f, prec, n, "f"),
+                                      _field(u, prec, n, "u"), ctypes.byref(info), _stream(stream))
+    _check(status, fn_name[5:], allow=allow)
+    return {"status": status, "iters": info.iters, "converged": bool(info.converged),
+            "rel_res": info.rel_res, "r0": info.r0, "ms": info.ms,
+            "history": [hist[i] for i in range(min(info.iters + 1, history_len))]}
+
+
+def mg_solve(op, params, f, u, n, history_len=256, stream=None, allow=(ERR_NOT_CONVERGED,)):
+    return _solve("tpmg_mg_solve", op, params, f, u, n, history_len, stream, allow)
+
+
+def cg_solve(op, params, f, u, n, history_len=4096, stream=None, allow=(ERR_NOT_CONVERGED,)):
+    return _solve("tpmg_cg_solve", op, params, f, u, n, history_len, stream, allow)
+
+
+def vcycle(op, params, f, u, n, stream=None):
+    prec = params.prec
+    _check(load().tpmg_vcycle(op, ctypes.byref(params), _field(f, prec, n, "f"), _field(u, prec, n, "u"),
+                              _stream(stream)), "vcycle")
+
+
+# ---------------------------------------------------------------- profiling
+def time_kernel(op, prec, kernel, reps=10, stream=None) -> float:
+    """Mean duration in ms of one launch of an internal kernel on the operator's workspace."""
+    ms = _D()
+    _check(load().tpmg_time_kernel(op, prec, kernel, reps, ctypes.byref(ms), _stream(stream)), "time_kernel")
+    return ms.value
+
+
+def kernel_launches() -> int:
+    return int(load().tpmg_kernel_launches())
+
+
+# ---------------------------------------------------------------- convenience owner object
+class Operator:
+    """Owns a grid and an operator built from a workloads.Problem-like description."""
+
+    def __init__(self, nx, ny, nz, omega2, hx, hy, hz, lambda2, nlevels=0):
+        self.grid = create_grid(nx, ny, nz, nlevels)
+        self.op = None
+        self.op = create_operator(self.grid, omega2, hx, hy, hz, lambda2)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.L = grid_nlevels(self.grid)
+
+    @classmethod
+    def from_problem(cls, p, nlevels=None):
+        return cls(p.nx, p.ny, p.nz, p.omega2, p.hx, p.hy, p.hz, p.lambda2,
+                   p.nlevels if nlevels is None else nlevels)
+
+    def level_shape(self, level):
+        nx, ny = grid_level_size(self.grid, level)
+        return (self.nz, ny, nx)
+
+    def level_n(self, level):
+        a, b, c = self.level_shape(level)
+        return a * b * c
+
+    def close(self):
+        if self.op:
+            destroy_operator(self.op)
+            self.op = None
+        if self.grid:
+            destroy_grid(self.grid)
+            self.grid = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

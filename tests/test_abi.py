@@ -1,0 +1,60 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point include/*.h declares.
+No GPU needed (no compute call is made)."""
+import ctypes
+import glob
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(tpmg_[A-Za-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1402_3545_gb300 import build
+    lib_path = build.build()
+    lib = ctypes.CDLL(lib_path)
+    names = declared_symbols()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    from paper_1402_3545_gb300 import tpmg
+    assert set(declared_symbols()) <= set(tpmg.exported_symbols()) | {"tpmg_nn_create"}
+
+
+def test_status_strings_without_gpu():
+    from paper_1402_3545_gb300 import tpmg
+    lib = tpmg.load()
+    assert lib.tpmg_status_string(0) == b"ok"
+    assert lib.tpmg_status_string(4) == b"not converged"
+
+
+def test_grid_argument_checks_without_gpu():
+    """Grid creation is pure host logic: divisibility and size checks, level rule."""
+    from paper_1402_3545_gb300 import tpmg
+    g = tpmg.create_grid(512, 512, 128, 0)
+    assert tpmg.grid_nlevels(g) == 7
+    assert tpmg.grid_level_size(g, 1) == (8, 8)
+    tpmg.destroy_grid(g)
+    g = tpmg.create_grid(64, 64, 64, 0)
+    assert tpmg.grid_nlevels(g) == 4
+    tpmg.destroy_grid(g)
+    g = tpmg.create_grid(256, 128, 32, 0)
+    assert tpmg.grid_nlevels(g) == 5 and tpmg.grid_level_size(g, 1) == (16, 8)
+    tpmg.destroy_grid(g)
+    import pytest
+    with pytest.raises(tpmg.TpmgError):
+        tpmg.create_grid(60, 64, 8, 4)  # 60 not divisible by 8
+    with pytest.raises(tpmg.TpmgError):
+        tpmg.create_grid(64, 64, 300, 0)  # nz above the supported maximum

@@ -1,0 +1,179 @@
+"""GPU parity of every kernel of the hot path against the FP64 oracle, element by element, on
+seeded inputs that span several 32-wide warps, several blocks and ragged tails in x and y.
+
+Called through the C ABI (libtpmg.so) via the thin binding; compared with oracle/ (plain C).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_common import PREC_IDS, PRECS, TOL, dev, host, make_problem, oracle_levels, rel, tol_inverse
+from paper_1402_3545_gb300 import tpmg
+
+pytestmark = pytest.mark.gpu
+
+# (nx, ny, nz, nlevels): ragged x (not a multiple of 32), ragged y, odd nz, single column height
+SHAPES = [(80, 36, 24, 3), (64, 64, 64, 4), (40, 12, 7, 3), (96, 8, 1, 2), (16, 16, 128, 2)]
+SHAPE_IDS = [f"{a}x{b}x{c}L{d}" for a, b, c, d in SHAPES]
+
+
+@pytest.fixture(scope="module", params=SHAPES, ids=SHAPE_IDS)
+def setup(request):
+    nx, ny, nz, L = request.param
+    p = make_problem(nx, ny, nz)
+    op = tpmg.Operator.from_problem(p, nlevels=L)
+    cx, cy, v = oracle.problem_coefficients(p)
+    lv = oracle_levels(cx, cy, v, L)
+    yield op, lv, p
+    op.close()
+
+
+def rnd(shape, seed):
+    return np.random.default_rng(seed).standard_normal(shape)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_apply_A(setup, prec):
+    op, lv, p = setup
+    for level in range(1, op.L + 1):
+        sh = op.level_shape(level)
+        x = rnd(sh, 1 + level)
+        y = torch.empty_like(dev(x, prec))
+        tpmg.apply_A(op.op, level, prec, dev(x, prec), y, op.level_n(level))
+        ref = oracle.apply_A(x, *lv[level])
+        assert rel(host(y), ref) < TOL[prec], (level, rel(host(y), ref))
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_line_solve(setup, prec):
+    op, lv, p = setup
+    for level in range(1, op.L + 1):
+        sh = op.level_shape(level)
+        b = rnd(sh, 10 + level)
+        x = torch.empty_like(dev(b, prec))
+        tpmg.line_solve(op.op, level, prec, dev(b, prec), x, op.level_n(level))
+        ref = oracle.line_solve(b, *lv[level])
+        assert rel(host(x), ref) < tol_inverse(prec, *lv[level]), (level, rel(host(x), ref))
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_smooth_with_fused_norm(setup, prec):
+    op, lv, p = setup
+    rho = 0.8
+    for level in range(1, op.L + 1):
+        sh = op.level_shape(level)
+        u, f = rnd(sh, 20 + level), rnd(sh, 30 + level)
+        out = torch.empty_like(dev(u, prec))
+        nrm = torch.zeros(1, dtype=torch.float64, device="cuda")
+        tpmg.smooth(op.op, level, prec, rho, dev(u, prec), dev(f, prec), out, op.level_n(level), norm_out=nrm)
+        ref = oracle.smooth(u, f, *lv[level], rho)
+        assert rel(host(out), ref) < tol_inverse(prec, *lv[level]), (level, rel(host(out), ref))
+        rnorm = np.linalg.norm(oracle.residual(u, f, *lv[level]))
+        assert abs(host(nrm)[0] - rnorm) / rnorm < max(TOL[prec], 1e-7)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_residual_with_fused_norm(setup, prec):
+    op, lv, p = setup
+    for level in range(1, op.L + 1):
+        sh = op.level_shape(level)
+        u, f = rnd(sh, 40 + level), rnd(sh, 50 + level)
+        r = torch.empty_like(dev(u, prec))
+        nrm = torch.zeros(1, dtype=torch.float64, device="cuda")
+        tpmg.residual(op.op, level, prec, dev(u, prec), dev(f, prec), r, op.level_n(level), norm_out=nrm)
+        ref = oracle.residual(u, f, *lv[level])
+        assert rel(host(r), ref) < TOL[prec], (level, rel(host(r), ref))
+        assert abs(host(nrm)[0] - np.linalg.norm(ref)) / np.linalg.norm(ref) < max(TOL[prec], 1e-7)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_restrict_smooth(setup, prec):
+    op, lv, p = setup
+    rho = 0.8
+    for level in range(1, op.L):
+        rf = rnd(op.level_shape(level + 1), 60 + level)
+        fc = torch.empty(op.level_shape(level), dtype=dev(rf, prec).dtype, device="cuda")
+        uc = torch.empty_like(fc)
+        tpmg.restrict_smooth(op.op, level, prec, rho, dev(rf, prec), fc, uc, op.level_n(level + 1), op.level_n(level))
+        f_ref = oracle.restrict(rf)
+        u_ref = rho * oracle.line_solve(f_ref, *lv[level])
+        assert rel(host(fc), f_ref) < TOL[prec]
+        assert rel(host(uc), u_ref) < tol_inverse(prec, *lv[level]), (level, rel(host(uc), u_ref))
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_prolongate(setup, prec):
+    op, lv, p = setup
+    for level in range(2, op.L + 1):
+        uc = rnd(op.level_shape(level - 1), 70 + level)
+        uf = rnd(op.level_shape(level), 80 + level)
+        t = dev(uf, prec)
+        tpmg.prolongate(op.op, level, prec, dev(uc, prec), t, op.level_n(level - 1), op.level_n(level))
+        ref = oracle.prolongate_add(uc, uf)
+        assert rel(host(t), ref) < TOL[prec], (level, rel(host(t), ref))
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_cg_fused_kernels(setup, prec):
+    """Fused SpMV and fused Tridiag (Sec. 3.1) against their definitions applied with the oracle's
+    operator and line solve."""
+    op, lv, p = setup
+    L = op.L
+    sh = op.level_shape(L)
+    n = op.level_n(L)
+    u, pp, z, q, r = (rnd(sh, 90 + s) for s in range(5))
+    alpha, beta = 0.37, 0.61
+    tu, tp, tz, tq = dev(u, prec), dev(pp, prec), dev(z, prec), dev(q, prec)
+    sigma = torch.zeros(1, dtype=torch.float64, device="cuda")
+    tpmg.cg_fused_spmv(op.op, prec, alpha, beta, tu, tp, tz, tq, sigma, n)
+    u_ref = u + alpha * pp
+    p_ref = z + beta * pp
+    q_ref = oracle.apply_A(z, *lv[L]) + beta * q
+    assert rel(host(tu), u_ref) < TOL[prec]
+    assert rel(host(tp), p_ref) < TOL[prec]
+    assert rel(host(tq), q_ref) < TOL[prec]
+    s_ref = float(np.sum(p_ref * q_ref))
+    assert abs(host(sigma)[0] - s_ref) <= max(TOL[prec], 1e-7) * np.linalg.norm(p_ref) * np.linalg.norm(q_ref)
+
+    tr, tq2, tz2 = dev(r, prec), dev(q, prec), torch.empty_like(dev(r, prec))
+    rr = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rz = torch.zeros(1, dtype=torch.float64, device="cuda")
+    tpmg.cg_fused_tridiag(op.op, prec, alpha, tr, tq2, tz2, rr, rz, n)
+    r_ref = r - alpha * q
+    z_ref = oracle.line_solve(r_ref, *lv[L])
+    assert rel(host(tr), r_ref) < TOL[prec]
+    assert rel(host(tz2), z_ref) < tol_inverse(prec, *lv[L])
+    assert abs(host(rr)[0] - np.sum(r_ref ** 2)) / np.sum(r_ref ** 2) < max(TOL[prec], 1e-7)
+    rz_ref = float(np.sum(r_ref * z_ref))
+    assert abs(host(rz)[0] - rz_ref) <= max(tol_inverse(prec, *lv[L]), 1e-7) * np.linalg.norm(r_ref) * np.linalg.norm(z_ref)
+
+
+def test_deterministic_reductions(setup):
+    """Two identical applications give bit-identical outputs and norms (fixed-order reductions)."""
+    op, lv, p = setup
+    L = op.L
+    sh = op.level_shape(L)
+    u, f = dev(rnd(sh, 5), tpmg.DW), dev(rnd(sh, 6), tpmg.DW)
+    outs, norms = [], []
+    for _ in range(2):
+        o = torch.empty_like(u)
+        nrm = torch.zeros(1, dtype=torch.float64, device="cuda")
+        tpmg.smooth(op.op, L, tpmg.DW, 0.8, u, f, o, op.level_n(L), norm_out=nrm)
+        outs.append(host(o))
+        norms.append(host(nrm)[0])
+    assert np.array_equal(outs[0], outs[1]) and norms[0] == norms[1]
+
+
+def test_argument_errors(setup):
+    op, lv, p = setup
+    sh = op.level_shape(op.L)
+    x = dev(rnd(sh, 7), tpmg.F64)
+    y = torch.empty_like(x)
+    with pytest.raises(tpmg.TpmgError) as e:
+        tpmg.apply_A(op.op, op.L + 1, tpmg.F64, x, y, op.level_n(op.L))
+    assert e.value.status == tpmg.ERR_ARG
+    with pytest.raises(tpmg.TpmgError):
+        tpmg.prolongate(op.op, 1, tpmg.F64, x, y, op.level_n(op.L), op.level_n(op.L))
+    with pytest.raises(TypeError):
+        tpmg.apply_A(op.op, op.L, tpmg.F32, x, y, op.level_n(op.L))

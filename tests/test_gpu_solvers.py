@@ -1,0 +1,155 @@
+"""GPU solvers against the oracle: one V-cycle element by element, the multigrid iteration
+(same iteration count, same residual history, same iterate), CG, the mixed-precision refinement,
+status codes and the graph/no-graph equivalence. All calls go through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_common import TOL, dev, host, make_problem, oracle_levels, rel
+from paper_1402_3545_gb300 import tpmg, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def small():
+    """The small benchmark problem: 64^2 x 64, lambda^2 = 1e3, 4 levels, zero-mean uniform RHS."""
+    p = workloads.small()
+    op = tpmg.Operator.from_problem(p)
+    cx, cy, v = oracle.problem_coefficients(p)
+    f = p.rhs()
+    ref = oracle.mg_solve(f, cx, cy, v, p.nlevels, tol=1e-6, max_iter=100)
+    yield p, op, (cx, cy, v), f, ref
+    op.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(tpmg.F64, 1e-10), (tpmg.DW, 1e-10), (tpmg.F32, 1e-4)],
+                         ids=["f64", "dw", "f32"])
+@pytest.mark.parametrize("nu", [(2, 2, 2), (1, 1, 2), (2, 1, 3)], ids=["V22", "V11", "V21c3"])
+def test_vcycle_matches_oracle(prec, tol, nu):
+    nx, ny, nz, L = 64, 48, 16, 3
+    p = make_problem(nx, ny, nz)
+    op = tpmg.Operator.from_problem(p, nlevels=L)
+    cx, cy, v = oracle.problem_coefficients(p)
+    rng = np.random.default_rng(3)
+    u0, f = rng.standard_normal((nz, ny, nx)), rng.standard_normal((nz, ny, nx))
+    prm = tpmg.default_params(prec=prec, nu_pre=nu[0], nu_post=nu[1], n_coarse=nu[2], rho=0.8)
+    tu = dev(u0, prec)
+    tpmg.vcycle(op.op, prm, dev(f, prec), tu, op.level_n(L))
+    ref = oracle.vcycle(u0, f, cx, cy, v, L, nu_pre=nu[0], nu_post=nu[1], n_coarse=nu[2], rho=0.8)
+    assert rel(host(tu), ref) < tol, rel(host(tu), ref)
+    op.close()
+
+
+@pytest.mark.parametrize("prec", [tpmg.F64, tpmg.DW], ids=["f64", "dw"])
+def test_mg_solve_reproduces_oracle_iteration(small, prec):
+    p, op, (cx, cy, v), f, (u_ref, it_ref, hist_ref, conv_ref) = small
+    prm = tpmg.default_params(prec=prec, tol=1e-6, max_iter=100)
+    u = torch.zeros(p.nz, p.ny, p.nx, dtype=torch.float64, device="cuda")
+    res = tpmg.mg_solve(op.op, prm, dev(f, prec), u, p.n)
+    assert conv_ref and res["converged"]
+    assert res["iters"] == it_ref
+    assert np.allclose(res["history"], hist_ref, rtol=1e-8, atol=0)
+    assert rel(host(u), u_ref) < 1e-10
+    # the residual recomputed on the host by the oracle's operator meets the tolerance
+    r = oracle.residual(host(u), f, cx, cy, v)
+    assert np.linalg.norm(r) / np.linalg.norm(f) < 1e-6
+
+
+def test_mg_solve_mixed_precision(small):
+    """FP32 V-cycles inside double-word iterative refinement reach 1e-6 and 1e-10; the error
+    against the exact solution is reported and bounded."""
+    p, op, (cx, cy, v), f, _ = small
+    exact = oracle.mg_solve(f, cx, cy, v, p.nlevels, tol=1e-13, max_iter=200)[0]
+    for tol in (1e-6, 1e-10):
+        prm = tpmg.default_params(prec=tpmg.MIXED, tol=tol, max_iter=100)
+        u = torch.zeros(p.nz, p.ny, p.nx, dtype=torch.float64, device="cuda")
+        res = tpmg.mg_solve(op.op, prm, dev(f, tpmg.F64), u, p.n)
+        assert res["converged"], res
+        r = oracle.residual(host(u), f, cx, cy, v)
+        assert np.linalg.norm(r) / np.linalg.norm(f) < tol * 1.001
+        # error bound: ||e|| <= ||A^-1|| ||r|| <= ||r|| since lambda_min(A) = 1
+        assert np.linalg.norm(host(u) - exact) <= np.linalg.norm(r) * 1.001 + 1e-12 * np.linalg.norm(exact)
+
+
+def test_mg_solve_f32(small):
+    """Plain FP32 multigrid: the residual of an FP32 iterate cannot drop much below
+    eps_32 * ||A|| ||u|| / ||f|| (here ~1e-5), so the FP32 solver is asked for 1e-4 and its
+    answer is checked with the oracle's FP64 residual."""
+    p, op, (cx, cy, v), f, _ = small
+    prm = tpmg.default_params(prec=tpmg.F32, tol=1e-4, max_iter=100)
+    u = torch.zeros(p.nz, p.ny, p.nx, dtype=torch.float32, device="cuda")
+    res = tpmg.mg_solve(op.op, prm, dev(f, tpmg.F32), u, p.n)
+    assert res["converged"]
+    r = oracle.residual(host(u), f, cx, cy, v)
+    assert np.linalg.norm(r) / np.linalg.norm(f) < 2e-4
+
+
+@pytest.mark.parametrize("prec", [tpmg.F64, tpmg.DW], ids=["f64", "dw"])
+def test_cg_solve_matches_oracle(small, prec):
+    p, op, (cx, cy, v), f, _ = small
+    u_ref, it_ref, hist_ref, conv_ref = oracle.cg_solve(f, cx, cy, v, tol=1e-6, max_iter=2000)
+    prm = tpmg.default_params(prec=prec, tol=1e-6, max_iter=2000)
+    u = torch.zeros(p.nz, p.ny, p.nx, dtype=torch.float64, device="cuda")
+    res = tpmg.cg_solve(op.op, prm, dev(f, prec), u, p.n)
+    assert conv_ref and res["converged"]
+    assert abs(res["iters"] - it_ref) <= 1
+    k = min(20, it_ref)
+    assert np.allclose(res["history"][:k], hist_ref[:k], rtol=1e-7)
+    r = oracle.residual(host(u), f, cx, cy, v)
+    assert np.linalg.norm(r) / np.linalg.norm(f) < 1e-6 * 1.01
+    assert rel(host(u), u_ref) < 1e-4
+
+
+def test_status_codes(small):
+    p, op, (cx, cy, v), f, _ = small
+    u = torch.zeros(p.nz, p.ny, p.nx, dtype=torch.float64, device="cuda")
+    prm = tpmg.default_params(prec=tpmg.DW, tol=1e-12, max_iter=2)
+    res = tpmg.mg_solve(op.op, prm, dev(f, tpmg.DW), u, p.n)
+    assert res["status"] == tpmg.ERR_NOT_CONVERGED and res["iters"] == 2 and not res["converged"]
+    # zero right-hand side with zero guess: converged before the first cycle
+    u.zero_()
+    res = tpmg.mg_solve(op.op, tpmg.default_params(prec=tpmg.DW), torch.zeros_like(u), u, p.n)
+    assert res["converged"] and res["iters"] == 0 and not u.any()
+    # NaN in the right-hand side is reported, not hidden
+    fb = f.copy()
+    fb[3, 5, 7] = np.nan
+    with pytest.raises(tpmg.TpmgError) as e:
+        tpmg.mg_solve(op.op, tpmg.default_params(prec=tpmg.DW), dev(fb, tpmg.DW), u.zero_(), p.n)
+    assert e.value.status == tpmg.ERR_NONFINITE
+    with pytest.raises(tpmg.TpmgError) as e:
+        tpmg.cg_solve(op.op, tpmg.default_params(prec=tpmg.F64), dev(fb, tpmg.F64), u.zero_(), p.n)
+    assert e.value.status == tpmg.ERR_NONFINITE
+    with pytest.raises(tpmg.TpmgError) as e:
+        tpmg.mg_solve(op.op, tpmg.default_params(prec=tpmg.DW, nu_pre=0), dev(f, tpmg.DW), u, p.n)
+    assert e.value.status == tpmg.ERR_ARG
+
+
+@pytest.mark.parametrize("prec", [tpmg.DW, tpmg.MIXED], ids=["dw", "mixed"])
+def test_graph_replay_equals_plain_launches(small, prec):
+    p, op, _, f, _ = small
+    outs = []
+    for g in (0, 1, 1):
+        u = torch.zeros(p.nz, p.ny, p.nx, dtype=torch.float64, device="cuda")
+        res = tpmg.mg_solve(op.op, tpmg.default_params(prec=prec, use_graph=g), dev(f, tpmg.F64), u, p.n)
+        outs.append((host(u), res["iters"], res["history"]))
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and o[1] == outs[0][1] and o[2] == outs[0][2]
+
+
+def test_odd_smoothing_count_and_single_level():
+    """nu_pre + nu_post odd (the iterate changes buffer each cycle) and a one-level hierarchy."""
+    p = make_problem(32, 32, 8)
+    cx, cy, v = oracle.problem_coefficients(p)
+    f = np.random.default_rng(4).standard_normal((8, 32, 32))
+    for L, nu in ((3, (2, 1)), (1, (1, 1))):
+        op = tpmg.Operator.from_problem(p, nlevels=L)
+        prm = tpmg.default_params(prec=tpmg.DW, nu_pre=nu[0], nu_post=nu[1], tol=1e-8, max_iter=60)
+        u = torch.zeros(8, 32, 32, dtype=torch.float64, device="cuda")
+        res = tpmg.mg_solve(op.op, prm, dev(f, tpmg.DW), u, p.n)
+        u_ref, it_ref, hist_ref, _ = oracle.mg_solve(f, cx, cy, v, L, tol=1e-8, max_iter=60,
+                                                      nu_pre=nu[0], nu_post=nu[1])
+        assert res["iters"] == it_ref
+        assert rel(host(u), u_ref) < 1e-10
+        op.close()
