@@ -190,6 +190,34 @@ tpmg_status tpmg_time_kernel(tpmg_op* op, tpmg_precision prec, tpmg_kernel k, in
  * counts every kernel node it contains). */
 unsigned long long tpmg_kernel_launches(void);
 
+/* ---------------------------------------------------------------- allocation-free variant
+ * The paper has no counterpart: this entry point exists for callers that must not allocate device
+ * memory while they run -- applications whose framework already owns nearly all device memory
+ * through its own pool (a raw cudaMalloc there can fail or fragment that pool) and latency-critical
+ * loops where cudaMalloc's implicit device synchronisation is not acceptable. Every other entry
+ * point allocates workspace inside its operator; this one needs no operator and allocates nothing
+ * (no cudaMalloc, cudaFree or allocating library routine).
+ *
+ * r = f - A u and *norm_out = ||r||_2 on one nx x ny x nz level, native FP64, with A as in the
+ * header comment: cx, cy the horizontal couplings, v a DEVICE array of ny*nx vertical couplings
+ * (index j*nx + i); u, f, r DEVICE arrays of nz*ny*nx doubles (x fastest, r must not overlap u or
+ * f); norm_out a DEVICE double. Same kernels and results as tpmg_residual(op, L, TPMG_F64, ...).
+ *
+ * Scratch: one partial sum per thread block in a fixed file-scope device array of
+ * TPMG_NOALLOC_MAX_BLOCKS doubles (512 KB), held by every GPU that loads the library until the
+ * process exits. Sizes needing more blocks (ceil(nx/32) * ceil(ny/4) > TPMG_NOALLOC_MAX_BLOCKS,
+ * e.g. nx*ny above about 8.4 million columns) are rejected with TPMG_ERR_ARG and a message in
+ * tpmg_noalloc_last_error(). All calls share the array and each call overwrites the entries it
+ * reads before reading them, so no clearing is needed; calls that overlap on the GPU (on
+ * different streams or host threads without ordering) race on it and must be serialised.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture. */
+#define TPMG_NOALLOC_MAX_BLOCKS 65536
+tpmg_status tpmg_residual_norm_noalloc(int nx, int ny, int nz, double cx, double cy, const double* v,
+                                       const double* u, const double* f, double* r, double* norm_out,
+                                       void* stream);
+const char* tpmg_noalloc_last_error(void);
+
 const char* tpmg_status_string(tpmg_status s);
 /* Message of the last error in the calling thread ("" if none). */
 const char* tpmg_last_error(void);

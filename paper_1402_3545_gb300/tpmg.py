@@ -70,6 +70,8 @@ _SIGNATURES = {
     "tpmg_mg_solve": [_P, ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Info), _P],
     "tpmg_vcycle": [_P, ctypes.POINTER(Params), _P, _P, _P],
     "tpmg_cg_solve": [_P, ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Info), _P],
+    "tpmg_residual_norm_noalloc": [_I, _I, _I, _D, _D, _P, _P, _P, _P, _P, _P],
+    "tpmg_noalloc_last_error": [],
     "tpmg_time_kernel": [_P, _I, _I, _I, ctypes.POINTER(_D), _P],
     "tpmg_kernel_launches": [],
     "tpmg_status_string": [_I],
@@ -92,6 +94,7 @@ def load():
             fn.restype = _I
         lib.tpmg_status_string.restype = ctypes.c_char_p
         lib.tpmg_last_error.restype = ctypes.c_char_p
+        lib.tpmg_noalloc_last_error.restype = ctypes.c_char_p
         lib.tpmg_grid_nlevels.restype = _I
         lib.tpmg_default_params.restype = None
         lib.tpmg_kernel_launches.restype = ctypes.c_ulonglong
@@ -274,6 +277,26 @@ def vcycle(op, params, f, u, n, stream=None):
     prec = params.prec
     _check(load().tpmg_vcycle(op, ctypes.byref(params), _field(f, prec, n, "f"), _field(u, prec, n, "u"),
                               _stream(stream)), "vcycle")
+
+
+# ---------------------------------------------------------------- allocation-free variant
+NOALLOC_MAX_BLOCKS = 65536
+
+
+def residual_norm_noalloc(nx, ny, nz, cx, cy, v, u, f, r, norm_out, stream=None):
+    """r = f - A u and ||r|| (FP64) for callers that must not allocate device memory: no operator,
+    no workspace; the per-block partial sums live in the library's fixed device array. v is a CUDA
+    float64 tensor of ny*nx vertical couplings; u, f, r are CUDA float64 fields; norm_out a CUDA
+    float64 tensor of at least one element. Calls that overlap on the GPU must be serialised."""
+    n = nx * ny * nz
+    if not (isinstance(v, torch.Tensor) and v.is_cuda and v.dtype == torch.float64 and v.numel() == nx * ny
+            and v.is_contiguous()):
+        raise TypeError("v must be a contiguous CUDA float64 tensor of ny*nx elements")
+    status = load().tpmg_residual_norm_noalloc(nx, ny, nz, cx, cy, v.data_ptr(), _field(u, F64, n, "u"),
+                                               _field(f, F64, n, "f"), _field(r, F64, n, "r"),
+                                               _scalar_out(norm_out), _stream(stream))
+    if status != OK:
+        raise TpmgError(status, "residual_norm_noalloc", load().tpmg_noalloc_last_error().decode())
 
 
 # ---------------------------------------------------------------- profiling
