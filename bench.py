@@ -183,6 +183,8 @@ def run_ours(args, rank, world, dist):
     prec = tpmg.DW
     prm = tpmg.default_params(prec=prec, tol=1e-6, max_iter=100)
     tpmg.op_reserve(op.op, prec)
+    from paper_1402_3545_gb300 import autotune
+    variants_dw = autotune.tune(op, prec, lambda_varies=True)
     fd = torch.from_numpy(f).to(dev)
     u = torch.zeros_like(fd)
     stream = torch.cuda.current_stream()
@@ -238,6 +240,11 @@ def run_ours(args, rank, world, dist):
         ("residual", tpmg.K_RESIDUAL), ("restrict_smooth", tpmg.K_RESTRICT_SMOOTH),
         ("prolongate", tpmg.K_PROLONGATE), ("cg_spmv", tpmg.K_CG_SPMV), ("cg_tridiag", tpmg.K_CG_TRIDIAG)]}
     kernel_ms["smooth"] = round(t_smooth, 4)
+    tpmg.op_reserve(op.op, tpmg.MIXED)
+    variants_f32 = autotune.tune(op, tpmg.F32, lambda_varies=True)
+    kernel_ms_f32 = {name: round(tpmg.time_kernel(op.op, tpmg.F32, kid, reps=10), 4) for name, kid in [
+        ("smooth", tpmg.K_SMOOTH), ("residual", tpmg.K_RESIDUAL), ("line_solve", tpmg.K_LINE_SOLVE),
+        ("restrict_smooth", tpmg.K_RESTRICT_SMOOTH), ("prolongate", tpmg.K_PROLONGATE)]}
     n_smooth = 4 * iters[-1] + 1
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
@@ -291,7 +298,8 @@ def run_ours(args, rank, world, dist):
                            "solver": "V(2,2), rho 0.8, 2 coarse steps", "tol": 1e-6, "precision": "DW",
                            "parallelism": f"replicas{world}",
                            "l2": "inputs larger than L2 (268 MB per FP64 field > 129 MB)"},
-                "iters": iters[-1], "roofline": roofline, "kernel_ms": kernel_ms, "variants": variants,
+                "iters": iters[-1], "roofline": roofline, "kernel_ms": kernel_ms, "kernel_ms_f32": kernel_ms_f32,
+                "tile_variants": {"dw": variants_dw, "f32": variants_f32}, "variants": variants,
                 "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": 8 * n,
                         "d2h_bytes_per_step": 8 * n},
                 "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches)}

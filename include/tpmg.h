@@ -190,6 +190,18 @@ tpmg_status tpmg_time_kernel(tpmg_op* op, tpmg_precision prec, tpmg_kernel k, in
  * counts every kernel node it contains). */
 unsigned long long tpmg_kernel_launches(void);
 
+/* ---------------------------------------------------------------- autotuning
+ * The plane-pipelined Smooth has TPMG_NUM_VARIANTS tile shapes (columns per block x ring depth).
+ * tpmg_autotune times each of them `reps` times on every level of precision `prec` (on the
+ * operator's workspace, CUDA events on `stream`) and keeps the fastest per level; if variants_out
+ * is not NULL it receives the choice of level l in variants_out[l] (host array of L+1 ints).
+ * tpmg_set_variant sets one level's choice (e.g. from a saved tuning table). Both invalidate the
+ * operator's cached CUDA graphs. Variants change the schedule, not the per-cell arithmetic (only the
+ * grouping of the residual norm's partial sums differs). */
+#define TPMG_NUM_VARIANTS 3
+tpmg_status tpmg_autotune(tpmg_op* op, tpmg_precision prec, int reps, int* variants_out, void* stream);
+tpmg_status tpmg_set_variant(tpmg_op* op, tpmg_precision prec, int level, int variant);
+
 /* ---------------------------------------------------------------- allocation-free variant
  * The paper has no counterpart: this entry point exists for callers that must not allocate device
  * memory while they run -- applications whose framework already owns nearly all device memory

@@ -76,6 +76,7 @@ struct tpmg_op {
     double kappa_M[MAXL + 1] = {}; // condition number of the level's column blocks
     int lsw_dw = 1;                // the double-word solver uses native FP64 below this level
     bool fac_ready[3] = {false, false, false};
+    int variant[3][MAXL + 1];      // autotuned tile variant of the pipelined Smooth (-1: default)
     void* cgbuf[3][4] = {};  // r, z, p, q per policy
     void* io[4] = {};        // DW conversion buffers for single applications (finest-level size)
     double* partials = nullptr;
@@ -114,6 +115,7 @@ static Lv<P> level_view(const tpmg_op* op, int l) {
     L.finv = (const typename P::S*)op->finv[P::id][l];
     L.fw = (const typename P::S*)op->fw[P::id][l];
     L.fac_percol = op->percol[l];
+    L.variant = op->variant[P::id][l];
     return L;
 }
 
@@ -439,9 +441,8 @@ static tpmg_status mixed_loop(tpmg_op* op, const tpmg_params* prm, float2* uD, c
     const size_t nfine = lvl_cells(op, L);
     Lv<PolDW> LD = level_view<PolDW>(op, L);
     Lv<PolF32> L32 = level_view<PolF32>(op, L);
-    const int nparts = sweep_shape(LD.nx, LD.ny, LD.nz, sizeof(dw), false).nblocks();
     launch_scalars_init(op->sc, prm->tol, prm->max_iter, s);
-    launch_residual<PolDW, PolF32>(LD, uD, fD, r32, op->partials, done, s);
+    const int nparts = launch_residual<PolDW, PolF32>(LD, uD, fD, r32, op->partials, done, s);
     launch_finalize_norm(op->partials, nparts, FIN_MG_INIT, op->sc, op->history, nullptr, s);
     CK(cudaGetLastError());
     TRY(read_scalars(op, s));
@@ -453,8 +454,8 @@ static tpmg_status mixed_loop(tpmg_op* op, const tpmg_params* prm, float2* uD, c
         launch_line_solve<PolF32>(L32, r32, e, prm->rho, done, st);
         c.rest(cur, oth);
         launch_correct<PolDW>(nfine, uD, (const float*)cur, done, st);
-        launch_residual<PolDW, PolF32>(LD, uD, fD, r32, op->partials, done, st);
-        launch_finalize_norm(op->partials, nparts, FIN_MG_CYCLE, op->sc, op->history, nullptr, st);
+        const int np = launch_residual<PolDW, PolF32>(LD, uD, fD, r32, op->partials, done, st);
+        launch_finalize_norm(op->partials, np, FIN_MG_CYCLE, op->sc, op->history, nullptr, st);
     };
     std::vector<const void*> key = {uD, fD, e, op->history, (const void*)(size_t)prm->nu_pre,
                                     (const void*)(size_t)prm->nu_post, (const void*)(size_t)prm->n_coarse,
@@ -815,10 +816,8 @@ tpmg_status tpmg_residual(tpmg_op* op, int level, tpmg_precision prec, const voi
         auto* ui = in_ptr<P>(op, s, 0, u, n);
         auto* fi = in_ptr<P>(op, s, 1, f, n);
         auto* ro = out_ptr<P>(op, 2, r);
-        launch_residual<P, P>(LL, ui, fi, ro, norm_out ? op->partials : nullptr, nullptr, s);
-        if (norm_out)
-            launch_finalize_norm(op->partials, sweep_shape(LL.nx, LL.ny, LL.nz, sizeof(typename P::R), false).nblocks(),
-                                 FIN_STORE, op->sc, nullptr, norm_out, s);
+        const int np = launch_residual<P, P>(LL, ui, fi, ro, norm_out ? op->partials : nullptr, nullptr, s);
+        if (norm_out) launch_finalize_norm(op->partials, np, FIN_STORE, op->sc, nullptr, norm_out, s);
         out_back<P>(op, s, 2, r, n);
     });
     CK(cudaGetLastError());
@@ -1032,6 +1031,60 @@ tpmg_status tpmg_vcycle(tpmg_op* op, const tpmg_params* prm, const void* f, void
 }
 
 unsigned long long tpmg_kernel_launches(void) { return launch_counter(); }
+
+tpmg_status tpmg_set_variant(tpmg_op* op, tpmg_precision prec, int level, int variant) {
+    TRY(check_level(op, level));
+    if (prec != TPMG_F64 && prec != TPMG_F32 && prec != TPMG_DW) return set_err(TPMG_ERR_ARG, "bad precision");
+    if (variant < 0 || variant >= TPMG_NUM_VARIANTS) return set_err(TPMG_ERR_ARG, "bad variant");
+    if (op->variant[pid_of(prec)][level] != variant) {
+        op->variant[pid_of(prec)][level] = variant;
+        invalidate_graphs(op);
+    }
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_autotune(tpmg_op* op, tpmg_precision prec, int reps, int* variants_out, void* stream) {
+    if (!op || reps < 1) return set_err(TPMG_ERR_ARG, "NULL operator or reps < 1");
+    if (prec != TPMG_F64 && prec != TPMG_F32 && prec != TPMG_DW) return set_err(TPMG_ERR_ARG, "bad precision");
+    const int pid = pid_of(prec);
+    TRY(ensure_hier(op, pid, true));
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int l = 1; l <= op->g.L; ++l) {
+        double best = 1e300;
+        int best_v = 0;
+        for (int v = 0; v < TPMG_NUM_VARIANTS; ++v) {
+            op->variant[pid][l] = v;
+            auto run = [&](auto tag) {
+                typedef decltype(tag) P;
+                typedef typename P::S S;
+                Hier& h = op->hier[pid];
+                launch_smooth<P>(level_view<P>(op, l), 0.8, (const S*)h.u[l], (const S*)h.f[l], (S*)h.ub[l],
+                                 op->partials, nullptr, s);
+            };
+            auto once = [&]() {
+                if (pid == 0) run(PolF64());
+                else if (pid == 1) run(PolF32());
+                else run(PolDW());
+            };
+            once();
+            CK(cudaEventRecord(op->ev0, s));
+            for (int t = 0; t < reps; ++t) once();
+            CK(cudaEventRecord(op->ev1, s));
+            CK(cudaEventSynchronize(op->ev1));
+            CK(cudaGetLastError());
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, op->ev0, op->ev1));
+            if (ms < best) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        op->variant[pid][l] = best_v;
+        if (variants_out) variants_out[l] = best_v;
+    }
+    invalidate_graphs(op);
+    return TPMG_OK;
+}
 
 tpmg_status tpmg_time_kernel(tpmg_op* op, tpmg_precision prec, tpmg_kernel k, int reps, double* ms,
                              void* stream) {

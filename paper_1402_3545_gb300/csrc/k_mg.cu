@@ -368,6 +368,7 @@ void launch_apply_A(const Lv<P>& L, const typename P::S* x, typename P::S* y, cu
 template <class P>
 void launch_line_solve(const Lv<P>& L, const typename P::S* b, typename P::S* x, double scale, const int* done,
                        cudaStream_t s) {
+    if (launch_line_solve_pp<P>(L, b, x, scale, done, s) >= 0) return;
     Shape sh = sweep_shape(L.nx, L.ny, L.nz, sizeof(typename P::R), true);
     allow_smem(k_line_solve<P>, sh.smem);
     k_line_solve<P><<<sh.grid, sh.block, sh.smem, s>>>(L, b, x, scale, done);
@@ -376,24 +377,35 @@ void launch_line_solve(const Lv<P>& L, const typename P::S* b, typename P::S* x,
 template <class P>
 int launch_smooth(const Lv<P>& L, double rho, const typename P::S* u, const typename P::S* f,
                    typename P::S* uo, double* partials, const int* done, cudaStream_t s) {
-    int nparts = 0;
-    if (launch_smooth_pp<P>(L, rho, u, f, uo, partials, done, s, &nparts)) return nparts;
+    const int nparts = launch_smooth_pp<P>(L, rho, u, f, uo, partials, done, s);
+    if (nparts >= 0) return nparts;
     Shape sh = sweep_shape(L.nx, L.ny, L.nz, sizeof(typename P::R), true);
     allow_smem(k_smooth<P>, sh.smem);
     k_smooth<P><<<sh.grid, sh.block, sh.smem, s>>>(L, rho, u, f, uo, partials, done);
     note_launch();
     return sh.nblocks();
 }
+int residual_blocks(int nx, int ny, int nz, int bytes_per_value) {
+    if (nx % 32 == 0 && ny % 4 == 0 && nx >= 32) return (nx / 32) * (ny / 4);  // pipelined kernel
+    return sweep_shape(nx, ny, nz, bytes_per_value, false).nblocks();
+}
 template <class P, class PO>
-void launch_residual(const Lv<P>& L, const typename P::S* u, const typename P::S* f,
-                     typename PO::S* r, double* partials, const int* done, cudaStream_t s) {
+int launch_residual(const Lv<P>& L, const typename P::S* u, const typename P::S* f,
+                    typename PO::S* r, double* partials, const int* done, cudaStream_t s) {
+    const int nb = launch_residual_pp<P, PO>(L, u, f, r, partials, done, s);
+    if (nb >= 0) return nb;
     Shape sh = sweep_shape(L.nx, L.ny, L.nz, sizeof(typename P::R), false);
     k_residual<P, PO><<<sh.grid, sh.block, 0, s>>>(L, u, f, r, partials, done);
     note_launch();
+    return sh.nblocks();
 }
 template <class PF, class P>
 void launch_restrict_smooth(const Lv<P>& Lc, double rho, const typename PF::S* rf,
                             typename P::S* fc, typename P::S* uc, const int* done, cudaStream_t s) {
+    // the pipelined kernel copies pairs of fine values: their address must be pair-aligned
+    if (((uintptr_t)rf % (2 * sizeof(typename PF::S))) == 0 &&
+        launch_restrict_smooth_pp<PF, P>(Lc, rho, rf, fc, uc, done, s) >= 0)
+        return;
     Shape sh = sweep_shape(Lc.nx, Lc.ny, Lc.nz, sizeof(typename P::R), true);
     allow_smem(k_restrict_smooth<PF, P>, sh.smem);
     k_restrict_smooth<PF, P><<<sh.grid, sh.block, sh.smem, s>>>(Lc, rho, rf, fc, uc, done);
@@ -419,7 +431,7 @@ void launch_correct(size_t n, typename P::S* u, const float* e, const int* done,
     template void launch_line_solve<P>(const Lv<P>&, const P::S*, P::S*, double, const int*, cudaStream_t); \
     template int launch_smooth<P>(const Lv<P>&, double, const P::S*, const P::S*, P::S*, double*, \
                                    const int*, cudaStream_t);                                      \
-    template void launch_residual<P, P>(const Lv<P>&, const P::S*, const P::S*, P::S*, double*,    \
+    template int launch_residual<P, P>(const Lv<P>&, const P::S*, const P::S*, P::S*, double*,     \
                                         const int*, cudaStream_t);                                 \
     template void launch_restrict_smooth<P, P>(const Lv<P>&, double, const P::S*, P::S*, P::S*,   \
                                             const int*, cudaStream_t);                             \
@@ -428,9 +440,9 @@ void launch_correct(size_t n, typename P::S* u, const float* e, const int* done,
 TPMG_INST(PolF64)
 TPMG_INST(PolF32)
 TPMG_INST(PolDW)
-template void launch_residual<PolDW, PolF32>(const Lv<PolDW>&, const float2*, const float2*, float*,
+template int launch_residual<PolDW, PolF32>(const Lv<PolDW>&, const float2*, const float2*, float*,
                                              double*, const int*, cudaStream_t);
-template void launch_residual<PolF64, PolF32>(const Lv<PolF64>&, const double*, const double*,
+template int launch_residual<PolF64, PolF32>(const Lv<PolF64>&, const double*, const double*,
                                               float*, double*, const int*, cudaStream_t);
 template void launch_correct<PolDW>(size_t, float2*, const float*, const int*, cudaStream_t);
 template void launch_restrict_smooth<PolDW, PolF64>(const Lv<PolF64>&, double, const float2*, double*, double*,

@@ -1,16 +1,19 @@
-// k_sweep.cu -- plane-pipelined column sweeps for the large levels, and the Thomas factors.
+// k_sweep.cu -- plane-pipelined column sweeps for the large levels (Smooth, Residual, line solve,
+// RestrictSmooth), the Thomas factors, and the tile variants the autotuner chooses from.
 //
 // A block owns 32 x TY vertical columns (one thread each, 32 consecutive x per warp). It walks the
-// planes k = 0..nz-1 of its tile; each plane of u (with its one-cell periodic halo in x and y), of
-// f and, when lambda^2 varies, of the factor 1/m_k is fetched with cp.async into a ring of PD
-// shared-memory slots, PD planes ahead of the computation, so the loads of many planes are in
-// flight while the Thomas recurrence of the current plane runs. The forward-eliminated values d'_k
-// go to a per-thread stack in shared memory; the back substitution streams u_k (and v/m_k) through
-// the same ring in reverse order and writes u' = u + rho x once per cell.
+// planes k = 0..nz-1 of its tile; each plane of its inputs -- u with its one-cell periodic halo in
+// x and y when a stencil is applied, f or the right-hand side, and, when lambda^2 varies over the
+// level, the Thomas factor 1/m_k -- is fetched with cp.async into a ring of PD shared-memory slots,
+// PD planes ahead of the computation, so many planes' loads are in flight while the recurrence of
+// the current plane runs. The forward-eliminated values d'_k go to a per-thread stack in shared
+// memory; the back substitution streams u_k and v/m_k through the ring in reverse order and writes
+// each output value once.
 //
-// Per cell the kernel moves the algorithmic minimum of the smoother -- read u and f, write u' --
-// plus the factor arrays when lambda^2 varies over the level, and u once more in the backward pass
-// (an L2 hit: the block's tile was read a few microseconds earlier).
+// Per cell the kernels move the algorithmic minimum of their operation plus the factor arrays when
+// lambda^2 varies over the level (constant lambda^2: one table of nz factors, read through L1).
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace tpmg {
@@ -61,18 +64,25 @@ void launch_factors(const Lv<P>& L, typename P::S* finv, typename P::S* fw, int 
     note_launch();
 }
 
-// ---------------------------------------------------------------- Smooth, plane pipelined
-// uo = u + rho M^{-1}(f - A u) (Eq. 11) with block partial sums of ||f - A u||^2.
-template <class P, int TY, int PD>
-__global__ void __launch_bounds__(32 * TY) k_smooth_pp(Lv<P> L, double rho_d, const typename P::S* __restrict__ u,
-                                                       const typename P::S* __restrict__ f,
-                                                       typename P::S* __restrict__ uo, double* partials,
-                                                       const int* done) {
+// ---------------------------------------------------------------- generic pipelined sweep
+enum { MODE_SMOOTH = 0, MODE_RESIDUAL = 1, MODE_LINESOLVE = 2 };
+
+// MODE_SMOOTH:    out = u + coef M^{-1}(f - A u), partial sums of ||f - A u||^2      (Eq. 11)
+// MODE_RESIDUAL:  out = f - A u (stored in PO's precision), partial sums of ||f - A u||^2
+// MODE_LINESOLVE: out = coef M^{-1} u (u is the right-hand side; f unused)            (Eq. 9)
+template <class P, class PO, int TY, int PD, int MODE>
+__global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, const typename P::S* __restrict__ u,
+                                                      const typename P::S* __restrict__ f,
+                                                      typename PO::S* __restrict__ out, double* partials,
+                                                      const int* done) {
     typedef typename P::S S;
     typedef typename P::R R;
     constexpr int NT = 32 * TY;
-    constexpr int UPL = (TY + 2) * 34;  // u plane tile with halo
-    constexpr int FPL = NT;             // f (and 1/m) plane tile
+    constexpr bool HALO = MODE != MODE_LINESOLVE;  // the stencil needs the u plane with its halo
+    constexpr bool STACK = MODE != MODE_RESIDUAL;  // a Thomas solve follows
+    constexpr int UPL = HALO ? (TY + 2) * 34 : 0;
+    constexpr int FPL = NT;
+    constexpr int IPL = STACK ? NT : 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (done && *(volatile const int*)done) return;
 
@@ -81,39 +91,40 @@ __global__ void __launch_bounds__(32 * TY) k_smooth_pp(Lv<P> L, double rho_d, co
     S* ringU = reinterpret_cast<S*>(smem_raw);
     S* ringF = ringU + PD * UPL;
     S* ringI = ringF + PD * FPL;
-    const size_t ring_bytes = ((size_t)PD * (UPL + 2 * FPL) * sizeof(S) + 15) & ~(size_t)15;
+    const size_t ring_bytes = ((size_t)PD * (UPL + FPL + IPL) * sizeof(S) + 15) & ~(size_t)15;
     R* stack = reinterpret_cast<R*>(smem_raw + ring_bytes);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY;
     const size_t pl = (size_t)nx * ny;
     const size_t c = (size_t)(j0 + ty) * nx + (i0 + tx);
+    const S* rhs = (MODE == MODE_LINESOLVE) ? u : f;
 
     auto issue_plane = [&](int k, int slot) {
         if (k < nz) {
             const size_t b = (size_t)k * pl;
-            S* Us = ringU + slot * UPL;
-            cp_async<sizeof(S)>(&Us[(ty + 1) * 34 + tx + 1], u + b + c);
-            cp_async<sizeof(S)>(&ringF[slot * FPL + tid], f + b + c);
-            if (percol) cp_async<sizeof(S)>(&ringI[slot * FPL + tid], L.finv + b + c);
-            // halo: rows j0-1 and j0+TY (32 each), columns i0-1 and i0+32 (TY+2 each)
-            for (int it = tid; it < 64 + 2 * (TY + 2); it += NT) {
-                int rr, cc, gj, gi;
-                if (it < 64) {
-                    rr = (it < 32) ? 0 : TY + 1;
-                    cc = (it & 31) + 1;
-                    gj = (it < 32) ? j0 - 1 : j0 + TY;
-                    gi = i0 + (it & 31);
-                } else {
-                    const int q = it - 64;
-                    rr = q >> 1;
-                    cc = (q & 1) ? 33 : 0;
-                    gj = j0 - 1 + rr;
-                    gi = (q & 1) ? i0 + 32 : i0 - 1;
+            cp_async<sizeof(S)>(&ringF[slot * FPL + tid], rhs + b + c);
+            if (STACK && percol) cp_async<sizeof(S)>(&ringI[slot * FPL + tid], L.finv + b + c);
+            if (HALO) {
+                S* Us = ringU + slot * UPL;
+                cp_async<sizeof(S)>(&Us[(ty + 1) * 34 + tx + 1], u + b + c);
+                // halo: rows j0-1 and j0+TY (32 each), columns i0-1 and i0+32 (TY+2 each)
+                for (int it = tid; it < 64 + 2 * (TY + 2); it += NT) {
+                    int rr, cc, gj, gi;
+                    if (it < 64) {
+                        rr = (it < 32) ? 0 : TY + 1;
+                        cc = (it & 31) + 1;
+                        gj = (it < 32) ? j0 - 1 : j0 + TY;
+                        gi = i0 + (it & 31);
+                    } else {
+                        const int q = it - 64;
+                        rr = q >> 1;
+                        cc = (q & 1) ? 33 : 0;
+                        gj = j0 - 1 + rr;
+                        gi = (q & 1) ? i0 + 32 : i0 - 1;
+                    }
+                    cp_async<sizeof(S)>(&Us[rr * 34 + cc], u + b + (size_t)wrap_p(gj, ny) * nx + wrap_p(gi, nx));
                 }
-                gj = wrap_p(gj, ny);
-                gi = wrap_p(gi, nx);
-                cp_async<sizeof(S)>(&Us[rr * 34 + cc], u + b + (size_t)gj * nx + gi);
             }
         }
         cp_commit();
@@ -121,51 +132,252 @@ __global__ void __launch_bounds__(32 * TY) k_smooth_pp(Lv<P> L, double rho_d, co
 
     for (int s = 0; s < PD; ++s) issue_plane(s, s);
 
-    const R cx = P::cst(L.cx), cy = P::cst(L.cy), vv = P::ld(L.v, c);
+    const R vv = P::ld(L.v, c);
+    const R cx = P::cst(L.cx), cy = P::cst(L.cy);
     const R dh = P::cst(1.0 + 2.0 * L.cx + 2.0 * L.cy);
     const R dh1 = P::add(dh, vv), dh2 = P::add(dh1, vv);
     typename P::Acc acc = 0, cmp = 0;
     R um = P::zero(), uc = P::zero(), d_prev = P::zero();
     int slot = 0;
+    const int ctr = (ty + 1) * 34 + tx + 1;
     for (int k = 0; k < nz; ++k) {
-        cp_wait<PD - 2>();
-        __syncthreads();
-        const S* Us = ringU + slot * UPL;
         const int nslot = (slot + 1 == PD) ? 0 : slot + 1;
-        const int ctr = (ty + 1) * 34 + tx + 1;
-        if (k == 0) uc = P::ld_plain(Us, ctr);
-        const R up = (k + 1 < nz) ? P::ld_plain(ringU + nslot * UPL, ctr) : P::zero();
-        const R hx = P::add(P::ld_plain(Us, ctr - 1), P::ld_plain(Us, ctr + 1));
-        const R hy = P::add(P::ld_plain(Us, ctr - 34), P::ld_plain(Us, ctr + 34));
-        const R diag = (nz == 1) ? dh : ((k == 0 || k == nz - 1) ? dh1 : dh2);
-        R au = P::mul(diag, uc);
-        au = P::sub(au, P::mul(cx, hx));
-        au = P::sub(au, P::mul(cy, hy));
-        au = P::sub(au, P::mul(vv, P::add(um, up)));
-        const R r = P::sub(P::ld_plain(ringF, slot * FPL + tid), au);
-        P::acc_dot(acc, cmp, r, r);
-        const R inv = percol ? P::ld_plain(ringI, slot * FPL + tid) : P::ld(L.finv, k);
-        const R d = P::mul(P::add(r, P::mul(vv, d_prev)), inv);
-        stack[(size_t)k * NT + tid] = d;
-        d_prev = d;
-        um = uc;
-        uc = up;
-        __syncthreads();
+        R r;
+        if constexpr (HALO) {
+            cp_wait<PD - 2>();  // planes k and k+1 (the upper neighbour) have landed
+            __syncthreads();    // ... including the halo values other threads fetched
+            const S* Us = ringU + slot * UPL;
+            if (k == 0) uc = P::ld_plain(Us, ctr);
+            const R up = (k + 1 < nz) ? P::ld_plain(ringU + nslot * UPL, ctr) : P::zero();
+            const R hx = P::add(P::ld_plain(Us, ctr - 1), P::ld_plain(Us, ctr + 1));
+            const R hy = P::add(P::ld_plain(Us, ctr - 34), P::ld_plain(Us, ctr + 34));
+            const R diag = (nz == 1) ? dh : ((k == 0 || k == nz - 1) ? dh1 : dh2);
+            R au = P::mul(diag, uc);
+            au = P::sub(au, P::mul(cx, hx));
+            au = P::sub(au, P::mul(cy, hy));
+            au = P::sub(au, P::mul(vv, P::add(um, up)));
+            r = P::sub(P::ld_plain(ringF, slot * FPL + tid), au);
+            P::acc_dot(acc, cmp, r, r);
+            um = uc;
+            uc = up;
+        } else {
+            cp_wait<PD - 1>();  // only this thread's own copies are read: no barrier needed
+            r = P::ld_plain(ringF, slot * FPL + tid);
+        }
+        if constexpr (MODE == MODE_RESIDUAL) {
+            const size_t id = (size_t)k * pl + c;
+            if constexpr (std::is_same<P, PO>::value)
+                P::st(out, id, r);
+            else
+                PO::st(out, id, PO::from_f(P::to_f(r)));
+        }
+        if constexpr (STACK) {
+            const R inv = percol ? P::ld_plain(ringI, slot * FPL + tid) : P::ld(L.finv, k);
+            const R d = P::mul(P::add(r, P::mul(vv, d_prev)), inv);
+            stack[(size_t)k * NT + tid] = d;
+            d_prev = d;
+        }
+        if constexpr (HALO) __syncthreads();  // the slot is reused by the next issue
         issue_plane(k + PD, slot);
         slot = nslot;
     }
     cp_wait<0>();
-    __syncthreads();
 
-    // back substitution, streaming u_k (and v/m_k) through the ring in reverse order
-    S* bU = reinterpret_cast<S*>(smem_raw);
-    S* bW = bU + PD * NT;
-    auto issue_back = [&](int k, int s2) {
-        if (k >= 0) {
+    if constexpr (STACK) {
+        __syncthreads();  // the backward ring reuses the forward ring's shared memory
+        // back substitution, streaming u_k (Smooth) and v/m_k through the ring in reverse order
+        constexpr bool NEED_U = MODE == MODE_SMOOTH;
+        S* bU = reinterpret_cast<S*>(smem_raw);
+        S* bW = bU + (NEED_U ? PD * NT : 0);
+        auto issue_back = [&](int k, int s2) {
+            if (k >= 0) {
+                const size_t id = (size_t)k * pl + c;
+                if (NEED_U) cp_async<sizeof(S)>(&bU[s2 * NT + tid], u + id);
+                if (percol) cp_async<sizeof(S)>(&bW[s2 * NT + tid], L.fw + id);
+            }
+            cp_commit();
+        };
+        for (int s = 0; s < PD; ++s) issue_back(nz - 1 - s, s);
+        const R cf = P::cst(coef);
+        const bool scaled = coef != 1.0;
+        R xn = P::zero();
+        slot = 0;
+        for (int k = nz - 1; k >= 0; --k) {
+            cp_wait<PD - 1>();
+            const R w = percol ? P::ld_plain(bW, slot * NT + tid) : P::ld(L.fw, k);
+            xn = P::add(stack[(size_t)k * NT + tid], P::mul(w, xn));
             const size_t id = (size_t)k * pl + c;
-            cp_async<sizeof(S)>(&bU[s2 * NT + tid], u + id);
-            if (percol) cp_async<sizeof(S)>(&bW[s2 * NT + tid], L.fw + id);
+            if constexpr (MODE == MODE_SMOOTH)
+                P::st(reinterpret_cast<S*>(out), id, P::add(P::ld_plain(bU, slot * NT + tid), P::mul(cf, xn)));
+            else
+                P::st(reinterpret_cast<S*>(out), id, scaled ? P::mul(cf, xn) : xn);
+            issue_back(k - PD, slot);
+            slot = (slot + 1 == PD) ? 0 : slot + 1;
         }
+        cp_wait<0>();
+    }
+    if (MODE != MODE_LINESOLVE && partials) {
+        double sm = block_sum(P::acc_get(acc, cmp));
+        if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = sm;
+    }
+}
+
+template <class P, int TY, int PD, int MODE>
+static size_t sweep_pp_smem(int nz) {
+    typedef typename P::S S;
+    const int UPL = MODE != MODE_LINESOLVE ? (TY + 2) * 34 : 0;
+    const int IPL = MODE != MODE_RESIDUAL ? 32 * TY : 0;
+    const size_t ring = ((size_t)PD * (UPL + 32 * TY + IPL) * sizeof(S) + 15) & ~(size_t)15;
+    const size_t stack = MODE != MODE_RESIDUAL ? (size_t)nz * 32 * TY * sizeof(typename P::R) : 0;
+    return ring + stack;
+}
+
+template <class P, int TY, bool FACTORS = true>
+static bool pp_fits(const Lv<P>& L) {
+    return L.nx % 32 == 0 && L.ny % TY == 0 && L.nx >= 32 && (!FACTORS || (L.finv && L.fw));
+}
+
+template <class P, class PO, int TY, int PD, int MODE>
+static int run_sweep_pp(const Lv<P>& L, double coef, const typename P::S* u, const typename P::S* f,
+                        typename PO::S* out, double* partials, const int* done, cudaStream_t s) {
+    const size_t smem = sweep_pp_smem<P, TY, PD, MODE>(L.nz);
+    auto kern = k_sweep_pp<P, PO, TY, PD, MODE>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grd(L.nx / 32, L.ny / TY), blk(32, TY);
+    kern<<<grd, blk, smem, s>>>(L, coef, u, f, out, partials, done);
+    note_launch();
+    return (int)(grd.x * grd.y);
+}
+
+// ---------------------------------------------------------------- tile variants
+// Smooth: three (TY, PD) variants per precision; the autotuner (tpmg_autotune) times them per
+// level and stores its choice in Lv::variant. Without a choice, variant 0 is used.
+template <class P>
+struct SmoothVariants;
+template <>
+struct SmoothVariants<PolF32> {
+    static constexpr int TY[3] = {2, 4, 1};
+};
+template <>
+struct SmoothVariants<PolF64> {
+    static constexpr int TY[3] = {1, 2, 2};
+};
+template <>
+struct SmoothVariants<PolDW> {
+    static constexpr int TY[3] = {1, 2, 2};
+};
+
+template <class P>
+static int smooth_dispatch(const Lv<P>& L, double rho, const typename P::S* u, const typename P::S* f,
+                           typename P::S* uo, double* partials, const int* done, cudaStream_t s) {
+    const int v = (L.variant >= 0 && L.variant < 3) ? L.variant : 0;
+    if (P::id == 1) {  // FP32
+        if (v == 0 && pp_fits<P, 2>(L)) return run_sweep_pp<P, P, 2, 8, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s);
+        if (v == 1 && pp_fits<P, 4>(L)) return run_sweep_pp<P, P, 4, 6, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s);
+        if (v == 2 && pp_fits<P, 1>(L)) return run_sweep_pp<P, P, 1, 8, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s);
+        if (pp_fits<P, 2>(L)) return run_sweep_pp<P, P, 2, 8, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s);
+    } else {  // 8-byte values
+        if (v == 1 && pp_fits<P, 2>(L)) return run_sweep_pp<P, P, 2, 4, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s);
+        if (v == 2 && pp_fits<P, 2>(L)) return run_sweep_pp<P, P, 2, 6, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s);
+        if (pp_fits<P, 1>(L)) return run_sweep_pp<P, P, 1, 6, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s);
+    }
+    return -1;
+}
+
+template <class P>
+int launch_smooth_pp(const Lv<P>& L, double rho, const typename P::S* u, const typename P::S* f,
+                     typename P::S* uo, double* partials, const int* done, cudaStream_t s) {
+    if (L.nz * 32 * 8 > 160 * 1024) return -1;  // stack too deep for shared memory
+    return smooth_dispatch<P>(L, rho, u, f, uo, partials, done, s);
+}
+
+template <class P, class PO>
+int launch_residual_pp(const Lv<P>& L, const typename P::S* u, const typename P::S* f, typename PO::S* r,
+                       double* partials, const int* done, cudaStream_t s) {
+    if (!pp_fits<P, 4, false>(L)) return -1;
+    return run_sweep_pp<P, PO, 4, 6, MODE_RESIDUAL>(L, 1.0, u, f, r, partials, done, s);
+}
+
+template <class P>
+int launch_line_solve_pp(const Lv<P>& L, const typename P::S* b, typename P::S* x, double scale, const int* done,
+                         cudaStream_t s) {
+    if (L.nz * 32 * 8 > 160 * 1024) return -1;
+    if (P::id == 1) {
+        if (!pp_fits<P, 2>(L)) return -1;
+        return run_sweep_pp<P, P, 2, 8, MODE_LINESOLVE>(L, scale, b, nullptr, x, nullptr, done, s);
+    }
+    if (!pp_fits<P, 1>(L)) return -1;
+    return run_sweep_pp<P, P, 1, 8, MODE_LINESOLVE>(L, scale, b, nullptr, x, nullptr, done, s);
+}
+
+
+// ---------------------------------------------------------------- RestrictSmooth, pipelined
+// Coarse tile of 32 x TY columns; per coarse plane each thread fetches its 2 x 2 fine children
+// (two contiguous pairs) and, when lambda^2 varies, 1/m_k; f_c = 1/4 (sum of the children) is
+// written in the forward sweep, u_c = rho M_c^{-1} f_c in the backward sweep.
+template <class PF, class P, int TY, int PD>
+__global__ void __launch_bounds__(32 * TY) k_restrict_smooth_pp(Lv<P> Lc, double rho_d,
+                                                                const typename PF::S* __restrict__ rf,
+                                                                typename P::S* __restrict__ fc,
+                                                                typename P::S* __restrict__ uc, const int* done) {
+    typedef typename PF::S SF;
+    typedef typename P::S S;
+    typedef typename P::R R;
+    constexpr int NT = 32 * TY;
+    constexpr int CPL = 4 * NT;  // fine children per coarse plane tile
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (done && *(volatile const int*)done) return;
+    const int nxc = Lc.nx, nyc = Lc.ny, nz = Lc.nz, nxf = 2 * nxc;
+    const bool percol = Lc.fac_percol != 0;
+    SF* ringC = reinterpret_cast<SF*>(smem_raw);
+    S* ringI = reinterpret_cast<S*>(smem_raw + (size_t)PD * CPL * sizeof(SF));
+    const size_t ring_bytes = (((size_t)PD * CPL * sizeof(SF) + (size_t)PD * NT * sizeof(S)) + 15) & ~(size_t)15;
+    R* stack = reinterpret_cast<R*>(smem_raw + ring_bytes);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int I = blockIdx.x * 32 + tx, J = blockIdx.y * TY + ty;
+    const size_t plc = (size_t)nxc * nyc, plf = 4 * plc;
+    const size_t c = (size_t)J * nxc + I;
+    const size_t f0 = (size_t)(2 * J) * nxf + 2 * I, f1 = f0 + nxf;
+    auto issue_plane = [&](int k, int slot) {
+        if (k < nz) {
+            const size_t bf = (size_t)k * plf;
+            cp_async<2 * sizeof(SF)>(&ringC[slot * CPL + 4 * tid], rf + bf + f0);
+            cp_async<2 * sizeof(SF)>(&ringC[slot * CPL + 4 * tid + 2], rf + bf + f1);
+            if (percol) cp_async<sizeof(S)>(&ringI[slot * NT + tid], Lc.finv + (size_t)k * plc + c);
+        }
+        cp_commit();
+    };
+    for (int s = 0; s < PD; ++s) issue_plane(s, s);
+    const R vv = P::ld(Lc.v, c), quarter = P::cst(0.25);
+    R d_prev = P::zero();
+    int slot = 0;
+    for (int k = 0; k < nz; ++k) {
+        cp_wait<PD - 1>();
+        const SF* ch = ringC + slot * CPL + 4 * tid;
+        R s4;
+        if constexpr (std::is_same<PF, P>::value) {
+            s4 = P::add(P::add(P::ld_plain(ch, 0), P::ld_plain(ch, 1)), P::add(P::ld_plain(ch, 2), P::ld_plain(ch, 3)));
+        } else {
+            auto cv = [&](int q) { return P::cst(PF::to_d(PF::ld_plain(ch, q))); };
+            s4 = P::add(P::add(cv(0), cv(1)), P::add(cv(2), cv(3)));
+        }
+        const R fk = P::mul(quarter, s4);
+        P::st(fc, (size_t)k * plc + c, fk);
+        const R inv = percol ? P::ld_plain(ringI, slot * NT + tid) : P::ld(Lc.finv, k);
+        const R d = P::mul(P::add(fk, P::mul(vv, d_prev)), inv);
+        stack[(size_t)k * NT + tid] = d;
+        d_prev = d;
+        issue_plane(k + PD, slot);
+        slot = (slot + 1 == PD) ? 0 : slot + 1;
+    }
+    cp_wait<0>();
+    // the backward ring reuses shared memory that other threads' forward slots occupied: wait
+    // until every thread of the block has finished its forward sweep
+    __syncthreads();
+    // back substitution with v/m_k streamed in reverse (each thread reads only its own copies)
+    S* bW = reinterpret_cast<S*>(smem_raw);
+    auto issue_back = [&](int k, int s2) {
+        if (k >= 0 && percol) cp_async<sizeof(S)>(&bW[s2 * NT + tid], Lc.fw + (size_t)k * plc + c);
         cp_commit();
     };
     for (int s = 0; s < PD; ++s) issue_back(nz - 1 - s, s);
@@ -174,62 +386,49 @@ __global__ void __launch_bounds__(32 * TY) k_smooth_pp(Lv<P> L, double rho_d, co
     slot = 0;
     for (int k = nz - 1; k >= 0; --k) {
         cp_wait<PD - 1>();
-        const R w = percol ? P::ld_plain(bW, slot * NT + tid) : P::ld(L.fw, k);
+        const R w = percol ? P::ld_plain(bW, slot * NT + tid) : P::ld(Lc.fw, k);
         xn = P::add(stack[(size_t)k * NT + tid], P::mul(w, xn));
-        const R uk = P::ld_plain(bU, slot * NT + tid);
-        P::st(uo, (size_t)k * pl + c, P::add(uk, P::mul(rho, xn)));
+        P::st(uc, (size_t)k * plc + c, P::mul(rho, xn));
         issue_back(k - PD, slot);
         slot = (slot + 1 == PD) ? 0 : slot + 1;
     }
     cp_wait<0>();
-    if (partials) {
-        double sm = block_sum(P::acc_get(acc, cmp));
-        if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = sm;
-    }
 }
 
-template <class P, int TY, int PD>
-static size_t smooth_pp_smem(int nz) {
-    typedef typename P::S S;
-    const size_t ring = ((size_t)PD * ((TY + 2) * 34 + 2 * 32 * TY) * sizeof(S) + 15) & ~(size_t)15;
-    return ring + (size_t)nz * 32 * TY * sizeof(typename P::R);
-}
-
-template <class P, int TY, int PD>
-static bool try_smooth_pp(const Lv<P>& L, double rho, const typename P::S* u, const typename P::S* f,
-                          typename P::S* uo, double* partials, const int* done, cudaStream_t s, int* nparts) {
-    if (L.nx % 32 != 0 || L.ny % TY != 0 || L.nx < 32 || !L.finv || !L.fw) return false;
-    const size_t smem = smooth_pp_smem<P, TY, PD>(L.nz);
-    if (smem > 200 * 1024) return false;
-    auto kern = k_smooth_pp<P, TY, PD>;
+template <class PF, class P>
+int launch_restrict_smooth_pp(const Lv<P>& Lc, double rho, const typename PF::S* rf, typename P::S* fc,
+                              typename P::S* uc, const int* done, cudaStream_t s) {
+    constexpr int TY = (P::id == 1) ? 2 : 1;
+    constexpr int PD = 6;
+    if (!pp_fits<P, TY>(Lc) || Lc.nz * 32 * 8 > 160 * 1024) return -1;
+    const size_t ring = (((size_t)PD * 4 * 32 * TY * sizeof(typename PF::S) + (size_t)PD * 32 * TY * sizeof(typename P::S)) + 15) & ~(size_t)15;
+    const size_t smem = ring + (size_t)Lc.nz * 32 * TY * sizeof(typename P::R);
+    auto kern = k_restrict_smooth_pp<PF, P, TY, PD>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grd(L.nx / 32, L.ny / TY), blk(32, TY);
-    kern<<<grd, blk, smem, s>>>(L, rho, u, f, uo, partials, done);
+    dim3 grd(Lc.nx / 32, Lc.ny / TY), blk(32, TY);
+    kern<<<grd, blk, smem, s>>>(Lc, rho, rf, fc, uc, done);
     note_launch();
-    if (nparts) *nparts = (int)(grd.x * grd.y);
-    return true;
+    return 1;
 }
 
-// Tile shapes: FP32 uses 64-column blocks (two 32-wide rows) and an 8-plane ring; the 8-byte
-// types use 32-column blocks and a 6-plane ring so that two or more blocks share an SM.
-template <>
-bool launch_smooth_pp<PolF32>(const Lv<PolF32>& L, double rho, const float* u, const float* f, float* uo,
-                              double* partials, const int* done, cudaStream_t s, int* nparts) {
-    return try_smooth_pp<PolF32, 2, 8>(L, rho, u, f, uo, partials, done, s, nparts);
-}
-template <>
-bool launch_smooth_pp<PolF64>(const Lv<PolF64>& L, double rho, const double* u, const double* f, double* uo,
-                              double* partials, const int* done, cudaStream_t s, int* nparts) {
-    return try_smooth_pp<PolF64, 1, 6>(L, rho, u, f, uo, partials, done, s, nparts);
-}
-template <>
-bool launch_smooth_pp<PolDW>(const Lv<PolDW>& L, double rho, const float2* u, const float2* f, float2* uo,
-                             double* partials, const int* done, cudaStream_t s, int* nparts) {
-    return try_smooth_pp<PolDW, 1, 6>(L, rho, u, f, uo, partials, done, s, nparts);
-}
+#define TPMG_SWEEP_INST(P)                                                                                  \
+    template void launch_factors<P>(const Lv<P>&, P::S*, P::S*, int, cudaStream_t);                         \
+    template int launch_smooth_pp<P>(const Lv<P>&, double, const P::S*, const P::S*, P::S*, double*, const int*, \
+                                     cudaStream_t);                                                          \
+    template int launch_residual_pp<P, P>(const Lv<P>&, const P::S*, const P::S*, P::S*, double*, const int*,  \
+                                          cudaStream_t);                                                     \
+    template int launch_line_solve_pp<P>(const Lv<P>&, const P::S*, P::S*, double, const int*, cudaStream_t); \
+    template int launch_restrict_smooth_pp<P, P>(const Lv<P>&, double, const P::S*, P::S*, P::S*, const int*, \
+                                                 cudaStream_t);
 
-template void launch_factors<PolF64>(const Lv<PolF64>&, double*, double*, int, cudaStream_t);
-template void launch_factors<PolF32>(const Lv<PolF32>&, float*, float*, int, cudaStream_t);
-template void launch_factors<PolDW>(const Lv<PolDW>&, float2*, float2*, int, cudaStream_t);
+TPMG_SWEEP_INST(PolF64)
+TPMG_SWEEP_INST(PolF32)
+TPMG_SWEEP_INST(PolDW)
+template int launch_residual_pp<PolF64, PolF32>(const Lv<PolF64>&, const double*, const double*, float*, double*,
+                                                const int*, cudaStream_t);
+template int launch_residual_pp<PolDW, PolF32>(const Lv<PolDW>&, const float2*, const float2*, float*, double*,
+                                               const int*, cudaStream_t);
+template int launch_restrict_smooth_pp<PolDW, PolF64>(const Lv<PolF64>&, double, const float2*, double*, double*,
+                                                      const int*, cudaStream_t);
 
 }  // namespace tpmg

@@ -39,6 +39,7 @@ struct Lv {
     const typename P::S* finv;
     const typename P::S* fw;
     int fac_percol;
+    int variant;  // tile variant of the pipelined Smooth chosen by the autotuner (-1: default)
 };
 
 // Device-resident solver scalars (one struct per running solve). All solver control decisions
@@ -72,10 +73,22 @@ int max_partials(int nx, int ny);
 // Thomas factors of level L into finv/fw (per cell when percol, else a table of nz entries).
 template <class P>
 void launch_factors(const Lv<P>& L, typename P::S* finv, typename P::S* fw, int percol, cudaStream_t s);
-// Plane-pipelined Smooth for levels with nx % 32 == 0; returns false if the level does not fit.
+// Plane-pipelined kernels for levels with nx % 32 == 0; each returns its number of thread blocks
+// (= partial sums written), or -1 when the level does not fit and the caller must fall back.
 template <class P>
-bool launch_smooth_pp(const Lv<P>& L, double rho, const typename P::S* u, const typename P::S* f,
-                      typename P::S* uo, double* partials, const int* done, cudaStream_t s, int* nparts);
+int launch_smooth_pp(const Lv<P>& L, double rho, const typename P::S* u, const typename P::S* f,
+                     typename P::S* uo, double* partials, const int* done, cudaStream_t s);
+template <class P, class PO>
+int launch_residual_pp(const Lv<P>& L, const typename P::S* u, const typename P::S* f, typename PO::S* r,
+                       double* partials, const int* done, cudaStream_t s);
+template <class P>
+int launch_line_solve_pp(const Lv<P>& L, const typename P::S* b, typename P::S* x, double scale, const int* done,
+                         cudaStream_t s);
+template <class PF, class P>
+int launch_restrict_smooth_pp(const Lv<P>& Lc, double rho, const typename PF::S* rf, typename P::S* fc,
+                              typename P::S* uc, const int* done, cudaStream_t s);
+// number of blocks launch_residual uses on an nx x ny level (= partial sums it writes)
+int residual_blocks(int nx, int ny, int nz, int bytes_per_value);
 
 // ---------------------------------------------------------------- launchers (k_mg.cu)
 template <class P>
@@ -90,8 +103,8 @@ int launch_smooth(const Lv<P>& L, double rho, const typename P::S* u, const type
                    typename P::S* uo, double* partials, const int* done, cudaStream_t s);
 // residual with the output in policy PO's storage (PO = P, or PolF32 for the mixed hand-over)
 template <class P, class PO>
-void launch_residual(const Lv<P>& L, const typename P::S* u, const typename P::S* f,
-                     typename PO::S* r, double* partials, const int* done, cudaStream_t s);
+int launch_residual(const Lv<P>& L, const typename P::S* u, const typename P::S* f,
+                    typename PO::S* r, double* partials, const int* done, cudaStream_t s);
 // fine level in policy PF (its residual r_f), coarse level in P
 template <class PF, class P>
 void launch_restrict_smooth(const Lv<P>& Lc, double rho, const typename PF::S* rf,

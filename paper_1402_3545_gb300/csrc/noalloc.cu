@@ -52,9 +52,9 @@ extern "C" tpmg_status tpmg_residual_norm_noalloc(int nx, int ny, int nz, double
         g_noalloc_err = "tpmg_residual_norm_noalloc: sizes must be >= 1 and pointers non-NULL";
         return TPMG_ERR_ARG;
     }
-    const Shape sh = sweep_shape(nx, ny, nz, (int)sizeof(double), false);
-    if (sh.nblocks() > TPMG_NOALLOC_MAX_BLOCKS) {
-        g_noalloc_err = "tpmg_residual_norm_noalloc: " + std::to_string(sh.nblocks()) +
+    const int nblocks = residual_blocks(nx, ny, nz, (int)sizeof(double));
+    if (nblocks > TPMG_NOALLOC_MAX_BLOCKS) {
+        g_noalloc_err = "tpmg_residual_norm_noalloc: " + std::to_string(nblocks) +
                         " thread blocks needed, the fixed scratch holds " +
                         std::to_string(TPMG_NOALLOC_MAX_BLOCKS) + " (nx*ny too large)";
         return TPMG_ERR_ARG;
@@ -76,10 +76,15 @@ extern "C" tpmg_status tpmg_residual_norm_noalloc(int nx, int ny, int nz, double
     L.finv = nullptr;
     L.fw = nullptr;
     L.fac_percol = 0;
+    L.variant = -1;
     // every entry that the sum reads is written by this call's residual kernel before the
     // finalize kernel runs (same stream), so nothing has to be cleared beforehand
-    launch_residual<PolF64, PolF64>(L, u, f, r, partials, nullptr, s);
-    launch_finalize_norm(partials, sh.nblocks(), FIN_STORE, nullptr, nullptr, norm_out, s);
+    const int launched = launch_residual<PolF64, PolF64>(L, u, f, r, partials, nullptr, s);
+    if (launched != nblocks) {
+        g_noalloc_err = "tpmg_residual_norm_noalloc: internal block-count mismatch";
+        return TPMG_ERR_CUDA;
+    }
+    launch_finalize_norm(partials, nblocks, FIN_STORE, nullptr, nullptr, norm_out, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         g_noalloc_err = std::string("launch: ") + cudaGetErrorString(e);

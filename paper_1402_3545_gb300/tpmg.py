@@ -74,6 +74,8 @@ _SIGNATURES = {
     "tpmg_noalloc_last_error": [],
     "tpmg_time_kernel": [_P, _I, _I, _I, ctypes.POINTER(_D), _P],
     "tpmg_kernel_launches": [],
+    "tpmg_autotune": [_P, _I, _I, _P, _P],
+    "tpmg_set_variant": [_P, _I, _I, _I],
     "tpmg_status_string": [_I],
     "tpmg_last_error": [],
 }
@@ -309,6 +311,21 @@ def time_kernel(op, prec, kernel, reps=10, stream=None) -> float:
 
 def kernel_launches() -> int:
     return int(load().tpmg_kernel_launches())
+
+
+NUM_VARIANTS = 3
+
+
+def autotune(op, prec, nlevels, reps=5, stream=None) -> list[int]:
+    """Times the Smooth tile variants per level and keeps the fastest; returns [variant of level
+    1, ..., variant of level L]."""
+    out = (ctypes.c_int * (nlevels + 1))()
+    _check(load().tpmg_autotune(op, prec, reps, ctypes.cast(out, _P), _stream(stream)), "autotune")
+    return [out[l] for l in range(1, nlevels + 1)]
+
+
+def set_variant(op, prec, level, variant) -> None:
+    _check(load().tpmg_set_variant(op, prec, level, variant), "set_variant")
 
 
 # ---------------------------------------------------------------- convenience owner object
