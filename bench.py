@@ -142,6 +142,48 @@ def cpu_baseline_sample(p, f, iters_hint):
     return est_ms, {"t_cycle_s": round(t_cycle, 3), "t_residual_s": round(t_res, 3), "oracle_iters": iters}
 
 
+def bench_batched(tpmg, torch):
+    probs = workloads.batched()
+    ops = [tpmg.Operator.from_problem(p) for p in probs]
+    fs = [torch.from_numpy(p.rhs()).cuda() for p in probs]
+    us = [torch.zeros_like(f) for f in fs]
+    prm = tpmg.default_params(prec=tpmg.MIXED, tol=1e-6, max_iter=60)
+    handles = [o.op for o in ops]
+    for _ in range(2):
+        for u in us:
+            u.zero_()
+        res = tpmg.mg_solve_batched(handles, prm, fs, us)
+    times = []
+    for _ in range(3):
+        for u in us:
+            u.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res = tpmg.mg_solve_batched(handles, prm, fs, us)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    seq = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for o, f, u, p in zip(ops, fs, us, probs):
+            u.zero_()
+            tpmg.mg_solve(o.op, prm, f, u, p.n)
+        e1.record()
+        torch.cuda.synchronize()
+        seq.append(e0.elapsed_time(e1))
+    out = {"ms": round(min(times), 3), "sequential_single_solves_ms": round(min(seq), 3),
+           "problems": len(probs), "cells": int(sum(p.n for p in probs)),
+           "all_converged": all(r["converged"] for r in res["problems"]),
+           "iters_max": max(r["iters"] for r in res["problems"])}
+    for o in ops:
+        o.close()
+    return out
+
+
 def run_reference(args, rank, world):
     p = workloads.mid()
     f = p.rhs()
@@ -281,6 +323,9 @@ def run_ours(args, rank, world, dist):
     u.zero_()
     r = tpmg.cg_solve(op.op, tpmg.default_params(prec=tpmg.DW, tol=1e-6, max_iter=5000), fd, u, n)
     variants["cg_dw"] = {"ms": round(r["ms"], 3), "iters": r["iters"], "rel_res": r["rel_res"]}
+
+    # batched workload: 64 problems of drawn sizes in one persistent launch vs one solve after another
+    variants["batched_64"] = bench_batched(tpmg, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -66,7 +66,9 @@ typedef struct tpmg_grid tpmg_grid; /* opaque, library owned */
 typedef struct tpmg_op tpmg_op;     /* opaque, library owned */
 
 /* Grid of nx x ny x nz cells with `nlevels` multigrid levels (0 = halve nx and ny while both stay
- * even and the smaller one exceeds 8). nx and ny must be divisible by 2^(nlevels-1);
+ * even and the larger one exceeds 8: 8 x 8 for square grids; on elongated grids the short side may
+ * reach 1, which keeps the coarsest level well conditioned). nx and ny must be divisible by
+ * 2^(nlevels-1);
  * 1 <= nz <= 256; nlevels <= 16. Sec. 2.2 (horizontal-only semicoarsening, nz fixed). */
 tpmg_status tpmg_create_grid(int nx, int ny, int nz, int nlevels, tpmg_grid** out);
 tpmg_status tpmg_destroy_grid(tpmg_grid* g);
@@ -137,6 +139,8 @@ typedef struct {
     double tol;      /* stop when ||f - A u|| / ||f - A u_0|| < tol, Eq. (10) */
     tpmg_precision prec;
     int use_graph;   /* 1: replay each iteration from a CUDA graph (default), 0: plain launches */
+    double timeout_s; /* time limit of every device-side wait (the batched solver's grid barrier);
+                         default 1.0 s; when it runs out the solve ends with TPMG_ERR_TIMEOUT */
 } tpmg_params;
 
 typedef struct {
@@ -150,7 +154,7 @@ typedef struct {
     double ms;          /* device time of the solve in milliseconds (CUDA events on `stream`) */
 } tpmg_info;
 
-/* V(2,2), 2 coarse steps, rho 0.8, tol 1e-6, max_iter 100, TPMG_DW, graphs on. */
+/* V(2,2), 2 coarse steps, rho 0.8, tol 1e-6, max_iter 100, TPMG_DW, graphs on, 1 s wait limit. */
 void tpmg_default_params(tpmg_params* p);
 
 /* Multigrid solve (Sec. 2.2, Algorithm 1 with nu_pre/nu_post smoothing steps): V-cycles from the
@@ -229,6 +233,18 @@ tpmg_status tpmg_residual_norm_noalloc(int nx, int ny, int nz, double cx, double
                                        const double* u, const double* f, double* r, double* norm_out,
                                        void* stream);
 const char* tpmg_noalloc_last_error(void);
+
+/* Batched solve: nprob independent problems (each its own operator, all on one device, no operator
+ * twice) solved together by one cooperative persistent kernel -- the mixed-precision iterative
+ * refinement of tpmg_mg_solve (prm->prec must be TPMG_MIXED) with the steps of every problem's
+ * FP32 V-cycle interleaved phase by phase, a bounded grid barrier between phases (prm->timeout_s)
+ * and a per-problem convergence mask. f[b], u[b]: DEVICE double fields of problem b's finest level;
+ * infos: NULL or nprob entries (ms = the whole batch). The tables and a CUDA graph of the whole
+ * solve (conversions, the persistent launch) are built on the first call for a set of operators
+ * and parameters and replayed afterwards. Returns TPMG_ERR_TIMEOUT if a barrier wait ran out (the
+ * device stays usable), TPMG_ERR_NONFINITE or TPMG_ERR_NOT_CONVERGED if any problem ended so. */
+tpmg_status tpmg_mg_solve_batched(int nprob, tpmg_op* const* ops, const tpmg_params* prm,
+                                  const double* const* f, double* const* u, tpmg_info* infos, void* stream);
 
 const char* tpmg_status_string(tpmg_status s);
 /* Message of the last error in the calling thread ("" if none). */

@@ -535,7 +535,7 @@ tpmg_status tpmg_create_grid(int nx, int ny, int nz, int nlevels, tpmg_grid** ou
     if (L == 0) {
         L = 1;
         int a = nx, b = ny;
-        while (a % 2 == 0 && b % 2 == 0 && (a < b ? a : b) > 8 && L < MAXL) {
+        while (a % 2 == 0 && b % 2 == 0 && (a > b ? a : b) > 8 && L < MAXL) {
             a /= 2;
             b /= 2;
             ++L;
@@ -649,9 +649,12 @@ tpmg_status tpmg_create_operator(const tpmg_grid* g, double omega2, double hx, d
     return TPMG_OK;
 }
 
+static void drop_batches_of(const tpmg_op* op);
+
 tpmg_status tpmg_destroy_operator(tpmg_op* op) {
     if (!op) return TPMG_OK;
     cudaDeviceSynchronize();
+    drop_batches_of(op);
     invalidate_graphs(op);
     for (int l = 0; l <= MAXL; ++l) {
         dfree((void*&)op->v64[l]);
@@ -927,6 +930,7 @@ void tpmg_default_params(tpmg_params* p) {
     p->tol = 1e-6;
     p->prec = TPMG_DW;
     p->use_graph = 1;
+    p->timeout_s = 1.0;
 }
 
 tpmg_status tpmg_mg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, void* u, tpmg_info* info,
@@ -1185,3 +1189,373 @@ tpmg_status tpmg_cg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, vo
 }
 
 }  // extern "C"
+
+// ================================================================ batched persistent solver
+// Tables for k_batched (see kernels.cuh): per problem its level descriptors and buffers, per phase
+// the tasks of all problems; built once per set of operators and parameters and kept with a CUDA
+// graph of the whole batched solve (conversions in, one persistent launch, conversions out).
+struct BatchCache {
+    std::vector<tpmg_op*> ops;
+    int nu_pre = 0, nu_post = 0, n_coarse = 0, max_iter = 0;
+    double rho = 0, tol = 0, timeout_s = 0;
+    std::vector<const void*> io_key;
+    int nprob = 0, nphase = 0, ntasks = 0, total_parts = 0, nz_max = 0, grid = 0;
+    size_t smem = 0;
+    BProbDesc* d_probs = nullptr;
+    BState* d_state = nullptr;
+    BState* h_state = nullptr;  // pinned: initial state (copied in each solve) and results
+    BTask* d_tasks = nullptr;
+    int* d_phase_begin = nullptr;
+    int* d_phase_tiles = nullptr;
+    double* d_partials = nullptr;
+    unsigned* d_bar = nullptr;  // count, generation
+    int* d_flags = nullptr;     // error, n_active
+    int* h_flags = nullptr;     // pinned: initial flags and results
+    double* d_hist = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    unsigned long long graph_kernels = 0;
+    std::vector<BTask> h_tasks;
+    std::vector<int> h_phase_begin, h_phase_tiles;
+    ~BatchCache() {
+        if (graph) cudaGraphExecDestroy(graph);
+        void* ptrs[] = {d_probs, d_state, d_tasks, d_phase_begin, d_phase_tiles, d_partials, d_bar, d_flags, d_hist};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+        if (h_state) cudaFreeHost(h_state);
+        if (h_flags) cudaFreeHost(h_flags);
+    }
+};
+static std::vector<BatchCache*> g_batches;
+
+static void drop_batches_of(const tpmg_op* op) {
+    for (size_t i = 0; i < g_batches.size();) {
+        bool uses = false;
+        for (tpmg_op* o : g_batches[i]->ops) uses |= (o == op);
+        if (uses) {
+            delete g_batches[i];
+            g_batches.erase(g_batches.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+// the FP32 inner V-cycle of problem b as a list of tasks (same steps and buffers as Cycle)
+static void cycle_tasks(tpmg_op* op, int b, const tpmg_params* prm, std::vector<BTask>& out) {
+    Hier& h = op->hier[1];
+    const int L = op->g.L;
+    auto task = [&](int type, int level, const void* a, const void* rhs, void* o, void* o2) {
+        BTask t;
+        t.type = type;
+        t.prob = b;
+        t.level = level;
+        t.a = a;
+        t.b = rhs;
+        t.out = o;
+        t.out2 = o2;
+        const int nxl = (type == BT_RS) ? op->g.lnx[level] : op->g.lnx[level];
+        const int nyl = op->g.lny[level];
+        t.tiles_x = (nxl + 31) / 32;
+        t.tiles_y = (nyl + BTY - 1) / BTY;
+        t.tile_base = 0;
+        out.push_back(t);
+    };
+    void* cur = h.u[L];
+    void* oth = h.ub[L];
+    auto smooth = [&](int l, void*& c, void*& o, const void* rhs) {
+        task(BT_SMOOTH, l, c, rhs, o, nullptr);
+        std::swap(c, o);
+    };
+    task(BT_LS0, L, nullptr, h.f[L], cur, nullptr);
+    if (L == 1) {
+        for (int s = 1; s < prm->n_coarse; ++s) smooth(L, cur, oth, h.f[L]);
+    } else {
+        for (int s = 1; s < prm->nu_pre; ++s) smooth(L, cur, oth, h.f[L]);
+        task(BT_RESID, L, cur, h.f[L], h.r[L], nullptr);
+        std::vector<void*> lcur(L + 1), loth(L + 1);
+        // descend
+        for (int l = L - 1; l >= 1; --l) {
+            lcur[l] = h.u[l];
+            loth[l] = h.ub[l];
+            task(BT_RS, l, h.r[l + 1], nullptr, h.f[l], lcur[l]);
+            if (l == 1) {
+                for (int s = 1; s < prm->n_coarse; ++s) smooth(l, lcur[l], loth[l], h.f[l]);
+            } else {
+                for (int s = 1; s < prm->nu_pre; ++s) smooth(l, lcur[l], loth[l], h.f[l]);
+                task(BT_RESID, l, lcur[l], h.f[l], h.r[l], nullptr);
+            }
+        }
+        // ascend
+        for (int l = 2; l < L; ++l) {
+            task(BT_PROL, l, lcur[l - 1], nullptr, lcur[l], nullptr);
+            for (int s = 0; s < prm->nu_post; ++s) smooth(l, lcur[l], loth[l], h.f[l]);
+        }
+        task(BT_PROL, L, lcur[L - 1], nullptr, cur, nullptr);
+        for (int s = 0; s < prm->nu_post; ++s) smooth(L, cur, oth, h.f[L]);
+    }
+    task(BT_CORR, L, cur, nullptr, nullptr, nullptr);
+}
+
+static tpmg_status build_batch(BatchCache* bc, const tpmg_params* prm) {
+    const int np = (int)bc->ops.size();
+    bc->nprob = np;
+    std::vector<BProbDesc> probs(np);
+    std::vector<std::vector<BTask>> lists(np);
+    int parts = 0, maxlen = 0, nz_max = 1;
+    for (int b = 0; b < np; ++b) {
+        tpmg_op* op = bc->ops[b];
+        const int L = op->g.L;
+        BProbDesc& pd = probs[b];
+        memset(&pd, 0, sizeof(pd));
+        pd.L = L;
+        pd.nz = op->g.nz;
+        nz_max = op->g.nz > nz_max ? op->g.nz : nz_max;
+        for (int l = 1; l <= L; ++l) {
+            BLevelDesc& ld = pd.lev[l];
+            ld.nx = op->g.lnx[l];
+            ld.ny = op->g.lny[l];
+            ld.nz = op->g.nz;
+            ld.percol = op->percol[l];
+            ld.cx = op->cx[l];
+            ld.cy = op->cy[l];
+            ld.v = op->v32[l];
+            ld.finv = (const float*)op->finv[1][l];
+            ld.fw = (const float*)op->fw[1][l];
+        }
+        pd.uD = (float2*)op->hier[2].u[L];
+        pd.fD = (const float2*)op->hier[2].f[L];
+        pd.vD = op->vdw[L];
+        pd.r32 = (float*)op->hier[1].f[L];
+        pd.fine_tiles = ((op->g.lnx[L] + 31) / 32) * ((op->g.lny[L] + BTY - 1) / BTY);
+        pd.part_base = parts;
+        parts += pd.fine_tiles;
+        cycle_tasks(op, b, prm, lists[b]);
+        maxlen = (int)lists[b].size() > maxlen ? (int)lists[b].size() : maxlen;
+    }
+    bc->nz_max = nz_max;
+    bc->total_parts = parts;
+    // phases: outer residual, convergence decision, then the p-th step of every problem's cycle
+    std::vector<BTask>& tasks = bc->h_tasks;
+    tasks.clear();
+    bc->h_phase_begin.clear();
+    bc->h_phase_tiles.clear();
+    auto close_phase = [&](size_t first) {
+        int tiles = 0;
+        for (size_t t = first; t < tasks.size(); ++t) {
+            tasks[t].tile_base = tiles;
+            tiles += tasks[t].tiles_x * tasks[t].tiles_y;
+        }
+        bc->h_phase_tiles.push_back(tiles);
+    };
+    for (int ph = 0; ph < 2 + maxlen; ++ph) {
+        const size_t first = tasks.size();
+        bc->h_phase_begin.push_back((int)first);
+        for (int b = 0; b < np; ++b) {
+            tpmg_op* op = bc->ops[b];
+            BTask t;
+            memset(&t, 0, sizeof(t));
+            t.prob = b;
+            t.level = op->g.L;
+            if (ph < 2) {
+                t.type = ph == 0 ? BT_OUTRES : BT_FINAL;
+                t.tiles_x = ph == 0 ? (op->g.lnx[op->g.L] + 31) / 32 : 1;
+                t.tiles_y = ph == 0 ? (op->g.lny[op->g.L] + BTY - 1) / BTY : 1;
+                tasks.push_back(t);
+            } else if (ph - 2 < (int)lists[b].size()) {
+                tasks.push_back(lists[b][ph - 2]);
+            }
+        }
+        close_phase(first);
+    }
+    bc->h_phase_begin.push_back((int)tasks.size());
+    bc->nphase = (int)bc->h_phase_tiles.size();
+    bc->ntasks = (int)tasks.size();
+    // device tables
+    const int hist_len = prm->max_iter + 1;
+    for (int b = 0; b < np; ++b) probs[b].history = nullptr;  // set below once d_hist exists
+    TRY(dalloc((void**)&bc->d_hist, sizeof(double) * (size_t)np * hist_len));
+    for (int b = 0; b < np; ++b) probs[b].history = bc->d_hist + (size_t)b * hist_len;
+    TRY(dalloc((void**)&bc->d_probs, sizeof(BProbDesc) * np));
+    TRY(dalloc((void**)&bc->d_state, sizeof(BState) * np));
+    TRY(dalloc((void**)&bc->d_tasks, sizeof(BTask) * tasks.size()));
+    TRY(dalloc((void**)&bc->d_phase_begin, sizeof(int) * bc->h_phase_begin.size()));
+    TRY(dalloc((void**)&bc->d_phase_tiles, sizeof(int) * bc->h_phase_tiles.size()));
+    TRY(dalloc((void**)&bc->d_partials, sizeof(double) * (parts > 0 ? parts : 1)));
+    TRY(dalloc((void**)&bc->d_bar, sizeof(unsigned) * 2));
+    TRY(dalloc((void**)&bc->d_flags, sizeof(int) * 2));
+    CK(cudaMallocHost((void**)&bc->h_state, sizeof(BState) * np));
+    CK(cudaMallocHost((void**)&bc->h_flags, sizeof(int) * 2));
+    CK(cudaMemcpy(bc->d_probs, probs.data(), sizeof(BProbDesc) * np, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(bc->d_tasks, tasks.data(), sizeof(BTask) * tasks.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(bc->d_phase_begin, bc->h_phase_begin.data(), sizeof(int) * bc->h_phase_begin.size(),
+                  cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(bc->d_phase_tiles, bc->h_phase_tiles.data(), sizeof(int) * bc->h_phase_tiles.size(),
+                  cudaMemcpyHostToDevice));
+    bc->smem = batched_smem(nz_max);
+    int per_sm = batched_blocks_per_sm(nz_max);
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, bc->ops[0]->device));
+    if (per_sm < 1) return set_err(TPMG_ERR_ARG, "batched kernel does not fit on an SM (nz too large)");
+    bc->grid = per_sm * nsm;
+    return TPMG_OK;
+}
+
+extern "C" tpmg_status tpmg_mg_solve_batched(int nprob, tpmg_op* const* ops, const tpmg_params* prm,
+                                             const double* const* f, double* const* u, tpmg_info* infos,
+                                             void* stream) {
+    if (nprob < 1 || !ops || !prm || !f || !u) return set_err(TPMG_ERR_ARG, "bad batched arguments");
+    if (prm->prec != TPMG_MIXED) return set_err(TPMG_ERR_ARG, "the batched solver runs TPMG_MIXED");
+    if (prm->nu_pre < 1 || prm->nu_post < 0 || prm->n_coarse < 1 || prm->max_iter < 0 || !(prm->rho > 0.0))
+        return set_err(TPMG_ERR_ARG, "bad multigrid parameters");
+    const int dev = ops[0]->device;
+    for (int b = 0; b < nprob; ++b) {
+        if (!ops[b] || !f[b] || !u[b]) return set_err(TPMG_ERR_ARG, "NULL operator or field");
+        if (ops[b]->device != dev) return set_err(TPMG_ERR_ARG, "all operators must live on one device");
+        for (int c = 0; c < b; ++c)
+            if (ops[c] == ops[b]) return set_err(TPMG_ERR_ARG, "an operator appears twice in the batch");
+        TRY(ensure_hier(ops[b], 2, true));
+        TRY(ensure_hier(ops[b], 1, true));
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const double timeout_s = prm->timeout_s >= 0.0 ? prm->timeout_s : 1.0;
+    // find or build the tables
+    BatchCache* bc = nullptr;
+    for (BatchCache* c : g_batches) {
+        if ((int)c->ops.size() != nprob || c->nu_pre != prm->nu_pre || c->nu_post != prm->nu_post ||
+            c->n_coarse != prm->n_coarse || c->max_iter != prm->max_iter || c->rho != prm->rho || c->tol != prm->tol ||
+            c->timeout_s != timeout_s)
+            continue;
+        bool same = true;
+        for (int b = 0; b < nprob && same; ++b) same = c->ops[b] == ops[b];
+        if (same) bc = c;
+    }
+    if (!bc) {
+        bc = new BatchCache();
+        bc->ops.assign(ops, ops + nprob);
+        bc->nu_pre = prm->nu_pre;
+        bc->nu_post = prm->nu_post;
+        bc->n_coarse = prm->n_coarse;
+        bc->max_iter = prm->max_iter;
+        bc->rho = prm->rho;
+        bc->tol = prm->tol;
+        bc->timeout_s = timeout_s;
+        tpmg_status st = build_batch(bc, prm);
+        if (st != TPMG_OK) {
+            delete bc;
+            return st;
+        }
+        g_batches.push_back(bc);
+    }
+    for (int b = 0; b < nprob; ++b) {
+        memset(&bc->h_state[b], 0, sizeof(BState));
+        bc->h_state[b].active = 1;
+    }
+    bc->h_flags[0] = 0;
+    bc->h_flags[1] = nprob;
+    BatchDesc d;
+    d.nprob = nprob;
+    d.ntasks = bc->ntasks;
+    d.nphase = bc->nphase;
+    d.probs = bc->d_probs;
+    d.state = bc->d_state;
+    d.tasks = bc->d_tasks;
+    d.phase_begin = bc->d_phase_begin;
+    d.phase_tiles = bc->d_phase_tiles;
+    d.partials = bc->d_partials;
+    d.bar_count = bc->d_bar;
+    d.bar_gen = bc->d_bar + 1;
+    d.error = bc->d_flags;
+    d.n_active = bc->d_flags + 1;
+    d.rho = prm->rho;
+    d.tol = prm->tol;
+    d.max_iter = prm->max_iter;
+    d.timeout_ns = (unsigned long long)(timeout_s * 1e9);
+    d.nz_max = bc->nz_max;
+    std::vector<const void*> io_key;
+    for (int b = 0; b < nprob; ++b) {
+        io_key.push_back(f[b]);
+        io_key.push_back(u[b]);
+    }
+    cudaError_t launch_err = cudaSuccess;
+    auto body = [&](cudaStream_t st) {
+        CK(cudaMemcpyAsync(bc->d_state, bc->h_state, sizeof(BState) * nprob, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(bc->d_flags, bc->h_flags, sizeof(int) * 2, cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(bc->d_bar, 0, sizeof(unsigned) * 2, st));
+        for (int b = 0; b < nprob; ++b) {
+            const size_t n = lvl_cells(ops[b], ops[b]->g.L);
+            launch_f64_to_dw(n, f[b], (float2*)ops[b]->hier[2].f[ops[b]->g.L], st);
+            launch_f64_to_dw(n, u[b], (float2*)ops[b]->hier[2].u[ops[b]->g.L], st);
+        }
+        launch_err = launch_batched(d, bc->grid, bc->smem, st);
+        for (int b = 0; b < nprob; ++b) {
+            const size_t n = lvl_cells(ops[b], ops[b]->g.L);
+            launch_dw_to_f64(n, (const float2*)ops[b]->hier[2].u[ops[b]->g.L], u[b], st);
+        }
+        return TPMG_OK;
+    };
+    tpmg_op* op0 = ops[0];
+    CK(cudaEventRecord(op0->ev0, s));
+    bool ran = false;
+    if (prm->use_graph) {
+        if (!bc->graph || bc->io_key != io_key) {
+            if (bc->graph) cudaGraphExecDestroy(bc->graph);
+            bc->graph = nullptr;
+            if (cudaStreamBeginCapture(op0->cap_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+                const unsigned long long c0 = launch_counter();
+                body(op0->cap_stream);
+                bc->graph_kernels = launch_counter() - c0;
+                launch_counter() = c0;
+                cudaGraph_t g = nullptr;
+                if (cudaStreamEndCapture(op0->cap_stream, &g) == cudaSuccess && launch_err == cudaSuccess &&
+                    cudaGraphInstantiate(&bc->graph, g, 0) == cudaSuccess) {
+                    bc->io_key = io_key;
+                } else {
+                    bc->graph = nullptr;
+                }
+                if (g) cudaGraphDestroy(g);
+            }
+            cudaGetLastError();  // a failed capture falls back to direct launches
+        }
+        if (bc->graph) {
+            CK(cudaGraphLaunch(bc->graph, s));
+            launch_counter() += bc->graph_kernels;
+            ran = true;
+        }
+    }
+    if (!ran) {
+        launch_err = cudaSuccess;
+        TRY(body(s));
+        if (launch_err != cudaSuccess)
+            return set_err(TPMG_ERR_CUDA, std::string("cooperative launch: ") + cudaGetErrorString(launch_err));
+    }
+    CK(cudaEventRecord(op0->ev1, s));
+    CK(cudaMemcpyAsync(bc->h_state, bc->d_state, sizeof(BState) * nprob, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(bc->h_flags, bc->d_flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, op0->ev0, op0->ev1));
+    bool any_nonfinite = false, all_conv = true;
+    for (int b = 0; b < nprob; ++b) {
+        const BState& stt = bc->h_state[b];
+        any_nonfinite |= stt.nonfinite != 0;
+        all_conv &= stt.converged != 0;
+        if (infos) {
+            tpmg_info& in = infos[b];
+            in.iters = stt.iters;
+            in.converged = stt.converged;
+            in.rel_res = stt.rel;
+            in.r0 = stt.r0;
+            in.ms = ms;
+            if (in.history && in.history_len > 0) {
+                int nh = stt.iters + 1 < in.history_len ? stt.iters + 1 : in.history_len;
+                CK(cudaMemcpy(in.history, bc->d_hist + (size_t)b * (prm->max_iter + 1), sizeof(double) * nh,
+                              cudaMemcpyDeviceToHost));
+            }
+        }
+    }
+    if (bc->h_flags[0]) return set_err(TPMG_ERR_TIMEOUT, "a grid barrier wait of the batched solver timed out");
+    if (any_nonfinite) return set_err(TPMG_ERR_NONFINITE, "non-finite residual in a batched problem");
+    if (!all_conv) return set_err(TPMG_ERR_NOT_CONVERGED, "max_iter reached for a batched problem");
+    return TPMG_OK;
+}

@@ -128,6 +128,67 @@ template <class P>
 void launch_cg_finish(size_t n, const Scalars* sc, typename P::S* u, const typename P::S* p,
                       cudaStream_t s);
 
+// ---------------------------------------------------------------- batched persistent solver (k_batched.cu)
+// Many independent problems of different sizes advance through one mixed-precision iterative
+// refinement together, inside one cooperative persistent launch: the work of each step of the
+// cycle ("phase") is cut into tiles of 32 x BTY columns over all problems; a bounded grid barrier
+// separates the phases. Per-problem state decides which problems are still active.
+enum { BT_OUTRES = 0, BT_FINAL = 1, BT_LS0 = 2, BT_SMOOTH = 3, BT_RESID = 4, BT_RS = 5, BT_PROL = 6, BT_CORR = 7 };
+static constexpr int BTY = 4;  // rows of columns per tile (block = 32 x BTY threads)
+static constexpr int BMAXL = 16;
+
+struct BLevelDesc {  // FP32 view of one level of one problem
+    int nx, ny, nz, percol;
+    double cx, cy;
+    const float* v;
+    const float* finv;
+    const float* fw;
+};
+struct BProbDesc {
+    int L, nz;
+    BLevelDesc lev[BMAXL + 1];
+    float2* uD;         // double-word finest iterate
+    const float2* fD;   // double-word finest right-hand side
+    const float2* vD;   // double-word finest v per column
+    float* r32;         // FP32 right-hand side of the inner cycle (finest level)
+    int part_base;      // first partial-sum slot of this problem's outer residual norm
+    int fine_tiles;
+    double* history;    // relative residual history (max_iter + 1 doubles)
+};
+struct BTask {
+    int type, prob, level;
+    const void* a;  // input field (iterate / residual / coarse correction)
+    const void* b;  // right-hand side
+    void* out;
+    void* out2;
+    int tiles_x, tiles_y, tile_base;
+};
+struct BState {
+    double r0, rel;
+    int iters, active, converged, nonfinite;
+};
+struct BatchDesc {
+    int nprob, ntasks, nphase;
+    const BProbDesc* probs;
+    BState* state;
+    const BTask* tasks;
+    const int* phase_begin;  // nphase + 1 task offsets
+    const int* phase_tiles;  // tiles per phase
+    double* partials;
+    unsigned* bar_count;
+    unsigned* bar_gen;
+    int* error;     // 1: a barrier wait timed out
+    int* n_active;  // problems still iterating
+    double rho, tol;
+    int max_iter;
+    unsigned long long timeout_ns;
+    int nz_max;
+};
+// cooperative launch of the persistent kernel; returns the CUDA status of the launch
+cudaError_t launch_batched(const BatchDesc& d, int grid, size_t smem, cudaStream_t s);
+size_t batched_smem(int nz_max);
+int batched_blocks_per_sm(int nz_max);
+
 // ---------------------------------------------------------------- scalar kernels (k_util.cu)
 // modes of finalize_norm
 enum { FIN_STORE = 0, FIN_MG_INIT = 1, FIN_MG_CYCLE = 2, FIN_SUM = 3 };

@@ -35,7 +35,7 @@ class TpmgError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("n_coarse", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("rho", ctypes.c_double), ("tol", ctypes.c_double),
-                ("prec", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("use_graph", ctypes.c_int), ("timeout_s", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -70,6 +70,7 @@ _SIGNATURES = {
     "tpmg_mg_solve": [_P, ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Info), _P],
     "tpmg_vcycle": [_P, ctypes.POINTER(Params), _P, _P, _P],
     "tpmg_cg_solve": [_P, ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Info), _P],
+    "tpmg_mg_solve_batched": [_I, _P, ctypes.POINTER(Params), _P, _P, _P, _P],
     "tpmg_residual_norm_noalloc": [_I, _I, _I, _D, _D, _P, _P, _P, _P, _P, _P],
     "tpmg_noalloc_last_error": [],
     "tpmg_time_kernel": [_P, _I, _I, _I, ctypes.POINTER(_D), _P],
@@ -273,6 +274,26 @@ def mg_solve(op, params, f, u, n, history_len=256, stream=None, allow=(ERR_NOT_C
 
 def cg_solve(op, params, f, u, n, history_len=4096, stream=None, allow=(ERR_NOT_CONVERGED,)):
     return _solve("tpmg_cg_solve", op, params, f, u, n, history_len, stream, allow)
+
+
+def mg_solve_batched(ops, params, fs, us, history_len=128, stream=None, allow=(ERR_NOT_CONVERGED,)):
+    """ops: list of operator handles; fs, us: lists of CUDA float64 fields (finest level of each)."""
+    nb = len(ops)
+    op_arr = (_P * nb)(*ops)
+    f_arr = (_P * nb)(*[_field(f, F64, f.numel(), "f") for f in fs])
+    u_arr = (_P * nb)(*[_field(u, F64, f.numel(), "u") for f, u in zip(fs, us)])
+    infos = (Info * nb)()
+    hists = [(ctypes.c_double * history_len)() for _ in range(nb)]
+    for b in range(nb):
+        infos[b].history = ctypes.cast(hists[b], ctypes.POINTER(ctypes.c_double))
+        infos[b].history_len = history_len
+    status = load().tpmg_mg_solve_batched(nb, ctypes.cast(op_arr, _P), ctypes.byref(params), ctypes.cast(f_arr, _P),
+                                          ctypes.cast(u_arr, _P), ctypes.cast(infos, _P), _stream(stream))
+    _check(status, "mg_solve_batched", allow=allow)
+    return {"status": status, "ms": infos[0].ms,
+            "problems": [{"iters": infos[b].iters, "converged": bool(infos[b].converged), "rel_res": infos[b].rel_res,
+                          "r0": infos[b].r0, "history": [hists[b][i] for i in range(min(infos[b].iters + 1, history_len))]}
+                         for b in range(nb)]}
 
 
 def vcycle(op, params, f, u, n, stream=None):

@@ -60,9 +60,11 @@ def make_rhs(nx: int, ny: int, nz: int, seed: int, kind: str) -> np.ndarray:
 
 
 def levels_to_8(nx: int, ny: int) -> int:
-    """Number of levels when halving both horizontal sizes until the smaller one reaches 8."""
+    """Number of levels when halving both horizontal sizes while both are even and the larger one
+    exceeds 8 (square grids: down to 8 x 8; elongated grids keep coarsening the long side, the short
+    side may reach 1, so the coarsest level stays well conditioned)."""
     L = 1
-    while nx % 2 == 0 and ny % 2 == 0 and min(nx, ny) > 8:
+    while nx % 2 == 0 and ny % 2 == 0 and max(nx, ny) > 8:
         nx //= 2
         ny //= 2
         L += 1
@@ -110,7 +112,8 @@ def paper_shaped(nx: int = 512, nz: int = 128, lambda2: float = 1e3) -> Problem:
 
 def batched(nprob: int = 64, seed: int = 0) -> list[Problem]:
     """Batched: sizes drawn uniformly from {64,128,256,512}^2 x {32,64,128} (seed 0), lambda^2
-    log-uniform in [1e2, 1e4], problem b's uniform[-1,1] RHS from seed 1000 + b."""
+    log-uniform in [1e2, 1e4], problem b's uniform[-1,1] RHS from seed 1000 + b. Horizontal cells are
+    square, hx = hy = 1/max(nx, ny) (the unit square spans the longer side), hz = 1/nz."""
     rng = np.random.default_rng(seed)
     probs = []
     for b in range(nprob):
@@ -118,7 +121,8 @@ def batched(nprob: int = 64, seed: int = 0) -> list[Problem]:
         ny = int(rng.choice([64, 128, 256, 512]))
         nz = int(rng.choice([32, 64, 128]))
         lam2 = float(10.0 ** rng.uniform(2.0, 4.0))
-        probs.append(Problem(f"batch{b}", nx, ny, nz, 1e-2, 1.0 / nx, 1.0 / ny, 1.0 / nz, lam2,
+        h = 1.0 / max(nx, ny)
+        probs.append(Problem(f"batch{b}", nx, ny, nz, 1e-2, h, h, 1.0 / nz, lam2,
                              levels_to_8(nx, ny), 1000 + b, "uniform"))
     return probs
 

@@ -51,7 +51,7 @@ def test_grid_argument_checks_without_gpu():
     assert tpmg.grid_nlevels(g) == 4
     tpmg.destroy_grid(g)
     g = tpmg.create_grid(256, 128, 32, 0)
-    assert tpmg.grid_nlevels(g) == 5 and tpmg.grid_level_size(g, 1) == (16, 8)
+    assert tpmg.grid_nlevels(g) == 6 and tpmg.grid_level_size(g, 1) == (8, 4)
     tpmg.destroy_grid(g)
     import pytest
     with pytest.raises(tpmg.TpmgError):
