@@ -218,3 +218,104 @@ def ir_solve(f, cx, cy, v, nlevels, tol=1e-6, max_iter=100, u0=None, nu_pre=2, n
     if it < 0:
         raise ValueError("bad multigrid arguments")
     return u, it, hist[: it + 1], bool(conv.value)
+
+
+# ------------------------------------------------------------------ learned stage and flexible CG
+class _OrcPrec(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("L", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
+                ("n_coarse", ctypes.c_int), ("rho", ctypes.c_double), ("cin", ctypes.c_int),
+                ("params", ctypes.c_void_p), ("aux", ctypes.c_void_p), ("nn_used", ctypes.c_int),
+                ("nn_rejected", ctypes.c_int)]
+
+
+def _nnlib():
+    lib = _load()
+    if not getattr(lib, "_nn_ready", False):
+        for name, args, res in [
+            ("orc_conv3d_fwd", [_I, _I, _I, _I, _I, _P, _P, _I, _P, _P], None),
+            ("orc_conv3d_bwd", [_I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P], None),
+            ("orc_nn_forward", [_I, _I, _I, _I, _P, _P, _P, _P], None),
+            ("orc_nn_loss_grad", [_I, _I, _I, _I, _P, _P, _P, _P], _D),
+            ("orc_adam_step", [ctypes.c_size_t, _P, _P, _P, _P, _I, _D, _D, _D, _D], None),
+            ("orc_fcg_solve", [_I, _I, _I, _D, _D, _P, ctypes.POINTER(_OrcPrec), _D, _I, _P, _P, _P, _P], _I),
+            ("orc_nn_nparams", [_I], ctypes.c_size_t),
+        ]:
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        lib._nn_ready = True
+    return lib
+
+
+def nn_nparams(cin: int) -> int:
+    return int(_nnlib().orc_nn_nparams(cin))
+
+
+def conv3d(x, W, b, relu=False):
+    """Cross-correlation with 3x3x3 kernels, circular in x and y, zero-padded in z.
+    x: (cin, nz, ny, nx); W: (cout, cin, 3, 3, 3); b: (cout,) or None."""
+    x = _f64(x)
+    W = _f64(W)
+    cin, nz, ny, nx = x.shape
+    cout = W.shape[0]
+    y = np.empty((cout, nz, ny, nx))
+    bb = None if b is None else _f64(b)
+    _nnlib().orc_conv3d_fwd(nx, ny, nz, cin, cout, _ptr(W), None if bb is None else _ptr(bb), int(relu),
+                            _ptr(x), _ptr(y))
+    return y
+
+
+def conv3d_backward(x, W, dy, want_dx=True):
+    """(dx, dW, db) of one layer for the gradient dy of its output."""
+    x, W, dy = _f64(x), _f64(W), _f64(dy)
+    cin, nz, ny, nx = x.shape
+    cout = W.shape[0]
+    dx = np.empty_like(x) if want_dx else None
+    dW = np.zeros_like(W)
+    db = np.zeros(cout)
+    _nnlib().orc_conv3d_bwd(nx, ny, nz, cin, cout, _ptr(W), _ptr(x), _ptr(dy), None if dx is None else _ptr(dx),
+                            _ptr(dW), _ptr(db))
+    return dx, dW, db
+
+
+def nn_forward(params, x):
+    """The 4-layer network (cin -> 16 -> 16 -> 16 -> 1); x: (cin, nz, ny, nx); returns (nz, ny, nx)."""
+    params, x = _f64(params), _f64(x)
+    cin, nz, ny, nx = x.shape
+    out = np.empty((nz, ny, nx))
+    _nnlib().orc_nn_forward(nx, ny, nz, cin, _ptr(params), _ptr(x), _ptr(out), None)
+    return out
+
+
+def nn_loss_grad(params, x, target):
+    """Mean-squared loss of the network output against target, and its parameter gradient."""
+    params, x, target = _f64(params), _f64(x), _f64(target)
+    cin, nz, ny, nx = x.shape
+    g = np.empty_like(params)
+    loss = _nnlib().orc_nn_loss_grad(nx, ny, nz, cin, _ptr(params), _ptr(x), _ptr(target), _ptr(g))
+    return loss, g
+
+
+def adam_step(theta, g, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In place on theta, m, v (float64 numpy arrays)."""
+    g = _f64(g)
+    _nnlib().orc_adam_step(theta.size, _ptr(theta), _ptr(g), _ptr(m), _ptr(v), t, lr, beta1, beta2, eps)
+
+
+def fcg_solve(f, cx, cy, v, mode=1, nlevels=1, tol=1e-6, max_iter=500, params=None, aux=None, u0=None,
+              nu_pre=2, nu_post=2, n_coarse=2, rho=0.8):
+    """Flexible CG(1); mode 0: line-solve preconditioner, 1: V-cycle, 2: V-cycle + learned stage.
+    Returns (u, iters, history, converged, nn_used, nn_rejected)."""
+    f = _f64(f)
+    nz, ny, nx = f.shape
+    v = _vcol(v, nx, ny)
+    u = np.zeros_like(f) if u0 is None else _f64(u0).copy()
+    hist = np.zeros(max_iter + 1)
+    conv = ctypes.c_int(0)
+    pp = None if params is None else _f64(params)
+    ax = None if aux is None else _f64(aux)
+    P = _OrcPrec(mode, nlevels, nu_pre, nu_post, n_coarse, rho, 1 if ax is None else 2,
+                 None if pp is None else pp.ctypes.data, None if ax is None else ax.ctypes.data, 0, 0)
+    it = _nnlib().orc_fcg_solve(nx, ny, nz, cx, cy, _ptr(v), ctypes.byref(P), tol, max_iter, _ptr(f), _ptr(u),
+                                _ptr(hist), ctypes.byref(conv))
+    return u, it, hist[: it + 1], bool(conv.value), P.nn_used, P.nn_rejected
