@@ -305,6 +305,7 @@ def adam_step(theta, g, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
 def fcg_solve(f, cx, cy, v, mode=1, nlevels=1, tol=1e-6, max_iter=500, params=None, aux=None, u0=None,
               nu_pre=2, nu_post=2, n_coarse=2, rho=0.8):
     """Flexible CG(1); mode 0: line-solve preconditioner, 1: V-cycle, 2: V-cycle + learned stage.
+    aux: the network's second input channel, per column (ny, nx) or per cell (nz, ny, nx).
     Returns (u, iters, history, converged, nn_used, nn_rejected)."""
     f = _f64(f)
     nz, ny, nx = f.shape
@@ -313,7 +314,7 @@ def fcg_solve(f, cx, cy, v, mode=1, nlevels=1, tol=1e-6, max_iter=500, params=No
     hist = np.zeros(max_iter + 1)
     conv = ctypes.c_int(0)
     pp = None if params is None else _f64(params)
-    ax = None if aux is None else _f64(aux)
+    ax = None if aux is None else _f64(np.broadcast_to(np.asarray(aux, dtype=np.float64), (nz, ny, nx)))
     P = _OrcPrec(mode, nlevels, nu_pre, nu_post, n_coarse, rho, 1 if ax is None else 2,
                  None if pp is None else pp.ctypes.data, None if ax is None else ax.ctypes.data, 0, 0)
     it = _nnlib().orc_fcg_solve(nx, ny, nz, cx, cy, _ptr(v), ctypes.byref(P), tol, max_iter, _ptr(f), _ptr(u),

@@ -163,8 +163,9 @@ typedef struct {
     int nn_used, nn_rejected;
 } orc_prec;
 
-/* z = B(r). Mode 2: z1 = V-cycle(r), r1 = r - A z1, z = z1 + ||r1|| NN(r1/||r1||); the learned
- * correction is dropped (z = z1) when ||r - A z|| >= ||r1|| or the result is not finite. */
+/* z = B(r). Mode 2: z1 = V-cycle(r), r1 = r - A z1, s = rms(r1) = ||r1|| / sqrt(n),
+ * z = z1 + s NN(r1 / s) (the network sees a residual of unit mean square, whatever the grid size);
+ * the learned correction is dropped (z = z1) when ||r - A z|| >= ||r1|| or the result is not finite. */
 static void fcg_precondition(int nx, int ny, int nz, double cx, double cy, const double *v, orc_prec *P,
                              const double *r, double *z) {
     size_t n = (size_t)nx * ny * nz;
@@ -184,10 +185,11 @@ static void fcg_precondition(int nx, int ny, int nz, double cx, double cy, const
     double nr1 = sqrt(orc_dot(n, r1, r1));
     int accept = 0;
     if (nr1 > 0.0 && isfinite(nr1)) {
-        for (size_t p = 0; p < n; ++p) x[p] = r1[p] / nr1;
+        double rms = nr1 / sqrt((double)n);
+        for (size_t p = 0; p < n; ++p) x[p] = r1[p] / rms;
         if (P->cin > 1) memcpy(x + n, P->aux, sizeof(double) * n);
         orc_nn_forward(nx, ny, nz, P->cin, P->params, x, c, NULL);
-        for (size_t p = 0; p < n; ++p) c[p] = z[p] + nr1 * c[p];
+        for (size_t p = 0; p < n; ++p) c[p] = z[p] + rms * c[p];
         orc_apply_A(nx, ny, nz, cx, cy, v, c, Az);
         double s = 0.0;
         for (size_t p = 0; p < n; ++p) {
@@ -237,6 +239,7 @@ int orc_fcg_solve(int nx, int ny, int nz, double cx, double cy, const double *v,
                 *converged = 1;
                 break;
             }
+            if (it == max_iter) break;
             fcg_precondition(nx, ny, nz, cx, cy, v, P, r, z);
             double beta = orc_dot(n, z, q) / pq;
             for (size_t s = 0; s < n; ++s) p[s] = z[s] - beta * p[s];

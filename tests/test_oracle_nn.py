@@ -149,3 +149,52 @@ def test_learned_stage_with_zero_network_always_falls_back():
     assert it1 == it2 and np.array_equal(h1, h2)
     # one application before the loop and one after every iteration but the last
     assert used == 0 and rejected == it2
+
+
+def affine_network(cin, alpha, beta):
+    """Parameters of a network computing NN(x) = alpha * x[0] + beta exactly: layer 1 splits channel 0
+    into relu(x) and relu(-x) (centre taps +1 and -1), layers 2 and 3 pass those two channels through
+    (centre taps 1), layer 4 recombines them as alpha * (relu(x) - relu(-x)) + beta."""
+    n1, n2, n4 = 16 * cin * 27, 16 * 16 * 27, 16 * 27
+    p = np.zeros(oracle.nn_nparams(cin))
+    W1 = p[:n1].reshape(16, cin, 27)
+    W1[0, 0, 13], W1[1, 0, 13] = 1.0, -1.0
+    o2 = n1 + 16
+    for o in (o2, o2 + n2 + 16):
+        W = p[o:o + n2].reshape(16, 16, 27)
+        W[0, 0, 13] = W[1, 1, 13] = 1.0
+    o4 = o2 + 2 * (n2 + 16)
+    W4 = p[o4:o4 + n4].reshape(16, 27)
+    W4[0, 13], W4[1, 13] = alpha, -alpha
+    p[o4 + n4] = beta
+    return p
+
+
+def test_affine_network_is_affine():
+    p = affine_network(2, 0.3, -0.7)
+    x = rnd((2, 4, 5, 6), 30)
+    assert np.allclose(oracle.nn_forward(p, x), 0.3 * x[0] - 0.7, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("alpha,beta", [(2.0 ** -12, 1e-3), (2.0 ** -12, 50.0)], ids=["accepted", "rejected"])
+def test_learned_stage_first_step_by_hand(alpha, beta):
+    """One FCG step from u = 0 with the affine network, derived here from the V-cycle, the operator
+    and the definitions: z1 = V(f), r1 = f - A z1, s = ||r1|| / sqrt(n), c = z1 + s (alpha r1/s + beta)
+    = z1 + alpha r1 + beta s, kept iff ||f - A c|| < ||r1||; then u1 = (<z, f> / <z, A z>) z.
+    The constant beta s is where the residual normalisation shows: a 2-norm reading instead of the
+    root-mean-square one changes it by sqrt(n)."""
+    f, cx, cy, v = _problem()
+    n = f.size
+    z1 = oracle.vcycle(np.zeros_like(f), f, cx, cy, v, 2)
+    r1 = f - oracle.apply_A(z1, cx, cy, v)
+    s = np.linalg.norm(r1) / np.sqrt(n)
+    c = z1 + alpha * r1 + beta * s
+    keep = np.linalg.norm(f - oracle.apply_A(c, cx, cy, v)) < np.linalg.norm(r1)
+    assert keep == (beta < 1.0)  # the two cases cover both branches
+    z = c if keep else z1
+    u1 = (np.vdot(z, f) / np.vdot(z, oracle.apply_A(z, cx, cy, v))) * z
+    p = affine_network(1, alpha, beta)
+    u, it, _, _, used, rejected = oracle.fcg_solve(f, cx, cy, v, mode=2, nlevels=2, tol=1e-300, max_iter=1,
+                                                   params=p)
+    assert it == 1 and (used, rejected) == ((1, 0) if keep else (0, 1))
+    assert rel(u, u1) < 1e-12
