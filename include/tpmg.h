@@ -206,6 +206,49 @@ unsigned long long tpmg_kernel_launches(void);
 tpmg_status tpmg_autotune(tpmg_op* op, tpmg_precision prec, int reps, int* variants_out, void* stream);
 tpmg_status tpmg_set_variant(tpmg_op* op, tpmg_precision prec, int level, int variant);
 
+/* ---------------------------------------------------------------- learned preconditioner stage
+ * A 3-D convolutional network used as an extra preconditioner stage inside flexible CG (an
+ * extension of the method: the paper's preconditioners are the line solve and the V-cycle).
+ * Architecture: cin (1 or 2) -> 16 -> 16 -> 16 -> 1 channels, 3x3x3 kernels, ReLU after the first
+ * three layers, periodic padding in x and y and zero padding in z (the problem's boundaries).
+ * Parameters: tpmg_nn_nparams(cin) floats, flat W1 b1 W2 b2 W3 b3 W4 b4 with W[co][ci][dz][dy][dx].
+ * Inference and training run in BF16 with FP32 accumulation (the 16 -> 16 layers and their weight
+ * gradients on the tensor cores); FP32 master weights; Adam (lr given, beta 0.9/0.999, eps 1e-8).
+ * Network inputs x are DEVICE fp32, channels-last (cin values per cell, cell index (k*ny+j)*nx+i);
+ * outputs and targets DEVICE fp32 (one value per cell). Grids need nx % 64 == 0 and ny % 2 == 0. */
+typedef struct tpmg_nn tpmg_nn;
+int tpmg_nn_nparams(int cin);
+/* params_host: HOST array of nparams floats, or NULL for all zeros */
+tpmg_status tpmg_nn_create(int cin, const float* params_host, tpmg_nn** out);
+tpmg_status tpmg_nn_destroy(tpmg_nn* nn);
+tpmg_status tpmg_nn_get_params(const tpmg_nn* nn, float* host);
+/* replaces the parameters and resets the Adam moments */
+tpmg_status tpmg_nn_set_params(tpmg_nn* nn, const float* host);
+tpmg_status tpmg_nn_forward(tpmg_nn* nn, int nx, int ny, int nz, const float* x, float* out, void* stream);
+/* loss = mean over cells of (NN(x) - target)^2 into the DEVICE double *loss_out; its gradient
+ * w.r.t. the parameters into the DEVICE array grad_out (nparams floats) if not NULL */
+tpmg_status tpmg_nn_loss_grad(tpmg_nn* nn, int nx, int ny, int nz, const float* x, const float* target,
+                              double* loss_out, float* grad_out, void* stream);
+/* one Adam step on the loss above */
+tpmg_status tpmg_nn_train_step(tpmg_nn* nn, int nx, int ny, int nz, const float* x, const float* target,
+                               double lr, double* loss_out, void* stream);
+/* Training pair from an iterate u_k of a solve with exact solution u_star and its residual r
+ * (DEVICE doubles, one per cell): x = (r/rms(r) and, if cin == 2, aux per column (DEVICE fp32,
+ * ny*nx)) in BF16-rounded fp32, target = (u_star - u_k)/rms(r) (target_out may be NULL, then
+ * u_star and u_k may be too). Synchronises `stream`; allocates its scratch (a training utility). */
+tpmg_status tpmg_nn_make_pair(int nx, int ny, int nz, int cin, const double* r, const double* u_star,
+                              const double* u_k, const float* aux, float* x_out, float* target_out,
+                              void* stream);
+/* Flexible CG with truncation 1 (Notay's FCG(1)) for A u = f on the finest level, double-word
+ * vectors; preconditioner: one FP32 V-cycle z1 of r (the mixed solver's inner cycle, prm's
+ * smoothing parameters) and, if nn is not NULL, the learned correction
+ * z = z1 + rms(r1) NN(r1/rms(r1)), r1 = r - A z1, kept only when ||r - A z|| < ||r1|| (else z = z1).
+ * aux: DEVICE fp32 second input channel per column (2-channel networks), else NULL.
+ * *nn_accepted (host, may be NULL) receives how many learned corrections were kept. Stops on
+ * Eq. (10) like the other solvers; same return values as tpmg_mg_solve. */
+tpmg_status tpmg_fcg_solve(tpmg_op* op, tpmg_nn* nn, const float* aux, const tpmg_params* prm, const double* f,
+                           double* u, tpmg_info* info, int* nn_accepted, void* stream);
+
 /* ---------------------------------------------------------------- allocation-free variant
  * The paper has no counterpart: this entry point exists for callers that must not allocate device
  * memory while they run -- applications whose framework already owns nearly all device memory

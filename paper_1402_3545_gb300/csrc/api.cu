@@ -88,6 +88,9 @@ struct tpmg_op {
     cudaStream_t cap_stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     GraphCache graphs[8];
+    void* fcg_sc = nullptr;    // device scalars of flexible CG
+    void* fcg_host = nullptr;  // pinned copy
+    void* fcgbuf[3] = {};      // flexible CG scratch vectors (double-word)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -138,7 +141,8 @@ static size_t elem_bytes(int pid) { return pid == 1 ? 4 : 8; }
 
 static tpmg_status ensure_common(tpmg_op* op) {
     if (!op->partials) {
-        op->max_parts = max_partials(op->g.nx, op->g.ny);
+        // at least 152 x 8 per half: the grid-stride reductions of flexible CG use up to that many blocks
+        op->max_parts = std::max(max_partials(op->g.nx, op->g.ny), 152 * 8);
         TRY(dalloc((void**)&op->partials, sizeof(double) * 2 * (size_t)op->max_parts));
     }
     if (!op->sc) TRY(dalloc((void**)&op->sc, sizeof(Scalars)));
@@ -672,6 +676,9 @@ tpmg_status tpmg_destroy_operator(tpmg_op* op) {
     for (int p = 0; p < 3; ++p)
         for (int t = 0; t < 4; ++t) dfree(op->cgbuf[p][t]);
     for (int t = 0; t < 4; ++t) dfree(op->io[t]);
+    for (int t = 0; t < 3; ++t) dfree(op->fcgbuf[t]);
+    dfree(op->fcg_sc);
+    if (op->fcg_host) cudaFreeHost(op->fcg_host);
     dfree((void*&)op->partials);
     dfree((void*&)op->sc);
     dfree((void*&)op->history);
@@ -1557,5 +1564,322 @@ extern "C" tpmg_status tpmg_mg_solve_batched(int nprob, tpmg_op* const* ops, con
     if (bc->h_flags[0]) return set_err(TPMG_ERR_TIMEOUT, "a grid barrier wait of the batched solver timed out");
     if (any_nonfinite) return set_err(TPMG_ERR_NONFINITE, "non-finite residual in a batched problem");
     if (!all_conv) return set_err(TPMG_ERR_NOT_CONVERGED, "max_iter reached for a batched problem");
+    return TPMG_OK;
+}
+
+// ================================================================ learned stage and flexible CG
+#include "fcg.cuh"
+#include "nn.cuh"
+
+struct tpmg_nn {
+    NNBufs b;
+    int adam_t = 0;
+    bool weights_ready = false;
+};
+
+static tpmg_status nn_ensure_cap(tpmg_nn* nn, size_t n) {
+    NNBufs& b = nn->b;
+    if (n <= b.ncap) return TPMG_OK;
+    void* ptrs[] = {b.a1, b.a2, b.a3, b.d1, b.d2, b.x, b.out, b.d4};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    b.a1 = b.a2 = b.a3 = b.d1 = b.d2 = b.x = nullptr;
+    b.out = b.d4 = nullptr;
+    b.ncap = 0;
+    TRY(dalloc((void**)&b.a1, n * 32));
+    TRY(dalloc((void**)&b.a2, n * 32));
+    TRY(dalloc((void**)&b.a3, n * 32));
+    TRY(dalloc((void**)&b.d1, n * 32));
+    TRY(dalloc((void**)&b.d2, n * 32));
+    TRY(dalloc((void**)&b.x, n * 2 * (size_t)b.cin));
+    TRY(dalloc((void**)&b.out, n * 4));
+    TRY(dalloc((void**)&b.d4, n * 4));
+    b.ncap = n;
+    return TPMG_OK;
+}
+
+static tpmg_status nn_check_shape(int nx, int ny, int nz) {
+    if (nx < 64 || nx % 64 != 0 || ny < 2 || ny % 2 != 0 || nz < 1)
+        return set_err(TPMG_ERR_ARG, "the network kernels need nx a multiple of 64 and ny even");
+    return TPMG_OK;
+}
+
+static void nn_refresh(tpmg_nn* nn, cudaStream_t s) {
+    nn_prepare_weights(nn->b, s);
+    nn->weights_ready = true;
+}
+
+extern "C" {
+
+int tpmg_nn_nparams(int cin) { return 16 * cin * 27 + 16 + 2 * (16 * 16 * 27 + 16) + 16 * 27 + 1; }
+
+tpmg_status tpmg_nn_create(int cin, const float* params_host, tpmg_nn** out) {
+    if (!out || (cin != 1 && cin != 2)) return set_err(TPMG_ERR_ARG, "cin must be 1 or 2");
+    tpmg_nn* nn = new tpmg_nn();
+    memset(&nn->b, 0, sizeof(NNBufs));
+    NNBufs& b = nn->b;
+    b.cin = cin;
+    b.nparams = tpmg_nn_nparams(cin);
+    const size_t np = (size_t)b.nparams;
+    tpmg_status st = TPMG_OK;
+    void** bufs[] = {(void**)&b.params, (void**)&b.grad, (void**)&b.adam_m, (void**)&b.adam_v};
+    for (void** q : bufs)
+        if ((st = dalloc(q, np * sizeof(float))) != TPMG_OK) break;
+    void** wb[] = {(void**)&b.w1, (void**)&b.w2f, (void**)&b.w2b, (void**)&b.w3f, (void**)&b.w3b, (void**)&b.w4};
+    for (void** q : wb)
+        if (st == TPMG_OK) st = dalloc(q, 16 * 16 * 27 * 2);
+    if (st == TPMG_OK) st = dalloc((void**)&b.part, sizeof(float) * 1024 * 16 * 16 * 27);
+    if (st == TPMG_OK) st = dalloc((void**)&b.dpart, sizeof(double) * 4096);
+    if (st == TPMG_OK && params_host)
+        if (cudaMemcpy(b.params, params_host, np * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            st = set_err(TPMG_ERR_CUDA, "parameter upload failed");
+    if (st != TPMG_OK) {
+        tpmg_nn_destroy(nn);
+        return st;
+    }
+    *out = nn;
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_nn_destroy(tpmg_nn* nn) {
+    if (!nn) return TPMG_OK;
+    cudaDeviceSynchronize();
+    NNBufs& b = nn->b;
+    void* ptrs[] = {b.params, b.grad, b.adam_m, b.adam_v, b.w1, b.w2f, b.w2b, b.w3f, b.w3b, b.w4,
+                    b.a1,     b.a2,   b.a3,     b.d1,     b.d2, b.x,   b.out, b.d4,  b.part, b.dpart};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete nn;
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_nn_get_params(const tpmg_nn* nn, float* host) {
+    if (!nn || !host) return set_err(TPMG_ERR_ARG, "NULL network or buffer");
+    CK(cudaMemcpy(host, nn->b.params, sizeof(float) * nn->b.nparams, cudaMemcpyDeviceToHost));
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_nn_set_params(tpmg_nn* nn, const float* host) {
+    if (!nn || !host) return set_err(TPMG_ERR_ARG, "NULL network or buffer");
+    CK(cudaMemcpy(nn->b.params, host, sizeof(float) * nn->b.nparams, cudaMemcpyHostToDevice));
+    CK(cudaMemset(nn->b.adam_m, 0, sizeof(float) * nn->b.nparams));
+    CK(cudaMemset(nn->b.adam_v, 0, sizeof(float) * nn->b.nparams));
+    nn->adam_t = 0;
+    nn->weights_ready = false;
+    return TPMG_OK;
+}
+
+// x: DEVICE fp32, channels-last (cin values per cell)
+static tpmg_status nn_load_input(tpmg_nn* nn, size_t n, const float* x, cudaStream_t s);
+
+tpmg_status tpmg_nn_forward(tpmg_nn* nn, int nx, int ny, int nz, const float* x, float* out, void* stream) {
+    if (!nn || !x || !out) return set_err(TPMG_ERR_ARG, "NULL argument");
+    TRY(nn_check_shape(nx, ny, nz));
+    const size_t n = (size_t)nx * ny * nz;
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(nn_ensure_cap(nn, n));
+    if (!nn->weights_ready) nn_refresh(nn, s);
+    TRY(nn_load_input(nn, n, x, s));
+    nn_forward(nn->b, nx, ny, nz, nn->b.x, out, s);
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_nn_loss_grad(tpmg_nn* nn, int nx, int ny, int nz, const float* x, const float* target,
+                              double* loss_out, float* grad_out, void* stream) {
+    if (!nn || !x || !target || !loss_out) return set_err(TPMG_ERR_ARG, "NULL argument");
+    TRY(nn_check_shape(nx, ny, nz));
+    const size_t n = (size_t)nx * ny * nz;
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(nn_ensure_cap(nn, n));
+    if (!nn->weights_ready) nn_refresh(nn, s);
+    TRY(nn_load_input(nn, n, x, s));
+    NNBufs& b = nn->b;
+    nn_forward(b, nx, ny, nz, b.x, b.out, s);
+    const int nbl = 2048;
+    nn_mse(b.out, target, b.d4, b.dpart, n, nbl, s);
+    launch_finalize_norm(b.dpart, nbl, FIN_SUM, nullptr, nullptr, loss_out, s);
+    nn_backward(b, nx, ny, nz, b.x, b.d4, grad_out ? grad_out : b.grad, s);
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_nn_train_step(tpmg_nn* nn, int nx, int ny, int nz, const float* x, const float* target, double lr,
+                               double* loss_out, void* stream) {
+    TRY(tpmg_nn_loss_grad(nn, nx, ny, nz, x, target, loss_out, nullptr, stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    NNBufs& b = nn->b;
+    nn_adam(b.nparams, b.params, b.grad, b.adam_m, b.adam_v, (float)lr, ++nn->adam_t, s);
+    nn_refresh(nn, s);
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+}  // extern "C"
+
+__global__ void k_nn_input_f32(size_t n, int cin, const float* __restrict__ x, __nv_bfloat16* __restrict__ xb) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n * cin; t += (size_t)gridDim.x * blockDim.x)
+        xb[t] = __float2bfloat16_rn(x[t]);
+}
+static tpmg_status nn_load_input(tpmg_nn* nn, size_t n, const float* x, cudaStream_t s) {
+    size_t blocks = (n * nn->b.cin + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_nn_input_f32<<<(unsigned)blocks, 256, 0, s>>>(n, nn->b.cin, x, nn->b.x);
+    note_launch();
+    return TPMG_OK;
+}
+
+__global__ void k_sumsq_f64(size_t n, const double* __restrict__ r, double* partials) {
+    double s = 0.0;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        s = fma(r[t], r[t], s);
+    s = block_sum(s);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+__global__ void k_bf16_to_f32(size_t n, const __nv_bfloat16* __restrict__ a, float* __restrict__ b) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+        b[t] = __bfloat162float(a[t]);
+}
+
+extern "C" tpmg_status tpmg_nn_make_pair(int nx, int ny, int nz, int cin, const double* r, const double* u_star,
+                                         const double* u_k, const float* aux, float* x_out, float* target_out,
+                                         void* stream) {
+    if (nx < 1 || ny < 1 || nz < 1 || (cin != 1 && cin != 2) || !r || !x_out || (cin == 2 && !aux) ||
+        (target_out && (!u_star || !u_k)))
+        return set_err(TPMG_ERR_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)nx * ny * nz, ncol = (size_t)nx * ny;
+    // scratch: partial sums, their total and the bf16 input (allocated per call: a training tool)
+    double* part = nullptr;
+    __nv_bfloat16* xb = nullptr;
+    TRY(dalloc((void**)&part, sizeof(double) * 1025));
+    if (dalloc((void**)&xb, n * 2 * cin) != TPMG_OK) {
+        cudaFree(part);
+        return TPMG_ERR_OOM;
+    }
+    k_sumsq_f64<<<1024, 256, 0, s>>>(n, r, part);
+    launch_finalize_norm(part, 1024, FIN_SUM, nullptr, nullptr, part + 1024, s);
+    nn_make_input_f64(n, ncol, cin, r, aux, part + 1024, xb, u_star, u_k, target_out, s);
+    k_bf16_to_f32<<<1024, 256, 0, s>>>(n * cin, xb, x_out);
+    note_launch();
+    note_launch();
+    cudaError_t err = cudaStreamSynchronize(s);
+    cudaFree(part);
+    cudaFree(xb);
+    if (err != cudaSuccess) return set_err(TPMG_ERR_CUDA, cudaGetErrorString(err));
+    return TPMG_OK;
+}
+
+static tpmg_status read_fcg(tpmg_op* op, cudaStream_t s) {
+    CK(cudaMemcpyAsync(op->fcg_host, op->fcg_sc, sizeof(FcgScalars), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return TPMG_OK;
+}
+
+// Flexible CG(1) on double-word vectors (the iteration of the oracle's orc_fcg_solve); the
+// preconditioner is one FP32 V-cycle of the mixed solver and, when a network is given, the learned
+// correction, kept only when it lowers the residual.
+extern "C" tpmg_status tpmg_fcg_solve(tpmg_op* op, tpmg_nn* nn, const float* aux, const tpmg_params* prm,
+                                      const double* f, double* u, tpmg_info* info, int* nn_accepted, void* stream) {
+    TRY(check_params(op, prm));
+    if (!f || !u) return set_err(TPMG_ERR_ARG, "NULL field");
+    const int L = op->g.L;
+    const int nx = op->g.nx, ny = op->g.ny, nz = op->g.nz;
+    if (nn) {
+        TRY(nn_check_shape(nx, ny, nz));
+        if (nn->b.cin == 2 && !aux) return set_err(TPMG_ERR_ARG, "a 2-channel network needs the aux field");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = lvl_cells(op, L), ncol = (size_t)nx * ny;
+    TRY(ensure_hier(op, 2, true));
+    TRY(ensure_hier(op, 1, true));
+    TRY(ensure_cg(op, 2));
+    TRY(ensure_history(op, prm->max_iter + 2));
+    if (!op->fcg_sc) TRY(dalloc((void**)&op->fcg_sc, sizeof(FcgScalars)));
+    if (!op->fcg_host) CK(cudaMallocHost((void**)&op->fcg_host, sizeof(FcgScalars)));
+    for (int t = 0; t < 3; ++t) TRY(dalloc(&op->fcgbuf[t], n * sizeof(float2)));
+    if (nn) {
+        TRY(nn_ensure_cap(nn, n));
+        if (!nn->weights_ready) nn_refresh(nn, s);
+    }
+    FcgScalars* sc = (FcgScalars*)op->fcg_sc;
+    const FcgScalars* hs = (const FcgScalars*)op->fcg_host;
+    float2* uD = (float2*)op->hier[2].u[L];
+    float2* fD = (float2*)op->hier[2].f[L];
+    float2* r = (float2*)op->cgbuf[2][0];
+    float2* z = (float2*)op->cgbuf[2][1];
+    float2* p = (float2*)op->cgbuf[2][2];
+    float2* q = (float2*)op->cgbuf[2][3];
+    float2* z1 = (float2*)op->fcgbuf[0];
+    float2* c = (float2*)op->fcgbuf[1];
+    float2* w = (float2*)op->fcgbuf[2];
+    Hier& h32 = op->hier[1];
+    float* r32 = (float*)h32.f[L];
+    Lv<PolDW> LD = level_view<PolDW>(op, L);
+    Lv<PolF32> L32 = level_view<PolF32>(op, L);
+    double* part = op->partials;
+    auto precondition = [&]() {
+        // z1 = V-cycle_FP32(r): the mixed solver's inner cycle from a zero guess
+        fcg_f32_from_dw(n, r, r32, s);
+        Cycle<PolF32, PolF32> cyc(op, prm, s, nullptr, 1);
+        void* cur = h32.u[L];
+        void* oth = h32.ub[L];
+        launch_line_solve<PolF32>(L32, r32, (float*)cur, prm->rho, nullptr, s);
+        cyc.rest(cur, oth);
+        fcg_dw_from_f32(n, (const float*)cur, nn ? z1 : z, s);
+        if (!nn) return;
+        // learned stage: r1 = r - A z1; c = z1 + rms(r1) NN(r1 / rms(r1)); keep c if ||r - A c|| < ||r1||
+        const int nr = launch_residual<PolDW, PolDW>(LD, z1, r, c, part, nullptr, s);
+        fcg_scalar(FCG_R1, part, nr, sc, nullptr, s);
+        nn_make_input_dw(n, ncol, nn->b.cin, c, aux, &sc->r1sq, nn->b.x, s);
+        nn_forward(nn->b, nx, ny, nz, nn->b.x, nn->b.out, s);
+        fcg_learned(n, sc, z1, nn->b.out, c, s);
+        const int nr2 = launch_residual<PolDW, PolDW>(LD, c, r, w, part, nullptr, s);
+        fcg_scalar(FCG_DECIDE, part, nr2, sc, nullptr, s);
+        fcg_select(n, sc, c, z1, z, s);
+    };
+    CK(cudaEventRecord(op->ev0, s));
+    launch_f64_to_dw(n, (const double*)u, uD, s);
+    launch_f64_to_dw(n, f, fD, s);
+    fcg_init(sc, prm->tol, prm->max_iter, s);
+    const int nb = launch_residual<PolDW, PolDW>(LD, uD, fD, r, part, nullptr, s);  // r = f - A u
+    fcg_scalar(FCG_INIT_NORM, part, nb, sc, op->history, s);
+    TRY(read_fcg(op, s));
+    if (!hs->done) {
+        precondition();
+        CK(cudaMemcpyAsync(p, z, n * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+        for (int guard = 0; guard <= prm->max_iter + 1; ++guard) {
+            const int na = fcg_apply(LD, p, r, q, part, s);  // q = A p, <p, q>, <p, r>
+            fcg_scalar(FCG_ALPHA, part, na, sc, nullptr, s);
+            const int nu = fcg_update(n, sc, uD, p, r, q, part, s);  // u += alpha p, r -= alpha q
+            fcg_scalar(FCG_CHECK, part, nu, sc, op->history, s);
+            TRY(read_fcg(op, s));
+            if (hs->done) break;
+            precondition();
+            const int nd = fcg_dot(n, z, q, part, s);  // beta = <z, q> / <p, q>
+            fcg_scalar(FCG_BETA, part, nd, sc, nullptr, s);
+            fcg_direction(n, sc, z, p, s);  // p = z - beta p
+        }
+    }
+    launch_dw_to_f64(n, uD, u, s);
+    CK(cudaEventRecord(op->ev1, s));
+    TRY(read_fcg(op, s));
+    CK(cudaGetLastError());
+    if (nn_accepted) *nn_accepted = hs->accepted;
+    if (info) {
+        info->iters = hs->iters;
+        info->converged = hs->converged;
+        info->rel_res = hs->rel;
+        info->r0 = hs->r0;
+        if (info->history && info->history_len > 0) {
+            const int nh = hs->iters + 1 < info->history_len ? hs->iters + 1 : info->history_len;
+            CK(cudaMemcpy(info->history, op->history, sizeof(double) * nh, cudaMemcpyDeviceToHost));
+        }
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, op->ev0, op->ev1));
+        info->ms = ms;
+    }
+    if (hs->nonfinite) return set_err(TPMG_ERR_NONFINITE, "non-finite value in flexible CG");
+    if (!hs->converged) return set_err(TPMG_ERR_NOT_CONVERGED, "max_iter reached");
     return TPMG_OK;
 }

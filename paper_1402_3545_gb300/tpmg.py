@@ -71,6 +71,16 @@ _SIGNATURES = {
     "tpmg_vcycle": [_P, ctypes.POINTER(Params), _P, _P, _P],
     "tpmg_cg_solve": [_P, ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Info), _P],
     "tpmg_mg_solve_batched": [_I, _P, ctypes.POINTER(Params), _P, _P, _P, _P],
+    "tpmg_nn_nparams": [_I],
+    "tpmg_nn_create": [_I, _P, ctypes.POINTER(_P)],
+    "tpmg_nn_destroy": [_P],
+    "tpmg_nn_get_params": [_P, _P],
+    "tpmg_nn_set_params": [_P, _P],
+    "tpmg_nn_forward": [_P, _I, _I, _I, _P, _P, _P],
+    "tpmg_nn_loss_grad": [_P, _I, _I, _I, _P, _P, _P, _P, _P],
+    "tpmg_nn_train_step": [_P, _I, _I, _I, _P, _P, _D, _P, _P],
+    "tpmg_nn_make_pair": [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P],
+    "tpmg_fcg_solve": [_P, _P, _P, ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Info), ctypes.POINTER(_I), _P],
     "tpmg_residual_norm_noalloc": [_I, _I, _I, _D, _D, _P, _P, _P, _P, _P, _P],
     "tpmg_noalloc_last_error": [],
     "tpmg_time_kernel": [_P, _I, _I, _I, ctypes.POINTER(_D), _P],
@@ -300,6 +310,113 @@ def vcycle(op, params, f, u, n, stream=None):
     prec = params.prec
     _check(load().tpmg_vcycle(op, ctypes.byref(params), _field(f, prec, n, "f"), _field(u, prec, n, "u"),
                               _stream(stream)), "vcycle")
+
+
+# ---------------------------------------------------------------- learned stage and flexible CG
+def _f32(t, numel, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+            and t.numel() == numel):
+        raise TypeError(f"{name} must be a contiguous CUDA float32 tensor of {numel} elements")
+    return t.data_ptr()
+
+
+def nn_nparams(cin: int) -> int:
+    return int(load().tpmg_nn_nparams(cin))
+
+
+class Network:
+    """Owns a tpmg_nn (the 4-layer convolutional preconditioner stage)."""
+
+    def __init__(self, cin: int = 2, params=None):
+        import numpy as np
+        self.cin = cin
+        self.nparams = nn_nparams(cin)
+        h = _P()
+        ptr = None
+        if params is not None:
+            self._init = np.ascontiguousarray(params, dtype=np.float32)
+            assert self._init.size == self.nparams
+            ptr = self._init.ctypes.data_as(_P)
+        _check(load().tpmg_nn_create(cin, ptr, ctypes.byref(h)), "nn_create")
+        self.h = h.value
+
+    def get_params(self):
+        import numpy as np
+        out = np.empty(self.nparams, dtype=np.float32)
+        _check(load().tpmg_nn_get_params(self.h, out.ctypes.data_as(_P)), "nn_get_params")
+        return out
+
+    def set_params(self, params):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        assert a.size == self.nparams
+        _check(load().tpmg_nn_set_params(self.h, a.ctypes.data_as(_P)), "nn_set_params")
+
+    def forward(self, x, shape, stream=None):
+        nz, ny, nx = shape
+        n = nx * ny * nz
+        out = torch.empty(n, dtype=torch.float32, device=x.device)
+        _check(load().tpmg_nn_forward(self.h, nx, ny, nz, _f32(x, n * self.cin, "x"), out.data_ptr(),
+                                      _stream(stream)), "nn_forward")
+        return out
+
+    def loss_grad(self, x, target, shape, stream=None):
+        nz, ny, nx = shape
+        n = nx * ny * nz
+        loss = torch.zeros(1, dtype=torch.float64, device=x.device)
+        grad = torch.empty(self.nparams, dtype=torch.float32, device=x.device)
+        _check(load().tpmg_nn_loss_grad(self.h, nx, ny, nz, _f32(x, n * self.cin, "x"), _f32(target, n, "target"),
+                                        loss.data_ptr(), grad.data_ptr(), _stream(stream)), "nn_loss_grad")
+        return loss, grad
+
+    def train_step(self, x, target, shape, lr, stream=None):
+        nz, ny, nx = shape
+        n = nx * ny * nz
+        loss = torch.zeros(1, dtype=torch.float64, device=x.device)
+        _check(load().tpmg_nn_train_step(self.h, nx, ny, nz, _f32(x, n * self.cin, "x"), _f32(target, n, "target"),
+                                         lr, loss.data_ptr(), _stream(stream)), "nn_train_step")
+        return loss
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().tpmg_nn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def nn_make_pair(shape, cin, r, u_star=None, u_k=None, aux=None, stream=None):
+    """(x, target) for the network from a residual r and the error u_star - u_k (CUDA float64)."""
+    nz, ny, nx = shape
+    n = nx * ny * nz
+    x = torch.empty(n * cin, dtype=torch.float32, device=r.device)
+    target = torch.empty(n, dtype=torch.float32, device=r.device) if u_star is not None else None
+    _check(load().tpmg_nn_make_pair(nx, ny, nz, cin, _field(r, F64, n, "r"),
+                                    None if u_star is None else _field(u_star, F64, n, "u_star"),
+                                    None if u_k is None else _field(u_k, F64, n, "u_k"),
+                                    None if aux is None else _f32(aux, nx * ny, "aux"), x.data_ptr(),
+                                    None if target is None else target.data_ptr(), _stream(stream)), "nn_make_pair")
+    return x, target
+
+
+def fcg_solve(op, params, f, u, n, nn=None, aux=None, history_len=512, stream=None, allow=(ERR_NOT_CONVERGED,)):
+    hist = (ctypes.c_double * history_len)()
+    info = Info()
+    info.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+    info.history_len = history_len
+    acc = _I(0)
+    status = load().tpmg_fcg_solve(op, None if nn is None else nn.h,
+                                   None if aux is None else aux.data_ptr(), ctypes.byref(params),
+                                   _field(f, F64, n, "f"), _field(u, F64, n, "u"), ctypes.byref(info),
+                                   ctypes.byref(acc), _stream(stream))
+    _check(status, "fcg_solve", allow=allow)
+    return {"status": status, "iters": info.iters, "converged": bool(info.converged), "rel_res": info.rel_res,
+            "ms": info.ms, "nn_accepted": acc.value,
+            "history": [hist[i] for i in range(min(info.iters + 1, history_len))]}
 
 
 # ---------------------------------------------------------------- allocation-free variant

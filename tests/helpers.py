@@ -86,3 +86,26 @@ def rel(a, b) -> float:
     """||a - b||_2 / ||b||_2."""
     nb = np.linalg.norm(np.ravel(b))
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / (nb if nb > 0 else 1.0))
+
+
+def affine_network(cin, alpha, beta, gamma=0.0, nparams=None):
+    """Flat parameters (W1 b1 W2 b2 W3 b3 W4 b4, W[co][ci][tap]) of the 4-layer network that computes
+    NN(x) = alpha * x[0] + beta (+ gamma * relu(x[1]) when cin == 2) exactly: layer 1 splits channel 0
+    into relu(x) and relu(-x) (centre taps +1 and -1) and copies relu(x[1]) to channel 2, layers 2
+    and 3 pass channels 0..2 through (centre taps 1), layer 4 recombines them. All weights are
+    powers of two or zero when alpha and gamma are, so BF16 holds them exactly."""
+    n1, n2, n4 = 16 * cin * 27, 16 * 16 * 27, 16 * 27
+    p = np.zeros(n1 + 16 + 2 * (n2 + 16) + n4 + 1 if nparams is None else nparams)
+    W1 = p[:n1].reshape(16, cin, 27)
+    W1[0, 0, 13], W1[1, 0, 13] = 1.0, -1.0
+    if cin == 2:
+        W1[2, 1, 13] = 1.0
+    o2 = n1 + 16
+    for o in (o2, o2 + n2 + 16):
+        W = p[o:o + n2].reshape(16, 16, 27)
+        W[0, 0, 13] = W[1, 1, 13] = W[2, 2, 13] = 1.0
+    o4 = o2 + 2 * (n2 + 16)
+    W4 = p[o4:o4 + n4].reshape(16, 27)
+    W4[0, 13], W4[1, 13], W4[2, 13] = alpha, -alpha, gamma
+    p[o4 + n4] = beta
+    return p

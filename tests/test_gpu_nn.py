@@ -1,0 +1,185 @@
+"""The learned stage on the GPU against the oracle: the network's forward pass, its loss and
+parameter gradient, Adam, and the training-pair builder, all through the C ABI.
+
+The kernels keep weights, inputs and hidden activations in BF16 and accumulate in FP32. The oracle
+runs in FP64 on the same BF16-rounded weights and inputs, so what separates the two is the
+rounding of the three hidden activations (relative 2^-9 each) and of the data gradients in the
+backward pass. Tolerances, relative 2-norm: output 2e-2 (three roundings of 2^-9 that add in
+quadrature, times a cancellation factor of a few at the 16-channel sums); loss 2e-2; parameter
+gradients 5e-2 (a fourth and fifth BF16 rounding on the data gradients). A network built to be
+affine (helpers.affine_network) has no rounding after its input, so its output is held to FP32
+accuracy."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import affine_network, rel
+from paper_1402_3545_gb300 import tpmg
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(3, 4, 64), (5, 6, 128), (1, 2, 64)]  # (nz, ny, nx): several tiles, odd nz, nz = 1
+
+
+def bf16(a) -> np.ndarray:
+    return torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).double().numpy()
+
+
+def random_params(cin, seed, scale=1.0):
+    """He-initialised weights and small biases (flat, the C ABI's layout)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for ci, co in ((cin, 16), (16, 16), (16, 16), (16, 1)):
+        parts.append(scale * np.sqrt(2.0 / (27 * ci)) * rng.standard_normal(co * ci * 27))
+        parts.append(0.1 * rng.standard_normal(co))
+    p = np.concatenate(parts).astype(np.float32)
+    assert p.size == tpmg.nn_nparams(cin)
+    return p
+
+
+def weights_bf16(p, cin):
+    """The parameters as the kernels use them: weights rounded to BF16, biases kept in FP32."""
+    q = np.asarray(p, dtype=np.float64).copy()
+    o = 0
+    for ci, co in ((cin, 16), (16, 16), (16, 16), (16, 1)):
+        q[o:o + co * ci * 27] = bf16(q[o:o + co * ci * 27])
+        o += co * ci * 27 + co
+    return q
+
+
+def channels_last(x):
+    """(cin, nz, ny, nx) -> flat CUDA fp32 tensor, cin values per cell."""
+    return torch.from_numpy(np.ascontiguousarray(np.moveaxis(x, 0, -1)).astype(np.float32).ravel()).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("cin", [1, 2])
+def test_forward_matches_oracle(shape, cin):
+    p = random_params(cin, seed=cin)
+    x = np.random.default_rng(7).standard_normal((cin,) + shape)
+    net = tpmg.Network(cin, p)
+    y = host(net.forward(channels_last(x), shape)).reshape(shape)
+    ref = oracle.nn_forward(weights_bf16(p, cin), bf16(x))
+    assert rel(y, ref) < 2e-2, rel(y, ref)
+    assert np.max(np.abs(y - ref)) < 5e-2 * np.max(np.abs(ref))
+    net.close()
+
+
+@pytest.mark.parametrize("cin", [1, 2])
+def test_affine_network_is_exact(cin):
+    """alpha * bf16(x0) + beta (+ gamma relu(bf16(x1))) to FP32 accuracy: the hidden layers only
+    copy BF16 values, which BF16 holds exactly."""
+    shape = (3, 4, 128)
+    p = affine_network(cin, 2.0 ** -3, 0.37, gamma=0.5 if cin == 2 else 0.0).astype(np.float32)
+    x = np.random.default_rng(8).standard_normal((cin,) + shape)
+    net = tpmg.Network(cin, p)
+    y = host(net.forward(channels_last(x), shape)).reshape(shape)
+    xb = bf16(x)
+    ref = 2.0 ** -3 * xb[0] + np.float32(0.37) + (0.5 * np.maximum(xb[1], 0.0) if cin == 2 else 0.0)
+    assert np.max(np.abs(y - ref)) < 1e-6
+    net.close()
+
+
+@pytest.mark.parametrize("shape", SHAPES[:2], ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("cin", [1, 2])
+def test_loss_and_gradient_match_oracle(shape, cin):
+    p = random_params(cin, seed=10 + cin)
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal((cin,) + shape)
+    target = rng.standard_normal(shape)
+    net = tpmg.Network(cin, p)
+    loss, grad = net.loss_grad(channels_last(x), torch.from_numpy(target.astype(np.float32).ravel()).cuda(), shape)
+    loss, grad = float(host(loss)[0]), host(grad)
+    ref_loss, ref_grad = oracle.nn_loss_grad(weights_bf16(p, cin), bf16(x), np.float32(target).astype(np.float64))
+    assert abs(loss - ref_loss) < 2e-2 * ref_loss
+    o = 0
+    for ci, co in ((cin, 16), (16, 16), (16, 16), (16, 1)):
+        for size, what in ((co * ci * 27, "W"), (co, "b")):
+            g, r = grad[o:o + size], ref_grad[o:o + size]
+            assert rel(g, r) < 5e-2, (what, ci, co, rel(g, r))
+            o += size
+    assert o == grad.size
+    net.close()
+
+
+def test_adam_steps_match_oracle():
+    """Three Adam steps on the GPU against the oracle's Adam fed with the GPU's own gradients:
+    only the update rule is compared here (FP32 against FP64, relative 1e-5 of the step)."""
+    cin, shape, lr = 2, (3, 4, 64), 1e-3
+    p = random_params(cin, seed=20)
+    rng = np.random.default_rng(21)
+    x = channels_last(rng.standard_normal((cin,) + shape))
+    target = torch.from_numpy(rng.standard_normal(shape).astype(np.float32).ravel()).cuda()
+    net = tpmg.Network(cin, p)
+    theta = p.astype(np.float64)
+    m, v = np.zeros_like(theta), np.zeros_like(theta)
+    for t in range(1, 4):
+        _, g = net.loss_grad(x, target, shape)
+        oracle.adam_step(theta, host(g), m, v, t, lr=lr)
+        net.train_step(x, target, shape, lr)
+        got = net.get_params().astype(np.float64)
+        assert np.max(np.abs(got - theta)) < 1e-5 * lr * t + 1e-7 * np.max(np.abs(theta))
+    net.close()
+
+
+def test_training_reduces_the_loss():
+    """Fitting a target the network can represent (a smoothed copy of its input) by Adam."""
+    cin, shape = 1, (4, 8, 64)
+    rng = np.random.default_rng(30)
+    xin = rng.standard_normal((cin,) + shape)
+    target = 0.5 * xin[0] + 0.25 * (np.roll(xin[0], 1, axis=2) + np.roll(xin[0], -1, axis=2))
+    x = channels_last(xin)
+    tt = torch.from_numpy(target.astype(np.float32).ravel()).cuda()
+    net = tpmg.Network(cin, random_params(cin, seed=31, scale=0.5))
+    first = float(host(net.train_step(x, tt, shape, 3e-3))[0])
+    for _ in range(200):
+        last = float(host(net.train_step(x, tt, shape, 3e-3))[0])
+    assert last < 0.1 * first, (first, last)
+    net.close()
+
+
+@pytest.mark.parametrize("cin", [1, 2])
+def test_make_pair(cin):
+    shape = (3, 4, 16)
+    n = int(np.prod(shape))
+    rng = np.random.default_rng(40)
+    r, us, uk = (rng.standard_normal(shape) for _ in range(3))
+    aux = rng.uniform(0.5, 2.0, shape[1:])
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()
+    x, target = tpmg.nn_make_pair(shape, cin, d(r), d(us), d(uk),
+                                  aux=d(aux.astype(np.float32)) if cin == 2 else None)
+    rms = np.sqrt(np.sum(r * r) / n)
+    x = host(x).reshape(shape + (cin,))
+    ref0 = bf16(r / rms)
+    # the scaled residual may round differently in its last FP32 bit: allow one BF16 step
+    assert np.all(np.abs(x[..., 0] - ref0) <= 2.0 ** -7 * np.abs(ref0))
+    if cin == 2:
+        assert np.array_equal(x[..., 1], np.broadcast_to(bf16(aux.astype(np.float32)), shape))
+    assert np.allclose(host(target).reshape(shape), (us - uk) / rms, rtol=1e-6, atol=1e-7)
+
+
+def test_shape_and_argument_errors():
+    net = tpmg.Network(1)
+    x = torch.zeros(2 * 4 * 96, dtype=torch.float32, device="cuda")
+    with pytest.raises(tpmg.TpmgError):
+        net.forward(x, (2, 4, 96))  # nx not a multiple of 64
+    with pytest.raises(tpmg.TpmgError):
+        net.forward(torch.zeros(3 * 64, dtype=torch.float32, device="cuda"), (1, 3, 64))  # odd ny
+    with pytest.raises(tpmg.TpmgError):
+        tpmg.Network(3)
+    net.close()
+
+
+def test_params_round_trip_and_zero_default():
+    net = tpmg.Network(2)
+    assert not np.any(net.get_params())
+    p = random_params(2, seed=50)
+    net.set_params(p)
+    assert np.array_equal(net.get_params(), p)
+    net.close()

@@ -8,7 +8,7 @@ import torch
 import torch.nn.functional as F
 
 import oracle
-from helpers import rel, spectral_solve
+from helpers import affine_network, rel, spectral_solve
 
 
 def torch_conv(x, W, b):
@@ -149,25 +149,6 @@ def test_learned_stage_with_zero_network_always_falls_back():
     assert it1 == it2 and np.array_equal(h1, h2)
     # one application before the loop and one after every iteration but the last
     assert used == 0 and rejected == it2
-
-
-def affine_network(cin, alpha, beta):
-    """Parameters of a network computing NN(x) = alpha * x[0] + beta exactly: layer 1 splits channel 0
-    into relu(x) and relu(-x) (centre taps +1 and -1), layers 2 and 3 pass those two channels through
-    (centre taps 1), layer 4 recombines them as alpha * (relu(x) - relu(-x)) + beta."""
-    n1, n2, n4 = 16 * cin * 27, 16 * 16 * 27, 16 * 27
-    p = np.zeros(oracle.nn_nparams(cin))
-    W1 = p[:n1].reshape(16, cin, 27)
-    W1[0, 0, 13], W1[1, 0, 13] = 1.0, -1.0
-    o2 = n1 + 16
-    for o in (o2, o2 + n2 + 16):
-        W = p[o:o + n2].reshape(16, 16, 27)
-        W[0, 0, 13] = W[1, 1, 13] = 1.0
-    o4 = o2 + 2 * (n2 + 16)
-    W4 = p[o4:o4 + n4].reshape(16, 27)
-    W4[0, 13], W4[1, 13] = alpha, -alpha
-    p[o4 + n4] = beta
-    return p
 
 
 def test_affine_network_is_affine():
