@@ -184,6 +184,91 @@ def bench_batched(tpmg, torch):
     return out
 
 
+def nn_flops_per_voxel(cin: int) -> int:
+    """Multiply-adds x 2 of the 4-layer network per voxel: 3x3x3 taps, cin -> 16 -> 16 -> 16 -> 1."""
+    return 2 * 27 * (cin * 16 + 16 * 16 + 16 * 16 + 16)
+
+
+def bench_mixed(tpmg, torch):
+    """Mixed precision on its own workload (1024^2 x 128, lambda^2 = 1e4): FP32 V-cycles inside
+    double-word refinement at 1e-6 and 1e-10, error against a 1e-12 double-word solution."""
+    p = workloads.mixed()
+    op = tpmg.Operator.from_problem(p)
+    f = torch.from_numpy(p.rhs()).cuda()
+    n = p.n
+    ustar = torch.zeros_like(f)
+    tpmg.mg_solve(op.op, tpmg.default_params(prec=tpmg.DW, tol=1e-12, max_iter=100), f, ustar, n)
+    nrm = float(torch.linalg.vector_norm(ustar).item())
+    out = {"workload": p.name}
+    for name, prec, tol in [("dw_1e-6", tpmg.DW, 1e-6), ("mixed_1e-6", tpmg.MIXED, 1e-6),
+                            ("mixed_1e-10", tpmg.MIXED, 1e-10)]:
+        prm = tpmg.default_params(prec=prec, tol=tol, max_iter=100)
+        u = torch.zeros_like(f)
+        ms = []
+        for _ in range(3):
+            u.zero_()
+            r = tpmg.mg_solve(op.op, prm, f, u, n)
+            ms.append(r["ms"])
+        err = float(torch.linalg.vector_norm(u - ustar).item()) / nrm
+        out[name] = {"ms": round(min(ms[1:]), 3), "iters": r["iters"], "rel_res": r["rel_res"],
+                     "rel_err_vs_u_star": err}
+    op.close()
+    return out
+
+
+def bench_learned(tpmg, torch):
+    """The learned stage: pairs from the multigrid solver on 256^2 x 64 crops, Adam on the residual
+    loss, then flexible CG with and without the network on 2048^2 x 64 (h = 1/2048), beside plain
+    double-word multigrid and the mixed solver, all to 1e-6."""
+    from paper_1402_3545_gb300 import learned
+    cfg = learned.TrainConfig(n_problems=8, steps=400)
+    t0 = time.perf_counter()
+    pairs = learned.generate_pairs(cfg)
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    held = learned.generate_pairs(learned.TrainConfig(n_problems=2, seed=1000))
+    net, losses, t_train = learned.train(cfg, pairs)
+    ev = learned.evaluate(net, held, cfg.shape)
+    vox = cfg.nx * cfg.ny * cfg.nz
+    p = workloads.learned_target()
+    x = torch.randn(p.n * cfg.cin, device="cuda", dtype=torch.float32)
+    for _ in range(2):
+        net.forward(x, (p.nz, p.ny, p.nx))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        net.forward(x, (p.nz, p.ny, p.nx))
+    e1.record()
+    torch.cuda.synchronize()
+    t_fwd = e0.elapsed_time(e1) / 3
+    del x
+    fl = nn_flops_per_voxel(cfg.cin)
+    out = {"workload": p.name, "train": {
+        "pairs": len(pairs), "pair_generation_s": round(t_pairs, 2), "steps": cfg.steps, "seconds": round(t_train, 2),
+        "voxels_per_s": round(cfg.steps * vox / t_train, 1), "loss": cfg.loss,
+        "first_loss": round(float(np.mean(losses[:10])), 5), "last_loss": round(float(np.mean(losses[-20:])), 5),
+        "held_out_relative": {k: round(v, 5) for k, v in ev.items()}},
+        "nn_forward": {"ms": round(t_fwd, 3), "flop_per_voxel": fl,
+                       "tflops": round(fl * p.n / (t_fwd * 1e-3) / 1e12, 2)}}
+    r = learned.fcg_compare(p, net, tol=1e-6, reps=2)
+    out.update(r)
+    op = tpmg.Operator.from_problem(p)
+    f = torch.from_numpy(p.rhs()).cuda()
+    for name, prec in [("mg_dw", tpmg.DW), ("mg_mixed", tpmg.MIXED)]:
+        prm = tpmg.default_params(prec=prec, tol=1e-6, max_iter=100)
+        u = torch.zeros_like(f)
+        ms = []
+        for _ in range(2):
+            u.zero_()
+            res = tpmg.mg_solve(op.op, prm, f, u, p.n)
+            ms.append(res["ms"])
+        out[name] = {"ms": round(min(ms), 3), "iters": res["iters"], "rel_res": res["rel_res"]}
+    op.close()
+    net.close()
+    return out
+
+
 def run_reference(args, rank, world):
     p = workloads.mid()
     f = p.rhs()
@@ -326,6 +411,8 @@ def run_ours(args, rank, world, dist):
 
     # batched workload: 64 problems of drawn sizes in one persistent launch vs one solve after another
     variants["batched_64"] = bench_batched(tpmg, torch)
+    variants["mixed_1024x1024x128"] = bench_mixed(tpmg, torch)
+    variants["learned_2048x2048x64"] = bench_learned(tpmg, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -232,17 +232,30 @@ tpmg_status tpmg_nn_loss_grad(tpmg_nn* nn, int nx, int ny, int nz, const float* 
 /* one Adam step on the loss above */
 tpmg_status tpmg_nn_train_step(tpmg_nn* nn, int nx, int ny, int nz, const float* x, const float* target,
                                double lr, double* loss_out, void* stream);
-/* Training pair from an iterate u_k of a solve with exact solution u_star and its residual r
- * (DEVICE doubles, one per cell): x = (r/rms(r) and, if cin == 2, aux per column (DEVICE fp32,
- * ny*nx)) in BF16-rounded fp32, target = (u_star - u_k)/rms(r) (target_out may be NULL, then
- * u_star and u_k may be too). Synchronises `stream`; allocates its scratch (a training utility). */
-tpmg_status tpmg_nn_make_pair(int nx, int ny, int nz, int cin, const double* r, const double* u_star,
-                              const double* u_k, const float* aux, float* x_out, float* target_out,
-                              void* stream);
+/* Residual loss for the operator op (its finest level, FP32 arithmetic; the grid is op's, with the
+ * network's nx % 64 == 0 and ny even rule): with r the input's channel 0, y = NN(x) and D = diag(A),
+ * loss = mean over cells of (r - A D^{-1} y)^2 -- the mean square of the residual that the
+ * correction D^{-1} y leaves, which is what the learned stage's acceptance test compares -- into
+ * the DEVICE double *loss_out, and its parameter gradient (through
+ * dLoss/dy = -2 D^{-1} A (r - A D^{-1} y) / n) into grad_out (DEVICE, nparams floats) if not NULL.
+ * x as in tpmg_nn_forward. */
+tpmg_status tpmg_nn_loss_grad_residual(tpmg_nn* nn, tpmg_op* op, const float* x, double* loss_out, float* grad_out,
+                                       void* stream);
+/* one Adam step on the residual loss */
+tpmg_status tpmg_nn_train_step_residual(tpmg_nn* nn, tpmg_op* op, const float* x, double lr, double* loss_out,
+                                        void* stream);
+/* Training pair from an iterate u_k of a solve on op's finest level with exact solution u_star and
+ * residual r (DEVICE doubles, one per cell): x = (r/rms(r) and, if cin == 2, aux per column (DEVICE
+ * fp32, ny*nx)) in BF16-rounded fp32, target = D (u_star - u_k)/rms(r) with D = diag(A) -- the
+ * error in the network's output unit (target_out may be NULL, then u_star and u_k may be too).
+ * Synchronises `stream`; allocates its scratch (a training utility). */
+tpmg_status tpmg_nn_make_pair(tpmg_op* op, int cin, const double* r, const double* u_star, const double* u_k,
+                              const float* aux, float* x_out, float* target_out, void* stream);
 /* Flexible CG with truncation 1 (Notay's FCG(1)) for A u = f on the finest level, double-word
  * vectors; preconditioner: one FP32 V-cycle z1 of r (the mixed solver's inner cycle, prm's
  * smoothing parameters) and, if nn is not NULL, the learned correction
- * z = z1 + rms(r1) NN(r1/rms(r1)), r1 = r - A z1, kept only when ||r - A z|| < ||r1|| (else z = z1).
+ * z = z1 + rms(r1) D^{-1} NN(r1/rms(r1)), r1 = r - A z1, D = diag(A) (the network answers in units
+ * of a Jacobi step), kept only when ||r - A z|| < ||r1|| (else z = z1).
  * aux: DEVICE fp32 second input channel per column (2-channel networks), else NULL.
  * *nn_accepted (host, may be NULL) receives how many learned corrections were kept. Stops on
  * Eq. (10) like the other solvers; same return values as tpmg_mg_solve. */

@@ -236,6 +236,9 @@ def _nnlib():
             ("orc_conv3d_bwd", [_I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P], None),
             ("orc_nn_forward", [_I, _I, _I, _I, _P, _P, _P, _P], None),
             ("orc_nn_loss_grad", [_I, _I, _I, _I, _P, _P, _P, _P], _D),
+            ("orc_nn_loss_grad_residual", [_I, _I, _I, _I, _D, _D, _P, _P, _P, _P], _D),
+            ("orc_diag_inv", [_I, _I, _I, _D, _D, _P, _P], None),
+            ("orc_fcg_precondition", [_I, _I, _I, _D, _D, _P, ctypes.POINTER(_OrcPrec), _P, _P, _P], None),
             ("orc_adam_step", [ctypes.c_size_t, _P, _P, _P, _P, _I, _D, _D, _D, _D], None),
             ("orc_fcg_solve", [_I, _I, _I, _D, _D, _P, ctypes.POINTER(_OrcPrec), _D, _I, _P, _P, _P, _P], _I),
             ("orc_nn_nparams", [_I], ctypes.c_size_t),
@@ -296,10 +299,46 @@ def nn_loss_grad(params, x, target):
     return loss, g
 
 
+def diag_inv(shape, cx, cy, v):
+    """1 / diag(A) per cell, shape (nz, ny, nx): the unit of the network's output."""
+    nz, ny, nx = shape
+    v = _vcol(v, nx, ny)
+    out = np.empty(shape)
+    _nnlib().orc_diag_inv(nx, ny, nz, cx, cy, _ptr(v), _ptr(out))
+    return out
+
+
+def nn_loss_grad_residual(params, x, cx, cy, v):
+    """Residual loss mean((x[0] - A D^-1 NN(x))^2), D = diag(A), for the operator (cx, cy, v) and
+    its parameter gradient."""
+    params, x = _f64(params), _f64(x)
+    cin, nz, ny, nx = x.shape
+    v = _vcol(v, nx, ny)
+    g = np.empty_like(params)
+    loss = _nnlib().orc_nn_loss_grad_residual(nx, ny, nz, cin, cx, cy, _ptr(v), _ptr(params), _ptr(x), _ptr(g))
+    return loss, g
+
+
 def adam_step(theta, g, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     """In place on theta, m, v (float64 numpy arrays)."""
     g = _f64(g)
     _nnlib().orc_adam_step(theta.size, _ptr(theta), _ptr(g), _ptr(m), _ptr(v), t, lr, beta1, beta2, eps)
+
+
+def fcg_precondition(r, cx, cy, v, mode=1, nlevels=1, params=None, aux=None, nu_pre=2, nu_post=2, n_coarse=2,
+                     rho=0.8):
+    """One application of flexible CG's preconditioner to r: (z, learned candidate, kept)."""
+    r = _f64(r)
+    nz, ny, nx = r.shape
+    v = _vcol(v, nx, ny)
+    z = np.zeros_like(r)
+    cand = np.full_like(r, np.nan)
+    pp = None if params is None else _f64(params)
+    ax = None if aux is None else _f64(np.broadcast_to(np.asarray(aux, dtype=np.float64), (nz, ny, nx)))
+    P = _OrcPrec(mode, nlevels, nu_pre, nu_post, n_coarse, rho, 1 if ax is None else 2,
+                 None if pp is None else pp.ctypes.data, None if ax is None else ax.ctypes.data, 0, 0)
+    _nnlib().orc_fcg_precondition(nx, ny, nz, cx, cy, _ptr(v), ctypes.byref(P), _ptr(r), _ptr(z), _ptr(cand))
+    return z, cand, bool(P.nn_used)
 
 
 def fcg_solve(f, cx, cy, v, mode=1, nlevels=1, tol=1e-6, max_iter=500, params=None, aux=None, u0=None,

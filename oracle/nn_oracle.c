@@ -90,29 +90,18 @@ void orc_nn_forward(int nx, int ny, int nz, int cin, const double *params, const
     if (!acts) free(a1);
 }
 
-/* Loss = mean over cells of (out - target)^2 and its gradient w.r.t. all parameters (grad, nparams
- * doubles, overwritten). Returns the loss. Backpropagation through the four layers. */
-double orc_nn_loss_grad(int nx, int ny, int nz, int cin, const double *params, const double *x,
-                        const double *target, double *grad) {
+/* Backpropagation through the four layers: given the forward activations (acts, as filled by
+ * orc_nn_forward) and d4 = dLoss/dout, the gradient w.r.t. all parameters (grad, overwritten). */
+static void nn_backward(int nx, int ny, int nz, int cin, const double *params, const double *x,
+                        const double *acts, const double *d4, double *grad) {
     size_t n = (size_t)nx * ny * nz;
-    size_t np = nn_nparams(cin);
-    const double *W1 = params, *W2 = W1 + 16 * cin * 27 + 16, *W3 = W2 + 16 * 16 * 27 + 16,
+    const double *W2 = params + 16 * cin * 27 + 16, *W3 = W2 + 16 * 16 * 27 + 16,
                  *W4 = W3 + 16 * 16 * 27 + 16;
     double *gW1 = grad, *gb1 = gW1 + 16 * cin * 27, *gW2 = gb1 + 16, *gb2 = gW2 + 16 * 16 * 27,
            *gW3 = gb2 + 16, *gb3 = gW3 + 16 * 16 * 27, *gW4 = gb3 + 16, *gb4 = gW4 + 16 * 27;
-    memset(grad, 0, sizeof(double) * np);
-    double *acts = (double *)malloc(sizeof(double) * 3 * 16 * n);
-    double *out = (double *)malloc(sizeof(double) * n);
-    orc_nn_forward(nx, ny, nz, cin, params, x, out, acts);
-    double *a1 = acts, *a2 = a1 + 16 * n, *a3 = a2 + 16 * n;
-    double loss = 0.0;
-    double *d4 = (double *)malloc(sizeof(double) * n);
-    for (size_t p = 0; p < n; ++p) {
-        double e = out[p] - target[p];
-        loss += e * e;
-        d4[p] = 2.0 * e / (double)n;
-    }
-    loss /= (double)n;
+    const double *W1 = params;
+    memset(grad, 0, sizeof(double) * nn_nparams(cin));
+    const double *a1 = acts, *a2 = a1 + 16 * n, *a3 = a2 + 16 * n;
     double *d3 = (double *)malloc(sizeof(double) * 16 * n);
     double *d2 = (double *)malloc(sizeof(double) * 16 * n);
     orc_conv3d_bwd(nx, ny, nz, 16, 1, W4, a3, d4, d3, gW4, gb4);
@@ -122,11 +111,83 @@ double orc_nn_loss_grad(int nx, int ny, int nz, int cin, const double *params, c
     orc_conv3d_bwd(nx, ny, nz, 16, 16, W2, a1, d2, d3, gW2, gb2);
     for (size_t p = 0; p < 16 * n; ++p) if (a1[p] <= 0.0) d3[p] = 0.0;
     orc_conv3d_bwd(nx, ny, nz, cin, 16, W1, x, d3, NULL, gW1, gb1);
+    free(d3);
+    free(d2);
+}
+
+/* Loss = mean over cells of (out - target)^2 and its gradient w.r.t. all parameters (grad, nparams
+ * doubles, overwritten). Returns the loss. */
+double orc_nn_loss_grad(int nx, int ny, int nz, int cin, const double *params, const double *x,
+                        const double *target, double *grad) {
+    size_t n = (size_t)nx * ny * nz;
+    double *acts = (double *)malloc(sizeof(double) * 3 * 16 * n);
+    double *out = (double *)malloc(sizeof(double) * n);
+    double *d4 = (double *)malloc(sizeof(double) * n);
+    orc_nn_forward(nx, ny, nz, cin, params, x, out, acts);
+    double loss = 0.0;
+    for (size_t p = 0; p < n; ++p) {
+        double e = out[p] - target[p];
+        loss += e * e;
+        d4[p] = 2.0 * e / (double)n;
+    }
+    loss /= (double)n;
+    nn_backward(nx, ny, nz, cin, params, x, acts, d4, grad);
     free(acts);
     free(out);
     free(d4);
-    free(d3);
-    free(d2);
+    return loss;
+}
+
+void orc_apply_A(int nx, int ny, int nz, double cx, double cy, const double *v, const double *x, double *y);
+
+/* D = diag(A) per cell: 1 + 2cx + 2cy plus v for each vertical neighbour inside the column. The
+ * network's output is measured in units of D^{-1} (a Jacobi step): the learned correction is
+ * s D^{-1} NN(r/s), so NN's targets are O(1) whatever the mesh width and lambda^2. */
+static void diag_inv(int nx, int ny, int nz, double cx, double cy, const double *v, double *dinv) {
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                double vij = v[(size_t)j * nx + i];
+                double d = 1.0 + 2.0 * cx + 2.0 * cy + (k > 0 ? vij : 0.0) + (k < nz - 1 ? vij : 0.0);
+                dinv[((size_t)k * ny + j) * nx + i] = 1.0 / d;
+            }
+}
+
+void orc_diag_inv(int nx, int ny, int nz, double cx, double cy, const double *v, double *dinv) {
+    diag_inv(nx, ny, nz, cx, cy, v, dinv);
+}
+
+/* Residual loss: with r = x[0] (the normalised residual channel), y = NN(x) and D = diag(A),
+ *   loss = mean over cells of (r - A D^{-1} y)^2,
+ * the mean square of the residual left after the correction D^{-1} y; A is the operator with
+ * couplings cx, cy and v (per column). A is symmetric, so dLoss/dy = -2 D^{-1} A (r - A D^{-1} y) / n.
+ * Returns the loss; grad (nparams doubles) is overwritten. */
+double orc_nn_loss_grad_residual(int nx, int ny, int nz, int cin, double cx, double cy, const double *v,
+                                 const double *params, const double *x, double *grad) {
+    size_t n = (size_t)nx * ny * nz;
+    double *acts = (double *)malloc(sizeof(double) * 3 * 16 * n);
+    double *out = (double *)malloc(sizeof(double) * n);
+    double *e = (double *)malloc(sizeof(double) * n);
+    double *d4 = (double *)malloc(sizeof(double) * n);
+    double *dinv = (double *)malloc(sizeof(double) * n);
+    diag_inv(nx, ny, nz, cx, cy, v, dinv);
+    orc_nn_forward(nx, ny, nz, cin, params, x, out, acts);
+    for (size_t p = 0; p < n; ++p) out[p] *= dinv[p];
+    orc_apply_A(nx, ny, nz, cx, cy, v, out, e);
+    double loss = 0.0;
+    for (size_t p = 0; p < n; ++p) {
+        e[p] = x[p] - e[p];
+        loss += e[p] * e[p];
+    }
+    loss /= (double)n;
+    orc_apply_A(nx, ny, nz, cx, cy, v, e, d4);
+    for (size_t p = 0; p < n; ++p) d4[p] *= -2.0 * dinv[p] / (double)n;
+    nn_backward(nx, ny, nz, cin, params, x, acts, d4, grad);
+    free(acts);
+    free(out);
+    free(e);
+    free(d4);
+    free(dinv);
     return loss;
 }
 
@@ -147,7 +208,6 @@ void orc_adam_step(size_t n, double *theta, const double *g, double *m, double *
 /* is z_i A-orthogonalised against the previous direction only, so a preconditioner that changes  */
 /* from one application to the next is allowed.                                                   */
 /* ------------------------------------------------------------------------------------------ */
-void orc_apply_A(int nx, int ny, int nz, double cx, double cy, const double *v, const double *x, double *y);
 void orc_line_solve(int nx, int ny, int nz, double cx, double cy, const double *v, const double *b, double *x);
 int orc_vcycle(int nx, int ny, int nz, int L, double cx, double cy, const double *v, int nu_pre, int nu_post,
                int n_coarse, double rho, const double *f, double *u);
@@ -164,10 +224,11 @@ typedef struct {
 } orc_prec;
 
 /* z = B(r). Mode 2: z1 = V-cycle(r), r1 = r - A z1, s = rms(r1) = ||r1|| / sqrt(n),
- * z = z1 + s NN(r1 / s) (the network sees a residual of unit mean square, whatever the grid size);
- * the learned correction is dropped (z = z1) when ||r - A z|| >= ||r1|| or the result is not finite. */
+ * z = z1 + s D^{-1} NN(r1 / s) with D = diag(A) (the network sees a residual of unit mean square
+ * and answers in units of a Jacobi step, whatever the grid size and coefficients); the learned
+ * correction is dropped (z = z1) when ||r - A z|| >= ||r1|| or the result is not finite. */
 static void fcg_precondition(int nx, int ny, int nz, double cx, double cy, const double *v, orc_prec *P,
-                             const double *r, double *z) {
+                             const double *r, double *z, double *cand) {
     size_t n = (size_t)nx * ny * nz;
     if (P->mode == 0) {
         orc_line_solve(nx, ny, nz, cx, cy, v, r, z);
@@ -180,6 +241,8 @@ static void fcg_precondition(int nx, int ny, int nz, double cx, double cy, const
     double *r1 = (double *)malloc(sizeof(double) * n);
     double *x = (double *)malloc(sizeof(double) * n * (size_t)P->cin);
     double *c = (double *)malloc(sizeof(double) * n);
+    double *dinv = (double *)malloc(sizeof(double) * n);
+    diag_inv(nx, ny, nz, cx, cy, v, dinv);
     orc_apply_A(nx, ny, nz, cx, cy, v, z, Az);
     for (size_t p = 0; p < n; ++p) r1[p] = r[p] - Az[p];
     double nr1 = sqrt(orc_dot(n, r1, r1));
@@ -189,7 +252,7 @@ static void fcg_precondition(int nx, int ny, int nz, double cx, double cy, const
         for (size_t p = 0; p < n; ++p) x[p] = r1[p] / rms;
         if (P->cin > 1) memcpy(x + n, P->aux, sizeof(double) * n);
         orc_nn_forward(nx, ny, nz, P->cin, P->params, x, c, NULL);
-        for (size_t p = 0; p < n; ++p) c[p] = z[p] + rms * c[p];
+        for (size_t p = 0; p < n; ++p) c[p] = z[p] + rms * dinv[p] * c[p];
         orc_apply_A(nx, ny, nz, cx, cy, v, c, Az);
         double s = 0.0;
         for (size_t p = 0; p < n; ++p) {
@@ -198,6 +261,7 @@ static void fcg_precondition(int nx, int ny, int nz, double cx, double cy, const
         }
         s = sqrt(s);
         accept = isfinite(s) && s < nr1;
+        if (cand) memcpy(cand, c, sizeof(double) * n);
         if (accept) memcpy(z, c, sizeof(double) * n);
     }
     P->nn_used += accept;
@@ -206,6 +270,14 @@ static void fcg_precondition(int nx, int ny, int nz, double cx, double cy, const
     free(r1);
     free(x);
     free(c);
+    free(dinv);
+}
+
+/* One application of the preconditioner (test access): z = B(r); cand (may be NULL) receives the
+ * learned candidate z1 + s D^{-1} NN(r1/s) of mode 2 whether or not it was kept. */
+void orc_fcg_precondition(int nx, int ny, int nz, double cx, double cy, const double *v, orc_prec *P,
+                          const double *r, double *z, double *cand) {
+    fcg_precondition(nx, ny, nz, cx, cy, v, P, r, z, cand);
 }
 
 int orc_fcg_solve(int nx, int ny, int nz, double cx, double cy, const double *v, orc_prec *P, double tol,
@@ -222,7 +294,7 @@ int orc_fcg_solve(int nx, int ny, int nz, double cx, double cy, const double *v,
     if (r0 == 0.0) {
         *converged = 1;
     } else {
-        fcg_precondition(nx, ny, nz, cx, cy, v, P, r, z);
+        fcg_precondition(nx, ny, nz, cx, cy, v, P, r, z, NULL);
         memcpy(p, z, sizeof(double) * n);
         orc_apply_A(nx, ny, nz, cx, cy, v, p, q);
         while (it < max_iter) {
@@ -240,7 +312,7 @@ int orc_fcg_solve(int nx, int ny, int nz, double cx, double cy, const double *v,
                 break;
             }
             if (it == max_iter) break;
-            fcg_precondition(nx, ny, nz, cx, cy, v, P, r, z);
+            fcg_precondition(nx, ny, nz, cx, cy, v, P, r, z, NULL);
             double beta = orc_dot(n, z, q) / pq;
             for (size_t s = 0; s < n; ++s) p[s] = z[s] - beta * p[s];
             orc_apply_A(nx, ny, nz, cx, cy, v, p, q);

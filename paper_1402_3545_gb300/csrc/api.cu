@@ -1580,11 +1580,11 @@ struct tpmg_nn {
 static tpmg_status nn_ensure_cap(tpmg_nn* nn, size_t n) {
     NNBufs& b = nn->b;
     if (n <= b.ncap) return TPMG_OK;
-    void* ptrs[] = {b.a1, b.a2, b.a3, b.d1, b.d2, b.x, b.out, b.d4};
+    void* ptrs[] = {b.a1, b.a2, b.a3, b.d1, b.d2, b.x, b.out, b.d4, b.tmp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     b.a1 = b.a2 = b.a3 = b.d1 = b.d2 = b.x = nullptr;
-    b.out = b.d4 = nullptr;
+    b.out = b.d4 = b.tmp = nullptr;
     b.ncap = 0;
     TRY(dalloc((void**)&b.a1, n * 32));
     TRY(dalloc((void**)&b.a2, n * 32));
@@ -1594,6 +1594,7 @@ static tpmg_status nn_ensure_cap(tpmg_nn* nn, size_t n) {
     TRY(dalloc((void**)&b.x, n * 2 * (size_t)b.cin));
     TRY(dalloc((void**)&b.out, n * 4));
     TRY(dalloc((void**)&b.d4, n * 4));
+    TRY(dalloc((void**)&b.tmp, n * 4));
     b.ncap = n;
     return TPMG_OK;
 }
@@ -1646,7 +1647,7 @@ tpmg_status tpmg_nn_destroy(tpmg_nn* nn) {
     cudaDeviceSynchronize();
     NNBufs& b = nn->b;
     void* ptrs[] = {b.params, b.grad, b.adam_m, b.adam_v, b.w1, b.w2f, b.w2b, b.w3f, b.w3b, b.w4,
-                    b.a1,     b.a2,   b.a3,     b.d1,     b.d2, b.x,   b.out, b.d4,  b.part, b.dpart};
+                    b.a1,     b.a2,   b.a3,     b.d1,     b.d2, b.x,   b.out, b.d4,  b.part, b.dpart, b.tmp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete nn;
@@ -1715,6 +1716,46 @@ tpmg_status tpmg_nn_train_step(tpmg_nn* nn, int nx, int ny, int nz, const float*
     return TPMG_OK;
 }
 
+// Residual loss mean((r - A D^{-1} NN(x))^2) on the finest level of op (FP32 operator, D = diag(A)),
+// r = channel 0 of x; its gradient w.r.t. the output is -2 D^{-1} A (r - A D^{-1} NN(x)) / n.
+tpmg_status tpmg_nn_loss_grad_residual(tpmg_nn* nn, tpmg_op* op, const float* x, double* loss_out, float* grad_out,
+                                       void* stream) {
+    if (!nn || !op || !x || !loss_out) return set_err(TPMG_ERR_ARG, "NULL argument");
+    const int L = op->g.L, nx = op->g.nx, ny = op->g.ny, nz = op->g.nz;
+    TRY(nn_check_shape(nx, ny, nz));
+    TRY(prep_unit(op, TPMG_F32));
+    const size_t n = (size_t)nx * ny * nz;
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(nn_ensure_cap(nn, n));
+    if (!nn->weights_ready) nn_refresh(nn, s);
+    TRY(nn_load_input(nn, n, x, s));
+    NNBufs& b = nn->b;
+    const Lv<PolF32> LF = level_view<PolF32>(op, L);
+    const size_t ncol = (size_t)nx * ny;
+    nn_forward(b, nx, ny, nz, b.x, b.out, s);
+    nn_scale_dinv(n, ncol, nz, LF.cx, LF.cy, LF.v, b.out, b.tmp, s);  // D^{-1} y
+    launch_apply_A<PolF32>(LF, b.tmp, b.d4, s);                      // q = A D^{-1} y
+    const int nbl = 2048;
+    nn_res_loss(b.x, b.cin, b.d4, b.tmp, b.dpart, n, nbl, s);  // tmp = -2 (r - q) / n
+    launch_finalize_norm(b.dpart, nbl, FIN_SUM, nullptr, nullptr, loss_out, s);
+    launch_apply_A<PolF32>(LF, b.tmp, b.out, s);                   // A tmp
+    nn_scale_dinv(n, ncol, nz, LF.cx, LF.cy, LF.v, b.out, b.d4, s);  // dLoss/dy = D^{-1} A tmp
+    nn_backward(b, nx, ny, nz, b.x, b.d4, grad_out ? grad_out : b.grad, s);
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_nn_train_step_residual(tpmg_nn* nn, tpmg_op* op, const float* x, double lr, double* loss_out,
+                                        void* stream) {
+    TRY(tpmg_nn_loss_grad_residual(nn, op, x, loss_out, nullptr, stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    NNBufs& b = nn->b;
+    nn_adam(b.nparams, b.params, b.grad, b.adam_m, b.adam_v, (float)lr, ++nn->adam_t, s);
+    nn_refresh(nn, s);
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
 }  // extern "C"
 
 __global__ void k_nn_input_f32(size_t n, int cin, const float* __restrict__ x, __nv_bfloat16* __restrict__ xb) {
@@ -1741,14 +1782,15 @@ __global__ void k_bf16_to_f32(size_t n, const __nv_bfloat16* __restrict__ a, flo
         b[t] = __bfloat162float(a[t]);
 }
 
-extern "C" tpmg_status tpmg_nn_make_pair(int nx, int ny, int nz, int cin, const double* r, const double* u_star,
+extern "C" tpmg_status tpmg_nn_make_pair(tpmg_op* op, int cin, const double* r, const double* u_star,
                                          const double* u_k, const float* aux, float* x_out, float* target_out,
                                          void* stream) {
-    if (nx < 1 || ny < 1 || nz < 1 || (cin != 1 && cin != 2) || !r || !x_out || (cin == 2 && !aux) ||
-        (target_out && (!u_star || !u_k)))
+    if (!op || (cin != 1 && cin != 2) || !r || !x_out || (cin == 2 && !aux) || (target_out && (!u_star || !u_k)))
         return set_err(TPMG_ERR_ARG, "bad arguments");
+    const int L = op->g.L, nx = op->g.nx, ny = op->g.ny, nz = op->g.nz;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = (size_t)nx * ny * nz, ncol = (size_t)nx * ny;
+    const Lv<PolF32> LF = level_view<PolF32>(op, L);
     // scratch: partial sums, their total and the bf16 input (allocated per call: a training tool)
     double* part = nullptr;
     __nv_bfloat16* xb = nullptr;
@@ -1759,7 +1801,7 @@ extern "C" tpmg_status tpmg_nn_make_pair(int nx, int ny, int nz, int cin, const 
     }
     k_sumsq_f64<<<1024, 256, 0, s>>>(n, r, part);
     launch_finalize_norm(part, 1024, FIN_SUM, nullptr, nullptr, part + 1024, s);
-    nn_make_input_f64(n, ncol, cin, r, aux, part + 1024, xb, u_star, u_k, target_out, s);
+    nn_make_input_f64(n, ncol, nz, cin, r, aux, part + 1024, xb, u_star, u_k, LF.cx, LF.cy, LF.v, target_out, s);
     k_bf16_to_f32<<<1024, 256, 0, s>>>(n * cin, xb, x_out);
     note_launch();
     note_launch();
@@ -1831,9 +1873,9 @@ extern "C" tpmg_status tpmg_fcg_solve(tpmg_op* op, tpmg_nn* nn, const float* aux
         // learned stage: r1 = r - A z1; c = z1 + rms(r1) NN(r1 / rms(r1)); keep c if ||r - A c|| < ||r1||
         const int nr = launch_residual<PolDW, PolDW>(LD, z1, r, c, part, nullptr, s);
         fcg_scalar(FCG_R1, part, nr, sc, nullptr, s);
-        nn_make_input_dw(n, ncol, nn->b.cin, c, aux, &sc->r1sq, nn->b.x, s);
+        nn_make_input_dw(n, ncol, nz, nn->b.cin, c, aux, &sc->r1sq, nn->b.x, s);
         nn_forward(nn->b, nx, ny, nz, nn->b.x, nn->b.out, s);
-        fcg_learned(n, sc, z1, nn->b.out, c, s);
+        fcg_learned(n, ncol, nz, op->cx[L], op->cy[L], op->v32[L], sc, z1, nn->b.out, c, s);
         const int nr2 = launch_residual<PolDW, PolDW>(LD, c, r, w, part, nullptr, s);
         fcg_scalar(FCG_DECIDE, part, nr2, sc, nullptr, s);
         fcg_select(n, sc, c, z1, z, s);

@@ -20,7 +20,9 @@ int fcg_update(size_t n, const FcgScalars* sc, float2* u, const float2* p, float
                cudaStream_t s);
 int fcg_dot(size_t n, const float2* a, const float2* b, double* partials, cudaStream_t s);
 void fcg_direction(size_t n, const FcgScalars* sc, const float2* z, float2* p, cudaStream_t s);
-void fcg_learned(size_t n, const FcgScalars* sc, const float2* z1, const float* y, float2* c, cudaStream_t s);
+// c = z1 + rms(r1) D^{-1} y (D = diag(A) from cx, cy and the per-column couplings v32)
+void fcg_learned(size_t n, size_t ncol, int nz, double cx, double cy, const float* v32, const FcgScalars* sc,
+                 const float2* z1, const float* y, float2* c, cudaStream_t s);
 void fcg_select(size_t n, const FcgScalars* sc, const float2* c, const float2* z1, float2* z, cudaStream_t s);
 void fcg_dw_from_f32(size_t n, const float* a, float2* b, cudaStream_t s);
 void fcg_f32_from_dw(size_t n, const float2* a, float* b, cudaStream_t s);

@@ -95,14 +95,21 @@ __global__ void __launch_bounds__(256) k_fcg_direction(size_t n, const FcgScalar
         P::st(p, t, P::sub(P::ld(z, t), P::mul(be, P::ld_plain(p, t))));
 }
 
-// c = z1 + s * y with s = ||r1|| / sqrt(n) (the input normalisation), y the network output (fp32)
-__global__ void __launch_bounds__(256) k_fcg_learned(size_t n, const FcgScalars* sc, const float2* __restrict__ z1,
-                                                     const float* __restrict__ y, float2* __restrict__ c) {
+// c = z1 + s D^{-1} y with s = ||r1|| / sqrt(n) (the input normalisation), D = diag(A) and y the
+// network output (fp32)
+__global__ void __launch_bounds__(256) k_fcg_learned(size_t n, size_t ncol, int nz, float cx2cy2,
+                                                     const float* __restrict__ v32, const FcgScalars* sc,
+                                                     const float2* __restrict__ z1, const float* __restrict__ y,
+                                                     float2* __restrict__ c) {
     typedef PolDW P;
     const double rms = sqrt(sc->r1sq / (double)n);
     const P::R s = P::cst(rms);
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
-        P::st(c, t, P::add(P::ld(z1, t), dw_mul_f(s, __ldg(y + t))));
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t col = t % ncol;
+        const int k = (int)(t / ncol);
+        const float yd = __ldg(y + t) * diag_inv_f32(cx2cy2, __ldg(v32 + col), k, nz);
+        P::st(c, t, P::add(P::ld(z1, t), dw_mul_f(s, yd)));
+    }
 }
 
 // z = keep ? c : z1 (decided on the device by k_fcg_scalar mode FCG_DECIDE)
@@ -252,8 +259,9 @@ void fcg_direction(size_t n, const FcgScalars* sc, const float2* z, float2* p, c
     k_fcg_direction<<<grid_n(n), 256, 0, s>>>(n, sc, z, p);
     note_launch();
 }
-void fcg_learned(size_t n, const FcgScalars* sc, const float2* z1, const float* y, float2* c, cudaStream_t s) {
-    k_fcg_learned<<<grid_n(n), 256, 0, s>>>(n, sc, z1, y, c);
+void fcg_learned(size_t n, size_t ncol, int nz, double cx, double cy, const float* v32, const FcgScalars* sc,
+                 const float2* z1, const float* y, float2* c, cudaStream_t s) {
+    k_fcg_learned<<<grid_n(n), 256, 0, s>>>(n, ncol, nz, (float)(2.0 * cx + 2.0 * cy), v32, sc, z1, y, c);
     note_launch();
 }
 void fcg_select(size_t n, const FcgScalars* sc, const float2* c, const float2* z1, float2* z, cudaStream_t s) {

@@ -416,12 +416,35 @@ __global__ void k_mse(const float* __restrict__ out, const float* __restrict__ t
     if (threadIdx.x == 0) partials[blockIdx.x] = red[0] / (double)n;
 }
 
+// residual loss: e = r - q with r the input's channel 0 and q = A NN(x); tmp = -2 e / n (A tmp is
+// then the loss gradient w.r.t. the output); partial sums of e^2 / n per block
+__global__ void k_res_loss(const __nv_bfloat16* __restrict__ x, int cin, const float* __restrict__ q,
+                           float* __restrict__ tmp, double* __restrict__ partials, size_t n) {
+    double s = 0.0;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+        const float e = __bfloat162float(x[p * cin]) - q[p];
+        tmp[p] = -2.f * e / (float)n;
+        s += (double)e * e;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = red[0] / (double)n;
+}
+
 // network input from a residual: channel 0 = r / rms(r) (rms from *sumsq), channel 1 = aux per
-// column; optional target (ea - eb) / rms(r) (the error of an iterate: exact solution minus iterate)
+// column; optional target D (ea - eb) / rms(r) (the error of an iterate, exact solution minus
+// iterate, in the network's output unit D^{-1}; D from cx2cy2 = 2cx + 2cy and v32 per column)
 template <class SR>
-__global__ void k_make_input(size_t n, size_t ncol, int cin, const SR* __restrict__ r, const float* __restrict__ aux,
-                             const double* __restrict__ sumsq, __nv_bfloat16* __restrict__ x, const double* __restrict__ ea,
-                             const double* __restrict__ eb, float* __restrict__ target) {
+__global__ void k_make_input(size_t n, size_t ncol, int nz, int cin, const SR* __restrict__ r,
+                             const float* __restrict__ aux, const double* __restrict__ sumsq,
+                             __nv_bfloat16* __restrict__ x, const double* __restrict__ ea,
+                             const double* __restrict__ eb, float cx2cy2, const float* __restrict__ v32,
+                             float* __restrict__ target) {
     const double rms = sqrt(*sumsq / (double)n);
     const double inv = rms > 0.0 ? 1.0 / rms : 0.0;
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
@@ -430,8 +453,18 @@ __global__ void k_make_input(size_t n, size_t ncol, int cin, const SR* __restric
         else rv = (double)r[p].x + (double)r[p].y;
         x[p * cin] = __float2bfloat16_rn((float)(rv * inv));
         if (cin > 1) x[p * cin + 1] = __float2bfloat16_rn(aux[p % ncol]);
-        if (target) target[p] = (float)((ea[p] - eb[p]) * inv);
+        if (target) {
+            const float dinv = diag_inv_f32(cx2cy2, v32[p % ncol], (int)(p / ncol), nz);
+            target[p] = (float)((ea[p] - eb[p]) * inv) / dinv;
+        }
     }
+}
+
+// out = D^{-1} in (D = diag(A) of an FP32 level)
+__global__ void k_scale_dinv(size_t n, size_t ncol, int nz, float cx2cy2, const float* __restrict__ v32,
+                             const float* __restrict__ in, float* __restrict__ out) {
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+        out[p] = in[p] * diag_inv_f32(cx2cy2, __ldg(v32 + p % ncol), (int)(p / ncol), nz);
 }
 
 // ================================================================ host launchers
@@ -520,6 +553,12 @@ void nn_mse(const float* out, const float* target, float* d4, double* partials, 
     note_launch();
 }
 
+void nn_res_loss(const __nv_bfloat16* x, int cin, const float* q, float* tmp, double* partials, size_t n, int nblocks,
+                 cudaStream_t s) {
+    k_res_loss<<<nblocks, 256, 0, s>>>(x, cin, q, tmp, partials, n);
+    note_launch();
+}
+
 void nn_adam(int n, float* theta, const float* g, float* m, float* v, float lr, int t, cudaStream_t s) {
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
@@ -527,16 +566,23 @@ void nn_adam(int n, float* theta, const float* g, float* m, float* v, float lr, 
     note_launch();
 }
 
-void nn_make_input_f64(size_t n, size_t ncol, int cin, const double* r, const float* aux, const double* sumsq,
-                       __nv_bfloat16* x, const double* ea, const double* eb, float* target, cudaStream_t s) {
-    k_make_input<double><<<blocks_for(n) < 4096 ? blocks_for(n) : 4096, 256, 0, s>>>(n, ncol, cin, r, aux, sumsq, x, ea,
-                                                                                      eb, target);
+void nn_make_input_f64(size_t n, size_t ncol, int nz, int cin, const double* r, const float* aux, const double* sumsq,
+                       __nv_bfloat16* x, const double* ea, const double* eb, double cx, double cy, const float* v32,
+                       float* target, cudaStream_t s) {
+    k_make_input<double><<<blocks_for(n) < 4096 ? blocks_for(n) : 4096, 256, 0, s>>>(
+        n, ncol, nz, cin, r, aux, sumsq, x, ea, eb, (float)(2.0 * cx + 2.0 * cy), v32, target);
     note_launch();
 }
-void nn_make_input_dw(size_t n, size_t ncol, int cin, const float2* r, const float* aux, const double* sumsq,
+void nn_make_input_dw(size_t n, size_t ncol, int nz, int cin, const float2* r, const float* aux, const double* sumsq,
                       __nv_bfloat16* x, cudaStream_t s) {
-    k_make_input<float2><<<blocks_for(n) < 4096 ? blocks_for(n) : 4096, 256, 0, s>>>(n, ncol, cin, r, aux, sumsq, x,
-                                                                                      nullptr, nullptr, nullptr);
+    k_make_input<float2><<<blocks_for(n) < 4096 ? blocks_for(n) : 4096, 256, 0, s>>>(
+        n, ncol, nz, cin, r, aux, sumsq, x, nullptr, nullptr, 0.f, nullptr, nullptr);
+    note_launch();
+}
+void nn_scale_dinv(size_t n, size_t ncol, int nz, double cx, double cy, const float* v32, const float* in, float* out,
+                   cudaStream_t s) {
+    k_scale_dinv<<<blocks_for(n) < 4096 ? blocks_for(n) : 4096, 256, 0, s>>>(n, ncol, nz, (float)(2.0 * cx + 2.0 * cy),
+                                                                             v32, in, out);
     note_launch();
 }
 

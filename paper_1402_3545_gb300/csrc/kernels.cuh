@@ -208,4 +208,12 @@ void launch_f64_to_f32(size_t n, const double* x, float* y, cudaStream_t s);
 void launch_f32_to_f64(size_t n, const float* x, double* y, cudaStream_t s);
 void launch_coarsen_v_f64(int nxf, int nyf, const double* vf, double* vc, cudaStream_t s);
 
+// 1 / diag(A) at plane k of a column with vertical coupling vc: 1 + 2cx + 2cy plus vc for each
+// vertical neighbour inside the column (Eq. 6's flat-box diagonal with the Neumann ends). The
+// learned stage measures the network's output in these units (a Jacobi step).
+__device__ __forceinline__ float diag_inv_f32(float cx2cy2, float vc, int k, int nz) {
+    const float d = 1.f + cx2cy2 + (k > 0 ? vc : 0.f) + (k < nz - 1 ? vc : 0.f);
+    return 1.f / d;
+}
+
 }  // namespace tpmg

@@ -24,6 +24,7 @@ struct NNBufs {
     __nv_bfloat16* x;             // network input (cin channels)
     float* out;                   // network output
     float* d4;                    // gradient of the output
+    float* tmp;                   // scratch field (residual loss)
     float* part;                  // per-block partial sums of the weight gradients
     double* dpart;                // per-block partial sums of the loss
 };
@@ -36,12 +37,20 @@ void nn_backward(const NNBufs& b, int nx, int ny, int nz, const __nv_bfloat16* x
                  cudaStream_t s);
 int nn_grad_blocks(size_t n);
 void nn_mse(const float* out, const float* target, float* d4, double* partials, size_t n, int nblocks, cudaStream_t s);
+// residual loss: e = x[channel 0] - q (q = A NN(x)), tmp = -2 e / n, partial sums of e^2 / n
+void nn_res_loss(const __nv_bfloat16* x, int cin, const float* q, float* tmp, double* partials, size_t n, int nblocks,
+                 cudaStream_t s);
 void nn_adam(int n, float* theta, const float* g, float* m, float* v, float lr, int t, cudaStream_t s);
 // network input from a residual r (fp64 or double-word), normalised by its root-mean-square
-// (sum of squares in *sumsq); optional training target (ea - eb) / rms
-void nn_make_input_f64(size_t n, size_t ncol, int cin, const double* r, const float* aux, const double* sumsq,
-                       __nv_bfloat16* x, const double* ea, const double* eb, float* target, cudaStream_t s);
-void nn_make_input_dw(size_t n, size_t ncol, int cin, const float2* r, const float* aux, const double* sumsq,
+// (sum of squares in *sumsq); optional training target D (ea - eb) / rms with D = diag(A) of the
+// level (cx, cy, per-column couplings v32)
+void nn_make_input_f64(size_t n, size_t ncol, int nz, int cin, const double* r, const float* aux, const double* sumsq,
+                       __nv_bfloat16* x, const double* ea, const double* eb, double cx, double cy, const float* v32,
+                       float* target, cudaStream_t s);
+void nn_make_input_dw(size_t n, size_t ncol, int nz, int cin, const float2* r, const float* aux, const double* sumsq,
                       __nv_bfloat16* x, cudaStream_t s);
+// out = D^{-1} in
+void nn_scale_dinv(size_t n, size_t ncol, int nz, double cx, double cy, const float* v32, const float* in, float* out,
+                   cudaStream_t s);
 
 }  // namespace tpmg

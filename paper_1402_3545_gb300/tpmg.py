@@ -79,7 +79,9 @@ _SIGNATURES = {
     "tpmg_nn_forward": [_P, _I, _I, _I, _P, _P, _P],
     "tpmg_nn_loss_grad": [_P, _I, _I, _I, _P, _P, _P, _P, _P],
     "tpmg_nn_train_step": [_P, _I, _I, _I, _P, _P, _D, _P, _P],
-    "tpmg_nn_make_pair": [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P],
+    "tpmg_nn_loss_grad_residual": [_P, _P, _P, _P, _P, _P],
+    "tpmg_nn_train_step_residual": [_P, _P, _P, _D, _P, _P],
+    "tpmg_nn_make_pair": [_P, _I, _P, _P, _P, _P, _P, _P, _P],
     "tpmg_fcg_solve": [_P, _P, _P, ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Info), ctypes.POINTER(_I), _P],
     "tpmg_residual_norm_noalloc": [_I, _I, _I, _D, _D, _P, _P, _P, _P, _P, _P],
     "tpmg_noalloc_last_error": [],
@@ -377,6 +379,21 @@ class Network:
                                          lr, loss.data_ptr(), _stream(stream)), "nn_train_step")
         return loss
 
+    def loss_grad_residual(self, op, x, n, stream=None):
+        """Residual loss mean((x0 - A D^-1 NN(x))^2), D = diag(A), on the finest level of the operator
+        handle op (n cells)."""
+        loss = torch.zeros(1, dtype=torch.float64, device=x.device)
+        grad = torch.empty(self.nparams, dtype=torch.float32, device=x.device)
+        _check(load().tpmg_nn_loss_grad_residual(self.h, op, _f32(x, n * self.cin, "x"), loss.data_ptr(),
+                                                 grad.data_ptr(), _stream(stream)), "nn_loss_grad_residual")
+        return loss, grad
+
+    def train_step_residual(self, op, x, n, lr, stream=None):
+        loss = torch.zeros(1, dtype=torch.float64, device=x.device)
+        _check(load().tpmg_nn_train_step_residual(self.h, op, _f32(x, n * self.cin, "x"), lr, loss.data_ptr(),
+                                                  _stream(stream)), "nn_train_step_residual")
+        return loss
+
     def close(self):
         if getattr(self, "h", None):
             load().tpmg_nn_destroy(self.h)
@@ -389,13 +406,14 @@ class Network:
             pass
 
 
-def nn_make_pair(shape, cin, r, u_star=None, u_k=None, aux=None, stream=None):
-    """(x, target) for the network from a residual r and the error u_star - u_k (CUDA float64)."""
+def nn_make_pair(op, shape, cin, r, u_star=None, u_k=None, aux=None, stream=None):
+    """(x, target) for the network from a residual r and the error u_star - u_k (CUDA float64) on the
+    finest level of the operator handle op (of the given (nz, ny, nx) shape)."""
     nz, ny, nx = shape
     n = nx * ny * nz
     x = torch.empty(n * cin, dtype=torch.float32, device=r.device)
     target = torch.empty(n, dtype=torch.float32, device=r.device) if u_star is not None else None
-    _check(load().tpmg_nn_make_pair(nx, ny, nz, cin, _field(r, F64, n, "r"),
+    _check(load().tpmg_nn_make_pair(op, cin, _field(r, F64, n, "r"),
                                     None if u_star is None else _field(u_star, F64, n, "u_star"),
                                     None if u_k is None else _field(u_k, F64, n, "u_k"),
                                     None if aux is None else _f32(aux, nx * ny, "aux"), x.data_ptr(),

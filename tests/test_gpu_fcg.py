@@ -31,13 +31,6 @@ def prob():
     op.close()
 
 
-def alpha_for(cx, cy, v) -> float:
-    """A power of two below 1/lambda_max(A) (Gershgorin: lambda_max <= 1 + 4cx + 4cy + 4 max v),
-    so that r1 -> r1 - alpha A r1 is a contraction and the affine network's correction helps."""
-    lam = 1.0 + 4.0 * cx + 4.0 * cy + 4.0 * float(np.max(v))
-    return 2.0 ** -int(np.ceil(np.log2(lam)))
-
-
 def run_gpu(op, p, f, nn=None, aux=None, tol=TOL, max_iter=200):
     prm = tpmg.default_params(tol=tol, max_iter=max_iter)
     u = torch.zeros(p.nz, p.ny, p.nx, dtype=torch.float64, device="cuda")
@@ -75,14 +68,38 @@ def test_zero_network_is_always_rejected(prob):
     net.close()
 
 
-@pytest.mark.parametrize("cin", [1, 2])
-def test_affine_network_matches_oracle(prob, cin):
-    """With NN(x) = alpha x0 + beta (+ gamma relu(x1)) the learned correction is a damped
-    Richardson step plus a constant; both sides accept it at the same iterations and converge in
-    the same number of iterations (+-1)."""
+@pytest.mark.parametrize("bad", ["nan", "huge"])
+def test_corrupted_network_falls_back(prob, bad):
+    """Corrupted weights (NaN, or 1e30 so that the output overflows) give non-finite or useless
+    corrections; every one is rejected and the iteration is the V-cycle-only one, bit for bit."""
     p, op, (cx, cy, v), f = prob
-    alpha = alpha_for(cx, cy, v)
-    params = affine_network(cin, alpha, 1e-3, gamma=2.0 ** -14 if cin == 2 else 0.0)
+    _, base = run_gpu(op, p, f)
+    params = np.full(tpmg.nn_nparams(1), np.nan if bad == "nan" else 1e30, dtype=np.float32)
+    net = tpmg.Network(1, params)
+    u, res = run_gpu(op, p, f, nn=net)
+    assert res["nn_accepted"] == 0
+    assert res["iters"] == base["iters"] and res["history"] == base["history"]
+    check_solution(u, f, cx, cy, v)
+    net.close()
+
+
+@pytest.fixture(scope="module")
+def prob_small():
+    p = make_problem(64, 32, 16)
+    op = tpmg.Operator.from_problem(p)
+    cx, cy, v = oracle.problem_coefficients(p)
+    f = p.rhs()
+    yield p, op, (cx, cy, v), f
+    op.close()
+
+
+@pytest.mark.parametrize("cin", [1, 2])
+def test_affine_network_matches_oracle(prob_small, cin):
+    """With NN(x) = alpha x0 + beta (+ gamma relu(x1)) the learned correction D^-1 NN is a damped
+    Jacobi step (alpha = 1/8) plus a small constant; both sides accept it and converge in the same
+    number of iterations (+-1)."""
+    p, op, (cx, cy, v), f = prob_small
+    params = affine_network(cin, 0.125, 1e-3, gamma=2.0 ** -14 if cin == 2 else 0.0)
     aux = np.random.default_rng(5).uniform(0.0, 1.0, (p.ny, p.nx))
     net = tpmg.Network(cin, params.astype(np.float32))
     u, res = run_gpu(op, p, f, nn=net,

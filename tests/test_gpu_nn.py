@@ -108,6 +108,26 @@ def test_loss_and_gradient_match_oracle(shape, cin):
     net.close()
 
 
+@pytest.mark.parametrize("cin", [1, 2])
+def test_residual_loss_and_gradient_match_oracle(cin):
+    """mean((x0 - A NN(x))^2) with A the operator's finest level (FP32 on the GPU)."""
+    from gpu_common import make_problem
+    shape = (3, 4, 64)
+    prob = make_problem(shape[2], shape[1], shape[0])
+    op = tpmg.Operator.from_problem(prob, nlevels=1)
+    cx, cy, v = oracle.problem_coefficients(prob)
+    p = random_params(cin, seed=60 + cin, scale=0.3)
+    x = np.random.default_rng(61).standard_normal((cin,) + shape)
+    net = tpmg.Network(cin, p)
+    loss, grad = net.loss_grad_residual(op.op, channels_last(x), prob.n)
+    loss, grad = float(host(loss)[0]), host(grad)
+    ref_loss, ref_grad = oracle.nn_loss_grad_residual(weights_bf16(p, cin), bf16(x), cx, cy, v)
+    assert abs(loss - ref_loss) < 2e-2 * ref_loss, (loss, ref_loss)
+    assert rel(grad, ref_grad) < 5e-2, rel(grad, ref_grad)
+    net.close()
+    op.close()
+
+
 def test_adam_steps_match_oracle():
     """Three Adam steps on the GPU against the oracle's Adam fed with the GPU's own gradients:
     only the update rule is compared here (FP32 against FP64, relative 1e-5 of the step)."""
@@ -146,13 +166,18 @@ def test_training_reduces_the_loss():
 
 @pytest.mark.parametrize("cin", [1, 2])
 def test_make_pair(cin):
+    """x = bf16(r / rms(r)) (and bf16(aux)), target = D (u* - u_k) / rms(r) with D = diag(A)."""
+    from gpu_common import make_problem
     shape = (3, 4, 16)
     n = int(np.prod(shape))
+    prob = make_problem(shape[2], shape[1], shape[0])
+    op = tpmg.Operator.from_problem(prob, nlevels=1)
+    cx, cy, v = oracle.problem_coefficients(prob)
     rng = np.random.default_rng(40)
     r, us, uk = (rng.standard_normal(shape) for _ in range(3))
     aux = rng.uniform(0.5, 2.0, shape[1:])
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a).ravel()).cuda()
-    x, target = tpmg.nn_make_pair(shape, cin, d(r), d(us), d(uk),
+    x, target = tpmg.nn_make_pair(op.op, shape, cin, d(r), d(us), d(uk),
                                   aux=d(aux.astype(np.float32)) if cin == 2 else None)
     rms = np.sqrt(np.sum(r * r) / n)
     x = host(x).reshape(shape + (cin,))
@@ -161,7 +186,9 @@ def test_make_pair(cin):
     assert np.all(np.abs(x[..., 0] - ref0) <= 2.0 ** -7 * np.abs(ref0))
     if cin == 2:
         assert np.array_equal(x[..., 1], np.broadcast_to(bf16(aux.astype(np.float32)), shape))
-    assert np.allclose(host(target).reshape(shape), (us - uk) / rms, rtol=1e-6, atol=1e-7)
+    ref_t = (us - uk) / rms / oracle.diag_inv(shape, cx, cy, v)
+    assert np.allclose(host(target).reshape(shape), ref_t, rtol=1e-6, atol=1e-7 * np.max(np.abs(ref_t)))
+    op.close()
 
 
 def test_shape_and_argument_errors():

@@ -8,7 +8,7 @@ import torch
 import torch.nn.functional as F
 
 import oracle
-from helpers import affine_network, rel, spectral_solve
+from helpers import affine_network, assemble, rel, spectral_solve
 
 
 def torch_conv(x, W, b):
@@ -68,6 +68,43 @@ def test_network_gradient_matches_finite_differences():
         pm[idx] -= h
         num = (oracle.nn_loss_grad(pp, x, target)[0] - oracle.nn_loss_grad(pm, x, target)[0]) / (2 * h)
         assert abs(num - g[idx]) <= 1e-6 * max(1.0, abs(g[idx])) + 1e-9, (idx, num, g[idx])
+
+
+def _operator(nx, ny, seed):
+    rng = np.random.default_rng(seed)
+    return 3.0, 2.0, rng.uniform(5.0, 50.0, (ny, nx))
+
+
+def test_residual_loss_gradient_matches_finite_differences():
+    cin = 2
+    p = _params(cin, 12)
+    x = rnd((cin, 4, 5, 6), 13)
+    cx, cy, v = _operator(6, 5, 14)
+    loss, g = oracle.nn_loss_grad_residual(p, x, cx, cy, v)
+    # the loss is what its definition says, with D taken from the assembled matrix's diagonal
+    shape = x.shape[1:]
+    D = np.diag(assemble(lambda a: oracle.apply_A(a, cx, cy, v), shape)).reshape(shape)
+    assert np.allclose(oracle.diag_inv(shape, cx, cy, v), 1.0 / D, rtol=1e-15, atol=0)
+    y = oracle.nn_forward(p, x) / D
+    assert abs(loss - np.mean((x[0] - oracle.apply_A(y, cx, cy, v)) ** 2)) < 1e-12 * loss
+    rng = np.random.default_rng(15)
+    for idx in rng.choice(p.size, size=25, replace=False):
+        h = 1e-6
+        pp, pm = p.copy(), p.copy()
+        pp[idx] += h
+        pm[idx] -= h
+        num = (oracle.nn_loss_grad_residual(pp, x, cx, cy, v)[0] - oracle.nn_loss_grad_residual(pm, x, cx, cy, v)[0]) / (2 * h)
+        assert abs(num - g[idx]) <= 1e-6 * max(1.0, abs(g[idx])) + 1e-9, (idx, num, g[idx])
+
+
+def test_residual_loss_with_identity_operator_is_the_error_loss():
+    """cx = cy = v = 0 leaves A = D = I: the residual loss is the error loss with target x[0]."""
+    cin = 2
+    p = _params(cin, 16)
+    x = rnd((cin, 3, 4, 5), 17)
+    l1, g1 = oracle.nn_loss_grad_residual(p, x, 0.0, 0.0, np.zeros((4, 5)))
+    l2, g2 = oracle.nn_loss_grad(p, x, x[0])
+    assert abs(l1 - l2) < 1e-14 * l2 and rel(g1, g2) < 1e-13
 
 
 def test_network_forward_and_gradient_match_autograd():
@@ -157,25 +194,38 @@ def test_affine_network_is_affine():
     assert np.allclose(oracle.nn_forward(p, x), 0.3 * x[0] - 0.7, rtol=0, atol=1e-15)
 
 
-@pytest.mark.parametrize("alpha,beta", [(2.0 ** -12, 1e-3), (2.0 ** -12, 50.0)], ids=["accepted", "rejected"])
-def test_learned_stage_first_step_by_hand(alpha, beta):
-    """One FCG step from u = 0 with the affine network, derived here from the V-cycle, the operator
-    and the definitions: z1 = V(f), r1 = f - A z1, s = ||r1|| / sqrt(n), c = z1 + s (alpha r1/s + beta)
-    = z1 + alpha r1 + beta s, kept iff ||f - A c|| < ||r1||; then u1 = (<z, f> / <z, A z>) z.
-    The constant beta s is where the residual normalisation shows: a 2-norm reading instead of the
-    root-mean-square one changes it by sqrt(n)."""
+@pytest.mark.parametrize("alpha,beta", [(0.125, 0.0), (0.5, 1e-3), (0.125, -2e-3)])
+def test_learned_candidate_by_hand(alpha, beta):
+    """The learned candidate of one preconditioner application with the affine network, derived
+    here from the V-cycle, the operator and the definitions: z1 = V(r), r1 = r - A z1,
+    s = ||r1|| / sqrt(n), D = diag(A) read off the assembled matrix,
+    c = z1 + s D^-1 (alpha r1/s + beta) = z1 + alpha D^-1 r1 + beta s D^-1 (a damped Jacobi step plus
+    a constant), kept iff ||r - A c|| < ||r1||. The term beta s D^-1 is where the residual
+    normalisation shows: a 2-norm reading instead of the root-mean-square one changes it by
+    sqrt(n)."""
     f, cx, cy, v = _problem()
     n = f.size
+    D = np.diag(assemble(lambda a: oracle.apply_A(a, cx, cy, v), f.shape)).reshape(f.shape)
     z1 = oracle.vcycle(np.zeros_like(f), f, cx, cy, v, 2)
     r1 = f - oracle.apply_A(z1, cx, cy, v)
     s = np.linalg.norm(r1) / np.sqrt(n)
-    c = z1 + alpha * r1 + beta * s
+    c = z1 + alpha * r1 / D + beta * s / D
     keep = np.linalg.norm(f - oracle.apply_A(c, cx, cy, v)) < np.linalg.norm(r1)
-    assert keep == (beta < 1.0)  # the two cases cover both branches
-    z = c if keep else z1
+    z, cand, kept = oracle.fcg_precondition(f, cx, cy, v, mode=2, nlevels=2, params=affine_network(1, alpha, beta))
+    assert rel(cand, c) < 1e-13
+    assert kept == keep
+    assert rel(z, c if keep else z1) < 1e-13
+
+
+def test_learned_stage_first_step_by_hand():
+    """One FCG step from u = 0: u1 = (<z, f> / <z, A z>) z with z the preconditioner's output
+    (the damped-Jacobi candidate alpha = 1/8, which lowers the residual and is kept)."""
+    f, cx, cy, v = _problem()
+    p = affine_network(1, 0.125, 0.0)
+    z, _, kept = oracle.fcg_precondition(f, cx, cy, v, mode=2, nlevels=2, params=p)
+    assert kept
     u1 = (np.vdot(z, f) / np.vdot(z, oracle.apply_A(z, cx, cy, v))) * z
-    p = affine_network(1, alpha, beta)
     u, it, _, _, used, rejected = oracle.fcg_solve(f, cx, cy, v, mode=2, nlevels=2, tol=1e-300, max_iter=1,
                                                    params=p)
-    assert it == 1 and (used, rejected) == ((1, 0) if keep else (0, 1))
+    assert it == 1 and (used, rejected) == (1, 0)
     assert rel(u, u1) < 1e-12
