@@ -71,6 +71,7 @@ struct tpmg_op {
     float2* vdw[MAXL + 1] = {};
     Hier hier[3];  // by policy id (F64, F32, DW)
     void* finv[3][MAXL + 1] = {};  // Thomas factors 1/m_k per policy and level
+    void* pcr[3][MAXL + 1] = {};   // PCR factors of the small levels per policy and level
     void* fw[3][MAXL + 1] = {};    // Thomas factors v/m_k
     int percol[MAXL + 1] = {};     // 1 if lambda^2 varies over the level (factors per cell)
     double kappa_M[MAXL + 1] = {}; // condition number of the level's column blocks
@@ -119,6 +120,8 @@ static Lv<P> level_view(const tpmg_op* op, int l) {
     L.fw = (const typename P::S*)op->fw[P::id][l];
     L.fac_percol = op->percol[l];
     L.variant = op->variant[P::id][l];
+    L.pcr = (const typename P::S*)op->pcr[P::id][l];
+    L.pcr_steps = pcr_steps_for(op->g.nz);
     return L;
 }
 
@@ -183,6 +186,29 @@ static tpmg_status ensure_factors(tpmg_op* op, int pid) {
             case 0: launch_factors<PolF64>(level_view<PolF64>(op, l), (double*)op->finv[0][l], (double*)op->fw[0][l], op->percol[l], 0); break;
             case 1: launch_factors<PolF32>(level_view<PolF32>(op, l), (float*)op->finv[1][l], (float*)op->fw[1][l], op->percol[l], 0); break;
             default: launch_factors<PolDW>(level_view<PolDW>(op, l), (float2*)op->finv[2][l], (float2*)op->fw[2][l], op->percol[l], 0); break;
+        }
+        // small levels: parallel-cyclic-reduction factors for the cell-parallel kernels
+        if ((size_t)op->g.lnx[l] * op->g.lny[l] <= (size_t)PCR_MAX_COLS && op->g.nz <= 256) {
+            switch (pid) {
+                case 0: {
+                    Lv<PolF64> L = level_view<PolF64>(op, l);
+                    TRY(dalloc(&op->pcr[0][l], pcr_factor_count(L, op->percol[l]) * eb));
+                    launch_pcr_factors<PolF64>(L, (double*)op->pcr[0][l], op->percol[l], 0);
+                    break;
+                }
+                case 1: {
+                    Lv<PolF32> L = level_view<PolF32>(op, l);
+                    TRY(dalloc(&op->pcr[1][l], pcr_factor_count(L, op->percol[l]) * eb));
+                    launch_pcr_factors<PolF32>(L, (float*)op->pcr[1][l], op->percol[l], 0);
+                    break;
+                }
+                default: {
+                    Lv<PolDW> L = level_view<PolDW>(op, l);
+                    TRY(dalloc(&op->pcr[2][l], pcr_factor_count(L, op->percol[l]) * eb));
+                    launch_pcr_factors<PolDW>(L, (float2*)op->pcr[2][l], op->percol[l], 0);
+                    break;
+                }
+            }
         }
     }
     CK(cudaDeviceSynchronize());
@@ -666,6 +692,7 @@ tpmg_status tpmg_destroy_operator(tpmg_op* op) {
         dfree((void*&)op->vdw[l]);
         for (int p = 0; p < 3; ++p) {
             dfree(op->finv[p][l]);
+            dfree(op->pcr[p][l]);
             dfree(op->fw[p][l]);
             dfree(op->hier[p].u[l]);
             dfree(op->hier[p].ub[l]);

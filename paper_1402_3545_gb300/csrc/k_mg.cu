@@ -238,15 +238,6 @@ __global__ void __launch_bounds__(256) k_residual(Lv<P> L, const typename P::S* 
     }
 }
 
-// value of policy PA converted to policy PB's arithmetic (no-op when they coincide)
-template <class PA, class PB>
-struct Conv {
-    __device__ __forceinline__ static typename PB::R f(typename PA::R x) { return PB::cst(PA::to_d(x)); }
-};
-template <class P>
-struct Conv<P, P> {
-    __device__ __forceinline__ static typename P::R f(typename P::R x) { return x; }
-};
 
 // ---------------------------------------------------------------- RestrictSmooth
 // Coarse column (I, J): f_c = 1/4 (sum of the 2x2 fine children of r_f), then the first smoothing
@@ -352,7 +343,11 @@ Shape sweep_shape(int nx, int ny, int nz, int bytes_per_value, bool stack) {
     return sh;
 }
 
-int max_partials(int nx, int ny) { return ((nx + TX - 1) / TX) * ny; }
+int max_partials(int nx, int ny) {
+    const int col_kernels = ((nx + TX - 1) / TX) * ny;
+    const int cell_kernels = nx * ny <= PCR_MAX_COLS ? nx * ny : 0;  // at most one block per column
+    return col_kernels > cell_kernels ? col_kernels : cell_kernels;
+}
 
 template <class K>
 static void allow_smem(K kernel, size_t bytes) {
@@ -368,6 +363,7 @@ void launch_apply_A(const Lv<P>& L, const typename P::S* x, typename P::S* y, cu
 template <class P>
 void launch_line_solve(const Lv<P>& L, const typename P::S* b, typename P::S* x, double scale, const int* done,
                        cudaStream_t s) {
+    if (launch_line_solve_pcr<P>(L, b, x, scale, done, s) >= 0) return;
     if (launch_line_solve_pp<P>(L, b, x, scale, done, s) >= 0) return;
     Shape sh = sweep_shape(L.nx, L.ny, L.nz, sizeof(typename P::R), true);
     allow_smem(k_line_solve<P>, sh.smem);
@@ -377,7 +373,9 @@ void launch_line_solve(const Lv<P>& L, const typename P::S* b, typename P::S* x,
 template <class P>
 int launch_smooth(const Lv<P>& L, double rho, const typename P::S* u, const typename P::S* f,
                    typename P::S* uo, double* partials, const int* done, cudaStream_t s) {
-    const int nparts = launch_smooth_pp<P>(L, rho, u, f, uo, partials, done, s);
+    int nparts = launch_smooth_pcr<P>(L, rho, u, f, uo, partials, done, s);
+    if (nparts >= 0) return nparts;
+    nparts = launch_smooth_pp<P>(L, rho, u, f, uo, partials, done, s);
     if (nparts >= 0) return nparts;
     Shape sh = sweep_shape(L.nx, L.ny, L.nz, sizeof(typename P::R), true);
     allow_smem(k_smooth<P>, sh.smem);
@@ -386,13 +384,16 @@ int launch_smooth(const Lv<P>& L, double rho, const typename P::S* u, const type
     return sh.nblocks();
 }
 int residual_blocks(int nx, int ny, int nz, int bytes_per_value) {
+    if ((size_t)nx * ny <= (size_t)PCR_MAX_COLS) return cell_blocks((size_t)nx * ny * nz);  // pointwise kernel
     if (nx % 32 == 0 && ny % 4 == 0 && nx >= 32) return (nx / 32) * (ny / 4);  // pipelined kernel
     return sweep_shape(nx, ny, nz, bytes_per_value, false).nblocks();
 }
 template <class P, class PO>
 int launch_residual(const Lv<P>& L, const typename P::S* u, const typename P::S* f,
                     typename PO::S* r, double* partials, const int* done, cudaStream_t s) {
-    const int nb = launch_residual_pp<P, PO>(L, u, f, r, partials, done, s);
+    int nb = launch_residual_cell<P, PO>(L, u, f, r, partials, done, s);
+    if (nb >= 0) return nb;
+    nb = launch_residual_pp<P, PO>(L, u, f, r, partials, done, s);
     if (nb >= 0) return nb;
     Shape sh = sweep_shape(L.nx, L.ny, L.nz, sizeof(typename P::R), false);
     k_residual<P, PO><<<sh.grid, sh.block, 0, s>>>(L, u, f, r, partials, done);
@@ -402,6 +403,7 @@ int launch_residual(const Lv<P>& L, const typename P::S* u, const typename P::S*
 template <class PF, class P>
 void launch_restrict_smooth(const Lv<P>& Lc, double rho, const typename PF::S* rf,
                             typename P::S* fc, typename P::S* uc, const int* done, cudaStream_t s) {
+    if (launch_restrict_smooth_pcr<PF, P>(Lc, rho, rf, fc, uc, done, s) >= 0) return;
     // the pipelined kernel copies pairs of fine values: their address must be pair-aligned
     if (((uintptr_t)rf % (2 * sizeof(typename PF::S))) == 0 &&
         launch_restrict_smooth_pp<PF, P>(Lc, rho, rf, fc, uc, done, s) >= 0)
@@ -414,6 +416,7 @@ void launch_restrict_smooth(const Lv<P>& Lc, double rho, const typename PF::S* r
 template <class P, class PF>
 void launch_prolongate(int nxc, int nyc, int nz, const typename P::S* uc, typename PF::S* uf,
                        const int* done, cudaStream_t s) {
+    if (launch_prolongate_cell<P, PF>(nxc, nyc, nz, uc, uf, done, s) >= 0) return;
     Shape sh = sweep_shape(2 * nxc, 2 * nyc, nz, sizeof(typename P::R), false);
     k_prolongate<P, PF><<<sh.grid, sh.block, 0, s>>>(nxc, nyc, nz, uc, uf, done);
     note_launch();

@@ -40,6 +40,30 @@ struct Lv {
     const typename P::S* fw;
     int fac_percol;
     int variant;  // tile variant of the pipelined Smooth chosen by the autotuner (-1: default)
+    // parallel-cyclic-reduction factors of the column blocks (small levels only, else null):
+    // for each of pcr_steps strides 1, 2, 4, ... the two elimination multipliers per cell, then
+    // 1/b of the decoupled rows; per cell when fac_percol, else one shared table of nz rows
+    const typename P::S* pcr = nullptr;
+    int pcr_steps = 0;
+};
+
+// Levels with at most this many columns run the cell-parallel kernels (one thread per cell,
+// the column solve by parallel cyclic reduction): a thread per column leaves the GPU idle there.
+static constexpr int PCR_MAX_COLS = 4096;
+inline int pcr_steps_for(int nz) {
+    int s = 0;
+    while ((1 << s) < nz) ++s;
+    return s;
+}
+
+// value of policy PA converted to policy PB's arithmetic (no-op when they coincide)
+template <class PA, class PB>
+struct Conv {
+    __device__ __forceinline__ static typename PB::R f(typename PA::R x) { return PB::cst(PA::to_d(x)); }
+};
+template <class P>
+struct Conv<P, P> {
+    __device__ __forceinline__ static typename P::R f(typename P::R x) { return x; }
 };
 
 // Device-resident solver scalars (one struct per running solve). All solver control decisions
@@ -89,6 +113,32 @@ int launch_restrict_smooth_pp(const Lv<P>& Lc, double rho, const typename PF::S*
                               typename P::S* uc, const int* done, cudaStream_t s);
 // number of blocks launch_residual uses on an nx x ny level (= partial sums it writes)
 int residual_blocks(int nx, int ny, int nz, int bytes_per_value);
+
+// ---------------------------------------------------------------- launchers (k_coarse.cu)
+// Cell-parallel kernels for levels of at most PCR_MAX_COLS columns; each returns its number of
+// blocks (= partial sums written), or -1 when the level is too large (or has no PCR factors).
+template <class P>
+size_t pcr_factor_count(const Lv<P>& L, int percol);
+template <class P>
+void launch_pcr_factors(const Lv<P>& L, typename P::S* pcr, int percol, cudaStream_t s);
+template <class P>
+int pcr_blocks(const Lv<P>& L);
+template <class P>
+int launch_smooth_pcr(const Lv<P>& L, double rho, const typename P::S* u, const typename P::S* f, typename P::S* uo,
+                      double* partials, const int* done, cudaStream_t s);
+template <class P>
+int launch_line_solve_pcr(const Lv<P>& L, const typename P::S* b, typename P::S* x, double scale, const int* done,
+                          cudaStream_t s);
+template <class PF, class P>
+int launch_restrict_smooth_pcr(const Lv<P>& Lc, double rho, const typename PF::S* rf, typename P::S* fc,
+                               typename P::S* uc, const int* done, cudaStream_t s);
+template <class P, class PO>
+int launch_residual_cell(const Lv<P>& L, const typename P::S* u, const typename P::S* f, typename PO::S* r,
+                         double* partials, const int* done, cudaStream_t s);
+template <class P, class PF>
+int launch_prolongate_cell(int nxc, int nyc, int nz, const typename P::S* uc, typename PF::S* uf, const int* done,
+                           cudaStream_t s);
+int cell_blocks(size_t n);
 
 // ---------------------------------------------------------------- launchers (k_mg.cu)
 template <class P>

@@ -14,7 +14,11 @@ from paper_1402_3545_gb300 import tpmg
 pytestmark = pytest.mark.gpu
 
 # (nx, ny, nz, nlevels): ragged x (not a multiple of 32), ragged y, odd nz, single column height
-SHAPES = [(80, 36, 24, 3), (64, 64, 64, 4), (40, 12, 7, 3), (96, 8, 1, 2), (16, 16, 128, 2)]
+# levels of at most 4096 columns run the cell-parallel kernels (parallel cyclic reduction), larger
+# ones the column kernels (pipelined when nx % 32 == 0): 100 x 50 exercises the plain column
+# kernels on its finest level; nz = 7, 9, 200 are not powers of two; nz = 256 is the largest
+SHAPES = [(80, 36, 24, 3), (64, 64, 64, 4), (40, 12, 7, 3), (96, 8, 1, 2), (16, 16, 128, 2), (100, 50, 9, 2),
+          (16, 4, 200, 2), (8, 8, 256, 2)]
 SHAPE_IDS = [f"{a}x{b}x{c}L{d}" for a, b, c, d in SHAPES]
 
 
