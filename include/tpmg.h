@@ -202,7 +202,7 @@ unsigned long long tpmg_kernel_launches(void);
  * tpmg_set_variant sets one level's choice (e.g. from a saved tuning table). Both invalidate the
  * operator's cached CUDA graphs. Variants change the schedule, not the per-cell arithmetic (only the
  * grouping of the residual norm's partial sums differs). */
-#define TPMG_NUM_VARIANTS 3
+#define TPMG_NUM_VARIANTS 5
 tpmg_status tpmg_autotune(tpmg_op* op, tpmg_precision prec, int reps, int* variants_out, void* stream);
 tpmg_status tpmg_set_variant(tpmg_op* op, tpmg_precision prec, int level, int variant);
 

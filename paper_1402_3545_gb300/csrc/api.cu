@@ -72,6 +72,7 @@ struct tpmg_op {
     Hier hier[3];  // by policy id (F64, F32, DW)
     void* finv[3][MAXL + 1] = {};  // Thomas factors 1/m_k per policy and level
     void* pcr[3][MAXL + 1] = {};   // PCR factors of the small levels per policy and level
+    void* gstack = nullptr;        // Thomas-stack scratch of the persistent sweep variants
     void* fw[3][MAXL + 1] = {};    // Thomas factors v/m_k
     int percol[MAXL + 1] = {};     // 1 if lambda^2 varies over the level (factors per cell)
     double kappa_M[MAXL + 1] = {}; // condition number of the level's column blocks
@@ -121,6 +122,7 @@ static Lv<P> level_view(const tpmg_op* op, int l) {
     L.fac_percol = op->percol[l];
     L.variant = op->variant[P::id][l];
     L.pcr = (const typename P::S*)op->pcr[P::id][l];
+    L.gstack = op->gstack;
     L.pcr_steps = pcr_steps_for(op->g.nz);
     return L;
 }
@@ -177,6 +179,7 @@ static tpmg_status ensure_history(tpmg_op* op, int n) {
 // Thomas factors of every level in precision pid, computed once (they depend on the operator only)
 static tpmg_status ensure_factors(tpmg_op* op, int pid) {
     if (op->fac_ready[pid]) return TPMG_OK;
+    TRY(dalloc(&op->gstack, gstack_bytes(op->g.nz)));
     const size_t eb = elem_bytes(pid);
     for (int l = 1; l <= op->g.L; ++l) {
         size_t nvals = op->percol[l] ? lvl_cells(op, l) : (size_t)op->g.nz;
@@ -707,6 +710,7 @@ tpmg_status tpmg_destroy_operator(tpmg_op* op) {
     dfree(op->fcg_sc);
     if (op->fcg_host) cudaFreeHost(op->fcg_host);
     dfree((void*&)op->partials);
+    dfree(op->gstack);
     dfree((void*&)op->sc);
     dfree((void*&)op->history);
     if (op->sc_host) cudaFreeHost(op->sc_host);

@@ -70,7 +70,14 @@ enum { MODE_SMOOTH = 0, MODE_RESIDUAL = 1, MODE_LINESOLVE = 2 };
 // MODE_SMOOTH:    out = u + coef M^{-1}(f - A u), partial sums of ||f - A u||^2      (Eq. 11)
 // MODE_RESIDUAL:  out = f - A u (stored in PO's precision), partial sums of ||f - A u||^2
 // MODE_LINESOLVE: out = coef M^{-1} u (u is the right-hand side; f unused)            (Eq. 9)
-template <class P, class PO, int TY, int PD, int MODE>
+//
+// GS = false: one tile per block, the forward-eliminated values d'_k on a shared-memory stack
+// (nz values per thread: shared memory, not registers, then limits the SM to a few warps).
+// GS = true: the stack lives in a global scratch of gridDim.x * nz * NT values that the blocks
+// reuse tile after tile (a persistent loop over the tiles with a grid of a few blocks per SM), so
+// the scratch stays resident in L2 and shared memory holds only the rings; d'_k is written with
+// plain stores in the forward sweep and streamed back through the backward ring.
+template <class P, class PO, int TY, int PD, int MODE, bool GS>
 __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, const typename P::S* __restrict__ u,
                                                       const typename P::S* __restrict__ f,
                                                       typename PO::S* __restrict__ out, double* partials,
@@ -93,128 +100,144 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
     S* ringI = ringF + PD * FPL;
     const size_t ring_bytes = ((size_t)PD * (UPL + FPL + IPL) * sizeof(S) + 15) & ~(size_t)15;
     R* stack = reinterpret_cast<R*>(smem_raw + ring_bytes);
+    S* gstack = GS ? reinterpret_cast<S*>(L.gstack) + (size_t)blockIdx.x * nz * NT : nullptr;
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY;
     const size_t pl = (size_t)nx * ny;
-    const size_t c = (size_t)(j0 + ty) * nx + (i0 + tx);
+    const int tiles_x = nx / 32;
+    const int ntiles = GS ? tiles_x * (ny / TY) : 1;
     const S* rhs = (MODE == MODE_LINESOLVE) ? u : f;
-
-    auto issue_plane = [&](int k, int slot) {
-        if (k < nz) {
-            const size_t b = (size_t)k * pl;
-            cp_async<sizeof(S)>(&ringF[slot * FPL + tid], rhs + b + c);
-            if (STACK && percol) cp_async<sizeof(S)>(&ringI[slot * FPL + tid], L.finv + b + c);
-            if (HALO) {
-                S* Us = ringU + slot * UPL;
-                cp_async<sizeof(S)>(&Us[(ty + 1) * 34 + tx + 1], u + b + c);
-                // halo: rows j0-1 and j0+TY (32 each), columns i0-1 and i0+32 (TY+2 each)
-                for (int it = tid; it < 64 + 2 * (TY + 2); it += NT) {
-                    int rr, cc, gj, gi;
-                    if (it < 64) {
-                        rr = (it < 32) ? 0 : TY + 1;
-                        cc = (it & 31) + 1;
-                        gj = (it < 32) ? j0 - 1 : j0 + TY;
-                        gi = i0 + (it & 31);
-                    } else {
-                        const int q = it - 64;
-                        rr = q >> 1;
-                        cc = (q & 1) ? 33 : 0;
-                        gj = j0 - 1 + rr;
-                        gi = (q & 1) ? i0 + 32 : i0 - 1;
-                    }
-                    cp_async<sizeof(S)>(&Us[rr * 34 + cc], u + b + (size_t)wrap_p(gj, ny) * nx + wrap_p(gi, nx));
-                }
-            }
-        }
-        cp_commit();
-    };
-
-    for (int s = 0; s < PD; ++s) issue_plane(s, s);
-
-    const R vv = P::ld(L.v, c);
-    const R cx = P::cst(L.cx), cy = P::cst(L.cy);
-    const R dh = P::cst(1.0 + 2.0 * L.cx + 2.0 * L.cy);
-    const R dh1 = P::add(dh, vv), dh2 = P::add(dh1, vv);
+    const R vzero = P::zero();
     typename P::Acc acc = 0, cmp = 0;
-    R um = P::zero(), uc = P::zero(), d_prev = P::zero();
-    int slot = 0;
-    const int ctr = (ty + 1) * 34 + tx + 1;
-    for (int k = 0; k < nz; ++k) {
-        const int nslot = (slot + 1 == PD) ? 0 : slot + 1;
-        R r;
-        if constexpr (HALO) {
-            cp_wait<PD - 2>();  // planes k and k+1 (the upper neighbour) have landed
-            __syncthreads();    // ... including the halo values other threads fetched
-            const S* Us = ringU + slot * UPL;
-            if (k == 0) uc = P::ld_plain(Us, ctr);
-            const R up = (k + 1 < nz) ? P::ld_plain(ringU + nslot * UPL, ctr) : P::zero();
-            const R hx = P::add(P::ld_plain(Us, ctr - 1), P::ld_plain(Us, ctr + 1));
-            const R hy = P::add(P::ld_plain(Us, ctr - 34), P::ld_plain(Us, ctr + 34));
-            const R diag = (nz == 1) ? dh : ((k == 0 || k == nz - 1) ? dh1 : dh2);
-            R au = P::mul(diag, uc);
-            au = P::sub(au, P::mul(cx, hx));
-            au = P::sub(au, P::mul(cy, hy));
-            au = P::sub(au, P::mul(vv, P::add(um, up)));
-            r = P::sub(P::ld_plain(ringF, slot * FPL + tid), au);
-            P::acc_dot(acc, cmp, r, r);
-            um = uc;
-            uc = up;
-        } else {
-            cp_wait<PD - 1>();  // only this thread's own copies are read: no barrier needed
-            r = P::ld_plain(ringF, slot * FPL + tid);
-        }
-        if constexpr (MODE == MODE_RESIDUAL) {
-            const size_t id = (size_t)k * pl + c;
-            if constexpr (std::is_same<P, PO>::value)
-                P::st(out, id, r);
-            else
-                PO::st(out, id, PO::from_f(P::to_f(r)));
-        }
-        if constexpr (STACK) {
-            const R inv = percol ? P::ld_plain(ringI, slot * FPL + tid) : P::ld(L.finv, k);
-            const R d = P::mul(P::add(r, P::mul(vv, d_prev)), inv);
-            stack[(size_t)k * NT + tid] = d;
-            d_prev = d;
-        }
-        if constexpr (HALO) __syncthreads();  // the slot is reused by the next issue
-        issue_plane(k + PD, slot);
-        slot = nslot;
-    }
-    cp_wait<0>();
 
-    if constexpr (STACK) {
-        __syncthreads();  // the backward ring reuses the forward ring's shared memory
-        // back substitution, streaming u_k (Smooth) and v/m_k through the ring in reverse order
-        constexpr bool NEED_U = MODE == MODE_SMOOTH;
-        S* bU = reinterpret_cast<S*>(smem_raw);
-        S* bW = bU + (NEED_U ? PD * NT : 0);
-        auto issue_back = [&](int k, int s2) {
-            if (k >= 0) {
-                const size_t id = (size_t)k * pl + c;
-                if (NEED_U) cp_async<sizeof(S)>(&bU[s2 * NT + tid], u + id);
-                if (percol) cp_async<sizeof(S)>(&bW[s2 * NT + tid], L.fw + id);
+    for (int tile = GS ? blockIdx.x : 0; tile < ntiles; tile += GS ? gridDim.x : 1) {
+        const int i0 = GS ? (tile % tiles_x) * 32 : blockIdx.x * 32;
+        const int j0 = GS ? (tile / tiles_x) * TY : blockIdx.y * TY;
+        const size_t c = (size_t)(j0 + ty) * nx + (i0 + tx);
+        if (GS) __syncthreads();  // the previous tile's backward ring is no longer read
+
+        auto issue_plane = [&](int k, int slot) {
+            if (k < nz) {
+                const size_t b = (size_t)k * pl;
+                cp_async<sizeof(S)>(&ringF[slot * FPL + tid], rhs + b + c);
+                if (STACK && percol) cp_async<sizeof(S)>(&ringI[slot * FPL + tid], L.finv + b + c);
+                if (HALO) {
+                    S* Us = ringU + slot * UPL;
+                    cp_async<sizeof(S)>(&Us[(ty + 1) * 34 + tx + 1], u + b + c);
+                    // halo: rows j0-1 and j0+TY (32 each), columns i0-1 and i0+32 (TY+2 each)
+                    for (int it = tid; it < 64 + 2 * (TY + 2); it += NT) {
+                        int rr, cc, gj, gi;
+                        if (it < 64) {
+                            rr = (it < 32) ? 0 : TY + 1;
+                            cc = (it & 31) + 1;
+                            gj = (it < 32) ? j0 - 1 : j0 + TY;
+                            gi = i0 + (it & 31);
+                        } else {
+                            const int q = it - 64;
+                            rr = q >> 1;
+                            cc = (q & 1) ? 33 : 0;
+                            gj = j0 - 1 + rr;
+                            gi = (q & 1) ? i0 + 32 : i0 - 1;
+                        }
+                        cp_async<sizeof(S)>(&Us[rr * 34 + cc], u + b + (size_t)wrap_p(gj, ny) * nx + wrap_p(gi, nx));
+                    }
+                }
             }
             cp_commit();
         };
-        for (int s = 0; s < PD; ++s) issue_back(nz - 1 - s, s);
-        const R cf = P::cst(coef);
-        const bool scaled = coef != 1.0;
-        R xn = P::zero();
-        slot = 0;
-        for (int k = nz - 1; k >= 0; --k) {
-            cp_wait<PD - 1>();
-            const R w = percol ? P::ld_plain(bW, slot * NT + tid) : P::ld(L.fw, k);
-            xn = P::add(stack[(size_t)k * NT + tid], P::mul(w, xn));
-            const size_t id = (size_t)k * pl + c;
-            if constexpr (MODE == MODE_SMOOTH)
-                P::st(reinterpret_cast<S*>(out), id, P::add(P::ld_plain(bU, slot * NT + tid), P::mul(cf, xn)));
-            else
-                P::st(reinterpret_cast<S*>(out), id, scaled ? P::mul(cf, xn) : xn);
-            issue_back(k - PD, slot);
-            slot = (slot + 1 == PD) ? 0 : slot + 1;
+
+        for (int s = 0; s < PD; ++s) issue_plane(s, s);
+
+        const R vv = P::ld(L.v, c);
+        const R cx = P::cst(L.cx), cy = P::cst(L.cy);
+        const R dh = P::cst(1.0 + 2.0 * L.cx + 2.0 * L.cy);
+        const R dh1 = P::add(dh, vv), dh2 = P::add(dh1, vv);
+        R um = vzero, uc = vzero, d_prev = vzero;
+        int slot = 0;
+        const int ctr = (ty + 1) * 34 + tx + 1;
+        for (int k = 0; k < nz; ++k) {
+            const int nslot = (slot + 1 == PD) ? 0 : slot + 1;
+            R r;
+            if constexpr (HALO) {
+                cp_wait<PD - 2>();  // planes k and k+1 (the upper neighbour) have landed
+                __syncthreads();    // ... including the halo values other threads fetched
+                const S* Us = ringU + slot * UPL;
+                if (k == 0) uc = P::ld_plain(Us, ctr);
+                const R up = (k + 1 < nz) ? P::ld_plain(ringU + nslot * UPL, ctr) : vzero;
+                const R hx = P::add(P::ld_plain(Us, ctr - 1), P::ld_plain(Us, ctr + 1));
+                const R hy = P::add(P::ld_plain(Us, ctr - 34), P::ld_plain(Us, ctr + 34));
+                const R diag = (nz == 1) ? dh : ((k == 0 || k == nz - 1) ? dh1 : dh2);
+                R au = P::mul(diag, uc);
+                au = P::sub(au, P::mul(cx, hx));
+                au = P::sub(au, P::mul(cy, hy));
+                au = P::sub(au, P::mul(vv, P::add(um, up)));
+                r = P::sub(P::ld_plain(ringF, slot * FPL + tid), au);
+                P::acc_dot(acc, cmp, r, r);
+                um = uc;
+                uc = up;
+            } else {
+                cp_wait<PD - 1>();  // only this thread's own copies are read: no barrier needed
+                r = P::ld_plain(ringF, slot * FPL + tid);
+            }
+            if constexpr (MODE == MODE_RESIDUAL) {
+                const size_t id = (size_t)k * pl + c;
+                if constexpr (std::is_same<P, PO>::value)
+                    P::st(out, id, r);
+                else
+                    PO::st(out, id, PO::from_f(P::to_f(r)));
+            }
+            if constexpr (STACK) {
+                const R inv = percol ? P::ld_plain(ringI, slot * FPL + tid) : P::ld(L.finv, k);
+                const R d = P::mul(P::add(r, P::mul(vv, d_prev)), inv);
+                if constexpr (GS)
+                    P::st(gstack, (size_t)k * NT + tid, d);
+                else
+                    stack[(size_t)k * NT + tid] = d;
+                d_prev = d;
+            }
+            if constexpr (HALO) __syncthreads();  // the slot is reused by the next issue
+            issue_plane(k + PD, slot);
+            slot = nslot;
         }
         cp_wait<0>();
+
+        if constexpr (STACK) {
+            __syncthreads();  // the backward ring reuses the forward ring's shared memory
+            // back substitution, streaming u_k (Smooth), v/m_k and (GS) d'_k through the ring in
+            // reverse order; every thread reads only its own copies
+            constexpr bool NEED_U = MODE == MODE_SMOOTH;
+            S* bU = reinterpret_cast<S*>(smem_raw);
+            S* bW = bU + (NEED_U ? PD * NT : 0);
+            S* bD = bW + PD * NT;
+            auto issue_back = [&](int k, int s2) {
+                if (k >= 0) {
+                    const size_t id = (size_t)k * pl + c;
+                    if (NEED_U) cp_async<sizeof(S)>(&bU[s2 * NT + tid], u + id);
+                    if (percol) cp_async<sizeof(S)>(&bW[s2 * NT + tid], L.fw + id);
+                    if (GS) cp_async<sizeof(S)>(&bD[s2 * NT + tid], gstack + (size_t)k * NT + tid);
+                }
+                cp_commit();
+            };
+            for (int s = 0; s < PD; ++s) issue_back(nz - 1 - s, s);
+            const R cf = P::cst(coef);
+            const bool scaled = coef != 1.0;
+            R xn = vzero;
+            slot = 0;
+            for (int k = nz - 1; k >= 0; --k) {
+                cp_wait<PD - 1>();
+                const R w = percol ? P::ld_plain(bW, slot * NT + tid) : P::ld(L.fw, k);
+                const R dk = GS ? P::ld_plain(bD, slot * NT + tid) : stack[(size_t)k * NT + tid];
+                xn = P::add(dk, P::mul(w, xn));
+                const size_t id = (size_t)k * pl + c;
+                if constexpr (MODE == MODE_SMOOTH)
+                    P::st(reinterpret_cast<S*>(out), id, P::add(P::ld_plain(bU, slot * NT + tid), P::mul(cf, xn)));
+                else
+                    P::st(reinterpret_cast<S*>(out), id, scaled ? P::mul(cf, xn) : xn);
+                issue_back(k - PD, slot);
+                slot = (slot + 1 == PD) ? 0 : slot + 1;
+            }
+            cp_wait<0>();
+        }
     }
     if (MODE != MODE_LINESOLVE && partials) {
         double sm = block_sum(P::acc_get(acc, cmp));
@@ -222,14 +245,16 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
     }
 }
 
-template <class P, int TY, int PD, int MODE>
+template <class P, int TY, int PD, int MODE, bool GS = false>
 static size_t sweep_pp_smem(int nz) {
     typedef typename P::S S;
     const int UPL = MODE != MODE_LINESOLVE ? (TY + 2) * 34 : 0;
     const int IPL = MODE != MODE_RESIDUAL ? 32 * TY : 0;
     const size_t ring = ((size_t)PD * (UPL + 32 * TY + IPL) * sizeof(S) + 15) & ~(size_t)15;
-    const size_t stack = MODE != MODE_RESIDUAL ? (size_t)nz * 32 * TY * sizeof(typename P::R) : 0;
-    return ring + stack;
+    const size_t stack = (MODE != MODE_RESIDUAL && !GS) ? (size_t)nz * 32 * TY * sizeof(typename P::R) : 0;
+    // the backward ring (u, v/m and, GS, d') reuses the forward ring: take the larger
+    const size_t back = (size_t)PD * 32 * TY * sizeof(S) * 3;
+    return (GS && back > ring ? back : ring) + stack;
 }
 
 template <class P, int TY, bool FACTORS = true>
@@ -237,21 +262,49 @@ static bool pp_fits(const Lv<P>& L) {
     return L.nx % 32 == 0 && L.ny % TY == 0 && L.nx >= 32 && (!FACTORS || (L.finv && L.fw));
 }
 
-template <class P, class PO, int TY, int PD, int MODE>
+static int g_num_sms = 0;
+static int num_sms() {
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+size_t gstack_bytes(int nz) { return (size_t)num_sms() * GS_BLOCKS_PER_SM * GS_MAX_NT * nz * 8; }
+
+template <class P, class PO, int TY, int PD, int MODE, bool GS = false>
 static int run_sweep_pp(const Lv<P>& L, double coef, const typename P::S* u, const typename P::S* f,
-                        typename PO::S* out, double* partials, const int* done, cudaStream_t s) {
-    const size_t smem = sweep_pp_smem<P, TY, PD, MODE>(L.nz);
-    auto kern = k_sweep_pp<P, PO, TY, PD, MODE>;
+                        typename PO::S* out, double* partials, const int* done, cudaStream_t s,
+                        int cap = GS_BLOCKS_PER_SM) {
+    static_assert(!GS || 32 * TY <= GS_MAX_NT, "persistent variants own GS_MAX_NT-thread stack slots");
+    const size_t smem = sweep_pp_smem<P, TY, PD, MODE, GS>(L.nz);
+    auto kern = k_sweep_pp<P, PO, TY, PD, MODE, GS>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grd(L.nx / 32, L.ny / TY), blk(32, TY);
+    if (GS) {
+        // persistent: at most GS_BLOCKS_PER_SM resident blocks per SM, each owning a stack slot
+        const int ntiles = (L.nx / 32) * (L.ny / TY);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * TY, smem);
+        if (cap > GS_BLOCKS_PER_SM) cap = GS_BLOCKS_PER_SM;
+        if (per_sm > cap) per_sm = cap;
+        if (per_sm < 1) per_sm = 1;
+        int nb = num_sms() * per_sm;
+        if (nb > ntiles) nb = ntiles;
+        grd = dim3(nb, 1);
+    }
     kern<<<grd, blk, smem, s>>>(L, coef, u, f, out, partials, done);
     note_launch();
     return (int)(grd.x * grd.y);
 }
 
 // ---------------------------------------------------------------- tile variants
-// Smooth: three (TY, PD) variants per precision; the autotuner (tpmg_autotune) times them per
-// level and stores its choice in Lv::variant. Without a choice, variant 0 is used.
+// Smooth: five variants per precision -- three (TY, PD) tile shapes with the shared-memory stack
+// and two persistent ones with the stack in global scratch; the autotuner (tpmg_autotune) times
+// them per level and stores its choice in Lv::variant. Without a choice, variant 0 is used.
 template <class P>
 struct SmoothVariants;
 template <>
@@ -270,15 +323,23 @@ struct SmoothVariants<PolDW> {
 template <class P>
 static int smooth_dispatch(const Lv<P>& L, double rho, const typename P::S* u, const typename P::S* f,
                            typename P::S* uo, double* partials, const int* done, cudaStream_t s) {
-    const int v = (L.variant >= 0 && L.variant < 3) ? L.variant : 0;
+    const int v = (L.variant >= 0 && L.variant < 5) ? L.variant : 0;
     if (P::id == 1) {  // FP32
         if (v == 0 && pp_fits<P, 2>(L)) return run_sweep_pp<P, P, 2, 8, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s);
         if (v == 1 && pp_fits<P, 4>(L)) return run_sweep_pp<P, P, 4, 6, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s);
         if (v == 2 && pp_fits<P, 1>(L)) return run_sweep_pp<P, P, 1, 8, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s);
+        if (L.gstack && v == 3 && pp_fits<P, 2>(L))
+            return run_sweep_pp<P, P, 2, 8, MODE_SMOOTH, true>(L, rho, u, f, uo, partials, done, s, 8);
+        if (L.gstack && v == 4 && pp_fits<P, 2>(L))
+            return run_sweep_pp<P, P, 2, 8, MODE_SMOOTH, true>(L, rho, u, f, uo, partials, done, s, 16);
         if (pp_fits<P, 2>(L)) return run_sweep_pp<P, P, 2, 8, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s);
     } else {  // 8-byte values
         if (v == 1 && pp_fits<P, 2>(L)) return run_sweep_pp<P, P, 2, 4, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s);
         if (v == 2 && pp_fits<P, 2>(L)) return run_sweep_pp<P, P, 2, 6, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s);
+        if (L.gstack && v == 3 && pp_fits<P, 2>(L))
+            return run_sweep_pp<P, P, 2, 4, MODE_SMOOTH, true>(L, rho, u, f, uo, partials, done, s, 8);
+        if (L.gstack && v == 4 && pp_fits<P, 2>(L))
+            return run_sweep_pp<P, P, 2, 4, MODE_SMOOTH, true>(L, rho, u, f, uo, partials, done, s, 16);
         if (pp_fits<P, 1>(L)) return run_sweep_pp<P, P, 1, 6, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s);
     }
     return -1;

@@ -45,7 +45,16 @@ struct Lv {
     // 1/b of the decoupled rows; per cell when fac_percol, else one shared table of nz rows
     const typename P::S* pcr = nullptr;
     int pcr_steps = 0;
+    // global scratch for the Thomas stacks of the persistent sweep variants (gstack_bytes(nz)
+    // bytes, shared by the levels; null: those variants are not used)
+    void* gstack = nullptr;
 };
+
+// persistent sweep variants: at most GS_BLOCKS_PER_SM blocks per SM, each of at most GS_MAX_NT
+// threads, own a stack slot of the scratch
+static constexpr int GS_BLOCKS_PER_SM = 16;
+static constexpr int GS_MAX_NT = 64;
+size_t gstack_bytes(int nz);
 
 // Levels with at most this many columns run the cell-parallel kernels (one thread per cell,
 // the column solve by parallel cyclic reduction): a thread per column leaves the GPU idle there.
