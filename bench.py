@@ -45,6 +45,11 @@ def parse_args():
     ap.add_argument("--solve-only", action="store_true",
                     help="time the solves only (no kernel timing, e2e, variants or CPU baseline): "
                          "the command the ncu launch-list profile runs")
+    ap.add_argument("--kernel-only", choices=["smooth", "residual", "restrict_smooth", "prolongate"],
+                    help="launch only this finest-level kernel a few times (tile variant --variant, "
+                         "no autotuning): the command a per-kernel ncu capture runs")
+    ap.add_argument("--variant", type=int, default=3)
+    ap.add_argument("--precision", choices=["dw", "f32", "f64"], default="dw")
     return ap.parse_args()
 
 
@@ -296,6 +301,25 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_kernel_only(args):
+    """A few launches of one finest-level kernel of the mid problem, for a profiler capture."""
+    import torch
+    from paper_1402_3545_gb300 import tpmg
+    prec = {"dw": tpmg.DW, "f32": tpmg.F32, "f64": tpmg.F64}[args.precision]
+    kid = {"smooth": tpmg.K_SMOOTH, "residual": tpmg.K_RESIDUAL, "restrict_smooth": tpmg.K_RESTRICT_SMOOTH,
+           "prolongate": tpmg.K_PROLONGATE}[args.kernel_only]
+    p = workloads.mid()
+    op = tpmg.Operator.from_problem(p)
+    tpmg.op_reserve(op.op, tpmg.MIXED if prec == tpmg.F32 else prec)
+    for l in range(1, op.L + 1):
+        tpmg.set_variant(op.op, prec, l, args.variant)
+    ms = tpmg.time_kernel(op.op, prec, kid, reps=max(args.steps, 1))
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel": args.kernel_only, "precision": args.precision, "variant": args.variant,
+                      "workload": p.name, "ms_per_launch": round(ms, 4)}), flush=True)
+    op.close()
+
+
 def run_ours(args, rank, world, dist):
     import torch
     from paper_1402_3545_gb300 import tpmg
@@ -446,6 +470,9 @@ def main():
     dist = None
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.kernel_only:
+        run_kernel_only(args)
         return
     if world > 1:
         import torch

@@ -116,6 +116,35 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
         const size_t c = (size_t)(j0 + ty) * nx + (i0 + tx);
         if (GS) __syncthreads();  // the previous tile's backward ring is no longer read
 
+        // halo of the u plane: rows j0-1 and j0+TY (32 each), columns i0-1 and i0+32 (TY+2 each);
+        // thread tid fetches items tid, tid + NT, ...: their ring offsets and in-plane sources are
+        // the same for every plane, so they are computed once per tile
+        constexpr int NHALO = 64 + 2 * (TY + 2);
+        constexpr int HPT = (NHALO + NT - 1) / NT;
+        int h_dst[HPT];
+        size_t h_src[HPT];
+        if constexpr (HALO) {
+#pragma unroll
+            for (int q = 0; q < HPT; ++q) {
+                const int it = tid + q * NT;
+                int rr = 0, cc = 0, gj = j0, gi = i0;
+                if (it < 64) {
+                    rr = (it < 32) ? 0 : TY + 1;
+                    cc = (it & 31) + 1;
+                    gj = (it < 32) ? j0 - 1 : j0 + TY;
+                    gi = i0 + (it & 31);
+                } else if (it < NHALO) {
+                    const int e = it - 64;
+                    rr = e >> 1;
+                    cc = (e & 1) ? 33 : 0;
+                    gj = j0 - 1 + rr;
+                    gi = (e & 1) ? i0 + 32 : i0 - 1;
+                }
+                h_dst[q] = it < NHALO ? rr * 34 + cc : -1;
+                h_src[q] = (size_t)wrap_p(gj, ny) * nx + wrap_p(gi, nx);
+            }
+        }
+
         auto issue_plane = [&](int k, int slot) {
             if (k < nz) {
                 const size_t b = (size_t)k * pl;
@@ -124,23 +153,9 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
                 if (HALO) {
                     S* Us = ringU + slot * UPL;
                     cp_async<sizeof(S)>(&Us[(ty + 1) * 34 + tx + 1], u + b + c);
-                    // halo: rows j0-1 and j0+TY (32 each), columns i0-1 and i0+32 (TY+2 each)
-                    for (int it = tid; it < 64 + 2 * (TY + 2); it += NT) {
-                        int rr, cc, gj, gi;
-                        if (it < 64) {
-                            rr = (it < 32) ? 0 : TY + 1;
-                            cc = (it & 31) + 1;
-                            gj = (it < 32) ? j0 - 1 : j0 + TY;
-                            gi = i0 + (it & 31);
-                        } else {
-                            const int q = it - 64;
-                            rr = q >> 1;
-                            cc = (q & 1) ? 33 : 0;
-                            gj = j0 - 1 + rr;
-                            gi = (q & 1) ? i0 + 32 : i0 - 1;
-                        }
-                        cp_async<sizeof(S)>(&Us[rr * 34 + cc], u + b + (size_t)wrap_p(gj, ny) * nx + wrap_p(gi, nx));
-                    }
+#pragma unroll
+                    for (int q = 0; q < HPT; ++q)
+                        if (h_dst[q] >= 0) cp_async<sizeof(S)>(&Us[h_dst[q]], u + b + h_src[q]);
                 }
             }
             cp_commit();
@@ -152,6 +167,8 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
         const R cx = P::cst(L.cx), cy = P::cst(L.cy);
         const R dh = P::cst(1.0 + 2.0 * L.cx + 2.0 * L.cy);
         const R dh1 = P::add(dh, vv), dh2 = P::add(dh1, vv);
+        const bool iso = L.cx == L.cy;  // square cells: one product for the four horizontal neighbours
+        const bool want_norm = partials != nullptr;
         R um = vzero, uc = vzero, d_prev = vzero;
         int slot = 0;
         const int ctr = (ty + 1) * 34 + tx + 1;
@@ -168,11 +185,15 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
                 const R hy = P::add(P::ld_plain(Us, ctr - 34), P::ld_plain(Us, ctr + 34));
                 const R diag = (nz == 1) ? dh : ((k == 0 || k == nz - 1) ? dh1 : dh2);
                 R au = P::mul(diag, uc);
-                au = P::sub(au, P::mul(cx, hx));
-                au = P::sub(au, P::mul(cy, hy));
+                if (iso) {
+                    au = P::sub(au, P::mul(cx, P::add(hx, hy)));
+                } else {
+                    au = P::sub(au, P::mul(cx, hx));
+                    au = P::sub(au, P::mul(cy, hy));
+                }
                 au = P::sub(au, P::mul(vv, P::add(um, up)));
                 r = P::sub(P::ld_plain(ringF, slot * FPL + tid), au);
-                P::acc_dot(acc, cmp, r, r);
+                if (want_norm) P::acc_dot(acc, cmp, r, r);
                 um = uc;
                 uc = up;
             } else {
