@@ -322,10 +322,244 @@ static int run_sweep_pp(const Lv<P>& L, double coef, const typename P::S* u, con
     return (int)(grd.x * grd.y);
 }
 
+// ---------------------------------------------------------------- two columns per thread
+// The persistent sweep with each thread owning two adjacent columns: a block row covers 64
+// columns, every per-thread load, store and cp.async moves a 16-byte pair, and the two independent
+// Thomas recurrences interleave (twice the instruction-level parallelism per warp). Per cell this
+// halves the address arithmetic, the barriers and the loop control of the one-column kernel.
+// Shared ring per slot: u rows of stride UW = 68 (pad, left halo, 64 columns, right halo, pad),
+// rows j0-1 .. j0+TY; f pairs; 1/m_k pairs. Requires nx % 64 == 0 and 16-byte aligned fields.
+template <class P, class PO, int TY, int PD, int MODE>
+__global__ void __launch_bounds__(32 * TY) k_sweep_x2(Lv<P> L, double coef, const typename P::S* __restrict__ u,
+                                                      const typename P::S* __restrict__ f,
+                                                      typename PO::S* __restrict__ out, double* partials,
+                                                      const int* done) {
+    typedef typename P::S S;
+    typedef typename P::R R;
+    constexpr int NT = 32 * TY;
+    constexpr int UW = 68;
+    constexpr bool STACK = MODE == MODE_SMOOTH;
+    constexpr int UPL = (TY + 2) * UW;
+    constexpr int FPL = 2 * NT;
+    constexpr int IPL = STACK ? 2 * NT : 0;
+    constexpr int PB = 2 * (int)sizeof(S);  // bytes of a column pair
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (done && *(volatile const int*)done) return;
+
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const bool percol = L.fac_percol != 0;
+    S* ringU = reinterpret_cast<S*>(smem_raw);
+    S* ringF = ringU + PD * UPL;
+    S* ringI = ringF + PD * FPL;
+    S* gstack = STACK ? reinterpret_cast<S*>(L.gstack) + (size_t)blockIdx.x * nz * 2 * NT : nullptr;
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const size_t pl = (size_t)nx * ny;
+    const int tiles_x = nx / 64;
+    const int ntiles = tiles_x * (ny / TY);
+    const S* rhs = f;
+    const R vzero = P::zero();
+    typename P::Acc acc = 0, cmp = 0;
+    const bool want_norm = partials != nullptr;
+    const bool iso = L.cx == L.cy;
+
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int i0 = (tile % tiles_x) * 64, j0 = (tile / tiles_x) * TY;
+        const size_t c = (size_t)(j0 + ty) * nx + (i0 + 2 * tx);  // the thread's first column
+        __syncthreads();  // the previous tile's rings are no longer read
+
+        // halo of the u plane: 2 rows x 32 pairs (one pair per thread when TY = 2) and 2 TY side
+        // singles; ring offsets and in-plane sources are the same for every plane
+        constexpr int NPAIR = 64, NSIDE = 2 * TY;
+        constexpr int PPT = (NPAIR + NT - 1) / NT;
+        int hp_dst[PPT];
+        size_t hp_src[PPT];
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            const int it = tid + q * NT;
+            const int top = it < 32, p = it & 31;
+            const int gj = top ? (j0 == 0 ? ny - 1 : j0 - 1) : (j0 + TY == ny ? 0 : j0 + TY);
+            hp_dst[q] = it < NPAIR ? (top ? 0 : (TY + 1) * UW) + 2 + 2 * p : -1;
+            hp_src[q] = (size_t)gj * nx + i0 + 2 * p;
+        }
+        int hs_dst = -1;
+        size_t hs_src = 0;
+        if (tid < NSIDE) {
+            const int r = tid >> 1, right = tid & 1;
+            hs_dst = (r + 1) * UW + (right ? 66 : 1);
+            hs_src = (size_t)(j0 + r) * nx + (right ? (i0 + 64 == nx ? 0 : i0 + 64) : (i0 == 0 ? nx - 1 : i0 - 1));
+        }
+
+        auto issue_plane = [&](int k, int slot) {
+            if (k < nz) {
+                const size_t b = (size_t)k * pl;
+                S* Us = ringU + slot * UPL;
+                cp_async<PB>(&ringF[slot * FPL + 2 * tid], rhs + b + c);
+                if (STACK && percol) cp_async<PB>(&ringI[slot * FPL + 2 * tid], L.finv + b + c);
+                cp_async<PB>(&Us[(ty + 1) * UW + 2 + 2 * tx], u + b + c);
+#pragma unroll
+                for (int q = 0; q < PPT; ++q)
+                    if (hp_dst[q] >= 0) cp_async<PB>(&Us[hp_dst[q]], u + b + hp_src[q]);
+                if (hs_dst >= 0) cp_async<sizeof(S)>(&Us[hs_dst], u + b + hs_src);
+            }
+            cp_commit();
+        };
+        for (int s = 0; s < PD; ++s) issue_plane(s, s);
+
+        const R v0 = P::ld(L.v, c), v1 = P::ld(L.v, c + 1);
+        const R cx = P::cst(L.cx), cy = P::cst(L.cy);
+        const R dh = P::cst(1.0 + 2.0 * L.cx + 2.0 * L.cy);
+        const R dh1a = P::add(dh, v0), dh2a = P::add(dh1a, v0);
+        const R dh1b = P::add(dh, v1), dh2b = P::add(dh1b, v1);
+        R um0 = vzero, um1 = vzero, uc0 = vzero, uc1 = vzero, dp0 = vzero, dp1 = vzero;
+        int slot = 0;
+        const int ctr = (ty + 1) * UW + 2 + 2 * tx;
+        for (int k = 0; k < nz; ++k) {
+            const int nslot = (slot + 1 == PD) ? 0 : slot + 1;
+            cp_wait<PD - 2>();  // planes k and k+1 have landed
+            __syncthreads();    // ... including the halo values other threads fetched
+            const S* Us = ringU + slot * UPL;
+            if (k == 0) {
+                uc0 = P::ld_plain(Us, ctr);
+                uc1 = P::ld_plain(Us, ctr + 1);
+            }
+            R up0 = vzero, up1 = vzero;
+            if (k + 1 < nz) {
+                up0 = P::ld_plain(ringU + nslot * UPL, ctr);
+                up1 = P::ld_plain(ringU + nslot * UPL, ctr + 1);
+            }
+            const R wv = P::ld_plain(Us, ctr - 1), ev = P::ld_plain(Us, ctr + 2);
+            const R s0 = P::ld_plain(Us, ctr - UW), s1 = P::ld_plain(Us, ctr - UW + 1);
+            const R n0 = P::ld_plain(Us, ctr + UW), n1 = P::ld_plain(Us, ctr + UW + 1);
+            const bool end = nz == 1 || k == 0 || k == nz - 1;
+            const R dga = nz == 1 ? dh : (end ? dh1a : dh2a), dgb = nz == 1 ? dh : (end ? dh1b : dh2b);
+            const R hx0 = P::add(wv, uc1), hx1 = P::add(uc0, ev);
+            const R hy0 = P::add(s0, n0), hy1 = P::add(s1, n1);
+            R a0 = P::mul(dga, uc0), a1 = P::mul(dgb, uc1);
+            if (iso) {
+                a0 = P::sub(a0, P::mul(cx, P::add(hx0, hy0)));
+                a1 = P::sub(a1, P::mul(cx, P::add(hx1, hy1)));
+            } else {
+                a0 = P::sub(P::sub(a0, P::mul(cx, hx0)), P::mul(cy, hy0));
+                a1 = P::sub(P::sub(a1, P::mul(cx, hx1)), P::mul(cy, hy1));
+            }
+            a0 = P::sub(a0, P::mul(v0, P::add(um0, up0)));
+            a1 = P::sub(a1, P::mul(v1, P::add(um1, up1)));
+            const R r0 = P::sub(P::ld_plain(ringF, slot * FPL + 2 * tid), a0);
+            const R r1 = P::sub(P::ld_plain(ringF, slot * FPL + 2 * tid + 1), a1);
+            if (want_norm) {
+                P::acc_dot(acc, cmp, r0, r0);
+                P::acc_dot(acc, cmp, r1, r1);
+            }
+            um0 = uc0;
+            um1 = uc1;
+            uc0 = up0;
+            uc1 = up1;
+            if constexpr (MODE == MODE_RESIDUAL) {
+                const size_t id = (size_t)k * pl + c;
+                if constexpr (std::is_same<P, PO>::value) {
+                    P::st(out, id, r0);
+                    P::st(out, id + 1, r1);
+                } else {
+                    PO::st(out, id, PO::from_f(P::to_f(r0)));
+                    PO::st(out, id + 1, PO::from_f(P::to_f(r1)));
+                }
+            }
+            if constexpr (STACK) {
+                R i0v, i1v;
+                if (percol) {
+                    i0v = P::ld_plain(ringI, slot * FPL + 2 * tid);
+                    i1v = P::ld_plain(ringI, slot * FPL + 2 * tid + 1);
+                } else {
+                    i0v = i1v = P::ld(L.finv, k);
+                }
+                dp0 = P::mul(P::add(r0, P::mul(v0, dp0)), i0v);
+                dp1 = P::mul(P::add(r1, P::mul(v1, dp1)), i1v);
+                P::st(gstack, ((size_t)k * NT + tid) * 2, dp0);
+                P::st(gstack, ((size_t)k * NT + tid) * 2 + 1, dp1);
+            }
+            __syncthreads();  // the slot is reused by the next issue
+            issue_plane(k + PD, slot);
+            slot = nslot;
+        }
+        cp_wait<0>();
+
+        if constexpr (STACK) {
+            __syncthreads();  // the backward ring reuses the forward ring's shared memory
+            S* bU = reinterpret_cast<S*>(smem_raw);
+            S* bW = bU + PD * 2 * NT;
+            S* bD = bW + PD * 2 * NT;
+            auto issue_back = [&](int k, int s2) {
+                if (k >= 0) {
+                    const size_t id = (size_t)k * pl + c;
+                    cp_async<PB>(&bU[(s2 * NT + tid) * 2], u + id);
+                    if (percol) cp_async<PB>(&bW[(s2 * NT + tid) * 2], L.fw + id);
+                    cp_async<PB>(&bD[(s2 * NT + tid) * 2], gstack + ((size_t)k * NT + tid) * 2);
+                }
+                cp_commit();
+            };
+            for (int s = 0; s < PD; ++s) issue_back(nz - 1 - s, s);
+            const R cf = P::cst(coef);
+            R x0 = vzero, x1 = vzero;
+            slot = 0;
+            for (int k = nz - 1; k >= 0; --k) {
+                cp_wait<PD - 1>();
+                const int o = (slot * NT + tid) * 2;
+                R w0, w1;
+                if (percol) {
+                    w0 = P::ld_plain(bW, o);
+                    w1 = P::ld_plain(bW, o + 1);
+                } else {
+                    w0 = w1 = P::ld(L.fw, k);
+                }
+                x0 = P::add(P::ld_plain(bD, o), P::mul(w0, x0));
+                x1 = P::add(P::ld_plain(bD, o + 1), P::mul(w1, x1));
+                const size_t id = (size_t)k * pl + c;
+                P::st(reinterpret_cast<S*>(out), id, P::add(P::ld_plain(bU, o), P::mul(cf, x0)));
+                P::st(reinterpret_cast<S*>(out), id + 1, P::add(P::ld_plain(bU, o + 1), P::mul(cf, x1)));
+                issue_back(k - PD, slot);
+                slot = (slot + 1 == PD) ? 0 : slot + 1;
+            }
+            cp_wait<0>();
+        }
+    }
+    if (partials) {
+        double sm = block_sum(P::acc_get(acc, cmp));
+        if (tid == 0) partials[blockIdx.x] = sm;
+    }
+}
+
+template <class P, class PO, int TY, int PD, int MODE>
+static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, const typename P::S* f,
+                        typename PO::S* out, double* partials, const int* done, cudaStream_t s, int cap) {
+    typedef typename P::S S;
+    constexpr bool STACK = MODE == MODE_SMOOTH;
+    if (L.nx % 64 || L.ny % TY || (STACK && (!L.gstack || !L.finv || !L.fw))) return -1;
+    auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+    if (!al(u) || !al(f) || !al(out) || (STACK && (!al(L.finv) || !al(L.fw)))) return -1;
+    const size_t fwd = (size_t)PD * ((TY + 2) * 68 + 2 * 32 * TY + (STACK ? 2 * 32 * TY : 0)) * sizeof(S);
+    const size_t back = STACK ? (size_t)PD * 3 * 2 * 32 * TY * sizeof(S) : 0;
+    const size_t smem = fwd > back ? fwd : back;
+    auto kern = k_sweep_x2<P, PO, TY, PD, MODE>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int ntiles = (L.nx / 64) * (L.ny / TY);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * TY, smem);
+    if (cap > GS_BLOCKS_PER_SM) cap = GS_BLOCKS_PER_SM;
+    if (per_sm > cap) per_sm = cap;
+    if (per_sm < 1) per_sm = 1;
+    int nb = num_sms() * per_sm;
+    if (nb > ntiles) nb = ntiles;
+    kern<<<nb, dim3(32, TY), smem, s>>>(L, coef, u, f, out, partials, done);
+    note_launch();
+    return nb;
+}
+
 // ---------------------------------------------------------------- tile variants
-// Smooth: five variants per precision -- three (TY, PD) tile shapes with the shared-memory stack
-// and two persistent ones with the stack in global scratch; the autotuner (tpmg_autotune) times
-// them per level and stores its choice in Lv::variant. Without a choice, variant 0 is used.
+// Smooth: seven variants per precision -- three (TY, PD) tile shapes with the shared-memory stack,
+// two persistent ones with the stack in global scratch, and two persistent ones with two columns
+// per thread (k_sweep_x2); the autotuner (tpmg_autotune) times them per level and stores its
+// choice in Lv::variant. Without a choice, variant 0 is used.
 template <class P>
 struct SmoothVariants;
 template <>
@@ -344,7 +578,15 @@ struct SmoothVariants<PolDW> {
 template <class P>
 static int smooth_dispatch(const Lv<P>& L, double rho, const typename P::S* u, const typename P::S* f,
                            typename P::S* uo, double* partials, const int* done, cudaStream_t s) {
-    const int v = (L.variant >= 0 && L.variant < 5) ? L.variant : 0;
+    const int v = (L.variant >= 0 && L.variant < 7) ? L.variant : 0;
+    if (v == 5 && L.gstack) {
+        const int nb = run_sweep_x2<P, P, 2, 4, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s, 8);
+        if (nb >= 0) return nb;
+    }
+    if (v == 6 && L.gstack) {
+        const int nb = run_sweep_x2<P, P, 1, 6, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s, 16);
+        if (nb >= 0) return nb;
+    }
     if (P::id == 1) {  // FP32
         if (v == 0 && pp_fits<P, 2>(L)) return run_sweep_pp<P, P, 2, 8, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s);
         if (v == 1 && pp_fits<P, 4>(L)) return run_sweep_pp<P, P, 4, 6, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s);
@@ -376,6 +618,9 @@ int launch_smooth_pp(const Lv<P>& L, double rho, const typename P::S* u, const t
 template <class P, class PO>
 int launch_residual_pp(const Lv<P>& L, const typename P::S* u, const typename P::S* f, typename PO::S* r,
                        double* partials, const int* done, cudaStream_t s) {
+    // two columns per thread when the level allows it (nx % 64 == 0, 16-byte aligned fields)
+    const int nb = run_sweep_x2<P, PO, 2, 4, MODE_RESIDUAL>(L, 1.0, u, f, r, partials, done, s, 8);
+    if (nb >= 0) return nb;
     if (!pp_fits<P, 4, false>(L)) return -1;
     return run_sweep_pp<P, PO, 4, 6, MODE_RESIDUAL>(L, 1.0, u, f, r, partials, done, s);
 }

@@ -50,10 +50,10 @@ struct Lv {
     void* gstack = nullptr;
 };
 
-// persistent sweep variants: at most GS_BLOCKS_PER_SM blocks per SM, each of at most GS_MAX_NT
-// threads, own a stack slot of the scratch
+// persistent sweep variants: at most GS_BLOCKS_PER_SM blocks per SM, each covering at most GS_MAX_NT
+// columns, own a stack slot of the scratch
 static constexpr int GS_BLOCKS_PER_SM = 16;
-static constexpr int GS_MAX_NT = 64;
+static constexpr int GS_MAX_NT = 128;
 size_t gstack_bytes(int nz);
 
 // Levels with at most this many columns run the cell-parallel kernels (one thread per cell,

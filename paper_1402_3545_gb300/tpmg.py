@@ -469,7 +469,7 @@ def kernel_launches() -> int:
     return int(load().tpmg_kernel_launches())
 
 
-NUM_VARIANTS = 5
+NUM_VARIANTS = 7
 
 
 def autotune(op, prec, nlevels, reps=5, stream=None) -> list[int]:
