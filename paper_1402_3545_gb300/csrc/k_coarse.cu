@@ -282,6 +282,42 @@ __global__ void __launch_bounds__(256) k_prolongate_cell(int nxc, int nyc, int n
     }
 }
 
+// ---------------------------------------------------------------- Prolongate, 2 x 2 fine cells per thread
+// One thread per (coarse column, plane): the four fine cells (2I+a, 2J+b) of coarse cell (I, J)
+// take 9/16 of it, 3/16 of its x and y neighbours on their side and 1/16 of the diagonal one;
+// the 3 x 3 coarse neighbourhood is read once for all four (read-only cache), the fine values move
+// as 16-byte (8-byte for FP32) pairs. No loop over the planes: every (column, plane) is a thread.
+template <class P, class PF>
+__global__ void __launch_bounds__(128) k_prolongate_x4(int nxc, int nyc, int nz, const typename P::S* __restrict__ uc,
+                                                       typename PF::S* __restrict__ uf, const int* done) {
+    typedef typename P::R R;
+    typedef typename PF::S SF;
+    if (done && *(volatile const int*)done) return;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+    if (I >= nxc || J >= nyc) return;
+    const size_t plc = (size_t)nxc * nyc;
+    const typename P::S* cp = uc + (size_t)k * plc;
+    const int Im = cwrap(I - 1, nxc), Ip = cwrap(I + 1, nxc);
+    const size_t rm = (size_t)cwrap(J - 1, nyc) * nxc, r0 = (size_t)J * nxc, rp = (size_t)cwrap(J + 1, nyc) * nxc;
+    const R c = P::ld(cp, r0 + I);
+    const R xm = P::ld(cp, r0 + Im), xp = P::ld(cp, r0 + Ip);
+    const R ym = P::ld(cp, rm + I), yp = P::ld(cp, rp + I);
+    const R dmm = P::ld(cp, rm + Im), dpm = P::ld(cp, rm + Ip), dmp = P::ld(cp, rp + Im), dpp = P::ld(cp, rp + Ip);
+    const R w9 = P::cst(0.5625), w3 = P::cst(0.1875), w1 = P::cst(0.0625);
+    const R c9 = P::mul(w9, c);
+    // fine (a, b): a = 0 takes the x neighbour I-1, a = 1 takes I+1; likewise b in y
+    const R v00 = P::add(P::add(c9, P::mul(w3, xm)), P::add(P::mul(w3, ym), P::mul(w1, dmm)));
+    const R v10 = P::add(P::add(c9, P::mul(w3, xp)), P::add(P::mul(w3, ym), P::mul(w1, dpm)));
+    const R v01 = P::add(P::add(c9, P::mul(w3, xm)), P::add(P::mul(w3, yp), P::mul(w1, dmp)));
+    const R v11 = P::add(P::add(c9, P::mul(w3, xp)), P::add(P::mul(w3, yp), P::mul(w1, dpp)));
+    const int nxf = 2 * nxc;
+    const size_t f0 = (size_t)k * 4 * plc + (size_t)(2 * J) * nxf + 2 * I, f1 = f0 + nxf;
+    PF::st(uf, f0, PF::add(PF::ld_plain(uf, f0), Conv<P, PF>::f(v00)));
+    PF::st(uf, f0 + 1, PF::add(PF::ld_plain(uf, f0 + 1), Conv<P, PF>::f(v10)));
+    PF::st(uf, f1, PF::add(PF::ld_plain(uf, f1), Conv<P, PF>::f(v01)));
+    PF::st(uf, f1 + 1, PF::add(PF::ld_plain(uf, f1 + 1), Conv<P, PF>::f(v11)));
+}
+
 // ---------------------------------------------------------------- launchers
 // columns per block: the block is cpb x nz threads (nz <= 256), at most 256 threads
 static int pcr_cpb(int nz, int ncol) {
@@ -369,6 +405,15 @@ int launch_prolongate_cell(int nxc, int nyc, int nz, const typename P::S* uc, ty
     return nb;
 }
 
+template <class P, class PF>
+int launch_prolongate_x4(int nxc, int nyc, int nz, const typename P::S* uc, typename PF::S* uf, const int* done,
+                         cudaStream_t s) {
+    dim3 blk(32, 4), grd((nxc + 31) / 32, (nyc + 3) / 4, nz);
+    k_prolongate_x4<P, PF><<<grd, blk, 0, s>>>(nxc, nyc, nz, uc, uf, done);
+    note_launch();
+    return (int)(grd.x * grd.y * grd.z);
+}
+
 #define TPMG_COARSE_INST(P)                                                                                 \
     template size_t pcr_factor_count<P>(const Lv<P>&, int);                                                  \
     template void launch_pcr_factors<P>(const Lv<P>&, P::S*, int, cudaStream_t);                             \
@@ -380,7 +425,8 @@ int launch_prolongate_cell(int nxc, int nyc, int nz, const typename P::S* uc, ty
                                                   cudaStream_t);                                             \
     template int launch_residual_cell<P, P>(const Lv<P>&, const P::S*, const P::S*, P::S*, double*, const int*, \
                                             cudaStream_t);                                                   \
-    template int launch_prolongate_cell<P, P>(int, int, int, const P::S*, P::S*, const int*, cudaStream_t);
+    template int launch_prolongate_cell<P, P>(int, int, int, const P::S*, P::S*, const int*, cudaStream_t);     \
+    template int launch_prolongate_x4<P, P>(int, int, int, const P::S*, P::S*, const int*, cudaStream_t);
 
 TPMG_COARSE_INST(PolF64)
 TPMG_COARSE_INST(PolF32)
@@ -388,6 +434,7 @@ TPMG_COARSE_INST(PolDW)
 template int launch_restrict_smooth_pcr<PolDW, PolF64>(const Lv<PolF64>&, double, const float2*, double*, double*,
                                                        const int*, cudaStream_t);
 template int launch_prolongate_cell<PolF64, PolDW>(int, int, int, const double*, float2*, const int*, cudaStream_t);
+template int launch_prolongate_x4<PolF64, PolDW>(int, int, int, const double*, float2*, const int*, cudaStream_t);
 template int launch_residual_cell<PolDW, PolF32>(const Lv<PolDW>&, const float2*, const float2*, float*, double*,
                                                  const int*, cudaStream_t);
 template int launch_residual_cell<PolF64, PolF32>(const Lv<PolF64>&, const double*, const double*, float*, double*,

@@ -417,6 +417,7 @@ template <class P, class PF>
 void launch_prolongate(int nxc, int nyc, int nz, const typename P::S* uc, typename PF::S* uf,
                        const int* done, cudaStream_t s) {
     if (launch_prolongate_cell<P, PF>(nxc, nyc, nz, uc, uf, done, s) >= 0) return;
+    if (launch_prolongate_x4<P, PF>(nxc, nyc, nz, uc, uf, done, s) >= 0) return;
     Shape sh = sweep_shape(2 * nxc, 2 * nyc, nz, sizeof(typename P::R), false);
     k_prolongate<P, PF><<<sh.grid, sh.block, 0, s>>>(nxc, nyc, nz, uc, uf, done);
     note_launch();

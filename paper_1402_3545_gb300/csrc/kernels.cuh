@@ -148,6 +148,10 @@ template <class P, class PF>
 int launch_prolongate_cell(int nxc, int nyc, int nz, const typename P::S* uc, typename PF::S* uf, const int* done,
                            cudaStream_t s);
 int cell_blocks(size_t n);
+// u_f += P u_c with one thread per (coarse column, plane) and its 2 x 2 fine cells (any level)
+template <class P, class PF>
+int launch_prolongate_x4(int nxc, int nyc, int nz, const typename P::S* uc, typename PF::S* uf, const int* done,
+                         cudaStream_t s);
 
 // ---------------------------------------------------------------- launchers (k_mg.cu)
 template <class P>
