@@ -338,8 +338,9 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_x2(Lv<P> L, double coef, cons
     typedef typename P::R R;
     constexpr int NT = 32 * TY;
     constexpr int UW = 68;
-    constexpr bool STACK = MODE == MODE_SMOOTH;
-    constexpr int UPL = (TY + 2) * UW;
+    constexpr bool STACK = MODE != MODE_RESIDUAL;
+    constexpr bool HALO = MODE != MODE_LINESOLVE;
+    constexpr int UPL = HALO ? (TY + 2) * UW : 0;
     constexpr int FPL = 2 * NT;
     constexpr int IPL = STACK ? 2 * NT : 0;
     constexpr int PB = 2 * (int)sizeof(S);  // bytes of a column pair
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_x2(Lv<P> L, double coef, cons
     const size_t pl = (size_t)nx * ny;
     const int tiles_x = nx / 64;
     const int ntiles = tiles_x * (ny / TY);
-    const S* rhs = f;
+    const S* rhs = (MODE == MODE_LINESOLVE) ? u : f;
     const R vzero = P::zero();
     typename P::Acc acc = 0, cmp = 0;
     const bool want_norm = partials != nullptr;
@@ -396,11 +397,13 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_x2(Lv<P> L, double coef, cons
                 S* Us = ringU + slot * UPL;
                 cp_async<PB>(&ringF[slot * FPL + 2 * tid], rhs + b + c);
                 if (STACK && percol) cp_async<PB>(&ringI[slot * FPL + 2 * tid], L.finv + b + c);
-                cp_async<PB>(&Us[(ty + 1) * UW + 2 + 2 * tx], u + b + c);
+                if (HALO) {
+                    cp_async<PB>(&Us[(ty + 1) * UW + 2 + 2 * tx], u + b + c);
 #pragma unroll
-                for (int q = 0; q < PPT; ++q)
-                    if (hp_dst[q] >= 0) cp_async<PB>(&Us[hp_dst[q]], u + b + hp_src[q]);
-                if (hs_dst >= 0) cp_async<sizeof(S)>(&Us[hs_dst], u + b + hs_src);
+                    for (int q = 0; q < PPT; ++q)
+                        if (hp_dst[q] >= 0) cp_async<PB>(&Us[hp_dst[q]], u + b + hp_src[q]);
+                    if (hs_dst >= 0) cp_async<sizeof(S)>(&Us[hs_dst], u + b + hs_src);
+                }
             }
             cp_commit();
         };
@@ -416,45 +419,52 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_x2(Lv<P> L, double coef, cons
         const int ctr = (ty + 1) * UW + 2 + 2 * tx;
         for (int k = 0; k < nz; ++k) {
             const int nslot = (slot + 1 == PD) ? 0 : slot + 1;
-            cp_wait<PD - 2>();  // planes k and k+1 have landed
-            __syncthreads();    // ... including the halo values other threads fetched
-            const S* Us = ringU + slot * UPL;
-            if (k == 0) {
-                uc0 = P::ld_plain(Us, ctr);
-                uc1 = P::ld_plain(Us, ctr + 1);
-            }
-            R up0 = vzero, up1 = vzero;
-            if (k + 1 < nz) {
-                up0 = P::ld_plain(ringU + nslot * UPL, ctr);
-                up1 = P::ld_plain(ringU + nslot * UPL, ctr + 1);
-            }
-            const R wv = P::ld_plain(Us, ctr - 1), ev = P::ld_plain(Us, ctr + 2);
-            const R s0 = P::ld_plain(Us, ctr - UW), s1 = P::ld_plain(Us, ctr - UW + 1);
-            const R n0 = P::ld_plain(Us, ctr + UW), n1 = P::ld_plain(Us, ctr + UW + 1);
-            const bool end = nz == 1 || k == 0 || k == nz - 1;
-            const R dga = nz == 1 ? dh : (end ? dh1a : dh2a), dgb = nz == 1 ? dh : (end ? dh1b : dh2b);
-            const R hx0 = P::add(wv, uc1), hx1 = P::add(uc0, ev);
-            const R hy0 = P::add(s0, n0), hy1 = P::add(s1, n1);
-            R a0 = P::mul(dga, uc0), a1 = P::mul(dgb, uc1);
-            if (iso) {
-                a0 = P::sub(a0, P::mul(cx, P::add(hx0, hy0)));
-                a1 = P::sub(a1, P::mul(cx, P::add(hx1, hy1)));
+            R r0, r1;
+            if constexpr (!HALO) {
+                cp_wait<PD - 1>();  // only this thread's own copies are read: no barrier needed
+                r0 = P::ld_plain(ringF, slot * FPL + 2 * tid);
+                r1 = P::ld_plain(ringF, slot * FPL + 2 * tid + 1);
             } else {
-                a0 = P::sub(P::sub(a0, P::mul(cx, hx0)), P::mul(cy, hy0));
-                a1 = P::sub(P::sub(a1, P::mul(cx, hx1)), P::mul(cy, hy1));
+                cp_wait<PD - 2>();  // planes k and k+1 have landed
+                __syncthreads();    // ... including the halo values other threads fetched
+                const S* Us = ringU + slot * UPL;
+                if (k == 0) {
+                    uc0 = P::ld_plain(Us, ctr);
+                    uc1 = P::ld_plain(Us, ctr + 1);
+                }
+                R up0 = vzero, up1 = vzero;
+                if (k + 1 < nz) {
+                    up0 = P::ld_plain(ringU + nslot * UPL, ctr);
+                    up1 = P::ld_plain(ringU + nslot * UPL, ctr + 1);
+                }
+                const R wv = P::ld_plain(Us, ctr - 1), ev = P::ld_plain(Us, ctr + 2);
+                const R s0 = P::ld_plain(Us, ctr - UW), s1 = P::ld_plain(Us, ctr - UW + 1);
+                const R n0 = P::ld_plain(Us, ctr + UW), n1 = P::ld_plain(Us, ctr + UW + 1);
+                const bool end = nz == 1 || k == 0 || k == nz - 1;
+                const R dga = nz == 1 ? dh : (end ? dh1a : dh2a), dgb = nz == 1 ? dh : (end ? dh1b : dh2b);
+                const R hx0 = P::add(wv, uc1), hx1 = P::add(uc0, ev);
+                const R hy0 = P::add(s0, n0), hy1 = P::add(s1, n1);
+                R a0 = P::mul(dga, uc0), a1 = P::mul(dgb, uc1);
+                if (iso) {
+                    a0 = P::sub(a0, P::mul(cx, P::add(hx0, hy0)));
+                    a1 = P::sub(a1, P::mul(cx, P::add(hx1, hy1)));
+                } else {
+                    a0 = P::sub(P::sub(a0, P::mul(cx, hx0)), P::mul(cy, hy0));
+                    a1 = P::sub(P::sub(a1, P::mul(cx, hx1)), P::mul(cy, hy1));
+                }
+                a0 = P::sub(a0, P::mul(v0, P::add(um0, up0)));
+                a1 = P::sub(a1, P::mul(v1, P::add(um1, up1)));
+                r0 = P::sub(P::ld_plain(ringF, slot * FPL + 2 * tid), a0);
+                r1 = P::sub(P::ld_plain(ringF, slot * FPL + 2 * tid + 1), a1);
+                if (want_norm) {
+                    P::acc_dot(acc, cmp, r0, r0);
+                    P::acc_dot(acc, cmp, r1, r1);
+                }
+                um0 = uc0;
+                um1 = uc1;
+                uc0 = up0;
+                uc1 = up1;
             }
-            a0 = P::sub(a0, P::mul(v0, P::add(um0, up0)));
-            a1 = P::sub(a1, P::mul(v1, P::add(um1, up1)));
-            const R r0 = P::sub(P::ld_plain(ringF, slot * FPL + 2 * tid), a0);
-            const R r1 = P::sub(P::ld_plain(ringF, slot * FPL + 2 * tid + 1), a1);
-            if (want_norm) {
-                P::acc_dot(acc, cmp, r0, r0);
-                P::acc_dot(acc, cmp, r1, r1);
-            }
-            um0 = uc0;
-            um1 = uc1;
-            uc0 = up0;
-            uc1 = up1;
             if constexpr (MODE == MODE_RESIDUAL) {
                 const size_t id = (size_t)k * pl + c;
                 if constexpr (std::is_same<P, PO>::value) {
@@ -478,13 +488,14 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_x2(Lv<P> L, double coef, cons
                 P::st(gstack, ((size_t)k * NT + tid) * 2, dp0);
                 P::st(gstack, ((size_t)k * NT + tid) * 2 + 1, dp1);
             }
-            __syncthreads();  // the slot is reused by the next issue
+            if (HALO) __syncthreads();  // the slot is reused by the next issue
             issue_plane(k + PD, slot);
             slot = nslot;
         }
         cp_wait<0>();
 
         if constexpr (STACK) {
+            constexpr bool NEED_U = MODE == MODE_SMOOTH;
             __syncthreads();  // the backward ring reuses the forward ring's shared memory
             S* bU = reinterpret_cast<S*>(smem_raw);
             S* bW = bU + PD * 2 * NT;
@@ -492,7 +503,7 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_x2(Lv<P> L, double coef, cons
             auto issue_back = [&](int k, int s2) {
                 if (k >= 0) {
                     const size_t id = (size_t)k * pl + c;
-                    cp_async<PB>(&bU[(s2 * NT + tid) * 2], u + id);
+                    if (NEED_U) cp_async<PB>(&bU[(s2 * NT + tid) * 2], u + id);
                     if (percol) cp_async<PB>(&bW[(s2 * NT + tid) * 2], L.fw + id);
                     cp_async<PB>(&bD[(s2 * NT + tid) * 2], gstack + ((size_t)k * NT + tid) * 2);
                 }
@@ -515,8 +526,13 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_x2(Lv<P> L, double coef, cons
                 x0 = P::add(P::ld_plain(bD, o), P::mul(w0, x0));
                 x1 = P::add(P::ld_plain(bD, o + 1), P::mul(w1, x1));
                 const size_t id = (size_t)k * pl + c;
-                P::st(reinterpret_cast<S*>(out), id, P::add(P::ld_plain(bU, o), P::mul(cf, x0)));
-                P::st(reinterpret_cast<S*>(out), id + 1, P::add(P::ld_plain(bU, o + 1), P::mul(cf, x1)));
+                if constexpr (NEED_U) {
+                    P::st(reinterpret_cast<S*>(out), id, P::add(P::ld_plain(bU, o), P::mul(cf, x0)));
+                    P::st(reinterpret_cast<S*>(out), id + 1, P::add(P::ld_plain(bU, o + 1), P::mul(cf, x1)));
+                } else {
+                    P::st(reinterpret_cast<S*>(out), id, coef != 1.0 ? P::mul(cf, x0) : x0);
+                    P::st(reinterpret_cast<S*>(out), id + 1, coef != 1.0 ? P::mul(cf, x1) : x1);
+                }
                 issue_back(k - PD, slot);
                 slot = (slot + 1 == PD) ? 0 : slot + 1;
             }
@@ -533,11 +549,12 @@ template <class P, class PO, int TY, int PD, int MODE>
 static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, const typename P::S* f,
                         typename PO::S* out, double* partials, const int* done, cudaStream_t s, int cap) {
     typedef typename P::S S;
-    constexpr bool STACK = MODE == MODE_SMOOTH;
+    constexpr bool STACK = MODE != MODE_RESIDUAL;
+    constexpr bool HALO = MODE != MODE_LINESOLVE;
     if (L.nx % 64 || L.ny % TY || (STACK && (!L.gstack || !L.finv || !L.fw))) return -1;
     auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
-    if (!al(u) || !al(f) || !al(out) || (STACK && (!al(L.finv) || !al(L.fw)))) return -1;
-    const size_t fwd = (size_t)PD * ((TY + 2) * 68 + 2 * 32 * TY + (STACK ? 2 * 32 * TY : 0)) * sizeof(S);
+    if (!al(u) || (HALO && !al(f)) || !al(out) || (STACK && (!al(L.finv) || !al(L.fw)))) return -1;
+    const size_t fwd = (size_t)PD * ((HALO ? (TY + 2) * 68 : 0) + 2 * 32 * TY + (STACK ? 2 * 32 * TY : 0)) * sizeof(S);
     const size_t back = STACK ? (size_t)PD * 3 * 2 * 32 * TY * sizeof(S) : 0;
     const size_t smem = fwd > back ? fwd : back;
     auto kern = k_sweep_x2<P, PO, TY, PD, MODE>;
@@ -642,7 +659,7 @@ int launch_line_solve_pp(const Lv<P>& L, const typename P::S* b, typename P::S* 
 // Coarse tile of 32 x TY columns; per coarse plane each thread fetches its 2 x 2 fine children
 // (two contiguous pairs) and, when lambda^2 varies, 1/m_k; f_c = 1/4 (sum of the children) is
 // written in the forward sweep, u_c = rho M_c^{-1} f_c in the backward sweep.
-template <class PF, class P, int TY, int PD>
+template <class PF, class P, int TY, int PD, bool GS>
 __global__ void __launch_bounds__(32 * TY) k_restrict_smooth_pp(Lv<P> Lc, double rho_d,
                                                                 const typename PF::S* __restrict__ rf,
                                                                 typename P::S* __restrict__ fc,
@@ -660,66 +677,82 @@ __global__ void __launch_bounds__(32 * TY) k_restrict_smooth_pp(Lv<P> Lc, double
     S* ringI = reinterpret_cast<S*>(smem_raw + (size_t)PD * CPL * sizeof(SF));
     const size_t ring_bytes = (((size_t)PD * CPL * sizeof(SF) + (size_t)PD * NT * sizeof(S)) + 15) & ~(size_t)15;
     R* stack = reinterpret_cast<R*>(smem_raw + ring_bytes);
+    S* gstack = GS ? reinterpret_cast<S*>(Lc.gstack) + (size_t)blockIdx.x * nz * NT : nullptr;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-    const int I = blockIdx.x * 32 + tx, J = blockIdx.y * TY + ty;
     const size_t plc = (size_t)nxc * nyc, plf = 4 * plc;
-    const size_t c = (size_t)J * nxc + I;
-    const size_t f0 = (size_t)(2 * J) * nxf + 2 * I, f1 = f0 + nxf;
-    auto issue_plane = [&](int k, int slot) {
-        if (k < nz) {
-            const size_t bf = (size_t)k * plf;
-            cp_async<2 * sizeof(SF)>(&ringC[slot * CPL + 4 * tid], rf + bf + f0);
-            cp_async<2 * sizeof(SF)>(&ringC[slot * CPL + 4 * tid + 2], rf + bf + f1);
-            if (percol) cp_async<sizeof(S)>(&ringI[slot * NT + tid], Lc.finv + (size_t)k * plc + c);
+    const int tiles_x = nxc / 32;
+    const int ntiles = GS ? tiles_x * (nyc / TY) : 1;
+    for (int tile = GS ? blockIdx.x : 0; tile < ntiles; tile += GS ? gridDim.x : 1) {
+        const int I = (GS ? (tile % tiles_x) : blockIdx.x) * 32 + tx;
+        const int J = (GS ? (tile / tiles_x) : blockIdx.y) * TY + ty;
+        const size_t c = (size_t)J * nxc + I;
+        const size_t f0 = (size_t)(2 * J) * nxf + 2 * I, f1 = f0 + nxf;
+        if (GS) __syncthreads();  // the previous tile's backward ring is no longer read
+        auto issue_plane = [&](int k, int slot) {
+            if (k < nz) {
+                const size_t bf = (size_t)k * plf;
+                cp_async<2 * sizeof(SF)>(&ringC[slot * CPL + 4 * tid], rf + bf + f0);
+                cp_async<2 * sizeof(SF)>(&ringC[slot * CPL + 4 * tid + 2], rf + bf + f1);
+                if (percol) cp_async<sizeof(S)>(&ringI[slot * NT + tid], Lc.finv + (size_t)k * plc + c);
+            }
+            cp_commit();
+        };
+        for (int s = 0; s < PD; ++s) issue_plane(s, s);
+        const R vv = P::ld(Lc.v, c), quarter = P::cst(0.25);
+        R d_prev = P::zero();
+        int slot = 0;
+        for (int k = 0; k < nz; ++k) {
+            cp_wait<PD - 1>();
+            const SF* ch = ringC + slot * CPL + 4 * tid;
+            R s4;
+            if constexpr (std::is_same<PF, P>::value) {
+                s4 = P::add(P::add(P::ld_plain(ch, 0), P::ld_plain(ch, 1)), P::add(P::ld_plain(ch, 2), P::ld_plain(ch, 3)));
+            } else {
+                auto cv = [&](int q) { return P::cst(PF::to_d(PF::ld_plain(ch, q))); };
+                s4 = P::add(P::add(cv(0), cv(1)), P::add(cv(2), cv(3)));
+            }
+            const R fk = P::mul(quarter, s4);
+            P::st(fc, (size_t)k * plc + c, fk);
+            const R inv = percol ? P::ld_plain(ringI, slot * NT + tid) : P::ld(Lc.finv, k);
+            const R d = P::mul(P::add(fk, P::mul(vv, d_prev)), inv);
+            if constexpr (GS)
+                P::st(gstack, (size_t)k * NT + tid, d);
+            else
+                stack[(size_t)k * NT + tid] = d;
+            d_prev = d;
+            issue_plane(k + PD, slot);
+            slot = (slot + 1 == PD) ? 0 : slot + 1;
         }
-        cp_commit();
-    };
-    for (int s = 0; s < PD; ++s) issue_plane(s, s);
-    const R vv = P::ld(Lc.v, c), quarter = P::cst(0.25);
-    R d_prev = P::zero();
-    int slot = 0;
-    for (int k = 0; k < nz; ++k) {
-        cp_wait<PD - 1>();
-        const SF* ch = ringC + slot * CPL + 4 * tid;
-        R s4;
-        if constexpr (std::is_same<PF, P>::value) {
-            s4 = P::add(P::add(P::ld_plain(ch, 0), P::ld_plain(ch, 1)), P::add(P::ld_plain(ch, 2), P::ld_plain(ch, 3)));
-        } else {
-            auto cv = [&](int q) { return P::cst(PF::to_d(PF::ld_plain(ch, q))); };
-            s4 = P::add(P::add(cv(0), cv(1)), P::add(cv(2), cv(3)));
+        cp_wait<0>();
+        // the backward ring reuses shared memory that other threads' forward slots occupied: wait
+        // until every thread of the block has finished its forward sweep
+        __syncthreads();
+        // back substitution with v/m_k and (GS) d'_k streamed in reverse (each thread reads only
+        // its own copies)
+        S* bW = reinterpret_cast<S*>(smem_raw);
+        S* bD = bW + PD * NT;
+        auto issue_back = [&](int k, int s2) {
+            if (k >= 0) {
+                if (percol) cp_async<sizeof(S)>(&bW[s2 * NT + tid], Lc.fw + (size_t)k * plc + c);
+                if (GS) cp_async<sizeof(S)>(&bD[s2 * NT + tid], gstack + (size_t)k * NT + tid);
+            }
+            cp_commit();
+        };
+        for (int s = 0; s < PD; ++s) issue_back(nz - 1 - s, s);
+        const R rho = P::cst(rho_d);
+        R xn = P::zero();
+        slot = 0;
+        for (int k = nz - 1; k >= 0; --k) {
+            cp_wait<PD - 1>();
+            const R w = percol ? P::ld_plain(bW, slot * NT + tid) : P::ld(Lc.fw, k);
+            const R dk = GS ? P::ld_plain(bD, slot * NT + tid) : stack[(size_t)k * NT + tid];
+            xn = P::add(dk, P::mul(w, xn));
+            P::st(uc, (size_t)k * plc + c, P::mul(rho, xn));
+            issue_back(k - PD, slot);
+            slot = (slot + 1 == PD) ? 0 : slot + 1;
         }
-        const R fk = P::mul(quarter, s4);
-        P::st(fc, (size_t)k * plc + c, fk);
-        const R inv = percol ? P::ld_plain(ringI, slot * NT + tid) : P::ld(Lc.finv, k);
-        const R d = P::mul(P::add(fk, P::mul(vv, d_prev)), inv);
-        stack[(size_t)k * NT + tid] = d;
-        d_prev = d;
-        issue_plane(k + PD, slot);
-        slot = (slot + 1 == PD) ? 0 : slot + 1;
+        cp_wait<0>();
     }
-    cp_wait<0>();
-    // the backward ring reuses shared memory that other threads' forward slots occupied: wait
-    // until every thread of the block has finished its forward sweep
-    __syncthreads();
-    // back substitution with v/m_k streamed in reverse (each thread reads only its own copies)
-    S* bW = reinterpret_cast<S*>(smem_raw);
-    auto issue_back = [&](int k, int s2) {
-        if (k >= 0 && percol) cp_async<sizeof(S)>(&bW[s2 * NT + tid], Lc.fw + (size_t)k * plc + c);
-        cp_commit();
-    };
-    for (int s = 0; s < PD; ++s) issue_back(nz - 1 - s, s);
-    const R rho = P::cst(rho_d);
-    R xn = P::zero();
-    slot = 0;
-    for (int k = nz - 1; k >= 0; --k) {
-        cp_wait<PD - 1>();
-        const R w = percol ? P::ld_plain(bW, slot * NT + tid) : P::ld(Lc.fw, k);
-        xn = P::add(stack[(size_t)k * NT + tid], P::mul(w, xn));
-        P::st(uc, (size_t)k * plc + c, P::mul(rho, xn));
-        issue_back(k - PD, slot);
-        slot = (slot + 1 == PD) ? 0 : slot + 1;
-    }
-    cp_wait<0>();
 }
 
 template <class PF, class P>
@@ -729,8 +762,23 @@ int launch_restrict_smooth_pp(const Lv<P>& Lc, double rho, const typename PF::S*
     constexpr int PD = 6;
     if (!pp_fits<P, TY>(Lc) || Lc.nz * 32 * 8 > 160 * 1024) return -1;
     const size_t ring = (((size_t)PD * 4 * 32 * TY * sizeof(typename PF::S) + (size_t)PD * 32 * TY * sizeof(typename P::S)) + 15) & ~(size_t)15;
+    if (Lc.gstack) {
+        // persistent, the stack in global scratch (the backward ring of v/m and d' fits the ring)
+        auto kern = k_restrict_smooth_pp<PF, P, TY, PD, true>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
+        const int ntiles = (Lc.nx / 32) * (Lc.ny / TY);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * TY, ring);
+        if (per_sm > GS_BLOCKS_PER_SM) per_sm = GS_BLOCKS_PER_SM;
+        if (per_sm < 1) per_sm = 1;
+        int nb = num_sms() * per_sm;
+        if (nb > ntiles) nb = ntiles;
+        kern<<<nb, dim3(32, TY), ring, s>>>(Lc, rho, rf, fc, uc, done);
+        note_launch();
+        return 1;
+    }
     const size_t smem = ring + (size_t)Lc.nz * 32 * TY * sizeof(typename P::R);
-    auto kern = k_restrict_smooth_pp<PF, P, TY, PD>;
+    auto kern = k_restrict_smooth_pp<PF, P, TY, PD, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grd(Lc.nx / 32, Lc.ny / TY), blk(32, TY);
     kern<<<grd, blk, smem, s>>>(Lc, rho, rf, fc, uc, done);
