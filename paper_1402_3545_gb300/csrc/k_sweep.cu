@@ -181,18 +181,10 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
                 const S* Us = ringU + slot * UPL;
                 if (k == 0) uc = P::ld_plain(Us, ctr);
                 const R up = (k + 1 < nz) ? P::ld_plain(ringU + nslot * UPL, ctr) : vzero;
-                const R hx = P::add(P::ld_plain(Us, ctr - 1), P::ld_plain(Us, ctr + 1));
-                const R hy = P::add(P::ld_plain(Us, ctr - 34), P::ld_plain(Us, ctr + 34));
                 const R diag = (nz == 1) ? dh : ((k == 0 || k == nz - 1) ? dh1 : dh2);
-                R au = P::mul(diag, uc);
-                if (iso) {
-                    au = P::sub(au, P::mul(cx, P::add(hx, hy)));
-                } else {
-                    au = P::sub(au, P::mul(cx, hx));
-                    au = P::sub(au, P::mul(cy, hy));
-                }
-                au = P::sub(au, P::mul(vv, P::add(um, up)));
-                r = P::sub(P::ld_plain(ringF, slot * FPL + tid), au);
+                r = sweep_residual<P>(P::ld_plain(ringF, slot * FPL + tid), diag, uc, P::ld_plain(Us, ctr - 1),
+                                      P::ld_plain(Us, ctr + 1), P::ld_plain(Us, ctr - 34), P::ld_plain(Us, ctr + 34),
+                                      um, up, cx, cy, vv, iso);
                 if (want_norm) P::acc_dot(acc, cmp, r, r);
                 um = uc;
                 uc = up;
@@ -209,7 +201,7 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
             }
             if constexpr (STACK) {
                 const R inv = percol ? P::ld_plain(ringI, slot * FPL + tid) : P::ld(L.finv, k);
-                const R d = P::mul(P::add(r, P::mul(vv, d_prev)), inv);
+                const R d = P::mul(P::fma(vv, d_prev, r), inv);
                 if constexpr (GS)
                     P::st(gstack, (size_t)k * NT + tid, d);
                 else
@@ -248,10 +240,10 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
                 cp_wait<PD - 1>();
                 const R w = percol ? P::ld_plain(bW, slot * NT + tid) : P::ld(L.fw, k);
                 const R dk = GS ? P::ld_plain(bD, slot * NT + tid) : stack[(size_t)k * NT + tid];
-                xn = P::add(dk, P::mul(w, xn));
+                xn = P::fma(w, xn, dk);
                 const size_t id = (size_t)k * pl + c;
                 if constexpr (MODE == MODE_SMOOTH)
-                    P::st(reinterpret_cast<S*>(out), id, P::add(P::ld_plain(bU, slot * NT + tid), P::mul(cf, xn)));
+                    P::st(reinterpret_cast<S*>(out), id, P::fma(cf, xn, P::ld_plain(bU, slot * NT + tid)));
                 else
                     P::st(reinterpret_cast<S*>(out), id, scaled ? P::mul(cf, xn) : xn);
                 issue_back(k - PD, slot);
@@ -442,20 +434,10 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_x2(Lv<P> L, double coef, cons
                 const R n0 = P::ld_plain(Us, ctr + UW), n1 = P::ld_plain(Us, ctr + UW + 1);
                 const bool end = nz == 1 || k == 0 || k == nz - 1;
                 const R dga = nz == 1 ? dh : (end ? dh1a : dh2a), dgb = nz == 1 ? dh : (end ? dh1b : dh2b);
-                const R hx0 = P::add(wv, uc1), hx1 = P::add(uc0, ev);
-                const R hy0 = P::add(s0, n0), hy1 = P::add(s1, n1);
-                R a0 = P::mul(dga, uc0), a1 = P::mul(dgb, uc1);
-                if (iso) {
-                    a0 = P::sub(a0, P::mul(cx, P::add(hx0, hy0)));
-                    a1 = P::sub(a1, P::mul(cx, P::add(hx1, hy1)));
-                } else {
-                    a0 = P::sub(P::sub(a0, P::mul(cx, hx0)), P::mul(cy, hy0));
-                    a1 = P::sub(P::sub(a1, P::mul(cx, hx1)), P::mul(cy, hy1));
-                }
-                a0 = P::sub(a0, P::mul(v0, P::add(um0, up0)));
-                a1 = P::sub(a1, P::mul(v1, P::add(um1, up1)));
-                r0 = P::sub(P::ld_plain(ringF, slot * FPL + 2 * tid), a0);
-                r1 = P::sub(P::ld_plain(ringF, slot * FPL + 2 * tid + 1), a1);
+                r0 = sweep_residual<P>(P::ld_plain(ringF, slot * FPL + 2 * tid), dga, uc0, wv, uc1, s0, n0, um0, up0,
+                                       cx, cy, v0, iso);
+                r1 = sweep_residual<P>(P::ld_plain(ringF, slot * FPL + 2 * tid + 1), dgb, uc1, uc0, ev, s1, n1, um1,
+                                       up1, cx, cy, v1, iso);
                 if (want_norm) {
                     P::acc_dot(acc, cmp, r0, r0);
                     P::acc_dot(acc, cmp, r1, r1);
@@ -483,8 +465,8 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_x2(Lv<P> L, double coef, cons
                 } else {
                     i0v = i1v = P::ld(L.finv, k);
                 }
-                dp0 = P::mul(P::add(r0, P::mul(v0, dp0)), i0v);
-                dp1 = P::mul(P::add(r1, P::mul(v1, dp1)), i1v);
+                dp0 = P::mul(P::fma(v0, dp0, r0), i0v);
+                dp1 = P::mul(P::fma(v1, dp1, r1), i1v);
                 P::st(gstack, ((size_t)k * NT + tid) * 2, dp0);
                 P::st(gstack, ((size_t)k * NT + tid) * 2 + 1, dp1);
             }
@@ -523,12 +505,12 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_x2(Lv<P> L, double coef, cons
                 } else {
                     w0 = w1 = P::ld(L.fw, k);
                 }
-                x0 = P::add(P::ld_plain(bD, o), P::mul(w0, x0));
-                x1 = P::add(P::ld_plain(bD, o + 1), P::mul(w1, x1));
+                x0 = P::fma(w0, x0, P::ld_plain(bD, o));
+                x1 = P::fma(w1, x1, P::ld_plain(bD, o + 1));
                 const size_t id = (size_t)k * pl + c;
                 if constexpr (NEED_U) {
-                    P::st(reinterpret_cast<S*>(out), id, P::add(P::ld_plain(bU, o), P::mul(cf, x0)));
-                    P::st(reinterpret_cast<S*>(out), id + 1, P::add(P::ld_plain(bU, o + 1), P::mul(cf, x1)));
+                    P::st(reinterpret_cast<S*>(out), id, P::fma(cf, x0, P::ld_plain(bU, o)));
+                    P::st(reinterpret_cast<S*>(out), id + 1, P::fma(cf, x1, P::ld_plain(bU, o + 1)));
                 } else {
                     P::st(reinterpret_cast<S*>(out), id, coef != 1.0 ? P::mul(cf, x0) : x0);
                     P::st(reinterpret_cast<S*>(out), id + 1, coef != 1.0 ? P::mul(cf, x1) : x1);
@@ -714,7 +696,7 @@ __global__ void __launch_bounds__(32 * TY) k_restrict_smooth_pp(Lv<P> Lc, double
             const R fk = P::mul(quarter, s4);
             P::st(fc, (size_t)k * plc + c, fk);
             const R inv = percol ? P::ld_plain(ringI, slot * NT + tid) : P::ld(Lc.finv, k);
-            const R d = P::mul(P::add(fk, P::mul(vv, d_prev)), inv);
+            const R d = P::mul(P::fma(vv, d_prev, fk), inv);
             if constexpr (GS)
                 P::st(gstack, (size_t)k * NT + tid, d);
             else
@@ -746,7 +728,7 @@ __global__ void __launch_bounds__(32 * TY) k_restrict_smooth_pp(Lv<P> Lc, double
             cp_wait<PD - 1>();
             const R w = percol ? P::ld_plain(bW, slot * NT + tid) : P::ld(Lc.fw, k);
             const R dk = GS ? P::ld_plain(bD, slot * NT + tid) : stack[(size_t)k * NT + tid];
-            xn = P::add(dk, P::mul(w, xn));
+            xn = P::fma(w, xn, dk);
             P::st(uc, (size_t)k * plc + c, P::mul(rho, xn));
             issue_back(k - PD, slot);
             slot = (slot + 1 == PD) ? 0 : slot + 1;

@@ -65,6 +65,23 @@ inline int pcr_steps_for(int nz) {
     return s;
 }
 
+// r = f - (A u) at one cell of the plane-streaming sweeps, as a chain of fused multiply-adds:
+// f - diag u_c + cx (u_w + u_e) + cy (u_s + u_n) + v (u_{k-1} + u_{k+1}); on square cells
+// (cx == cy) one product covers the four horizontal neighbours.
+template <class P>
+__device__ __forceinline__ typename P::R sweep_residual(typename P::R fk, typename P::R diag, typename P::R uc,
+                                                        typename P::R w, typename P::R e, typename P::R s,
+                                                        typename P::R n, typename P::R um, typename P::R up,
+                                                        typename P::R cx, typename P::R cy, typename P::R vv,
+                                                        bool iso) {
+    typename P::R r = P::fma(P::neg(diag), uc, fk);
+    if (iso)
+        r = P::fma(cx, P::sum4(w, e, s, n), r);
+    else
+        r = P::fma(cy, P::add(s, n), P::fma(cx, P::add(w, e), r));
+    return P::fma(vv, P::add(um, up), r);
+}
+
 // value of policy PA converted to policy PB's arithmetic (no-op when they coincide)
 template <class PA, class PB>
 struct Conv {
