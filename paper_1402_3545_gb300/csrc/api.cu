@@ -20,7 +20,9 @@ using namespace tpmg;
 
 static constexpr int MAXL = 16;
 static constexpr int MAX_NZ = 256;
-static constexpr double DW_KAPPA_MAX = 4000.0;
+// the double-word solver runs a level in double-word arithmetic while 4 u kappa(M) <= 1e-10 with
+// u = 2^-48 (the forward-error bound of its line solves stays at the FP64 parity tolerance)
+static constexpr double DW_KAPPA_MAX = 7000.0;
 
 static thread_local std::string g_err;
 
@@ -672,7 +674,7 @@ tpmg_status tpmg_create_operator(const tpmg_grid* g, double omega2, double hx, d
     }
     // Double-word arithmetic (unit roundoff ~2^-48) loses log2(kappa(M)) bits in the line solves;
     // levels with kappa(M) > DW_KAPPA_MAX (all coarse and small) run in native FP64 instead, which
-    // keeps every smoother application within 1e-10 of an FP64 computation.
+    // keeps every smoother application within 1e-10 of an FP64 computation (4 u kappa <= 1e-10).
     op->lsw_dw = L + 1;
     for (int l = L; l >= 1 && op->kappa_M[l] <= DW_KAPPA_MAX; --l) op->lsw_dw = l;
     if (cudaStreamCreateWithFlags(&op->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||

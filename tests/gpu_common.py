@@ -29,7 +29,8 @@ def tol_inverse(prec: int, cx, cy, v) -> float:
     """Tolerance of kernels that apply M^{-1} (line solve, Smooth, RestrictSmooth, fused Tridiag):
     a backward-stable tridiagonal solve has forward error <= kappa(M) * (a few unit roundoffs);
     here 4 u kappa(M), never tighter than the plain tolerance of the precision. The double-word
-    path runs levels with kappa(M) > 4000 in native FP64, so 1e-10 holds there as well."""
+    path runs levels with kappa(M) > 7000 (4 u kappa(M) > 1e-10) in native FP64, so 1e-10 holds there
+    as well."""
     return max(TOL[prec], 4.0 * UNIT_ROUNDOFF[prec] * kappa_M(cx, cy, v)) if prec == tpmg.F32 else TOL[prec]
 PRECS = [tpmg.F64, tpmg.DW, tpmg.F32]
 PREC_IDS = ["f64", "dw", "f32"]
