@@ -32,6 +32,10 @@ import numpy as np  # noqa: E402
 from paper_1402_3545_gb300 import workloads  # noqa: E402
 
 METRIC = "MG solve ms to 1e-6 rel. residual & % of HBM peak, FP64 vs mixed/learned"
+# dram__bytes_read.sum + dram__bytes_write.sum of one finest-level Smooth launch (k_sweep_x2,
+# double-word, tile variant 5) on the 512^2 x 128 problem: 1.5606 GB + 0.5152 GB
+PROFILED_SMOOTH_VARIANT = 5
+PROFILED_SMOOTH_TRAFFIC = 2075800000
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -387,6 +391,7 @@ def run_ours(args, rank, world, dist):
     peaks, peak_kind = measured_peaks()
     bytes_smooth = 3 * 8 * n  # read u, f; write u' (8-byte values)
     achieved = bytes_smooth / (t_smooth * 1e-3) / 1e9
+    finest_variant = variants_dw[-1] if variants_dw else None
     kernel_ms = {name: round(tpmg.time_kernel(op.op, prec, kid, reps=10), 4) for name, kid in [
         ("residual", tpmg.K_RESIDUAL), ("restrict_smooth", tpmg.K_RESTRICT_SMOOTH),
         ("prolongate", tpmg.K_PROLONGATE), ("cg_spmv", tpmg.K_CG_SPMV), ("cg_tridiag", tpmg.K_CG_TRIDIAG)]}
@@ -397,11 +402,17 @@ def run_ours(args, rank, world, dist):
         ("smooth", tpmg.K_SMOOTH), ("residual", tpmg.K_RESIDUAL), ("line_solve", tpmg.K_LINE_SOLVE),
         ("restrict_smooth", tpmg.K_RESTRICT_SMOOTH), ("prolongate", tpmg.K_PROLONGATE)]}
     n_smooth = 4 * iters[-1] + 1
+    # DRAM bytes of one launch from the ncu capture summarised in
+    # profiles/k_sweep_x2_dw_smooth_mid_512x512x128.md (tile variant 5; null for another variant)
+    traffic = PROFILED_SMOOTH_TRAFFIC if finest_variant == PROFILED_SMOOTH_VARIANT else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
-                "kernel": "k_smooth<PolDW> (finest level)", "peak_source": peak_kind,
-                "bytes_per_launch": bytes_smooth, "ms_per_launch": round(t_smooth, 4),
-                "share_of_solve": round(n_smooth * t_smooth / ms_per_step, 3)}
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                "kernel": f"finest-level double-word Smooth (tile variant {finest_variant})",
+                "peak_source": peak_kind, "bytes_per_launch": bytes_smooth, "ms_per_launch": round(t_smooth, 4),
+                "share_of_solve": round(n_smooth * t_smooth / ms_per_step, 3),
+                # lambda^2 varies over the level, so the Thomas factors 1/m_k and v/m_k are read per cell
+                "bytes_with_factors": 5 * 8 * n,
+                "frac_with_factors": round(5 * 8 * n / (t_smooth * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
 
     # end to end through the public API with host buffers: H2D of f, solve, D2H of u each step
     f_h = torch.from_numpy(f).pin_memory()
