@@ -321,8 +321,8 @@ static int run_sweep_pp(const Lv<P>& L, double coef, const typename P::S* u, con
 // halves the address arithmetic, the barriers and the loop control of the one-column kernel.
 // Shared ring per slot: u rows of stride UW = 68 (pad, left halo, 64 columns, right halo, pad),
 // rows j0-1 .. j0+TY; f pairs; 1/m_k pairs. Requires nx % 64 == 0 and 16-byte aligned fields.
-template <class P, class PO, int TY, int PD, int MODE>
-__global__ void __launch_bounds__(32 * TY) k_sweep_x2(Lv<P> L, double coef, const typename P::S* __restrict__ u,
+template <class P, class PO, int TY, int PD, int MODE, int MINB = 1>
+__global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef, const typename P::S* __restrict__ u,
                                                       const typename P::S* __restrict__ f,
                                                       typename PO::S* __restrict__ out, double* partials,
                                                       const int* done) {
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_x2(Lv<P> L, double coef, cons
     }
 }
 
-template <class P, class PO, int TY, int PD, int MODE>
+template <class P, class PO, int TY, int PD, int MODE, int MINB = 1>
 static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, const typename P::S* f,
                         typename PO::S* out, double* partials, const int* done, cudaStream_t s, int cap) {
     typedef typename P::S S;
@@ -539,7 +539,7 @@ static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, con
     const size_t fwd = (size_t)PD * ((HALO ? (TY + 2) * 68 : 0) + 2 * 32 * TY + (STACK ? 2 * 32 * TY : 0)) * sizeof(S);
     const size_t back = STACK ? (size_t)PD * 3 * 2 * 32 * TY * sizeof(S) : 0;
     const size_t smem = fwd > back ? fwd : back;
-    auto kern = k_sweep_x2<P, PO, TY, PD, MODE>;
+    auto kern = k_sweep_x2<P, PO, TY, PD, MODE, MINB>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int ntiles = (L.nx / 64) * (L.ny / TY);
     int per_sm = 0;
@@ -583,7 +583,7 @@ static int smooth_dispatch(const Lv<P>& L, double rho, const typename P::S* u, c
         if (nb >= 0) return nb;
     }
     if (v == 6 && L.gstack) {
-        const int nb = run_sweep_x2<P, P, 1, 6, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s, 16);
+        const int nb = run_sweep_x2<P, P, 2, 4, MODE_SMOOTH, 10>(L, rho, u, f, uo, partials, done, s, 12);
         if (nb >= 0) return nb;
     }
     if (P::id == 1) {  // FP32
@@ -618,7 +618,7 @@ template <class P, class PO>
 int launch_residual_pp(const Lv<P>& L, const typename P::S* u, const typename P::S* f, typename PO::S* r,
                        double* partials, const int* done, cudaStream_t s) {
     // two columns per thread when the level allows it (nx % 64 == 0, 16-byte aligned fields)
-    const int nb = run_sweep_x2<P, PO, 2, 4, MODE_RESIDUAL>(L, 1.0, u, f, r, partials, done, s, 8);
+    const int nb = run_sweep_x2<P, PO, 2, 4, MODE_RESIDUAL>(L, 1.0, u, f, r, partials, done, s, 16);
     if (nb >= 0) return nb;
     if (!pp_fits<P, 4, false>(L)) return -1;
     return run_sweep_pp<P, PO, 4, 6, MODE_RESIDUAL>(L, 1.0, u, f, r, partials, done, s);
