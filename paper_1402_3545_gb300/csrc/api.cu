@@ -1252,13 +1252,15 @@ struct BatchCache {
     int* d_flags = nullptr;     // error, n_active
     int* h_flags = nullptr;     // pinned: initial flags and results
     double* d_hist = nullptr;
+    float* d_scratch = nullptr;  // the persistent blocks' Thomas stacks
     cudaGraphExec_t graph = nullptr;
     unsigned long long graph_kernels = 0;
     std::vector<BTask> h_tasks;
     std::vector<int> h_phase_begin, h_phase_tiles;
     ~BatchCache() {
         if (graph) cudaGraphExecDestroy(graph);
-        void* ptrs[] = {d_probs, d_state, d_tasks, d_phase_begin, d_phase_tiles, d_partials, d_bar, d_flags, d_hist};
+        void* ptrs[] = {d_probs,    d_state, d_tasks, d_phase_begin, d_phase_tiles, d_partials,
+                        d_bar,      d_flags, d_hist,  d_scratch};
         for (void* p : ptrs)
             if (p) cudaFree(p);
         if (h_state) cudaFreeHost(h_state);
@@ -1431,12 +1433,13 @@ static tpmg_status build_batch(BatchCache* bc, const tpmg_params* prm) {
                   cudaMemcpyHostToDevice));
     CK(cudaMemcpy(bc->d_phase_tiles, bc->h_phase_tiles.data(), sizeof(int) * bc->h_phase_tiles.size(),
                   cudaMemcpyHostToDevice));
-    bc->smem = batched_smem(nz_max);
-    int per_sm = batched_blocks_per_sm(nz_max);
+    bc->smem = 0;
+    int per_sm = batched_blocks_per_sm();
     int nsm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, bc->ops[0]->device));
-    if (per_sm < 1) return set_err(TPMG_ERR_ARG, "batched kernel does not fit on an SM (nz too large)");
+    if (per_sm < 1) return set_err(TPMG_ERR_ARG, "batched kernel does not fit on an SM");
     bc->grid = per_sm * nsm;
+    TRY(dalloc((void**)&bc->d_scratch, sizeof(float) * batched_scratch_floats(bc->grid, nz_max)));
     return TPMG_OK;
 }
 
@@ -1511,6 +1514,7 @@ extern "C" tpmg_status tpmg_mg_solve_batched(int nprob, tpmg_op* const* ops, con
     d.max_iter = prm->max_iter;
     d.timeout_ns = (unsigned long long)(timeout_s * 1e9);
     d.nz_max = bc->nz_max;
+    d.scratch = bc->d_scratch;
     std::vector<const void*> io_key;
     for (int b = 0; b < nprob; ++b) {
         io_key.push_back(f[b]);

@@ -12,7 +12,8 @@
 //
 // One thread per column sweeps k with the Thomas recurrence (precomputed factors: a table of nz
 // entries when lambda^2 is constant on the level, which is the batched workload's case), the
-// forward-eliminated values on a shared-memory stack.
+// forward-eliminated values on a per-block stack in global scratch (L2-resident; a stack in shared
+// memory would leave room for only three blocks per SM).
 #include "kernels.cuh"
 
 namespace tpmg {
@@ -266,8 +267,7 @@ __device__ void t_final(const BatchDesc& d, int prob, int it) {
 
 // ---------------------------------------------------------------- the persistent kernel
 __global__ void __launch_bounds__(32 * BTY) k_batched(BatchDesc d) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* stack = reinterpret_cast<float*>(smem_raw);
+    float* stack = d.scratch + (size_t)blockIdx.x * d.nz_max * 32 * BTY;
     __shared__ double red[32];
     const float rho = (float)d.rho;
     for (int it = 0; it <= d.max_iter; ++it) {
@@ -331,18 +331,15 @@ __global__ void __launch_bounds__(32 * BTY) k_batched(BatchDesc d) {
     }
 }
 
-size_t batched_smem(int nz_max) { return (size_t)nz_max * 32 * BTY * sizeof(float); }
-
-int batched_blocks_per_sm(int nz_max) {
-    const size_t smem = batched_smem(nz_max);
-    cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+int batched_blocks_per_sm() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batched, 32 * BTY, smem) != cudaSuccess) return 0;
-    return nb;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batched, 32 * BTY, 0) != cudaSuccess) return 0;
+    return nb < 8 ? nb : 8;  // 8 x 128 threads per SM; more only grows the scratch
 }
 
+size_t batched_scratch_floats(int grid, int nz_max) { return (size_t)grid * nz_max * 32 * BTY; }
+
 cudaError_t launch_batched(const BatchDesc& d, int grid, size_t smem, cudaStream_t s) {
-    cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     BatchDesc arg = d;
     void* args[] = {&arg};
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_batched, dim3(grid), dim3(32, BTY), args, smem, s);

@@ -263,11 +263,13 @@ struct BatchDesc {
     int max_iter;
     unsigned long long timeout_ns;
     int nz_max;
+    float* scratch;  // Thomas stacks: nz_max x 32 BTY floats per block
 };
 // cooperative launch of the persistent kernel; returns the CUDA status of the launch
 cudaError_t launch_batched(const BatchDesc& d, int grid, size_t smem, cudaStream_t s);
-size_t batched_smem(int nz_max);
-int batched_blocks_per_sm(int nz_max);
+// blocks per SM of the persistent kernel (its stacks live in the scratch, so registers decide)
+int batched_blocks_per_sm();
+size_t batched_scratch_floats(int grid, int nz_max);
 
 // ---------------------------------------------------------------- scalar kernels (k_util.cu)
 // modes of finalize_norm
