@@ -248,6 +248,7 @@ static tpmg_status ensure_io(tpmg_op* op) {
 }
 
 static tpmg_status ensure_cg(tpmg_op* op, int pid) {
+    TRY(ensure_factors(op, pid));  // the fused Tridiag reads the precomputed Thomas factors
     size_t bytes = lvl_cells(op, op->g.L) * elem_bytes(pid);
     for (int t = 0; t < 4; ++t) TRY(dalloc(&op->cgbuf[pid][t], bytes));
     if (pid == 2) TRY(ensure_hier(op, 2, true));  // DW fine u, f copies live in the DW hierarchy
@@ -515,8 +516,8 @@ static tpmg_status cg_loop(tpmg_op* op, const tpmg_params* prm, typename P::S* u
     const int L = op->g.L;
     const size_t n = lvl_cells(op, L);
     Lv<P> LL = level_view<P>(op, L);
-    const int nb_spmv = sweep_shape(LL.nx, LL.ny, LL.nz, sizeof(typename P::R), false).nblocks();
-    const int nb_tri = sweep_shape(LL.nx, LL.ny, LL.nz, sizeof(typename P::R), true).nblocks();
+    const int nb_spmv = cg_spmv_blocks(LL);
+    const int nb_tri = cg_tridiag_blocks(LL);
     launch_scalars_init(op->sc, prm->tol, prm->max_iter, s);
     launch_residual<P, P>(LL, u, f, r, nullptr, nullptr, s);
     CK(cudaMemsetAsync(p, 0, n * sizeof(S), s));
@@ -922,9 +923,8 @@ tpmg_status tpmg_cg_fused_spmv(tpmg_op* op, tpmg_precision prec, double alpha, d
         auto* pi = in_ptr<P>(op, s, 1, p, n);
         auto* zi = in_ptr<P>(op, s, 2, z, n);
         auto* qi = in_ptr<P>(op, s, 3, q, n);
-        launch_cg_spmv<P>(LL, op->sc, ui, pi, zi, qi, op->partials, s);
-        launch_finalize_norm(op->partials, sweep_shape(LL.nx, LL.ny, LL.nz, sizeof(typename P::R), false).nblocks(),
-                             FIN_SUM, op->sc, nullptr, sigma_out, s);
+        const int nb = launch_cg_spmv<P>(LL, op->sc, ui, pi, zi, qi, op->partials, s);
+        launch_finalize_norm(op->partials, nb, FIN_SUM, op->sc, nullptr, sigma_out, s);
         out_back<P>(op, s, 0, u, n);
         out_back<P>(op, s, 1, p, n);
         out_back<P>(op, s, 3, q, n);
@@ -948,8 +948,7 @@ tpmg_status tpmg_cg_fused_tridiag(tpmg_op* op, tpmg_precision prec, double alpha
         auto* ri = in_ptr<P>(op, s, 0, r, n);
         auto* qi = in_ptr<P>(op, s, 1, q, n);
         auto* zo = out_ptr<P>(op, 2, z);
-        launch_cg_tridiag<P>(LL, op->sc, ri, qi, zo, op->partials, s);
-        const int nb = sweep_shape(LL.nx, LL.ny, LL.nz, sizeof(typename P::R), true).nblocks();
+        const int nb = launch_cg_tridiag<P>(LL, op->sc, ri, qi, zo, op->partials, s);
         launch_finalize_norm(op->partials, nb, FIN_SUM, op->sc, nullptr, rr_out, s);
         launch_finalize_norm(op->partials + nb, nb, FIN_SUM, op->sc, nullptr, rz_out, s);
         out_back<P>(op, s, 0, r, n);

@@ -113,6 +113,57 @@ __global__ void __launch_bounds__(256) k_cg_tridiag(Lv<P> L, const Scalars* __re
     }
 }
 
+// The same fused Tridiag with the level's precomputed Thomas factors (1/m_k, v/m_k) and the
+// forward-eliminated values on a per-block stack in the global scratch (L.gstack): a persistent
+// grid of a few blocks per SM loops over tiles of 32 x 4 columns. No reciprocal per cell and no
+// shared-memory stack, so the SM holds as many warps as its registers allow.
+template <class P>
+__global__ void __launch_bounds__(128) k_cg_tridiag_gs(Lv<P> L, const Scalars* __restrict__ sc,
+                                                       typename P::S* __restrict__ r,
+                                                       const typename P::S* __restrict__ q,
+                                                       typename P::S* __restrict__ z, double* partials) {
+    typedef typename P::R R;
+    typedef typename P::S S;
+    if (*(volatile const int*)&sc->done) return;
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int tiles_x = (nx + 31) / 32, ntiles = tiles_x * ((ny + 3) / 4);
+    const size_t pl = (size_t)nx * ny;
+    const bool percol = L.fac_percol != 0;
+    S* gst = reinterpret_cast<S*>(L.gstack) + (size_t)blockIdx.x * nz * 128;
+    const R nalpha = P::neg(P::cst(sc->alpha));
+    typename P::Acc arr = 0, crr = 0, arz = 0, crz = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int i = (tile % tiles_x) * 32 + threadIdx.x, j = (tile / tiles_x) * 4 + threadIdx.y;
+        if (i >= nx || j >= ny) continue;
+        const size_t c = (size_t)j * nx + i;
+        const R vv = P::ld(L.v, c);
+        R d_prev = P::zero();
+        for (int k = 0; k < nz; ++k) {
+            const size_t id = (size_t)k * pl + c;
+            const R rn = P::fma(nalpha, P::ld(q, id), P::ld_plain(r, id));
+            P::st(r, id, rn);
+            P::acc_dot(arr, crr, rn, rn);
+            const R inv = P::ld(L.finv, percol ? id : (size_t)k);
+            d_prev = P::mul(P::fma(vv, d_prev, rn), inv);
+            P::st(gst, (size_t)k * 128 + tid, d_prev);
+        }
+        R xn = P::zero();
+        for (int k = nz - 1; k >= 0; --k) {
+            const size_t id = (size_t)k * pl + c;
+            xn = P::fma(P::ld(L.fw, percol ? id : (size_t)k), xn, P::ld_plain(gst, (size_t)k * 128 + tid));
+            P::st(z, id, xn);
+            P::acc_dot(arz, crz, P::ld_plain(r, id), xn);
+        }
+    }
+    double s1 = block_sum(P::acc_get(arr, crr));
+    double s2 = block_sum(P::acc_get(arz, crz));
+    if (tid == 0) {
+        partials[blockIdx.x] = s1;
+        partials[gridDim.x + blockIdx.x] = s2;
+    }
+}
+
 // u <- u + alpha p : the lagged solution update after the last iteration.
 template <class P>
 __global__ void k_cg_finish(size_t n, const Scalars* __restrict__ sc, typename P::S* __restrict__ u,
@@ -123,20 +174,52 @@ __global__ void k_cg_finish(size_t n, const Scalars* __restrict__ sc, typename P
 }
 
 template <class P>
-void launch_cg_spmv(const Lv<P>& L, const Scalars* sc, typename P::S* u, typename P::S* p,
-                    const typename P::S* z, typename P::S* q, double* partials, cudaStream_t s) {
+int cg_spmv_blocks(const Lv<P>& L) {
+    return sweep_shape(L.nx, L.ny, L.nz, sizeof(typename P::R), false).nblocks();
+}
+template <class P>
+int launch_cg_spmv(const Lv<P>& L, const Scalars* sc, typename P::S* u, typename P::S* p,
+                   const typename P::S* z, typename P::S* q, double* partials, cudaStream_t s) {
     Shape sh = sweep_shape(L.nx, L.ny, L.nz, sizeof(typename P::R), false);
     k_cg_spmv<P><<<sh.grid, sh.block, 0, s>>>(L, sc, u, p, z, q, partials);
     note_launch();
+    return sh.nblocks();
+}
+// blocks of the fused Tridiag (= partial sums per quantity); the persistent form when the level has
+// its factors and the scratch
+template <class P>
+int cg_tridiag_blocks(const Lv<P>& L) {
+    if (L.gstack && L.finv && L.fw) {
+        static int per_sm = 0;
+        if (per_sm == 0) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_tridiag_gs<P>, 128, 0);
+            if (per_sm > GS_BLOCKS_PER_SM) per_sm = GS_BLOCKS_PER_SM;
+            if (per_sm < 1) per_sm = 1;
+        }
+        int nsm = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const int ntiles = ((L.nx + 31) / 32) * ((L.ny + 3) / 4);
+        const int nb = nsm * per_sm;
+        return nb < ntiles ? nb : ntiles;
+    }
+    return sweep_shape(L.nx, L.ny, L.nz, sizeof(typename P::R), true).nblocks();
 }
 template <class P>
-void launch_cg_tridiag(const Lv<P>& L, const Scalars* sc, typename P::S* r, const typename P::S* q,
-                       typename P::S* z, double* partials, cudaStream_t s) {
+int launch_cg_tridiag(const Lv<P>& L, const Scalars* sc, typename P::S* r, const typename P::S* q,
+                      typename P::S* z, double* partials, cudaStream_t s) {
+    if (L.gstack && L.finv && L.fw) {
+        const int nb = cg_tridiag_blocks(L);
+        k_cg_tridiag_gs<P><<<nb, dim3(32, 4), 0, s>>>(L, sc, r, q, z, partials);
+        note_launch();
+        return nb;
+    }
     Shape sh = sweep_shape(L.nx, L.ny, L.nz, sizeof(typename P::R), true);
     if (sh.smem > 32 * 1024)
         cudaFuncSetAttribute(k_cg_tridiag<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
     k_cg_tridiag<P><<<sh.grid, sh.block, sh.smem, s>>>(L, sc, r, q, z, partials);
     note_launch();
+    return sh.nblocks();
 }
 template <class P>
 void launch_cg_finish(size_t n, const Scalars* sc, typename P::S* u, const typename P::S* p,
@@ -148,10 +231,12 @@ void launch_cg_finish(size_t n, const Scalars* sc, typename P::S* u, const typen
 }
 
 #define TPMG_CG_INST(P)                                                                             \
-    template void launch_cg_spmv<P>(const Lv<P>&, const Scalars*, P::S*, P::S*, const P::S*, P::S*, \
-                                    double*, cudaStream_t);                                        \
-    template void launch_cg_tridiag<P>(const Lv<P>&, const Scalars*, P::S*, const P::S*, P::S*,     \
-                                       double*, cudaStream_t);                                     \
+    template int cg_spmv_blocks<P>(const Lv<P>&);                                                   \
+    template int cg_tridiag_blocks<P>(const Lv<P>&);                                                \
+    template int launch_cg_spmv<P>(const Lv<P>&, const Scalars*, P::S*, P::S*, const P::S*, P::S*,  \
+                                   double*, cudaStream_t);                                         \
+    template int launch_cg_tridiag<P>(const Lv<P>&, const Scalars*, P::S*, const P::S*, P::S*,      \
+                                      double*, cudaStream_t);                                      \
     template void launch_cg_finish<P>(size_t, const Scalars*, P::S*, const P::S*, cudaStream_t);
 
 TPMG_CG_INST(PolF64)

@@ -198,12 +198,17 @@ template <class P>
 void launch_correct(size_t n, typename P::S* u, const float* e, const int* done, cudaStream_t s);
 
 // ---------------------------------------------------------------- launchers (k_cg.cu)
+// each returns its number of blocks (partial sums per reduced quantity; *_blocks predicts it)
 template <class P>
-void launch_cg_spmv(const Lv<P>& L, const Scalars* sc, typename P::S* u, typename P::S* p,
-                    const typename P::S* z, typename P::S* q, double* partials, cudaStream_t s);
+int cg_spmv_blocks(const Lv<P>& L);
 template <class P>
-void launch_cg_tridiag(const Lv<P>& L, const Scalars* sc, typename P::S* r, const typename P::S* q,
-                       typename P::S* z, double* partials, cudaStream_t s);
+int cg_tridiag_blocks(const Lv<P>& L);
+template <class P>
+int launch_cg_spmv(const Lv<P>& L, const Scalars* sc, typename P::S* u, typename P::S* p,
+                   const typename P::S* z, typename P::S* q, double* partials, cudaStream_t s);
+template <class P>
+int launch_cg_tridiag(const Lv<P>& L, const Scalars* sc, typename P::S* r, const typename P::S* q,
+                      typename P::S* z, double* partials, cudaStream_t s);
 template <class P>
 void launch_cg_finish(size_t n, const Scalars* sc, typename P::S* u, const typename P::S* p,
                       cudaStream_t s);
