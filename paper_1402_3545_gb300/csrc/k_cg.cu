@@ -61,6 +61,69 @@ __global__ void __launch_bounds__(256) k_cg_spmv(Lv<P> L, const Scalars* __restr
     if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
+// The fused SpMV pointwise: the stencil has no recurrence along the column, so every pair of
+// x-adjacent cells of a plane is a thread (grid-stride over the pairs, a fixed number of blocks for
+// the partial sums); neighbours come through the read-only cache. Requires nx even.
+template <class P>
+__global__ void __launch_bounds__(256) k_cg_spmv_cell(Lv<P> L, const Scalars* __restrict__ sc,
+                                                      typename P::S* __restrict__ u, typename P::S* __restrict__ p,
+                                                      const typename P::S* __restrict__ z,
+                                                      typename P::S* __restrict__ q, double* partials) {
+    typedef typename P::R R;
+    if (*(volatile const int*)&sc->done) return;
+    const int nx = L.nx, ny = L.ny, nz = L.nz, hx2 = nx / 2;
+    const size_t pl = (size_t)nx * ny, npairs = (size_t)hx2 * ny * nz;
+    const R alpha = P::cst(sc->alpha), beta = P::cst(sc->beta);
+    const R cx = P::cst(L.cx), cy = P::cst(L.cy);
+    const R dh = P::cst(1.0 + 2.0 * L.cx + 2.0 * L.cy);
+    const bool iso = L.cx == L.cy;
+    typename P::Acc acc = 0, cmp = 0;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < npairs; t += (size_t)gridDim.x * blockDim.x) {
+        const int ip = (int)(t % hx2), j = (int)((t / hx2) % ny), k = (int)(t / ((size_t)hx2 * ny));
+        const int i = 2 * ip;
+        const size_t c = (size_t)j * nx + i, b = (size_t)k * pl, id = b + c;
+        const size_t rs = (size_t)wrapc(j - 1, ny) * nx + i, rn = (size_t)wrapc(j + 1, ny) * nx + i;
+        const R z0 = P::ld(z, id), z1 = P::ld(z, id + 1);
+        const R zw = P::ld(z, b + (size_t)j * nx + wrapc(i - 1, nx)), ze = P::ld(z, b + (size_t)j * nx + wrapc(i + 2, nx));
+        const R zs0 = P::ld(z, b + rs), zs1 = P::ld(z, b + rs + 1), zn0 = P::ld(z, b + rn), zn1 = P::ld(z, b + rn + 1);
+        R zm0 = P::zero(), zm1 = P::zero(), zp0 = P::zero(), zp1 = P::zero();
+        if (k > 0) {
+            zm0 = P::ld(z, id - pl);
+            zm1 = P::ld(z, id - pl + 1);
+        }
+        if (k + 1 < nz) {
+            zp0 = P::ld(z, id + pl);
+            zp1 = P::ld(z, id + pl + 1);
+        }
+        const R v0 = P::ld(L.v, c), v1 = P::ld(L.v, c + 1);
+        R d0 = dh, d1 = dh;
+        if (k > 0) {
+            d0 = P::add(d0, v0);
+            d1 = P::add(d1, v1);
+        }
+        if (k + 1 < nz) {
+            d0 = P::add(d0, v0);
+            d1 = P::add(d1, v1);
+        }
+        // A z = -(f - A z) with f = 0: the sweep residual of a zero right-hand side, negated
+        const R az0 = P::neg(sweep_residual<P>(P::zero(), d0, z0, zw, z1, zs0, zn0, zm0, zp0, cx, cy, v0, iso));
+        const R az1 = P::neg(sweep_residual<P>(P::zero(), d1, z1, z0, ze, zs1, zn1, zm1, zp1, cx, cy, v1, iso));
+        const R po0 = P::ld_plain(p, id), po1 = P::ld_plain(p, id + 1);
+        P::st(u, id, P::fma(alpha, po0, P::ld_plain(u, id)));
+        P::st(u, id + 1, P::fma(alpha, po1, P::ld_plain(u, id + 1)));
+        const R pn0 = P::fma(beta, po0, z0), pn1 = P::fma(beta, po1, z1);
+        const R qn0 = P::fma(beta, P::ld_plain(q, id), az0), qn1 = P::fma(beta, P::ld_plain(q, id + 1), az1);
+        P::st(p, id, pn0);
+        P::st(p, id + 1, pn1);
+        P::st(q, id, qn0);
+        P::st(q, id + 1, qn1);
+        P::acc_dot(acc, cmp, pn0, qn0);
+        P::acc_dot(acc, cmp, pn1, qn1);
+    }
+    const double s = block_sum(P::acc_get(acc, cmp));
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 template <class P>
 __global__ void __launch_bounds__(256) k_cg_tridiag(Lv<P> L, const Scalars* __restrict__ sc,
                                                     typename P::S* __restrict__ r,
@@ -173,13 +236,25 @@ __global__ void k_cg_finish(size_t n, const Scalars* __restrict__ sc, typename P
         P::st(u, t, P::add(P::ld_plain(u, t), P::mul(alpha, P::ld(p, t))));
 }
 
+// the pointwise SpMV for the FP32-pipe policies (native FP64 keeps the column kernel, which reuses
+// the vertical neighbours from registers and runs faster on the slow FP64 pipe)
 template <class P>
 int cg_spmv_blocks(const Lv<P>& L) {
+    if (L.nx % 2 == 0 && P::id != 0) {
+        const size_t b = ((size_t)L.nx / 2 * L.ny * L.nz + 255) / 256;
+        return (int)(b < 152 * 8 ? (b ? b : 1) : 152 * 8);
+    }
     return sweep_shape(L.nx, L.ny, L.nz, sizeof(typename P::R), false).nblocks();
 }
 template <class P>
 int launch_cg_spmv(const Lv<P>& L, const Scalars* sc, typename P::S* u, typename P::S* p,
                    const typename P::S* z, typename P::S* q, double* partials, cudaStream_t s) {
+    if (L.nx % 2 == 0 && P::id != 0) {
+        const int nb = cg_spmv_blocks(L);
+        k_cg_spmv_cell<P><<<nb, 256, 0, s>>>(L, sc, u, p, z, q, partials);
+        note_launch();
+        return nb;
+    }
     Shape sh = sweep_shape(L.nx, L.ny, L.nz, sizeof(typename P::R), false);
     k_cg_spmv<P><<<sh.grid, sh.block, 0, s>>>(L, sc, u, p, z, q, partials);
     note_launch();
