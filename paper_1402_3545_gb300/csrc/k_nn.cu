@@ -4,12 +4,12 @@
 //
 // Activations are channels-last BF16 (16 channels = 32 bytes per cell, cell index (k*ny + j)*nx + i);
 // weights are BF16 copies of FP32 master parameters; all sums accumulate in FP32.
-// The 16 -> 16 layers are implicit GEMMs on the tensor cores: a block computes a tile of 64 x 2
-// cells of one plane; each warp owns 16 consecutive cells (the M = 16 rows of mma.m16n8k16), the
-// K dimension runs over the 27 taps x 16 input channels, N = 16 output channels (two n8 tiles).
-// The input tile with its one-cell halo (66 x 4 x 3 cells) and the 27 x 16 x 16 weights are staged
-// in shared memory and fed to the MMAs with ldmatrix. The same kernel computes the data gradient
-// of the backward pass with flipped, transposed weights and a ReLU-mask epilogue. The weight
+// The 16 -> 16 layers are implicit GEMMs on the tensor cores: a block computes tiles of 64 x 2
+// cells, plane after plane; each warp owns 16 consecutive cells (the M = 16 rows of
+// mma.m16n8k16), the K dimension runs over the 27 taps x 16 input channels, N = 16 output channels
+// (two n8 tiles). The 27 x 16 x 16 weights and the input planes with their one-cell halo (66 x 4
+// cells) are staged in shared memory and fed to the MMAs with ldmatrix. The same kernel computes
+// the data gradient of the backward pass with flipped, transposed weights and a ReLU-mask epilogue. The weight
 // gradients of the 16 -> 16 layers are tensor-core GEMMs too (cells are the K dimension).
 #include <cuda_bf16.h>
 
@@ -67,130 +67,441 @@ __device__ void load_halo16(const __nv_bfloat16* __restrict__ act, int nx, int n
     }
 }
 
-// ---------------------------------------------------------------- 16 -> 16 convolution (tensor cores)
-// EPI_RELU: out = bf16(relu(acc + bias)); EPI_MASK: out = bf16(mask > 0 ? acc : 0) (data gradient)
+// ---------------------------------------------------------------- 16 -> 16, marching in z
+// The same implicit GEMM as k_conv16, but a persistent block stages the weights once and walks
+// whole columns of tiles: it keeps the planes k-1, k, k+1 of its 66 x 4 halo tile in a 4-slot ring
+// and fetches plane k+2 with cp.async while the tensor cores work on plane k, so every input plane
+// is read once per tile (not three times) and the loads overlap the MMAs.
+__device__ __forceinline__ unsigned sa_nn(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa_nn(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_commit_nn() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait_nn() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+static constexpr int PLANE_CELLS = HX * HY;        // 66 x 4 cells of one halo plane
+static constexpr int PLANE_BYTES = PLANE_CELLS * 32;
+
 template <int EPI>
-__global__ void __launch_bounds__(256) k_conv16(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Wt,
-                                                const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask,
-                                                __nv_bfloat16* __restrict__ out, int nx, int ny, int nz) {
+__global__ void __launch_bounds__(256) k_conv16z(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Wt,
+                                                 const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask,
+                                                 __nv_bfloat16* __restrict__ out, int nx, int ny, int nz) {
     extern __shared__ __align__(16) unsigned char smem[];
-    unsigned char* H = smem;
-    unsigned char* Ws = smem + HALO_BYTES;
-    const int x0 = blockIdx.x * TXC, y0 = blockIdx.y * TYC, k = blockIdx.z;
-    for (int q = threadIdx.x; q < W_BYTES / 16; q += blockDim.x)
+    unsigned char* Ws = smem;
+    unsigned char* ring = smem + W_BYTES;  // 4 planes
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int q = tid; q < W_BYTES / 16; q += blockDim.x)
         reinterpret_cast<uint4*>(Ws)[q] = __ldg(reinterpret_cast<const uint4*>(Wt) + q);
-    load_halo16(in, nx, ny, nz, x0, y0, k, H);
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_x = nx / TXC, ntiles = tiles_x * (ny / TYC);
     const int yw = warp >> 2, xw = (warp & 3) * 16;
-    float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
-    const int ar = lane & 15, acol = (lane >> 4) * 8;                       // A: row, column block
-    const int bco = ((lane >> 4) << 3) + (lane & 7), bci = ((lane >> 3) & 1) * 8;  // B: out, in channel
-#pragma unroll 1
-    for (int dz = 0; dz < 3; ++dz)
-#pragma unroll 1
-        for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-                const int tap = (dz * 3 + dy) * 3 + dx;
-                const int cell = (dz * HY + yw + dy) * HX + xw + ar + dx;
-                uint32_t a0, a1, a2, a3, b0, b1, b2, b3;
-                ldm_x4(saddr(H + cell * 32 + acol * 2), a0, a1, a2, a3);
-                ldm_x4(saddr(Ws + ((tap * 16 + bco) * 16 + bci) * 2), b0, b1, b2, b3);
-                mma16816(c0, a0, a1, a2, a3, b0, b1);
-                mma16816(c1, a0, a1, a2, a3, b2, b3);
-            }
-    // epilogue: lane holds cells g, g+8 and channel pairs 2t, 2t+1 (+8 for the second n tile)
+    const int ar = lane & 15, acol = (lane >> 4) * 8;
+    const int bco = ((lane >> 4) << 3) + (lane & 7), bci = ((lane >> 3) & 1) * 8;
     const int g = lane >> 2, t2 = (lane & 3) * 2;
-    const int y = y0 + yw;
-    if (y >= ny) return;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int x = x0 + xw + g + 8 * h;
-        if (x >= nx) continue;
-        const size_t p = ((size_t)k * ny + y) * nx + x;
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            const float* c = nt ? c1 : c0;
-            const int co = t2 + 8 * nt;
-            float v0 = c[2 * h], v1 = c[2 * h + 1];
-            if (EPI == EPI_RELU) {
-                v0 = fmaxf(v0 + __ldg(bias + co), 0.f);
-                v1 = fmaxf(v1 + __ldg(bias + co + 1), 0.f);
-            } else {
-                const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(mask + p * 16 + co);
-                if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
-                if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
+    float bco0 = 0.f, bco1 = 0.f, bco8 = 0.f, bco9 = 0.f;
+    if (EPI == EPI_RELU) {
+        bco0 = __ldg(bias + t2);
+        bco1 = __ldg(bias + t2 + 1);
+        bco8 = __ldg(bias + t2 + 8);
+        bco9 = __ldg(bias + t2 + 9);
+    }
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (tile % tiles_x) * TXC, y0 = (tile / tiles_x) * TYC;
+        // plane kk of the tile into ring slot (kk + 1) & 3 (zeros beyond the z ends)
+        auto load_plane = [&](int kk) {
+            unsigned char* P = ring + ((kk + 1) & 3) * PLANE_BYTES;
+            for (int q = tid; q < PLANE_CELLS * 2; q += blockDim.x) {
+                const int v = q >> 1, half = q & 1;
+                const int xx = v % HX, yy = v / HX;
+                if (kk >= 0 && kk < nz) {
+                    const int i = nwrap(x0 - 1 + xx, nx), j = nwrap(y0 - 1 + yy, ny);
+                    cp16(P + (size_t)q * 16, in + (((size_t)kk * ny + j) * nx + i) * 16 + half * 8);
+                } else {
+                    reinterpret_cast<uint4*>(P)[q] = make_uint4(0, 0, 0, 0);
+                }
             }
-            *reinterpret_cast<__nv_bfloat162*>(out + p * 16 + co) = __floats2bfloat162_rn(v0, v1);
+            cp_commit_nn();
+        };
+        __syncthreads();  // the previous tile's ring (and, first time, the weights) are settled
+        load_plane(-1);
+        load_plane(0);
+        load_plane(1);
+        for (int k = 0; k < nz; ++k) {
+            load_plane(k + 2);  // into the slot of plane k-2, read by nobody now
+            cp_wait_nn<1>();    // planes up to k+1 have landed (this thread's copies)
+            __syncthreads();    // ... and every other thread's
+            float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+            for (int dz = 0; dz < 3; ++dz) {
+                const unsigned char* H = ring + ((k + dz) & 3) * PLANE_BYTES;  // plane k - 1 + dz
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const int tap = (dz * 3 + dy) * 3 + dx;
+                        const int cell = (yw + dy) * HX + xw + ar + dx;
+                        uint32_t a0, a1, a2, a3, b0, b1, b2, b3;
+                        ldm_x4(saddr(H + cell * 32 + acol * 2), a0, a1, a2, a3);
+                        ldm_x4(saddr(Ws + ((tap * 16 + bco) * 16 + bci) * 2), b0, b1, b2, b3);
+                        mma16816(c0, a0, a1, a2, a3, b0, b1);
+                        mma16816(c1, a0, a1, a2, a3, b2, b3);
+                    }
+            }
+            const int y = y0 + yw;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int x = x0 + xw + g + 8 * h;
+                const size_t p = ((size_t)k * ny + y) * nx + x;
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    const float* c = nt ? c1 : c0;
+                    const int co = t2 + 8 * nt;
+                    float v0 = c[2 * h], v1 = c[2 * h + 1];
+                    if (EPI == EPI_RELU) {
+                        v0 = fmaxf(v0 + (nt ? bco8 : bco0), 0.f);
+                        v1 = fmaxf(v1 + (nt ? bco9 : bco1), 0.f);
+                    } else {
+                        const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(mask + p * 16 + co);
+                        if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
+                        if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
+                    }
+                    *reinterpret_cast<__nv_bfloat162*>(out + p * 16 + co) = __floats2bfloat162_rn(v0, v1);
+                }
+            }
+            __syncthreads();  // the slot of plane k-1 is refilled by the next step's load
+        }
+        cp_wait_nn<0>();
+    }
+}
+
+static int conv16z_grid(int nx, int ny) {
+    static int per_sm = 0, nsm = 0;
+    const size_t smem = W_BYTES + 4 * PLANE_BYTES;
+    if (per_sm == 0) {
+        cudaFuncSetAttribute(k_conv16z<EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_conv16z<EPI_MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv16z<EPI_RELU>, 256, smem);
+        if (per_sm < 1) per_sm = 1;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const int ntiles = (nx / TXC) * (ny / TYC);
+    const int nb = per_sm * nsm;
+    return nb < ntiles ? nb : ntiles;
+}
+
+// ---------------------------------------------------------------- thin layers, marching in z
+// The first layer (cin -> 16), the last (16 -> 1) and their weight gradients in the persistent
+// z-marching form of k_conv16z: a block of 128 threads owns a 64 x 2 tile, one cell per thread,
+// keeps the input planes k-1, k, k+1 (one-cell halo) in a 4-slot ring and the weights in shared
+// memory as FP32, so every input value is read from memory once per tile and the weight reads are
+// shared-memory broadcasts.
+static constexpr int TCELLS = TXC * TYC;  // 128 cells per tile plane
+
+// thin input (C = 1 or 2 channels, bf16): plane kk of the tile into ring slot (kk + 1) & 3
+template <int C>
+__device__ __forceinline__ void load_thin(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* ring, int nx, int ny,
+                                          int nz, int x0, int y0, int kk) {
+    __nv_bfloat16* P = ring + ((kk + 1) & 3) * (PLANE_CELLS * C);
+    for (int q = threadIdx.x; q < PLANE_CELLS; q += blockDim.x) {
+        const int xx = q % HX, yy = q / HX;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+            if (kk >= 0 && kk < nz) {
+                const int i = nwrap(x0 - 1 + xx, nx), j = nwrap(y0 - 1 + yy, ny);
+                v = in[(((size_t)kk * ny + j) * nx + i) * C + c];
+            }
+            P[q * C + c] = v;
+        }
+    }
+}
+// 16-channel input: plane kk into slot (kk + 1) & 3 with 16-byte cp.async (zeros beyond the ends)
+__device__ __forceinline__ void load_wide(const __nv_bfloat16* __restrict__ in, unsigned char* ring, int nx, int ny,
+                                          int nz, int x0, int y0, int kk) {
+    unsigned char* P = ring + ((kk + 1) & 3) * PLANE_BYTES;
+    for (int q = threadIdx.x; q < PLANE_CELLS * 2; q += blockDim.x) {
+        const int v = q >> 1, half = q & 1;
+        const int xx = v % HX, yy = v / HX;
+        if (kk >= 0 && kk < nz) {
+            const int i = nwrap(x0 - 1 + xx, nx), j = nwrap(y0 - 1 + yy, ny);
+            cp16(P + (size_t)q * 16, in + (((size_t)kk * ny + j) * nx + i) * 16 + half * 8);
+        } else {
+            reinterpret_cast<uint4*>(P)[q] = make_uint4(0, 0, 0, 0);
+        }
+    }
+    cp_commit_nn();
+}
+
+static int thin_grid(int nx, int ny, int cap) {
+    int nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int ntiles = (nx / TXC) * (ny / TYC);
+    int nb = nsm * 8;
+    if (nb > cap) nb = cap;
+    return nb < ntiles ? nb : ntiles;
+}
+
+// a1 = relu(conv(x, W1) + b1); W1 (bf16, [co][ci][tap]) held as FP32 [tap][ci][co]
+template <int CIN>
+__global__ void __launch_bounds__(128) k_first_z(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ W,
+                                                 const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
+                                                 int nx, int ny, int nz) {
+    __shared__ __align__(16) float w[27 * CIN * 16];
+    __shared__ __align__(16) __nv_bfloat16 ring[4 * PLANE_CELLS * CIN];
+    const int tid = threadIdx.x;
+    for (int q = tid; q < 16 * CIN * 27; q += blockDim.x) {
+        const int co = q / (CIN * 27), ci = (q / 27) % CIN, tap = q % 27;
+        w[(tap * CIN + ci) * 16 + co] = __bfloat162float(W[q]);
+    }
+    float bs[16];
+#pragma unroll
+    for (int co = 0; co < 16; ++co) bs[co] = __ldg(bias + co);
+    const int tiles_x = nx / TXC, ntiles = tiles_x * (ny / TYC);
+    const int cx = tid % TXC, cy = tid / TXC;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (tile % tiles_x) * TXC, y0 = (tile / tiles_x) * TYC;
+        __syncthreads();
+        load_thin<CIN>(in, ring, nx, ny, nz, x0, y0, -1);
+        load_thin<CIN>(in, ring, nx, ny, nz, x0, y0, 0);
+        for (int k = 0; k < nz; ++k) {
+            load_thin<CIN>(in, ring, nx, ny, nz, x0, y0, k + 1);
+            __syncthreads();
+            float acc[16];
+#pragma unroll
+            for (int co = 0; co < 16; ++co) acc[co] = bs[co];
+#pragma unroll 1
+            for (int dz = 0; dz < 3; ++dz) {
+                const __nv_bfloat16* P = ring + ((k + dz) & 3) * (PLANE_CELLS * CIN);
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const int tap = (dz * 3 + dy) * 3 + dx;
+                        const int cell = (cy + dy) * HX + cx + dx;
+#pragma unroll
+                        for (int ci = 0; ci < CIN; ++ci) {
+                            const float xv = __bfloat162float(P[cell * CIN + ci]);
+                            const float4* wv = reinterpret_cast<const float4*>(w + (tap * CIN + ci) * 16);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const float4 ww = wv[q];
+                                acc[4 * q] = fmaf(ww.x, xv, acc[4 * q]);
+                                acc[4 * q + 1] = fmaf(ww.y, xv, acc[4 * q + 1]);
+                                acc[4 * q + 2] = fmaf(ww.z, xv, acc[4 * q + 2]);
+                                acc[4 * q + 3] = fmaf(ww.w, xv, acc[4 * q + 3]);
+                            }
+                        }
+                    }
+            }
+            __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+            for (int co = 0; co < 16; ++co) o[co] = __float2bfloat16_rn(fmaxf(acc[co], 0.f));
+            const size_t p = ((size_t)k * ny + y0 + cy) * nx + x0 + cx;
+            reinterpret_cast<uint4*>(out + p * 16)[0] = reinterpret_cast<uint4*>(o)[0];
+            reinterpret_cast<uint4*>(out + p * 16)[1] = reinterpret_cast<uint4*>(o)[1];
+            __syncthreads();  // the slot of plane k-1 is refilled next
         }
     }
 }
 
-// ---------------------------------------------------------------- first layer: cin -> 16 (SIMT)
-template <int CIN>
-__global__ void __launch_bounds__(256) k_conv_first(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ W,
-                                                    const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
-                                                    int nx, int ny, int nz) {
-    __shared__ float w[16 * CIN * 27];
-    for (int q = threadIdx.x; q < 16 * CIN * 27; q += blockDim.x) w[q] = __bfloat162float(W[q]);
-    __syncthreads();
-    const size_t n = (size_t)nx * ny * nz;
-    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const int i = (int)(p % nx), j = (int)((p / nx) % ny), k = (int)(p / ((size_t)nx * ny));
-    float acc[16];
+// out = conv(a3, W4) + b4 (16 -> 1); W4 held as FP32 [tap][ci]
+__global__ void __launch_bounds__(128) k_last_z(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ W,
+                                                const float* __restrict__ bias, float* __restrict__ out, int nx, int ny,
+                                                int nz) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* w = reinterpret_cast<float*>(smem);
+    unsigned char* ring = smem + 27 * 16 * 4;
+    const int tid = threadIdx.x;
+    for (int q = tid; q < 16 * 27; q += blockDim.x) w[(q % 27) * 16 + q / 27] = __bfloat162float(W[q]);
+    const float b4 = __ldg(bias);
+    const int tiles_x = nx / TXC, ntiles = tiles_x * (ny / TYC);
+    const int cx = tid % TXC, cy = tid / TXC;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (tile % tiles_x) * TXC, y0 = (tile / tiles_x) * TYC;
+        __syncthreads();
+        load_wide(in, ring, nx, ny, nz, x0, y0, -1);
+        load_wide(in, ring, nx, ny, nz, x0, y0, 0);
+        load_wide(in, ring, nx, ny, nz, x0, y0, 1);
+        for (int k = 0; k < nz; ++k) {
+            load_wide(in, ring, nx, ny, nz, x0, y0, k + 2);
+            cp_wait_nn<1>();
+            __syncthreads();
+            float acc = b4;
+#pragma unroll 1
+            for (int dz = 0; dz < 3; ++dz) {
+                const unsigned char* P = ring + ((k + dz) & 3) * PLANE_BYTES;
 #pragma unroll
-    for (int co = 0; co < 16; ++co) acc[co] = __ldg(bias + co);
-    for (int dz = -1; dz <= 1; ++dz) {
-        const int kk = k + dz;
-        if (kk < 0 || kk >= nz) continue;
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int tap = ((dz + 1) * 3 + dy + 1) * 3 + dx + 1;
-                const size_t q = ((size_t)kk * ny + nwrap(j + dy, ny)) * nx + nwrap(i + dx, nx);
+                for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-                for (int ci = 0; ci < CIN; ++ci) {
-                    const float xv = __bfloat162float(in[q * CIN + ci]);
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const int tap = (dz * 3 + dy) * 3 + dx;
+                        const uint4* a = reinterpret_cast<const uint4*>(P + ((cy + dy) * HX + cx + dx) * 32);
+                        const float4* wv = reinterpret_cast<const float4*>(w + tap * 16);
 #pragma unroll
-                    for (int co = 0; co < 16; ++co) acc[co] = fmaf(w[(co * CIN + ci) * 27 + tap], xv, acc[co]);
-                }
+                        for (int hq = 0; hq < 2; ++hq) {
+                            const uint4 av = a[hq];
+                            const __nv_bfloat162* ab = reinterpret_cast<const __nv_bfloat162*>(&av);
+                            const float4 w0 = wv[2 * hq], w1 = wv[2 * hq + 1];
+                            float2 f0 = __bfloat1622float2(ab[0]), f1 = __bfloat1622float2(ab[1]);
+                            float2 f2 = __bfloat1622float2(ab[2]), f3 = __bfloat1622float2(ab[3]);
+                            acc = fmaf(w0.x, f0.x, acc);
+                            acc = fmaf(w0.y, f0.y, acc);
+                            acc = fmaf(w0.z, f1.x, acc);
+                            acc = fmaf(w0.w, f1.y, acc);
+                            acc = fmaf(w1.x, f2.x, acc);
+                            acc = fmaf(w1.y, f2.y, acc);
+                            acc = fmaf(w1.z, f3.x, acc);
+                            acc = fmaf(w1.w, f3.y, acc);
+                        }
+                    }
             }
+            out[((size_t)k * ny + y0 + cy) * nx + x0 + cx] = acc;
+            __syncthreads();
+        }
+        cp_wait_nn<0>();
     }
-    __align__(16) __nv_bfloat16 o[16];
-#pragma unroll
-    for (int co = 0; co < 16; ++co) o[co] = __float2bfloat16_rn(fmaxf(acc[co], 0.f));
-    reinterpret_cast<uint4*>(out + p * 16)[0] = reinterpret_cast<uint4*>(o)[0];
-    reinterpret_cast<uint4*>(out + p * 16)[1] = reinterpret_cast<uint4*>(o)[1];
 }
 
-// ---------------------------------------------------------------- last layer: 16 -> 1 (SIMT)
-__global__ void __launch_bounds__(256) k_conv_last(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ W,
-                                                   const float* __restrict__ bias, float* __restrict__ out, int nx,
-                                                   int ny, int nz) {
-    __shared__ float w[16 * 27];
-    for (int q = threadIdx.x; q < 16 * 27; q += blockDim.x) w[q] = __bfloat162float(W[q]);
-    __syncthreads();
-    const size_t n = (size_t)nx * ny * nz;
-    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const int i = (int)(p % nx), j = (int)((p / nx) % ny), k = (int)(p / ((size_t)nx * ny));
-    float acc = __ldg(bias);
-    for (int dz = -1; dz <= 1; ++dz) {
-        const int kk = k + dz;
-        if (kk < 0 || kk >= nz) continue;
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int tap = ((dz + 1) * 3 + dy + 1) * 3 + dx + 1;
-                const size_t q = ((size_t)kk * ny + nwrap(j + dy, ny)) * nx + nwrap(i + dx, nx);
-                __align__(16) __nv_bfloat16 a[16];
-                reinterpret_cast<uint4*>(a)[0] = __ldg(reinterpret_cast<const uint4*>(in + q * 16));
-                reinterpret_cast<uint4*>(a)[1] = __ldg(reinterpret_cast<const uint4*>(in + q * 16) + 1);
+// partial weight gradient of the first layer: dW1[co][ci][tap] = sum_p d1[p][co] x[p + d(tap)][ci].
+// Thread t < 27 CIN G owns one (ci, tap) for all 16 co over the cells of group t / (27 CIN)
+// (G = 108 / (27 CIN) groups of the 128 tile cells); one partial per block and weight.
+template <int CIN>
+__global__ void __launch_bounds__(128) k_dwfirst_z(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ dy,
+                                                   float* __restrict__ partials, int nx, int ny, int nz) {
+    constexpr int NPAIR = 27 * CIN, G = 108 / NPAIR, CPG = TCELLS / G;
+    __shared__ __align__(16) __nv_bfloat16 ring[4 * PLANE_CELLS * CIN];
+    __shared__ __align__(16) __nv_bfloat16 dys[TCELLS * 16];
+    const int tid = threadIdx.x;
+    const bool act = tid < NPAIR * G;
+    const int pair = tid % NPAIR, grp = tid / NPAIR;
+    const int ci = pair % CIN, tap = pair / CIN;
+    const int dz = tap / 9, dyy = (tap / 3) % 3, dxx = tap % 3;
+    float acc[16];
 #pragma unroll
-                for (int ci = 0; ci < 16; ++ci) acc = fmaf(w[ci * 27 + tap], __bfloat162float(a[ci]), acc);
+    for (int co = 0; co < 16; ++co) acc[co] = 0.f;
+    const int tiles_x = nx / TXC, ntiles = tiles_x * (ny / TYC);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (tile % tiles_x) * TXC, y0 = (tile / tiles_x) * TYC;
+        __syncthreads();
+        load_thin<CIN>(x, ring, nx, ny, nz, x0, y0, -1);
+        load_thin<CIN>(x, ring, nx, ny, nz, x0, y0, 0);
+        for (int k = 0; k < nz; ++k) {
+            load_thin<CIN>(x, ring, nx, ny, nz, x0, y0, k + 1);
+            for (int q = tid; q < TCELLS * 2; q += blockDim.x) {
+                const int v = q >> 1, half = q & 1;
+                const size_t p = ((size_t)k * ny + y0 + v / TXC) * nx + x0 + v % TXC;
+                reinterpret_cast<uint4*>(dys)[q] = __ldg(reinterpret_cast<const uint4*>(dy + p * 16) + half);
             }
+            __syncthreads();
+            if (act) {
+                const __nv_bfloat16* P = ring + ((k + dz) & 3) * (PLANE_CELLS * CIN);
+                for (int cc = grp * CPG; cc < (grp + 1) * CPG; ++cc) {
+                    const int cx = cc % TXC, cy = cc / TXC;
+                    const float xv = __bfloat162float(P[((cy + dyy) * HX + cx + dxx) * CIN + ci]);
+                    const uint4* g = reinterpret_cast<const uint4*>(dys + cc * 16);
+#pragma unroll
+                    for (int hq = 0; hq < 2; ++hq) {
+                        const uint4 gv = g[hq];
+                        const __nv_bfloat162* gb = reinterpret_cast<const __nv_bfloat162*>(&gv);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float2 f = __bfloat1622float2(gb[e]);
+                            acc[8 * hq + 2 * e] = fmaf(f.x, xv, acc[8 * hq + 2 * e]);
+                            acc[8 * hq + 2 * e + 1] = fmaf(f.y, xv, acc[8 * hq + 2 * e + 1]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
     }
-    out[p] = acc;
+    // the groups of one (ci, tap) add up in shared memory, in group order
+    __shared__ float red[108 * 16];
+    if (act)
+#pragma unroll
+        for (int co = 0; co < 16; ++co) red[tid * 16 + co] = acc[co];
+    __syncthreads();
+    if (tid < NPAIR) {
+        float* dst = partials + (size_t)blockIdx.x * (16 * CIN * 27);
+        for (int co = 0; co < 16; ++co) {
+            float sm = 0.f;
+            for (int gq = 0; gq < G; ++gq) sm += red[(gq * NPAIR + tid) * 16 + co];
+            dst[(co * CIN + ci) * 27 + tap] = sm;
+        }
+    }
+}
+
+// partial weight gradient of the last layer: dW4[ci][tap] = sum_p d4[p] a3[p + d(tap)][ci];
+// thread t < 108 owns tap t % 27 for all 16 ci over the cells of group t / 27 (4 groups)
+__global__ void __launch_bounds__(128) k_dwlast_z(const __nv_bfloat16* __restrict__ a3, const float* __restrict__ d4,
+                                                  float* __restrict__ partials, int nx, int ny, int nz) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char* ring = smem;
+    float* ds = reinterpret_cast<float*>(smem + 4 * PLANE_BYTES);
+    const int tid = threadIdx.x;
+    const bool act = tid < 108;
+    const int tap = tid % 27, grp = tid / 27;
+    const int dz = tap / 9, dyy = (tap / 3) % 3, dxx = tap % 3;
+    float acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = 0.f;
+    const int tiles_x = nx / TXC, ntiles = tiles_x * (ny / TYC);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (tile % tiles_x) * TXC, y0 = (tile / tiles_x) * TYC;
+        __syncthreads();
+        load_wide(a3, ring, nx, ny, nz, x0, y0, -1);
+        load_wide(a3, ring, nx, ny, nz, x0, y0, 0);
+        load_wide(a3, ring, nx, ny, nz, x0, y0, 1);
+        for (int k = 0; k < nz; ++k) {
+            load_wide(a3, ring, nx, ny, nz, x0, y0, k + 2);
+            {
+                const int v = tid;
+                const size_t p = ((size_t)k * ny + y0 + v / TXC) * nx + x0 + v % TXC;
+                ds[v] = __ldg(d4 + p);
+            }
+            cp_wait_nn<1>();
+            __syncthreads();
+            if (act) {
+                const unsigned char* P = ring + ((k + dz) & 3) * PLANE_BYTES;
+                for (int cc = grp * 32; cc < grp * 32 + 32; ++cc) {
+                    const int cx = cc % TXC, cy = cc / TXC;
+                    const float g = ds[cc];
+                    const uint4* a = reinterpret_cast<const uint4*>(P + ((cy + dyy) * HX + cx + dxx) * 32);
+#pragma unroll
+                    for (int hq = 0; hq < 2; ++hq) {
+                        const uint4 av = a[hq];
+                        const __nv_bfloat162* ab = reinterpret_cast<const __nv_bfloat162*>(&av);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float2 f = __bfloat1622float2(ab[e]);
+                            acc[8 * hq + 2 * e] = fmaf(g, f.x, acc[8 * hq + 2 * e]);
+                            acc[8 * hq + 2 * e + 1] = fmaf(g, f.y, acc[8 * hq + 2 * e + 1]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        cp_wait_nn<0>();
+    }
+    float* red = reinterpret_cast<float*>(smem);  // the ring is no longer read
+    __syncthreads();
+    if (act)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) red[tid * 16 + c] = acc[c];
+    __syncthreads();
+    if (tid < 27) {
+        float* dst = partials + (size_t)blockIdx.x * (16 * 27);
+        for (int c = 0; c < 16; ++c) {
+            const float sm = (red[tid * 16 + c] + red[(27 + tid) * 16 + c]) + (red[(54 + tid) * 16 + c] + red[(81 + tid) * 16 + c]);
+            dst[c * 27 + tid] = sm;
+        }
+    }
 }
 
 // ---------------------------------------------------------------- backward of the last layer
@@ -299,33 +610,6 @@ __global__ void __launch_bounds__(256) k_dw16(const __nv_bfloat16* __restrict__ 
                 dst[(co * 16 + ci) * 27 + tap] = acc[s][nt][2 * h];
                 dst[(co * 16 + ci + 1) * 27 + tap] = acc[s][nt][2 * h + 1];
             }
-    }
-}
-
-// ---------------------------------------------------------------- weight gradient of thin layers
-// dW[co][ci][tap] for a layer with CIN inputs and COUT outputs where one side is thin: one thread per
-// weight, a block per slice of cells, one partial sum per (block, weight). x: CIN channels-last bf16;
-// dy: COUT channels (bf16 channels-last, or fp32 when COUT == 1).
-template <int CIN, int COUT, bool DYF32>
-__global__ void k_dw_thin(const __nv_bfloat16* __restrict__ x, const void* __restrict__ dyv, float* __restrict__ partials,
-                          int nx, int ny, int nz, size_t cells_per_block) {
-    constexpr int NW = COUT * CIN * 27;
-    const size_t n = (size_t)nx * ny * nz;
-    const size_t p0 = blockIdx.x * cells_per_block, p1 = p0 + cells_per_block < n ? p0 + cells_per_block : n;
-    for (int wi = threadIdx.x; wi < NW; wi += blockDim.x) {
-        const int co = wi / (CIN * 27), ci = (wi / 27) % CIN, tap = wi % 27;
-        const int dz = tap / 9 - 1, dyy = (tap / 3) % 3 - 1, dxx = tap % 3 - 1;
-        float s = 0.f;
-        for (size_t p = p0; p < p1; ++p) {
-            const int i = (int)(p % nx), j = (int)((p / nx) % ny), k = (int)(p / ((size_t)nx * ny));
-            const int kk = k + dz;
-            if (kk < 0 || kk >= nz) continue;
-            const float g = DYF32 ? __ldg(reinterpret_cast<const float*>(dyv) + p)
-                                  : __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(dyv)[p * COUT + co]);
-            const size_t q = ((size_t)kk * ny + nwrap(j + dyy, ny)) * nx + nwrap(i + dxx, nx);
-            s = fmaf(g, __bfloat162float(x[q * CIN + ci]), s);
-        }
-        partials[(size_t)blockIdx.x * NW + wi] = s;
     }
 }
 
@@ -481,17 +765,17 @@ void nn_forward(const NNBufs& b, int nx, int ny, int nz, const __nv_bfloat16* x,
     const float* b2 = b1 + 16 + 16 * 16 * 27;
     const float* b3 = b2 + 16 + 16 * 16 * 27;
     const float* b4 = b3 + 16 + 16 * 27;
-    if (b.cin == 1) k_conv_first<1><<<blocks_for(n), 256, 0, s>>>(x, b.w1, b1, b.a1, nx, ny, nz);
-    else k_conv_first<2><<<blocks_for(n), 256, 0, s>>>(x, b.w1, b1, b.a1, nx, ny, nz);
+    const int gt = thin_grid(nx, ny, 1 << 30);
+    if (b.cin == 1) k_first_z<1><<<gt, 128, 0, s>>>(x, b.w1, b1, b.a1, nx, ny, nz);
+    else k_first_z<2><<<gt, 128, 0, s>>>(x, b.w1, b1, b.a1, nx, ny, nz);
     note_launch();
-    const size_t smem = HALO_BYTES + W_BYTES;
-    cudaFuncSetAttribute(k_conv16<EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grd(nx / TXC, ny / TYC, nz);
-    k_conv16<EPI_RELU><<<grd, 256, smem, s>>>(b.a1, b.w2f, b2, nullptr, b.a2, nx, ny, nz);
+    const size_t smemz = W_BYTES + 4 * PLANE_BYTES;
+    const int gz = conv16z_grid(nx, ny);
+    k_conv16z<EPI_RELU><<<gz, 256, smemz, s>>>(b.a1, b.w2f, b2, nullptr, b.a2, nx, ny, nz);
     note_launch();
-    k_conv16<EPI_RELU><<<grd, 256, smem, s>>>(b.a2, b.w3f, b3, nullptr, b.a3, nx, ny, nz);
+    k_conv16z<EPI_RELU><<<gz, 256, smemz, s>>>(b.a2, b.w3f, b3, nullptr, b.a3, nx, ny, nz);
     note_launch();
-    k_conv_last<<<blocks_for(n), 256, 0, s>>>(b.a3, b.w4, b4, out, nx, ny, nz);
+    k_last_z<<<gt, 128, 27 * 16 * 4 + 4 * PLANE_BYTES, s>>>(b.a3, b.w4, b4, out, nx, ny, nz);
     note_launch();
 }
 
@@ -515,34 +799,34 @@ void nn_backward(const NNBufs& b, int nx, int ny, int nz, const __nv_bfloat16* x
     float* gb4 = gW4 + n4;
     const int nb = nn_grad_blocks(n);
     const size_t cpb = (n + nb - 1) / nb;
+    const int nbt = thin_grid(nx, ny, 1024);  // partial sums of the thin weight gradients
     // layer 4: dW4, db4 and d3 = mask(a3) * W4^T d4
-    k_dw_thin<16, 1, true><<<nb, 128, 0, s>>>(b.a3, d4, b.part, nx, ny, nz, cpb);
-    k_reduce_partials<<<(n4 + 255) / 256, 256, 0, s>>>(b.part, nb, n4, gW4);
+    k_dwlast_z<<<nbt, 128, 4 * PLANE_BYTES + TCELLS * 4, s>>>(b.a3, d4, b.part, nx, ny, nz);
+    k_reduce_partials<<<(n4 + 255) / 256, 256, 0, s>>>(b.part, nbt, n4, gW4);
     k_chansum<1, true><<<nb, 256, 0, s>>>(d4, b.part, n, cpb);
     k_reduce_partials<<<1, 256, 0, s>>>(b.part, nb, 1, gb4);
     k_bwd_last<<<blocks_for(n), 256, 0, s>>>(d4, b.w4, b.a3, b.d1, nx, ny, nz);
     for (int q = 0; q < 5; ++q) note_launch();
-    const size_t smem = HALO_BYTES + W_BYTES;
-    cudaFuncSetAttribute(k_conv16<EPI_MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smemz = W_BYTES + 4 * PLANE_BYTES;
+    const int gz = conv16z_grid(nx, ny);
     const size_t smem_dw = HALO_BYTES + TXC * TYC * 32;
     cudaFuncSetAttribute(k_dw16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dw);
-    dim3 grd(nx / TXC, ny / TYC, nz);
     // layer 3: dW3 from (a2, d3); d2 = mask(a2) * conv(d3, W3 flipped)
     k_dw16<<<nb, 256, smem_dw, s>>>(b.a2, b.d1, b.part, nx, ny, nz);
     k_reduce_partials<<<(n2 + 255) / 256, 256, 0, s>>>(b.part, nb, n2, gW3);
     k_chansum<16, false><<<nb, 256, 0, s>>>(b.d1, b.part, n, cpb);
     k_reduce_partials<<<1, 256, 0, s>>>(b.part, nb, 16, gb3);
-    k_conv16<EPI_MASK><<<grd, 256, smem, s>>>(b.d1, b.w3b, nullptr, b.a2, b.d2, nx, ny, nz);
+    k_conv16z<EPI_MASK><<<gz, 256, smemz, s>>>(b.d1, b.w3b, nullptr, b.a2, b.d2, nx, ny, nz);
     // layer 2: dW2 from (a1, d2); d1 = mask(a1) * conv(d2, W2 flipped)
     k_dw16<<<nb, 256, smem_dw, s>>>(b.a1, b.d2, b.part, nx, ny, nz);
     k_reduce_partials<<<(n2 + 255) / 256, 256, 0, s>>>(b.part, nb, n2, gW2);
     k_chansum<16, false><<<nb, 256, 0, s>>>(b.d2, b.part, n, cpb);
     k_reduce_partials<<<1, 256, 0, s>>>(b.part, nb, 16, gb2);
-    k_conv16<EPI_MASK><<<grd, 256, smem, s>>>(b.d2, b.w2b, nullptr, b.a1, b.d1, nx, ny, nz);
+    k_conv16z<EPI_MASK><<<gz, 256, smemz, s>>>(b.d2, b.w2b, nullptr, b.a1, b.d1, nx, ny, nz);
     // layer 1: dW1 from (x, d1)
-    if (cin == 1) k_dw_thin<1, 16, false><<<nb, 128, 0, s>>>(x, b.d1, b.part, nx, ny, nz, cpb);
-    else k_dw_thin<2, 16, false><<<nb, 128, 0, s>>>(x, b.d1, b.part, nx, ny, nz, cpb);
-    k_reduce_partials<<<(n1 + 255) / 256, 256, 0, s>>>(b.part, nb, n1, gW1);
+    if (cin == 1) k_dwfirst_z<1><<<nbt, 128, 0, s>>>(x, b.d1, b.part, nx, ny, nz);
+    else k_dwfirst_z<2><<<nbt, 128, 0, s>>>(x, b.d1, b.part, nx, ny, nz);
+    k_reduce_partials<<<(n1 + 255) / 256, 256, 0, s>>>(b.part, nbt, n1, gW1);
     k_chansum<16, false><<<nb, 256, 0, s>>>(b.d1, b.part, n, cpb);
     k_reduce_partials<<<1, 256, 0, s>>>(b.part, nb, 16, gb1);
     for (int q = 0; q < 14; ++q) note_launch();
