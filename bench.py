@@ -49,7 +49,7 @@ def parse_args():
     ap.add_argument("--solve-only", action="store_true",
                     help="time the solves only (no kernel timing, e2e, variants or CPU baseline): "
                          "the command the ncu launch-list profile runs")
-    ap.add_argument("--kernel-only", choices=["smooth", "residual", "restrict_smooth", "prolongate"],
+    ap.add_argument("--kernel-only", choices=["smooth", "residual", "restrict_smooth", "prolongate", "nn_forward"],
                     help="launch only this finest-level kernel a few times (tile variant --variant, "
                          "no autotuning): the command a per-kernel ncu capture runs")
     ap.add_argument("--variant", type=int, default=3)
@@ -309,6 +309,26 @@ def run_kernel_only(args):
     """A few launches of one finest-level kernel of the mid problem, for a profiler capture."""
     import torch
     from paper_1402_3545_gb300 import tpmg
+    if args.kernel_only == "nn_forward":
+        # the learned stage's forward pass on one 256^2 x 64 training crop (4.2 M voxels)
+        from paper_1402_3545_gb300 import learned
+        shape = (64, 256, 256)
+        nvox = shape[0] * shape[1] * shape[2]
+        net = tpmg.Network(2, learned.init_params(2, 0))
+        x = torch.randn(nvox * 2, device="cuda", dtype=torch.float32, generator=torch.Generator("cuda").manual_seed(0))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        net.forward(x, shape)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(max(args.steps, 1)):
+            net.forward(x, shape)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(args.steps, 1)
+        print(json.dumps({"kernel": "nn_forward", "voxels": nvox, "ms_per_forward": round(ms, 4),
+                          "tflops": round(nn_flops_per_voxel(2) * nvox / (ms * 1e-3) / 1e12, 2)}), flush=True)
+        net.close()
+        return
     prec = {"dw": tpmg.DW, "f32": tpmg.F32, "f64": tpmg.F64}[args.precision]
     kid = {"smooth": tpmg.K_SMOOTH, "residual": tpmg.K_RESIDUAL, "restrict_smooth": tpmg.K_RESTRICT_SMOOTH,
            "prolongate": tpmg.K_PROLONGATE}[args.kernel_only]

@@ -85,6 +85,11 @@ __device__ __forceinline__ void cp_wait_nn() {
 static constexpr int PLANE_CELLS = HX * HY;        // 66 x 4 cells of one halo plane
 static constexpr int PLANE_BYTES = PLANE_CELLS * 32;
 
+// Shared-memory offset of the 16-byte half `h` of 32-byte row `r` (a cell's 16 channels, or a
+// weight row): the halves of rows 4..7 (mod 8) swap places, so the 8 rows an ldmatrix phase reads
+// (32 bytes apart) fall on 8 distinct groups of 4 banks instead of 2-way conflicts.
+__device__ __forceinline__ int swz(int r, int h) { return r * 32 + ((h ^ ((r >> 2) & 1)) << 4); }
+
 template <int EPI>
 __global__ void __launch_bounds__(256) k_conv16z(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Wt,
                                                  const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask,
@@ -94,7 +99,7 @@ __global__ void __launch_bounds__(256) k_conv16z(const __nv_bfloat16* __restrict
     unsigned char* ring = smem + W_BYTES;  // 4 planes
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int q = tid; q < W_BYTES / 16; q += blockDim.x)
-        reinterpret_cast<uint4*>(Ws)[q] = __ldg(reinterpret_cast<const uint4*>(Wt) + q);
+        *reinterpret_cast<uint4*>(Ws + swz(q >> 1, q & 1)) = __ldg(reinterpret_cast<const uint4*>(Wt) + q);
     const int tiles_x = nx / TXC, ntiles = tiles_x * (ny / TYC);
     const int yw = warp >> 2, xw = (warp & 3) * 16;
     const int ar = lane & 15, acol = (lane >> 4) * 8;
@@ -117,9 +122,9 @@ __global__ void __launch_bounds__(256) k_conv16z(const __nv_bfloat16* __restrict
                 const int xx = v % HX, yy = v / HX;
                 if (kk >= 0 && kk < nz) {
                     const int i = nwrap(x0 - 1 + xx, nx), j = nwrap(y0 - 1 + yy, ny);
-                    cp16(P + (size_t)q * 16, in + (((size_t)kk * ny + j) * nx + i) * 16 + half * 8);
+                    cp16(P + swz(v, half), in + (((size_t)kk * ny + j) * nx + i) * 16 + half * 8);
                 } else {
-                    reinterpret_cast<uint4*>(P)[q] = make_uint4(0, 0, 0, 0);
+                    *reinterpret_cast<uint4*>(P + swz(v, half)) = make_uint4(0, 0, 0, 0);
                 }
             }
             cp_commit_nn();
@@ -143,8 +148,8 @@ __global__ void __launch_bounds__(256) k_conv16z(const __nv_bfloat16* __restrict
                         const int tap = (dz * 3 + dy) * 3 + dx;
                         const int cell = (yw + dy) * HX + xw + ar + dx;
                         uint32_t a0, a1, a2, a3, b0, b1, b2, b3;
-                        ldm_x4(saddr(H + cell * 32 + acol * 2), a0, a1, a2, a3);
-                        ldm_x4(saddr(Ws + ((tap * 16 + bco) * 16 + bci) * 2), b0, b1, b2, b3);
+                        ldm_x4(saddr(H + swz(cell, acol >> 3)), a0, a1, a2, a3);
+                        ldm_x4(saddr(Ws + swz(tap * 16 + bco, bci >> 3)), b0, b1, b2, b3);
                         mma16816(c0, a0, a1, a2, a3, b0, b1);
                         mma16816(c1, a0, a1, a2, a3, b2, b3);
                     }
@@ -228,9 +233,9 @@ __device__ __forceinline__ void load_wide(const __nv_bfloat16* __restrict__ in, 
         const int xx = v % HX, yy = v / HX;
         if (kk >= 0 && kk < nz) {
             const int i = nwrap(x0 - 1 + xx, nx), j = nwrap(y0 - 1 + yy, ny);
-            cp16(P + (size_t)q * 16, in + (((size_t)kk * ny + j) * nx + i) * 16 + half * 8);
+            cp16(P + swz(v, half), in + (((size_t)kk * ny + j) * nx + i) * 16 + half * 8);
         } else {
-            reinterpret_cast<uint4*>(P)[q] = make_uint4(0, 0, 0, 0);
+            *reinterpret_cast<uint4*>(P + swz(v, half)) = make_uint4(0, 0, 0, 0);
         }
     }
     cp_commit_nn();
@@ -340,11 +345,11 @@ __global__ void __launch_bounds__(128) k_last_z(const __nv_bfloat16* __restrict_
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx) {
                         const int tap = (dz * 3 + dy) * 3 + dx;
-                        const uint4* a = reinterpret_cast<const uint4*>(P + ((cy + dy) * HX + cx + dx) * 32);
+                        const int cell = (cy + dy) * HX + cx + dx;
                         const float4* wv = reinterpret_cast<const float4*>(w + tap * 16);
 #pragma unroll
                         for (int hq = 0; hq < 2; ++hq) {
-                            const uint4 av = a[hq];
+                            const uint4 av = *reinterpret_cast<const uint4*>(P + swz(cell, hq));
                             const __nv_bfloat162* ab = reinterpret_cast<const __nv_bfloat162*>(&av);
                             const float4 w0 = wv[2 * hq], w1 = wv[2 * hq + 1];
                             float2 f0 = __bfloat1622float2(ab[0]), f1 = __bfloat1622float2(ab[1]);
@@ -471,10 +476,10 @@ __global__ void __launch_bounds__(128) k_dwlast_z(const __nv_bfloat16* __restric
                 for (int cc = grp * 32; cc < grp * 32 + 32; ++cc) {
                     const int cx = cc % TXC, cy = cc / TXC;
                     const float g = ds[cc];
-                    const uint4* a = reinterpret_cast<const uint4*>(P + ((cy + dyy) * HX + cx + dxx) * 32);
+                    const int cell = (cy + dyy) * HX + cx + dxx;
 #pragma unroll
                     for (int hq = 0; hq < 2; ++hq) {
-                        const uint4 av = a[hq];
+                        const uint4 av = *reinterpret_cast<const uint4*>(P + swz(cell, hq));
                         const __nv_bfloat162* ab = reinterpret_cast<const __nv_bfloat162*>(&av);
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
