@@ -90,10 +90,12 @@ static constexpr int PLANE_BYTES = PLANE_CELLS * 32;
 // (32 bytes apart) fall on 8 distinct groups of 4 banks instead of 2-way conflicts.
 __device__ __forceinline__ int swz(int r, int h) { return r * 32 + ((h ^ ((r >> 2) & 1)) << 4); }
 
-template <int EPI>
-__global__ void __launch_bounds__(256) k_conv16z(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Wt,
-                                                 const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask,
-                                                 __nv_bfloat16* __restrict__ out, int nx, int ny, int nz) {
+// MT m-tiles (16 cells each) per warp: the weight fragment of a tap is loaded once for MT tiles
+template <int EPI, int MT>
+__global__ void __launch_bounds__(256 / MT) k_conv16z(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Wt,
+                                                      const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask,
+                                                      __nv_bfloat16* __restrict__ out, int nx, int ny, int nz) {
+    constexpr int WPR = 4 / MT;  // warps per tile row
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char* Ws = smem;
     unsigned char* ring = smem + W_BYTES;  // 4 planes
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(256) k_conv16z(const __nv_bfloat16* __restrict
     for (int q = tid; q < W_BYTES / 16; q += blockDim.x)
         *reinterpret_cast<uint4*>(Ws + swz(q >> 1, q & 1)) = __ldg(reinterpret_cast<const uint4*>(Wt) + q);
     const int tiles_x = nx / TXC, ntiles = tiles_x * (ny / TYC);
-    const int yw = warp >> 2, xw = (warp & 3) * 16;
+    const int yw = warp / WPR, xw = (warp % WPR) * 16 * MT;
     const int ar = lane & 15, acol = (lane >> 4) * 8;
     const int bco = ((lane >> 4) << 3) + (lane & 7), bci = ((lane >> 3) & 1) * 8;
     const int g = lane >> 2, t2 = (lane & 3) * 2;
@@ -137,7 +139,13 @@ __global__ void __launch_bounds__(256) k_conv16z(const __nv_bfloat16* __restrict
             load_plane(k + 2);  // into the slot of plane k-2, read by nobody now
             cp_wait_nn<1>();    // planes up to k+1 have landed (this thread's copies)
             __syncthreads();    // ... and every other thread's
-            float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+            float c[MT][2][4];
+#pragma unroll
+            for (int m = 0; m < MT; ++m)
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) c[m][nt][e] = 0.f;
 #pragma unroll 1
             for (int dz = 0; dz < 3; ++dz) {
                 const unsigned char* H = ring + ((k + dz) & 3) * PLANE_BYTES;  // plane k - 1 + dz
@@ -146,48 +154,55 @@ __global__ void __launch_bounds__(256) k_conv16z(const __nv_bfloat16* __restrict
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx) {
                         const int tap = (dz * 3 + dy) * 3 + dx;
-                        const int cell = (yw + dy) * HX + xw + ar + dx;
-                        uint32_t a0, a1, a2, a3, b0, b1, b2, b3;
-                        ldm_x4(saddr(H + swz(cell, acol >> 3)), a0, a1, a2, a3);
+                        uint32_t b0, b1, b2, b3;
                         ldm_x4(saddr(Ws + swz(tap * 16 + bco, bci >> 3)), b0, b1, b2, b3);
-                        mma16816(c0, a0, a1, a2, a3, b0, b1);
-                        mma16816(c1, a0, a1, a2, a3, b2, b3);
+#pragma unroll
+                        for (int m = 0; m < MT; ++m) {
+                            const int cell = (yw + dy) * HX + xw + 16 * m + ar + dx;
+                            uint32_t a0, a1, a2, a3;
+                            ldm_x4(saddr(H + swz(cell, acol >> 3)), a0, a1, a2, a3);
+                            mma16816(c[m][0], a0, a1, a2, a3, b0, b1);
+                            mma16816(c[m][1], a0, a1, a2, a3, b2, b3);
+                        }
                     }
             }
             const int y = y0 + yw;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int x = x0 + xw + g + 8 * h;
-                const size_t p = ((size_t)k * ny + y) * nx + x;
+            for (int m = 0; m < MT; ++m)
 #pragma unroll
-                for (int nt = 0; nt < 2; ++nt) {
-                    const float* c = nt ? c1 : c0;
-                    const int co = t2 + 8 * nt;
-                    float v0 = c[2 * h], v1 = c[2 * h + 1];
-                    if (EPI == EPI_RELU) {
-                        v0 = fmaxf(v0 + (nt ? bco8 : bco0), 0.f);
-                        v1 = fmaxf(v1 + (nt ? bco9 : bco1), 0.f);
-                    } else {
-                        const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(mask + p * 16 + co);
-                        if (!(__bfloat162float(m.x) > 0.f)) v0 = 0.f;
-                        if (!(__bfloat162float(m.y) > 0.f)) v1 = 0.f;
+                for (int h = 0; h < 2; ++h) {
+                    const int x = x0 + xw + 16 * m + g + 8 * h;
+                    const size_t p = ((size_t)k * ny + y) * nx + x;
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt) {
+                        const int co = t2 + 8 * nt;
+                        float v0 = c[m][nt][2 * h], v1 = c[m][nt][2 * h + 1];
+                        if (EPI == EPI_RELU) {
+                            v0 = fmaxf(v0 + (nt ? bco8 : bco0), 0.f);
+                            v1 = fmaxf(v1 + (nt ? bco9 : bco1), 0.f);
+                        } else {
+                            const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(mask + p * 16 + co);
+                            if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
+                            if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
+                        }
+                        *reinterpret_cast<__nv_bfloat162*>(out + p * 16 + co) = __floats2bfloat162_rn(v0, v1);
                     }
-                    *reinterpret_cast<__nv_bfloat162*>(out + p * 16 + co) = __floats2bfloat162_rn(v0, v1);
                 }
-            }
             __syncthreads();  // the slot of plane k-1 is refilled by the next step's load
         }
         cp_wait_nn<0>();
     }
 }
 
+static constexpr int CONV_MT = 2;  // m-tiles per warp of the 16 -> 16 convolution
+
 static int conv16z_grid(int nx, int ny) {
     static int per_sm = 0, nsm = 0;
     const size_t smem = W_BYTES + 4 * PLANE_BYTES;
     if (per_sm == 0) {
-        cudaFuncSetAttribute(k_conv16z<EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_conv16z<EPI_MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv16z<EPI_RELU>, 256, smem);
+        cudaFuncSetAttribute(k_conv16z<EPI_RELU, CONV_MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_conv16z<EPI_MASK, CONV_MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv16z<EPI_RELU, CONV_MT>, 256 / CONV_MT, smem);
         if (per_sm < 1) per_sm = 1;
         int dev = 0;
         cudaGetDevice(&dev);
@@ -776,9 +791,9 @@ void nn_forward(const NNBufs& b, int nx, int ny, int nz, const __nv_bfloat16* x,
     note_launch();
     const size_t smemz = W_BYTES + 4 * PLANE_BYTES;
     const int gz = conv16z_grid(nx, ny);
-    k_conv16z<EPI_RELU><<<gz, 256, smemz, s>>>(b.a1, b.w2f, b2, nullptr, b.a2, nx, ny, nz);
+    k_conv16z<EPI_RELU, CONV_MT><<<gz, 256 / CONV_MT, smemz, s>>>(b.a1, b.w2f, b2, nullptr, b.a2, nx, ny, nz);
     note_launch();
-    k_conv16z<EPI_RELU><<<gz, 256, smemz, s>>>(b.a2, b.w3f, b3, nullptr, b.a3, nx, ny, nz);
+    k_conv16z<EPI_RELU, CONV_MT><<<gz, 256 / CONV_MT, smemz, s>>>(b.a2, b.w3f, b3, nullptr, b.a3, nx, ny, nz);
     note_launch();
     k_last_z<<<gt, 128, 27 * 16 * 4 + 4 * PLANE_BYTES, s>>>(b.a3, b.w4, b4, out, nx, ny, nz);
     note_launch();
@@ -821,13 +836,13 @@ void nn_backward(const NNBufs& b, int nx, int ny, int nz, const __nv_bfloat16* x
     k_reduce_partials<<<(n2 + 255) / 256, 256, 0, s>>>(b.part, nb, n2, gW3);
     k_chansum<16, false><<<nb, 256, 0, s>>>(b.d1, b.part, n, cpb);
     k_reduce_partials<<<1, 256, 0, s>>>(b.part, nb, 16, gb3);
-    k_conv16z<EPI_MASK><<<gz, 256, smemz, s>>>(b.d1, b.w3b, nullptr, b.a2, b.d2, nx, ny, nz);
+    k_conv16z<EPI_MASK, CONV_MT><<<gz, 256 / CONV_MT, smemz, s>>>(b.d1, b.w3b, nullptr, b.a2, b.d2, nx, ny, nz);
     // layer 2: dW2 from (a1, d2); d1 = mask(a1) * conv(d2, W2 flipped)
     k_dw16<<<nb, 256, smem_dw, s>>>(b.a1, b.d2, b.part, nx, ny, nz);
     k_reduce_partials<<<(n2 + 255) / 256, 256, 0, s>>>(b.part, nb, n2, gW2);
     k_chansum<16, false><<<nb, 256, 0, s>>>(b.d2, b.part, n, cpb);
     k_reduce_partials<<<1, 256, 0, s>>>(b.part, nb, 16, gb2);
-    k_conv16z<EPI_MASK><<<gz, 256, smemz, s>>>(b.d2, b.w2b, nullptr, b.a1, b.d1, nx, ny, nz);
+    k_conv16z<EPI_MASK, CONV_MT><<<gz, 256 / CONV_MT, smemz, s>>>(b.d2, b.w2b, nullptr, b.a1, b.d1, nx, ny, nz);
     // layer 1: dW1 from (x, d1)
     if (cin == 1) k_dwfirst_z<1><<<nbt, 128, 0, s>>>(x, b.d1, b.part, nx, ny, nz);
     else k_dwfirst_z<2><<<nbt, 128, 0, s>>>(x, b.d1, b.part, nx, ny, nz);
