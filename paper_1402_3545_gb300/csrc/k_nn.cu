@@ -214,11 +214,12 @@ static int conv16z_grid(int nx, int ny) {
 }
 
 // ---------------------------------------------------------------- thin layers, marching in z
-// The first layer (cin -> 16), the last (16 -> 1) and their weight gradients in the persistent
-// z-marching form of k_conv16z: a block of 128 threads owns a 64 x 2 tile, one cell per thread,
-// keeps the input planes k-1, k, k+1 (one-cell halo) in a 4-slot ring and the weights in shared
-// memory as FP32, so every input value is read from memory once per tile and the weight reads are
-// shared-memory broadcasts.
+// The one-channel first layer (1 -> 16) and the weight gradients of the first and last layers in
+// the persistent z-marching form of k_conv16z: a block of 128 threads owns a 64 x 2 tile, one cell
+// per thread, keeps the input planes k-1, k, k+1 (one-cell halo) in a 4-slot ring and the weights
+// in shared memory as FP32, so every input value is read from memory once per tile and the weight
+// reads are shared-memory broadcasts. (The two-channel first layer and the last layer run on the
+// tensor cores: k_first_tc, k_last_tc.)
 static constexpr int TCELLS = TXC * TYC;  // 128 cells per tile plane
 
 // thin input (C = 1 or 2 channels, bf16): plane kk of the tile into ring slot (kk + 1) & 3
@@ -329,18 +330,113 @@ __global__ void __launch_bounds__(128) k_first_z(const __nv_bfloat16* __restrict
     }
 }
 
-// out = conv(a3, W4) + b4 (16 -> 1); W4 held as FP32 [tap][ci]
-__global__ void __launch_bounds__(128) k_last_z(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ W,
-                                                const float* __restrict__ bias, float* __restrict__ out, int nx, int ny,
-                                                int nz) {
+// ---------------------------------------------------------------- thin layers on the tensor cores
+// First layer (2 -> 16) as one implicit GEMM per 16 cells: K = 27 taps x 2 channels, padded to 64
+// (4 k16 blocks of 8 taps); an A fragment register holds the 2 channels of one cell and tap (one
+// 32-bit shared load), the B fragments (the weights) stay in registers for the whole kernel.
+__global__ void __launch_bounds__(128) k_first_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ W,
+                                                  const float* __restrict__ bias, __nv_bfloat16* __restrict__ out, int nx,
+                                                  int ny, int nz) {
+    __shared__ __align__(16) __nv_bfloat16 ring[4 * PLANE_CELLS * 2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, t = lane & 3, t2 = 2 * t;
+    // B fragments: k = 2 j + ci within block kb <-> tap 8 kb + j; column n = output channel
+    uint32_t bf[4][2][2];
+#pragma unroll
+    for (int kb = 0; kb < 4; ++kb)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int tap = 8 * kb + t + 4 * r, co = g + 8 * nt;
+                __nv_bfloat162 v = __floats2bfloat162_rn(0.f, 0.f);
+                if (tap < 27) {
+                    v.x = W[(co * 2 + 0) * 27 + tap];
+                    v.y = W[(co * 2 + 1) * 27 + tap];
+                }
+                bf[kb][nt][r] = *reinterpret_cast<uint32_t*>(&v);
+            }
+    const float bc0 = __ldg(bias + t2), bc1 = __ldg(bias + t2 + 1), bc8 = __ldg(bias + t2 + 8), bc9 = __ldg(bias + t2 + 9);
+    const int tiles_x = nx / TXC, ntiles = tiles_x * (ny / TYC);
+    const int yw = warp >> 1, xw = (warp & 1) * 32;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (tile % tiles_x) * TXC, y0 = (tile / tiles_x) * TYC;
+        __syncthreads();
+        load_thin<2>(in, ring, nx, ny, nz, x0, y0, -1);
+        load_thin<2>(in, ring, nx, ny, nz, x0, y0, 0);
+        for (int k = 0; k < nz; ++k) {
+            load_thin<2>(in, ring, nx, ny, nz, x0, y0, k + 1);
+            __syncthreads();
+            float c[2][2][4];
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) c[m][nt][e] = 0.f;
+#pragma unroll
+            for (int kb = 0; kb < 4; ++kb) {
+                uint32_t a[2][4];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {  // r = 0: taps 8 kb + t, r = 1: taps 8 kb + t + 4
+                    const int tap = 8 * kb + t + 4 * r;
+                    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+                    const uint32_t* P = reinterpret_cast<const uint32_t*>(ring + ((k + dz) & 3) * (PLANE_CELLS * 2));
+#pragma unroll
+                    for (int m = 0; m < 2; ++m) {
+                        const int cell = (yw + dy) * HX + xw + 16 * m + g + dx;
+                        a[m][2 * r] = tap < 27 ? P[cell] : 0u;
+                        a[m][2 * r + 1] = tap < 27 ? P[cell + 8] : 0u;
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    // fragment order: a0 (row g, k 2t), a1 (row g+8, k 2t), a2 (row g, k 2t+8), a3 (row g+8, k 2t+8)
+                    mma16816(c[m][0], a[m][0], a[m][1], a[m][2], a[m][3], bf[kb][0][0], bf[kb][0][1]);
+                    mma16816(c[m][1], a[m][0], a[m][1], a[m][2], a[m][3], bf[kb][1][0], bf[kb][1][1]);
+                }
+            }
+            const int y = y0 + yw;
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const size_t p = ((size_t)k * ny + y) * nx + x0 + xw + 16 * m + g + 8 * h;
+                    *reinterpret_cast<__nv_bfloat162*>(out + p * 16 + t2) =
+                        __floats2bfloat162_rn(fmaxf(c[m][0][2 * h] + bc0, 0.f), fmaxf(c[m][0][2 * h + 1] + bc1, 0.f));
+                    *reinterpret_cast<__nv_bfloat162*>(out + p * 16 + t2 + 8) =
+                        __floats2bfloat162_rn(fmaxf(c[m][1][2 * h] + bc8, 0.f), fmaxf(c[m][1][2 * h + 1] + bc9, 0.f));
+                }
+            __syncthreads();
+        }
+    }
+}
+
+// Last layer (16 -> 1) on the tensor cores: per tap one m16n8k16 MMA with the activations as A
+// (ldmatrix from the swizzled plane ring) and W4[:, tap] as the only non-zero column of B.
+__global__ void __launch_bounds__(128) k_last_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ W,
+                                                 const float* __restrict__ bias, float* __restrict__ out, int nx, int ny,
+                                                 int nz) {
     extern __shared__ __align__(16) unsigned char smem[];
-    float* w = reinterpret_cast<float*>(smem);
-    unsigned char* ring = smem + 27 * 16 * 4;
-    const int tid = threadIdx.x;
-    for (int q = tid; q < 16 * 27; q += blockDim.x) w[(q % 27) * 16 + q / 27] = __bfloat162float(W[q]);
+    uint2* bt = reinterpret_cast<uint2*>(smem);  // [tap][lane] B fragments
+    unsigned char* ring = smem + 27 * 32 * 8;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, t2 = (lane & 3) * 2;
+    for (int q = tid; q < 27 * 32; q += blockDim.x) {
+        const int tap = q / 32, ln = q % 32, lg = ln >> 2, lt = (ln & 3) * 2;
+        __nv_bfloat162 b0 = __floats2bfloat162_rn(0.f, 0.f), b1 = b0;
+        if (lg == 0) {  // column n = 0 is the output channel
+            b0.x = W[lt * 27 + tap];
+            b0.y = W[(lt + 1) * 27 + tap];
+            b1.x = W[(lt + 8) * 27 + tap];
+            b1.y = W[(lt + 9) * 27 + tap];
+        }
+        bt[q] = make_uint2(*reinterpret_cast<uint32_t*>(&b0), *reinterpret_cast<uint32_t*>(&b1));
+    }
     const float b4 = __ldg(bias);
     const int tiles_x = nx / TXC, ntiles = tiles_x * (ny / TYC);
-    const int cx = tid % TXC, cy = tid / TXC;
+    const int yw = warp >> 1, xw = (warp & 1) * 32;
+    const int ar = lane & 15, acol = (lane >> 4) * 8;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int x0 = (tile % tiles_x) * TXC, y0 = (tile / tiles_x) * TYC;
         __syncthreads();
@@ -351,36 +447,33 @@ __global__ void __launch_bounds__(128) k_last_z(const __nv_bfloat16* __restrict_
             load_wide(in, ring, nx, ny, nz, x0, y0, k + 2);
             cp_wait_nn<1>();
             __syncthreads();
-            float acc = b4;
+            float c[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll 1
             for (int dz = 0; dz < 3; ++dz) {
-                const unsigned char* P = ring + ((k + dz) & 3) * PLANE_BYTES;
+                const unsigned char* H = ring + ((k + dz) & 3) * PLANE_BYTES;
 #pragma unroll
                 for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx) {
                         const int tap = (dz * 3 + dy) * 3 + dx;
-                        const int cell = (cy + dy) * HX + cx + dx;
-                        const float4* wv = reinterpret_cast<const float4*>(w + tap * 16);
+                        const uint2 b = bt[tap * 32 + lane];
 #pragma unroll
-                        for (int hq = 0; hq < 2; ++hq) {
-                            const uint4 av = *reinterpret_cast<const uint4*>(P + swz(cell, hq));
-                            const __nv_bfloat162* ab = reinterpret_cast<const __nv_bfloat162*>(&av);
-                            const float4 w0 = wv[2 * hq], w1 = wv[2 * hq + 1];
-                            float2 f0 = __bfloat1622float2(ab[0]), f1 = __bfloat1622float2(ab[1]);
-                            float2 f2 = __bfloat1622float2(ab[2]), f3 = __bfloat1622float2(ab[3]);
-                            acc = fmaf(w0.x, f0.x, acc);
-                            acc = fmaf(w0.y, f0.y, acc);
-                            acc = fmaf(w0.z, f1.x, acc);
-                            acc = fmaf(w0.w, f1.y, acc);
-                            acc = fmaf(w1.x, f2.x, acc);
-                            acc = fmaf(w1.y, f2.y, acc);
-                            acc = fmaf(w1.z, f3.x, acc);
-                            acc = fmaf(w1.w, f3.y, acc);
+                        for (int m = 0; m < 2; ++m) {
+                            uint32_t a0, a1, a2, a3;
+                            ldm_x4(saddr(H + swz((yw + dy) * HX + xw + 16 * m + ar + dx, acol >> 3)), a0, a1, a2, a3);
+                            mma16816(c[m], a0, a1, a2, a3, b.x, b.y);
                         }
                     }
             }
-            out[((size_t)k * ny + y0 + cy) * nx + x0 + cx] = acc;
+            if (t2 == 0) {  // lanes holding output column 0: cells g and g + 8
+                const int y = y0 + yw;
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const size_t p = ((size_t)k * ny + y) * nx + x0 + xw + 16 * m + g;
+                    out[p] = c[m][0] + b4;
+                    out[p + 8] = c[m][2] + b4;
+                }
+            }
             __syncthreads();
         }
         cp_wait_nn<0>();
@@ -787,7 +880,7 @@ void nn_forward(const NNBufs& b, int nx, int ny, int nz, const __nv_bfloat16* x,
     const float* b4 = b3 + 16 + 16 * 27;
     const int gt = thin_grid(nx, ny, 1 << 30);
     if (b.cin == 1) k_first_z<1><<<gt, 128, 0, s>>>(x, b.w1, b1, b.a1, nx, ny, nz);
-    else k_first_z<2><<<gt, 128, 0, s>>>(x, b.w1, b1, b.a1, nx, ny, nz);
+    else k_first_tc<<<gt, 128, 0, s>>>(x, b.w1, b1, b.a1, nx, ny, nz);
     note_launch();
     const size_t smemz = W_BYTES + 4 * PLANE_BYTES;
     const int gz = conv16z_grid(nx, ny);
@@ -795,7 +888,7 @@ void nn_forward(const NNBufs& b, int nx, int ny, int nz, const __nv_bfloat16* x,
     note_launch();
     k_conv16z<EPI_RELU, CONV_MT><<<gz, 256 / CONV_MT, smemz, s>>>(b.a2, b.w3f, b3, nullptr, b.a3, nx, ny, nz);
     note_launch();
-    k_last_z<<<gt, 128, 27 * 16 * 4 + 4 * PLANE_BYTES, s>>>(b.a3, b.w4, b4, out, nx, ny, nz);
+    k_last_tc<<<gt, 128, 27 * 32 * 8 + 4 * PLANE_BYTES, s>>>(b.a3, b.w4, b4, out, nx, ny, nz);
     note_launch();
 }
 
