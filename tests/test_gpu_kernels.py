@@ -17,8 +17,10 @@ pytestmark = pytest.mark.gpu
 # levels of at most 4096 columns run the cell-parallel kernels (parallel cyclic reduction), larger
 # ones the column kernels (pipelined when nx % 32 == 0): 100 x 50 exercises the plain column
 # kernels on its finest level; nz = 7, 9, 200 are not powers of two; nz = 256 is the largest
+# kernels, and 128 x 48 (6144 columns, nx % 64 == 0) the plane-pipelined Smooth, the two-column
+# Residual and the 2 x 2 prolongation on its finest level
 SHAPES = [(80, 36, 24, 3), (64, 64, 64, 4), (40, 12, 7, 3), (96, 8, 1, 2), (16, 16, 128, 2), (100, 50, 9, 2),
-          (16, 4, 200, 2), (8, 8, 256, 2)]
+          (16, 4, 200, 2), (8, 8, 256, 2), (128, 48, 20, 2)]
 SHAPE_IDS = [f"{a}x{b}x{c}L{d}" for a, b, c, d in SHAPES]
 
 
@@ -181,3 +183,24 @@ def test_argument_errors(setup):
         tpmg.prolongate(op.op, 1, tpmg.F64, x, y, op.level_n(op.L), op.level_n(op.L))
     with pytest.raises(TypeError):
         tpmg.apply_A(op.op, op.L, tpmg.F32, x, y, op.level_n(op.L))
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+@pytest.mark.parametrize("variant", range(tpmg.NUM_VARIANTS))
+def test_every_smooth_variant_matches_oracle(prec, variant):
+    """Each tile variant of the large-level Smooth (shared-memory stack, persistent with the stack
+    in global scratch, two columns per thread) against the oracle, with its fused norm."""
+    nx, ny, nz = 128, 48, 20
+    p = make_problem(nx, ny, nz)
+    op = tpmg.Operator.from_problem(p, nlevels=2)
+    cx, cy, v = oracle.problem_coefficients(p)
+    tpmg.set_variant(op.op, prec, 2, variant)
+    u, f = rnd((nz, ny, nx), 70), rnd((nz, ny, nx), 71)
+    out = torch.empty_like(dev(u, prec))
+    nrm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    tpmg.smooth(op.op, 2, prec, 0.8, dev(u, prec), dev(f, prec), out, p.n, norm_out=nrm)
+    ref = oracle.smooth(u, f, cx, cy, v, 0.8)
+    assert rel(host(out), ref) < tol_inverse(prec, cx, cy, v), rel(host(out), ref)
+    rnorm = np.linalg.norm(oracle.residual(u, f, cx, cy, v))
+    assert abs(host(nrm)[0] - rnorm) / rnorm < max(TOL[prec], 1e-7)
+    op.close()
