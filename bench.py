@@ -193,6 +193,22 @@ def bench_batched(tpmg, torch):
     return out
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of the ranks' values (every rank receives it); x itself on one process."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def per_solve_ms(elapsed_max_ms: float, steps: int, world: int) -> float:
+    """Replicas only: every rank solves its own copy `steps` times, so the job solves steps * world
+    problems in the slowest rank's time."""
+    return elapsed_max_ms / (steps * world)
+
+
 def nn_flops_per_voxel(cin: int) -> int:
     """Multiply-adds x 2 of the 4-layer network per voxel: 3x3x3 taps, cin -> 16 -> 16 -> 16 -> 1."""
     return 2 * 27 * (cin * 16 + 16 * 16 + 16 * 16 + 16)
@@ -279,10 +295,10 @@ def bench_learned(tpmg, torch):
 
 
 def run_reference(args, rank, world):
+    if rank != 0:  # replicas of the oracle would time the same host cores: rank 0 alone runs
+        return
     p = workloads.mid()
     f = p.rhs()
-    if rank != 0:
-        return
     import oracle
     oracle.build()
     vals, info = [], None
@@ -393,12 +409,9 @@ def run_ours(args, rank, world, dist):
     launches = tpmg.kernel_launches() - k0
     clocks = sampler.stop()
     elapsed = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, dist, dev)
     ms_per_step = elapsed / args.steps
-    value = elapsed / (args.steps * world)  # ms per solve over all replicas' solves
+    value = per_solve_ms(elapsed, args.steps, world)
     if args.solve_only:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": round(value, 4), "unit": "ms", "iters": iters[-1],
