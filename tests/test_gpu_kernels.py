@@ -204,3 +204,32 @@ def test_every_smooth_variant_matches_oracle(prec, variant):
     rnorm = np.linalg.norm(oracle.residual(u, f, cx, cy, v))
     assert abs(host(nrm)[0] - rnorm) / rnorm < max(TOL[prec], 1e-7)
     op.close()
+
+
+def test_double_word_conversion_round_trip_is_exact():
+    """FP64 -> double-word -> FP64 through an identity operator (omega^2 = 0, so A = I) reproduces
+    float64(hi) + float64(lo) with hi = float32(x) and lo = float32(x - hi) bit for bit, over the
+    float range (no infinities: the stencil's zero couplings would turn a neighbour's inf into NaN)
+    including zeros, float denormals, the float extremes and round-to-nearest-even ties."""
+    rng = np.random.default_rng(90)
+    nz, ny, nx = 8, 4, 64
+    n = nz * ny * nx
+    vals = [rng.standard_normal(n // 2) * 10.0 ** rng.uniform(-30, 30, n // 2)]
+    edge = [0.0, -0.0, 1.0, -1.0, 2.0 ** -60, 2.0 ** -61, 2.0 ** 100, 2.0 ** 101, 1e-300, 5e-324, 1e-40,
+            3.4028234663852886e38 / 4, 1.1754943508222875e-38, 1 + 2.0 ** -24, 1 + 2.0 ** -23 + 2.0 ** -24,
+            1 - 2.0 ** -25, 0.1, 1.0 / 3.0]
+    # significands exactly halfway between two floats (ties to even) and just off it
+    base = rng.uniform(1.0, 2.0, 64).astype(np.float32).astype(np.float64)
+    ties = np.concatenate([base + 2.0 ** -24, base - 2.0 ** -24, base + 2.0 ** -24 * (1 + 2.0 ** -20)])
+    x = np.concatenate([vals[0], np.array(edge), ties])
+    x = np.concatenate([x, rng.standard_normal(n - x.size)]).reshape(nz, ny, nx)
+    op = tpmg.Operator(nx, ny, nz, 0.0, 1.0 / nx, 1.0 / ny, 1.0 / nz, 1.0, 1)
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    with np.errstate(under="ignore"):
+        tpmg.apply_A(op.op, 1, tpmg.DW, torch.from_numpy(x.ravel()).cuda(), y, n)
+        hi = x.ravel().astype(np.float32)
+        lo = (x.ravel() - hi.astype(np.float64)).astype(np.float32)
+        ref = hi.astype(np.float64) + lo.astype(np.float64)
+    got = host(y)
+    assert np.array_equal(got, ref), np.flatnonzero(got != ref)[:10]
+    op.close()
