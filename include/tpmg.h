@@ -141,6 +141,8 @@ typedef struct {
     int use_graph;   /* 1: replay each iteration from a CUDA graph (default), 0: plain launches */
     double timeout_s; /* time limit of every device-side wait (the batched solver's grid barrier);
                          default 1.0 s; when it runs out the solve ends with TPMG_ERR_TIMEOUT */
+    int zero_guess;  /* 1: start from u = 0 without reading u (u is then output only), 0: start from
+                        the u passed in (default) */
 } tpmg_params;
 
 typedef struct {
@@ -159,7 +161,10 @@ void tpmg_default_params(tpmg_params* p);
 
 /* Multigrid solve (Sec. 2.2, Algorithm 1 with nu_pre/nu_post smoothing steps): V-cycles from the
  * initial guess in u until Eq. (10) holds. f and u are finest-level device fields (double for
- * TPMG_F64, TPMG_DW and TPMG_MIXED, float for TPMG_F32). TPMG_MIXED runs iterative refinement:
+ * TPMG_F64, TPMG_DW and TPMG_MIXED, float for TPMG_F32). With TPMG_DW and TPMG_MIXED, f and u may
+ * instead be host memory the device addresses (page-locked allocations such as cudaHostAlloc's):
+ * the solve then reads f and the initial u from the host and writes the final u there inside its
+ * first and last kernels (one pass each way, no separate copy). TPMG_MIXED runs iterative refinement:
  * r = f - A u in double-word arithmetic (stored FP32), one FP32 V-cycle for A e = r from e = 0,
  * u += e in double-word arithmetic. Returns TPMG_OK, TPMG_ERR_NOT_CONVERGED or
  * TPMG_ERR_NONFINITE (u then holds the last iterate), or an argument/CUDA error. */

@@ -970,6 +970,19 @@ void tpmg_default_params(tpmg_params* p) {
     p->prec = TPMG_DW;
     p->use_graph = 1;
     p->timeout_s = 1.0;
+    p->zero_guess = 0;
+}
+
+// The initial iterate: the caller's u, converted to the solve's storage, or zero without reading u.
+static tpmg_status init_u_dw(size_t n, const tpmg_params* prm, const void* u, float2* uD, cudaStream_t s) {
+    if (prm->zero_guess) CK(cudaMemsetAsync(uD, 0, n * sizeof(float2), s));
+    else launch_f64_to_dw(n, (const double*)u, uD, s);
+    return TPMG_OK;
+}
+
+static tpmg_status init_u(size_t n, size_t bytes, const tpmg_params* prm, void* u, cudaStream_t s) {
+    if (prm->zero_guess) CK(cudaMemsetAsync(u, 0, n * bytes, s));
+    return TPMG_OK;
 }
 
 tpmg_status tpmg_mg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, void* u, tpmg_info* info,
@@ -986,11 +999,13 @@ tpmg_status tpmg_mg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, vo
         case TPMG_F64:
             TRY(ensure_hier(op, 0, false));
             CK(cudaEventRecord(op->ev0, s));
+            TRY(init_u(n, sizeof(double), prm, u, s));
             TRY((mg_loop<PolF64, PolF64>(op, prm, (double*)u, (double*)f, 1, s)));
             break;
         case TPMG_F32:
             TRY(ensure_hier(op, 1, false));
             CK(cudaEventRecord(op->ev0, s));
+            TRY(init_u(n, sizeof(float), prm, u, s));
             TRY((mg_loop<PolF32, PolF32>(op, prm, (float*)u, (float*)f, 1, s)));
             break;
         case TPMG_DW: {
@@ -999,7 +1014,7 @@ tpmg_status tpmg_mg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, vo
             float2* uD = (float2*)op->hier[2].u[L];
             float2* fD = (float2*)op->hier[2].f[L];
             CK(cudaEventRecord(op->ev0, s));
-            launch_f64_to_dw(n, (const double*)u, uD, s);
+            TRY(init_u_dw(n, prm, u, uD, s));
             launch_f64_to_dw(n, (const double*)f, fD, s);
             TRY((mg_loop<PolDW, PolF64>(op, prm, uD, fD, op->lsw_dw, s)));
             launch_dw_to_f64(n, uD, (double*)u, s);
@@ -1011,7 +1026,7 @@ tpmg_status tpmg_mg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, vo
             float2* uD = (float2*)op->hier[2].u[L];
             float2* fD = (float2*)op->hier[2].f[L];
             CK(cudaEventRecord(op->ev0, s));
-            launch_f64_to_dw(n, (const double*)u, uD, s);
+            TRY(init_u_dw(n, prm, u, uD, s));
             launch_f64_to_dw(n, (const double*)f, fD, s);
             TRY(mixed_loop(op, prm, uD, fD, s));
             launch_dw_to_f64(n, uD, (double*)u, s);
@@ -1202,11 +1217,13 @@ tpmg_status tpmg_cg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, vo
         case TPMG_F64:
             TRY(ensure_cg(op, 0));
             CK(cudaEventRecord(op->ev0, s));
+            TRY(init_u(n, sizeof(double), prm, u, s));
             TRY(cg_loop<PolF64>(op, prm, (double*)u, (const double*)f, s));
             break;
         case TPMG_F32:
             TRY(ensure_cg(op, 1));
             CK(cudaEventRecord(op->ev0, s));
+            TRY(init_u(n, sizeof(float), prm, u, s));
             TRY(cg_loop<PolF32>(op, prm, (float*)u, (const float*)f, s));
             break;
         case TPMG_DW: {
@@ -1214,7 +1231,7 @@ tpmg_status tpmg_cg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, vo
             float2* uD = (float2*)op->hier[2].u[L];
             float2* fD = (float2*)op->hier[2].f[L];
             CK(cudaEventRecord(op->ev0, s));
-            launch_f64_to_dw(n, (const double*)u, uD, s);
+            TRY(init_u_dw(n, prm, u, uD, s));
             launch_f64_to_dw(n, (const double*)f, fD, s);
             TRY(cg_loop<PolDW>(op, prm, uD, fD, s));
             launch_dw_to_f64(n, uD, (double*)u, s);
@@ -1519,6 +1536,7 @@ extern "C" tpmg_status tpmg_mg_solve_batched(int nprob, tpmg_op* const* ops, con
         io_key.push_back(f[b]);
         io_key.push_back(u[b]);
     }
+    io_key.push_back(prm->zero_guess ? (const void*)1 : nullptr);  // the graph holds a memset instead of u's conversion
     cudaError_t launch_err = cudaSuccess;
     auto body = [&](cudaStream_t st) {
         CK(cudaMemcpyAsync(bc->d_state, bc->h_state, sizeof(BState) * nprob, cudaMemcpyHostToDevice, st));
@@ -1527,7 +1545,10 @@ extern "C" tpmg_status tpmg_mg_solve_batched(int nprob, tpmg_op* const* ops, con
         for (int b = 0; b < nprob; ++b) {
             const size_t n = lvl_cells(ops[b], ops[b]->g.L);
             launch_f64_to_dw(n, f[b], (float2*)ops[b]->hier[2].f[ops[b]->g.L], st);
-            launch_f64_to_dw(n, u[b], (float2*)ops[b]->hier[2].u[ops[b]->g.L], st);
+            if (prm->zero_guess)
+                CK(cudaMemsetAsync(ops[b]->hier[2].u[ops[b]->g.L], 0, n * sizeof(float2), st));
+            else
+                launch_f64_to_dw(n, u[b], (float2*)ops[b]->hier[2].u[ops[b]->g.L], st);
         }
         launch_err = launch_batched(d, bc->grid, bc->smem, st);
         for (int b = 0; b < nprob; ++b) {
@@ -1917,7 +1938,7 @@ extern "C" tpmg_status tpmg_fcg_solve(tpmg_op* op, tpmg_nn* nn, const float* aux
         fcg_select(n, sc, c, z1, z, s);
     };
     CK(cudaEventRecord(op->ev0, s));
-    launch_f64_to_dw(n, (const double*)u, uD, s);
+    TRY(init_u_dw(n, prm, u, uD, s));
     launch_f64_to_dw(n, f, fD, s);
     fcg_init(sc, prm->tol, prm->max_iter, s);
     const int nb = launch_residual<PolDW, PolDW>(LD, uD, fD, r, part, nullptr, s);  // r = f - A u

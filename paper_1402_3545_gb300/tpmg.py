@@ -35,7 +35,8 @@ class TpmgError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("n_coarse", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("rho", ctypes.c_double), ("tol", ctypes.c_double),
-                ("prec", ctypes.c_int), ("use_graph", ctypes.c_int), ("timeout_s", ctypes.c_double)]
+                ("prec", ctypes.c_int), ("use_graph", ctypes.c_int), ("timeout_s", ctypes.c_double),
+                ("zero_guess", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -259,7 +260,10 @@ def cg_fused_tridiag(op, prec, alpha, r, q, z, rr_out, rz_out, n, stream=None):
 def default_params(**kw) -> Params:
     p = Params()
     load().tpmg_default_params(ctypes.byref(p))
+    names = {name for name, _ in Params._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown solver parameter {k!r}")
         if k == "prec" and isinstance(v, str):
             v = PREC[v]
         setattr(p, k, v)
@@ -282,6 +286,27 @@ def _solve(fn_name, op, params, f, u, n, history_len, stream, allow):
 
 def mg_solve(op, params, f, u, n, history_len=256, stream=None, allow=(ERR_NOT_CONVERGED,)):
     return _solve("tpmg_mg_solve", op, params, f, u, n, history_len, stream, allow)
+
+
+def mg_solve_host(op, params, f, u, n, history_len=256, stream=None, allow=(ERR_NOT_CONVERGED,)):
+    """mg_solve on page-locked host fields (CPU float64 tensors with is_pinned()): the solve reads f
+    and the initial u from the host and writes u back in its first and last kernels."""
+    if params.prec not in (DW, MIXED):
+        raise ValueError("host fields need prec DW or MIXED")
+    for t, name in ((f, "f"), (u, "u")):
+        if not (isinstance(t, torch.Tensor) and not t.is_cuda and t.is_pinned() and t.dtype == torch.float64
+                and t.is_contiguous() and t.numel() == n):
+            raise TypeError(f"{name} must be a pinned contiguous CPU float64 tensor of {n} elements")
+    hist = (ctypes.c_double * max(history_len, 1))()
+    info = Info()
+    info.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+    info.history_len = history_len
+    status = load().tpmg_mg_solve(op, ctypes.byref(params), f.data_ptr(), u.data_ptr(), ctypes.byref(info),
+                                  _stream(stream))
+    _check(status, "mg_solve", allow=allow)
+    return {"status": status, "iters": info.iters, "converged": bool(info.converged),
+            "rel_res": info.rel_res, "r0": info.r0, "ms": info.ms,
+            "history": [hist[i] for i in range(min(info.iters + 1, history_len))]}
 
 
 def cg_solve(op, params, f, u, n, history_len=4096, stream=None, allow=(ERR_NOT_CONVERGED,)):

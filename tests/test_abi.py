@@ -58,3 +58,15 @@ def test_grid_argument_checks_without_gpu():
         tpmg.create_grid(60, 64, 8, 4)  # 60 not divisible by 8
     with pytest.raises(tpmg.TpmgError):
         tpmg.create_grid(64, 64, 300, 0)  # nz above the supported maximum
+
+
+def test_default_params_layout_without_gpu():
+    """tpmg_default_params fills every field of the binding's struct: a field missing or out of
+    place in the binding would show up as a wrong default here."""
+    import pytest
+    from paper_1402_3545_gb300 import tpmg
+    p = tpmg.default_params()
+    assert (p.nu_pre, p.nu_post, p.n_coarse, p.max_iter) == (2, 2, 2, 100)
+    assert (p.rho, p.tol, p.prec, p.use_graph, p.timeout_s, p.zero_guess) == (0.8, 1e-6, tpmg.DW, 1, 1.0, 0)
+    with pytest.raises(TypeError):
+        tpmg.default_params(zero_gues=1)

@@ -117,3 +117,18 @@ def test_batched_argument_errors():
                               [us[0], us[0]])
     for o in ops:
         o.close()
+
+
+def test_batched_zero_guess_ignores_u():
+    """zero_guess = 1 on fields full of NaN gives bit for bit the batched solve from u = 0 (the same
+    operators, so the kept tables are reused and only the captured graph changes)."""
+    probs = small_batch(3, seed=13)
+    ops, fs, us, res = run_batch(probs, tol=1e-6)
+    us2 = [torch.full_like(f, float("nan")) for f in fs]
+    res2 = tpmg.mg_solve_batched([o.op for o in ops], tpmg.default_params(prec=tpmg.MIXED, tol=1e-6, zero_guess=1),
+                                 fs, us2)
+    for a, b, u, u2 in zip(res["problems"], res2["problems"], us, us2):
+        assert a["iters"] == b["iters"] and a["history"] == b["history"]
+        assert torch.equal(u, u2)
+    for o in ops:
+        o.close()

@@ -141,3 +141,14 @@ def test_fcg_zero_rhs_and_max_iter(prob):
     assert res["converged"] and res["iters"] == 0 and not np.any(u)
     _, res = run_gpu(op, p, f, tol=1e-14, max_iter=2)
     assert res["status"] == tpmg.ERR_NOT_CONVERGED and res["iters"] == 2
+
+
+def test_fcg_zero_guess_ignores_u(prob):
+    """zero_guess = 1 on a u full of NaN gives bit for bit the solve from u = 0."""
+    p, op, _, f = prob
+    u0, r0 = run_gpu(op, p, f)
+    prm = tpmg.default_params(tol=TOL, max_iter=200, zero_guess=1)
+    u = torch.full((p.nz, p.ny, p.nx), float("nan"), dtype=torch.float64, device="cuda")
+    r1 = tpmg.fcg_solve(op.op, prm, dev(f, tpmg.F64), u, p.n)
+    assert r1["iters"] == r0["iters"] and r1["history"] == r0["history"]
+    assert np.array_equal(host(u), u0)

@@ -153,3 +153,40 @@ def test_odd_smoothing_count_and_single_level():
         assert res["iters"] == it_ref
         assert rel(host(u), u_ref) < 1e-10
         op.close()
+
+
+@pytest.mark.parametrize("prec", [tpmg.DW, tpmg.MIXED], ids=["dw", "mixed"])
+@pytest.mark.parametrize("zero_guess", [0, 1], ids=["u_in", "zero_guess"])
+def test_mg_solve_with_host_fields(small, prec, zero_guess):
+    """f and u in page-locked host memory: the solve reads and writes them in place and gives the
+    device-field result bit for bit. With zero_guess the host u starts as NaN and is never read."""
+    p, op, (cx, cy, v), f, _ = small
+    prm = tpmg.default_params(prec=prec, tol=1e-8, max_iter=100, zero_guess=zero_guess)
+    ud = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    rd = tpmg.mg_solve(op.op, prm, dev(f, tpmg.F64).reshape(-1), ud, p.n)
+    fh = torch.from_numpy(f.ravel().copy()).pin_memory()
+    uh = torch.full((p.n,), float("nan") if zero_guess else 0.0, dtype=torch.float64).pin_memory()
+    rh = tpmg.mg_solve_host(op.op, prm, fh, uh, p.n)
+    torch.cuda.synchronize()
+    assert rh["iters"] == rd["iters"] and rh["history"] == rd["history"]
+    assert np.array_equal(uh.numpy(), host(ud))
+
+
+@pytest.mark.parametrize("solver", ["mg", "cg"])
+@pytest.mark.parametrize("prec", [tpmg.F64, tpmg.DW, tpmg.F32, tpmg.MIXED], ids=["f64", "dw", "f32", "mixed"])
+def test_zero_guess_ignores_u(small, solver, prec):
+    """zero_guess = 1 on a u full of NaN gives bit for bit the solve from u = 0."""
+    if solver == "cg" and prec == tpmg.MIXED:
+        pytest.skip("CG has no mixed-precision variant")
+    p, op, _, f, _ = small
+    solve = tpmg.mg_solve if solver == "mg" else tpmg.cg_solve
+    dt = torch.float32 if prec == tpmg.F32 else torch.float64
+    fd = dev(f, tpmg.F32 if prec == tpmg.F32 else tpmg.F64).reshape(-1)
+    out = []
+    for zg, fill in ((0, 0.0), (1, float("nan"))):
+        prm = tpmg.default_params(prec=prec, tol=1e-6, max_iter=100 if solver == "mg" else 2000, zero_guess=zg)
+        u = torch.full((p.n,), fill, dtype=dt, device="cuda")
+        res = solve(op.op, prm, fd, u, p.n)
+        out.append((res["iters"], res["history"], host(u)))
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
+    assert np.array_equal(out[0][2], out[1][2])
