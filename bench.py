@@ -33,9 +33,9 @@ from paper_1402_3545_gb300 import workloads  # noqa: E402
 
 METRIC = "MG solve ms to 1e-6 rel. residual & % of HBM peak, FP64 vs mixed/learned"
 # dram__bytes_read.sum + dram__bytes_write.sum of one finest-level Smooth launch (k_sweep_x2,
-# double-word, tile variant 5) on the 512^2 x 128 problem: 1.5606 GB + 0.5152 GB
-PROFILED_SMOOTH_VARIANT = 5
-PROFILED_SMOOTH_TRAFFIC = 2075800000
+# double-word) on the 512^2 x 128 problem, per tile variant, from the ncu captures summarised in
+# profiles/k_sweep_x2_dw_smooth_mid_512x512x128.md (variant 6: 1.4692 GB + 0.4064 GB)
+PROFILED_SMOOTH_TRAFFIC = {5: 1759268352, 6: 1875600000, 7: 1849546496}
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -435,8 +435,8 @@ def run_ours(args, rank, world, dist):
         ("restrict_smooth", tpmg.K_RESTRICT_SMOOTH), ("prolongate", tpmg.K_PROLONGATE)]}
     n_smooth = 4 * iters[-1] + 1
     # DRAM bytes of one launch from the ncu capture summarised in
-    # profiles/k_sweep_x2_dw_smooth_mid_512x512x128.md (tile variant 5; null for another variant)
-    traffic = PROFILED_SMOOTH_TRAFFIC if finest_variant == PROFILED_SMOOTH_VARIANT else None
+    # profiles/k_sweep_x2_dw_smooth_mid_512x512x128.md (null for a variant without a capture)
+    traffic = PROFILED_SMOOTH_TRAFFIC.get(finest_variant)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "kernel": f"finest-level double-word Smooth (tile variant {finest_variant})",

@@ -201,15 +201,17 @@ unsigned long long tpmg_kernel_launches(void);
 
 /* ---------------------------------------------------------------- autotuning
  * The plane-pipelined Smooth has TPMG_NUM_VARIANTS variants: tile shapes (columns per block x ring
- * depth) with the Thomas stack in shared memory, persistent ones with the stack in global scratch,
- * and persistent ones with two columns per thread.
+ * depth) with the Thomas stack in shared memory (0-2), persistent ones with the stack in global
+ * scratch (3, 4), and persistent ones with two columns per thread that steer L2 residency of the
+ * stack with eviction hints (5-7). A level that was never tuned or set takes variant 6 where it
+ * applies (nx % 64 == 0), else variant 3 (native FP64: variant 0).
  * tpmg_autotune times each of them `reps` times on every level of precision `prec` (on the
  * operator's workspace, CUDA events on `stream`) and keeps the fastest per level; if variants_out
  * is not NULL it receives the choice of level l in variants_out[l] (host array of L+1 ints).
  * tpmg_set_variant sets one level's choice (e.g. from a saved tuning table). Both invalidate the
  * operator's cached CUDA graphs. Variants change the schedule, not the per-cell arithmetic (only the
  * grouping of the residual norm's partial sums differs). */
-#define TPMG_NUM_VARIANTS 7
+#define TPMG_NUM_VARIANTS 8
 tpmg_status tpmg_autotune(tpmg_op* op, tpmg_precision prec, int reps, int* variants_out, void* stream);
 tpmg_status tpmg_set_variant(tpmg_op* op, tpmg_precision prec, int level, int variant);
 

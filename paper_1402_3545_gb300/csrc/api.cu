@@ -614,6 +614,8 @@ tpmg_status tpmg_create_operator(const tpmg_grid* g, double omega2, double hx, d
     if (!(omega2 >= 0.0) || !(hx > 0.0) || !(hy > 0.0) || !(hz > 0.0))
         return set_err(TPMG_ERR_ARG, "omega2 >= 0 and positive mesh widths required");
     tpmg_op* op = new tpmg_op();
+    for (int p = 0; p < 3; ++p)
+        for (int l = 0; l <= MAXL; ++l) op->variant[p][l] = -1;  // untuned: the launcher's default
     op->g = *g;
     op->omega2 = omega2;
     op->hx = hx;

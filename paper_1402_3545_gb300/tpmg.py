@@ -494,7 +494,7 @@ def kernel_launches() -> int:
     return int(load().tpmg_kernel_launches())
 
 
-NUM_VARIANTS = 7
+NUM_VARIANTS = 8
 
 
 def autotune(op, prec, nlevels, reps=5, stream=None) -> list[int]:
