@@ -203,8 +203,8 @@ unsigned long long tpmg_kernel_launches(void);
  * The plane-pipelined Smooth has TPMG_NUM_VARIANTS variants: tile shapes (columns per block x ring
  * depth) with the Thomas stack in shared memory (0-2), persistent ones with the stack in global
  * scratch (3, 4), and persistent ones with two columns per thread that steer L2 residency of the
- * stack with eviction hints (5-7). A level that was never tuned or set takes variant 6 where it
- * applies (nx % 64 == 0), else variant 3 (native FP64: variant 0).
+ * stack with eviction hints (5-7). A level that was never tuned or set takes variant 6 (double-word;
+ * 5 in FP32) where it applies (nx % 64 == 0), else variant 3 (native FP64: variant 0).
  * tpmg_autotune times each of them `reps` times on every level of precision `prec` (on the
  * operator's workspace, CUDA events on `stream`) and keeps the fastest per level; if variants_out
  * is not NULL it receives the choice of level l in variants_out[l] (host array of L+1 ints).

@@ -100,6 +100,10 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
     constexpr bool STACK = MODE != MODE_RESIDUAL;  // a Thomas solve follows
     constexpr int UPL = HALO ? (TY + 2) * 34 : 0;
     constexpr int FPL = NT;
+    // FP32 Smooth stacks g_k = u_k + rho d'_k - w_k u_{k+1} and back-substitutes u'_k = g_k + w_k
+    // u'_{k+1} (u'_k - u_k = rho x_k, x_k = d'_k + w_k x_{k+1}), so u is not read a second time;
+    // the double-word and FP64 sweeps, bound by their arithmetic, stack d'_k and re-read u instead
+    constexpr bool GFORM = MODE == MODE_SMOOTH && P::id == 1;
     constexpr int IPL = STACK ? NT : 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (done && *(volatile const int*)done) return;
@@ -180,6 +184,7 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
         const R dh1 = P::add(dh, vv), dh2 = P::add(dh1, vv);
         const bool iso = L.cx == L.cy;  // square cells: one product for the four horizontal neighbours
         const bool want_norm = partials != nullptr;
+        const R cf = P::cst(coef);
         R um = vzero, uc = vzero, d_prev = vzero;
         int slot = 0;
         const int ctr = (ty + 1) * 34 + tx + 1;
@@ -213,10 +218,16 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
             if constexpr (STACK) {
                 const R inv = percol ? P::ld_plain(ringI, slot * FPL + tid) : P::ld(L.finv, k);
                 const R d = P::mul(P::fma(vv, d_prev, r), inv);
+                R g = d;
+                if constexpr (GFORM) {
+                    // g_k = u_k + rho d'_k - w_k u_{k+1} (um, uc now hold u_k, u_{k+1})
+                    const R w = percol ? P::mul(vv, inv) : P::ld(L.fw, k);
+                    g = P::fma(P::neg(w), uc, P::fma(cf, d, um));
+                }
                 if constexpr (GS)
-                    P::st(gstack, (size_t)k * NT + tid, d);
+                    P::st(gstack, (size_t)k * NT + tid, g);
                 else
-                    stack[(size_t)k * NT + tid] = d;
+                    stack[(size_t)k * NT + tid] = g;
                 d_prev = d;
             }
             if constexpr (HALO) __syncthreads();  // the slot is reused by the next issue
@@ -227,12 +238,12 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
 
         if constexpr (STACK) {
             __syncthreads();  // the backward ring reuses the forward ring's shared memory
-            // back substitution, streaming u_k (Smooth), v/m_k and (GS) d'_k through the ring in
-            // reverse order; every thread reads only its own copies
-            constexpr bool NEED_U = MODE == MODE_SMOOTH;
-            S* bU = reinterpret_cast<S*>(smem_raw);
-            S* bW = bU + (NEED_U ? PD * NT : 0);
+            // back substitution, streaming v/m_k, (GS) the stacked values and (Smooth, unless
+            // GFORM) u_k through the ring in reverse order; every thread reads only its own copies
+            constexpr bool NEED_U = MODE == MODE_SMOOTH && !GFORM;
+            S* bW = reinterpret_cast<S*>(smem_raw);
             S* bD = bW + PD * NT;
+            S* bU = bD + PD * NT;
             auto issue_back = [&](int k, int s2) {
                 if (k >= 0) {
                     const size_t id = (size_t)k * pl + c;
@@ -243,7 +254,6 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
                 cp_commit();
             };
             for (int s = 0; s < PD; ++s) issue_back(nz - 1 - s, s);
-            const R cf = P::cst(coef);
             const bool scaled = coef != 1.0;
             R xn = vzero;
             slot = 0;
@@ -253,7 +263,9 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
                 const R dk = GS ? P::ld_plain(bD, slot * NT + tid) : stack[(size_t)k * NT + tid];
                 xn = P::fma(w, xn, dk);
                 const size_t id = (size_t)k * pl + c;
-                if constexpr (MODE == MODE_SMOOTH)
+                if constexpr (GFORM)
+                    P::st(reinterpret_cast<S*>(out), id, xn);
+                else if constexpr (MODE == MODE_SMOOTH)
                     P::st(reinterpret_cast<S*>(out), id, P::fma(cf, xn, P::ld_plain(bU, slot * NT + tid)));
                 else
                     P::st(reinterpret_cast<S*>(out), id, scaled ? P::mul(cf, xn) : xn);
@@ -276,7 +288,7 @@ static size_t sweep_pp_smem(int nz) {
     const int IPL = MODE != MODE_RESIDUAL ? 32 * TY : 0;
     const size_t ring = ((size_t)PD * (UPL + 32 * TY + IPL) * sizeof(S) + 15) & ~(size_t)15;
     const size_t stack = (MODE != MODE_RESIDUAL && !GS) ? (size_t)nz * 32 * TY * sizeof(typename P::R) : 0;
-    // the backward ring (u, v/m and, GS, d') reuses the forward ring: take the larger
+    // the backward ring (u, v/m and, GS, the stacked values) reuses the forward ring: take the larger
     const size_t back = (size_t)PD * 32 * TY * sizeof(S) * 3;
     return (GS && back > ring ? back : ring) + stack;
 }
@@ -353,6 +365,7 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
     constexpr int UW = 68;
     constexpr bool STACK = MODE != MODE_RESIDUAL;
     constexpr bool HALO = MODE != MODE_LINESOLVE;
+    constexpr bool GFORM = MODE == MODE_SMOOTH && P::id == 1;  // as in k_sweep_pp
     constexpr int UPL = HALO ? (TY + 2) * UW : 0;
     constexpr int FPL = 2 * NT;
     constexpr int IPL = STACK ? 2 * NT : 0;
@@ -433,7 +446,7 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
         for (int s = 0; s < PD; ++s) issue_plane(s, s);
 
         const R v0 = P::ld(L.v, c), v1 = P::ld(L.v, c + 1);
-        const R cx = P::cst(L.cx), cy = P::cst(L.cy);
+        const R cx = P::cst(L.cx), cy = P::cst(L.cy), cf = P::cst(coef);
         const R dh = P::cst(1.0 + 2.0 * L.cx + 2.0 * L.cy);
         const R dh1a = P::add(dh, v0), dh2a = P::add(dh1a, v0);
         const R dh1b = P::add(dh, v1), dh2b = P::add(dh1b, v1);
@@ -498,11 +511,24 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
                 }
                 dp0 = P::mul(P::fma(v0, dp0, r0), i0v);
                 dp1 = P::mul(P::fma(v1, dp1, r1), i1v);
+                R g0 = dp0, g1 = dp1;
+                if constexpr (GFORM) {
+                    // g_k = u_k + rho d'_k - w_k u_{k+1} (um*, uc* now hold u_k, u_{k+1})
+                    R w0, w1;
+                    if (percol) {
+                        w0 = P::mul(v0, i0v);
+                        w1 = P::mul(v1, i1v);
+                    } else {
+                        w0 = w1 = P::ld(L.fw, k);
+                    }
+                    g0 = P::fma(P::neg(w0), uc0, P::fma(cf, dp0, um0));
+                    g1 = P::fma(P::neg(w1), uc1, P::fma(cf, dp1, um1));
+                }
                 if constexpr ((HINT & HINT_KEEP) != 0) {
-                    st_pair_pol(gstack + ((size_t)k * NT + tid) * 2, dp0, dp1, pol_last);
+                    st_pair_pol(gstack + ((size_t)k * NT + tid) * 2, g0, g1, pol_last);
                 } else {
-                    P::st(gstack, ((size_t)k * NT + tid) * 2, dp0);
-                    P::st(gstack, ((size_t)k * NT + tid) * 2 + 1, dp1);
+                    P::st(gstack, ((size_t)k * NT + tid) * 2, g0);
+                    P::st(gstack, ((size_t)k * NT + tid) * 2 + 1, g1);
                 }
             }
             if (HALO) __syncthreads();  // the slot is reused by the next issue
@@ -512,11 +538,12 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
         cp_wait<0>();
 
         if constexpr (STACK) {
-            constexpr bool NEED_U = MODE == MODE_SMOOTH;
+            // back substitution from the stacked values and v/m_k (and u_k unless GFORM)
+            constexpr bool NEED_U = MODE == MODE_SMOOTH && !GFORM;
             __syncthreads();  // the backward ring reuses the forward ring's shared memory
-            S* bU = reinterpret_cast<S*>(smem_raw);
-            S* bW = bU + PD * 2 * NT;
+            S* bW = reinterpret_cast<S*>(smem_raw);
             S* bD = bW + PD * 2 * NT;
+            S* bU = bD + PD * 2 * NT;
             auto issue_back = [&](int k, int s2) {
                 if (k >= 0) {
                     const size_t id = (size_t)k * pl + c;
@@ -532,7 +559,6 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
                 cp_commit();
             };
             for (int s = 0; s < PD; ++s) issue_back(nz - 1 - s, s);
-            const R cf = P::cst(coef);
             R x0 = vzero, x1 = vzero;
             slot = 0;
             for (int k = nz - 1; k >= 0; --k) {
@@ -554,12 +580,18 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
                 x0 = P::fma(w0, x0, P::ld_plain(bD, o));
                 x1 = P::fma(w1, x1, P::ld_plain(bD, o + 1));
                 const size_t id = (size_t)k * pl + c;
-                if constexpr (NEED_U && (HINT & HINT_STREAM) != 0) {
-                    st_pair_pol(reinterpret_cast<S*>(out) + id, P::fma(cf, x0, P::ld_plain(bU, o)),
-                                P::fma(cf, x1, P::ld_plain(bU, o + 1)), pol_first);
-                } else if constexpr (NEED_U) {
-                    P::st(reinterpret_cast<S*>(out), id, P::fma(cf, x0, P::ld_plain(bU, o)));
-                    P::st(reinterpret_cast<S*>(out), id + 1, P::fma(cf, x1, P::ld_plain(bU, o + 1)));
+                if constexpr (MODE == MODE_SMOOTH) {
+                    R o0 = x0, o1 = x1;  // GFORM: the recurrence already yields u'
+                    if constexpr (NEED_U) {
+                        o0 = P::fma(cf, x0, P::ld_plain(bU, o));  // u' = u + rho x
+                        o1 = P::fma(cf, x1, P::ld_plain(bU, o + 1));
+                    }
+                    if constexpr ((HINT & HINT_STREAM) != 0) {
+                        st_pair_pol(reinterpret_cast<S*>(out) + id, o0, o1, pol_first);
+                    } else {
+                        P::st(reinterpret_cast<S*>(out), id, o0);
+                        P::st(reinterpret_cast<S*>(out), id + 1, o1);
+                    }
                 } else {
                     P::st(reinterpret_cast<S*>(out), id, coef != 1.0 ? P::mul(cf, x0) : x0);
                     P::st(reinterpret_cast<S*>(out), id + 1, coef != 1.0 ? P::mul(cf, x1) : x1);
@@ -610,9 +642,9 @@ static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, con
 // Smooth: eight variants per precision -- three (TY, PD) tile shapes with the shared-memory stack
 // (0-2), two persistent ones with the stack in global scratch (3, 4), and three persistent ones with
 // two columns per thread and L2 eviction hints (k_sweep_x2; 5-7); the autotuner (tpmg_autotune)
-// times them per level and stores its choice in Lv::variant. An untuned level takes variant 6 where
-// the two-column form applies (nx % 64 == 0, aligned fields), else variant 3; in native FP64,
-// variant 0.
+// times them per level and stores its choice in Lv::variant. An untuned level takes variant 6
+// (double-word) or 5 (FP32) where the two-column form applies (nx % 64 == 0, aligned fields), else
+// variant 3; in native FP64, variant 0.
 template <class P>
 struct SmoothVariants;
 template <>
@@ -635,7 +667,9 @@ static int smooth_dispatch(const Lv<P>& L, double rho, const typename P::S* u, c
     if (v < 0 || v >= TPMG_NUM_VARIANTS) {
         v = 0;
         if (L.gstack && P::id != 0) {  // native FP64 is bound by its slow pipe: one column per thread
-            const int nb = run_sweep_x2<P, P, 2, 4, MODE_SMOOTH, 10, HINT_ALL>(L, rho, u, f, uo, partials, done, s, 12);
+            const int nb = P::id == 1
+                               ? run_sweep_x2<P, P, 2, 4, MODE_SMOOTH, 1, HINT_ALL>(L, rho, u, f, uo, partials, done, s, 8)
+                               : run_sweep_x2<P, P, 2, 4, MODE_SMOOTH, 10, HINT_ALL>(L, rho, u, f, uo, partials, done, s, 12);
             if (nb >= 0) return nb;
             v = 3;
         }
