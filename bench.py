@@ -241,6 +241,32 @@ def bench_mixed(tpmg, torch):
     return out
 
 
+def bench_paper_shaped(tpmg, torch):
+    """The paper's own configuration on 512^2 x 128 (omega = 4.2 h, kappa ~ 142, lambda^2 = 1e3): V(1,1)
+    multigrid with rho = 2/3 on 5 levels and line-preconditioned CG, both to 1e-5, FP64-accurate
+    (double-word). The paper's figures on one K20X are context: 8 V-cycles of 88.8 ms, 59 CG
+    iterations of 29.7 ms."""
+    p = workloads.paper_shaped()
+    op = tpmg.Operator.from_problem(p, nlevels=5)
+    f = torch.from_numpy(p.rhs()).cuda()
+    u = torch.zeros_like(f)
+    out = {"workload": p.name}
+    for name, fn, prm in [
+            ("mg_v11", tpmg.mg_solve, tpmg.default_params(prec=tpmg.DW, tol=1e-5, max_iter=50, nu_pre=1, nu_post=1,
+                                                          rho=2.0 / 3.0, zero_guess=1)),
+            ("cg", tpmg.cg_solve, tpmg.default_params(prec=tpmg.DW, tol=1e-5, max_iter=500, zero_guess=1))]:
+        ms = []
+        for _ in range(3):
+            r = fn(op.op, prm, f, u, p.n)
+            ms.append(r["ms"])
+        best = min(ms[1:])
+        out[name] = {"ms": round(best, 3), "iters": r["iters"], "rel_res": r["rel_res"],
+                     "ms_per_iter": round(best / max(r["iters"], 1), 4)}
+    out["paper_k20x"] = {"mg_iters": 8, "ms_per_vcycle": 88.8, "cg_iters": 59, "ms_per_cg_iter": 29.7}
+    op.close()
+    return out
+
+
 def bench_learned(tpmg, torch):
     """The learned stage: pairs from the multigrid solver on 256^2 x 64 crops, Adam on the residual
     loss, then flexible CG with and without the network on 2048^2 x 64 (h = 1/2048), beside plain
@@ -495,6 +521,7 @@ def run_ours(args, rank, world, dist):
     # batched workload: 64 problems of drawn sizes in one persistent launch vs one solve after another
     variants["batched_64"] = bench_batched(tpmg, torch)
     variants["mixed_1024x1024x128"] = bench_mixed(tpmg, torch)
+    variants["paper_shaped_512x512x128"] = bench_paper_shaped(tpmg, torch)
     variants["learned_2048x2048x64"] = bench_learned(tpmg, torch)
 
     cpu = None

@@ -190,3 +190,28 @@ def test_zero_guess_ignores_u(small, solver, prec):
         out.append((res["iters"], res["history"], host(u)))
     assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
     assert np.array_equal(out[0][2], out[1][2])
+
+
+def test_paper_shaped_configuration_matches_oracle():
+    """The paper's own setting (Sec. 5: omega = 4.2 h, 5 levels, V(1,1), rho = 2/3, eps = 1e-5) on
+    128^2 x 64: the FP64-accurate GPU multigrid takes the oracle's cycles with its residual history,
+    and the GPU CG takes the oracle's iteration count within one."""
+    p = workloads.paper_shaped(128, 64)
+    op = tpmg.Operator.from_problem(p)
+    cx, cy, v = oracle.problem_coefficients(p)
+    f = p.rhs()
+    _, it_mg, hist_mg, _ = oracle.mg_solve(f, cx, cy, v, p.nlevels, tol=1e-5, max_iter=50, nu_pre=1, nu_post=1,
+                                           rho=2.0 / 3.0)
+    _, it_cg, _, _ = oracle.cg_solve(f, cx, cy, v, tol=1e-5, max_iter=500)
+    fd = dev(f, tpmg.F64).reshape(-1)
+    u = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    res = tpmg.mg_solve(op.op, tpmg.default_params(prec=tpmg.DW, tol=1e-5, max_iter=50, nu_pre=1, nu_post=1,
+                                                   rho=2.0 / 3.0), fd, u, p.n)
+    assert res["converged"] and res["iters"] == it_mg
+    assert np.allclose(res["history"], hist_mg, rtol=1e-8, atol=0)
+    u.zero_()
+    res = tpmg.cg_solve(op.op, tpmg.default_params(prec=tpmg.DW, tol=1e-5, max_iter=500), fd, u, p.n)
+    assert res["converged"] and abs(res["iters"] - it_cg) <= 1
+    r = oracle.residual(host(u).reshape(f.shape), f, cx, cy, v)
+    assert np.linalg.norm(r) / np.linalg.norm(f) < 1e-5
+    op.close()

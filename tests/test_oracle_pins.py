@@ -394,3 +394,24 @@ def test_vcycle_matches_matrix_form_of_algorithm_1(nu_pre, nu_post, n_coarse, rh
     got = oracle.vcycle(u0, f, cx, cy, v, nlevels=L, nu_pre=nu_pre, nu_post=nu_post,
                         n_coarse=n_coarse, rho=rho)
     assert rel(got, cyc(u0, f)) < 1e-11
+
+
+def test_paper_shaped_iteration_counts_near_the_paper():
+    """Sec. 5.1, Table SingleGPUTiming: with omega = 4.2 h, 5 levels, V(1,1), rho = 2/3 and eps =
+    1e-5 the paper's multigrid takes 8-9 cycles and line-preconditioned CG 58-70 iterations. The
+    paper's lambda(h) is not reproduced in its text (this build takes lambda^2 = 1e3) and the grid
+    here is 128^2 x 64, so the counts are pinned to a band: multigrid within two cycles of the
+    paper's 9 at nx = 128, CG no more than the classical bound ceil(sqrt(kappa)/2 ln(2/eps)) and
+    no fewer than 3/4 of the paper's smallest count."""
+    from paper_1402_3545_gb300 import workloads
+    g = read_golden("paper_iterations.txt")
+    p = workloads.paper_shaped(128, 64)
+    assert p.nlevels == 5
+    cx, cy, v = oracle.problem_coefficients(p)
+    f = p.rhs()
+    _, it_mg, _, conv_mg = oracle.mg_solve(f, cx, cy, v, p.nlevels, tol=1e-5, max_iter=50, nu_pre=1, nu_post=1,
+                                           rho=2.0 / 3.0)
+    assert conv_mg and abs(it_mg - g["mg_128"]) <= 2, it_mg
+    _, it_cg, _, conv_cg = oracle.cg_solve(f, cx, cy, v, tol=1e-5, max_iter=500)
+    assert conv_cg
+    assert 0.75 * g["cg_768"] <= it_cg <= cg_iteration_bound(1 + 8 * cx, 1e-5), it_cg
