@@ -216,7 +216,8 @@ def nn_flops_per_voxel(cin: int) -> int:
 
 def bench_mixed(tpmg, torch):
     """Mixed precision on its own workload (1024^2 x 128, lambda^2 = 1e4): FP32 V-cycles inside
-    double-word refinement at 1e-6 and 1e-10, error against a 1e-12 double-word solution."""
+    double-word refinement at 1e-6 and 1e-10, error against a 1e-12 double-word solution; also with
+    the inner cycle's coarse levels holding BF16 values (coarse_bf16, a convergence measurement)."""
     p = workloads.mixed()
     op = tpmg.Operator.from_problem(p)
     f = torch.from_numpy(p.rhs()).cuda()
@@ -225,9 +226,11 @@ def bench_mixed(tpmg, torch):
     tpmg.mg_solve(op.op, tpmg.default_params(prec=tpmg.DW, tol=1e-12, max_iter=100), f, ustar, n)
     nrm = float(torch.linalg.vector_norm(ustar).item())
     out = {"workload": p.name}
-    for name, prec, tol in [("dw_1e-6", tpmg.DW, 1e-6), ("mixed_1e-6", tpmg.MIXED, 1e-6),
-                            ("mixed_1e-10", tpmg.MIXED, 1e-10)]:
-        prm = tpmg.default_params(prec=prec, tol=tol, max_iter=100)
+    for name, prec, tol, bf in [("dw_1e-6", tpmg.DW, 1e-6, 0), ("mixed_1e-6", tpmg.MIXED, 1e-6, 0),
+                                ("mixed_1e-10", tpmg.MIXED, 1e-10, 0),
+                                ("mixed_1e-6_bf16_coarse", tpmg.MIXED, 1e-6, 1),
+                                ("mixed_1e-10_bf16_coarse", tpmg.MIXED, 1e-10, 1)]:
+        prm = tpmg.default_params(prec=prec, tol=tol, max_iter=100, coarse_bf16=bf)
         u = torch.zeros_like(f)
         ms = []
         for _ in range(3):
@@ -507,9 +510,10 @@ def run_ours(args, rank, world, dist):
 
     # the other precisions on the same problem (one solve each, after a warm-up solve)
     variants = {}
-    for name, vprec, tol in [("f64_native", tpmg.F64, 1e-6), ("mixed_fp32_inner", tpmg.MIXED, 1e-6),
-                             ("mixed_fp32_inner_1e-10", tpmg.MIXED, 1e-10)]:
-        vp = tpmg.default_params(prec=vprec, tol=tol, max_iter=100)
+    for name, vprec, tol, bf in [("f64_native", tpmg.F64, 1e-6, 0), ("mixed_fp32_inner", tpmg.MIXED, 1e-6, 0),
+                                 ("mixed_fp32_inner_1e-10", tpmg.MIXED, 1e-10, 0),
+                                 ("mixed_bf16_coarse", tpmg.MIXED, 1e-6, 1)]:
+        vp = tpmg.default_params(prec=vprec, tol=tol, max_iter=100, coarse_bf16=bf)
         for _ in range(2):
             u.zero_()
             r = tpmg.mg_solve(op.op, vp, fd, u, n)

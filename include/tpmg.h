@@ -143,6 +143,9 @@ typedef struct {
                          default 1.0 s; when it runs out the solve ends with TPMG_ERR_TIMEOUT */
     int zero_guess;  /* 1: start from u = 0 without reading u (u is then output only), 0: start from
                         the u passed in (default) */
+    int coarse_bf16; /* TPMG_MIXED multigrid only: 1 rounds every value the inner FP32 V-cycle stores
+                        on the levels below the finest to BF16 (kept in FP32 words), to measure how
+                        BF16 storage of the coarse levels affects convergence; 0 (default): FP32 */
 } tpmg_params;
 
 typedef struct {

@@ -109,6 +109,8 @@ template <>
 const float* vptr<PolF32>(const tpmg_op* op, int l) { return op->v32[l]; }
 template <>
 const float2* vptr<PolDW>(const tpmg_op* op, int l) { return op->vdw[l]; }
+template <>
+const float* vptr<PolF32B>(const tpmg_op* op, int l) { return op->v32[l]; }
 
 template <class P>
 static Lv<P> level_view(const tpmg_op* op, int l) {
@@ -483,19 +485,24 @@ static tpmg_status mixed_loop(tpmg_op* op, const tpmg_params* prm, float2* uD, c
     CK(cudaGetLastError());
     TRY(read_scalars(op, s));
     auto body = [&](cudaStream_t st) {
-        Cycle<PolF32, PolF32> c(op, prm, st, done, 1);
         void* cur = e;
         void* oth = eb;
         // first smoothing step from e = 0: e = rho M^{-1} r
         launch_line_solve<PolF32>(L32, r32, e, prm->rho, done, st);
-        c.rest(cur, oth);
+        if (prm->coarse_bf16) {
+            Cycle<PolF32, PolF32B> c(op, prm, st, done, L);  // levels below the finest hold BF16 values
+            c.rest(cur, oth);
+        } else {
+            Cycle<PolF32, PolF32> c(op, prm, st, done, 1);
+            c.rest(cur, oth);
+        }
         launch_correct<PolDW>(nfine, uD, (const float*)cur, done, st);
         const int np = launch_residual<PolDW, PolF32>(LD, uD, fD, r32, op->partials, done, st);
         launch_finalize_norm(op->partials, np, FIN_MG_CYCLE, op->sc, op->history, nullptr, st);
     };
     std::vector<const void*> key = {uD, fD, e, op->history, (const void*)(size_t)prm->nu_pre,
                                     (const void*)(size_t)prm->nu_post, (const void*)(size_t)prm->n_coarse,
-                                    (const void*)(size_t)(prm->rho * 1e12)};
+                                    (const void*)(size_t)(prm->rho * 1e12), (const void*)(size_t)prm->coarse_bf16};
     int guard = 0;
     while (!op->sc_host->done && guard++ <= prm->max_iter + 1) {
         TRY(run_iteration(op, 3, key, prm->use_graph != 0, s, body));
@@ -973,6 +980,7 @@ void tpmg_default_params(tpmg_params* p) {
     p->use_graph = 1;
     p->timeout_s = 1.0;
     p->zero_guess = 0;
+    p->coarse_bf16 = 0;
 }
 
 // The initial iterate: the caller's u, converted to the solve's storage, or zero without reading u.

@@ -13,6 +13,7 @@
 //         sum (TwoSum of the high parts plus the low parts, renormalised): its error is bounded by
 //         a few units of 2^-48 times |a| + |b|, the absolute accuracy a stencil sum needs.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -116,6 +117,9 @@ struct PolF64 {
     __device__ __forceinline__ static R ld(const S* p, size_t i) { return __ldg(p + i); }
     __device__ __forceinline__ static R ld_plain(const S* p, size_t i) { return p[i]; }
     __device__ __forceinline__ static void st(S* p, size_t i, R x) { p[i] = x; }
+    // scratch store (never rounded to a storage format) and the storage rounding of a value
+    __device__ __forceinline__ static void sts(S* p, size_t i, R x) { p[i] = x; }
+    __device__ __forceinline__ static R rnd(R x) { return x; }
     __device__ __forceinline__ static R cst(double x) { return x; }
     __device__ __forceinline__ static double to_d(R x) { return x; }
     __device__ __forceinline__ static R zero() { return 0.0; }
@@ -142,6 +146,8 @@ struct PolF32 {
     __device__ __forceinline__ static R ld(const S* p, size_t i) { return __ldg(p + i); }
     __device__ __forceinline__ static R ld_plain(const S* p, size_t i) { return p[i]; }
     __device__ __forceinline__ static void st(S* p, size_t i, R x) { p[i] = x; }
+    __device__ __forceinline__ static void sts(S* p, size_t i, R x) { p[i] = x; }
+    __device__ __forceinline__ static R rnd(R x) { return x; }
     __device__ __forceinline__ static R cst(double x) { return (float)x; }
     __device__ __forceinline__ static double to_d(R x) { return (double)x; }
     __device__ __forceinline__ static R zero() { return 0.0f; }
@@ -178,6 +184,8 @@ struct PolDW {
         return dw{v.x, v.y};
     }
     __device__ __forceinline__ static void st(S* p, size_t i, R x) { p[i] = make_float2(x.hi, x.lo); }
+    __device__ __forceinline__ static void sts(S* p, size_t i, R x) { p[i] = make_float2(x.hi, x.lo); }
+    __device__ __forceinline__ static R rnd(R x) { return x; }
     __device__ __forceinline__ static R cst(double x) {
         float h = __double2float_rn(x);
         return dw{h, __double2float_rn(x - (double)h)};
@@ -204,6 +212,15 @@ struct PolDW {
     __device__ __forceinline__ static double acc_get(Acc s, Acc c) { return (double)s - (double)c; }
     __device__ __forceinline__ static float to_f(R x) { return __fadd_rn(x.hi, x.lo); }
     __device__ __forceinline__ static R from_f(float x) { return dw{x, 0.0f}; }
+};
+
+// FP32 arithmetic with every stored field value rounded to BF16 (8-bit significand, round to nearest
+// even) and kept in an FP32 word: the values a BF16 store of the coarse levels would hold, used to
+// measure how BF16 coarse-level storage affects convergence. Scratch (the Thomas stacks) is not
+// rounded. It shares the FP32 workspaces and Thomas factors (id 1).
+struct PolF32B : PolF32 {
+    __device__ __forceinline__ static float rnd(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+    __device__ __forceinline__ static void st(S* p, size_t i, R x) { p[i] = rnd(x); }
 };
 
 }  // namespace tpmg

@@ -108,7 +108,7 @@ __device__ __forceinline__ typename P::R pcr_solve(const Lv<P>& L, typename P::R
     const int colp = (L.fac_percol && act) ? col : 0;
     for (int t = 0; t < L.pcr_steps; ++t) {
         const int s = 1 << t;
-        P::st(buf, (size_t)k * cpb + tx, d);
+        P::sts(buf, (size_t)k * cpb + tx, d);
         __syncthreads();
         const R dm = (k - s >= 0) ? P::ld_plain(buf, (size_t)(k - s) * cpb + tx) : P::zero();
         const R dp = (k + s < nz) ? P::ld_plain(buf, (size_t)(k + s) * cpb + tx) : P::zero();
@@ -431,6 +431,11 @@ int launch_prolongate_x4(int nxc, int nyc, int nz, const typename P::S* uc, type
 TPMG_COARSE_INST(PolF64)
 TPMG_COARSE_INST(PolF32)
 TPMG_COARSE_INST(PolDW)
+TPMG_COARSE_INST(PolF32B)
+template int launch_restrict_smooth_pcr<PolF32, PolF32B>(const Lv<PolF32B>&, double, const float*, float*, float*,
+                                                         const int*, cudaStream_t);
+template int launch_prolongate_cell<PolF32B, PolF32>(int, int, int, const float*, float*, const int*, cudaStream_t);
+template int launch_prolongate_x4<PolF32B, PolF32>(int, int, int, const float*, float*, const int*, cudaStream_t);
 template int launch_restrict_smooth_pcr<PolDW, PolF64>(const Lv<PolF64>&, double, const float2*, double*, double*,
                                                        const int*, cudaStream_t);
 template int launch_prolongate_cell<PolF64, PolDW>(int, int, int, const double*, float2*, const int*, cudaStream_t);

@@ -444,6 +444,10 @@ void launch_correct(size_t n, typename P::S* u, const float* e, const int* done,
 TPMG_INST(PolF64)
 TPMG_INST(PolF32)
 TPMG_INST(PolDW)
+TPMG_INST(PolF32B)
+template void launch_restrict_smooth<PolF32, PolF32B>(const Lv<PolF32B>&, double, const float*, float*, float*,
+                                                      const int*, cudaStream_t);
+template void launch_prolongate<PolF32B, PolF32>(int, int, int, const float*, float*, const int*, cudaStream_t);
 template int launch_residual<PolDW, PolF32>(const Lv<PolDW>&, const float2*, const float2*, float*,
                                              double*, const int*, cudaStream_t);
 template int launch_residual<PolF64, PolF32>(const Lv<PolF64>&, const double*, const double*,

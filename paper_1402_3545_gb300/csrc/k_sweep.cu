@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
                     g = P::fma(P::neg(w), uc, P::fma(cf, d, um));
                 }
                 if constexpr (GS)
-                    P::st(gstack, (size_t)k * NT + tid, g);
+                    P::sts(gstack, (size_t)k * NT + tid, g);
                 else
                     stack[(size_t)k * NT + tid] = g;
                 d_prev = d;
@@ -527,8 +527,8 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
                 if constexpr ((HINT & HINT_KEEP) != 0) {
                     st_pair_pol(gstack + ((size_t)k * NT + tid) * 2, g0, g1, pol_last);
                 } else {
-                    P::st(gstack, ((size_t)k * NT + tid) * 2, g0);
-                    P::st(gstack, ((size_t)k * NT + tid) * 2 + 1, g1);
+                    P::sts(gstack, ((size_t)k * NT + tid) * 2, g0);
+                    P::sts(gstack, ((size_t)k * NT + tid) * 2 + 1, g1);
                 }
             }
             if (HALO) __syncthreads();  // the slot is reused by the next issue
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
                         o1 = P::fma(cf, x1, P::ld_plain(bU, o + 1));
                     }
                     if constexpr ((HINT & HINT_STREAM) != 0) {
-                        st_pair_pol(reinterpret_cast<S*>(out) + id, o0, o1, pol_first);
+                        st_pair_pol(reinterpret_cast<S*>(out) + id, P::rnd(o0), P::rnd(o1), pol_first);
                     } else {
                         P::st(reinterpret_cast<S*>(out), id, o0);
                         P::st(reinterpret_cast<S*>(out), id + 1, o1);
@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(32 * TY) k_restrict_smooth_pp(Lv<P> Lc, double
             const R inv = percol ? P::ld_plain(ringI, slot * NT + tid) : P::ld(Lc.finv, k);
             const R d = P::mul(P::fma(vv, d_prev, fk), inv);
             if constexpr (GS)
-                P::st(gstack, (size_t)k * NT + tid, d);
+                P::sts(gstack, (size_t)k * NT + tid, d);
             else
                 stack[(size_t)k * NT + tid] = d;
             d_prev = d;
@@ -876,6 +876,9 @@ int launch_restrict_smooth_pp(const Lv<P>& Lc, double rho, const typename PF::S*
 TPMG_SWEEP_INST(PolF64)
 TPMG_SWEEP_INST(PolF32)
 TPMG_SWEEP_INST(PolDW)
+TPMG_SWEEP_INST(PolF32B)
+template int launch_restrict_smooth_pp<PolF32, PolF32B>(const Lv<PolF32B>&, double, const float*, float*, float*,
+                                                        const int*, cudaStream_t);
 template int launch_residual_pp<PolF64, PolF32>(const Lv<PolF64>&, const double*, const double*, float*, double*,
                                                 const int*, cudaStream_t);
 template int launch_residual_pp<PolDW, PolF32>(const Lv<PolDW>&, const float2*, const float2*, float*, double*,

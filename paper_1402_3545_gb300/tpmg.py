@@ -36,7 +36,7 @@ class Params(ctypes.Structure):
     _fields_ = [("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("n_coarse", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("rho", ctypes.c_double), ("tol", ctypes.c_double),
                 ("prec", ctypes.c_int), ("use_graph", ctypes.c_int), ("timeout_s", ctypes.c_double),
-                ("zero_guess", ctypes.c_int)]
+                ("zero_guess", ctypes.c_int), ("coarse_bf16", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

@@ -67,6 +67,7 @@ def test_default_params_layout_without_gpu():
     from paper_1402_3545_gb300 import tpmg
     p = tpmg.default_params()
     assert (p.nu_pre, p.nu_post, p.n_coarse, p.max_iter) == (2, 2, 2, 100)
-    assert (p.rho, p.tol, p.prec, p.use_graph, p.timeout_s, p.zero_guess) == (0.8, 1e-6, tpmg.DW, 1, 1.0, 0)
+    assert (p.rho, p.tol, p.prec, p.use_graph, p.timeout_s, p.zero_guess, p.coarse_bf16) == (0.8, 1e-6, tpmg.DW, 1, 1.0,
+                                                                                           0, 0)
     with pytest.raises(TypeError):
         tpmg.default_params(zero_gues=1)

@@ -215,3 +215,22 @@ def test_paper_shaped_configuration_matches_oracle():
     r = oracle.residual(host(u).reshape(f.shape), f, cx, cy, v)
     assert np.linalg.norm(r) / np.linalg.norm(f) < 1e-5
     op.close()
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-10])
+def test_mixed_solve_with_bf16_coarse_levels(small, tol):
+    """BF16 values on the inner V-cycle's coarse levels (coarse_bf16): the refinement still reaches
+    the tolerance (the outer residual is double-word), within two cycles of FP32 coarse levels, and
+    the result's residual recomputed by the oracle meets it."""
+    p, op, (cx, cy, v), f, _ = small
+    fd = dev(f, tpmg.F64).reshape(-1)
+    its = []
+    for bf in (0, 1):
+        u = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+        res = tpmg.mg_solve(op.op, tpmg.default_params(prec=tpmg.MIXED, tol=tol, max_iter=60, coarse_bf16=bf), fd, u,
+                            p.n)
+        assert res["converged"], (bf, res)
+        r = oracle.residual(host(u).reshape(f.shape), f, cx, cy, v)
+        assert np.linalg.norm(r) / np.linalg.norm(f) < tol * 1.001
+        its.append(res["iters"])
+    assert its[1] <= its[0] + 2, its
