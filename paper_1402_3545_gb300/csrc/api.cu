@@ -1321,9 +1321,11 @@ static void cycle_tasks(tpmg_op* op, int b, const tpmg_params* prm, std::vector<
         t.b = rhs;
         t.out = o;
         t.out2 = o2;
-        const int nxl = (type == BT_RS) ? op->g.lnx[level] : op->g.lnx[level];
+        const int nxl = op->g.lnx[level];
         const int nyl = op->g.lny[level];
-        t.tiles_x = (nxl + 31) / 32;
+        t.x2 = (type == BT_SMOOTH || type == BT_RESID || type == BT_LS0) &&
+               batched_x2_fits(nxl, nyl, a ? a : rhs, rhs, o);
+        t.tiles_x = t.x2 ? nxl / 64 : (nxl + 31) / 32;
         t.tiles_y = (nyl + BTY - 1) / BTY;
         t.tile_base = 0;
         out.push_back(t);
@@ -1394,7 +1396,8 @@ static tpmg_status build_batch(BatchCache* bc, const tpmg_params* prm) {
         pd.fD = (const float2*)op->hier[2].f[L];
         pd.vD = op->vdw[L];
         pd.r32 = (float*)op->hier[1].f[L];
-        pd.fine_tiles = ((op->g.lnx[L] + 31) / 32) * ((op->g.lny[L] + BTY - 1) / BTY);
+        pd.fine_x2 = batched_x2_fits(op->g.lnx[L], op->g.lny[L], pd.uD, pd.fD, pd.r32) ? 1 : 0;
+        pd.fine_tiles = (pd.fine_x2 ? op->g.lnx[L] / 64 : (op->g.lnx[L] + 31) / 32) * ((op->g.lny[L] + BTY - 1) / BTY);
         pd.part_base = parts;
         parts += pd.fine_tiles;
         cycle_tasks(op, b, prm, lists[b]);
@@ -1426,7 +1429,8 @@ static tpmg_status build_batch(BatchCache* bc, const tpmg_params* prm) {
             t.level = op->g.L;
             if (ph < 2) {
                 t.type = ph == 0 ? BT_OUTRES : BT_FINAL;
-                t.tiles_x = ph == 0 ? (op->g.lnx[op->g.L] + 31) / 32 : 1;
+                t.x2 = ph == 0 ? probs[b].fine_x2 : 0;
+                t.tiles_x = ph == 0 ? (t.x2 ? op->g.lnx[op->g.L] / 64 : (op->g.lnx[op->g.L] + 31) / 32) : 1;
                 t.tiles_y = ph == 0 ? (op->g.lny[op->g.L] + BTY - 1) / BTY : 1;
                 tasks.push_back(t);
             } else if (ph - 2 < (int)lists[b].size()) {
@@ -1459,7 +1463,7 @@ static tpmg_status build_batch(BatchCache* bc, const tpmg_params* prm) {
                   cudaMemcpyHostToDevice));
     CK(cudaMemcpy(bc->d_phase_tiles, bc->h_phase_tiles.data(), sizeof(int) * bc->h_phase_tiles.size(),
                   cudaMemcpyHostToDevice));
-    bc->smem = 0;
+    bc->smem = batched_smem_bytes();
     int per_sm = batched_blocks_per_sm();
     int nsm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, bc->ops[0]->device));

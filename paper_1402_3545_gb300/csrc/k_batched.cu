@@ -15,6 +15,7 @@
 // forward-eliminated values on a per-block stack in global scratch (L2-resident; a stack in shared
 // memory would leave room for only three blocks per SM).
 #include "kernels.cuh"
+#include "sweep_x2.cuh"
 
 namespace tpmg {
 
@@ -265,9 +266,45 @@ __device__ void t_final(const BatchDesc& d, int prob, int it) {
     __syncthreads();
 }
 
+// ---------------------------------------------------------------- two-column tiles
+// Levels whose nx is a multiple of 64 (and ny of BTY) run their Smooth, Residual and first line
+// solve, and the outer double-word residual, on tiles of 64 x BTY columns with the plane-pipelined
+// two-column sweep of the single-problem solver (sweep_x2.cuh): the block's dynamic shared memory
+// holds the rings, its scratch slot the Thomas stack.
+constexpr int BPD = 4;  // ring depth of the two-column sweeps
+
+__device__ __forceinline__ Lv<PolF32> lv32(const BLevelDesc& b) {
+    Lv<PolF32> L;
+    L.nx = b.nx;
+    L.ny = b.ny;
+    L.nz = b.nz;
+    L.cx = b.cx;
+    L.cy = b.cy;
+    L.v = b.v;
+    L.finv = b.finv;
+    L.fw = b.fw;
+    L.fac_percol = b.percol;
+    L.variant = -1;
+    return L;
+}
+
+bool batched_x2_fits(int nx, int ny, const void* a, const void* b, const void* out) {
+    auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+    return nx % 64 == 0 && ny % BTY == 0 && al(a) && al(b) && al(out);
+}
+
+size_t batched_smem_bytes() {
+    size_t m = sweep_x2_smem<PolDW, BTY, BPD, MODE_RESIDUAL>();
+    const size_t s1 = sweep_x2_smem<PolF32, BTY, BPD, MODE_SMOOTH>();
+    const size_t s2 = sweep_x2_smem<PolF32, BTY, BPD, MODE_LINESOLVE>();
+    m = s1 > m ? s1 : m;
+    return s2 > m ? s2 : m;
+}
+
 // ---------------------------------------------------------------- the persistent kernel
-__global__ void __launch_bounds__(32 * BTY) k_batched(BatchDesc d) {
-    float* stack = d.scratch + (size_t)blockIdx.x * d.nz_max * 32 * BTY;
+__global__ void __launch_bounds__(32 * BTY, 4) k_batched(BatchDesc d) {
+    extern __shared__ __align__(16) unsigned char bsmem[];
+    float* stack = d.scratch + (size_t)blockIdx.x * d.nz_max * 64 * BTY;
     __shared__ double red[32];
     const float rho = (float)d.rho;
     for (int it = 0; it <= d.max_iter; ++it) {
@@ -291,6 +328,45 @@ __global__ void __launch_bounds__(32 * BTY) k_batched(BatchDesc d) {
                 const int loc = t - tk.tile_base;
                 const int i0 = (loc % tk.tiles_x) * 32, j0 = (loc / tk.tiles_x) * BTY;
                 const BProbDesc& pb = d.probs[tk.prob];
+                if (tk.x2) {
+                    switch (tk.type) {
+                        case BT_OUTRES: {
+                            Lv<PolDW> LD;
+                            const BLevelDesc& bl = pb.lev[pb.L];
+                            LD.nx = bl.nx;
+                            LD.ny = bl.ny;
+                            LD.nz = bl.nz;
+                            LD.cx = bl.cx;
+                            LD.cy = bl.cy;
+                            LD.v = pb.vD;
+                            LD.finv = LD.fw = nullptr;
+                            LD.fac_percol = 0;
+                            LD.variant = -1;
+                            const double s = sweep_x2_tiles<PolDW, PolF32, BTY, BPD, MODE_RESIDUAL, 0>(
+                                LD, 1.0, pb.uD, pb.fD, pb.r32, true, loc, loc + 1, 1, nullptr, bsmem);
+                            if (threadIdx.x == 0 && threadIdx.y == 0) d.partials[pb.part_base + loc] = s;
+                            break;
+                        }
+                        case BT_LS0:
+                            sweep_x2_tiles<PolF32, PolF32, BTY, BPD, MODE_LINESOLVE, HINT_ALL>(
+                                lv32(pb.lev[tk.level]), d.rho, (const float*)tk.b, nullptr, (float*)tk.out, false, loc,
+                                loc + 1, 1, stack, bsmem);
+                            break;
+                        case BT_SMOOTH:
+                            sweep_x2_tiles<PolF32, PolF32, BTY, BPD, MODE_SMOOTH, HINT_ALL>(
+                                lv32(pb.lev[tk.level]), d.rho, (const float*)tk.a, (const float*)tk.b, (float*)tk.out,
+                                false, loc, loc + 1, 1, stack, bsmem);
+                            break;
+                        case BT_RESID:
+                            sweep_x2_tiles<PolF32, PolF32, BTY, BPD, MODE_RESIDUAL, 0>(
+                                lv32(pb.lev[tk.level]), 1.0, (const float*)tk.a, (const float*)tk.b, (float*)tk.out,
+                                false, loc, loc + 1, 1, nullptr, bsmem);
+                            break;
+                        default:
+                            break;
+                    }
+                    continue;
+                }
                 switch (tk.type) {
                     case BT_OUTRES: {
                         double s = t_outres(pb, i0, j0);
@@ -333,11 +409,12 @@ __global__ void __launch_bounds__(32 * BTY) k_batched(BatchDesc d) {
 
 int batched_blocks_per_sm() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batched, 32 * BTY, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batched, 32 * BTY, batched_smem_bytes()) != cudaSuccess)
+        return 0;
     return nb < 8 ? nb : 8;  // 8 x 128 threads per SM; more only grows the scratch
 }
 
-size_t batched_scratch_floats(int grid, int nz_max) { return (size_t)grid * nz_max * 32 * BTY; }
+size_t batched_scratch_floats(int grid, int nz_max) { return (size_t)grid * nz_max * 64 * BTY; }
 
 cudaError_t launch_batched(const BatchDesc& d, int grid, size_t smem, cudaStream_t s) {
     BatchDesc arg = d;

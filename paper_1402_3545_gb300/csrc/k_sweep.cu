@@ -15,32 +15,10 @@
 #include <type_traits>
 
 #include "kernels.cuh"
+#include "sweep_x2.cuh"
 #include "tpmg.h"
 
 namespace tpmg {
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_addr(dst)), "l"(src), "n"(BYTES));
-}
-// the same with an L2 eviction-priority policy (createpolicy) attached to the global read
-template <int BYTES>
-__device__ __forceinline__ void cp_async_pol(void* dst, const void* src, unsigned long long pol) {
-    if constexpr (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst)), "l"(src),
-                     "l"(pol));
-    else
-        asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], %2, %3;\n" ::"r"(smem_addr(dst)), "l"(src),
-                     "n"(BYTES), "l"(pol));
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
 
 __device__ __forceinline__ int wrap_p(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
@@ -76,7 +54,6 @@ void launch_factors(const Lv<P>& L, typename P::S* finv, typename P::S* fw, int 
 }
 
 // ---------------------------------------------------------------- generic pipelined sweep
-enum { MODE_SMOOTH = 0, MODE_RESIDUAL = 1, MODE_LINESOLVE = 2 };
 
 // MODE_SMOOTH:    out = u + coef M^{-1}(f - A u), partial sums of ||f - A u||^2      (Eq. 11)
 // MODE_RESIDUAL:  out = f - A u (stored in PO's precision), partial sums of ||f - A u||^2
@@ -337,275 +314,22 @@ static int run_sweep_pp(const Lv<P>& L, double coef, const typename P::S* u, con
     return (int)(grd.x * grd.y);
 }
 
-// L2 eviction hints of the persistent sweeps (bit mask). The Thomas scratch of a persistent block
-// is written in the forward sweep and read back in the backward sweep a whole column later; the
-// fields stream through L2 in between and, at the default priority, push the scratch out to DRAM
-// (written back, then read again). HINT_STREAM marks the single-use reads (f, 1/m_k, v/m_k, the
-// backward re-read of u) and the result store evict-first; HINT_KEEP stores the scratch
-// evict-last; HINT_DISCARD drops each scratch line from L2 once the backward sweep has read it, so
-// dead scratch is never written back. On the mid workload these cut DRAM traffic of the DW Smooth
-// from 2.03 to 1.76 GB per launch.
-constexpr int HINT_STREAM = 1, HINT_KEEP = 2, HINT_DISCARD = 4, HINT_ALL = 7;
-
 // ---------------------------------------------------------------- two columns per thread
-// The persistent sweep with each thread owning two adjacent columns: a block row covers 64
-// columns, every per-thread load, store and cp.async moves a 16-byte pair, and the two independent
-// Thomas recurrences interleave (twice the instruction-level parallelism per warp). Per cell this
-// halves the address arithmetic, the barriers and the loop control of the one-column kernel.
-// Shared ring per slot: u rows of stride UW = 68 (pad, left halo, 64 columns, right halo, pad),
-// rows j0-1 .. j0+TY; f pairs; 1/m_k pairs. Requires nx % 64 == 0 and 16-byte aligned fields.
+// The body is sweep_x2_tiles (sweep_x2.cuh), shared with the batched persistent kernel.
 template <class P, class PO, int TY, int PD, int MODE, int MINB = 1, int HINT = 0>
 __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef, const typename P::S* __restrict__ u,
                                                       const typename P::S* __restrict__ f,
                                                       typename PO::S* __restrict__ out, double* partials,
                                                       const int* done) {
-    typedef typename P::S S;
-    typedef typename P::R R;
-    constexpr int NT = 32 * TY;
-    constexpr int UW = 68;
-    constexpr bool STACK = MODE != MODE_RESIDUAL;
-    constexpr bool HALO = MODE != MODE_LINESOLVE;
-    constexpr bool GFORM = MODE == MODE_SMOOTH && P::id == 1;  // as in k_sweep_pp
-    constexpr int UPL = HALO ? (TY + 2) * UW : 0;
-    constexpr int FPL = 2 * NT;
-    constexpr int IPL = STACK ? 2 * NT : 0;
-    constexpr int PB = 2 * (int)sizeof(S);  // bytes of a column pair
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (done && *(volatile const int*)done) return;
-
-    const int nx = L.nx, ny = L.ny, nz = L.nz;
-    const bool percol = L.fac_percol != 0;
-    S* ringU = reinterpret_cast<S*>(smem_raw);
-    S* ringF = ringU + PD * UPL;
-    S* ringI = ringF + PD * FPL;
-    S* gstack = STACK ? reinterpret_cast<S*>(L.gstack) + (size_t)blockIdx.x * nz * 2 * NT : nullptr;
-
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-    const size_t pl = (size_t)nx * ny;
-    const int tiles_x = nx / 64;
-    const int ntiles = tiles_x * (ny / TY);
-    const S* rhs = (MODE == MODE_LINESOLVE) ? u : f;
-    const R vzero = P::zero();
-    typename P::Acc acc = 0, cmp = 0;
-    const bool want_norm = partials != nullptr;
-    const bool iso = L.cx == L.cy;
-    unsigned long long pol_first = 0, pol_last = 0;
-    if constexpr (HINT != 0) {
-        pol_first = l2_evict_first();
-        pol_last = l2_evict_last();
-    }
-
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int i0 = (tile % tiles_x) * 64, j0 = (tile / tiles_x) * TY;
-        const size_t c = (size_t)(j0 + ty) * nx + (i0 + 2 * tx);  // the thread's first column
-        __syncthreads();  // the previous tile's rings are no longer read
-
-        // halo of the u plane: 2 rows x 32 pairs (one pair per thread when TY = 2) and 2 TY side
-        // singles; ring offsets and in-plane sources are the same for every plane
-        constexpr int NPAIR = 64, NSIDE = 2 * TY;
-        constexpr int PPT = (NPAIR + NT - 1) / NT;
-        int hp_dst[PPT];
-        size_t hp_src[PPT];
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-            const int it = tid + q * NT;
-            const int top = it < 32, p = it & 31;
-            const int gj = top ? (j0 == 0 ? ny - 1 : j0 - 1) : (j0 + TY == ny ? 0 : j0 + TY);
-            hp_dst[q] = it < NPAIR ? (top ? 0 : (TY + 1) * UW) + 2 + 2 * p : -1;
-            hp_src[q] = (size_t)gj * nx + i0 + 2 * p;
-        }
-        int hs_dst = -1;
-        size_t hs_src = 0;
-        if (tid < NSIDE) {
-            const int r = tid >> 1, right = tid & 1;
-            hs_dst = (r + 1) * UW + (right ? 66 : 1);
-            hs_src = (size_t)(j0 + r) * nx + (right ? (i0 + 64 == nx ? 0 : i0 + 64) : (i0 == 0 ? nx - 1 : i0 - 1));
-        }
-
-        auto issue_plane = [&](int k, int slot) {
-            if (k < nz) {
-                const size_t b = (size_t)k * pl;
-                S* Us = ringU + slot * UPL;
-                if constexpr ((HINT & HINT_STREAM) != 0) {
-                    cp_async_pol<PB>(&ringF[slot * FPL + 2 * tid], rhs + b + c, pol_first);
-                    if (STACK && percol) cp_async_pol<PB>(&ringI[slot * FPL + 2 * tid], L.finv + b + c, pol_first);
-                } else {
-                    cp_async<PB>(&ringF[slot * FPL + 2 * tid], rhs + b + c);
-                    if (STACK && percol) cp_async<PB>(&ringI[slot * FPL + 2 * tid], L.finv + b + c);
-                }
-                if (HALO) {
-                    cp_async<PB>(&Us[(ty + 1) * UW + 2 + 2 * tx], u + b + c);
-#pragma unroll
-                    for (int q = 0; q < PPT; ++q)
-                        if (hp_dst[q] >= 0) cp_async<PB>(&Us[hp_dst[q]], u + b + hp_src[q]);
-                    if (hs_dst >= 0) cp_async<sizeof(S)>(&Us[hs_dst], u + b + hs_src);
-                }
-            }
-            cp_commit();
-        };
-        for (int s = 0; s < PD; ++s) issue_plane(s, s);
-
-        const R v0 = P::ld(L.v, c), v1 = P::ld(L.v, c + 1);
-        const R cx = P::cst(L.cx), cy = P::cst(L.cy), cf = P::cst(coef);
-        const R dh = P::cst(1.0 + 2.0 * L.cx + 2.0 * L.cy);
-        const R dh1a = P::add(dh, v0), dh2a = P::add(dh1a, v0);
-        const R dh1b = P::add(dh, v1), dh2b = P::add(dh1b, v1);
-        R um0 = vzero, um1 = vzero, uc0 = vzero, uc1 = vzero, dp0 = vzero, dp1 = vzero;
-        int slot = 0;
-        const int ctr = (ty + 1) * UW + 2 + 2 * tx;
-        for (int k = 0; k < nz; ++k) {
-            const int nslot = (slot + 1 == PD) ? 0 : slot + 1;
-            R r0, r1;
-            if constexpr (!HALO) {
-                cp_wait<PD - 1>();  // only this thread's own copies are read: no barrier needed
-                r0 = P::ld_plain(ringF, slot * FPL + 2 * tid);
-                r1 = P::ld_plain(ringF, slot * FPL + 2 * tid + 1);
-            } else {
-                cp_wait<PD - 2>();  // planes k and k+1 have landed
-                __syncthreads();    // ... including the halo values other threads fetched
-                const S* Us = ringU + slot * UPL;
-                if (k == 0) {
-                    uc0 = P::ld_plain(Us, ctr);
-                    uc1 = P::ld_plain(Us, ctr + 1);
-                }
-                R up0 = vzero, up1 = vzero;
-                if (k + 1 < nz) {
-                    up0 = P::ld_plain(ringU + nslot * UPL, ctr);
-                    up1 = P::ld_plain(ringU + nslot * UPL, ctr + 1);
-                }
-                const R wv = P::ld_plain(Us, ctr - 1), ev = P::ld_plain(Us, ctr + 2);
-                const R s0 = P::ld_plain(Us, ctr - UW), s1 = P::ld_plain(Us, ctr - UW + 1);
-                const R n0 = P::ld_plain(Us, ctr + UW), n1 = P::ld_plain(Us, ctr + UW + 1);
-                const bool end = nz == 1 || k == 0 || k == nz - 1;
-                const R dga = nz == 1 ? dh : (end ? dh1a : dh2a), dgb = nz == 1 ? dh : (end ? dh1b : dh2b);
-                r0 = sweep_residual<P>(P::ld_plain(ringF, slot * FPL + 2 * tid), dga, uc0, wv, uc1, s0, n0, um0, up0,
-                                       cx, cy, v0, iso);
-                r1 = sweep_residual<P>(P::ld_plain(ringF, slot * FPL + 2 * tid + 1), dgb, uc1, uc0, ev, s1, n1, um1,
-                                       up1, cx, cy, v1, iso);
-                if (want_norm) {
-                    P::acc_dot(acc, cmp, r0, r0);
-                    P::acc_dot(acc, cmp, r1, r1);
-                }
-                um0 = uc0;
-                um1 = uc1;
-                uc0 = up0;
-                uc1 = up1;
-            }
-            if constexpr (MODE == MODE_RESIDUAL) {
-                const size_t id = (size_t)k * pl + c;
-                if constexpr (std::is_same<P, PO>::value) {
-                    P::st(out, id, r0);
-                    P::st(out, id + 1, r1);
-                } else {
-                    PO::st(out, id, PO::from_f(P::to_f(r0)));
-                    PO::st(out, id + 1, PO::from_f(P::to_f(r1)));
-                }
-            }
-            if constexpr (STACK) {
-                R i0v, i1v;
-                if (percol) {
-                    i0v = P::ld_plain(ringI, slot * FPL + 2 * tid);
-                    i1v = P::ld_plain(ringI, slot * FPL + 2 * tid + 1);
-                } else {
-                    i0v = i1v = P::ld(L.finv, k);
-                }
-                dp0 = P::mul(P::fma(v0, dp0, r0), i0v);
-                dp1 = P::mul(P::fma(v1, dp1, r1), i1v);
-                R g0 = dp0, g1 = dp1;
-                if constexpr (GFORM) {
-                    // g_k = u_k + rho d'_k - w_k u_{k+1} (um*, uc* now hold u_k, u_{k+1})
-                    R w0, w1;
-                    if (percol) {
-                        w0 = P::mul(v0, i0v);
-                        w1 = P::mul(v1, i1v);
-                    } else {
-                        w0 = w1 = P::ld(L.fw, k);
-                    }
-                    g0 = P::fma(P::neg(w0), uc0, P::fma(cf, dp0, um0));
-                    g1 = P::fma(P::neg(w1), uc1, P::fma(cf, dp1, um1));
-                }
-                if constexpr ((HINT & HINT_KEEP) != 0) {
-                    st_pair_pol(gstack + ((size_t)k * NT + tid) * 2, g0, g1, pol_last);
-                } else {
-                    P::sts(gstack, ((size_t)k * NT + tid) * 2, g0);
-                    P::sts(gstack, ((size_t)k * NT + tid) * 2 + 1, g1);
-                }
-            }
-            if (HALO) __syncthreads();  // the slot is reused by the next issue
-            issue_plane(k + PD, slot);
-            slot = nslot;
-        }
-        cp_wait<0>();
-
-        if constexpr (STACK) {
-            // back substitution from the stacked values and v/m_k (and u_k unless GFORM)
-            constexpr bool NEED_U = MODE == MODE_SMOOTH && !GFORM;
-            __syncthreads();  // the backward ring reuses the forward ring's shared memory
-            S* bW = reinterpret_cast<S*>(smem_raw);
-            S* bD = bW + PD * 2 * NT;
-            S* bU = bD + PD * 2 * NT;
-            auto issue_back = [&](int k, int s2) {
-                if (k >= 0) {
-                    const size_t id = (size_t)k * pl + c;
-                    if constexpr ((HINT & HINT_STREAM) != 0) {
-                        if (NEED_U) cp_async_pol<PB>(&bU[(s2 * NT + tid) * 2], u + id, pol_first);
-                        if (percol) cp_async_pol<PB>(&bW[(s2 * NT + tid) * 2], L.fw + id, pol_first);
-                    } else {
-                        if (NEED_U) cp_async<PB>(&bU[(s2 * NT + tid) * 2], u + id);
-                        if (percol) cp_async<PB>(&bW[(s2 * NT + tid) * 2], L.fw + id);
-                    }
-                    cp_async<PB>(&bD[(s2 * NT + tid) * 2], gstack + ((size_t)k * NT + tid) * 2);
-                }
-                cp_commit();
-            };
-            for (int s = 0; s < PD; ++s) issue_back(nz - 1 - s, s);
-            R x0 = vzero, x1 = vzero;
-            slot = 0;
-            for (int k = nz - 1; k >= 0; --k) {
-                cp_wait<PD - 1>();
-                if constexpr ((HINT & HINT_DISCARD) != 0) {
-                    // plane k of the stack has landed for every lane of the warp: its lines are dead
-                    constexpr int LANES_PER_LINE = 128 / PB;
-                    __syncwarp();
-                    if (tid % LANES_PER_LINE == 0) l2_discard(gstack + ((size_t)k * NT + tid) * 2);
-                }
-                const int o = (slot * NT + tid) * 2;
-                R w0, w1;
-                if (percol) {
-                    w0 = P::ld_plain(bW, o);
-                    w1 = P::ld_plain(bW, o + 1);
-                } else {
-                    w0 = w1 = P::ld(L.fw, k);
-                }
-                x0 = P::fma(w0, x0, P::ld_plain(bD, o));
-                x1 = P::fma(w1, x1, P::ld_plain(bD, o + 1));
-                const size_t id = (size_t)k * pl + c;
-                if constexpr (MODE == MODE_SMOOTH) {
-                    R o0 = x0, o1 = x1;  // GFORM: the recurrence already yields u'
-                    if constexpr (NEED_U) {
-                        o0 = P::fma(cf, x0, P::ld_plain(bU, o));  // u' = u + rho x
-                        o1 = P::fma(cf, x1, P::ld_plain(bU, o + 1));
-                    }
-                    if constexpr ((HINT & HINT_STREAM) != 0) {
-                        st_pair_pol(reinterpret_cast<S*>(out) + id, P::rnd(o0), P::rnd(o1), pol_first);
-                    } else {
-                        P::st(reinterpret_cast<S*>(out), id, o0);
-                        P::st(reinterpret_cast<S*>(out), id + 1, o1);
-                    }
-                } else {
-                    P::st(reinterpret_cast<S*>(out), id, coef != 1.0 ? P::mul(cf, x0) : x0);
-                    P::st(reinterpret_cast<S*>(out), id + 1, coef != 1.0 ? P::mul(cf, x1) : x1);
-                }
-                issue_back(k - PD, slot);
-                slot = (slot + 1 == PD) ? 0 : slot + 1;
-            }
-            cp_wait<0>();
-        }
-    }
-    if (partials) {
-        double sm = block_sum(P::acc_get(acc, cmp));
-        if (tid == 0) partials[blockIdx.x] = sm;
-    }
+    constexpr bool STACK = MODE != MODE_RESIDUAL;
+    typename P::S* slot =
+        STACK ? reinterpret_cast<typename P::S*>(L.gstack) + (size_t)blockIdx.x * L.nz * 2 * 32 * TY : nullptr;
+    const int ntiles = (L.nx / 64) * (L.ny / TY);
+    const double sm = sweep_x2_tiles<P, PO, TY, PD, MODE, HINT>(L, coef, u, f, out, partials != nullptr, blockIdx.x,
+                                                                 ntiles, gridDim.x, slot, smem_raw);
+    if (partials && threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.x] = sm;
 }
 
 template <class P, class PO, int TY, int PD, int MODE, int MINB = 1, int HINT = 0>
@@ -617,9 +341,7 @@ static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, con
     if (L.nx % 64 || L.ny % TY || (STACK && (!L.gstack || !L.finv || !L.fw))) return -1;
     auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
     if (!al(u) || (HALO && !al(f)) || !al(out) || (STACK && (!al(L.finv) || !al(L.fw)))) return -1;
-    const size_t fwd = (size_t)PD * ((HALO ? (TY + 2) * 68 : 0) + 2 * 32 * TY + (STACK ? 2 * 32 * TY : 0)) * sizeof(S);
-    const size_t back = STACK ? (size_t)PD * 3 * 2 * 32 * TY * sizeof(S) : 0;
-    const size_t smem = fwd > back ? fwd : back;
+    const size_t smem = sweep_x2_smem<P, TY, PD, MODE>();
     auto kern = k_sweep_x2<P, PO, TY, PD, MODE, MINB, HINT>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int ntiles = (L.nx / 64) * (L.ny / TY);

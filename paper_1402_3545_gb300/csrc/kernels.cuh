@@ -291,7 +291,8 @@ struct BProbDesc {
     const float2* vD;   // double-word finest v per column
     float* r32;         // FP32 right-hand side of the inner cycle (finest level)
     int part_base;      // first partial-sum slot of this problem's outer residual norm
-    int fine_tiles;
+    int fine_tiles;     // tiles of the outer residual (= its partial sums)
+    int fine_x2;        // 1: the outer residual runs on two-column tiles
     double* history;    // relative residual history (max_iter + 1 doubles)
 };
 struct BTask {
@@ -301,6 +302,7 @@ struct BTask {
     void* out;
     void* out2;
     int tiles_x, tiles_y, tile_base;
+    int x2;  // 1: tiles of 64 x BTY columns run by the two-column sweep (Smooth, Residual, line solve)
 };
 struct BState {
     double r0, rel;
@@ -322,13 +324,16 @@ struct BatchDesc {
     int max_iter;
     unsigned long long timeout_ns;
     int nz_max;
-    float* scratch;  // Thomas stacks: nz_max x 32 BTY floats per block
+    float* scratch;  // Thomas stacks: nz_max x 64 BTY floats per block
 };
 // cooperative launch of the persistent kernel; returns the CUDA status of the launch
 cudaError_t launch_batched(const BatchDesc& d, int grid, size_t smem, cudaStream_t s);
-// blocks per SM of the persistent kernel (its stacks live in the scratch, so registers decide)
+// blocks per SM of the persistent kernel and its dynamic shared memory (the two-column sweep's rings)
 int batched_blocks_per_sm();
+size_t batched_smem_bytes();
 size_t batched_scratch_floats(int grid, int nz_max);
+// whether a level of nx x ny columns and its fields suit the two-column sweep tiles
+bool batched_x2_fits(int nx, int ny, const void* a, const void* b, const void* out);
 
 // ---------------------------------------------------------------- scalar kernels (k_util.cu)
 // modes of finalize_norm
