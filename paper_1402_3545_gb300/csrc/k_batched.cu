@@ -95,6 +95,7 @@ __device__ void t_sweep(const BLevelDesc& L, float rho, const float* __restrict_
     const float dh = (float)(1.0 + 2.0 * L.cx + 2.0 * L.cy), dh1 = dh + vv, dh2 = dh1 + vv;
     float um = 0.f, uc = (MODE != 2) ? __ldg(u + c) : 0.f, d_prev = 0.f;
     float fnext = __ldg(f + c);
+    #pragma unroll 2
     for (int k = 0; k < nz; ++k) {
         const size_t b = (size_t)k * pl;
         const float fk = fnext;
@@ -120,6 +121,7 @@ __device__ void t_sweep(const BLevelDesc& L, float rho, const float* __restrict_
     }
     if (MODE == 1) return;
     float xn = 0.f;
+    #pragma unroll 4
     for (int k = nz - 1; k >= 0; --k) {
         const size_t id = (size_t)k * pl + c;
         xn = stack[(size_t)k * t.nt + t.tid] + fac(L.fw, L.percol, k, pl, c) * xn;
@@ -137,17 +139,40 @@ __device__ void t_restrict_smooth(const BLevelDesc& Lc, float rho, const float* 
     const size_t f00 = (size_t)(2 * t.j) * nxf + 2 * t.i, f01 = f00 + nxf;
     const float vv = __ldg(Lc.v + c);
     float d_prev = 0.f;
-    for (int k = 0; k < nz; ++k) {
+    auto fine = [&](int k) {
         const size_t bf = (size_t)k * plf;
-        const float fk = 0.25f * ((__ldg(rf + bf + f00) + __ldg(rf + bf + f00 + 1)) +
-                                  (__ldg(rf + bf + f01) + __ldg(rf + bf + f01 + 1)));
+        return 0.25f * ((__ldg(rf + bf + f00) + __ldg(rf + bf + f00 + 1)) +
+                        (__ldg(rf + bf + f01) + __ldg(rf + bf + f01 + 1)));
+    };
+    auto fwd = [&](int k, float fk) {
         fc[(size_t)k * plc + c] = fk;
         const float d = (fk + vv * d_prev) * fac(Lc.finv, Lc.percol, k, plc, c);
         stack[(size_t)k * t.nt + t.tid] = d;
         d_prev = d;
+    };
+    // the children of four planes are loaded before their recurrence steps
+    int k = 0;
+    for (; k + 4 <= nz; k += 4) {
+        float fk[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fk[q] = fine(k + q);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fwd(k + q, fk[q]);
     }
+    for (; k < nz; ++k) fwd(k, fine(k));
     float xn = 0.f;
-    for (int k = nz - 1; k >= 0; --k) {
+    k = nz - 1;
+    for (; k >= 3; k -= 4) {
+        float st[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) st[q] = stack[(size_t)(k - q) * t.nt + t.tid];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            xn = st[q] + fac(Lc.fw, Lc.percol, k - q, plc, c) * xn;
+            uc[(size_t)(k - q) * plc + c] = rho * xn;
+        }
+    }
+    for (; k >= 0; --k) {
         xn = stack[(size_t)k * t.nt + t.tid] + fac(Lc.fw, Lc.percol, k, plc, c) * xn;
         uc[(size_t)k * plc + c] = rho * xn;
     }
@@ -163,12 +188,24 @@ __device__ void t_prolongate(const BLevelDesc& Lf, const float* __restrict__ ucr
     const size_t plc = (size_t)nxc * nyc, plf = (size_t)Lf.nx * Lf.ny;
     const size_t a = (size_t)J * nxc + I, bq = (size_t)J * nxc + I2, cq = (size_t)J2 * nxc + I,
                  dq = (size_t)J2 * nxc + I2, o = (size_t)t.j * Lf.nx + t.i;
-    for (int k = 0; k < nz; ++k) {
+    auto pv = [&](int k) {
         const size_t bc = (size_t)k * plc;
-        const float val = 0.5625f * __ldg(ucrs + bc + a) + 0.1875f * __ldg(ucrs + bc + bq) +
-                          0.1875f * __ldg(ucrs + bc + cq) + 0.0625f * __ldg(ucrs + bc + dq);
-        uf[(size_t)k * plf + o] += val;
+        return 0.5625f * __ldg(ucrs + bc + a) + 0.1875f * __ldg(ucrs + bc + bq) + 0.1875f * __ldg(ucrs + bc + cq) +
+               0.0625f * __ldg(ucrs + bc + dq);
+    };
+    // four planes per step: all loads issued before the stores (the planes are disjoint)
+    int k = 0;
+    for (; k + 4 <= nz; k += 4) {
+        float val[4], old[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            val[q] = pv(k + q);
+            old[q] = uf[(size_t)(k + q) * plf + o];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) uf[(size_t)(k + q) * plf + o] = old[q] + val[q];
     }
+    for (; k < nz; ++k) uf[(size_t)k * plf + o] += pv(k);
 }
 
 // ---------------------------------------------------------------- double-word outer steps
@@ -213,7 +250,20 @@ __device__ void t_correct(const BProbDesc& pb, const float* __restrict__ e, int 
     TileIdx t = tile_idx(i0, j0, L.nx, L.ny);
     if (!t.act) return;
     const size_t pl = (size_t)L.nx * L.ny, c = (size_t)t.j * L.nx + t.i;
-    for (int k = 0; k < L.nz; ++k) {
+    // four planes per step: all loads issued before the stores (the planes are disjoint)
+    int k = 0;
+    for (; k + 4 <= L.nz; k += 4) {
+        PolDW::R uv[4];
+        float ev[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uv[q] = PolDW::ld_plain(pb.uD, (size_t)(k + q) * pl + c);
+            ev[q] = __ldg(e + (size_t)(k + q) * pl + c);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) PolDW::st(pb.uD, (size_t)(k + q) * pl + c, PolDW::add(uv[q], PolDW::from_f(ev[q])));
+    }
+    for (; k < L.nz; ++k) {
         const size_t id = (size_t)k * pl + c;
         PolDW::st(pb.uD, id, PolDW::add(PolDW::ld_plain(pb.uD, id), PolDW::from_f(__ldg(e + id))));
     }
