@@ -1702,6 +1702,8 @@ tpmg_status tpmg_nn_create(int cin, const float* params_host, tpmg_nn** out) {
         if (st == TPMG_OK) st = dalloc(q, 16 * 16 * 27 * 2);
     if (st == TPMG_OK) st = dalloc((void**)&b.part, sizeof(float) * 1024 * 16 * 16 * 27);
     if (st == TPMG_OK) st = dalloc((void**)&b.dpart, sizeof(double) * 4096);
+    if (st == TPMG_OK) st = dalloc((void**)&b.err, sizeof(int));
+    if (st == TPMG_OK && cudaMemset(b.err, 0, sizeof(int)) != cudaSuccess) st = set_err(TPMG_ERR_CUDA, "memset failed");
     if (st == TPMG_OK && params_host)
         if (cudaMemcpy(b.params, params_host, np * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             st = set_err(TPMG_ERR_CUDA, "parameter upload failed");
@@ -1718,17 +1720,25 @@ tpmg_status tpmg_nn_destroy(tpmg_nn* nn) {
     cudaDeviceSynchronize();
     NNBufs& b = nn->b;
     void* ptrs[] = {b.params, b.grad, b.adam_m, b.adam_v, b.w1, b.w2f, b.w2b, b.w3f, b.w3b, b.w4,
-                    b.a1,     b.a2,   b.a3,     b.d1,     b.d2, b.x,   b.out, b.d4,  b.part, b.dpart, b.tmp};
+                    b.a1,     b.a2,   b.a3,     b.d1,     b.d2, b.x,   b.out, b.d4,  b.part, b.dpart, b.tmp, b.err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete nn;
     return TPMG_OK;
 }
 
+// TPMG_ERR_TIMEOUT if a tensor-core convolution of this network gave up a wait (synchronises)
+static tpmg_status nn_check(const tpmg_nn* nn) {
+    int e = 0;
+    CK(cudaMemcpy(&e, nn->b.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) return set_err(TPMG_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+    return TPMG_OK;
+}
+
 tpmg_status tpmg_nn_get_params(const tpmg_nn* nn, float* host) {
     if (!nn || !host) return set_err(TPMG_ERR_ARG, "NULL network or buffer");
     CK(cudaMemcpy(host, nn->b.params, sizeof(float) * nn->b.nparams, cudaMemcpyDeviceToHost));
-    return TPMG_OK;
+    return nn_check(nn);
 }
 
 tpmg_status tpmg_nn_set_params(tpmg_nn* nn, const float* host) {
@@ -1992,6 +2002,7 @@ extern "C" tpmg_status tpmg_fcg_solve(tpmg_op* op, tpmg_nn* nn, const float* aux
         CK(cudaEventElapsedTime(&ms, op->ev0, op->ev1));
         info->ms = ms;
     }
+    if (nn) TRY(nn_check(nn));
     if (hs->nonfinite) return set_err(TPMG_ERR_NONFINITE, "non-finite value in flexible CG");
     if (!hs->converged) return set_err(TPMG_ERR_NOT_CONVERGED, "max_iter reached");
     return TPMG_OK;

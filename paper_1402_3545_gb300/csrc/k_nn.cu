@@ -213,6 +213,281 @@ static int conv16z_grid(int nx, int ny) {
     return nb < ntiles ? nb : ntiles;
 }
 
+// ---------------------------------------------------------------- 16 -> 16 on tcgen05
+// The same implicit GEMM on the fifth-generation tensor cores: per output row of TCX = 128
+// consecutive x cells (M = 128) and tap, one tcgen05.mma (kind::f16, BF16 in, FP32 accumulate in
+// tensor memory) with K = 16 input channels and N = 16 output channels; 27 MMAs per row. A block
+// of 128 TR threads owns TR rows and marches them in z: it keeps the planes k-1 .. k+3 of the
+// (TR + 2) x 130 halo rows in a 5-slot shared-memory ring (cp.async), one thread issues the MMAs of
+// plane k into one of two TMEM accumulator groups, and all threads drain the other group (tcgen05.ld,
+// bias + ReLU or the backward mask, BF16 store) for plane k-1 meanwhile. Operands are in the
+// canonical no-swizzle K-major layout: 16-byte rows of 8 channels, 8 cells (or output channels) per
+// 128-byte core matrix; for tap (dz, dy, dx) and tile row r the A operand is the halo row of plane
+// k-1+dz, row r+dy, starting dx cells in (a 16-byte aligned view, so no copy per tap).
+static constexpr int TCX = 128;                     // cells per tile row
+static constexpr int TC_ROWC = TCX + 2;             // halo row cells
+static constexpr int TC_HALF = TC_ROWC * 16;        // bytes of one K half of a halo row
+static constexpr int TC_ROWB = 2 * TC_HALF;         // bytes of one halo row (both K halves)
+static constexpr int TC_WB = 27 * 512;              // weights: per tap [K half][16 co][8 ci]
+static constexpr int TC_SLOTS = 5;                  // planes k-1 .. k+3 in flight
+static constexpr long long TC_SPIN = 1LL << 26;     // bound of every mbarrier wait
+// per tile row three independent accumulator chains of 9 MMAs (one per dz, 16 FP32 columns
+// each), summed in the epilogue; two groups in flight (double buffer)
+static constexpr int TC_ACC = 3;
+template <int TR>
+struct TcShape {
+    static constexpr int PLANEB = (TR + 2) * TC_ROWB;            // one halo plane
+    static constexpr int SMEM = TC_WB + TC_SLOTS * PLANEB;
+    static constexpr int GROUP_COLS = 16 * TC_ACC * TR;          // TMEM columns per group
+    static constexpr int TMEM_COLS = 2 * GROUP_COLS <= 64 ? 64 : (2 * GROUP_COLS <= 128 ? 128 : 256);
+};
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    // start address >> 4 (bits 0-13), leading (K) byte offset >> 4 (16-29), stride (M/N) byte
+    // offset >> 4 (32-45), descriptor version 1 (46-47), base offset 0, no swizzle (61-63 = 0)
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// kind::f16 instruction descriptor: D FP32 (bit 4), A and B BF16 (bits 7, 10), both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24
+static constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+    for (long long it = 0; it < TC_SPIN; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <int EPI, int TR>
+__global__ void __launch_bounds__(128 * TR) k_conv16_tc(const __nv_bfloat16* __restrict__ in,
+                                                        const __nv_bfloat16* __restrict__ Wt,
+                                                        const float* __restrict__ bias,
+                                                        const __nv_bfloat16* __restrict__ mask,
+                                                        __nv_bfloat16* __restrict__ out, int nx, int ny, int nz, int* err) {
+    typedef TcShape<TR> SH;
+    constexpr int NT = 128 * TR;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ float bsh[16];
+    unsigned char* Ws = smem;
+    unsigned char* ring = smem + TC_WB;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int erow = warp >> 2, ecell = (warp & 3) * 32 + (tid & 31);  // epilogue: tile row, cell
+    // weights Wt[tap][co][ci] -> per tap [ci / 8][co][ci % 8]
+    for (int q = tid; q < 27 * 32; q += NT) {
+        const int tap = q >> 5, co = (q >> 1) & 15, h = q & 1;
+        *reinterpret_cast<uint4*>(Ws + tap * 512 + h * 256 + co * 16) =
+            __ldg(reinterpret_cast<const uint4*>(Wt + (tap * 16 + co) * 16 + h * 8));
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
+                     "n"(SH::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid < 16) bsh[tid] = (EPI == EPI_RELU) ? __ldg(bias + tid) : 0.f;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+
+    const int tiles_x = nx / TCX, ntiles = tiles_x * (ny / TR);
+    unsigned step = 0;  // MMA groups issued by this block: accumulator step & 1, parity (step >> 1) & 1
+    bool ok = true;
+    // drain the accumulators of MMA group g (plane kk of the current tile) into the output
+    auto epilogue = [&](unsigned g, int kk, int x0, int y0) -> bool {
+        if (!tc_wait(saddr(&mbar[g & 1]), (g >> 1) & 1)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        float v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = 0.f;
+#pragma unroll
+        for (int a = 0; a < TC_ACC; ++a) {
+            uint32_t r[16];
+            const uint32_t ta = tmem + (g & 1) * SH::GROUP_COLS + (erow * TC_ACC + a) * 16 +
+                                ((uint32_t)((warp & 3) * 32) << 16);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+            for (int c = 0; c < 16; ++c) v[c] += __uint_as_float(r[c]);
+        }
+        const size_t p = ((size_t)kk * ny + y0 + erow) * nx + x0 + ecell;
+        if (EPI == EPI_RELU) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) v[c] = fmaxf(v[c] + bsh[c], 0.f);
+        } else {
+            const uint4 m0 = __ldg(reinterpret_cast<const uint4*>(mask + p * 16));
+            const uint4 m1 = __ldg(reinterpret_cast<const uint4*>(mask + p * 16 + 8));
+            const __nv_bfloat16* mk0 = reinterpret_cast<const __nv_bfloat16*>(&m0);
+            const __nv_bfloat16* mk1 = reinterpret_cast<const __nv_bfloat16*>(&m1);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                if (!(__bfloat162float(mk0[c]) > 0.f)) v[c] = 0.f;
+                if (!(__bfloat162float(mk1[c]) > 0.f)) v[c + 8] = 0.f;
+            }
+        }
+        uint4 o0, o1;
+        __nv_bfloat162* h0 = reinterpret_cast<__nv_bfloat162*>(&o0);
+        __nv_bfloat162* h1 = reinterpret_cast<__nv_bfloat162*>(&o1);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            h0[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
+            h1[c] = __floats2bfloat162_rn(v[8 + 2 * c], v[8 + 2 * c + 1]);
+        }
+        *reinterpret_cast<uint4*>(out + p * 16) = o0;
+        *reinterpret_cast<uint4*>(out + p * 16 + 8) = o1;
+        return true;
+    };
+
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
+        // this thread's 16-byte chunks of a halo plane: slot offset and in-plane source, the same for
+        // every plane of the tile
+        constexpr int NCH = (TR + 2) * TC_ROWC * 2, CPT = (NCH + NT - 1) / NT;
+        int ch_dst[CPT];
+        size_t ch_src[CPT];
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+            const int q = tid + NT * j;
+            const int h = q & 1, c = (q >> 1) % TC_ROWC, rr = (q >> 1) / TC_ROWC;
+            ch_dst[j] = q < NCH ? rr * TC_ROWB + h * TC_HALF + c * 16 : -1;
+            ch_src[j] = ((size_t)nwrap(y0 - 1 + rr, ny) * nx + nwrap(x0 - 1 + c, nx)) * 16 + h * 8;
+        }
+        // plane kk into ring slot (kk + 1) % TC_SLOTS; the z padding planes -1 and nz are zeros,
+        // later ones are never read (an empty group)
+        auto load_plane = [&](int kk) {
+            unsigned char* P = ring + ((kk + 1) % TC_SLOTS) * SH::PLANEB;
+            const bool real = kk >= 0 && kk < nz, pad = kk == -1 || kk == nz;
+            const __nv_bfloat16* src = in + (size_t)(real ? kk : 0) * ny * nx * 16;
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                if (ch_dst[j] < 0) continue;
+                if (real) cp16(P + ch_dst[j], src + ch_src[j]);
+                else if (pad) *reinterpret_cast<uint4*>(P + ch_dst[j]) = make_uint4(0, 0, 0, 0);
+            }
+            cp_commit_nn();
+        };
+        __syncthreads();  // the previous tile's ring is no longer read
+        load_plane(-1);
+        load_plane(0);
+        load_plane(1);
+        load_plane(2);
+        for (int k = 0; k < nz; ++k) {
+            cp_wait_nn<1>();                                 // planes up to k+1 (this thread's copies)
+            asm volatile("fence.proxy.async.shared::cta;");  // ... visible to the tensor core
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (tid == 0) {
+                const uint32_t dt = tmem + (step & 1) * SH::GROUP_COLS;
+                // descriptors of tap (dz, dy, dx), row r: the start-address field (bits 0-13,
+                // address >> 4) of the plane's descriptor advanced by the view's offset in the slot
+                uint64_t dplane[3];
+#pragma unroll
+                for (int dz = 0; dz < 3; ++dz)
+                    dplane[dz] = tc_desc(saddr(ring + ((k + dz) % TC_SLOTS) * SH::PLANEB), TC_HALF, 128);
+                const uint64_t dw0 = tc_desc(saddr(Ws), 256, 128);
+#pragma unroll
+                for (int i = 0; i < 27; ++i) {  // the three chains interleaved
+                    const int dz = i % 3, tap = dz * 9 + i / 3, dy = (tap / 3) % 3, dx = tap % 3;
+                    const uint64_t db = dw0 + (uint64_t)((tap * 512) >> 4);
+#pragma unroll
+                    for (int r = 0; r < TR; ++r) {
+                        const uint64_t da = dplane[dz] + (uint64_t)((((dy + r) * TC_ROWB) + dx * 16) >> 4);
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                dt + (r * TC_ACC + dz) * 16),
+                            "l"(da), "l"(db), "r"(TC_IDESC), "r"(tap % 9));
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    saddr(&mbar[step & 1])));
+            }
+            // plane k+3 into the slot of plane k-2, whose last readers (group step-1) must be done;
+            // then drain group step-1 (plane k-1)
+            if (k > 0 && !tc_wait(saddr(&mbar[(step - 1) & 1]), ((step - 1) >> 1) & 1)) {
+                ok = false;
+                break;
+            }
+            load_plane(k + 3);
+            if (k > 0 && !epilogue(step - 1, k - 1, x0, y0)) {
+                ok = false;
+                break;
+            }
+            ++step;
+        }
+        if (ok && !epilogue(step - 1, nz - 1, x0, y0)) ok = false;
+        asm volatile("tcgen05.fence::before_thread_sync;");
+    }
+    if (!ok) {
+        atomicExch(err, 1);
+        // the MMAs in flight may still complete: give them the bounded wait before the TMEM is freed
+        tc_wait(saddr(&mbar[(step - 1) & 1]), ((step - 1) >> 1) & 1);
+    }
+    cp_wait_nn<0>();
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(SH::TMEM_COLS));
+}
+
+template <int TR>
+static int conv16_tc_grid(int nx, int ny) {
+    typedef TcShape<TR> SH;
+    static int per_sm = 0, nsm = 0;
+    if (per_sm == 0) {
+        cudaFuncSetAttribute(k_conv16_tc<EPI_RELU, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM);
+        cudaFuncSetAttribute(k_conv16_tc<EPI_MASK, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM);
+        int dev = 0, smem_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        // blocks per SM by shared memory (1 KB per block reserved by the system) and by TMEM
+        per_sm = smem_sm / (SH::SMEM + 1024);
+        if (per_sm > 512 / SH::TMEM_COLS) per_sm = 512 / SH::TMEM_COLS;  // tcgen05.alloc never waits
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int ntiles = (nx / TCX) * (ny / TR);
+    const int nb = per_sm * nsm;
+    return nb < ntiles ? nb : ntiles;
+}
+
+// one 16 -> 16 layer: the tcgen05 kernel (two rows per block when ny is even) when nx is a
+// multiple of 128, else the mma.sync one
+template <int EPI>
+static void conv16(const NNBufs& b, const __nv_bfloat16* in, const __nv_bfloat16* W, const float* bias,
+                   const __nv_bfloat16* mask, __nv_bfloat16* out, int nx, int ny, int nz, cudaStream_t s) {
+    if (nx % TCX == 0 && ny % 2 == 0) {
+        k_conv16_tc<EPI, 2><<<conv16_tc_grid<2>(nx, ny), 256, TcShape<2>::SMEM, s>>>(in, W, bias, mask, out, nx, ny, nz,
+                                                                                   b.err);
+    } else if (nx % TCX == 0) {
+        k_conv16_tc<EPI, 1><<<conv16_tc_grid<1>(nx, ny), 128, TcShape<1>::SMEM, s>>>(in, W, bias, mask, out, nx, ny, nz,
+                                                                                   b.err);
+    } else {
+        const size_t smemz = W_BYTES + 4 * PLANE_BYTES;
+        k_conv16z<EPI, CONV_MT><<<conv16z_grid(nx, ny), 256 / CONV_MT, smemz, s>>>(in, W, bias, mask, out, nx, ny, nz);
+    }
+    note_launch();
+}
+
 // ---------------------------------------------------------------- thin layers, marching in z
 // The one-channel first layer (1 -> 16) and the weight gradients of the first and last layers in
 // the persistent z-marching form of k_conv16z: a block of 128 threads owns a 64 x 2 tile, one cell
@@ -882,12 +1157,8 @@ void nn_forward(const NNBufs& b, int nx, int ny, int nz, const __nv_bfloat16* x,
     if (b.cin == 1) k_first_z<1><<<gt, 128, 0, s>>>(x, b.w1, b1, b.a1, nx, ny, nz);
     else k_first_tc<<<gt, 128, 0, s>>>(x, b.w1, b1, b.a1, nx, ny, nz);
     note_launch();
-    const size_t smemz = W_BYTES + 4 * PLANE_BYTES;
-    const int gz = conv16z_grid(nx, ny);
-    k_conv16z<EPI_RELU, CONV_MT><<<gz, 256 / CONV_MT, smemz, s>>>(b.a1, b.w2f, b2, nullptr, b.a2, nx, ny, nz);
-    note_launch();
-    k_conv16z<EPI_RELU, CONV_MT><<<gz, 256 / CONV_MT, smemz, s>>>(b.a2, b.w3f, b3, nullptr, b.a3, nx, ny, nz);
-    note_launch();
+    conv16<EPI_RELU>(b, b.a1, b.w2f, b2, nullptr, b.a2, nx, ny, nz, s);
+    conv16<EPI_RELU>(b, b.a2, b.w3f, b3, nullptr, b.a3, nx, ny, nz, s);
     k_last_tc<<<gt, 128, 27 * 32 * 8 + 4 * PLANE_BYTES, s>>>(b.a3, b.w4, b4, out, nx, ny, nz);
     note_launch();
 }
@@ -920,8 +1191,6 @@ void nn_backward(const NNBufs& b, int nx, int ny, int nz, const __nv_bfloat16* x
     k_reduce_partials<<<1, 256, 0, s>>>(b.part, nb, 1, gb4);
     k_bwd_last<<<blocks_for(n), 256, 0, s>>>(d4, b.w4, b.a3, b.d1, nx, ny, nz);
     for (int q = 0; q < 5; ++q) note_launch();
-    const size_t smemz = W_BYTES + 4 * PLANE_BYTES;
-    const int gz = conv16z_grid(nx, ny);
     const size_t smem_dw = HALO_BYTES + TXC * TYC * 32;
     cudaFuncSetAttribute(k_dw16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dw);
     // layer 3: dW3 from (a2, d3); d2 = mask(a2) * conv(d3, W3 flipped)
@@ -929,20 +1198,20 @@ void nn_backward(const NNBufs& b, int nx, int ny, int nz, const __nv_bfloat16* x
     k_reduce_partials<<<(n2 + 255) / 256, 256, 0, s>>>(b.part, nb, n2, gW3);
     k_chansum<16, false><<<nb, 256, 0, s>>>(b.d1, b.part, n, cpb);
     k_reduce_partials<<<1, 256, 0, s>>>(b.part, nb, 16, gb3);
-    k_conv16z<EPI_MASK, CONV_MT><<<gz, 256 / CONV_MT, smemz, s>>>(b.d1, b.w3b, nullptr, b.a2, b.d2, nx, ny, nz);
+    conv16<EPI_MASK>(b, b.d1, b.w3b, nullptr, b.a2, b.d2, nx, ny, nz, s);
     // layer 2: dW2 from (a1, d2); d1 = mask(a1) * conv(d2, W2 flipped)
     k_dw16<<<nb, 256, smem_dw, s>>>(b.a1, b.d2, b.part, nx, ny, nz);
     k_reduce_partials<<<(n2 + 255) / 256, 256, 0, s>>>(b.part, nb, n2, gW2);
     k_chansum<16, false><<<nb, 256, 0, s>>>(b.d2, b.part, n, cpb);
     k_reduce_partials<<<1, 256, 0, s>>>(b.part, nb, 16, gb2);
-    k_conv16z<EPI_MASK, CONV_MT><<<gz, 256 / CONV_MT, smemz, s>>>(b.d2, b.w2b, nullptr, b.a1, b.d1, nx, ny, nz);
+    conv16<EPI_MASK>(b, b.d2, b.w2b, nullptr, b.a1, b.d1, nx, ny, nz, s);
     // layer 1: dW1 from (x, d1)
     if (cin == 1) k_dwfirst_z<1><<<nbt, 128, 0, s>>>(x, b.d1, b.part, nx, ny, nz);
     else k_dwfirst_z<2><<<nbt, 128, 0, s>>>(x, b.d1, b.part, nx, ny, nz);
     k_reduce_partials<<<(n1 + 255) / 256, 256, 0, s>>>(b.part, nbt, n1, gW1);
     k_chansum<16, false><<<nb, 256, 0, s>>>(b.d1, b.part, n, cpb);
     k_reduce_partials<<<1, 256, 0, s>>>(b.part, nb, 16, gb1);
-    for (int q = 0; q < 14; ++q) note_launch();
+    for (int q = 0; q < 12; ++q) note_launch();
 }
 
 void nn_mse(const float* out, const float* target, float* d4, double* partials, size_t n, int nblocks, cudaStream_t s) {

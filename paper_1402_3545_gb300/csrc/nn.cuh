@@ -27,6 +27,7 @@ struct NNBufs {
     float* tmp;                   // scratch field (residual loss)
     float* part;                  // per-block partial sums of the weight gradients
     double* dpart;                // per-block partial sums of the loss
+    int* err;                     // set by a tensor-core convolution whose wait ran out of time
 };
 
 void nn_prepare_weights(const NNBufs& b, cudaStream_t s);
