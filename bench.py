@@ -462,6 +462,17 @@ def run_ours(args, rank, world, dist):
     kernel_ms_f32 = {name: round(tpmg.time_kernel(op.op, tpmg.F32, kid, reps=10), 4) for name, kid in [
         ("smooth", tpmg.K_SMOOTH), ("residual", tpmg.K_RESIDUAL), ("line_solve", tpmg.K_LINE_SOLVE),
         ("restrict_smooth", tpmg.K_RESTRICT_SMOOTH), ("prolongate", tpmg.K_PROLONGATE)]}
+    # native FP64 Smooth against the FP64 ALU: per cell the stencil residual (3 FMAs and 4 adds),
+    # the forward elimination (FMA and multiply), the back substitution (2 FMAs) and the norm (FMA)
+    # are 12 FP64 operations; GB300's nominal FP64 rate is 1.25 TFLOP/s (0.625 T FMA-or-add/s)
+    tpmg.op_reserve(op.op, tpmg.F64)
+    t_smooth64 = tpmg.time_kernel(op.op, tpmg.F64, tpmg.K_SMOOTH, reps=5)
+    ops64 = 12 * n
+    roofline_f64 = {"bound": "alu", "kernel": "finest-level native FP64 Smooth", "unit": "T FP64 ops/s",
+                    "achieved": round(ops64 / (t_smooth64 * 1e-3) / 1e12, 4), "peak": 0.625,
+                    "frac": round(ops64 / (t_smooth64 * 1e-3) / 1e12 / 0.625, 4), "ms_per_launch": round(t_smooth64, 4),
+                    "ops_per_launch": ops64, "peak_source": "nominal 1.25 TFLOP/s FP64 (FMA or add per op)",
+                    "hbm_frac_same_launch": round(3 * 8 * n / (t_smooth64 * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
     n_smooth = 4 * iters[-1] + 1
     # DRAM bytes of one launch from the ncu capture summarised in
     # profiles/k_sweep_x2_dw_smooth_mid_512x512x128.md (null for a variant without a capture)
@@ -544,7 +555,8 @@ def run_ours(args, rank, world, dist):
                            "solver": "V(2,2), rho 0.8, 2 coarse steps", "tol": 1e-6, "precision": "DW",
                            "parallelism": f"replicas{world}",
                            "l2": "inputs larger than L2 (268 MB per FP64 field > 129 MB)"},
-                "iters": iters[-1], "roofline": roofline, "kernel_ms": kernel_ms, "kernel_ms_f32": kernel_ms_f32,
+                "iters": iters[-1], "roofline": roofline, "roofline_f64": roofline_f64, "kernel_ms": kernel_ms,
+                "kernel_ms_f32": kernel_ms_f32,
                 "tile_variants": {"dw": variants_dw, "f32": variants_f32}, "variants": variants,
                 "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": 8 * n,
                         "d2h_bytes_per_step": 8 * n, "path": e2e_path,
