@@ -77,6 +77,7 @@ struct tpmg_op {
     void* gstack = nullptr;        // Thomas-stack scratch of the persistent sweep variants
     void* fw[3][MAXL + 1] = {};    // Thomas factors v/m_k
     int percol[MAXL + 1] = {};     // 1 if lambda^2 varies over the level (factors per cell)
+    int fac_k0[3][MAXL + 1];       // first plane of the converged factor range (Lv::fac_k0)
     double kappa_M[MAXL + 1] = {}; // condition number of the level's column blocks
     int lsw_dw = 1;                // the double-word solver uses native FP64 below this level
     bool fac_ready[3] = {false, false, false};
@@ -124,6 +125,7 @@ static Lv<P> level_view(const tpmg_op* op, int l) {
     L.finv = (const typename P::S*)op->finv[P::id][l];
     L.fw = (const typename P::S*)op->fw[P::id][l];
     L.fac_percol = op->percol[l];
+    L.fac_k0 = op->fac_k0[P::id][l];
     L.variant = op->variant[P::id][l];
     L.pcr = (const typename P::S*)op->pcr[P::id][l];
     L.gstack = op->gstack;
@@ -183,6 +185,7 @@ static tpmg_status ensure_history(tpmg_op* op, int n) {
 // Thomas factors of every level in precision pid, computed once (they depend on the operator only)
 static tpmg_status ensure_factors(tpmg_op* op, int pid) {
     if (op->fac_ready[pid]) return TPMG_OK;
+    TRY(ensure_common(op));
     TRY(dalloc(&op->gstack, gstack_bytes(op->g.nz)));
     const size_t eb = elem_bytes(pid);
     for (int l = 1; l <= op->g.L; ++l) {
@@ -193,6 +196,19 @@ static tpmg_status ensure_factors(tpmg_op* op, int pid) {
             case 0: launch_factors<PolF64>(level_view<PolF64>(op, l), (double*)op->finv[0][l], (double*)op->fw[0][l], op->percol[l], 0); break;
             case 1: launch_factors<PolF32>(level_view<PolF32>(op, l), (float*)op->finv[1][l], (float*)op->fw[1][l], op->percol[l], 0); break;
             default: launch_factors<PolDW>(level_view<PolDW>(op, l), (float2*)op->finv[2][l], (float2*)op->fw[2][l], op->percol[l], 0); break;
+        }
+        if (op->percol[l] && op->g.nz >= 3) {
+            // the converged range of the per-cell factors
+            int* dk = (int*)op->partials;
+            CK(cudaMemsetAsync(dk, 0, sizeof(int), 0));
+            switch (pid) {
+                case 0: launch_factor_k0<PolF64>(level_view<PolF64>(op, l), (const double*)op->finv[0][l], (const double*)op->fw[0][l], dk, 0); break;
+                case 1: launch_factor_k0<PolF32>(level_view<PolF32>(op, l), (const float*)op->finv[1][l], (const float*)op->fw[1][l], dk, 0); break;
+                default: launch_factor_k0<PolDW>(level_view<PolDW>(op, l), (const float2*)op->finv[2][l], (const float2*)op->fw[2][l], dk, 0); break;
+            }
+            int k0 = 0;
+            CK(cudaMemcpy(&k0, dk, sizeof(int), cudaMemcpyDeviceToHost));
+            op->fac_k0[pid][l] = k0;
         }
         // small levels: parallel-cyclic-reduction factors for the cell-parallel kernels
         if ((size_t)op->g.lnx[l] * op->g.lny[l] <= (size_t)PCR_MAX_COLS && op->g.nz <= 256) {
@@ -622,7 +638,10 @@ tpmg_status tpmg_create_operator(const tpmg_grid* g, double omega2, double hx, d
         return set_err(TPMG_ERR_ARG, "omega2 >= 0 and positive mesh widths required");
     tpmg_op* op = new tpmg_op();
     for (int p = 0; p < 3; ++p)
-        for (int l = 0; l <= MAXL; ++l) op->variant[p][l] = -1;  // untuned: the launcher's default
+        for (int l = 0; l <= MAXL; ++l) {
+            op->variant[p][l] = -1;  // untuned: the launcher's default
+            op->fac_k0[p][l] = 1 << 30;
+        }
     op->g = *g;
     op->omega2 = omega2;
     op->hx = hx;

@@ -53,6 +53,37 @@ void launch_factors(const Lv<P>& L, typename P::S* finv, typename P::S* fw, int 
     note_launch();
 }
 
+// per column: the first plane k0 such that the stored factors of planes k0 .. nz-2 all equal (bit
+// for bit) those of plane nz-2; *k0 = the maximum over the columns
+template <class P>
+__global__ void k_factor_k0(Lv<P> L, const typename P::S* __restrict__ finv, const typename P::S* __restrict__ fw,
+                            int* k0) {
+    typedef typename P::S S;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= L.nx || j >= L.ny || L.nz < 3) return;
+    const size_t pl = (size_t)L.nx * L.ny, c = (size_t)j * L.nx + i;
+    const int ref = L.nz - 2;
+    const S ri = finv[(size_t)ref * pl + c], rw = fw[(size_t)ref * pl + c];
+    auto same = [](const S& a, const S& b) {
+        static_assert(sizeof(S) % 4 == 0, "32-bit words");
+        const unsigned* x = reinterpret_cast<const unsigned*>(&a);
+        const unsigned* y = reinterpret_cast<const unsigned*>(&b);
+        for (int q = 0; q < (int)(sizeof(S) / 4); ++q)
+            if (x[q] != y[q]) return false;
+        return true;
+    };
+    int k = ref;
+    while (k > 0 && same(finv[(size_t)(k - 1) * pl + c], ri) && same(fw[(size_t)(k - 1) * pl + c], rw)) --k;
+    atomicMax(k0, k);
+}
+
+template <class P>
+void launch_factor_k0(const Lv<P>& L, const typename P::S* finv, const typename P::S* fw, int* k0, cudaStream_t s) {
+    dim3 blk(32, 4), grd((L.nx + 31) / 32, (L.ny + 3) / 4);
+    k_factor_k0<P><<<grd, blk, 0, s>>>(L, finv, fw, k0);
+    note_launch();
+}
+
 // ---------------------------------------------------------------- generic pipelined sweep
 
 // MODE_SMOOTH:    out = u + coef M^{-1}(f - A u), partial sums of ||f - A u||^2      (Eq. 11)
@@ -587,6 +618,7 @@ int launch_restrict_smooth_pp(const Lv<P>& Lc, double rho, const typename PF::S*
 
 #define TPMG_SWEEP_INST(P)                                                                                  \
     template void launch_factors<P>(const Lv<P>&, P::S*, P::S*, int, cudaStream_t);                         \
+    template void launch_factor_k0<P>(const Lv<P>&, const P::S*, const P::S*, int*, cudaStream_t);          \
     template int launch_smooth_pp<P>(const Lv<P>&, double, const P::S*, const P::S*, P::S*, double*, const int*, \
                                      cudaStream_t);                                                          \
     template int launch_residual_pp<P, P>(const Lv<P>&, const P::S*, const P::S*, P::S*, double*, const int*,  \

@@ -93,6 +93,10 @@ struct Lv {
     const typename P::S* finv;
     const typename P::S* fw;
     int fac_percol;
+    // per-cell factors only: from plane fac_k0 to plane nz-2 every column's stored 1/m_k and v/m_k
+    // equal (bit for bit) those of plane nz-2 -- the forward elimination has converged to its fixed
+    // point -- so the sweeps may read plane nz-2's once per column instead (nz-1: no such range)
+    int fac_k0 = 1 << 30;
     int variant;  // tile variant of the pipelined Smooth chosen by the autotuner (-1: default)
     // parallel-cyclic-reduction factors of the column blocks (small levels only, else null):
     // for each of pcr_steps strides 1, 2, 4, ... the two elimination multipliers per cell, then
@@ -177,6 +181,10 @@ int max_partials(int nx, int ny);
 // Thomas factors of level L into finv/fw (per cell when percol, else a table of nz entries).
 template <class P>
 void launch_factors(const Lv<P>& L, typename P::S* finv, typename P::S* fw, int percol, cudaStream_t s);
+// first plane of the converged range of per-cell factors (see Lv::fac_k0), written to *k0 (device
+// int, initialised by the caller to 0): the maximum over the columns
+template <class P>
+void launch_factor_k0(const Lv<P>& L, const typename P::S* finv, const typename P::S* fw, int* k0, cudaStream_t s);
 // Plane-pipelined kernels for levels with nx % 32 == 0; each returns its number of thread blocks
 // (= partial sums written), or -1 when the level does not fit and the caller must fall back.
 template <class P>

@@ -83,6 +83,7 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
     const R vzero = P::zero();
     typename P::Acc acc = 0, cmp = 0;
     const bool iso = L.cx == L.cy;
+    const int k0 = L.fac_k0;
     unsigned long long pol_first = 0, pol_last = 0;
     if constexpr (HINT != 0) {
         pol_first = l2_evict_first();
@@ -120,12 +121,13 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
             if (k < nz) {
                 const size_t b = (size_t)k * pl;
                 S* Us = ringU + slot * UPL;
+                const bool fac = STACK && percol && !(k >= k0 && k <= nz - 2);  // factors of plane k needed
                 if constexpr ((HINT & HINT_STREAM) != 0) {
                     cp_async_pol<PB>(&ringF[slot * FPL + 2 * tid], rhs + b + c, pol_first);
-                    if (STACK && percol) cp_async_pol<PB>(&ringI[slot * FPL + 2 * tid], L.finv + b + c, pol_first);
+                    if (fac) cp_async_pol<PB>(&ringI[slot * FPL + 2 * tid], L.finv + b + c, pol_first);
                 } else {
                     cp_async<PB>(&ringF[slot * FPL + 2 * tid], rhs + b + c);
-                    if (STACK && percol) cp_async<PB>(&ringI[slot * FPL + 2 * tid], L.finv + b + c);
+                    if (fac) cp_async<PB>(&ringI[slot * FPL + 2 * tid], L.finv + b + c);
                 }
                 if (HALO) {
                     cp_async<PB>(&Us[(ty + 1) * UW + 2 + 2 * tx], u + b + c);
@@ -140,6 +142,15 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
         for (int s = 0; s < PD; ++s) issue_plane(s, s);
 
         const R v0 = P::ld(L.v, c), v1 = P::ld(L.v, c + 1);
+        // the converged factors (plane nz-2) of this thread's columns, used on planes k0 .. nz-2
+        R ci0 = vzero, ci1 = vzero, cw0 = vzero, cw1 = vzero;
+        if (STACK && percol && k0 <= nz - 2) {
+            const size_t r = (size_t)(nz - 2) * pl + c;
+            ci0 = P::ld(L.finv, r);
+            ci1 = P::ld(L.finv, r + 1);
+            cw0 = P::ld(L.fw, r);
+            cw1 = P::ld(L.fw, r + 1);
+        }
         const R cx = P::cst(L.cx), cy = P::cst(L.cy), cf = P::cst(coef);
         const R dh = P::cst(1.0 + 2.0 * L.cx + 2.0 * L.cy);
         const R dh1a = P::add(dh, v0), dh2a = P::add(dh1a, v0);
@@ -197,7 +208,10 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
             }
             if constexpr (STACK) {
                 R i0v, i1v;
-                if (percol) {
+                if (percol && k >= k0 && k <= nz - 2) {
+                    i0v = ci0;
+                    i1v = ci1;
+                } else if (percol) {
                     i0v = P::ld_plain(ringI, slot * FPL + 2 * tid);
                     i1v = P::ld_plain(ringI, slot * FPL + 2 * tid + 1);
                 } else {
@@ -241,12 +255,13 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
             auto issue_back = [&](int k, int s2) {
                 if (k >= 0) {
                     const size_t id = (size_t)k * pl + c;
+                    const bool fac = percol && !(k >= k0 && k <= nz - 2);
                     if constexpr ((HINT & HINT_STREAM) != 0) {
                         if (NEED_U) cp_async_pol<PB>(&bU[(s2 * NT + tid) * 2], u + id, pol_first);
-                        if (percol) cp_async_pol<PB>(&bW[(s2 * NT + tid) * 2], L.fw + id, pol_first);
+                        if (fac) cp_async_pol<PB>(&bW[(s2 * NT + tid) * 2], L.fw + id, pol_first);
                     } else {
                         if (NEED_U) cp_async<PB>(&bU[(s2 * NT + tid) * 2], u + id);
-                        if (percol) cp_async<PB>(&bW[(s2 * NT + tid) * 2], L.fw + id);
+                        if (fac) cp_async<PB>(&bW[(s2 * NT + tid) * 2], L.fw + id);
                     }
                     cp_async<PB>(&bD[(s2 * NT + tid) * 2], gstack + ((size_t)k * NT + tid) * 2);
                 }
@@ -265,7 +280,10 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
                 }
                 const int o = (slot * NT + tid) * 2;
                 R w0, w1;
-                if (percol) {
+                if (percol && k >= k0 && k <= nz - 2) {
+                    w0 = cw0;
+                    w1 = cw1;
+                } else if (percol) {
                     w0 = P::ld_plain(bW, o);
                     w1 = P::ld_plain(bW, o + 1);
                 } else {
