@@ -470,16 +470,13 @@ static int conv16_tc_grid(int nx, int ny) {
     return nb < ntiles ? nb : ntiles;
 }
 
-// one 16 -> 16 layer: the tcgen05 kernel (two rows per block when ny is even) when nx is a
-// multiple of 128, else the mma.sync one
+// one 16 -> 16 layer: the tcgen05 kernel (two rows per block; the network's shapes have even ny)
+// when nx is a multiple of 128, else the mma.sync one
 template <int EPI>
 static void conv16(const NNBufs& b, const __nv_bfloat16* in, const __nv_bfloat16* W, const float* bias,
                    const __nv_bfloat16* mask, __nv_bfloat16* out, int nx, int ny, int nz, cudaStream_t s) {
     if (nx % TCX == 0 && ny % 2 == 0) {
         k_conv16_tc<EPI, 2><<<conv16_tc_grid<2>(nx, ny), 256, TcShape<2>::SMEM, s>>>(in, W, bias, mask, out, nx, ny, nz,
-                                                                                   b.err);
-    } else if (nx % TCX == 0) {
-        k_conv16_tc<EPI, 1><<<conv16_tc_grid<1>(nx, ny), 128, TcShape<1>::SMEM, s>>>(in, W, bias, mask, out, nx, ny, nz,
                                                                                    b.err);
     } else {
         const size_t smemz = W_BYTES + 4 * PLANE_BYTES;
