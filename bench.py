@@ -49,7 +49,8 @@ def parse_args():
     ap.add_argument("--solve-only", action="store_true",
                     help="time the solves only (no kernel timing, e2e, variants or CPU baseline): "
                          "the command the ncu launch-list profile runs")
-    ap.add_argument("--kernel-only", choices=["smooth", "residual", "restrict_smooth", "prolongate", "nn_forward"],
+    ap.add_argument("--kernel-only", choices=["smooth", "residual", "restrict_smooth", "prolongate", "line_solve",
+                                              "cg_spmv", "cg_tridiag", "nn_forward"],
                     help="launch only this finest-level kernel a few times (tile variant --variant, "
                          "no autotuning): the command a per-kernel ncu capture runs")
     ap.add_argument("--variant", type=int, default=3)
@@ -376,7 +377,8 @@ def run_kernel_only(args):
         return
     prec = {"dw": tpmg.DW, "f32": tpmg.F32, "f64": tpmg.F64}[args.precision]
     kid = {"smooth": tpmg.K_SMOOTH, "residual": tpmg.K_RESIDUAL, "restrict_smooth": tpmg.K_RESTRICT_SMOOTH,
-           "prolongate": tpmg.K_PROLONGATE}[args.kernel_only]
+           "prolongate": tpmg.K_PROLONGATE, "line_solve": tpmg.K_LINE_SOLVE, "cg_spmv": tpmg.K_CG_SPMV,
+           "cg_tridiag": tpmg.K_CG_TRIDIAG}[args.kernel_only]
     p = workloads.mid()
     op = tpmg.Operator.from_problem(p)
     tpmg.op_reserve(op.op, tpmg.MIXED if prec == tpmg.F32 else prec)

@@ -205,20 +205,13 @@ __global__ void __launch_bounds__(128) k_cg_tridiag_gs(Lv<P> L, const Scalars* _
         const bool active = i < nx && j < ny;
         const size_t c = (size_t)j * nx + i;
         const R vv = active ? P::ld(L.v, c) : P::zero();
-        // planes k0 .. nz-2 share the converged factors of plane nz-2 (Lv::fac_k0)
-        const int k0 = L.fac_k0;
-        R ci = P::zero(), cw = P::zero();
-        if (active && percol && k0 <= nz - 2) {
-            ci = P::ld(L.finv, (size_t)(nz - 2) * pl + c);
-            cw = P::ld(L.fw, (size_t)(nz - 2) * pl + c);
-        }
         R d_prev = P::zero();
         for (int k = 0; k < nz && active; ++k) {
             const size_t id = (size_t)k * pl + c;
             const R rn = P::fma(nalpha, ld_pol(q + id, pol_first), P::ld_plain(r, id));
             P::st(r, id, rn);
             P::acc_dot(arr, crr, rn, rn);
-            const R inv = !percol ? P::ld(L.finv, k) : (k >= k0 && k <= nz - 2) ? ci : ld_pol(L.finv + id, pol_first);
+            const R inv = percol ? ld_pol(L.finv + id, pol_first) : P::ld(L.finv, k);
             d_prev = P::mul(P::fma(vv, d_prev, rn), inv);
             st_pol(gst + (size_t)k * 128 + tid, d_prev, pol_last);
         }
@@ -226,7 +219,7 @@ __global__ void __launch_bounds__(128) k_cg_tridiag_gs(Lv<P> L, const Scalars* _
         for (int k = nz - 1; k >= 0; --k) {
             const size_t id = (size_t)k * pl + c;
             if (active) {
-                const R w = !percol ? P::ld(L.fw, k) : (k >= k0 && k <= nz - 2) ? cw : ld_pol(L.fw + id, pol_first);
+                const R w = percol ? ld_pol(L.fw + id, pol_first) : P::ld(L.fw, k);
                 xn = P::fma(w, xn, P::ld_plain(gst, (size_t)k * 128 + tid));
                 st_pol(z + id, xn, pol_first);
                 P::acc_dot(arz, crz, P::ld_plain(r, id), xn);

@@ -475,6 +475,11 @@ int launch_residual_pp(const Lv<P>& L, const typename P::S* u, const typename P:
 template <class P>
 int launch_line_solve_pp(const Lv<P>& L, const typename P::S* b, typename P::S* x, double scale, const int* done,
                          cudaStream_t s) {
+    // two columns per thread with the stack in the L2-steered scratch where the level allows it
+    if (L.gstack && P::id != 0) {
+        const int nb = run_sweep_x2<P, P, 2, 4, MODE_LINESOLVE, 1, HINT_ALL>(L, scale, b, nullptr, x, nullptr, done, s, 8);
+        if (nb >= 0) return nb;
+    }
     if (L.nz * 32 * 8 > 160 * 1024) return -1;
     if (P::id == 1) {
         if (!pp_fits<P, 2>(L)) return -1;
