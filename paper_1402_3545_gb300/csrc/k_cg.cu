@@ -10,6 +10,7 @@
 // One thread owns one vertical column; the sums are reduced per block and summed in a fixed order
 // by the finalize kernels (k_util.cu), which also compute alpha and beta on the device.
 #include "kernels.cuh"
+#include "sweep_x2.cuh"
 
 namespace tpmg {
 
@@ -237,6 +238,172 @@ __global__ void __launch_bounds__(128) k_cg_tridiag_gs(Lv<P> L, const Scalars* _
     }
 }
 
+// The fused Tridiag on two columns per thread, plane-pipelined like the two-column Smooth
+// (sweep_x2.cuh): each plane's r, q and (where the elimination has not converged) 1/m_k pairs
+// arrive by cp.async PD planes ahead; the forward-eliminated values go to the block's scratch slot
+// (evict-last, each line dropped from L2 once read back). <r, z> is taken in the forward sweep: with
+// the column block M = U^T D U (D = diag(m_k), U unit upper bidiagonal), the elimination gives
+// yh = U^{-T} r (yh_k = r_k + v d'_{k-1}) and d'_k = yh_k / m_k, so <r, M^{-1} r> = sum_k yh_k d'_k,
+// a sum of non-negative terms, and the back substitution does not read r again.
+// Tiles of 64 x TY columns; requires nx % 64 == 0, ny % TY == 0, 16-byte aligned fields.
+template <class P, int TY, int PD>
+__global__ void __launch_bounds__(32 * TY) k_cg_tridiag_x2(Lv<P> L, const Scalars* __restrict__ sc,
+                                                           typename P::S* __restrict__ r,
+                                                           const typename P::S* __restrict__ q,
+                                                           typename P::S* __restrict__ z, double* partials) {
+    typedef typename P::S S;
+    typedef typename P::R R;
+    constexpr int NT = 32 * TY, SL = 2 * NT;  // values per ring slot and array
+    constexpr int PB = 2 * (int)sizeof(S);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (*(volatile const int*)&sc->done) return;
+    const int nx = L.nx, ny = L.ny, nz = L.nz, tid = threadIdx.y * 32 + threadIdx.x;
+    const size_t pl = (size_t)nx * ny;
+    const int tiles_x = nx / 64, ntiles = tiles_x * (ny / TY);
+    const bool percol = L.fac_percol != 0;
+    const int k0 = L.fac_k0;
+    S* ringR = reinterpret_cast<S*>(smem_raw);
+    S* ringQ = ringR + PD * SL;
+    S* ringI = ringQ + PD * SL;
+    S* gst = reinterpret_cast<S*>(L.gstack) + (size_t)blockIdx.x * nz * SL;
+    const R nalpha = P::neg(P::cst(sc->alpha));
+    const unsigned long long pol_first = l2_evict_first(), pol_last = l2_evict_last();
+    typename P::Acc arr = 0, crr = 0, arz = 0, crz = 0;
+    const R vzero = P::zero();
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int i0 = (tile % tiles_x) * 64, j0 = (tile / tiles_x) * TY;
+        const size_t c = (size_t)(j0 + threadIdx.y) * nx + i0 + 2 * threadIdx.x;
+        __syncthreads();  // the previous tile's rings are no longer read
+        auto issue_plane = [&](int k, int slot) {
+            if (k < nz) {
+                const size_t id = (size_t)k * pl + c;
+                cp_async<PB>(&ringR[slot * SL + 2 * tid], r + id);
+                cp_async_pol<PB>(&ringQ[slot * SL + 2 * tid], q + id, pol_first);
+                if (percol && !(k >= k0 && k <= nz - 2))
+                    cp_async_pol<PB>(&ringI[slot * SL + 2 * tid], L.finv + id, pol_first);
+            }
+            cp_commit();
+        };
+        for (int sl = 0; sl < PD; ++sl) issue_plane(sl, sl);
+        const R v0 = P::ld(L.v, c), v1 = P::ld(L.v, c + 1);
+        R ci0 = vzero, ci1 = vzero, cw0 = vzero, cw1 = vzero;
+        if (percol && k0 <= nz - 2) {
+            const size_t rr = (size_t)(nz - 2) * pl + c;
+            ci0 = P::ld(L.finv, rr);
+            ci1 = P::ld(L.finv, rr + 1);
+            cw0 = P::ld(L.fw, rr);
+            cw1 = P::ld(L.fw, rr + 1);
+        }
+        R dp0 = vzero, dp1 = vzero;
+        int slot = 0;
+        for (int k = 0; k < nz; ++k) {
+            cp_wait<PD - 1>();  // this thread's copies of plane k
+            const int o = slot * SL + 2 * tid;
+            const R rn0 = P::fma(nalpha, P::ld_plain(ringQ, o), P::ld_plain(ringR, o));
+            const R rn1 = P::fma(nalpha, P::ld_plain(ringQ, o + 1), P::ld_plain(ringR, o + 1));
+            const size_t id = (size_t)k * pl + c;
+            st_pair_pol(r + id, rn0, rn1, pol_first);
+            P::acc_dot(arr, crr, rn0, rn0);
+            P::acc_dot(arr, crr, rn1, rn1);
+            R i0v, i1v;
+            if (!percol) {
+                i0v = i1v = P::ld(L.finv, k);
+            } else if (k >= k0 && k <= nz - 2) {
+                i0v = ci0;
+                i1v = ci1;
+            } else {
+                i0v = P::ld_plain(ringI, o);
+                i1v = P::ld_plain(ringI, o + 1);
+            }
+            const R yh0 = P::fma(v0, dp0, rn0), yh1 = P::fma(v1, dp1, rn1);
+            dp0 = P::mul(yh0, i0v);
+            dp1 = P::mul(yh1, i1v);
+            P::acc_dot(arz, crz, yh0, dp0);
+            P::acc_dot(arz, crz, yh1, dp1);
+            st_pair_pol(gst + ((size_t)k * NT + tid) * 2, dp0, dp1, pol_last);
+            issue_plane(k + PD, slot);
+            slot = (slot + 1 == PD) ? 0 : slot + 1;
+        }
+        cp_wait<0>();
+        __syncthreads();  // the backward ring reuses the forward ring's shared memory
+        S* bW = reinterpret_cast<S*>(smem_raw);
+        S* bD = bW + PD * SL;
+        auto issue_back = [&](int k, int s2) {
+            if (k >= 0) {
+                if (percol && !(k >= k0 && k <= nz - 2))
+                    cp_async_pol<PB>(&bW[s2 * SL + 2 * tid], L.fw + (size_t)k * pl + c, pol_first);
+                cp_async<PB>(&bD[s2 * SL + 2 * tid], gst + ((size_t)k * NT + tid) * 2);
+            }
+            cp_commit();
+        };
+        for (int sl = 0; sl < PD; ++sl) issue_back(nz - 1 - sl, sl);
+        R x0 = vzero, x1 = vzero;
+        slot = 0;
+        for (int k = nz - 1; k >= 0; --k) {
+            cp_wait<PD - 1>();
+            {
+                // plane k of the stack has landed for every lane of the warp: its lines are dead
+                constexpr int LANES_PER_LINE = 128 / PB;
+                __syncwarp();
+                if (tid % LANES_PER_LINE == 0) l2_discard(gst + ((size_t)k * NT + tid) * 2);
+            }
+            const int o = slot * SL + 2 * tid;
+            R w0, w1;
+            if (!percol) {
+                w0 = w1 = P::ld(L.fw, k);
+            } else if (k >= k0 && k <= nz - 2) {
+                w0 = cw0;
+                w1 = cw1;
+            } else {
+                w0 = P::ld_plain(bW, o);
+                w1 = P::ld_plain(bW, o + 1);
+            }
+            x0 = P::fma(w0, x0, P::ld_plain(bD, o));
+            x1 = P::fma(w1, x1, P::ld_plain(bD, o + 1));
+            st_pair_pol(z + (size_t)k * pl + c, x0, x1, pol_first);
+            issue_back(k - PD, slot);
+            slot = (slot + 1 == PD) ? 0 : slot + 1;
+        }
+        cp_wait<0>();
+    }
+    const double s1 = block_sum(P::acc_get(arr, crr));
+    const double s2 = block_sum(P::acc_get(arz, crz));
+    if (tid == 0) {
+        partials[blockIdx.x] = s1;
+        partials[gridDim.x + blockIdx.x] = s2;
+    }
+}
+
+static constexpr int CGX_TY = 2, CGX_PD = 4;
+template <class P>
+static bool cg_x2_fits(const Lv<P>& L) {
+    return P::id != 0 && L.gstack && L.finv && L.fw && L.nx % 64 == 0 && L.ny % CGX_TY == 0;
+}
+template <class P>
+static size_t cg_x2_smem() {
+    return (size_t)CGX_PD * 3 * 2 * 32 * CGX_TY * sizeof(typename P::S);
+}
+template <class P>
+static int cg_x2_blocks(const Lv<P>& L) {
+    static int per_sm = 0, nsm = 0;
+    if (per_sm == 0) {
+        auto kern = k_cg_tridiag_x2<P, CGX_TY, CGX_PD>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cg_x2_smem<P>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * CGX_TY, cg_x2_smem<P>());
+        if (per_sm > 10) per_sm = 10;
+        if (per_sm < 1) per_sm = 1;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    int nb = nsm * per_sm;
+    // the scratch slots: 64 TY columns per block out of gstack_bytes
+    const int slots = nsm * GS_BLOCKS_PER_SM * GS_MAX_NT / (2 * 32 * CGX_TY);
+    if (nb > slots) nb = slots;
+    const int ntiles = (L.nx / 64) * (L.ny / CGX_TY);
+    return nb < ntiles ? nb : ntiles;
+}
+
 // u <- u + alpha p : the lagged solution update after the last iteration.
 template <class P>
 __global__ void k_cg_finish(size_t n, const Scalars* __restrict__ sc, typename P::S* __restrict__ u,
@@ -274,6 +441,7 @@ int launch_cg_spmv(const Lv<P>& L, const Scalars* sc, typename P::S* u, typename
 // its factors and the scratch
 template <class P>
 int cg_tridiag_blocks(const Lv<P>& L) {
+    if (cg_x2_fits(L)) return cg_x2_blocks(L);
     if (L.gstack && L.finv && L.fw) {
         static int per_sm = 0;
         if (per_sm == 0) {
@@ -293,6 +461,12 @@ int cg_tridiag_blocks(const Lv<P>& L) {
 template <class P>
 int launch_cg_tridiag(const Lv<P>& L, const Scalars* sc, typename P::S* r, const typename P::S* q,
                       typename P::S* z, double* partials, cudaStream_t s) {
+    if (cg_x2_fits(L)) {
+        const int nb = cg_x2_blocks(L);
+        k_cg_tridiag_x2<P, CGX_TY, CGX_PD><<<nb, dim3(32, CGX_TY), cg_x2_smem<P>(), s>>>(L, sc, r, q, z, partials);
+        note_launch();
+        return nb;
+    }
     if (L.gstack && L.finv && L.fw) {
         const int nb = cg_tridiag_blocks(L);
         k_cg_tridiag_gs<P><<<nb, dim3(32, 4), 0, s>>>(L, sc, r, q, z, partials);
