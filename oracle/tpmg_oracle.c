@@ -403,7 +403,8 @@ int orc_cg_solve(int nx, int ny, int nz, double cx, double cy, const double *v, 
 /* Iterative refinement around V-cycles (mixed-precision outer loop): r = f - A u,              */
 /* e = V-cycle(A e = r, e_0 = 0), u += e, until ||r||/||r_0|| < tol. The oracle runs the inner  */
 /* cycle in FP64; it is the mathematical algorithm the FP32-inner GPU solver approximates.      */
-/* parity unpinned beyond its fixed point (it must converge to A^{-1} f).                      */
+/* Pinned by dense LU (it converges to A^{-1} f) and by the multigrid iteration it must equal  */
+/* (the V-cycle is linear, so one cycle on the correction equation gives the next iterate).    */
 /* ------------------------------------------------------------------------------------------ */
 int orc_ir_solve(int nx, int ny, int nz, int L, double cx, double cy, const double *v,
                  int nu_pre, int nu_post, int n_coarse, double rho, double tol, int max_iter,

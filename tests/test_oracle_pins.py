@@ -265,7 +265,8 @@ def test_mg_vcycle_contraction_band():
 
 
 def test_mg_and_cg_match_dense_lu_variable_v():
-    """Variable lambda^2: both solvers reach the dense LU solution on a tiny grid."""
+    """Variable lambda^2: multigrid, CG and iterative refinement reach the dense LU solution on a
+    tiny grid."""
     nx, ny, nz = 8, 8, 4
     cx, cy = 30.0, 30.0
     v = rand_v(ny, nx, 16) * 10
@@ -274,9 +275,11 @@ def test_mg_and_cg_match_dense_lu_variable_v():
     ref = np.linalg.solve(A, f.ravel()).reshape(f.shape)
     u_mg, _, _, c1 = oracle.mg_solve(f, cx, cy, v, nlevels=3, tol=1e-13, max_iter=200)
     u_cg, _, _, c2 = oracle.cg_solve(f, cx, cy, v, tol=1e-13, max_iter=500)
-    assert c1 and c2
+    u_ir, _, _, c3 = oracle.ir_solve(f, cx, cy, v, nlevels=3, tol=1e-13, max_iter=200)
+    assert c1 and c2 and c3
     assert rel(u_mg, ref) < 1e-10
     assert rel(u_cg, ref) < 1e-10
+    assert rel(u_ir, ref) < 1e-10
 
 
 def test_preconditioned_condition_number_matches_paper():
