@@ -94,6 +94,32 @@ __device__ __forceinline__ dw dw_sum4(dw a, dw b, dw c, dw d) {
     return z;
 }
 
+// The same three operations without the final Fast2Sum: the result (s, t) is an unnormalised
+// pair (|t| may exceed ulp(s)/2 by a few ulps of the low part) whose value hi + lo carries the same
+// accuracy. Every operation above accepts such a pair as input (TwoSum needs no ordering; in the
+// products the low part only enters the FP32 cross terms), so a chain renormalises once, at its
+// end. Used inside the stencil and the forward elimination (three fewer operations each).
+__device__ __forceinline__ dw dw_fma_u(dw a, dw b, dw c) {
+    float ph = __fmul_rn(a.hi, b.hi);
+    float pl = __fmaf_rn(a.hi, b.hi, -ph);
+    pl = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, pl));
+    float s, e;
+    two_sum(ph, c.hi, s, e);
+    return dw{s, __fadd_rn(e, __fadd_rn(pl, c.lo))};
+}
+__device__ __forceinline__ dw dw_sum4_u(dw a, dw b, dw c, dw d) {
+    float s1, e1, s2, e2, s3, e3;
+    two_sum(a.hi, b.hi, s1, e1);
+    two_sum(c.hi, d.hi, s2, e2);
+    two_sum(s1, s2, s3, e3);
+    return dw{s3, __fadd_rn(__fadd_rn(__fadd_rn(a.lo, b.lo), __fadd_rn(c.lo, d.lo)), __fadd_rn(__fadd_rn(e1, e2), e3))};
+}
+__device__ __forceinline__ dw dw_add_u(dw a, dw b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return dw{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+}
+
 // 1/a: correctly rounded float reciprocal of the high part refined by one Newton step evaluated
 // in double-word arithmetic: y = y0 + y0 (1 - a y0). Relative error about 2^-47.
 __device__ __forceinline__ dw dw_rcp(dw a) {
@@ -129,6 +155,10 @@ struct PolF64 {
     // a*b + c
     __device__ __forceinline__ static R fma(R a, R b, R c) { return ::fma(a, b, c); }
     __device__ __forceinline__ static R sum4(R a, R b, R c, R d) { return (a + b) + (c + d); }
+    // the unnormalised forms of double-word chains (the plain operations here)
+    __device__ __forceinline__ static R fma_u(R a, R b, R c) { return ::fma(a, b, c); }
+    __device__ __forceinline__ static R sum4_u(R a, R b, R c, R d) { return (a + b) + (c + d); }
+    __device__ __forceinline__ static R add_u(R a, R b) { return a + b; }
     __device__ __forceinline__ static R neg(R a) { return -a; }
     __device__ __forceinline__ static R rcp(R a) { return 1.0 / a; }
     // per-thread partial sum type for dot products and norms
@@ -156,6 +186,9 @@ struct PolF32 {
     __device__ __forceinline__ static R mul(R a, R b) { return a * b; }
     __device__ __forceinline__ static R fma(R a, R b, R c) { return fmaf(a, b, c); }
     __device__ __forceinline__ static R sum4(R a, R b, R c, R d) { return (a + b) + (c + d); }
+    __device__ __forceinline__ static R fma_u(R a, R b, R c) { return fmaf(a, b, c); }
+    __device__ __forceinline__ static R sum4_u(R a, R b, R c, R d) { return (a + b) + (c + d); }
+    __device__ __forceinline__ static R add_u(R a, R b) { return a + b; }
     __device__ __forceinline__ static R neg(R a) { return -a; }
     __device__ __forceinline__ static R rcp(R a) { return __frcp_rn(a); }
     // Kahan-compensated float partial sums (the FP32 pipe is the fast one on this part)
@@ -197,6 +230,9 @@ struct PolDW {
     __device__ __forceinline__ static R mul(R a, R b) { return dw_mul(a, b); }
     __device__ __forceinline__ static R fma(R a, R b, R c) { return dw_fma(a, b, c); }
     __device__ __forceinline__ static R sum4(R a, R b, R c, R d) { return dw_sum4(a, b, c, d); }
+    __device__ __forceinline__ static R fma_u(R a, R b, R c) { return dw_fma_u(a, b, c); }
+    __device__ __forceinline__ static R sum4_u(R a, R b, R c, R d) { return dw_sum4_u(a, b, c, d); }
+    __device__ __forceinline__ static R add_u(R a, R b) { return dw_add_u(a, b); }
     __device__ __forceinline__ static R neg(R a) { return dw_neg(a); }
     __device__ __forceinline__ static R rcp(R a) { return dw_rcp(a); }
     // Kahan-compensated float partial sums of hi*hi + 2 hi*lo (relative accuracy ~1e-7 per

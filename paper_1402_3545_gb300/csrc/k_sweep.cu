@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
             }
             if constexpr (STACK) {
                 const R inv = percol ? P::ld_plain(ringI, slot * FPL + tid) : P::ld(L.finv, k);
-                const R d = P::mul(P::fma(vv, d_prev, r), inv);
+                const R d = P::mul(P::fma_u(vv, d_prev, r), inv);
                 R g = d;
                 if constexpr (GFORM) {
                     // g_k = u_k + rho d'_k - w_k u_{k+1} (um, uc now hold u_k, u_{k+1})

@@ -132,12 +132,13 @@ __device__ __forceinline__ typename P::R sweep_residual(typename P::R fk, typena
                                                         typename P::R n, typename P::R um, typename P::R up,
                                                         typename P::R cx, typename P::R cy, typename P::R vv,
                                                         bool iso) {
-    typename P::R r = P::fma(P::neg(diag), uc, fk);
+    // one renormalisation at the end of the chain (the _u forms, see arith.cuh)
+    typename P::R r = P::fma_u(P::neg(diag), uc, fk);
     if (iso)
-        r = P::fma(cx, P::sum4(w, e, s, n), r);
+        r = P::fma_u(cx, P::sum4_u(w, e, s, n), r);
     else
-        r = P::fma(cy, P::add(s, n), P::fma(cx, P::add(w, e), r));
-    return P::fma(vv, P::add(um, up), r);
+        r = P::fma_u(cy, P::add_u(s, n), P::fma_u(cx, P::add_u(w, e), r));
+    return P::fma(vv, P::add_u(um, up), r);
 }
 
 // value of policy PA converted to policy PB's arithmetic (no-op when they coincide)

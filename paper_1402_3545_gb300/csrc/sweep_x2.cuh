@@ -217,8 +217,8 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
                 } else {
                     i0v = i1v = P::ld(L.finv, k);
                 }
-                dp0 = P::mul(P::fma(v0, dp0, r0), i0v);
-                dp1 = P::mul(P::fma(v1, dp1, r1), i1v);
+                dp0 = P::mul(P::fma_u(v0, dp0, r0), i0v);
+                dp1 = P::mul(P::fma_u(v1, dp1, r1), i1v);
                 R g0 = dp0, g1 = dp1;
                 if constexpr (GFORM) {
                     // g_k = u_k + rho d'_k - w_k u_{k+1} (um*, uc* now hold u_k, u_{k+1})
