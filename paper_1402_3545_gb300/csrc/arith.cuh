@@ -114,6 +114,13 @@ __device__ __forceinline__ dw dw_sum4_u(dw a, dw b, dw c, dw d) {
     two_sum(s1, s2, s3, e3);
     return dw{s3, __fadd_rn(__fadd_rn(__fadd_rn(a.lo, b.lo), __fadd_rn(c.lo, d.lo)), __fadd_rn(__fadd_rn(e1, e2), e3))};
 }
+__device__ __forceinline__ dw dw_mul_u(dw a, dw b) {
+    float ch = __fmul_rn(a.hi, b.hi);
+    float cl1 = __fmaf_rn(a.hi, b.hi, -ch);
+    float tl = __fmul_rn(a.hi, b.lo);
+    float cl2 = __fmaf_rn(a.lo, b.hi, tl);
+    return dw{ch, __fadd_rn(cl1, cl2)};
+}
 __device__ __forceinline__ dw dw_add_u(dw a, dw b) {
     float s, e;
     two_sum(a.hi, b.hi, s, e);
@@ -159,6 +166,7 @@ struct PolF64 {
     __device__ __forceinline__ static R fma_u(R a, R b, R c) { return ::fma(a, b, c); }
     __device__ __forceinline__ static R sum4_u(R a, R b, R c, R d) { return (a + b) + (c + d); }
     __device__ __forceinline__ static R add_u(R a, R b) { return a + b; }
+    __device__ __forceinline__ static R mul_u(R a, R b) { return a * b; }
     __device__ __forceinline__ static R neg(R a) { return -a; }
     __device__ __forceinline__ static R rcp(R a) { return 1.0 / a; }
     // per-thread partial sum type for dot products and norms
@@ -189,6 +197,7 @@ struct PolF32 {
     __device__ __forceinline__ static R fma_u(R a, R b, R c) { return fmaf(a, b, c); }
     __device__ __forceinline__ static R sum4_u(R a, R b, R c, R d) { return (a + b) + (c + d); }
     __device__ __forceinline__ static R add_u(R a, R b) { return a + b; }
+    __device__ __forceinline__ static R mul_u(R a, R b) { return a * b; }
     __device__ __forceinline__ static R neg(R a) { return -a; }
     __device__ __forceinline__ static R rcp(R a) { return __frcp_rn(a); }
     // Kahan-compensated float partial sums (the FP32 pipe is the fast one on this part)
@@ -233,6 +242,7 @@ struct PolDW {
     __device__ __forceinline__ static R fma_u(R a, R b, R c) { return dw_fma_u(a, b, c); }
     __device__ __forceinline__ static R sum4_u(R a, R b, R c, R d) { return dw_sum4_u(a, b, c, d); }
     __device__ __forceinline__ static R add_u(R a, R b) { return dw_add_u(a, b); }
+    __device__ __forceinline__ static R mul_u(R a, R b) { return dw_mul_u(a, b); }
     __device__ __forceinline__ static R neg(R a) { return dw_neg(a); }
     __device__ __forceinline__ static R rcp(R a) { return dw_rcp(a); }
     // Kahan-compensated float partial sums of hi*hi + 2 hi*lo (relative accuracy ~1e-7 per

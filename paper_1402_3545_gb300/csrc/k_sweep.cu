@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
             }
             if constexpr (STACK) {
                 const R inv = percol ? P::ld_plain(ringI, slot * FPL + tid) : P::ld(L.finv, k);
-                const R d = P::mul(P::fma_u(vv, d_prev, r), inv);
+                const R d = P::mul_u(P::fma_u(vv, d_prev, r), inv);
                 R g = d;
                 if constexpr (GFORM) {
                     // g_k = u_k + rho d'_k - w_k u_{k+1} (um, uc now hold u_k, u_{k+1})
@@ -262,21 +262,20 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
                 cp_commit();
             };
             for (int s = 0; s < PD; ++s) issue_back(nz - 1 - s, s);
-            const bool scaled = coef != 1.0;
             R xn = vzero;
             slot = 0;
             for (int k = nz - 1; k >= 0; --k) {
                 cp_wait<PD - 1>();
                 const R w = percol ? P::ld_plain(bW, slot * NT + tid) : P::ld(L.fw, k);
                 const R dk = GS ? P::ld_plain(bD, slot * NT + tid) : stack[(size_t)k * NT + tid];
-                xn = P::fma(w, xn, dk);
+                xn = P::fma_u(w, xn, dk);  // the recurrence carries unnormalised pairs
                 const size_t id = (size_t)k * pl + c;
                 if constexpr (GFORM)
                     P::st(reinterpret_cast<S*>(out), id, xn);
                 else if constexpr (MODE == MODE_SMOOTH)
                     P::st(reinterpret_cast<S*>(out), id, P::fma(cf, xn, P::ld_plain(bU, slot * NT + tid)));
                 else
-                    P::st(reinterpret_cast<S*>(out), id, scaled ? P::mul(cf, xn) : xn);
+                    P::st(reinterpret_cast<S*>(out), id, P::mul(cf, xn));  // also renormalises the pair
                 issue_back(k - PD, slot);
                 slot = (slot + 1 == PD) ? 0 : slot + 1;
             }

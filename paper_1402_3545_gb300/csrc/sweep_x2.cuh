@@ -217,8 +217,8 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
                 } else {
                     i0v = i1v = P::ld(L.finv, k);
                 }
-                dp0 = P::mul(P::fma_u(v0, dp0, r0), i0v);
-                dp1 = P::mul(P::fma_u(v1, dp1, r1), i1v);
+                dp0 = P::mul_u(P::fma_u(v0, dp0, r0), i0v);
+                dp1 = P::mul_u(P::fma_u(v1, dp1, r1), i1v);
                 R g0 = dp0, g1 = dp1;
                 if constexpr (GFORM) {
                     // g_k = u_k + rho d'_k - w_k u_{k+1} (um*, uc* now hold u_k, u_{k+1})
@@ -289,8 +289,8 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
                 } else {
                     w0 = w1 = P::ld(L.fw, k);
                 }
-                x0 = P::fma(w0, x0, P::ld_plain(bD, o));
-                x1 = P::fma(w1, x1, P::ld_plain(bD, o + 1));
+                x0 = P::fma_u(w0, x0, P::ld_plain(bD, o));  // the recurrence carries unnormalised pairs
+                x1 = P::fma_u(w1, x1, P::ld_plain(bD, o + 1));
                 const size_t id = (size_t)k * pl + c;
                 if constexpr (MODE == MODE_SMOOTH) {
                     R o0 = x0, o1 = x1;  // GFORM: the recurrence already yields u'
@@ -305,8 +305,9 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
                         P::st(reinterpret_cast<S*>(out), id + 1, o1);
                     }
                 } else {
-                    P::st(reinterpret_cast<S*>(out), id, coef != 1.0 ? P::mul(cf, x0) : x0);
-                    P::st(reinterpret_cast<S*>(out), id + 1, coef != 1.0 ? P::mul(cf, x1) : x1);
+                    // the product also renormalises the pair the recurrence carried
+                    P::st(reinterpret_cast<S*>(out), id, P::mul(cf, x0));
+                    P::st(reinterpret_cast<S*>(out), id + 1, P::mul(cf, x1));
                 }
                 issue_back(k - PD, slot);
                 slot = (slot + 1 == PD) ? 0 : slot + 1;
