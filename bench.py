@@ -34,8 +34,8 @@ from paper_1402_3545_gb300 import workloads  # noqa: E402
 METRIC = "MG solve ms to 1e-6 rel. residual & % of HBM peak, FP64 vs mixed/learned"
 # dram__bytes_read.sum + dram__bytes_write.sum of one finest-level Smooth launch (k_sweep_x2,
 # double-word) on the 512^2 x 128 problem, per tile variant, from the ncu captures summarised in
-# profiles/k_sweep_x2_dw_smooth_mid_512x512x128.md (variant 6: 1.2749 GB + 0.4002 GB)
-PROFILED_SMOOTH_TRAFFIC = {5: 1557382400, 6: 1675119872, 7: 1642060800}
+# profiles/k_sweep_x2_dw_smooth_mid_512x512x128.md (variant 6: 1.2650 GB + 0.3982 GB)
+PROFILED_SMOOTH_TRAFFIC = {5: 1554562560, 6: 1663204352, 7: 1630302208}
 HBM_FALLBACK_GBS = 6800.0
 
 
