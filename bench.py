@@ -49,8 +49,8 @@ def parse_args():
     ap.add_argument("--solve-only", action="store_true",
                     help="time the solves only (no kernel timing, e2e, variants or CPU baseline): "
                          "the command the ncu launch-list profile runs")
-    ap.add_argument("--kernel-only", choices=["smooth", "residual", "restrict_smooth", "prolongate", "line_solve",
-                                              "cg_spmv", "cg_tridiag", "nn_forward"],
+    ap.add_argument("--kernel-only", choices=["smooth", "residual", "restrict_smooth", "residual_restrict",
+                                              "prolongate", "line_solve", "cg_spmv", "cg_tridiag", "nn_forward"],
                     help="launch only this finest-level kernel a few times (tile variant --variant, "
                          "no autotuning): the command a per-kernel ncu capture runs")
     ap.add_argument("--variant", type=int, default=3)
@@ -208,6 +208,21 @@ def per_solve_ms(elapsed_max_ms: float, steps: int, world: int) -> float:
     """Replicas only: every rank solves its own copy `steps` times, so the job solves steps * world
     problems in the slowest rank's time."""
     return elapsed_max_ms / (steps * world)
+
+
+def solve_memrefs(level_cells, iters: int, nu_pre: int = 2, nu_post: int = 2, n_coarse: int = 2) -> float:
+    """Memory references of a whole multigrid solve by the paper's per-kernel model (Table of the
+    kernels in Sec. 3.1: Smooth and Residual 3 per cell, RestrictSmooth 6 per coarse cell,
+    Prolongate 2.25 per fine cell): `iters` V(nu_pre, nu_post) cycles, each led by the finest-level
+    Smooth that also yields the previous cycle's residual norm, plus the solve's first Smooth.
+    level_cells[l] = cells of level l (1 = coarsest .. L = finest; index 0 unused)."""
+    L = len(level_cells) - 1
+    n = level_cells
+    cycle = (3 * (nu_pre + nu_post) + 3 + 2.25) * n[L]
+    for l in range(2, L):
+        cycle += (6 + 3 * (nu_pre - 1) + 3 + 2.25 + 3 * nu_post) * n[l]
+    cycle += (6 + 3 * (n_coarse - 1)) * n[1]
+    return 3 * n[L] + iters * cycle
 
 
 def nn_flops_per_voxel(cin: int) -> int:
@@ -378,7 +393,7 @@ def run_kernel_only(args):
     prec = {"dw": tpmg.DW, "f32": tpmg.F32, "f64": tpmg.F64}[args.precision]
     kid = {"smooth": tpmg.K_SMOOTH, "residual": tpmg.K_RESIDUAL, "restrict_smooth": tpmg.K_RESTRICT_SMOOTH,
            "prolongate": tpmg.K_PROLONGATE, "line_solve": tpmg.K_LINE_SOLVE, "cg_spmv": tpmg.K_CG_SPMV,
-           "cg_tridiag": tpmg.K_CG_TRIDIAG}[args.kernel_only]
+           "cg_tridiag": tpmg.K_CG_TRIDIAG, "residual_restrict": tpmg.K_RESIDUAL_RESTRICT}[args.kernel_only]
     p = workloads.mid()
     op = tpmg.Operator.from_problem(p)
     tpmg.op_reserve(op.op, tpmg.MIXED if prec == tpmg.F32 else prec)
@@ -457,13 +472,15 @@ def run_ours(args, rank, world, dist):
     finest_variant = variants_dw[-1] if variants_dw else None
     kernel_ms = {name: round(tpmg.time_kernel(op.op, prec, kid, reps=10), 4) for name, kid in [
         ("residual", tpmg.K_RESIDUAL), ("restrict_smooth", tpmg.K_RESTRICT_SMOOTH),
+        ("residual_restrict_fused", tpmg.K_RESIDUAL_RESTRICT),
         ("prolongate", tpmg.K_PROLONGATE), ("cg_spmv", tpmg.K_CG_SPMV), ("cg_tridiag", tpmg.K_CG_TRIDIAG)]}
     kernel_ms["smooth"] = round(t_smooth, 4)
     tpmg.op_reserve(op.op, tpmg.MIXED)
     variants_f32 = autotune.tune(op, tpmg.F32, lambda_varies=True)
     kernel_ms_f32 = {name: round(tpmg.time_kernel(op.op, tpmg.F32, kid, reps=10), 4) for name, kid in [
         ("smooth", tpmg.K_SMOOTH), ("residual", tpmg.K_RESIDUAL), ("line_solve", tpmg.K_LINE_SOLVE),
-        ("restrict_smooth", tpmg.K_RESTRICT_SMOOTH), ("prolongate", tpmg.K_PROLONGATE)]}
+        ("restrict_smooth", tpmg.K_RESTRICT_SMOOTH), ("residual_restrict_fused", tpmg.K_RESIDUAL_RESTRICT),
+        ("prolongate", tpmg.K_PROLONGATE)]}
     # native FP64 Smooth against the FP64 ALU: per cell the stencil residual (3 FMAs and 4 adds),
     # the forward elimination (FMA and multiply), the back substitution (2 FMAs) and the norm (FMA)
     # are 12 FP64 operations; GB300's nominal FP64 rate is 1.25 TFLOP/s (0.625 T FMA-or-add/s)
@@ -487,6 +504,18 @@ def run_ours(args, rank, world, dist):
                 # lambda^2 varies over the level, so the Thomas factors 1/m_k and v/m_k are read per cell
                 "bytes_with_factors": 5 * 8 * n,
                 "frac_with_factors": round(5 * 8 * n / (t_smooth * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
+
+    # the whole solve's useful bandwidth: the paper's per-kernel memory references x 8 B per solve
+    # (double-word and native FP64 levels both store 8-byte values) over the solve time
+    level_cells = [0] + [op.level_n(l) for l in range(1, op.L + 1)]
+    solve_bytes = 8 * solve_memrefs(level_cells, iters[-1])
+    solve_hbm = {"bytes_per_solve": int(solve_bytes), "ms_per_solve": round(value, 4),
+                 "achieved": round(solve_bytes / (value * 1e-3) / 1e9, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": round(solve_bytes / (value * 1e-3) / 1e9 / peaks["hbm_gbs"], 4), "peak_source": peak_kind,
+                 "model": ("memory references of the paper's kernels (Smooth and Residual 3 per cell, "
+                           "RestrictSmooth 6 per coarse cell, Prolongate 2.25 per fine cell) x 8 B, "
+                           f"{iters[-1]} V(2,2) cycles + the first Smooth; the fused Residual+RestrictSmooth "
+                           "moves less than its two kernels' share")}
 
     # end to end through the public API with host buffers, two ways: (a) the solve reads f from
     # page-locked host memory and writes u back there in its first and last kernels; (b) explicit
@@ -557,7 +586,8 @@ def run_ours(args, rank, world, dist):
                            "solver": "V(2,2), rho 0.8, 2 coarse steps", "tol": 1e-6, "precision": "DW",
                            "parallelism": f"replicas{world}",
                            "l2": "inputs larger than L2 (268 MB per FP64 field > 129 MB)"},
-                "iters": iters[-1], "roofline": roofline, "roofline_f64": roofline_f64, "kernel_ms": kernel_ms,
+                "iters": iters[-1], "roofline": roofline, "solve_hbm": solve_hbm, "roofline_f64": roofline_f64,
+                "kernel_ms": kernel_ms,
                 "kernel_ms_f32": kernel_ms_f32,
                 "tile_variants": {"dw": variants_dw, "f32": variants_f32}, "variants": variants,
                 "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": 8 * n,

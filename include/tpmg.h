@@ -113,6 +113,23 @@ tpmg_status tpmg_residual(tpmg_op* op, int level, tpmg_precision prec, const voi
  * r_f of level+1), u_c = rho M_c^{-1} f_c. */
 tpmg_status tpmg_restrict_smooth(tpmg_op* op, int level, tpmg_precision prec, double rho,
                                  const void* r_fine, void* f_c, void* u_c, void* stream);
+/* Residual of fine level level+1 and RestrictSmooth onto coarse level `level` (< L) in one pass
+ * (Algorithm 1: the kernels "Residual" and "RestrictSmooth" of Sec. 3.1 fused; the fine residual is
+ * not stored): f_c = R (f_fine - A u_fine), u_c = rho M_c^{-1} f_c. u_fine, f_fine are fields of
+ * level+1, f_c, u_c of `level` (caller-owned device memory, layout and element type as above). The
+ * fused kernel performs the two kernels' arithmetic operation for operation: in TPMG_F64 and
+ * TPMG_F32 the result equals tpmg_residual followed by tpmg_restrict_smooth bit for bit (in TPMG_DW
+ * those separate calls round the residual to double in between, the fused pass does not). Where the
+ * fused kernel does not apply (fine nx % 64 != 0 or odd ny, a coarse level of at most 4096 columns,
+ * 16-byte misaligned fine fields, a double-word fine level over a native-FP64 coarse one) the two
+ * kernels run instead. The multigrid cycles use the fusion unless tpmg_set_fusion turned it off. */
+tpmg_status tpmg_residual_restrict_smooth(tpmg_op* op, int level, tpmg_precision prec, double rho,
+                                          const void* u_fine, const void* f_fine, void* f_c, void* u_c,
+                                          void* stream);
+/* enable != 0 (the default): V-cycles of this operator fuse Residual and RestrictSmooth wherever
+ * tpmg_residual_restrict_smooth's fused kernel applies; 0: separate kernels. Invalidates the
+ * operator's cached CUDA graphs. */
+tpmg_status tpmg_set_fusion(tpmg_op* op, int enable);
 /* u_f += P u_c on fine level `level` (> 1), P the cell-centred bilinear interpolation from level-1
  * (kernel "Prolongate", Sec. 2.2). */
 tpmg_status tpmg_prolongate(tpmg_op* op, int level, tpmg_precision prec, const void* u_c, void* u_f,
@@ -190,7 +207,8 @@ typedef enum {
     TPMG_K_PROLONGATE = 5,      /* level L-1 -> L Prolongate */
     TPMG_K_CG_SPMV = 6,         /* fused CG SpMV on the finest level */
     TPMG_K_CG_TRIDIAG = 7,      /* fused CG Tridiag on the finest level */
-    TPMG_K_COUNT = 8
+    TPMG_K_RESIDUAL_RESTRICT = 8, /* level L Residual + level L-1 RestrictSmooth, fused */
+    TPMG_K_COUNT = 9
 } tpmg_kernel;
 /* Launches kernel `k` of precision `prec` (TPMG_F64, TPMG_F32 or TPMG_DW) `reps` times on the
  * operator's own workspace buffers of that precision (whatever they hold, e.g. after a solve) and

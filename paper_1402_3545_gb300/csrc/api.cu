@@ -82,6 +82,7 @@ struct tpmg_op {
     int lsw_dw = 1;                // the double-word solver uses native FP64 below this level
     bool fac_ready[3] = {false, false, false};
     int variant[3][MAXL + 1];      // autotuned tile variant of the pipelined Smooth (-1: default)
+    int fuse_restrict = 1;         // V-cycles fuse Residual and RestrictSmooth where the kernel applies
     void* cgbuf[3][4] = {};  // r, z, p, q per policy
     void* io[4] = {};        // DW conversion buffers for single applications (finest-level size)
     double* partials = nullptr;
@@ -344,18 +345,29 @@ struct Cycle {
         else
             launch_prolongate<PC, PC>(nxc, nyc, nz, (const SC*)uc, (SC*)cur, done, s);
     }
-    // coarse level l: RestrictSmooth from level l+1's residual, then the rest of the cycle
-    void* coarse(int l) {
+    // Residual of level l and RestrictSmooth onto level l-1 in one fused pass where both levels
+    // run in the same policy and the shapes fit, else the two kernels; then the rest of the cycle
+    // on level l-1. Returns level l-1's result.
+    void* residual_coarse(int l, const void* cur) {
+        if (hi(l) && hi(l - 1) && op->fuse_restrict &&
+            launch_residual_restrict<PF>(level_view<PF>(op, l), level_view<PF>(op, l - 1), prm->rho, (const SF*)cur,
+                                         (const SF*)f[l], (SF*)f[l - 1], (SF*)u[l - 1], done, s) >= 0)
+            return coarse(l - 1, true);
+        residual(l, cur);
+        return coarse(l - 1, false);
+    }
+    // coarse level l: RestrictSmooth from level l+1's residual (already done when restricted), then
+    // the rest of the cycle
+    void* coarse(int l, bool restricted) {
         void* cur = u[l];
         void* oth = ub[l];
-        restrict_smooth(l, cur);
+        if (!restricted) restrict_smooth(l, cur);
         if (l == 1) {
             for (int t = 1; t < prm->n_coarse; ++t) smooth(l, cur, oth, nullptr);
             return cur;
         }
         for (int t = 1; t < prm->nu_pre; ++t) smooth(l, cur, oth, nullptr);
-        residual(l, cur);
-        void* uc = coarse(l - 1);
+        void* uc = residual_coarse(l, cur);
         prolongate(l, uc, cur);
         for (int t = 0; t < prm->nu_post; ++t) smooth(l, cur, oth, nullptr);
         return cur;
@@ -368,8 +380,7 @@ struct Cycle {
             return;
         }
         for (int t = 1; t < prm->nu_pre; ++t) smooth(L, cur, oth, nullptr);
-        residual(L, cur);
-        void* uc = coarse(L - 1);
+        void* uc = residual_coarse(L, cur);
         prolongate(L, uc, cur);
         for (int t = 0; t < prm->nu_post; ++t) smooth(L, cur, oth, nullptr);
     }
@@ -917,6 +928,53 @@ tpmg_status tpmg_restrict_smooth(tpmg_op* op, int level, tpmg_precision prec, do
     return TPMG_OK;
 }
 
+tpmg_status tpmg_residual_restrict_smooth(tpmg_op* op, int level, tpmg_precision prec, double rho,
+                                          const void* u_fine, const void* f_fine, void* f_c, void* u_c,
+                                          void* stream) {
+    TRY(check_level(op, level));
+    if (level >= op->g.L) return set_err(TPMG_ERR_ARG, "residual_restrict_smooth needs a coarse level < L");
+    if (!u_fine || !f_fine || !f_c || !u_c) return set_err(TPMG_ERR_ARG, "NULL field");
+    if (prec == TPMG_DW && level + 1 < op->lsw_dw) prec = TPMG_F64;  // see DW_KAPPA_MAX
+    if (prec == TPMG_DW && level < op->lsw_dw) {
+        // double-word fine level over a native-FP64 coarse level: the two kernels, the residual
+        // handed over in FP64 through a staging buffer
+        TRY(prep_unit(op, prec));
+        TRY(tpmg_residual(op, level + 1, prec, u_fine, f_fine, op->io[3], nullptr, stream));
+        return tpmg_restrict_smooth(op, level, prec, rho, op->io[3], f_c, u_c, stream);
+    }
+    TRY(prep_unit(op, prec));
+    TRY(ensure_hier(op, pid_of(prec), true));  // the fine residual buffer of the unfused fallback
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nc = lvl_cells(op, level), nf = lvl_cells(op, level + 1);
+    DISPATCH_PREC(prec, {
+        typedef typename P::S S;
+        auto* ui = in_ptr<P>(op, s, 0, u_fine, nf);
+        auto* fi = in_ptr<P>(op, s, 1, f_fine, nf);
+        auto* fo = out_ptr<P>(op, 2, f_c);
+        auto* uo = out_ptr<P>(op, 3, u_c);
+        Lv<P> LF = level_view<P>(op, level + 1), LC = level_view<P>(op, level);
+        if (launch_residual_restrict<P>(LF, LC, rho, ui, fi, fo, uo, nullptr, s) < 0) {
+            S* r = (S*)op->hier[P::id].r[level + 1];
+            launch_residual<P, P>(LF, ui, fi, r, nullptr, nullptr, s);
+            launch_restrict_smooth<P, P>(LC, rho, r, fo, uo, nullptr, s);
+        }
+        out_back<P>(op, s, 2, f_c, nc);
+        out_back<P>(op, s, 3, u_c, nc);
+    });
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+tpmg_status tpmg_set_fusion(tpmg_op* op, int enable) {
+    if (!op) return set_err(TPMG_ERR_ARG, "NULL operator");
+    const int on = enable != 0;
+    if (op->fuse_restrict != on) {
+        op->fuse_restrict = on;
+        invalidate_graphs(op);
+    }
+    return TPMG_OK;
+}
+
 tpmg_status tpmg_prolongate(tpmg_op* op, int level, tpmg_precision prec, const void* u_c, void* u_f, void* stream) {
     TRY(check_level(op, level));
     if (prec == TPMG_DW && level - 1 < op->lsw_dw) prec = TPMG_F64;
@@ -1179,7 +1237,7 @@ tpmg_status tpmg_time_kernel(tpmg_op* op, tpmg_precision prec, tpmg_kernel k, in
     if (prec != TPMG_F64 && prec != TPMG_F32 && prec != TPMG_DW)
         return set_err(TPMG_ERR_ARG, "precision must be TPMG_F64, TPMG_F32 or TPMG_DW");
     const int pid = pid_of(prec), L = op->g.L;
-    if ((k == TPMG_K_RESTRICT_SMOOTH || k == TPMG_K_PROLONGATE) && L < 2)
+    if ((k == TPMG_K_RESTRICT_SMOOTH || k == TPMG_K_PROLONGATE || k == TPMG_K_RESIDUAL_RESTRICT) && L < 2)
         return set_err(TPMG_ERR_ARG, "transfer kernels need two levels");
     TRY(ensure_hier(op, pid, true));
     TRY(ensure_cg(op, pid));
@@ -1187,6 +1245,7 @@ tpmg_status tpmg_time_kernel(tpmg_op* op, tpmg_precision prec, tpmg_kernel k, in
     cudaStream_t s = (cudaStream_t)stream;
     launch_scalars_init(op->sc, 0.0, 1, s);
     const size_t n = lvl_cells(op, L);
+    bool bad = false;  // the kernel does not apply to this operator's levels
     auto run = [&](auto tag) {
         typedef decltype(tag) P;
         typedef typename P::S S;
@@ -1210,6 +1269,11 @@ tpmg_status tpmg_time_kernel(tpmg_op* op, tpmg_precision prec, tpmg_kernel k, in
                 break;
             case TPMG_K_CG_SPMV: launch_cg_spmv<P>(LL, op->sc, cg[0], cg[2], cg[1], cg[3], op->partials, s); break;
             case TPMG_K_CG_TRIDIAG: launch_cg_tridiag<P>(LL, op->sc, cg[0], cg[3], cg[1], op->partials, s); break;
+            case TPMG_K_RESIDUAL_RESTRICT:
+                if (launch_residual_restrict<P>(LL, level_view<P>(op, L - 1), 0.8, a, f, (S*)h.f[L - 1],
+                                                (S*)h.u[L - 1], nullptr, s) < 0)
+                    bad = true;
+                break;
             default: break;
         }
         (void)n;
@@ -1221,6 +1285,7 @@ tpmg_status tpmg_time_kernel(tpmg_op* op, tpmg_precision prec, tpmg_kernel k, in
         else run(PolDW());
     };
     once();  // warm-up
+    if (bad) return set_err(TPMG_ERR_ARG, "the fused kernel does not apply to this operator's finest levels");
     CK(cudaEventRecord(op->ev0, s));
     for (int t = 0; t < reps; ++t) once();
     CK(cudaEventRecord(op->ev1, s));

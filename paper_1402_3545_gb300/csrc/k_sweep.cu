@@ -353,9 +353,9 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
                                                       const int* done) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (done && *(volatile const int*)done) return;
-    constexpr bool STACK = MODE != MODE_RESIDUAL;
-    typename P::S* slot =
-        STACK ? reinterpret_cast<typename P::S*>(L.gstack) + (size_t)blockIdx.x * L.nz * 2 * 32 * TY : nullptr;
+    typename P::S* slot = x2_slot(MODE)
+                              ? reinterpret_cast<typename P::S*>(L.gstack) + (size_t)blockIdx.x * L.nz * 2 * 32 * TY
+                              : nullptr;
     const int ntiles = (L.nx / 64) * (L.ny / TY);
     const double sm = sweep_x2_tiles<P, PO, TY, PD, MODE, HINT>(L, coef, u, f, out, partials != nullptr, blockIdx.x,
                                                                  ntiles, gridDim.x, slot, smem_raw);
@@ -366,7 +366,7 @@ template <class P, class PO, int TY, int PD, int MODE, int MINB = 1, int HINT = 
 static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, const typename P::S* f,
                         typename PO::S* out, double* partials, const int* done, cudaStream_t s, int cap) {
     typedef typename P::S S;
-    constexpr bool STACK = MODE != MODE_RESIDUAL;
+    constexpr bool STACK = x2_stack(MODE);
     constexpr bool HALO = MODE != MODE_LINESOLVE;
     if (L.nx % 64 || L.ny % TY || (STACK && (!L.gstack || !L.finv || !L.fw))) return -1;
     auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
@@ -386,6 +386,53 @@ static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, con
     if (STACK && nb > slots) nb = slots;
     if (nb > ntiles) nb = ntiles;
     kern<<<nb, dim3(32, TY), smem, s>>>(L, coef, u, f, out, partials, done);
+    note_launch();
+    return nb;
+}
+
+// ---------------------------------------------------------------- Residual + RestrictSmooth, fused
+// One pass over the fine level L: r = f - A u per fine cell (not stored), f_c = R r and
+// u_c = rho M_c^{-1} f_c on the coarse level Lc (sweep_x2_tiles in MODE_RESTRICT). Per fine cell it
+// reads u and f once; per coarse cell it writes f_c and u_c -- 2.5 instead of 4.5 memory references
+// per fine cell for the two kernels. The arithmetic is that of the separate kernels, operation for
+// operation, so the results are the same bit for bit.
+template <class P, int PD>
+__global__ void __launch_bounds__(64) k_residual_restrict_x2(Lv<P> L, XRestrict<P> xr,
+                                                               const typename P::S* __restrict__ u,
+                                                               const typename P::S* __restrict__ f, const int* done) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (done && *(volatile const int*)done) return;
+    typename P::S* slot = reinterpret_cast<typename P::S*>(L.gstack) + (size_t)blockIdx.x * L.nz * 2 * 32 * 2;
+    const int ntiles = (L.nx / 64) * (L.ny / 2);
+    sweep_x2_tiles<P, P, 2, PD, MODE_RESTRICT, 0>(L, 1.0, u, f, nullptr, false, blockIdx.x, ntiles, gridDim.x, slot,
+                                                 smem_raw, &xr);
+}
+
+template <class P>
+int launch_residual_restrict(const Lv<P>& L, const Lv<P>& Lc, double rho, const typename P::S* u,
+                             const typename P::S* f, typename P::S* fc, typename P::S* uc, const int* done,
+                             cudaStream_t s) {
+    constexpr int PD = 4;
+    if (L.nx % 64 || L.ny % 2 || !L.gstack || !Lc.finv || !Lc.fw || !Lc.v) return -1;
+    if (Lc.nx * 2 != L.nx || Lc.ny * 2 != L.ny || Lc.nz != L.nz) return -1;
+    // small coarse levels solve their columns by cyclic reduction (k_coarse.cu)
+    if (Lc.pcr && (size_t)Lc.nx * Lc.ny <= (size_t)PCR_MAX_COLS && Lc.nz <= 256) return -1;
+    auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+    if (!al(u) || !al(f)) return -1;
+    const size_t smem = sweep_x2_smem<P, 2, PD, MODE_RESTRICT>();
+    auto kern = k_residual_restrict_x2<P, PD>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int ntiles = (L.nx / 64) * (L.ny / 2);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 64, smem);
+    if (per_sm > GS_BLOCKS_PER_SM) per_sm = GS_BLOCKS_PER_SM;
+    if (per_sm < 1) per_sm = 1;
+    int nb = num_sms() * per_sm;
+    const int slots = num_sms() * GS_BLOCKS_PER_SM * GS_MAX_NT / (2 * 32 * 2);
+    if (nb > slots) nb = slots;
+    if (nb > ntiles) nb = ntiles;
+    XRestrict<P> xr{Lc, rho, fc, uc};
+    kern<<<nb, dim3(32, 2), smem, s>>>(L, xr, u, f, done);
     note_launch();
     return nb;
 }
@@ -629,7 +676,9 @@ int launch_restrict_smooth_pp(const Lv<P>& Lc, double rho, const typename PF::S*
                                           cudaStream_t);                                                     \
     template int launch_line_solve_pp<P>(const Lv<P>&, const P::S*, P::S*, double, const int*, cudaStream_t); \
     template int launch_restrict_smooth_pp<P, P>(const Lv<P>&, double, const P::S*, P::S*, P::S*, const int*, \
-                                                 cudaStream_t);
+                                                 cudaStream_t);                                                \
+    template int launch_residual_restrict<P>(const Lv<P>&, const Lv<P>&, double, const P::S*, const P::S*, P::S*, \
+                                             P::S*, const int*, cudaStream_t);
 
 TPMG_SWEEP_INST(PolF64)
 TPMG_SWEEP_INST(PolF32)

@@ -200,6 +200,14 @@ int launch_line_solve_pp(const Lv<P>& L, const typename P::S* b, typename P::S* 
 template <class PF, class P>
 int launch_restrict_smooth_pp(const Lv<P>& Lc, double rho, const typename PF::S* rf, typename P::S* fc,
                               typename P::S* uc, const int* done, cudaStream_t s);
+// Residual of the fine level L and RestrictSmooth onto the coarse level Lc in one pass (the fine
+// residual is not stored): f_c = R (f - A u), u_c = rho M_c^{-1} f_c, the same values as
+// launch_residual followed by launch_restrict_smooth where those solve the coarse columns by the
+// Thomas algorithm. -1 when the levels do not fit (nx % 64, ny % 2, alignment, small coarse level).
+template <class P>
+int launch_residual_restrict(const Lv<P>& L, const Lv<P>& Lc, double rho, const typename P::S* u,
+                             const typename P::S* f, typename P::S* fc, typename P::S* uc, const int* done,
+                             cudaStream_t s);
 // number of blocks launch_residual uses on an nx x ny level (= partial sums it writes)
 int residual_blocks(int nx, int ny, int nz, int bytes_per_value);
 

@@ -31,7 +31,24 @@ __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
-enum { MODE_SMOOTH = 0, MODE_RESIDUAL = 1, MODE_LINESOLVE = 2 };
+enum { MODE_SMOOTH = 0, MODE_RESIDUAL = 1, MODE_LINESOLVE = 2, MODE_RESTRICT = 3 };
+// modes whose per-column Thomas stack lives in the block's scratch slot (MODE_RESTRICT keeps the
+// stack of the coarse column there)
+__host__ __device__ constexpr bool x2_stack(int mode) { return mode == MODE_SMOOTH || mode == MODE_LINESOLVE; }
+__host__ __device__ constexpr bool x2_slot(int mode) { return mode != MODE_RESIDUAL; }
+
+// MODE_RESTRICT: the fine level's residual r = f - A u is not stored; each 2 x 2 group of fine
+// columns is restricted on the fly to the coarse right-hand side f_c = 1/4 (sum of the children)
+// and the coarse level's first smoothing step from a zero guess, u_c = rho M_c^{-1} f_c, follows
+// (Residual and RestrictSmooth of Algorithm 1 in one pass over the fine level). The coarse level
+// and the two outputs:
+template <class P>
+struct XRestrict {
+    Lv<P> Lc;
+    double rho;
+    typename P::S* fc;
+    typename P::S* uc;
+};
 
 // L2 eviction hints of the persistent sweeps (bit mask). The Thomas scratch of a persistent block
 // is written in the forward sweep and read back in the backward sweep a whole column later; the
@@ -57,13 +74,15 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
                                                  const typename P::S* __restrict__ f,
                                                  typename PO::S* __restrict__ out, bool want_norm, int tile0,
                                                  int tile_end, int tile_step, typename P::S* gstack,
-                                                 unsigned char* smem_raw) {
+                                                 unsigned char* smem_raw, const XRestrict<P>* xr = nullptr) {
     typedef typename P::S S;
     typedef typename P::R R;
     constexpr int NT = 32 * TY;
     constexpr int UW = 68;
-    constexpr bool STACK = MODE != MODE_RESIDUAL;
+    constexpr bool STACK = x2_stack(MODE);
     constexpr bool HALO = MODE != MODE_LINESOLVE;
+    constexpr bool RESTR = MODE == MODE_RESTRICT;
+    static_assert(!RESTR || TY == 2, "the fused restriction pairs the block's two rows");
     constexpr bool GFORM = MODE == MODE_SMOOTH && P::id == 1;  // as in k_sweep_pp
     constexpr int UPL = HALO ? (TY + 2) * UW : 0;
     constexpr int FPL = 2 * NT;
@@ -75,6 +94,8 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
     S* ringU = reinterpret_cast<S*>(smem_raw);
     S* ringF = ringU + PD * UPL;
     S* ringI = ringF + PD * FPL;
+    S* ringIc = ringI + PD * IPL;  // RESTR: 1/m_k of the coarse columns, 32 per plane
+    S* xs = ringIc + (RESTR ? PD * 32 : 0);  // RESTR: row pair sums of the odd row, 2 planes
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const size_t pl = (size_t)nx * ny;
@@ -93,6 +114,9 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
     for (int tile = tile0; tile < tile_end; tile += tile_step) {
         const int i0 = (tile % tiles_x) * 64, j0 = (tile / tiles_x) * TY;
         const size_t c = (size_t)(j0 + ty) * nx + (i0 + 2 * tx);  // the thread's first column
+        // RESTR: the coarse column over this thread's pair and the pair of the next row
+        const size_t plc = pl / 4;
+        const size_t cc = (size_t)(j0 / 2) * (nx / 2) + (i0 / 2 + tx);
         __syncthreads();  // the previous tile's rings are no longer read
 
         // halo of the u plane: 2 rows x 32 pairs (one pair per thread when TY = 2) and 2 TY side
@@ -129,6 +153,11 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
                     cp_async<PB>(&ringF[slot * FPL + 2 * tid], rhs + b + c);
                     if (fac) cp_async<PB>(&ringI[slot * FPL + 2 * tid], L.finv + b + c);
                 }
+                if constexpr (RESTR) {
+                    const int kc0 = xr->Lc.fac_k0;
+                    if (ty == 0 && xr->Lc.fac_percol && !(k >= kc0 && k <= nz - 2))
+                        cp_async<sizeof(S)>(&ringIc[slot * 32 + tx], xr->Lc.finv + (size_t)k * plc + cc);
+                }
                 if (HALO) {
                     cp_async<PB>(&Us[(ty + 1) * UW + 2 + 2 * tx], u + b + c);
 #pragma unroll
@@ -156,6 +185,17 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
         const R dh1a = P::add(dh, v0), dh2a = P::add(dh1a, v0);
         const R dh1b = P::add(dh, v1), dh2b = P::add(dh1b, v1);
         R um0 = vzero, um1 = vzero, uc0 = vzero, uc1 = vzero, dp0 = vzero, dp1 = vzero;
+        // RESTR: coupling and converged factors of the coarse column, its forward-eliminated value
+        R vcc = vzero, cic = vzero, cwc = vzero, dpc = vzero, qv = vzero;
+        if constexpr (RESTR) {
+            if (ty == 0) {
+                vcc = P::ld(xr->Lc.v, cc);
+                if (xr->Lc.fac_percol && xr->Lc.fac_k0 <= nz - 2) {
+                    cic = P::ld(xr->Lc.finv, (size_t)(nz - 2) * plc + cc);
+                    cwc = P::ld(xr->Lc.fw, (size_t)(nz - 2) * plc + cc);
+                }
+            }
+        }
         int slot = 0;
         const int ctr = (ty + 1) * UW + 2 + 2 * tx;
         for (int k = 0; k < nz; ++k) {
@@ -195,6 +235,10 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
                 um1 = uc1;
                 uc0 = up0;
                 uc1 = up1;
+                if constexpr (RESTR) {
+                    qv = P::add(r0, r1);  // the row pair's sum; the odd row hands it over
+                    if (ty == 1) P::st(xs, (k & 1) * 32 + tx, qv);
+                }
             }
             if constexpr (MODE == MODE_RESIDUAL) {
                 const size_t id = (size_t)k * pl + c;
@@ -240,6 +284,22 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
                 }
             }
             if (HALO) __syncthreads();  // the slot is reused by the next issue
+            if constexpr (RESTR) {
+                if (ty == 0) {
+                    // f_c = 1/4 (even row pair + odd row pair), then the coarse forward elimination
+                    const R fk = P::mul(P::cst(0.25), P::add(qv, P::ld_plain(xs, (k & 1) * 32 + tx)));
+                    P::st(xr->fc, (size_t)k * plc + cc, fk);
+                    R ic;
+                    if (xr->Lc.fac_percol && k >= xr->Lc.fac_k0 && k <= nz - 2)
+                        ic = cic;
+                    else if (xr->Lc.fac_percol)
+                        ic = P::ld_plain(ringIc, slot * 32 + tx);
+                    else
+                        ic = P::ld(xr->Lc.finv, k);
+                    dpc = P::mul(P::fma(vcc, dpc, fk), ic);
+                    P::sts(gstack, (size_t)k * 32 + tx, dpc);
+                }
+            }
             issue_plane(k + PD, slot);
             slot = nslot;
         }
@@ -314,6 +374,43 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
             }
             cp_wait<0>();
         }
+        if constexpr (RESTR) {
+            // coarse back substitution by the even row: u_c = rho x, x_k = d'_k + (v/m_k) x_{k+1}
+            __syncthreads();  // the backward ring reuses the forward ring's shared memory
+            if (ty == 0) {
+                S* bW = reinterpret_cast<S*>(smem_raw);
+                S* bD = bW + PD * 32;
+                const bool pcc = xr->Lc.fac_percol != 0;
+                const int kc0 = xr->Lc.fac_k0;
+                auto issue_back = [&](int k, int s2) {
+                    if (k >= 0) {
+                        if (pcc && !(k >= kc0 && k <= nz - 2))
+                            cp_async<sizeof(S)>(&bW[s2 * 32 + tx], xr->Lc.fw + (size_t)k * plc + cc);
+                        cp_async<sizeof(S)>(&bD[s2 * 32 + tx], gstack + (size_t)k * 32 + tx);
+                    }
+                    cp_commit();
+                };
+                for (int s = 0; s < PD; ++s) issue_back(nz - 1 - s, s);
+                const R rho = P::cst(xr->rho);
+                R xn = vzero;
+                slot = 0;
+                for (int k = nz - 1; k >= 0; --k) {
+                    cp_wait<PD - 1>();
+                    R w;
+                    if (pcc && k >= kc0 && k <= nz - 2)
+                        w = cwc;
+                    else if (pcc)
+                        w = P::ld_plain(bW, slot * 32 + tx);
+                    else
+                        w = P::ld(xr->Lc.fw, k);
+                    xn = P::fma(w, xn, P::ld_plain(bD, slot * 32 + tx));
+                    P::st(xr->uc, (size_t)k * plc + cc, P::mul(rho, xn));
+                    issue_back(k - PD, slot);
+                    slot = (slot + 1 == PD) ? 0 : slot + 1;
+                }
+                cp_wait<0>();
+            }
+        }
     }
     return want_norm ? block_sum(P::acc_get(acc, cmp)) : 0.0;  // the block's sum, valid in thread 0
 }
@@ -321,9 +418,10 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
 
 template <class P, int TY, int PD, int MODE>
 constexpr size_t sweep_x2_smem() {
-    constexpr bool STACK = MODE != MODE_RESIDUAL;
+    constexpr bool STACK = x2_stack(MODE);
     constexpr bool HALO = MODE != MODE_LINESOLVE;
-    constexpr size_t fwd = (size_t)PD * ((HALO ? (TY + 2) * 68 : 0) + 2 * 32 * TY + (STACK ? 2 * 32 * TY : 0)) *
+    constexpr size_t fwd = ((size_t)PD * ((HALO ? (TY + 2) * 68 : 0) + 2 * 32 * TY + (STACK ? 2 * 32 * TY : 0)) +
+                            (MODE == MODE_RESTRICT ? (size_t)PD * 32 + 2 * 32 : 0)) *
                            sizeof(typename P::S);
     constexpr size_t back = STACK ? (size_t)PD * 3 * 2 * 32 * TY * sizeof(typename P::S) : 0;
     return fwd > back ? fwd : back;

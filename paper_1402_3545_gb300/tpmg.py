@@ -64,6 +64,8 @@ _SIGNATURES = {
     "tpmg_smooth": [_P, _I, _I, _D, _P, _P, _P, _P, _P],
     "tpmg_residual": [_P, _I, _I, _P, _P, _P, _P, _P],
     "tpmg_restrict_smooth": [_P, _I, _I, _D, _P, _P, _P, _P],
+    "tpmg_residual_restrict_smooth": [_P, _I, _I, _D, _P, _P, _P, _P, _P],
+    "tpmg_set_fusion": [_P, _I],
     "tpmg_prolongate": [_P, _I, _I, _P, _P, _P],
     "tpmg_cg_fused_spmv": [_P, _I, _D, _D, _P, _P, _P, _P, _P, _P],
     "tpmg_cg_fused_tridiag": [_P, _I, _D, _P, _P, _P, _P, _P, _P],
@@ -94,7 +96,8 @@ _SIGNATURES = {
     "tpmg_last_error": [],
 }
 
-K_SMOOTH, K_RESIDUAL, K_APPLY_A, K_LINE_SOLVE, K_RESTRICT_SMOOTH, K_PROLONGATE, K_CG_SPMV, K_CG_TRIDIAG = range(8)
+(K_SMOOTH, K_RESIDUAL, K_APPLY_A, K_LINE_SOLVE, K_RESTRICT_SMOOTH, K_PROLONGATE, K_CG_SPMV, K_CG_TRIDIAG,
+ K_RESIDUAL_RESTRICT) = range(9)
 
 
 def load():
@@ -237,6 +240,17 @@ def restrict_smooth(op, level, prec, rho, r_fine, f_c, u_c, n_fine, n_coarse, st
     _check(load().tpmg_restrict_smooth(op, level, prec, rho, _field(r_fine, prec, n_fine, "r_fine"),
                                        _field(f_c, prec, n_coarse, "f_c"), _field(u_c, prec, n_coarse, "u_c"),
                                        _stream(stream)), "restrict_smooth")
+
+
+def residual_restrict_smooth(op, level, prec, rho, u_fine, f_fine, f_c, u_c, n_fine, n_coarse, stream=None):
+    _check(load().tpmg_residual_restrict_smooth(op, level, prec, rho, _field(u_fine, prec, n_fine, "u_fine"),
+                                                _field(f_fine, prec, n_fine, "f_fine"),
+                                                _field(f_c, prec, n_coarse, "f_c"), _field(u_c, prec, n_coarse, "u_c"),
+                                                _stream(stream)), "residual_restrict_smooth")
+
+
+def set_fusion(op, enable) -> None:
+    _check(load().tpmg_set_fusion(op, 1 if enable else 0), "set_fusion")
 
 
 def prolongate(op, level, prec, u_c, u_f, n_coarse, n_fine, stream=None):

@@ -71,3 +71,20 @@ def test_default_params_layout_without_gpu():
                                                                                            0, 0)
     with pytest.raises(TypeError):
         tpmg.default_params(zero_gues=1)
+
+
+def test_solve_memory_reference_model():
+    """The whole-solve byte model bench.py reports: per V(2,2) cycle and fine cell
+    17.25 + 20.25 * sum_{j=1}^{L-2} 4^-j + 9 * 4^-(L-1) memory references of the paper's kernels
+    (about 23.7 for four levels, 24.0 for seven), plus one Smooth (3) per solve."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_model", os.path.join(os.path.dirname(__file__), "..", "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    for L, nx, nz in [(4, 64, 64), (7, 512, 128)]:
+        cells = [0] + [(nx >> (L - l)) ** 2 * nz for l in range(1, L + 1)]
+        closed = 17.25 + 20.25 * sum(4.0 ** -j for j in range(1, L - 1)) + 9 * 4.0 ** -(L - 1)
+        for iters in (1, 6):
+            got = bench.solve_memrefs(cells, iters) / cells[L]
+            assert abs(got - (3 + iters * closed)) < 1e-12
+    assert abs(closed - 23.9956) < 1e-4
