@@ -152,6 +152,85 @@ def cpu_baseline_sample(p, f, iters_hint):
     return est_ms, {"t_cycle_s": round(t_cycle, 3), "t_residual_s": round(t_res, 3), "oracle_iters": iters}
 
 
+def _oracle_replica(p, barrier, out):
+    """One replica of the oracle sample in its own (spawned) process: the same residual and V-cycle
+    on its own copy of the inputs, timed after every replica has its inputs ready."""
+    import oracle
+    f = p.rhs()
+    cx, cy, v = oracle.problem_coefficients(p)
+    u = np.zeros_like(f)
+    barrier.wait(timeout=600)
+    t0 = time.perf_counter()
+    oracle.residual(u, f, cx, cy, v)
+    t1 = time.perf_counter()
+    oracle.vcycle(u, f, cx, cy, v, p.nlevels)
+    out.put((t1 - t0, time.perf_counter() - t1))
+
+
+def host_memory_bytes() -> int:
+    """Memory this process may still use: MemAvailable, capped by a cgroup limit if one is set."""
+    avail = 0
+    with open("/proc/meminfo") as fh:
+        for line in fh:
+            if line.startswith("MemAvailable:"):
+                avail = int(line.split()[1]) * 1024
+    for path in ("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory/memory.limit_in_bytes"):
+        try:
+            raw = open(path).read().strip()
+        except OSError:
+            continue
+        if raw.isdigit():
+            used = 0
+            for upath in ("/sys/fs/cgroup/memory.current", "/sys/fs/cgroup/memory/memory.usage_in_bytes"):
+                try:
+                    used = int(open(upath).read().strip())
+                    break
+                except (OSError, ValueError):
+                    pass
+            avail = min(avail, int(raw) - used)
+    return avail
+
+
+def cpu_baseline_all_cores(p, iters: int, bytes_per_replica: int):
+    """The oracle on every host core at once: one replica of the single-core sample per core (as many
+    as host memory allows at bytes_per_replica each), spawned processes, started together. Returns
+    the per-solve time of the whole host (the slowest replica's solve estimate / replicas) and the
+    details, or None when fewer than two replicas fit."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    fit = int(0.5 * host_memory_bytes() // bytes_per_replica)
+    n = min(cores, fit)
+    if n < 2:
+        return None
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(n)
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_replica, args=(p, barrier, out)) for _ in range(n)]
+    for pr in procs:
+        pr.start()
+    res = []
+    deadline = time.time() + 1200
+    import queue
+    while len(res) < n:
+        try:
+            res.append(out.get(timeout=2))
+        except queue.Empty:
+            # a replica that died (or a run past the deadline) ends the measurement
+            if time.time() > deadline or any(pr.exitcode not in (None, 0) for pr in procs):
+                for pr in procs:
+                    if pr.is_alive():
+                        pr.terminate()
+                return None
+    for pr in procs:
+        pr.join(timeout=60)
+    est = max(1e3 * (tr + iters * (tc + tr)) for tr, tc in res)
+    return {"value": round(est / n, 3), "unit": "ms", "cores": n, "replicas": n,
+            "slowest_replica_solve_ms": round(est, 3),
+            "t_cycle_s_max": round(max(tc for _, tc in res), 3),
+            "sample": (f"{n} concurrent replicas of the single-core sample (one process per core), "
+                       f"slowest replica's solve estimate divided by {n}")}
+
+
 def bench_batched(tpmg, torch):
     probs = workloads.batched()
     ops = [tpmg.Operator.from_problem(p) for p in probs]
@@ -576,6 +655,10 @@ def run_ours(args, rank, world, dist):
         cpu = {"value": round(est, 3), "unit": "ms", "cores": 1, "kind": "oracle",
                "sample": (f"one oracle V(2,2) cycle + one residual on the full {p.nx}x{p.ny}x{p.nz} grid, "
                           f"scaled to a full solve with the oracle's iteration count"), **info}
+        # the same sample on all host cores at once (replicas; peak about 10 FP64 fields each)
+        allc = cpu_baseline_all_cores(p, info["oracle_iters"], 10 * 8 * p.n)
+        if allc is not None:
+            cpu["all_cores"] = allc
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
