@@ -127,8 +127,9 @@ tpmg_status tpmg_residual_restrict_smooth(tpmg_op* op, int level, tpmg_precision
                                           const void* u_fine, const void* f_fine, void* f_c, void* u_c,
                                           void* stream);
 /* enable != 0 (the default): V-cycles of this operator fuse Residual and RestrictSmooth wherever
- * tpmg_residual_restrict_smooth's fused kernel applies; 0: separate kernels. Invalidates the
- * operator's cached CUDA graphs. */
+ * tpmg_residual_restrict_smooth's fused kernel applies (in tpmg_mg_solve_batched: wherever the
+ * fine level takes its two-column tiles); 0: separate kernels. Same results bit for bit either way.
+ * Invalidates the operator's cached CUDA graphs and batched-solve tables. */
 tpmg_status tpmg_set_fusion(tpmg_op* op, int enable);
 /* u_f += P u_c on fine level `level` (> 1), P the cell-centred bilinear interpolation from level-1
  * (kernel "Prolongate", Sec. 2.2). */

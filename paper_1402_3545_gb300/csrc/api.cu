@@ -971,6 +971,7 @@ tpmg_status tpmg_set_fusion(tpmg_op* op, int enable) {
     if (op->fuse_restrict != on) {
         op->fuse_restrict = on;
         invalidate_graphs(op);
+        drop_batches_of(op);  // their task lists follow the switch
     }
     return TPMG_OK;
 }
@@ -1407,8 +1408,8 @@ static void cycle_tasks(tpmg_op* op, int b, const tpmg_params* prm, std::vector<
         t.out2 = o2;
         const int nxl = op->g.lnx[level];
         const int nyl = op->g.lny[level];
-        t.x2 = (type == BT_SMOOTH || type == BT_RESID || type == BT_LS0) &&
-               batched_x2_fits(nxl, nyl, a ? a : rhs, rhs, o);
+        t.x2 = (type == BT_SMOOTH || type == BT_RESID || type == BT_LS0 || type == BT_RRS) &&
+               batched_x2_fits(nxl, nyl, a ? a : rhs, rhs, type == BT_RRS ? a : o);
         t.tiles_x = t.x2 ? nxl / 64 : (nxl + 31) / 32;
         t.tiles_y = (nyl + BTY - 1) / BTY;
         t.tile_base = 0;
@@ -1425,18 +1426,30 @@ static void cycle_tasks(tpmg_op* op, int b, const tpmg_params* prm, std::vector<
         for (int s = 1; s < prm->n_coarse; ++s) smooth(L, cur, oth, h.f[L]);
     } else {
         for (int s = 1; s < prm->nu_pre; ++s) smooth(L, cur, oth, h.f[L]);
-        task(BT_RESID, L, cur, h.f[L], h.r[L], nullptr);
         std::vector<void*> lcur(L + 1), loth(L + 1);
-        // descend
-        for (int l = L - 1; l >= 1; --l) {
+        for (int l = 1; l < L; ++l) {
             lcur[l] = h.u[l];
             loth[l] = h.ub[l];
-            task(BT_RS, l, h.r[l + 1], nullptr, h.f[l], lcur[l]);
+        }
+        // Residual of level l, then RestrictSmooth onto l-1: one fused task where level l takes
+        // two-column tiles (the same arithmetic), else the two tasks; returns whether it fused
+        auto residual_restrict = [&](int l, const void* u_l) {
+            if (op->fuse_restrict && batched_x2_fits(op->g.lnx[l], op->g.lny[l], u_l, h.f[l], u_l)) {
+                task(BT_RRS, l, u_l, h.f[l], h.f[l - 1], lcur[l - 1]);
+                return true;
+            }
+            task(BT_RESID, l, u_l, h.f[l], h.r[l], nullptr);
+            return false;
+        };
+        bool restricted = residual_restrict(L, cur);
+        // descend
+        for (int l = L - 1; l >= 1; --l) {
+            if (!restricted) task(BT_RS, l, h.r[l + 1], nullptr, h.f[l], lcur[l]);
             if (l == 1) {
                 for (int s = 1; s < prm->n_coarse; ++s) smooth(l, lcur[l], loth[l], h.f[l]);
             } else {
                 for (int s = 1; s < prm->nu_pre; ++s) smooth(l, lcur[l], loth[l], h.f[l]);
-                task(BT_RESID, l, lcur[l], h.f[l], h.r[l], nullptr);
+                restricted = residual_restrict(l, lcur[l]);
             }
         }
         // ascend

@@ -347,7 +347,9 @@ size_t batched_smem_bytes() {
     size_t m = sweep_x2_smem<PolDW, BTY, BPD, MODE_RESIDUAL>();
     const size_t s1 = sweep_x2_smem<PolF32, BTY, BPD, MODE_SMOOTH>();
     const size_t s2 = sweep_x2_smem<PolF32, BTY, BPD, MODE_LINESOLVE>();
+    const size_t s3 = sweep_x2_smem<PolF32, BTY, BPD, MODE_RESTRICT>();
     m = s1 > m ? s1 : m;
+    m = s3 > m ? s3 : m;
     return s2 > m ? s2 : m;
 }
 
@@ -412,6 +414,14 @@ __global__ void __launch_bounds__(32 * BTY, 4) k_batched(BatchDesc d) {
                                 lv32(pb.lev[tk.level]), 1.0, (const float*)tk.a, (const float*)tk.b, (float*)tk.out,
                                 false, loc, loc + 1, 1, nullptr, bsmem);
                             break;
+                        case BT_RRS: {
+                            const XRestrict<PolF32> xr{lv32(pb.lev[tk.level - 1]), d.rho, (float*)tk.out,
+                                                       (float*)tk.out2};
+                            sweep_x2_tiles<PolF32, PolF32, BTY, BPD, MODE_RESTRICT, 0>(
+                                lv32(pb.lev[tk.level]), 1.0, (const float*)tk.a, (const float*)tk.b, nullptr, false,
+                                loc, loc + 1, 1, stack, bsmem, &xr);
+                            break;
+                        }
                         default:
                             break;
                     }

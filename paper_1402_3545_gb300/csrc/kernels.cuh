@@ -289,7 +289,10 @@ void launch_cg_finish(size_t n, const Scalars* sc, typename P::S* u, const typen
 // refinement together, inside one cooperative persistent launch: the work of each step of the
 // cycle ("phase") is cut into tiles of 32 x BTY columns over all problems; a bounded grid barrier
 // separates the phases. Per-problem state decides which problems are still active.
-enum { BT_OUTRES = 0, BT_FINAL = 1, BT_LS0 = 2, BT_SMOOTH = 3, BT_RESID = 4, BT_RS = 5, BT_PROL = 6, BT_CORR = 7 };
+// BT_RRS: Residual of level `level` and RestrictSmooth onto level-1 in one two-column sweep
+// (a = u, b = f of the fine level, out = f_c, out2 = u_c), where the fine level takes 64 x BTY tiles
+enum { BT_OUTRES = 0, BT_FINAL = 1, BT_LS0 = 2, BT_SMOOTH = 3, BT_RESID = 4, BT_RS = 5, BT_PROL = 6, BT_CORR = 7,
+       BT_RRS = 8 };
 static constexpr int BTY = 4;  // rows of columns per tile (block = 32 x BTY threads)
 static constexpr int BMAXL = 16;
 
@@ -319,7 +322,7 @@ struct BTask {
     void* out;
     void* out2;
     int tiles_x, tiles_y, tile_base;
-    int x2;  // 1: tiles of 64 x BTY columns run by the two-column sweep (Smooth, Residual, line solve)
+    int x2;  // 1: tiles of 64 x BTY columns run by the two-column sweep (Smooth, Residual, line solve, RRS)
 };
 struct BState {
     double r0, rel;

@@ -82,7 +82,8 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
     constexpr bool STACK = x2_stack(MODE);
     constexpr bool HALO = MODE != MODE_LINESOLVE;
     constexpr bool RESTR = MODE == MODE_RESTRICT;
-    static_assert(!RESTR || TY == 2, "the fused restriction pairs the block's two rows");
+    static_assert(!RESTR || TY % 2 == 0, "the fused restriction pairs the block's rows");
+    constexpr int CR = TY / 2;  // RESTR: coarse rows per tile
     constexpr bool GFORM = MODE == MODE_SMOOTH && P::id == 1;  // as in k_sweep_pp
     constexpr int UPL = HALO ? (TY + 2) * UW : 0;
     constexpr int FPL = 2 * NT;
@@ -94,10 +95,14 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
     S* ringU = reinterpret_cast<S*>(smem_raw);
     S* ringF = ringU + PD * UPL;
     S* ringI = ringF + PD * FPL;
-    S* ringIc = ringI + PD * IPL;  // RESTR: 1/m_k of the coarse columns, 32 per plane
-    S* xs = ringIc + (RESTR ? PD * 32 : 0);  // RESTR: row pair sums of the odd row, 2 planes
+    S* ringIc = ringI + PD * IPL;  // RESTR: 1/m_k of the coarse columns, 32 CR per plane
+    S* xs = ringIc + (RESTR ? PD * 32 * CR : 0);  // RESTR: row pair sums of the odd rows, 2 planes
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    // RESTR: rows 2q and 2q+1 of a tile are the children of coarse row q; the even row's thread
+    // owns coarse column ci of the tile
+    const int cr = ty >> 1, ci = cr * 32 + tx;
+    const bool even = (ty & 1) == 0;
     const size_t pl = (size_t)nx * ny;
     const int tiles_x = nx / 64;
     const S* rhs = (MODE == MODE_LINESOLVE) ? u : f;
@@ -114,9 +119,9 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
     for (int tile = tile0; tile < tile_end; tile += tile_step) {
         const int i0 = (tile % tiles_x) * 64, j0 = (tile / tiles_x) * TY;
         const size_t c = (size_t)(j0 + ty) * nx + (i0 + 2 * tx);  // the thread's first column
-        // RESTR: the coarse column over this thread's pair and the pair of the next row
+        // RESTR: the coarse column over this thread's pair and the pair of the row pair's other row
         const size_t plc = pl / 4;
-        const size_t cc = (size_t)(j0 / 2) * (nx / 2) + (i0 / 2 + tx);
+        const size_t cc = (size_t)(j0 / 2 + cr) * (nx / 2) + (i0 / 2 + tx);
         __syncthreads();  // the previous tile's rings are no longer read
 
         // halo of the u plane: 2 rows x 32 pairs (one pair per thread when TY = 2) and 2 TY side
@@ -155,8 +160,8 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
                 }
                 if constexpr (RESTR) {
                     const int kc0 = xr->Lc.fac_k0;
-                    if (ty == 0 && xr->Lc.fac_percol && !(k >= kc0 && k <= nz - 2))
-                        cp_async<sizeof(S)>(&ringIc[slot * 32 + tx], xr->Lc.finv + (size_t)k * plc + cc);
+                    if (even && xr->Lc.fac_percol && !(k >= kc0 && k <= nz - 2))
+                        cp_async<sizeof(S)>(&ringIc[slot * 32 * CR + ci], xr->Lc.finv + (size_t)k * plc + cc);
                 }
                 if (HALO) {
                     cp_async<PB>(&Us[(ty + 1) * UW + 2 + 2 * tx], u + b + c);
@@ -188,7 +193,7 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
         // RESTR: coupling and converged factors of the coarse column, its forward-eliminated value
         R vcc = vzero, cic = vzero, cwc = vzero, dpc = vzero, qv = vzero;
         if constexpr (RESTR) {
-            if (ty == 0) {
+            if (even) {
                 vcc = P::ld(xr->Lc.v, cc);
                 if (xr->Lc.fac_percol && xr->Lc.fac_k0 <= nz - 2) {
                     cic = P::ld(xr->Lc.finv, (size_t)(nz - 2) * plc + cc);
@@ -237,7 +242,7 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
                 uc1 = up1;
                 if constexpr (RESTR) {
                     qv = P::add(r0, r1);  // the row pair's sum; the odd row hands it over
-                    if (ty == 1) P::st(xs, (k & 1) * 32 + tx, qv);
+                    if (!even) P::st(xs, (k & 1) * 32 * CR + ci, qv);
                 }
             }
             if constexpr (MODE == MODE_RESIDUAL) {
@@ -285,19 +290,19 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
             }
             if (HALO) __syncthreads();  // the slot is reused by the next issue
             if constexpr (RESTR) {
-                if (ty == 0) {
+                if (even) {
                     // f_c = 1/4 (even row pair + odd row pair), then the coarse forward elimination
-                    const R fk = P::mul(P::cst(0.25), P::add(qv, P::ld_plain(xs, (k & 1) * 32 + tx)));
+                    const R fk = P::mul(P::cst(0.25), P::add(qv, P::ld_plain(xs, (k & 1) * 32 * CR + ci)));
                     P::st(xr->fc, (size_t)k * plc + cc, fk);
                     R ic;
                     if (xr->Lc.fac_percol && k >= xr->Lc.fac_k0 && k <= nz - 2)
                         ic = cic;
                     else if (xr->Lc.fac_percol)
-                        ic = P::ld_plain(ringIc, slot * 32 + tx);
+                        ic = P::ld_plain(ringIc, slot * 32 * CR + ci);
                     else
                         ic = P::ld(xr->Lc.finv, k);
                     dpc = P::mul(P::fma(vcc, dpc, fk), ic);
-                    P::sts(gstack, (size_t)k * 32 + tx, dpc);
+                    P::sts(gstack, (size_t)k * 32 * CR + ci, dpc);
                 }
             }
             issue_plane(k + PD, slot);
@@ -375,18 +380,18 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
             cp_wait<0>();
         }
         if constexpr (RESTR) {
-            // coarse back substitution by the even row: u_c = rho x, x_k = d'_k + (v/m_k) x_{k+1}
+            // coarse back substitution by the even rows: u_c = rho x, x_k = d'_k + (v/m_k) x_{k+1}
             __syncthreads();  // the backward ring reuses the forward ring's shared memory
-            if (ty == 0) {
+            if (even) {
                 S* bW = reinterpret_cast<S*>(smem_raw);
-                S* bD = bW + PD * 32;
+                S* bD = bW + PD * 32 * CR;
                 const bool pcc = xr->Lc.fac_percol != 0;
                 const int kc0 = xr->Lc.fac_k0;
                 auto issue_back = [&](int k, int s2) {
                     if (k >= 0) {
                         if (pcc && !(k >= kc0 && k <= nz - 2))
-                            cp_async<sizeof(S)>(&bW[s2 * 32 + tx], xr->Lc.fw + (size_t)k * plc + cc);
-                        cp_async<sizeof(S)>(&bD[s2 * 32 + tx], gstack + (size_t)k * 32 + tx);
+                            cp_async<sizeof(S)>(&bW[s2 * 32 * CR + ci], xr->Lc.fw + (size_t)k * plc + cc);
+                        cp_async<sizeof(S)>(&bD[s2 * 32 * CR + ci], gstack + (size_t)k * 32 * CR + ci);
                     }
                     cp_commit();
                 };
@@ -400,10 +405,10 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
                     if (pcc && k >= kc0 && k <= nz - 2)
                         w = cwc;
                     else if (pcc)
-                        w = P::ld_plain(bW, slot * 32 + tx);
+                        w = P::ld_plain(bW, slot * 32 * CR + ci);
                     else
                         w = P::ld(xr->Lc.fw, k);
-                    xn = P::fma(w, xn, P::ld_plain(bD, slot * 32 + tx));
+                    xn = P::fma(w, xn, P::ld_plain(bD, slot * 32 * CR + ci));
                     P::st(xr->uc, (size_t)k * plc + cc, P::mul(rho, xn));
                     issue_back(k - PD, slot);
                     slot = (slot + 1 == PD) ? 0 : slot + 1;
@@ -421,9 +426,10 @@ constexpr size_t sweep_x2_smem() {
     constexpr bool STACK = x2_stack(MODE);
     constexpr bool HALO = MODE != MODE_LINESOLVE;
     constexpr size_t fwd = ((size_t)PD * ((HALO ? (TY + 2) * 68 : 0) + 2 * 32 * TY + (STACK ? 2 * 32 * TY : 0)) +
-                            (MODE == MODE_RESTRICT ? (size_t)PD * 32 + 2 * 32 : 0)) *
+                            (MODE == MODE_RESTRICT ? (size_t)(PD + 2) * 32 * (TY / 2) : 0)) *
                            sizeof(typename P::S);
-    constexpr size_t back = STACK ? (size_t)PD * 3 * 2 * 32 * TY * sizeof(typename P::S) : 0;
+    constexpr size_t back = STACK ? (size_t)PD * 3 * 2 * 32 * TY * sizeof(typename P::S)
+                                  : (MODE == MODE_RESTRICT ? (size_t)PD * 2 * 32 * (TY / 2) * sizeof(typename P::S) : 0);
     return fwd > back ? fwd : back;
 }
 

@@ -132,3 +132,26 @@ def test_batched_zero_guess_ignores_u():
         assert torch.equal(u, u2)
     for o in ops:
         o.close()
+
+
+def test_batched_fused_residual_restrict_equals_separate_tasks():
+    """The batched cycle's fused Residual + RestrictSmooth tasks (levels 64 columns wide and more)
+    give bit for bit the solve with separate Residual and RestrictSmooth tasks."""
+    rng = np.random.default_rng(21)
+    probs = []
+    for b, (nx, ny, nz) in enumerate([(64, 64, 16), (128, 64, 32), (64, 32, 8), (32, 64, 16)]):
+        lam2 = float(10 ** rng.uniform(2, 4))
+        h = 1.0 / max(nx, ny)
+        probs.append(workloads.Problem(f"f{b}", nx, ny, nz, 1e-2, h, h, 1.0 / nz, lam2,
+                                       workloads.levels_to_8(nx, ny), 2000 + b, "uniform"))
+    ops, fs, us, res = run_batch(probs, tol=1e-8, max_iter=60)
+    for o in ops:
+        tpmg.set_fusion(o.op, False)
+    us2 = [torch.zeros_like(f) for f in fs]
+    res2 = tpmg.mg_solve_batched([o.op for o in ops], tpmg.default_params(prec=tpmg.MIXED, tol=1e-8, max_iter=60),
+                                 fs, us2)
+    for a, b, u, u2 in zip(res["problems"], res2["problems"], us, us2):
+        assert a["converged"] and a["iters"] == b["iters"] and a["history"] == b["history"]
+        assert torch.equal(u, u2)
+    for o in ops:
+        o.close()
