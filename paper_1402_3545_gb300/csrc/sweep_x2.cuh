@@ -101,8 +101,8 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     // RESTR: rows 2q and 2q+1 of a tile are the children of coarse row q; the even row's thread
     // owns coarse column ci of the tile
-    const int cr = ty >> 1, ci = cr * 32 + tx;
-    const bool even = (ty & 1) == 0;
+    const int cr = TY == 2 ? 0 : ty >> 1, ci = cr * 32 + tx;  // (threadIdx.y < TY: constant when TY = 2)
+    const bool even = TY == 2 ? ty == 0 : (ty & 1) == 0;
     const size_t pl = (size_t)nx * ny;
     const int tiles_x = nx / 64;
     const S* rhs = (MODE == MODE_LINESOLVE) ? u : f;
