@@ -73,7 +73,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     """Compile every csrc/*.cu for sm_103a and link libtpmg.so; returns the library path."""
     os.makedirs(BUILD, exist_ok=True)
     stamp = os.path.join(BUILD, "host.stamp")
-    # objects built on another host architecture (x86 here, aarch64 on the GPU box) are stale
+    # objects built on another host architecture (e.g. x86-64 vs aarch64) are stale
     if not os.path.exists(stamp) or open(stamp).read() != _host_stamp():
         force = True
         with open(stamp, "w") as fh:
