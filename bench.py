@@ -50,7 +50,8 @@ def parse_args():
                     help="time the solves only (no kernel timing, e2e, variants or CPU baseline): "
                          "the command the ncu launch-list profile runs")
     ap.add_argument("--kernel-only", choices=["smooth", "residual", "restrict_smooth", "residual_restrict",
-                                              "prolongate", "line_solve", "cg_spmv", "cg_tridiag", "nn_forward"],
+                                              "prolongate", "line_solve", "apply_A", "cg_spmv", "cg_tridiag",
+                                              "nn_forward"],
                     help="launch only this finest-level kernel a few times (tile variant --variant, "
                          "no autotuning): the command a per-kernel ncu capture runs")
     ap.add_argument("--variant", type=int, default=3)
@@ -472,7 +473,8 @@ def run_kernel_only(args):
     prec = {"dw": tpmg.DW, "f32": tpmg.F32, "f64": tpmg.F64}[args.precision]
     kid = {"smooth": tpmg.K_SMOOTH, "residual": tpmg.K_RESIDUAL, "restrict_smooth": tpmg.K_RESTRICT_SMOOTH,
            "prolongate": tpmg.K_PROLONGATE, "line_solve": tpmg.K_LINE_SOLVE, "cg_spmv": tpmg.K_CG_SPMV,
-           "cg_tridiag": tpmg.K_CG_TRIDIAG, "residual_restrict": tpmg.K_RESIDUAL_RESTRICT}[args.kernel_only]
+           "cg_tridiag": tpmg.K_CG_TRIDIAG, "residual_restrict": tpmg.K_RESIDUAL_RESTRICT,
+           "apply_A": tpmg.K_APPLY_A}[args.kernel_only]
     p = workloads.mid()
     op = tpmg.Operator.from_problem(p)
     tpmg.op_reserve(op.op, tpmg.MIXED if prec == tpmg.F32 else prec)
@@ -551,7 +553,7 @@ def run_ours(args, rank, world, dist):
     finest_variant = variants_dw[-1] if variants_dw else None
     kernel_ms = {name: round(tpmg.time_kernel(op.op, prec, kid, reps=10), 4) for name, kid in [
         ("residual", tpmg.K_RESIDUAL), ("restrict_smooth", tpmg.K_RESTRICT_SMOOTH),
-        ("residual_restrict_fused", tpmg.K_RESIDUAL_RESTRICT),
+        ("residual_restrict_fused", tpmg.K_RESIDUAL_RESTRICT), ("apply_A", tpmg.K_APPLY_A),
         ("prolongate", tpmg.K_PROLONGATE), ("cg_spmv", tpmg.K_CG_SPMV), ("cg_tridiag", tpmg.K_CG_TRIDIAG)]}
     kernel_ms["smooth"] = round(t_smooth, 4)
     tpmg.op_reserve(op.op, tpmg.MIXED)

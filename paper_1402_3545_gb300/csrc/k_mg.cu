@@ -356,6 +356,7 @@ static void allow_smem(K kernel, size_t bytes) {
 
 template <class P>
 void launch_apply_A(const Lv<P>& L, const typename P::S* x, typename P::S* y, cudaStream_t s) {
+    if (launch_apply_A_x2<P>(L, x, y, s) >= 0) return;
     Shape sh = sweep_shape(L.nx, L.ny, L.nz, sizeof(typename P::R), false);
     k_apply_A<P><<<sh.grid, sh.block, 0, s>>>(L, x, y);
     note_launch();

@@ -370,7 +370,8 @@ static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, con
     constexpr bool HALO = MODE != MODE_LINESOLVE;
     if (L.nx % 64 || L.ny % TY || (STACK && (!L.gstack || !L.finv || !L.fw))) return -1;
     auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
-    if (!al(u) || (HALO && !al(f)) || !al(out) || (STACK && (!al(L.finv) || !al(L.fw)))) return -1;
+    if (!al(u) || (HALO && MODE != MODE_APPLY && !al(f)) || !al(out) || (STACK && (!al(L.finv) || !al(L.fw))))
+        return -1;
     const size_t smem = sweep_x2_smem<P, TY, PD, MODE>();
     auto kern = k_sweep_x2<P, PO, TY, PD, MODE, MINB, HINT>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -516,6 +517,11 @@ int launch_residual_pp(const Lv<P>& L, const typename P::S* u, const typename P:
     if (nb >= 0) return nb;
     if (!pp_fits<P, 4, false>(L)) return -1;
     return run_sweep_pp<P, PO, 4, 6, MODE_RESIDUAL>(L, 1.0, u, f, r, partials, done, s);
+}
+
+template <class P>
+int launch_apply_A_x2(const Lv<P>& L, const typename P::S* x, typename P::S* y, cudaStream_t s) {
+    return run_sweep_x2<P, P, 2, 4, MODE_APPLY>(L, 1.0, x, nullptr, y, nullptr, nullptr, s, 16);
 }
 
 template <class P>
@@ -675,6 +681,7 @@ int launch_restrict_smooth_pp(const Lv<P>& Lc, double rho, const typename PF::S*
     template int launch_residual_pp<P, P>(const Lv<P>&, const P::S*, const P::S*, P::S*, double*, const int*,  \
                                           cudaStream_t);                                                     \
     template int launch_line_solve_pp<P>(const Lv<P>&, const P::S*, P::S*, double, const int*, cudaStream_t); \
+    template int launch_apply_A_x2<P>(const Lv<P>&, const P::S*, P::S*, cudaStream_t);                        \
     template int launch_restrict_smooth_pp<P, P>(const Lv<P>&, double, const P::S*, P::S*, P::S*, const int*, \
                                                  cudaStream_t);                                                \
     template int launch_residual_restrict<P>(const Lv<P>&, const Lv<P>&, double, const P::S*, const P::S*, P::S*, \

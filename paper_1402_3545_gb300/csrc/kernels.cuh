@@ -197,6 +197,9 @@ int launch_residual_pp(const Lv<P>& L, const typename P::S* u, const typename P:
 template <class P>
 int launch_line_solve_pp(const Lv<P>& L, const typename P::S* b, typename P::S* x, double scale, const int* done,
                          cudaStream_t s);
+// y = A x by the two-column sweep (nx % 64 == 0, 16-byte aligned fields), else -1
+template <class P>
+int launch_apply_A_x2(const Lv<P>& L, const typename P::S* x, typename P::S* y, cudaStream_t s);
 template <class PF, class P>
 int launch_restrict_smooth_pp(const Lv<P>& Lc, double rho, const typename PF::S* rf, typename P::S* fc,
                               typename P::S* uc, const int* done, cudaStream_t s);

@@ -31,11 +31,12 @@ __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
-enum { MODE_SMOOTH = 0, MODE_RESIDUAL = 1, MODE_LINESOLVE = 2, MODE_RESTRICT = 3 };
+// MODE_APPLY: out = A u (f unused), formed as -(0 - A u) by the residual's stencil: negation is exact
+enum { MODE_SMOOTH = 0, MODE_RESIDUAL = 1, MODE_LINESOLVE = 2, MODE_RESTRICT = 3, MODE_APPLY = 4 };
 // modes whose per-column Thomas stack lives in the block's scratch slot (MODE_RESTRICT keeps the
 // stack of the coarse column there)
 __host__ __device__ constexpr bool x2_stack(int mode) { return mode == MODE_SMOOTH || mode == MODE_LINESOLVE; }
-__host__ __device__ constexpr bool x2_slot(int mode) { return mode != MODE_RESIDUAL; }
+__host__ __device__ constexpr bool x2_slot(int mode) { return mode != MODE_RESIDUAL && mode != MODE_APPLY; }
 
 // MODE_RESTRICT: the fine level's residual r = f - A u is not stored; each 2 x 2 group of fine
 // columns is restricted on the fly to the coarse right-hand side f_c = 1/4 (sum of the children)
@@ -152,10 +153,10 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
                 S* Us = ringU + slot * UPL;
                 const bool fac = STACK && percol && !(k >= k0 && k <= nz - 2);  // factors of plane k needed
                 if constexpr ((HINT & HINT_STREAM) != 0) {
-                    cp_async_pol<PB>(&ringF[slot * FPL + 2 * tid], rhs + b + c, pol_first);
+                    if (MODE != MODE_APPLY) cp_async_pol<PB>(&ringF[slot * FPL + 2 * tid], rhs + b + c, pol_first);
                     if (fac) cp_async_pol<PB>(&ringI[slot * FPL + 2 * tid], L.finv + b + c, pol_first);
                 } else {
-                    cp_async<PB>(&ringF[slot * FPL + 2 * tid], rhs + b + c);
+                    if (MODE != MODE_APPLY) cp_async<PB>(&ringF[slot * FPL + 2 * tid], rhs + b + c);
                     if (fac) cp_async<PB>(&ringI[slot * FPL + 2 * tid], L.finv + b + c);
                 }
                 if constexpr (RESTR) {
@@ -228,9 +229,11 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
                 const R n0 = P::ld_plain(Us, ctr + UW), n1 = P::ld_plain(Us, ctr + UW + 1);
                 const bool end = nz == 1 || k == 0 || k == nz - 1;
                 const R dga = nz == 1 ? dh : (end ? dh1a : dh2a), dgb = nz == 1 ? dh : (end ? dh1b : dh2b);
-                r0 = sweep_residual<P>(P::ld_plain(ringF, slot * FPL + 2 * tid), dga, uc0, wv, uc1, s0, n0, um0, up0,
+                const R f0 = MODE == MODE_APPLY ? vzero : P::ld_plain(ringF, slot * FPL + 2 * tid);
+                const R f1 = MODE == MODE_APPLY ? vzero : P::ld_plain(ringF, slot * FPL + 2 * tid + 1);
+                r0 = sweep_residual<P>(f0, dga, uc0, wv, uc1, s0, n0, um0, up0,
                                        cx, cy, v0, iso);
-                r1 = sweep_residual<P>(P::ld_plain(ringF, slot * FPL + 2 * tid + 1), dgb, uc1, uc0, ev, s1, n1, um1,
+                r1 = sweep_residual<P>(f1, dgb, uc1, uc0, ev, s1, n1, um1,
                                        up1, cx, cy, v1, iso);
                 if (want_norm) {
                     P::acc_dot(acc, cmp, r0, r0);
@@ -244,6 +247,11 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
                     qv = P::add(r0, r1);  // the row pair's sum; the odd row hands it over
                     if (!even) P::st(xs, (k & 1) * 32 * CR + ci, qv);
                 }
+            }
+            if constexpr (MODE == MODE_APPLY) {
+                const size_t id = (size_t)k * pl + c;
+                P::st(out, id, P::neg(r0));
+                P::st(out, id + 1, P::neg(r1));
             }
             if constexpr (MODE == MODE_RESIDUAL) {
                 const size_t id = (size_t)k * pl + c;
