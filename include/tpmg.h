@@ -65,6 +65,21 @@ typedef enum {
 typedef struct tpmg_grid tpmg_grid; /* opaque, library owned */
 typedef struct tpmg_op tpmg_op;     /* opaque, library owned */
 
+/* Device memory. The library allocates its own buffers (hierarchy, workspace, scratch, tables)
+ * with cudaMalloc when an operator, solve or network first needs them, and frees them in the
+ * matching destroy call. tpmg_set_allocator installs a caller's allocator instead (for instance a
+ * framework's caching allocator, so that one pool serves everything): alloc_fn(bytes, ctx) returns
+ * device memory of at least `bytes` bytes, aligned to 256 bytes, usable on the streams the caller
+ * passes to this library, or NULL (the call that needed it fails with TPMG_ERR_OOM); free_fn(ptr,
+ * ctx) takes a block back; the library synchronises the device before it returns a block. Both
+ * functions NULL restores cudaMalloc / cudaFree; one NULL is TPMG_ERR_ARG. Process-wide: the
+ * functions installed when a buffer is allocated are the ones it is returned to, whatever is
+ * installed later; each call into the library that allocates must not overlap a
+ * tpmg_set_allocator call. */
+typedef void* (*tpmg_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*tpmg_free_fn)(void* ptr, void* ctx);
+tpmg_status tpmg_set_allocator(tpmg_alloc_fn alloc_fn, tpmg_free_fn free_fn, void* ctx);
+
 /* Grid of nx x ny x nz cells with `nlevels` multigrid levels (0 = halve nx and ny while both stay
  * even and the larger one exceeds 8: 8 x 8 for square grids; on elongated grids the short side may
  * reach 1, which keeps the coarsest level well conditioned). nx and ny must be divisible by

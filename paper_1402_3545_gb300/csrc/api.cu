@@ -10,7 +10,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "kernels.cuh"
@@ -134,19 +136,71 @@ static Lv<P> level_view(const tpmg_op* op, int l) {
     return L;
 }
 
+// Every device buffer of the library comes from dalloc: cudaMalloc, or the caller's allocator while
+// one is installed (tpmg_set_allocator); dev_free returns a buffer to the allocator that made it.
+struct AllocFns {
+    tpmg_alloc_fn alloc = nullptr;
+    tpmg_free_fn free = nullptr;
+    void* ctx = nullptr;
+};
+static std::mutex g_alloc_mu;
+static AllocFns g_alloc;
+static std::unordered_map<void*, AllocFns>& caller_blocks() {
+    static std::unordered_map<void*, AllocFns> m;
+    return m;
+}
+
 static tpmg_status dalloc(void** p, size_t bytes) {
     if (*p) return TPMG_OK;
-    cudaError_t e = cudaMalloc(p, bytes < 256 ? 256 : bytes);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        cudaGetLastError();
-        return set_err(TPMG_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    const size_t sz = bytes < 256 ? 256 : bytes;
+    AllocFns fns;
+    {
+        std::lock_guard<std::mutex> g(g_alloc_mu);
+        fns = g_alloc;
     }
-    cudaMemset(*p, 0, bytes < 256 ? 256 : bytes);  // defined contents for profiling runs
+    if (fns.alloc) {
+        void* q = fns.alloc(sz, fns.ctx);
+        if (!q) return set_err(TPMG_ERR_OOM, "the caller's allocator returned NULL");
+        if (((uintptr_t)q & 255) != 0) {
+            fns.free(q, fns.ctx);
+            return set_err(TPMG_ERR_ARG, "the caller's allocator returned a block not aligned to 256 bytes");
+        }
+        std::lock_guard<std::mutex> g(g_alloc_mu);
+        caller_blocks()[q] = fns;
+        *p = q;
+    } else {
+        cudaError_t e = cudaMalloc(p, sz);
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            cudaGetLastError();
+            return set_err(TPMG_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+    }
+    cudaMemset(*p, 0, sz);  // defined contents for profiling runs
     return TPMG_OK;
 }
+static void dev_free(void* p) {
+    if (!p) return;
+    AllocFns fns;
+    bool caller = false;
+    {
+        std::lock_guard<std::mutex> g(g_alloc_mu);
+        auto it = caller_blocks().find(p);
+        if (it != caller_blocks().end()) {
+            fns = it->second;
+            caller_blocks().erase(it);
+            caller = true;
+        }
+    }
+    if (caller) {
+        cudaDeviceSynchronize();  // no kernel of this library still uses the block
+        fns.free(p, fns.ctx);
+    } else {
+        cudaFree(p);
+    }
+}
 static void dfree(void*& p) {
-    if (p) cudaFree(p);
+    dev_free(p);
     p = nullptr;
 }
 static size_t elem_bytes(int pid) { return pid == 1 ? 4 : 8; }
@@ -173,7 +227,7 @@ static void invalidate_graphs(tpmg_op* op) {
 static tpmg_status ensure_history(tpmg_op* op, int n) {
     if (n <= op->history_cap) return TPMG_OK;
     if (op->history) {
-        cudaFree(op->history);
+        dev_free(op->history);
         op->history = nullptr;
         invalidate_graphs(op);
     }
@@ -965,6 +1019,16 @@ tpmg_status tpmg_residual_restrict_smooth(tpmg_op* op, int level, tpmg_precision
     return TPMG_OK;
 }
 
+tpmg_status tpmg_set_allocator(tpmg_alloc_fn alloc_fn, tpmg_free_fn free_fn, void* ctx) {
+    if ((alloc_fn == nullptr) != (free_fn == nullptr))
+        return set_err(TPMG_ERR_ARG, "tpmg_set_allocator needs both functions or neither");
+    std::lock_guard<std::mutex> g(g_alloc_mu);
+    g_alloc.alloc = alloc_fn;
+    g_alloc.free = free_fn;
+    g_alloc.ctx = alloc_fn ? ctx : nullptr;
+    return TPMG_OK;
+}
+
 tpmg_status tpmg_set_fusion(tpmg_op* op, int enable) {
     if (!op) return set_err(TPMG_ERR_ARG, "NULL operator");
     const int on = enable != 0;
@@ -1372,8 +1436,7 @@ struct BatchCache {
         if (graph) cudaGraphExecDestroy(graph);
         void* ptrs[] = {d_probs,    d_state, d_tasks, d_phase_begin, d_phase_tiles, d_partials,
                         d_bar,      d_flags, d_hist,  d_scratch};
-        for (void* p : ptrs)
-            if (p) cudaFree(p);
+        for (void* p : ptrs) dev_free(p);
         if (h_state) cudaFreeHost(h_state);
         if (h_flags) cudaFreeHost(h_flags);
     }
@@ -1749,8 +1812,7 @@ static tpmg_status nn_ensure_cap(tpmg_nn* nn, size_t n) {
     NNBufs& b = nn->b;
     if (n <= b.ncap) return TPMG_OK;
     void* ptrs[] = {b.a1, b.a2, b.a3, b.d1, b.d2, b.x, b.out, b.d4, b.tmp};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
+    for (void* p : ptrs) dev_free(p);
     b.a1 = b.a2 = b.a3 = b.d1 = b.d2 = b.x = nullptr;
     b.out = b.d4 = b.tmp = nullptr;
     b.ncap = 0;
@@ -1818,8 +1880,7 @@ tpmg_status tpmg_nn_destroy(tpmg_nn* nn) {
     NNBufs& b = nn->b;
     void* ptrs[] = {b.params, b.grad, b.adam_m, b.adam_v, b.w1, b.w2f, b.w2b, b.w3f, b.w3b, b.w4,
                     b.a1,     b.a2,   b.a3,     b.d1,     b.d2, b.x,   b.out, b.d4,  b.part, b.dpart, b.tmp, b.err};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
+    for (void* p : ptrs) dev_free(p);
     delete nn;
     return TPMG_OK;
 }
@@ -1974,7 +2035,7 @@ extern "C" tpmg_status tpmg_nn_make_pair(tpmg_op* op, int cin, const double* r, 
     __nv_bfloat16* xb = nullptr;
     TRY(dalloc((void**)&part, sizeof(double) * 1025));
     if (dalloc((void**)&xb, n * 2 * cin) != TPMG_OK) {
-        cudaFree(part);
+        dev_free(part);
         return TPMG_ERR_OOM;
     }
     k_sumsq_f64<<<1024, 256, 0, s>>>(n, r, part);
@@ -1984,8 +2045,8 @@ extern "C" tpmg_status tpmg_nn_make_pair(tpmg_op* op, int cin, const double* r, 
     note_launch();
     note_launch();
     cudaError_t err = cudaStreamSynchronize(s);
-    cudaFree(part);
-    cudaFree(xb);
+    dev_free(part);
+    dev_free(xb);
     if (err != cudaSuccess) return set_err(TPMG_ERR_CUDA, cudaGetErrorString(err));
     return TPMG_OK;
 }

@@ -49,6 +49,9 @@ _lib = None
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
+# tpmg_alloc_fn / tpmg_free_fn
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 _SIGNATURES = {
     "tpmg_create_grid": [_I, _I, _I, _I, ctypes.POINTER(_P)],
@@ -66,6 +69,7 @@ _SIGNATURES = {
     "tpmg_restrict_smooth": [_P, _I, _I, _D, _P, _P, _P, _P],
     "tpmg_residual_restrict_smooth": [_P, _I, _I, _D, _P, _P, _P, _P, _P],
     "tpmg_set_fusion": [_P, _I],
+    "tpmg_set_allocator": [ALLOC_FN, FREE_FN, _P],
     "tpmg_prolongate": [_P, _I, _I, _P, _P, _P],
     "tpmg_cg_fused_spmv": [_P, _I, _D, _D, _P, _P, _P, _P, _P, _P],
     "tpmg_cg_fused_tridiag": [_P, _I, _D, _P, _P, _P, _P, _P, _P],
@@ -247,6 +251,42 @@ def residual_restrict_smooth(op, level, prec, rho, u_fine, f_fine, f_c, u_c, n_f
                                                 _field(f_fine, prec, n_fine, "f_fine"),
                                                 _field(f_c, prec, n_coarse, "f_c"), _field(u_c, prec, n_coarse, "u_c"),
                                                 _stream(stream)), "residual_restrict_smooth")
+
+
+# every callback pair ever installed stays referenced: blocks it allocated go back to it later
+_installed_allocators: list = []
+
+
+def set_allocator(alloc, free) -> None:
+    """Install Python callables as the library's device allocator: alloc(nbytes) -> device address
+    (int, 256-byte aligned) or 0, free(address). None, None restores cudaMalloc / cudaFree."""
+    if alloc is None and free is None:
+        _check(load().tpmg_set_allocator(ALLOC_FN(), FREE_FN(), None), "set_allocator")
+        return
+
+    def _alloc(nbytes, ctx):
+        try:
+            return int(alloc(int(nbytes))) or None
+        except Exception:  # reported by the library as TPMG_ERR_OOM
+            return None
+
+    def _free(ptr, ctx):
+        free(int(ptr))
+
+    pair = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _installed_allocators.append(pair)
+    _check(load().tpmg_set_allocator(pair[0], pair[1], None), "set_allocator")
+
+
+def use_torch_allocator(device=None) -> None:
+    """Serve the library's device buffers from PyTorch's caching allocator (on `device`, default the
+    current one): the library's workspace then shows in torch.cuda.memory_allocated()."""
+    dev = torch.cuda.current_device() if device is None else device
+    set_allocator(lambda n: torch.cuda.caching_allocator_alloc(n, dev), torch.cuda.caching_allocator_delete)
+
+
+def use_cuda_allocator() -> None:
+    set_allocator(None, None)
 
 
 def set_fusion(op, enable) -> None:

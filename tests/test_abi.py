@@ -88,3 +88,12 @@ def test_solve_memory_reference_model():
             got = bench.solve_memrefs(cells, iters) / cells[L]
             assert abs(got - (3 + iters * closed)) < 1e-12
     assert abs(closed - 23.9956) < 1e-4
+
+
+def test_set_allocator_argument_checks_without_gpu():
+    from paper_1402_3545_gb300 import tpmg
+    lib = tpmg.load()
+    alloc = tpmg.ALLOC_FN(lambda n, c: None)
+    assert lib.tpmg_set_allocator(alloc, tpmg.FREE_FN(), None) == tpmg.ERR_ARG
+    assert b"both" in lib.tpmg_last_error()
+    assert lib.tpmg_set_allocator(tpmg.ALLOC_FN(), tpmg.FREE_FN(), None) == tpmg.OK
