@@ -631,6 +631,19 @@ def run_ours(args, rank, world, dist):
     else:
         e2e_ms, e2e_path = e2e_copy_ms, "cudaMemcpyAsync of f, tpmg_mg_solve on device fields, cudaMemcpyAsync of u"
 
+    # error of each solution against u*, a double-word solve of the same problem to a 1e-12
+    # relative residual (outside every timed region)
+    ustar = torch.zeros_like(fd)
+    tpmg.mg_solve(op.op, tpmg.default_params(prec=tpmg.DW, tol=1e-12, max_iter=100), fd, ustar, n)
+    ustar_norm = float(torch.linalg.vector_norm(ustar).item())
+
+    def err_vs_ustar(x):
+        return float(torch.linalg.vector_norm(x - ustar).item()) / ustar_norm
+
+    u.zero_()
+    solve()
+    headline_err = err_vs_ustar(u)
+
     # the other precisions on the same problem (one solve each, after a warm-up solve)
     variants = {}
     for name, vprec, tol, bf in [("f64_native", tpmg.F64, 1e-6, 0), ("mixed_fp32_inner", tpmg.MIXED, 1e-6, 0),
@@ -640,10 +653,13 @@ def run_ours(args, rank, world, dist):
         for _ in range(2):
             u.zero_()
             r = tpmg.mg_solve(op.op, vp, fd, u, n)
-        variants[name] = {"ms": round(r["ms"], 3), "iters": r["iters"], "rel_res": r["rel_res"]}
+        variants[name] = {"ms": round(r["ms"], 3), "iters": r["iters"], "rel_res": r["rel_res"],
+                          "rel_err_vs_u_star": err_vs_ustar(u)}
     u.zero_()
     r = tpmg.cg_solve(op.op, tpmg.default_params(prec=tpmg.DW, tol=1e-6, max_iter=5000), fd, u, n)
-    variants["cg_dw"] = {"ms": round(r["ms"], 3), "iters": r["iters"], "rel_res": r["rel_res"]}
+    variants["cg_dw"] = {"ms": round(r["ms"], 3), "iters": r["iters"], "rel_res": r["rel_res"],
+                         "rel_err_vs_u_star": err_vs_ustar(u)}
+    del ustar
 
     # batched workload: 64 problems of drawn sizes in one persistent launch vs one solve after another
     variants["batched_64"] = bench_batched(tpmg, torch)
@@ -671,7 +687,8 @@ def run_ours(args, rank, world, dist):
                            "solver": "V(2,2), rho 0.8, 2 coarse steps", "tol": 1e-6, "precision": "DW",
                            "parallelism": f"replicas{world}",
                            "l2": "inputs larger than L2 (268 MB per FP64 field > 129 MB)"},
-                "iters": iters[-1], "roofline": roofline, "solve_hbm": solve_hbm, "roofline_f64": roofline_f64,
+                "iters": iters[-1], "rel_err_vs_u_star": headline_err,
+                "roofline": roofline, "solve_hbm": solve_hbm, "roofline_f64": roofline_f64,
                 "kernel_ms": kernel_ms,
                 "kernel_ms_f32": kernel_ms_f32,
                 "tile_variants": {"dw": variants_dw, "f32": variants_f32}, "variants": variants,
