@@ -97,3 +97,20 @@ def test_set_allocator_argument_checks_without_gpu():
     assert lib.tpmg_set_allocator(alloc, tpmg.FREE_FN(), None) == tpmg.ERR_ARG
     assert b"both" in lib.tpmg_last_error()
     assert lib.tpmg_set_allocator(tpmg.ALLOC_FN(), tpmg.FREE_FN(), None) == tpmg.OK
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/tpmg.h is a C ABI: it compiles as strict C99 (no C++ or CUDA types in the signatures)
+    and every declared function can be referenced from C."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    refs = "\n".join(f"    (void)&{n};" for n in declared_symbols())
+    src.write_text('#include "tpmg.h"\nint main(void) {\n' + refs + "\n    return 0;\n}\n")
+    res = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                          "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
