@@ -290,19 +290,33 @@ def per_solve_ms(elapsed_max_ms: float, steps: int, world: int) -> float:
     return elapsed_max_ms / (steps * world)
 
 
-def solve_memrefs(level_cells, iters: int, nu_pre: int = 2, nu_post: int = 2, n_coarse: int = 2) -> float:
-    """Memory references of a whole multigrid solve by the paper's per-kernel model (Table of the
-    kernels in Sec. 3.1: Smooth and Residual 3 per cell, RestrictSmooth 6 per coarse cell,
-    Prolongate 2.25 per fine cell): `iters` V(nu_pre, nu_post) cycles, each led by the finest-level
-    Smooth that also yields the previous cycle's residual norm, plus the solve's first Smooth.
-    level_cells[l] = cells of level l (1 = coarsest .. L = finest; index 0 unused)."""
+def cycle_memrefs(level_cells, nu_pre: int = 2, nu_post: int = 2, n_coarse: int = 2, smooth: float = 3,
+                  residual: float = 3, restrict_smooth: float = 6, prolongate: float = 2.25, norm: float = 0,
+                  fine_only: bool = False) -> float:
+    """Memory references of one V(nu_pre, nu_post) cycle (Algorithm 1) from per-kernel costs per
+    cell: on the finest level nu_pre + nu_post Smooths, a Residual, a Prolongate into it and the
+    residual norm; on every coarser level but the coarsest a RestrictSmooth (the first pre-smoothing
+    step, per cell of that level), nu_pre - 1 Smooths, a Residual, a Prolongate into it and nu_post
+    Smooths; on the coarsest a RestrictSmooth and n_coarse - 1 Smooths. level_cells[l] = cells of
+    level l (1 = coarsest .. L = finest; index 0 unused). fine_only: the finest level's share."""
     L = len(level_cells) - 1
     n = level_cells
-    cycle = (3 * (nu_pre + nu_post) + 3 + 2.25) * n[L]
+    total = (smooth * (nu_pre + nu_post) + residual + prolongate + norm) * n[L]
+    if fine_only:
+        return total
     for l in range(2, L):
-        cycle += (6 + 3 * (nu_pre - 1) + 3 + 2.25 + 3 * nu_post) * n[l]
-    cycle += (6 + 3 * (n_coarse - 1)) * n[1]
-    return 3 * n[L] + iters * cycle
+        total += (restrict_smooth + smooth * (nu_pre - 1) + residual + prolongate + smooth * nu_post) * n[l]
+    total += (restrict_smooth + smooth * (n_coarse - 1)) * n[1]
+    return total
+
+
+def solve_memrefs(level_cells, iters: int, nu_pre: int = 2, nu_post: int = 2, n_coarse: int = 2) -> float:
+    """Memory references of a whole multigrid solve by the minimal per-kernel model (Smooth and
+    Residual 3 per cell -- the Thomas intermediates stay on chip --, RestrictSmooth 6 per coarse cell,
+    Prolongate 2.25 per fine cell, the residual norm fused into the next Smooth): `iters` cycles plus
+    the solve's first Smooth, which also yields the initial residual norm."""
+    L = len(level_cells) - 1
+    return 3 * level_cells[L] + iters * cycle_memrefs(level_cells, nu_pre, nu_post, n_coarse)
 
 
 def nn_flops_per_voxel(cin: int) -> int:

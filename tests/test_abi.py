@@ -114,3 +114,39 @@ def test_header_is_plain_c(tmp_path):
     res = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
                           "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
     assert res.returncode == 0, res.stderr
+
+
+def _kernel_table():
+    rows = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "kernel_table.txt")):
+        if line.strip() and not line.startswith("#"):
+            name, fl, mem, memc = line.split()
+            rows[name] = (float(fl), float(mem), float(memc))
+    return rows
+
+
+def test_cycle_accounting_reproduces_the_papers_kernel_table():
+    """bench.py's cycle accounting (which kernels run on which level, weighted by the level's cells)
+    fed with the paper's per-kernel counts reproduces the paper's totals for its V(1,1) on 5 levels
+    (Sec. 4.1, Table KernelTable): MemC 29.6 per fine cell (23 on the fine level), Mem 67.2 and
+    FLOPs 149.4 given the table's fine-level rows; and the fused CG's sums."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_model2", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    t = _kernel_table()
+    cells = [0] + [4.0 ** (l - 5) for l in range(1, 6)]  # fine level = 1; each coarser level 1/4
+    for col in (0, 1, 2):
+        k = {name: t[name][col] for name in ("Smooth", "ResSmooth", "Res", "Prolongate", "ResNorm")}
+        kw = dict(nu_pre=1, nu_post=1, n_coarse=2, smooth=k["Smooth"], residual=k["Res"],
+                  restrict_smooth=k["ResSmooth"], prolongate=k["Prolongate"], norm=k["ResNorm"])
+        fine = bench.cycle_memrefs(cells, fine_only=True, **kw)
+        total = bench.cycle_memrefs(cells, **kw)
+        if col == 2:
+            # MemC: the fine level is the sum of its kernels
+            assert fine == t["FineLevelOnly"][2]
+        # the coarser levels on top of the table's fine-level row give the table's total
+        coarse = total - fine
+        assert abs(t["FineLevelOnly"][col] + coarse - t["Total"][col]) < 0.05, (col, coarse)
+    assert t["SpMV"][2] + t["Tridiag"][2] == t["CGTotal"][2]
+    assert t["SpMV"][0] + t["Tridiag"][0] == t["CGTotal"][0]
