@@ -150,3 +150,23 @@ def test_cycle_accounting_reproduces_the_papers_kernel_table():
         assert abs(t["FineLevelOnly"][col] + coarse - t["Total"][col]) < 0.05, (col, coarse)
     assert t["SpMV"][2] + t["Tridiag"][2] == t["CGTotal"][2]
     assert t["SpMV"][0] + t["Tridiag"][0] == t["CGTotal"][0]
+
+
+def test_binding_refuses_host_tensors_without_gpu():
+    """No CPU fallback: every field argument must be a CUDA tensor of the precision's dtype and size;
+    host tensors are refused before the library is called (here without a GPU)."""
+    import pytest
+    import torch
+    from paper_1402_3545_gb300 import tpmg
+    x = torch.zeros(4 * 4 * 2, dtype=torch.float64)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        tpmg.apply_A(0, 1, tpmg.F64, x, x, x.numel())
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        tpmg.residual_restrict_smooth(0, 1, tpmg.DW, 0.8, x, x, x, x, x.numel(), x.numel())
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        tpmg.mg_solve(0, tpmg.default_params(prec=tpmg.F64), x, x, x.numel())
+    with pytest.raises(TypeError, match="scalar outputs"):
+        tpmg._scalar_out(torch.zeros(1, dtype=torch.float64))
+    # page-locked host fields are accepted only by the double-word and mixed solves
+    with pytest.raises(ValueError, match="prec DW or MIXED"):
+        tpmg.mg_solve_host(0, tpmg.default_params(prec=tpmg.F64), x, x, x.numel())
