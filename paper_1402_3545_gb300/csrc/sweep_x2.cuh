@@ -66,10 +66,12 @@ constexpr int HINT_STREAM = 1, HINT_KEEP = 2, HINT_DISCARD = 4, HINT_ALL = 7;
 // (t % (nx/64)) * 64, y from (t / (nx/64)) * TY), each thread owning two adjacent columns: every
 // per-thread load, store and cp.async moves a 16-byte pair (8 bytes in FP32), and the two
 // independent Thomas recurrences interleave. gstack is this block's scratch slot of nz x 64 TY
-// values (unused in residual mode); smem_raw its dynamic shared memory (sweep_x2_smem bytes).
-// Every thread of the block must call it (barriers). Shared ring per slot: u rows of stride
-// UW = 68 (pad, left halo, 64 columns, right halo, pad), rows j0-1 .. j0+TY; f pairs; 1/m_k pairs.
-// Requires nx % 64 == 0, ny % TY == 0 and 16-byte aligned fields.
+// values (unused in residual and apply modes; the coarse columns' stack in restrict mode); smem_raw
+// its dynamic shared memory (sweep_x2_smem bytes). Every thread of the block must call it
+// (barriers). Shared ring per slot: u rows of stride UW = 68 (pad, left halo, 64 columns, right
+// halo, pad), rows j0-1 .. j0+TY; f pairs; 1/m_k pairs (restrict mode: the coarse columns' 1/m_k,
+// then a two-plane buffer of the odd rows' pair sums). xr: the coarse level and outputs of restrict
+// mode (unused otherwise). Requires nx % 64 == 0, ny % TY == 0 and 16-byte aligned fields.
 template <class P, class PO, int TY, int PD, int MODE, int HINT = 0>
 __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, const typename P::S* __restrict__ u,
                                                  const typename P::S* __restrict__ f,
