@@ -323,13 +323,19 @@ tpmg_status tpmg_fcg_solve(tpmg_op* op, tpmg_nn* nn, const float* aux, const tpm
  *
  * Scratch: one partial sum per thread block in a fixed file-scope device array of
  * TPMG_NOALLOC_MAX_BLOCKS doubles (512 KB), held by every GPU that loads the library until the
- * process exits. Sizes needing more blocks (ceil(nx/32) * ceil(ny/4) > TPMG_NOALLOC_MAX_BLOCKS,
- * e.g. nx*ny above about 8.4 million columns) are rejected with TPMG_ERR_ARG and a message in
- * tpmg_noalloc_last_error(). All calls share the array and each call overwrites the entries it
- * reads before reading them, so no clearing is needed; calls that overlap on the GPU (on
- * different streams or host threads without ordering) race on it and must be serialised.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture. */
+ * process exits. The number of blocks is that of the residual kernel the grid takes: at most 1024
+ * on grids of at most 4096 columns; on grids with nx a multiple of 64, even ny and 16-byte aligned
+ * u, f, r (the two-column persistent sweep) at most 16 per SM whatever the size; otherwise
+ * (nx/32)*(ny/4) blocks for nx a multiple of 32 and ny of 4, else one per 32 x 4 columns rounded
+ * up. A call needing more than TPMG_NOALLOC_MAX_BLOCKS (above about 8.4 million columns on the
+ * last two kinds of grid) is rejected with TPMG_ERR_ARG and a message in
+ * tpmg_noalloc_last_error() before anything is launched. All calls share the array and each call
+ * overwrites the entries it reads before reading them, so no clearing is needed; calls that
+ * overlap on the GPU (on different streams or host threads without ordering) race on it and must
+ * be serialised. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life of the process; make
+ * that first call before any stream capture, and do not use this entry point on a device after a
+ * cudaDeviceReset there (the kept address would belong to the destroyed context). */
 #define TPMG_NOALLOC_MAX_BLOCKS 65536
 tpmg_status tpmg_residual_norm_noalloc(int nx, int ny, int nz, double cx, double cy, const double* v,
                                        const double* u, const double* f, double* r, double* norm_out,

@@ -384,10 +384,13 @@ int launch_smooth(const Lv<P>& L, double rho, const typename P::S* u, const type
     note_launch();
     return sh.nblocks();
 }
-int residual_blocks(int nx, int ny, int nz, int bytes_per_value) {
-    if ((size_t)nx * ny <= (size_t)PCR_MAX_COLS) return cell_blocks((size_t)nx * ny * nz);  // pointwise kernel
-    if (nx % 32 == 0 && ny % 4 == 0 && nx >= 32) return (nx / 32) * (ny / 4);  // pipelined kernel
-    return sweep_shape(nx, ny, nz, bytes_per_value, false).nblocks();
+template <class P, class PO>
+int residual_launch_blocks(const Lv<P>& L, const typename P::S* u, const typename P::S* f, typename PO::S* r) {
+    // launch_residual's three choices in its order: pointwise, plane-pipelined, one thread per column
+    if ((size_t)L.nx * L.ny <= (size_t)PCR_MAX_COLS) return cell_blocks((size_t)L.nx * L.ny * L.nz);
+    const int nb = residual_pp_blocks<P, PO>(L, u, f, r);
+    if (nb >= 0) return nb;
+    return sweep_shape(L.nx, L.ny, L.nz, sizeof(typename P::R), false).nblocks();
 }
 template <class P, class PO>
 int launch_residual(const Lv<P>& L, const typename P::S* u, const typename P::S* f,
@@ -436,6 +439,7 @@ void launch_correct(size_t n, typename P::S* u, const float* e, const int* done,
     template void launch_line_solve<P>(const Lv<P>&, const P::S*, P::S*, double, const int*, cudaStream_t); \
     template int launch_smooth<P>(const Lv<P>&, double, const P::S*, const P::S*, P::S*, double*, \
                                    const int*, cudaStream_t);                                      \
+    template int residual_launch_blocks<P, P>(const Lv<P>&, const P::S*, const P::S*, P::S*);     \
     template int launch_residual<P, P>(const Lv<P>&, const P::S*, const P::S*, P::S*, double*,     \
                                         const int*, cudaStream_t);                                 \
     template void launch_restrict_smooth<P, P>(const Lv<P>&, double, const P::S*, P::S*, P::S*,   \

@@ -362,10 +362,11 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
     if (partials && threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.x] = sm;
 }
 
+// Grid (number of persistent blocks) of the two-column sweep on level L with these fields, or -1
+// where the level or the fields do not take it. run_sweep_x2 launches exactly this many blocks, and
+// residual_launch_blocks reports it without launching.
 template <class P, class PO, int TY, int PD, int MODE, int MINB = 1, int HINT = 0>
-static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, const typename P::S* f,
-                        typename PO::S* out, double* partials, const int* done, cudaStream_t s, int cap) {
-    typedef typename P::S S;
+static int sweep_x2_grid(const Lv<P>& L, const void* u, const void* f, const void* out, int cap) {
     constexpr bool STACK = x2_stack(MODE);
     constexpr bool HALO = MODE != MODE_LINESOLVE;
     if (L.nx % 64 || L.ny % TY || (STACK && (!L.gstack || !L.finv || !L.fw))) return -1;
@@ -386,7 +387,16 @@ static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, con
     const int slots = num_sms() * GS_BLOCKS_PER_SM * GS_MAX_NT / (2 * 32 * TY);
     if (STACK && nb > slots) nb = slots;
     if (nb > ntiles) nb = ntiles;
-    kern<<<nb, dim3(32, TY), smem, s>>>(L, coef, u, f, out, partials, done);
+    return nb;
+}
+
+template <class P, class PO, int TY, int PD, int MODE, int MINB = 1, int HINT = 0>
+static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, const typename P::S* f,
+                        typename PO::S* out, double* partials, const int* done, cudaStream_t s, int cap) {
+    const int nb = sweep_x2_grid<P, PO, TY, PD, MODE, MINB, HINT>(L, u, f, out, cap);
+    if (nb < 0) return -1;
+    const size_t smem = sweep_x2_smem<P, TY, PD, MODE>();
+    k_sweep_x2<P, PO, TY, PD, MODE, MINB, HINT><<<nb, dim3(32, TY), smem, s>>>(L, coef, u, f, out, partials, done);
     note_launch();
     return nb;
 }
@@ -517,6 +527,16 @@ int launch_residual_pp(const Lv<P>& L, const typename P::S* u, const typename P:
     if (nb >= 0) return nb;
     if (!pp_fits<P, 4, false>(L)) return -1;
     return run_sweep_pp<P, PO, 4, 6, MODE_RESIDUAL>(L, 1.0, u, f, r, partials, done, s);
+}
+
+template <class P, class PO>
+int residual_pp_blocks(const Lv<P>& L, const typename P::S* u, const typename P::S* f, typename PO::S* r) {
+    // the same decisions as launch_residual_pp: the two-column grid, else the one-column pipelined
+    // kernel's (nx / 32) x (ny / 4) blocks (run_sweep_pp without the persistent stack)
+    const int nb = sweep_x2_grid<P, PO, 2, 4, MODE_RESIDUAL>(L, u, f, r, 16);
+    if (nb >= 0) return nb;
+    if (!pp_fits<P, 4, false>(L)) return -1;
+    return (L.nx / 32) * (L.ny / 4);
 }
 
 template <class P>
@@ -678,6 +698,7 @@ int launch_restrict_smooth_pp(const Lv<P>& Lc, double rho, const typename PF::S*
     template void launch_factor_k0<P>(const Lv<P>&, const P::S*, const P::S*, int*, cudaStream_t);          \
     template int launch_smooth_pp<P>(const Lv<P>&, double, const P::S*, const P::S*, P::S*, double*, const int*, \
                                      cudaStream_t);                                                          \
+    template int residual_pp_blocks<P, P>(const Lv<P>&, const P::S*, const P::S*, P::S*);                    \
     template int launch_residual_pp<P, P>(const Lv<P>&, const P::S*, const P::S*, P::S*, double*, const int*,  \
                                           cudaStream_t);                                                     \
     template int launch_line_solve_pp<P>(const Lv<P>&, const P::S*, P::S*, double, const int*, cudaStream_t); \

@@ -211,8 +211,10 @@ template <class P>
 int launch_residual_restrict(const Lv<P>& L, const Lv<P>& Lc, double rho, const typename P::S* u,
                              const typename P::S* f, typename P::S* fc, typename P::S* uc, const int* done,
                              cudaStream_t s);
-// number of blocks launch_residual uses on an nx x ny level (= partial sums it writes)
-int residual_blocks(int nx, int ny, int nz, int bytes_per_value);
+// number of blocks launch_residual_pp would launch for these fields (= partial sums it writes),
+// -1 where it would return -1; nothing is launched
+template <class P, class PO>
+int residual_pp_blocks(const Lv<P>& L, const typename P::S* u, const typename P::S* f, typename PO::S* r);
 
 // ---------------------------------------------------------------- launchers (k_coarse.cu)
 // Cell-parallel kernels for levels of at most PCR_MAX_COLS columns; each returns its number of
@@ -259,6 +261,9 @@ int launch_smooth(const Lv<P>& L, double rho, const typename P::S* u, const type
 template <class P, class PO>
 int launch_residual(const Lv<P>& L, const typename P::S* u, const typename P::S* f,
                     typename PO::S* r, double* partials, const int* done, cudaStream_t s);
+// number of blocks (= partial sums) launch_residual would launch for these fields, without launching
+template <class P, class PO>
+int residual_launch_blocks(const Lv<P>& L, const typename P::S* u, const typename P::S* f, typename PO::S* r);
 // fine level in policy PF (its residual r_f), coarse level in P
 template <class PF, class P>
 void launch_restrict_smooth(const Lv<P>& Lc, double rho, const typename PF::S* rf,

@@ -52,20 +52,6 @@ extern "C" tpmg_status tpmg_residual_norm_noalloc(int nx, int ny, int nz, double
         g_noalloc_err = "tpmg_residual_norm_noalloc: sizes must be >= 1 and pointers non-NULL";
         return TPMG_ERR_ARG;
     }
-    const int nblocks = residual_blocks(nx, ny, nz, (int)sizeof(double));
-    if (nblocks > TPMG_NOALLOC_MAX_BLOCKS) {
-        g_noalloc_err = "tpmg_residual_norm_noalloc: " + std::to_string(nblocks) +
-                        " thread blocks needed, the fixed scratch holds " +
-                        std::to_string(TPMG_NOALLOC_MAX_BLOCKS) + " (nx*ny too large)";
-        return TPMG_ERR_ARG;
-    }
-    double* partials = nullptr;
-    cudaError_t e = partials_for_current_device(&partials);
-    if (e != cudaSuccess) {
-        g_noalloc_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-        return TPMG_ERR_CUDA;
-    }
-    cudaStream_t s = (cudaStream_t)stream;
     Lv<PolF64> L;
     L.nx = nx;
     L.ny = ny;
@@ -77,6 +63,22 @@ extern "C" tpmg_status tpmg_residual_norm_noalloc(int nx, int ny, int nz, double
     L.fw = nullptr;
     L.fac_percol = 0;
     L.variant = -1;
+    // the block count is planned by the same decisions the launch takes, and checked against the
+    // fixed array before anything is launched: no kernel ever writes past its end
+    const int nblocks = residual_launch_blocks<PolF64, PolF64>(L, u, f, r);
+    if (nblocks < 1 || nblocks > TPMG_NOALLOC_MAX_BLOCKS) {
+        g_noalloc_err = "tpmg_residual_norm_noalloc: " + std::to_string(nblocks) +
+                        " thread blocks needed, the fixed scratch holds " +
+                        std::to_string(TPMG_NOALLOC_MAX_BLOCKS) + " (grid too large for its kernel)";
+        return TPMG_ERR_ARG;
+    }
+    double* partials = nullptr;
+    cudaError_t e = partials_for_current_device(&partials);
+    if (e != cudaSuccess) {
+        g_noalloc_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+        return TPMG_ERR_CUDA;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
     // every entry that the sum reads is written by this call's residual kernel before the
     // finalize kernel runs (same stream), so nothing has to be cleared beforehand
     const int launched = launch_residual<PolF64, PolF64>(L, u, f, r, partials, nullptr, s);
