@@ -235,6 +235,15 @@ tpmg_status tpmg_time_kernel(tpmg_op* op, tpmg_precision prec, tpmg_kernel k, in
 /* Number of kernel launches this library has issued since the process started (a graph replay
  * counts every kernel node it contains). */
 unsigned long long tpmg_kernel_launches(void);
+/* Arithmetic rate of the current GPU, the denominator of the ALU rooflines (the paper's kernels
+ * are bandwidth-bound on its K20X, Sec. 4; on a part with a narrow FP64 pipe the same per-cell
+ * arithmetic can bind first). which: 0 = FP64 fused multiply-add, 1 = FP64 add, 2 = FP64 multiply,
+ * 3 = FP32 fused multiply-add. Runs a full-occupancy grid of independent dependent chains `reps`
+ * times (after one warm-up) on the legacy default stream and writes the best launch's operations
+ * per second (one operation = one instruction's result per thread, so a multiply-add counts once)
+ * to *ops_per_s and its duration in ms to *ms_per_launch (may be NULL). Allocates and frees a small
+ * sink buffer; synchronises the device. */
+tpmg_status tpmg_measure_alu_rate(int which, int reps, double* ops_per_s, double* ms_per_launch);
 
 /* ---------------------------------------------------------------- autotuning
  * The plane-pipelined Smooth has TPMG_NUM_VARIANTS variants: tile shapes (columns per block x ring

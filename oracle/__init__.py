@@ -4,7 +4,10 @@ Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``b
 import this package. The CUDA library shares no code with it. Fields are numpy float64 arrays of
 shape (nz, ny, nx) (x fastest); the vertical coefficient ``v`` is an (ny, nx) array of
 omega^2 lambda^2 / hz^2 per column. Each wrapper names the passage of the paper it follows; the C
-source (``tpmg_oracle.c``) holds the arithmetic.
+source (``tpmg_oracle.c``) holds the arithmetic, with OpenMP over cells and columns where the host
+compiler has it (``set_threads``; results do not depend on the thread count). ``oracle.spectral``
+is the exact solver of constant-coefficient problems (library FFT/DCT and the closed-form
+eigenvalues), the reference for full-size solutions.
 """
 from __future__ import annotations
 
@@ -33,8 +36,11 @@ def build(force: bool = False) -> str:
     if not os.path.exists(stamp) or open(stamp).read() != platform.machine():
         force = True  # built on another host architecture
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
-        cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", _LIB] + srcs + ["-lm"]
-        subprocess.run(cmd, check=True)
+        # OpenMP over cells and columns where the host compiler has it (results do not depend on
+        # the thread count: see orc_set_threads), else the same code on one thread
+        base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", _LIB] + srcs + ["-lm"]
+        if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True).returncode != 0:
+            subprocess.run(base, check=True)
         with open(stamp, "w") as fh:
             fh.write(platform.machine())
     return _LIB
@@ -46,6 +52,7 @@ def _load():
         build()
         lib = ctypes.CDLL(_LIB)
         for name, args, res in [
+            ("orc_set_threads", [_I], _I),
             ("orc_apply_A", [_I, _I, _I, _D, _D, _P, _P, _P], None),
             ("orc_line_solve", [_I, _I, _I, _D, _D, _P, _P, _P], None),
             ("orc_residual", [_I, _I, _I, _D, _D, _P, _P, _P, _P], None),
@@ -63,6 +70,13 @@ def _load():
             fn.restype = res
         _lib = lib
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Host threads of the oracle's loops over cells and columns (n >= 1; 0 leaves the count as it
+    is); returns the count in effect. Results are the same for every count: each cell or column is
+    computed by the same code, and dot products and norms run in index order on one thread."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 def _f64(a) -> np.ndarray:

@@ -32,6 +32,24 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads: the loops over cells or columns may run on several host threads (OpenMP, when the
+ * library is built with it). Every cell or column is computed by the same code whichever thread
+ * takes it, so results do not depend on the thread count; the dot products and norms run on one
+ * thread in index order, so they do not either. orc_set_threads(n) sets the count (n >= 1) and
+ * returns the count in effect. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 #define ORC_MAX_LEVELS 16
 
@@ -49,6 +67,7 @@ static int wrap(int i, int n) {
  * "LocalMatrixStencil" with |T| = 1, a = 1, alpha_{TT'} diag(d) = -cx or -cy, b = c = -v). */
 void orc_apply_A(int nx, int ny, int nz, double cx, double cy, const double *v,
                  const double *x, double *y) {
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -78,8 +97,11 @@ void orc_apply_A(int nx, int ny, int nz, double cx, double cy, const double *v,
  * elimination k = 0..nz-1, then back substitution k = nz-1..0. */
 void orc_line_solve(int nx, int ny, int nz, double cx, double cy, const double *v,
                     const double *b, double *x) {
+#pragma omp parallel
+    {
     double *cp = (double *)malloc(sizeof(double) * (size_t)nz);
     double *dp = (double *)malloc(sizeof(double) * (size_t)nz);
+#pragma omp for collapse(2) schedule(static)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             double vij = v[(size_t)j * nx + i];
@@ -105,6 +127,7 @@ void orc_line_solve(int nx, int ny, int nz, double cx, double cy, const double *
         }
     free(cp);
     free(dp);
+    }
 }
 
 /* r = f - A u : the Residual kernel of Sec. 3.1. */
@@ -112,6 +135,7 @@ void orc_residual(int nx, int ny, int nz, double cx, double cy, const double *v,
                   const double *u, const double *f, double *r) {
     size_t n = (size_t)nx * ny * nz;
     orc_apply_A(nx, ny, nz, cx, cy, v, u, r);
+#pragma omp parallel for schedule(static)
     for (size_t p = 0; p < n; ++p) r[p] = f[p] - r[p];
 }
 
@@ -124,6 +148,7 @@ void orc_smooth(int nx, int ny, int nz, double cx, double cy, const double *v, d
     double *z = (double *)malloc(sizeof(double) * n);
     orc_residual(nx, ny, nz, cx, cy, v, u, f, r);
     orc_line_solve(nx, ny, nz, cx, cy, v, r, z);
+#pragma omp parallel for schedule(static)
     for (size_t p = 0; p < n; ++p) u_out[p] = u[p] + rho * z[p];
     free(r);
     free(z);
@@ -133,6 +158,7 @@ void orc_smooth(int nx, int ny, int nz, double cx, double cy, const double *v, d
  * text after Eq. (12)); the coarse cell (I,J) averages its 2x2 children. nxf, nyf even. */
 void orc_restrict(int nxf, int nyf, int nz, const double *rf, double *fc) {
     int nxc = nxf / 2, nyc = nyf / 2;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < nz; ++k)
         for (int J = 0; J < nyc; ++J)
             for (int I = 0; I < nxc; ++I) {
@@ -150,6 +176,7 @@ void orc_restrict(int nxf, int nyf, int nz, const double *rf, double *fc) {
  * direction, i.e. 9/16, 3/16, 3/16, 1/16 in 2-D. Coarse indices wrap periodically. */
 void orc_prolongate_add(int nxc, int nyc, int nz, const double *uc, double *uf) {
     int nxf = 2 * nxc, nyf = 2 * nyc;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < nyf; ++j)
             for (int i = 0; i < nxf; ++i) {
@@ -250,7 +277,8 @@ static void mg_smooth(orc_mg *mg, int l) {
     size_t n = lvl_n(mg, l);
     orc_smooth(mg->nx[l], mg->ny[l], mg->nz, mg->cx[l], mg->cy[l], mg->v[l], mg->rho, mg->u[l],
                mg->f[l], mg->tmp[l]);
-    memcpy(mg->u[l], mg->tmp[l], sizeof(double) * n);
+#pragma omp parallel for schedule(static)
+    for (size_t p = 0; p < n; ++p) mg->u[l][p] = mg->tmp[l][p];
 }
 
 /* Restriction of the next finer level's residual followed by the first smoothing step from a
@@ -260,6 +288,7 @@ static void mg_restrict_smooth(orc_mg *mg, int l) {
     orc_restrict(mg->nx[l + 1], mg->ny[l + 1], mg->nz, mg->r[l + 1], mg->f[l]);
     orc_line_solve(mg->nx[l], mg->ny[l], mg->nz, mg->cx[l], mg->cy[l], mg->v[l], mg->f[l],
                    mg->u[l]);
+#pragma omp parallel for schedule(static)
     for (size_t p = 0; p < n; ++p) mg->u[l][p] *= mg->rho;
 }
 
@@ -374,6 +403,7 @@ int orc_cg_solve(int nx, int ny, int nz, double cx, double cy, const double *v, 
         while (it < max_iter) {
             orc_apply_A(nx, ny, nz, cx, cy, v, p, q);
             double alpha = rz / orc_dot(n, p, q);
+#pragma omp parallel for schedule(static)
             for (size_t s = 0; s < n; ++s) {
                 u[s] += alpha * p[s];
                 r[s] -= alpha * q[s];
@@ -389,6 +419,7 @@ int orc_cg_solve(int nx, int ny, int nz, double cx, double cy, const double *v, 
             double rz_new = orc_dot(n, r, z);
             double beta = rz_new / rz;
             rz = rz_new;
+#pragma omp parallel for schedule(static)
             for (size_t s = 0; s < n; ++s) p[s] = z[s] + beta * p[s];
         }
     }
@@ -431,6 +462,7 @@ int orc_ir_solve(int nx, int ny, int nz, int L, double cx, double cy, const doub
         while (it < max_iter) {
             memset(e, 0, sizeof(double) * n);
             mg_vcycle(&mg, L);
+#pragma omp parallel for schedule(static)
             for (size_t s = 0; s < n; ++s) u[s] += e[s];
             ++it;
             orc_residual(nx, ny, nz, cx, cy, v, u, f, r);

@@ -94,6 +94,7 @@ _SIGNATURES = {
     "tpmg_noalloc_last_error": [],
     "tpmg_time_kernel": [_P, _I, _I, _I, ctypes.POINTER(_D), _P],
     "tpmg_kernel_launches": [],
+    "tpmg_measure_alu_rate": [_I, _I, _P, _P],
     "tpmg_autotune": [_P, _I, _I, _P, _P],
     "tpmg_set_variant": [_P, _I, _I, _I],
     "tpmg_status_string": [_I],
@@ -546,6 +547,17 @@ def time_kernel(op, prec, kernel, reps=10, stream=None) -> float:
 
 def kernel_launches() -> int:
     return int(load().tpmg_kernel_launches())
+
+
+ALU_FP64_FMA, ALU_FP64_ADD, ALU_FP64_MUL, ALU_FP32_FMA = range(4)
+
+
+def measure_alu_rate(which: int, reps: int = 3) -> tuple[float, float]:
+    """Measured arithmetic rate of the current GPU: (operations per second, ms per probe launch);
+    a multiply-add counts as one operation."""
+    rate, ms = _D(), _D()
+    _check(load().tpmg_measure_alu_rate(which, reps, ctypes.byref(rate), ctypes.byref(ms)), "measure_alu_rate")
+    return rate.value, ms.value
 
 
 NUM_VARIANTS = 8
