@@ -1,17 +1,21 @@
 #!/usr/bin/env python
 """Benchmark: multigrid solve time to a 1e-6 relative residual on the mid-size problem of the
 paper's family (512 x 512 x 128 cells, lambda^2(x, y) varying, N(0,1) right-hand side, 7-level
-V(2,2) tensor-product multigrid with vertical line smoothing), FP64-accurate arithmetic.
+V(2,2) tensor-product multigrid with vertical line smoothing), in native FP64 arithmetic -- the
+paper's precision -- beside the same solve in double-word and mixed FP32/FP64 arithmetic.
 
-One step = one complete solve from a zero initial guess (every kernel of the multigrid path:
-Smooth with fused residual norm, Residual, RestrictSmooth, Prolongate, the device-side
+One step = one complete native-FP64 solve from a zero initial guess (every kernel of the multigrid
+path: Smooth with fused residual norm, Residual + RestrictSmooth, Prolongate, the device-side
 convergence test), inputs resident in HBM. Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 With N > 1 (launched by torch.distributed.run) every rank solves its own copy of the problem:
 the path has no data-parallel exchange, so ranks are independent replicas ("replicas only").
-`--impl reference` times the oracle (plain FP64 C, test infrastructure) on the host cores.
+`--impl reference` times the oracle (plain FP64 C, test infrastructure) on the host cores, one
+complete solve per step. The CPU leg of the default run (rank 0, one GPU) times the oracle the same
+way and measures every GPU solution against an independent reference: the oracle's own solve to
+1e-12 for the varying-coefficient problem, the exact spectral solution for the constant ones.
 """
 from __future__ import annotations
 
@@ -32,11 +36,13 @@ import numpy as np  # noqa: E402
 from paper_1402_3545_gb300 import workloads  # noqa: E402
 
 METRIC = "MG solve ms to 1e-6 rel. residual & % of HBM peak, FP64 vs mixed/learned"
-# dram__bytes_read.sum + dram__bytes_write.sum of one finest-level Smooth launch (k_sweep_x2,
-# double-word) on the 512^2 x 128 problem, per tile variant, from the ncu captures summarised in
-# profiles/k_sweep_x2_dw_smooth_mid_512x512x128.md (variant 6: 1.2650 GB + 0.3982 GB)
-PROFILED_SMOOTH_TRAFFIC = {5: 1554562560, 6: 1663204352, 7: 1630302208}
 HBM_FALLBACK_GBS = 6800.0
+# DRAM bytes per launch from ncu captures, keyed by kernel, precision, tile variant and workload
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+# FP64 operations of one finest-level Smooth per cell (the timed launch also forms the norm):
+# stencil residual 3 multiply-adds + 4 adds, elimination 1 multiply-add + 1 multiply, back
+# substitution and update 2 multiply-adds, norm 1 multiply-add -> 12 instructions, 19 flops
+SMOOTH_F64_INSTR, SMOOTH_F64_FLOPS = 12, 19
 
 
 def parse_args():
@@ -47,13 +53,16 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve-only", action="store_true",
-                    help="time the solves only (no kernel timing, e2e, variants or CPU baseline): "
+                    help="time the solves only (no kernel timing, e2e, variants or CPU leg): "
                          "the command the ncu launch-list profile runs")
+    ap.add_argument("--solve-precision", choices=["f64", "dw", "mixed"], default="f64",
+                    help="precision of the --solve-only solves")
     ap.add_argument("--kernel-only", choices=["smooth", "residual", "restrict_smooth", "residual_restrict",
                                               "prolongate", "line_solve", "apply_A", "cg_spmv", "cg_tridiag",
-                                              "nn_forward"],
+                                              "nn_forward", "alu_rate", "transpose"],
                     help="launch only this finest-level kernel a few times (tile variant --variant, "
-                         "no autotuning): the command a per-kernel ncu capture runs")
+                         "no autotuning): the command a per-kernel ncu capture runs; alu_rate prints "
+                         "the measured FP64 and FP32 arithmetic rates")
     ap.add_argument("--variant", type=int, default=3)
     ap.add_argument("--precision", choices=["dw", "f32", "f64"], default="dw")
     return ap.parse_args()
@@ -68,15 +77,14 @@ def measured_peaks():
     return {"hbm_gbs": HBM_FALLBACK_GBS, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def oracle_counts():
-    path = os.path.join(ROOT, "tests", "golden", "oracle_counts.txt")
+def read_traffic() -> dict:
+    """{(kernel, precision, variant, workload): (bytes, source)} from the tracked ncu summary."""
     out = {}
-    if os.path.exists(path):
-        for line in open(path):
-            if line.startswith("#") or not line.strip():
-                continue
-            k, v = line.split(None, 1)
-            out[k] = float(v)
+    if os.path.exists(TRAFFIC_FILE):
+        for line in open(TRAFFIC_FILE):
+            parts = line.split()
+            if len(parts) >= 5 and not line.startswith("#"):
+                out[(parts[0], parts[1], int(parts[2]), parts[3])] = (int(parts[4]), " ".join(parts[5:]))
     return out
 
 
@@ -134,144 +142,112 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline_sample(p, f, iters_hint):
-    """The oracle as it stands, on the host: one V-cycle and one residual on the full grid; the
-    solve estimate is t_res + iters * (t_cycle + t_res) with the oracle's own iteration count."""
+def cpu_model() -> str:
+    """The host CPU's name from /proc/cpuinfo (x86: model name; Arm: implementer and part)."""
+    info = {}
+    try:
+        for line in open("/proc/cpuinfo"):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                info.setdefault(k.strip(), v.strip())
+    except OSError:
+        return "unknown"
+    if "model name" in info:
+        return info["model name"]
+    return f"implementer {info.get('CPU implementer', '?')} part {info.get('CPU part', '?')}"
+
+
+def oracle_solve(p, f, threads: int, tol: float = 1e-6, max_iter: int = 100):
+    """One complete oracle multigrid solve of problem p (V(2,2), rho 0.8, two coarse steps, from
+    zero) on `threads` host threads: (u, cycles, seconds, threads used)."""
     import oracle
     cx, cy, v = oracle.problem_coefficients(p)
-    u = np.zeros_like(f)
+    used = oracle.set_threads(threads)
     t0 = time.perf_counter()
-    r = oracle.residual(u, f, cx, cy, v)
-    t_res = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.vcycle(u, f, cx, cy, v, p.nlevels)
-    t_cycle = time.perf_counter() - t0
-    del r
-    counts = oracle_counts()
-    iters = int(counts.get("mid_iters", iters_hint))
-    est_ms = 1e3 * (t_res + iters * (t_cycle + t_res))
-    return est_ms, {"t_cycle_s": round(t_cycle, 3), "t_residual_s": round(t_res, 3), "oracle_iters": iters}
+    u, it, _, _ = oracle.mg_solve(f, cx, cy, v, p.nlevels, tol=tol, max_iter=max_iter)
+    return u, it, time.perf_counter() - t0, used
 
 
-def _oracle_replica(p, barrier, out):
-    """One replica of the oracle sample in its own (spawned) process: the same residual and V-cycle
-    on its own copy of the inputs, timed after every replica has its inputs ready."""
+def rel_err(u, ref) -> float:
+    u = np.asarray(u, dtype=np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.float64).ravel()
+    return float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+
+
+def cpu_leg(p, f, sols: dict):
+    """The CPU side of the default run: the oracle timed on the host cores (one complete solve on all
+    of them, and one on a single core), then every GPU solution measured against an independent
+    reference -- the oracle's own solve to 1e-12 for the varying-coefficient mid problem, the exact
+    spectral solution (oracle.spectral) for the constant-coefficient mixed, learned and batched
+    problems -- and the headline solution's residual recomputed by the oracle."""
     import oracle
-    f = p.rhs()
-    cx, cy, v = oracle.problem_coefficients(p)
-    u = np.zeros_like(f)
-    barrier.wait(timeout=600)
-    t0 = time.perf_counter()
-    oracle.residual(u, f, cx, cy, v)
-    t1 = time.perf_counter()
-    oracle.vcycle(u, f, cx, cy, v, p.nlevels)
-    out.put((t1 - t0, time.perf_counter() - t1))
-
-
-def host_memory_bytes() -> int:
-    """Memory this process may still use: MemAvailable, capped by a cgroup limit if one is set."""
-    avail = 0
-    with open("/proc/meminfo") as fh:
-        for line in fh:
-            if line.startswith("MemAvailable:"):
-                avail = int(line.split()[1]) * 1024
-    for path in ("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory/memory.limit_in_bytes"):
-        try:
-            raw = open(path).read().strip()
-        except OSError:
-            continue
-        if raw.isdigit():
-            used = 0
-            for upath in ("/sys/fs/cgroup/memory.current", "/sys/fs/cgroup/memory/memory.usage_in_bytes"):
-                try:
-                    used = int(open(upath).read().strip())
-                    break
-                except (OSError, ValueError):
-                    pass
-            avail = min(avail, int(raw) - used)
-    return avail
-
-
-def cpu_baseline_all_cores(p, iters: int, bytes_per_replica: int):
-    """The oracle on every host core at once: one replica of the single-core sample per core (as many
-    as host memory allows at bytes_per_replica each), spawned processes, started together. Returns
-    the per-solve time of the whole host (the slowest replica's solve estimate / replicas) and the
-    details, or None when fewer than two replicas fit."""
-    import multiprocessing as mp
+    from oracle import spectral
     cores = os.cpu_count() or 1
-    fit = int(0.5 * host_memory_bytes() // bytes_per_replica)
-    n = min(cores, fit)
-    if n < 2:
-        return None
-    ctx = mp.get_context("spawn")
-    barrier = ctx.Barrier(n)
-    out = ctx.Queue()
-    procs = [ctx.Process(target=_oracle_replica, args=(p, barrier, out)) for _ in range(n)]
-    for pr in procs:
-        pr.start()
-    res = []
-    deadline = time.time() + 1200
-    import queue
-    while len(res) < n:
-        try:
-            res.append(out.get(timeout=2))
-        except queue.Empty:
-            # a replica that died (or a run past the deadline) ends the measurement
-            if time.time() > deadline or any(pr.exitcode not in (None, 0) for pr in procs):
-                for pr in procs:
-                    if pr.is_alive():
-                        pr.terminate()
-                return None
-    for pr in procs:
-        pr.join(timeout=60)
-    est = max(1e3 * (tr + iters * (tc + tr)) for tr, tc in res)
-    return {"value": round(est / n, 3), "unit": "ms", "cores": n, "replicas": n,
-            "slowest_replica_solve_ms": round(est, 3),
-            "t_cycle_s_max": round(max(tc for _, tc in res), 3),
-            "sample": (f"{n} concurrent replicas of the single-core sample (one process per core), "
-                       f"slowest replica's solve estimate divided by {n}")}
+    u_all, it_all, t_all, used = oracle_solve(p, f, cores)
+    _, it1, t1, _ = oracle_solve(p, f, 1)
+    cpu = {"value": round(1e3 * t_all, 1), "unit": "ms", "cores": used, "kind": "oracle",
+           "sample": (f"one complete oracle solve of the {p.nx}x{p.ny}x{p.nz} problem to 1e-6 "
+                      f"({it_all} V(2,2) cycles) on {used} host threads (OpenMP over columns)"),
+           "oracle_iters": it_all, "cpu_model": cpu_model(),
+           "one_core": {"value": round(1e3 * t1, 1), "unit": "ms", "cores": 1, "oracle_iters": it1}}
+    del u_all
+    oracle.set_threads(cores)
+    t0 = time.perf_counter()
+    cx, cy, v = oracle.problem_coefficients(p)
+    ustar, it_s, hist, _ = oracle.mg_solve(f, cx, cy, v, p.nlevels, tol=1e-12, max_iter=40)
+    ref = {"mid": {"reference": f"oracle multigrid solve to {hist[-1]:.1e} ({it_s} cycles)",
+                   "rel_err": {k: rel_err(u, ustar) for k, u in sols.pop("mid").items()}}}
+    r = oracle.residual(sols["mid_headline_u"], f, cx, cy, v)
+    ref["mid"]["headline_rel_res_by_oracle"] = float(np.linalg.norm(r) / np.linalg.norm(f))
+    del ustar, r, sols["mid_headline_u"]
+    for key, prob in (("mixed", workloads.mixed()), ("learned", workloads.learned_target())):
+        if key not in sols:
+            continue
+        fx = prob.rhs()
+        cxx, cyy, vv = oracle.problem_coefficients(prob)
+        uex = spectral.exact_solve(fx, cxx, cyy, float(vv))
+        ref[key] = {"reference": "exact spectral solution (Fourier x Fourier x DCT-II)",
+                    "rel_err": {k: rel_err(u, uex) for k, u in sols.pop(key).items()}}
+        del fx, uex
+    if "batched" in sols:
+        errs = []
+        for prob, u in zip(workloads.batched(), sols.pop("batched")):
+            cxx, cyy, vv = oracle.problem_coefficients(prob)
+            errs.append(rel_err(u, spectral.exact_solve(prob.rhs(), cxx, cyy, float(vv))))
+        ref["batched"] = {"reference": "exact spectral solution of each problem",
+                          "rel_err_max": max(errs), "rel_err_median": float(np.median(errs))}
+    ref["seconds"] = round(time.perf_counter() - t0, 1)
+    return cpu, ref
 
 
-def bench_batched(tpmg, torch):
-    probs = workloads.batched()
-    ops = [tpmg.Operator.from_problem(p) for p in probs]
-    fs = [torch.from_numpy(p.rhs()).cuda() for p in probs]
-    us = [torch.zeros_like(f) for f in fs]
-    prm = tpmg.default_params(prec=tpmg.MIXED, tol=1e-6, max_iter=60)
-    handles = [o.op for o in ops]
-    for _ in range(2):
-        for u in us:
-            u.zero_()
-        res = tpmg.mg_solve_batched(handles, prm, fs, us)
-    times = []
-    for _ in range(3):
-        for u in us:
-            u.zero_()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        res = tpmg.mg_solve_batched(handles, prm, fs, us)
-        e1.record()
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-    seq = []
-    for _ in range(2):
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for o, f, u, p in zip(ops, fs, us, probs):
-            u.zero_()
-            tpmg.mg_solve(o.op, prm, f, u, p.n)
-        e1.record()
-        torch.cuda.synchronize()
-        seq.append(e0.elapsed_time(e1))
-    out = {"ms": round(min(times), 3), "sequential_single_solves_ms": round(min(seq), 3),
-           "problems": len(probs), "cells": int(sum(p.n for p in probs)),
-           "all_converged": all(r["converged"] for r in res["problems"]),
-           "iters_max": max(r["iters"] for r in res["problems"])}
-    for o in ops:
-        o.close()
-    return out
+def run_reference(args, rank, world):
+    """The reference arm: the oracle as it stands, one complete solve of the mid problem per step on
+    all host cores (OpenMP over columns). Rank 0 alone runs (replicas would time the same cores)."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    p = workloads.mid()
+    f = p.rhs()
+    cores = os.cpu_count() or 1
+    vals, iters, used = [], 0, cores
+    for s in range(args.warmup + args.steps):
+        _, iters, secs, used = oracle_solve(p, f, cores)
+        if s >= args.warmup:
+            vals.append(1e3 * secs)
+    value = float(np.mean(vals))
+    sample = (f"one complete oracle solve of the {p.nx}x{p.ny}x{p.nz} problem to 1e-6 ({iters} V(2,2) cycles) "
+              f"per step on {used} host threads (OpenMP over columns)")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 3),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": p.name, "nx": p.nx, "ny": p.ny, "nz": p.nz, "levels": p.nlevels,
+                       "solver": "V(2,2), rho 0.8, 2 coarse steps", "tol": 1e-6},
+            "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": used, "kind": "oracle",
+                             "sample": sample, "oracle_iters": iters, "cpu_model": cpu_model()},
+            "e2e": {"value": round(value, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -324,32 +300,76 @@ def nn_flops_per_voxel(cin: int) -> int:
     return 2 * 27 * (cin * 16 + 16 * 16 + 16 * 16 + 16)
 
 
-def bench_mixed(tpmg, torch):
-    """Mixed precision on its own workload (1024^2 x 128, lambda^2 = 1e4): FP32 V-cycles inside
-    double-word refinement at 1e-6 and 1e-10, error against a 1e-12 double-word solution; also with
-    the inner cycle's coarse levels holding BF16 values (coarse_bf16, a convergence measurement)."""
+def bench_batched(tpmg, torch, sols=None):
+    probs = workloads.batched()
+    ops = [tpmg.Operator.from_problem(p) for p in probs]
+    fs = [torch.from_numpy(p.rhs()).cuda() for p in probs]
+    us = [torch.zeros_like(f) for f in fs]
+    prm = tpmg.default_params(prec=tpmg.MIXED, tol=1e-6, max_iter=60)
+    handles = [o.op for o in ops]
+    for _ in range(2):
+        for u in us:
+            u.zero_()
+        res = tpmg.mg_solve_batched(handles, prm, fs, us)
+    times = []
+    for _ in range(3):
+        for u in us:
+            u.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        res = tpmg.mg_solve_batched(handles, prm, fs, us)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    if sols is not None:
+        sols["batched"] = [u.cpu().numpy() for u in us]
+    seq = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for o, f, u, p in zip(ops, fs, us, probs):
+            u.zero_()
+            tpmg.mg_solve(o.op, prm, f, u, p.n)
+        e1.record()
+        torch.cuda.synchronize()
+        seq.append(e0.elapsed_time(e1))
+    out = {"ms": round(min(times), 3), "sequential_single_solves_ms": round(min(seq), 3),
+           "problems": len(probs), "cells": int(sum(p.n for p in probs)),
+           "all_converged": all(r["converged"] for r in res["problems"]),
+           "iters_max": max(r["iters"] for r in res["problems"])}
+    for o in ops:
+        o.close()
+    return out
+
+
+def bench_mixed(tpmg, torch, sols=None):
+    """The mixed-precision workload (1024^2 x 128, lambda^2 = 1e4): FP32 V-cycles inside double-word
+    refinement at 1e-6 and 1e-10, beside native FP64 and double-word multigrid at 1e-6; also with the
+    inner cycle's coarse levels holding BF16 values (coarse_bf16, a convergence measurement). Each
+    solution's error against the exact spectral solution is measured in the CPU leg."""
     p = workloads.mixed()
     op = tpmg.Operator.from_problem(p)
     f = torch.from_numpy(p.rhs()).cuda()
     n = p.n
-    ustar = torch.zeros_like(f)
-    tpmg.mg_solve(op.op, tpmg.default_params(prec=tpmg.DW, tol=1e-12, max_iter=100), f, ustar, n)
-    nrm = float(torch.linalg.vector_norm(ustar).item())
     out = {"workload": p.name}
-    for name, prec, tol, bf in [("dw_1e-6", tpmg.DW, 1e-6, 0), ("mixed_1e-6", tpmg.MIXED, 1e-6, 0),
-                                ("mixed_1e-10", tpmg.MIXED, 1e-10, 0),
+    keep = {}
+    for name, prec, tol, bf in [("f64_1e-6", tpmg.F64, 1e-6, 0), ("dw_1e-6", tpmg.DW, 1e-6, 0),
+                                ("mixed_1e-6", tpmg.MIXED, 1e-6, 0), ("mixed_1e-10", tpmg.MIXED, 1e-10, 0),
                                 ("mixed_1e-6_bf16_coarse", tpmg.MIXED, 1e-6, 1),
                                 ("mixed_1e-10_bf16_coarse", tpmg.MIXED, 1e-10, 1)]:
-        prm = tpmg.default_params(prec=prec, tol=tol, max_iter=100, coarse_bf16=bf)
+        prm = tpmg.default_params(prec=prec, tol=tol, max_iter=100, coarse_bf16=bf, zero_guess=1)
         u = torch.zeros_like(f)
         ms = []
         for _ in range(3):
-            u.zero_()
             r = tpmg.mg_solve(op.op, prm, f, u, n)
             ms.append(r["ms"])
-        err = float(torch.linalg.vector_norm(u - ustar).item()) / nrm
-        out[name] = {"ms": round(min(ms[1:]), 3), "iters": r["iters"], "rel_res": r["rel_res"],
-                     "rel_err_vs_u_star": err}
+        out[name] = {"ms": round(min(ms[1:]), 3), "iters": r["iters"], "rel_res": r["rel_res"]}
+        if sols is not None and not bf:
+            keep[name] = u.cpu().numpy()
+    if sols is not None:
+        sols["mixed"] = keep
     op.close()
     return out
 
@@ -380,10 +400,10 @@ def bench_paper_shaped(tpmg, torch):
     return out
 
 
-def bench_learned(tpmg, torch):
+def bench_learned(tpmg, torch, sols=None):
     """The learned stage: pairs from the multigrid solver on 256^2 x 64 crops, Adam on the residual
-    loss, then flexible CG with and without the network on 2048^2 x 64 (h = 1/2048), beside plain
-    double-word multigrid and the mixed solver, all to 1e-6."""
+    loss, then flexible CG with and without the network on 2048^2 x 64 (h = 1/2048), beside native
+    FP64, double-word and mixed multigrid, all to 1e-6."""
     from paper_1402_3545_gb300 import learned
     cfg = learned.TrainConfig(n_problems=8, steps=400)
     t0 = time.perf_counter()
@@ -415,55 +435,42 @@ def bench_learned(tpmg, torch):
         "held_out_relative": {k: round(v, 5) for k, v in ev.items()}},
         "nn_forward": {"ms": round(t_fwd, 3), "flop_per_voxel": fl,
                        "tflops": round(fl * p.n / (t_fwd * 1e-3) / 1e12, 2)}}
-    r = learned.fcg_compare(p, net, tol=1e-6, reps=2)
+    keep = {} if sols is not None else None
+    r = learned.fcg_compare(p, net, tol=1e-6, reps=2, solutions=keep)
     out.update(r)
     op = tpmg.Operator.from_problem(p)
     f = torch.from_numpy(p.rhs()).cuda()
-    for name, prec in [("mg_dw", tpmg.DW), ("mg_mixed", tpmg.MIXED)]:
-        prm = tpmg.default_params(prec=prec, tol=1e-6, max_iter=100)
+    for name, prec in [("mg_f64", tpmg.F64), ("mg_dw", tpmg.DW), ("mg_mixed", tpmg.MIXED)]:
+        prm = tpmg.default_params(prec=prec, tol=1e-6, max_iter=100, zero_guess=1)
         u = torch.zeros_like(f)
         ms = []
         for _ in range(2):
-            u.zero_()
             res = tpmg.mg_solve(op.op, prm, f, u, p.n)
             ms.append(res["ms"])
         out[name] = {"ms": round(min(ms), 3), "iters": res["iters"], "rel_res": res["rel_res"]}
+        if keep is not None:
+            keep[name] = u.cpu().numpy()
+    if sols is not None:
+        sols["learned"] = keep
     op.close()
     net.close()
     return out
 
 
-def run_reference(args, rank, world):
-    if rank != 0:  # replicas of the oracle would time the same host cores: rank 0 alone runs
-        return
-    p = workloads.mid()
-    f = p.rhs()
-    import oracle
-    oracle.build()
-    vals, info = [], None
-    for s in range(args.warmup + args.steps):
-        est, info = cpu_baseline_sample(p, f, 6)
-        if s >= args.warmup:
-            vals.append(est)
-    value = float(np.mean(vals))
-    sample = (f"one oracle V(2,2) cycle + one residual on the full {p.nx}x{p.ny}x{p.nz} grid per step, "
-              f"scaled to a full solve with the oracle's iteration count ({info['oracle_iters']})")
-    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "ms", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 3),
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": p.name, "nx": p.nx, "ny": p.ny, "nz": p.nz, "levels": p.nlevels,
-                       "solver": "V(2,2), rho 0.8, 2 coarse steps", "tol": 1e-6},
-            "cpu_baseline": {"value": round(value, 3), "unit": "ms", "cores": 1, "kind": "oracle",
-                             "sample": sample, **info},
-            "e2e": {"value": round(value, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
 def run_kernel_only(args):
-    """A few launches of one finest-level kernel of the mid problem, for a profiler capture."""
+    """A few launches of one finest-level kernel of the mid problem, for a profiler capture; or the
+    measured arithmetic rates (alu_rate); or one host-buffer solve's copies and transposes."""
     import torch
     from paper_1402_3545_gb300 import tpmg
+    if args.kernel_only == "alu_rate":
+        out = {"kernel": "alu_rate", "unit": "T operations/s (a multiply-add counts once)"}
+        for name, which in [("fp64_fma", tpmg.ALU_FP64_FMA), ("fp64_add", tpmg.ALU_FP64_ADD),
+                            ("fp64_mul", tpmg.ALU_FP64_MUL), ("fp32_fma", tpmg.ALU_FP32_FMA)]:
+            rate, ms = tpmg.measure_alu_rate(which, reps=max(args.steps, 1))
+            out[name] = round(rate / 1e12, 4)
+            out[name + "_ms"] = round(ms, 3)
+        print(json.dumps(out), flush=True)
+        return
     if args.kernel_only == "nn_forward":
         # the learned stage's forward pass on one 256^2 x 64 training crop (4.2 M voxels)
         from paper_1402_3545_gb300 import learned
@@ -484,13 +491,24 @@ def run_kernel_only(args):
                           "tflops": round(nn_flops_per_voxel(2) * nvox / (ms * 1e-3) / 1e12, 2)}), flush=True)
         net.close()
         return
+    p = workloads.mid()
+    op = tpmg.Operator.from_problem(p)
+    if args.kernel_only == "transpose":
+        # host-buffer solves with the vertically contiguous host layout (copies + transposes + solve)
+        prm = tpmg.default_params(prec=tpmg.F64, tol=1e-6, max_iter=100, zero_guess=1)
+        f_h = torch.from_numpy(np.ascontiguousarray(p.rhs().transpose(1, 2, 0))).reshape(-1).pin_memory()
+        u_h = torch.zeros_like(f_h).pin_memory()
+        for _ in range(max(args.steps, 1)):
+            r = tpmg.mg_solve_host(op.op, prm, f_h, u_h, p.n, layout=tpmg.LAYOUT_Z)
+        print(json.dumps({"kernel": "transpose", "workload": p.name, "ms": round(r["ms"], 3),
+                          "ms_io": round(r["ms_io"], 3)}), flush=True)
+        op.close()
+        return
     prec = {"dw": tpmg.DW, "f32": tpmg.F32, "f64": tpmg.F64}[args.precision]
     kid = {"smooth": tpmg.K_SMOOTH, "residual": tpmg.K_RESIDUAL, "restrict_smooth": tpmg.K_RESTRICT_SMOOTH,
            "prolongate": tpmg.K_PROLONGATE, "line_solve": tpmg.K_LINE_SOLVE, "cg_spmv": tpmg.K_CG_SPMV,
            "cg_tridiag": tpmg.K_CG_TRIDIAG, "residual_restrict": tpmg.K_RESIDUAL_RESTRICT,
            "apply_A": tpmg.K_APPLY_A}[args.kernel_only]
-    p = workloads.mid()
-    op = tpmg.Operator.from_problem(p)
     tpmg.op_reserve(op.op, tpmg.MIXED if prec == tpmg.F32 else prec)
     for l in range(1, op.L + 1):
         tpmg.set_variant(op.op, prec, l, args.variant)
@@ -501,9 +519,24 @@ def run_kernel_only(args):
     op.close()
 
 
+def hbm_roofline(tpmg, op, prec, n, peaks, peak_kind, traffic, variant, label, value_bytes):
+    """HBM roofline of the finest-level Smooth in precision prec: algorithmic bytes (read u, f; write
+    u') over its CUDA-event launch time, against the measured copy rate."""
+    t = tpmg.time_kernel(op.op, prec, tpmg.K_SMOOTH, reps=20)
+    b = 3 * value_bytes * n
+    ach = b / (t * 1e-3) / 1e9
+    key = ("smooth", label, int(variant) if variant is not None else -1, "mid_512x512x128")
+    tr = traffic.get(key)
+    return {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": tr[0] if tr else None,
+            "traffic_source": (f"ncu capture: {tr[1]}" if tr else None),
+            "kernel": f"finest-level {label} Smooth (tile variant {variant})", "peak_source": peak_kind,
+            "bytes_per_launch": b, "ms_per_launch": round(t, 4)}
+
+
 def run_ours(args, rank, world, dist):
     import torch
-    from paper_1402_3545_gb300 import tpmg
+    from paper_1402_3545_gb300 import autotune, tpmg
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -512,16 +545,18 @@ def run_ours(args, rank, world, dist):
     f = p.rhs()
     n = p.n
     op = tpmg.Operator.from_problem(p)
-    prec = tpmg.DW
+    prec = {"f64": tpmg.F64, "dw": tpmg.DW, "mixed": tpmg.MIXED}[args.solve_precision if args.solve_only else "f64"]
     prm = tpmg.default_params(prec=prec, tol=1e-6, max_iter=100, zero_guess=1)
     tpmg.op_reserve(op.op, prec)
-    from paper_1402_3545_gb300 import autotune
-    variants_dw = autotune.tune(op, prec, lambda_varies=True)
+    tuned = {}
+    tuned["f64"] = autotune.tune(op, tpmg.F64, lambda_varies=True)
+    if prec != tpmg.F64:
+        tuned["dw"] = autotune.tune(op, tpmg.DW, lambda_varies=True)
     fd = torch.from_numpy(f).to(dev)
     u = torch.zeros_like(fd)
     stream = torch.cuda.current_stream()
 
-    def solve():  # from u = 0 (zero_guess: the solve clears its own copy of u, u is output only)
+    def solve():  # from u = 0 (zero_guess: the solve clears u itself, u is output only)
         return tpmg.mg_solve(op.op, prm, fd, u, n)
 
     for _ in range(max(args.warmup, 3)):
@@ -555,53 +590,44 @@ def run_ours(args, rank, world, dist):
     if args.solve_only:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": round(value, 4), "unit": "ms", "iters": iters[-1],
-                              "gpu_launches": int(launches), "solve_only": True}), flush=True)
+                              "precision": args.solve_precision, "gpu_launches": int(launches),
+                              "solve_only": True}), flush=True)
         op.close()
         return
+    sols = {"mid": {"f64": u.cpu().numpy()}}
+    sols["mid_headline_u"] = sols["mid"]["f64"]
 
-    # dominant kernel: the finest-level Smooth (4 of the 5 fine-level sweeps of each cycle)
-    t_smooth = tpmg.time_kernel(op.op, prec, tpmg.K_SMOOTH, reps=20)
+    # dominant kernel: the finest-level native FP64 Smooth (4 of the 5 fine-level sweeps of each
+    # cycle), bound by the FP64 pipe: FP64 flops over its CUDA-event launch time, against twice the
+    # FP64 multiply-add rate measured on this GPU in this process (a multiply-add is 2 flops)
     peaks, peak_kind = measured_peaks()
-    bytes_smooth = 3 * 8 * n  # read u, f; write u' (8-byte values)
-    achieved = bytes_smooth / (t_smooth * 1e-3) / 1e9
-    finest_variant = variants_dw[-1] if variants_dw else None
-    kernel_ms = {name: round(tpmg.time_kernel(op.op, prec, kid, reps=10), 4) for name, kid in [
-        ("residual", tpmg.K_RESIDUAL), ("restrict_smooth", tpmg.K_RESTRICT_SMOOTH),
-        ("residual_restrict_fused", tpmg.K_RESIDUAL_RESTRICT), ("apply_A", tpmg.K_APPLY_A),
-        ("prolongate", tpmg.K_PROLONGATE), ("cg_spmv", tpmg.K_CG_SPMV), ("cg_tridiag", tpmg.K_CG_TRIDIAG)]}
-    kernel_ms["smooth"] = round(t_smooth, 4)
-    tpmg.op_reserve(op.op, tpmg.MIXED)
-    variants_f32 = autotune.tune(op, tpmg.F32, lambda_varies=True)
-    kernel_ms_f32 = {name: round(tpmg.time_kernel(op.op, tpmg.F32, kid, reps=10), 4) for name, kid in [
-        ("smooth", tpmg.K_SMOOTH), ("residual", tpmg.K_RESIDUAL), ("line_solve", tpmg.K_LINE_SOLVE),
-        ("restrict_smooth", tpmg.K_RESTRICT_SMOOTH), ("residual_restrict_fused", tpmg.K_RESIDUAL_RESTRICT),
-        ("prolongate", tpmg.K_PROLONGATE)]}
-    # native FP64 Smooth against the FP64 ALU: per cell the stencil residual (3 FMAs and 4 adds),
-    # the forward elimination (FMA and multiply), the back substitution (2 FMAs) and the norm (FMA)
-    # are 12 FP64 operations; GB300's nominal FP64 rate is 1.25 TFLOP/s (0.625 T FMA-or-add/s)
-    tpmg.op_reserve(op.op, tpmg.F64)
-    t_smooth64 = tpmg.time_kernel(op.op, tpmg.F64, tpmg.K_SMOOTH, reps=5)
-    ops64 = 12 * n
-    roofline_f64 = {"bound": "alu", "kernel": "finest-level native FP64 Smooth", "unit": "T FP64 ops/s",
-                    "achieved": round(ops64 / (t_smooth64 * 1e-3) / 1e12, 4), "peak": 0.625,
-                    "frac": round(ops64 / (t_smooth64 * 1e-3) / 1e12 / 0.625, 4), "ms_per_launch": round(t_smooth64, 4),
-                    "ops_per_launch": ops64, "peak_source": "nominal 1.25 TFLOP/s FP64 (FMA or add per op)",
-                    "hbm_frac_same_launch": round(3 * 8 * n / (t_smooth64 * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
-    n_smooth = 4 * iters[-1] + 1
-    # DRAM bytes of one launch from the ncu capture summarised in
-    # profiles/k_sweep_x2_dw_smooth_mid_512x512x128.md (null for a variant without a capture)
-    traffic = PROFILED_SMOOTH_TRAFFIC.get(finest_variant)
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
-                "kernel": f"finest-level double-word Smooth (tile variant {finest_variant})",
-                "peak_source": peak_kind, "bytes_per_launch": bytes_smooth, "ms_per_launch": round(t_smooth, 4),
-                "share_of_solve": round(n_smooth * t_smooth / ms_per_step, 3),
-                # lambda^2 varies over the level, so the Thomas factors 1/m_k and v/m_k are read per cell
-                "bytes_with_factors": 5 * 8 * n,
-                "frac_with_factors": round(5 * 8 * n / (t_smooth * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
+    traffic = read_traffic()
+    fma_rate, _ = tpmg.measure_alu_rate(tpmg.ALU_FP64_FMA)
+    add_rate, _ = tpmg.measure_alu_rate(tpmg.ALU_FP64_ADD)
+    t_s64 = tpmg.time_kernel(op.op, tpmg.F64, tpmg.K_SMOOTH, reps=20)
+    v64 = tuned["f64"][-1] if tuned["f64"] else None
+    ach = SMOOTH_F64_FLOPS * n / (t_s64 * 1e-3) / 1e12
+    peak64 = 2.0 * fma_rate / 1e12
+    tr = traffic.get(("smooth", "f64", int(v64) if v64 is not None else -1, "mid_512x512x128"))
+    roofline = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak64, 4), "unit": "TFLOP/s",
+                "frac": round(ach / peak64, 4), "traffic": tr[0] if tr else None,
+                "traffic_source": (f"ncu capture: {tr[1]}" if tr else None),
+                "kernel": f"finest-level native FP64 Smooth (tile variant {v64})",
+                "peak_source": ("measured in this run: FP64 multiply-add rate of tpmg_measure_alu_rate x 2 "
+                                f"({fma_rate / 1e12:.4f} T FMA/s; FP64 add {add_rate / 1e12:.4f} T/s)"),
+                "flops_per_cell": SMOOTH_F64_FLOPS, "instructions_per_cell": SMOOTH_F64_INSTR,
+                "pipe_frac": round(SMOOTH_F64_INSTR * n / (t_s64 * 1e-3) / fma_rate, 4),
+                "ms_per_launch": round(t_s64, 4), "flops_per_launch": SMOOTH_F64_FLOPS * n,
+                "share_of_solve": round((4 * iters[-1] + 1) * t_s64 / ms_per_step, 3),
+                "hbm_frac_same_launch": round(3 * 8 * n / (t_s64 * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                "hbm_peak_source": peak_kind}
+    kernel_ms = {name: round(tpmg.time_kernel(op.op, tpmg.F64, kid, reps=10), 4) for name, kid in [
+        ("residual", tpmg.K_RESIDUAL), ("residual_restrict_fused", tpmg.K_RESIDUAL_RESTRICT),
+        ("prolongate", tpmg.K_PROLONGATE), ("apply_A", tpmg.K_APPLY_A), ("line_solve", tpmg.K_LINE_SOLVE),
+        ("cg_spmv", tpmg.K_CG_SPMV), ("cg_tridiag", tpmg.K_CG_TRIDIAG)]}
+    kernel_ms["smooth"] = round(t_s64, 4)
 
     # the whole solve's useful bandwidth: the paper's per-kernel memory references x 8 B per solve
-    # (double-word and native FP64 levels both store 8-byte values) over the solve time
     level_cells = [0] + [op.level_n(l) for l in range(1, op.L + 1)]
     solve_bytes = 8 * solve_memrefs(level_cells, iters[-1])
     solve_hbm = {"bytes_per_solve": int(solve_bytes), "ms_per_solve": round(value, 4),
@@ -609,107 +635,84 @@ def run_ours(args, rank, world, dist):
                  "frac": round(solve_bytes / (value * 1e-3) / 1e9 / peaks["hbm_gbs"], 4), "peak_source": peak_kind,
                  "model": ("memory references of the paper's kernels (Smooth and Residual 3 per cell, "
                            "RestrictSmooth 6 per coarse cell, Prolongate 2.25 per fine cell) x 8 B, "
-                           f"{iters[-1]} V(2,2) cycles + the first Smooth; the fused Residual+RestrictSmooth "
-                           "moves less than its two kernels' share")}
+                           f"{iters[-1]} V(2,2) cycles + the first Smooth")}
 
-    # end to end through the public API with host buffers, two ways: (a) the solve reads f from
-    # page-locked host memory and writes u back there in its first and last kernels; (b) explicit
-    # copies around a device solve (H2D of f, solve, D2H of u). Both start from u = 0 (zero_guess)
-    # and move 8 bytes per cell each way; the faster is reported.
-    f_h = torch.from_numpy(f).pin_memory()
+    # end to end through the public API with host buffers: tpmg_mg_solve_host on page-locked host
+    # fields in the vertically contiguous layout of a CPU code (copy of f to the device, transpose,
+    # native FP64 solve, transpose, copy of u back), the paper's "total solution time" (Sec. 5.1)
+    f_h = torch.from_numpy(np.ascontiguousarray(f.transpose(1, 2, 0))).reshape(-1).pin_memory()
     u_h = torch.zeros_like(f_h).pin_memory()
+    f_hx = torch.from_numpy(f).reshape(-1).pin_memory()
     for _ in range(2):
-        tpmg.mg_solve_host(op.op, prm, f_h, u_h, n)
+        tpmg.mg_solve_host(op.op, prm, f_h, u_h, n, layout=tpmg.LAYOUT_Z)
     torch.cuda.synchronize()
-    e0.record(stream)
+    e2e_ms, io_ms = [], []
     for _ in range(args.steps):
-        tpmg.mg_solve_host(op.op, prm, f_h, u_h, n)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_host_ms = e0.elapsed_time(e1) / args.steps
-    for _ in range(2):
-        fd.copy_(f_h, non_blocking=True)
-        solve()
-        u_h.copy_(u, non_blocking=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        fd.copy_(f_h, non_blocking=True)
-        solve()
-        u_h.copy_(u, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_copy_ms = e0.elapsed_time(e1) / args.steps
-    if e2e_host_ms <= e2e_copy_ms:
-        e2e_ms, e2e_path = e2e_host_ms, "tpmg_mg_solve on page-locked host f and u"
-    else:
-        e2e_ms, e2e_path = e2e_copy_ms, "cudaMemcpyAsync of f, tpmg_mg_solve on device fields, cudaMemcpyAsync of u"
+        r = tpmg.mg_solve_host(op.op, prm, f_h, u_h, n, layout=tpmg.LAYOUT_Z)
+        e2e_ms.append(r["ms"])
+        io_ms.append(r["ms_io"])
+    rx = [tpmg.mg_solve_host(op.op, prm, f_hx, u_h, n, layout=tpmg.LAYOUT_X)["ms"] for _ in range(2)]
+    e2e = {"value": round(float(np.mean(e2e_ms)), 4), "unit": "ms", "h2d_bytes_per_step": 8 * n,
+           "d2h_bytes_per_step": 8 * n,
+           "path": ("tpmg_mg_solve_host, native FP64, page-locked host f and u in the vertically contiguous "
+                    "layout: copy + transpose in, solve, transpose + copy out"),
+           "copy_and_transpose_ms": round(float(np.mean(io_ms)), 4),
+           "x_layout_ms": round(min(rx), 4)}
 
-    # error of each solution against u*, a double-word solve of the same problem to a 1e-12
-    # relative residual (outside every timed region)
-    ustar = torch.zeros_like(fd)
-    tpmg.mg_solve(op.op, tpmg.default_params(prec=tpmg.DW, tol=1e-12, max_iter=100), fd, ustar, n)
-    ustar_norm = float(torch.linalg.vector_norm(ustar).item())
-
-    def err_vs_ustar(x):
-        return float(torch.linalg.vector_norm(x - ustar).item()) / ustar_norm
-
-    u.zero_()
-    solve()
-    headline_err = err_vs_ustar(u)
-
-    # the other precisions on the same problem (one solve each, after a warm-up solve)
+    # the other precisions and CG on the same problem (after a warm-up solve each); DW and the
+    # mixed solver's FP32 Smooth get their own HBM rooflines
     variants = {}
-    for name, vprec, tol, bf in [("f64_native", tpmg.F64, 1e-6, 0), ("mixed_fp32_inner", tpmg.MIXED, 1e-6, 0),
-                                 ("mixed_fp32_inner_1e-10", tpmg.MIXED, 1e-10, 0),
-                                 ("mixed_bf16_coarse", tpmg.MIXED, 1e-6, 1)]:
-        vp = tpmg.default_params(prec=vprec, tol=tol, max_iter=100, coarse_bf16=bf)
-        for _ in range(2):
-            u.zero_()
+    tuned.setdefault("dw", autotune.tune(op, tpmg.DW, lambda_varies=True))
+    tpmg.op_reserve(op.op, tpmg.MIXED)
+    tuned["f32"] = autotune.tune(op, tpmg.F32, lambda_varies=True)
+    for name, vprec, tol, bf in [("dw", tpmg.DW, 1e-6, 0), ("mixed", tpmg.MIXED, 1e-6, 0),
+                                 ("mixed_1e-10", tpmg.MIXED, 1e-10, 0), ("mixed_bf16_coarse", tpmg.MIXED, 1e-6, 1)]:
+        vp = tpmg.default_params(prec=vprec, tol=tol, max_iter=100, coarse_bf16=bf, zero_guess=1)
+        ms = []
+        for _ in range(3):
             r = tpmg.mg_solve(op.op, vp, fd, u, n)
-        variants[name] = {"ms": round(r["ms"], 3), "iters": r["iters"], "rel_res": r["rel_res"],
-                          "rel_err_vs_u_star": err_vs_ustar(u)}
-    u.zero_()
-    r = tpmg.cg_solve(op.op, tpmg.default_params(prec=tpmg.DW, tol=1e-6, max_iter=5000), fd, u, n)
-    variants["cg_dw"] = {"ms": round(r["ms"], 3), "iters": r["iters"], "rel_res": r["rel_res"],
-                         "rel_err_vs_u_star": err_vs_ustar(u)}
-    del ustar
-
-    # batched workload: 64 problems of drawn sizes in one persistent launch vs one solve after another
-    variants["batched_64"] = bench_batched(tpmg, torch)
-    variants["mixed_1024x1024x128"] = bench_mixed(tpmg, torch)
+            ms.append(r["ms"])
+        variants[name] = {"ms": round(min(ms[1:]), 3), "iters": r["iters"], "rel_res": r["rel_res"],
+                          "speedup_vs_f64": round(value / min(ms[1:]), 3)}
+        if not bf:
+            sols["mid"][name] = u.cpu().numpy()
+    variants["dw"]["roofline"] = hbm_roofline(tpmg, op, tpmg.DW, n, peaks, peak_kind, traffic, tuned["dw"][-1],
+                                              "dw", 8)
+    variants["mixed"]["roofline_f32_smooth"] = hbm_roofline(tpmg, op, tpmg.F32, n, peaks, peak_kind, traffic,
+                                                            tuned["f32"][-1], "f32", 4)
+    variants["dw"]["kernel_ms"] = {name: round(tpmg.time_kernel(op.op, tpmg.DW, kid, reps=10), 4) for name, kid in [
+        ("smooth", tpmg.K_SMOOTH), ("residual", tpmg.K_RESIDUAL), ("residual_restrict_fused", tpmg.K_RESIDUAL_RESTRICT),
+        ("prolongate", tpmg.K_PROLONGATE), ("apply_A", tpmg.K_APPLY_A), ("cg_spmv", tpmg.K_CG_SPMV),
+        ("cg_tridiag", tpmg.K_CG_TRIDIAG)]}
+    variants["mixed"]["kernel_ms_f32"] = {name: round(tpmg.time_kernel(op.op, tpmg.F32, kid, reps=10), 4)
+                                          for name, kid in [
+        ("smooth", tpmg.K_SMOOTH), ("residual", tpmg.K_RESIDUAL), ("line_solve", tpmg.K_LINE_SOLVE),
+        ("residual_restrict_fused", tpmg.K_RESIDUAL_RESTRICT), ("prolongate", tpmg.K_PROLONGATE)]}
+    for name, vprec in [("cg_f64", tpmg.F64), ("cg_dw", tpmg.DW)]:
+        r = tpmg.cg_solve(op.op, tpmg.default_params(prec=vprec, tol=1e-6, max_iter=5000, zero_guess=1), fd, u, n)
+        variants[name] = {"ms": round(r["ms"], 3), "iters": r["iters"], "rel_res": r["rel_res"]}
+        sols["mid"][name] = u.cpu().numpy()
+    variants["batched_64"] = bench_batched(tpmg, torch, sols)
+    variants["mixed_1024x1024x128"] = bench_mixed(tpmg, torch, sols)
     variants["paper_shaped_512x512x128"] = bench_paper_shaped(tpmg, torch)
-    variants["learned_2048x2048x64"] = bench_learned(tpmg, torch)
+    variants["learned_2048x2048x64"] = bench_learned(tpmg, torch, sols)
 
-    cpu = None
+    cpu, errors = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, info = cpu_baseline_sample(p, f, iters[-1])
-        cpu = {"value": round(est, 3), "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": (f"one oracle V(2,2) cycle + one residual on the full {p.nx}x{p.ny}x{p.nz} grid, "
-                          f"scaled to a full solve with the oracle's iteration count"), **info}
-        # the same sample on all host cores at once (replicas; peak about 10 FP64 fields each)
-        allc = cpu_baseline_all_cores(p, info["oracle_iters"], 10 * 8 * p.n)
-        if allc is not None:
-            cpu["all_cores"] = allc
+        cpu, errors = cpu_leg(p, f, sols)
+    del sols
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": False,
-                "scaling": "weak", "vs_baseline": None,
-                "dtype": "dw (FP64 storage, double-word fp32 pair arithmetic)", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": p.name, "nx": p.nx, "ny": p.ny, "nz": p.nz, "levels": op.L,
-                           "solver": "V(2,2), rho 0.8, 2 coarse steps", "tol": 1e-6, "precision": "DW",
-                           "parallelism": f"replicas{world}",
+                           "solver": "V(2,2), rho 0.8, 2 coarse steps", "tol": 1e-6,
+                           "precision": "native FP64", "parallelism": f"replicas{world}",
                            "l2": "inputs larger than L2 (268 MB per FP64 field > 129 MB)"},
-                "iters": iters[-1], "rel_err_vs_u_star": headline_err,
-                "roofline": roofline, "solve_hbm": solve_hbm, "roofline_f64": roofline_f64,
-                "kernel_ms": kernel_ms,
-                "kernel_ms_f32": kernel_ms_f32,
-                "tile_variants": {"dw": variants_dw, "f32": variants_f32}, "variants": variants,
-                "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": 8 * n,
-                        "d2h_bytes_per_step": 8 * n, "path": e2e_path,
-                        "host_fields_ms": round(e2e_host_ms, 4), "explicit_copies_ms": round(e2e_copy_ms, 4)},
-                "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches)}
+                "iters": iters[-1], "roofline": roofline, "solve_hbm": solve_hbm, "kernel_ms": kernel_ms,
+                "tile_variants": tuned, "variants": variants, "errors_vs_reference": errors,
+                "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": int(launches)}
         print(json.dumps(line), flush=True)
     op.close()
 

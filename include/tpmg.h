@@ -206,6 +206,22 @@ void tpmg_default_params(tpmg_params* p);
  * TPMG_ERR_NONFINITE (u then holds the last iterate), or an argument/CUDA error. */
 tpmg_status tpmg_mg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, void* u,
                           tpmg_info* info, void* stream);
+/* Host-buffer solve, the paper's "total solution time" path (Sec. 5.1, Table SingleGPUTiming: the
+ * right-hand side copied to the device and transposed from the vertically contiguous layout of the
+ * CPU code to the horizontally contiguous one of Eq. (13), the solve, the solution transposed and
+ * copied back). f_host, u_host: HOST arrays of the finest level's nx*ny*nz values (double; float for
+ * TPMG_F32), in layout TPMG_LAYOUT_X (x fastest, index (k*ny + j)*nx + i, as on the device) or
+ * TPMG_LAYOUT_Z (z fastest: column c = j*nx + i holds its nz values at c*nz .. c*nz + nz-1).
+ * Page-locked memory (cudaHostAlloc) lets the copies run at the link's rate; pageable memory works
+ * too, with the driver's staging. u_host is read as the initial guess unless prm->zero_guess, and
+ * receives the final iterate (also on TPMG_ERR_NOT_CONVERGED / TPMG_ERR_NONFINITE). The copies,
+ * the transposes (one tiled kernel each way) and the solve (tpmg_mg_solve on library-owned device
+ * fields, allocated on the first call) are ordered on `stream`; returns after u_host is written.
+ * info->ms (if info) is the device time of the whole call; *ms_io (if ms_io) the part spent in the
+ * copies and transposes. Same return values as tpmg_mg_solve. */
+typedef enum { TPMG_LAYOUT_X = 0, TPMG_LAYOUT_Z = 1 } tpmg_layout;
+tpmg_status tpmg_mg_solve_host(tpmg_op* op, const tpmg_params* prm, int layout, const void* f_host,
+                               void* u_host, tpmg_info* info, double* ms_io, void* stream);
 /* One V-cycle from u (in place), for testing a cycle against a reference. */
 tpmg_status tpmg_vcycle(tpmg_op* op, const tpmg_params* prm, const void* f, void* u, void* stream);
 /* Line-preconditioned CG (Sec. 2.2) with the fused kernels of Sec. 3.1. prec: TPMG_F64, TPMG_F32

@@ -99,6 +99,8 @@ struct tpmg_op {
     void* fcg_sc = nullptr;    // device scalars of flexible CG
     void* fcg_host = nullptr;  // pinned copy
     void* fcgbuf[3] = {};      // flexible CG scratch vectors (double-word)
+    void* hio[3] = {};         // host-buffer solves: device f, u (finest level) and a transpose buffer
+    cudaEvent_t hev[4] = {};   // host-buffer solves: start, solve start, solve end, end
 };
 
 // ---------------------------------------------------------------- helpers
@@ -813,6 +815,9 @@ tpmg_status tpmg_destroy_operator(tpmg_op* op) {
     if (op->cap_stream) cudaStreamDestroy(op->cap_stream);
     if (op->ev0) cudaEventDestroy(op->ev0);
     if (op->ev1) cudaEventDestroy(op->ev1);
+    for (int t = 0; t < 3; ++t) dfree(op->hio[t]);
+    for (int t = 0; t < 4; ++t)
+        if (op->hev[t]) cudaEventDestroy(op->hev[t]);
     delete op;
     return TPMG_OK;
 }
@@ -1189,6 +1194,73 @@ tpmg_status tpmg_mg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, vo
     CK(cudaEventRecord(op->ev1, s));
     CK(cudaGetLastError());
     return finish_info(op, info, s);
+}
+
+// Host fields (Sec. 5.1, "total solution time"): f is copied to the device -- transposed there
+// from the vertically contiguous layout when asked --, the device solve runs, and u goes back the
+// same way. Every step is ordered on `stream`.
+tpmg_status tpmg_mg_solve_host(tpmg_op* op, const tpmg_params* prm, int layout, const void* f_host, void* u_host,
+                               tpmg_info* info, double* ms_io, void* stream) {
+    TRY(check_params(op, prm));
+    if (!f_host || !u_host) return set_err(TPMG_ERR_ARG, "NULL field");
+    if (layout != TPMG_LAYOUT_X && layout != TPMG_LAYOUT_Z) return set_err(TPMG_ERR_ARG, "unknown layout");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = op->g.L;
+    const size_t n = lvl_cells(op, L), ncol = (size_t)op->g.nx * op->g.ny, nz = (size_t)op->g.nz;
+    const bool f32 = prm->prec == TPMG_F32;
+    const size_t eb = f32 ? sizeof(float) : sizeof(double), bytes = n * eb;
+    // sized for 8-byte values whatever the precision, so a later call of another precision fits
+    for (int t = 0; t < (layout == TPMG_LAYOUT_Z ? 3 : 2); ++t) TRY(dalloc(&op->hio[t], n * sizeof(double)));
+    for (int t = 0; t < 4; ++t)
+        if (!op->hev[t]) CK(cudaEventCreate(&op->hev[t]));
+    void* fd = op->hio[0];
+    void* ud = op->hio[1];
+    // one field in: host -> device, then (z-contiguous host layout) columns-by-planes -> planes-by-columns
+    auto field_in = [&](const void* h, void* d) -> tpmg_status {
+        if (layout == TPMG_LAYOUT_X) {
+            CK(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s));
+        } else {
+            CK(cudaMemcpyAsync(op->hio[2], h, bytes, cudaMemcpyHostToDevice, s));
+            if (f32) launch_transpose<float>((const float*)op->hio[2], (float*)d, ncol, nz, s);
+            else launch_transpose<double>((const double*)op->hio[2], (double*)d, ncol, nz, s);
+        }
+        return TPMG_OK;
+    };
+    CK(cudaEventRecord(op->hev[0], s));
+    TRY(field_in(f_host, fd));
+    if (!prm->zero_guess) TRY(field_in(u_host, ud));
+    CK(cudaEventRecord(op->hev[1], s));
+    tpmg_info inner{};
+    if (info) {
+        inner.history = info->history;
+        inner.history_len = info->history_len;
+    }
+    const tpmg_status st = tpmg_mg_solve(op, prm, fd, ud, &inner, stream);
+    if (st != TPMG_OK && st != TPMG_ERR_NOT_CONVERGED && st != TPMG_ERR_NONFINITE) return st;
+    const std::string solve_err = g_err;
+    CK(cudaEventRecord(op->hev[2], s));
+    // u back (also on NOT_CONVERGED / NONFINITE: the last iterate, as tpmg_mg_solve leaves it)
+    if (layout == TPMG_LAYOUT_X) {
+        CK(cudaMemcpyAsync(u_host, ud, bytes, cudaMemcpyDeviceToHost, s));
+    } else {
+        if (f32) launch_transpose<float>((const float*)ud, (float*)op->hio[2], nz, ncol, s);
+        else launch_transpose<double>((const double*)ud, (double*)op->hio[2], nz, ncol, s);
+        CK(cudaMemcpyAsync(u_host, op->hio[2], bytes, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaEventRecord(op->hev[3], s));
+    CK(cudaEventSynchronize(op->hev[3]));
+    CK(cudaGetLastError());
+    float t_all = 0, t_in = 0, t_out = 0;
+    CK(cudaEventElapsedTime(&t_all, op->hev[0], op->hev[3]));
+    CK(cudaEventElapsedTime(&t_in, op->hev[0], op->hev[1]));
+    CK(cudaEventElapsedTime(&t_out, op->hev[2], op->hev[3]));
+    if (info) {
+        *info = inner;
+        info->ms = t_all;
+    }
+    if (ms_io) *ms_io = (double)t_in + (double)t_out;
+    if (st != TPMG_OK) return set_err(st, solve_err);
+    return TPMG_OK;
 }
 
 tpmg_status tpmg_vcycle(tpmg_op* op, const tpmg_params* prm, const void* f, void* u, void* stream) {

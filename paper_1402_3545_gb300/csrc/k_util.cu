@@ -260,4 +260,40 @@ void launch_coarsen_v_f64(int nxf, int nyf, const double* vf, double* vc, cudaSt
     note_launch();
 }
 
+// ---------------------------------------------------------------- layout transposition
+// out[c * rows + r] = in[r * cols + c]: a rows x cols row-major matrix transposed through 32 x 32
+// tiles in shared memory, padded by one element per row so that neither the row-wise fill nor the
+// column-wise drain of a tile meets a bank conflict; both global sides are read and written in
+// 32-element rows (coalesced). Converts between the vertically contiguous field layout of CPU codes
+// (column c = j*nx + i holds its nz values contiguously: rows = nx*ny, cols = nz) and the
+// horizontally contiguous layout of the kernels (rows = nz, cols = nx*ny), Sec. 5.1.
+template <class T>
+__global__ void __launch_bounds__(256) k_transpose(const T* __restrict__ in, T* __restrict__ out, size_t rows,
+                                                   size_t cols, size_t tiles_c) {
+    __shared__ T tile[32][33];
+    const size_t t = blockIdx.x;
+    const size_t r0 = (t / tiles_c) * 32, c0 = (t % tiles_c) * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8 threads, four rows each
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const size_t r = r0 + ty + 8 * q, c = c0 + tx;
+        if (r < rows && c < cols) tile[ty + 8 * q][tx] = in[r * cols + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const size_t c = c0 + ty + 8 * q, r = r0 + tx;
+        if (r < rows && c < cols) out[c * rows + r] = tile[tx][ty + 8 * q];
+    }
+}
+
+template <class T>
+void launch_transpose(const T* in, T* out, size_t rows, size_t cols, cudaStream_t s) {
+    const size_t tiles_r = (rows + 31) / 32, tiles_c = (cols + 31) / 32;
+    k_transpose<T><<<(unsigned)(tiles_r * tiles_c), dim3(32, 8), 0, s>>>(in, out, rows, cols, tiles_c);
+    note_launch();
+}
+template void launch_transpose<double>(const double*, double*, size_t, size_t, cudaStream_t);
+template void launch_transpose<float>(const float*, float*, size_t, size_t, cudaStream_t);
+
 }  // namespace tpmg

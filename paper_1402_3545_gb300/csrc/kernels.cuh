@@ -378,6 +378,9 @@ template <class P>
 void launch_copy(size_t n, const typename P::S* src, typename P::S* dst, const int* done, cudaStream_t s);
 void launch_f64_to_dw(size_t n, const double* x, float2* y, cudaStream_t s);
 void launch_dw_to_f64(size_t n, const float2* x, double* y, cudaStream_t s);
+// out = in transposed (in: rows x cols row-major, out: cols x rows row-major)
+template <class T>
+void launch_transpose(const T* in, T* out, size_t rows, size_t cols, cudaStream_t s);
 void launch_f64_to_f32(size_t n, const double* x, float* y, cudaStream_t s);
 void launch_f32_to_f64(size_t n, const float* x, double* y, cudaStream_t s);
 void launch_coarsen_v_f64(int nxf, int nyf, const double* vf, double* vc, cudaStream_t s);

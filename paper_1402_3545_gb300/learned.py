@@ -184,9 +184,11 @@ def load(path: str):
     return net, json.loads(str(z["meta"]))
 
 
-def fcg_compare(p: workloads.Problem, net=None, tol: float = 1e-6, max_iter: int = 200, reps: int = 1):
+def fcg_compare(p: workloads.Problem, net=None, tol: float = 1e-6, max_iter: int = 200, reps: int = 1,
+                solutions: dict | None = None):
     """Flexible CG with and without the learned stage on one problem (zero initial guess):
-    iterations, device ms (median of reps), accepted corrections and the final relative residual."""
+    iterations, device ms (median of reps), accepted corrections and the final relative residual.
+    With a dict as `solutions`, each variant's final iterate is also stored there (host numpy)."""
     op = tpmg.Operator.from_problem(p)
     n = p.n
     f = torch.from_numpy(p.rhs()).cuda()
@@ -203,6 +205,8 @@ def fcg_compare(p: workloads.Problem, net=None, tol: float = 1e-6, max_iter: int
             ms.append(res["ms"])
         out[name] = {"iters": res["iters"], "ms": float(np.median(ms)), "converged": res["converged"],
                      "rel_res": res["rel_res"], "nn_accepted": res["nn_accepted"]}
+        if solutions is not None:
+            solutions[name] = u.cpu().numpy()
     op.close()
     return out
 

@@ -75,6 +75,7 @@ _SIGNATURES = {
     "tpmg_cg_fused_tridiag": [_P, _I, _D, _P, _P, _P, _P, _P, _P],
     "tpmg_default_params": [ctypes.POINTER(Params)],
     "tpmg_mg_solve": [_P, ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Info), _P],
+    "tpmg_mg_solve_host": [_P, ctypes.POINTER(Params), _I, _P, _P, ctypes.POINTER(Info), _P, _P],
     "tpmg_vcycle": [_P, ctypes.POINTER(Params), _P, _P, _P],
     "tpmg_cg_solve": [_P, ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Info), _P],
     "tpmg_mg_solve_batched": [_I, _P, ctypes.POINTER(Params), _P, _P, _P, _P],
@@ -343,9 +344,10 @@ def mg_solve(op, params, f, u, n, history_len=256, stream=None, allow=(ERR_NOT_C
     return _solve("tpmg_mg_solve", op, params, f, u, n, history_len, stream, allow)
 
 
-def mg_solve_host(op, params, f, u, n, history_len=256, stream=None, allow=(ERR_NOT_CONVERGED,)):
-    """mg_solve on page-locked host fields (CPU float64 tensors with is_pinned()): the solve reads f
-    and the initial u from the host and writes u back in its first and last kernels."""
+def mg_solve_mapped(op, params, f, u, n, history_len=256, stream=None, allow=(ERR_NOT_CONVERGED,)):
+    """tpmg_mg_solve on page-locked host fields (CPU float64 tensors with is_pinned()) that the device
+    addresses directly: the solve reads f and the initial u from the host and writes u back in its
+    first and last kernels."""
     if params.prec not in (DW, MIXED):
         raise ValueError("host fields need prec DW or MIXED")
     for t, name in ((f, "f"), (u, "u")):
@@ -361,6 +363,32 @@ def mg_solve_host(op, params, f, u, n, history_len=256, stream=None, allow=(ERR_
     _check(status, "mg_solve", allow=allow)
     return {"status": status, "iters": info.iters, "converged": bool(info.converged),
             "rel_res": info.rel_res, "r0": info.r0, "ms": info.ms,
+            "history": [hist[i] for i in range(min(info.iters + 1, history_len))]}
+
+
+LAYOUT_X, LAYOUT_Z = 0, 1
+
+
+def mg_solve_host(op, params, f, u, n, layout=LAYOUT_Z, history_len=256, stream=None, allow=(ERR_NOT_CONVERGED,)):
+    """tpmg_mg_solve_host: f and u are CPU tensors (float64; float32 for F32) of n values in `layout`
+    (LAYOUT_X: x fastest as on the device; LAYOUT_Z: z fastest, column by column); the library copies
+    and transposes them on the device around the solve. Returns the solve's info plus "ms_io", the
+    device time of the copies and transposes (info "ms" covers the whole call)."""
+    dt = torch.float32 if params.prec == F32 else torch.float64
+    for t, name in ((f, "f"), (u, "u")):
+        if not (isinstance(t, torch.Tensor) and not t.is_cuda and t.dtype == dt and t.is_contiguous()
+                and t.numel() == n):
+            raise TypeError(f"{name} must be a contiguous CPU {dt} tensor of {n} elements")
+    hist = (ctypes.c_double * max(history_len, 1))()
+    info = Info()
+    info.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+    info.history_len = history_len
+    ms_io = _D()
+    status = load().tpmg_mg_solve_host(op, ctypes.byref(params), int(layout), f.data_ptr(), u.data_ptr(),
+                                       ctypes.byref(info), ctypes.byref(ms_io), _stream(stream))
+    _check(status, "mg_solve_host", allow=allow)
+    return {"status": status, "iters": info.iters, "converged": bool(info.converged),
+            "rel_res": info.rel_res, "r0": info.r0, "ms": info.ms, "ms_io": ms_io.value,
             "history": [hist[i] for i in range(min(info.iters + 1, history_len))]}
 
 

@@ -169,4 +169,4 @@ def test_binding_refuses_host_tensors_without_gpu():
         tpmg._scalar_out(torch.zeros(1, dtype=torch.float64))
     # page-locked host fields are accepted only by the double-word and mixed solves
     with pytest.raises(ValueError, match="prec DW or MIXED"):
-        tpmg.mg_solve_host(0, tpmg.default_params(prec=tpmg.F64), x, x, x.numel())
+        tpmg.mg_solve_mapped(0, tpmg.default_params(prec=tpmg.F64), x, x, x.numel())

@@ -166,7 +166,7 @@ def test_mg_solve_with_host_fields(small, prec, zero_guess):
     rd = tpmg.mg_solve(op.op, prm, dev(f, tpmg.F64).reshape(-1), ud, p.n)
     fh = torch.from_numpy(f.ravel().copy()).pin_memory()
     uh = torch.full((p.n,), float("nan") if zero_guess else 0.0, dtype=torch.float64).pin_memory()
-    rh = tpmg.mg_solve_host(op.op, prm, fh, uh, p.n)
+    rh = tpmg.mg_solve_mapped(op.op, prm, fh, uh, p.n)
     torch.cuda.synchronize()
     assert rh["iters"] == rd["iters"] and rh["history"] == rd["history"]
     assert np.array_equal(uh.numpy(), host(ud))
