@@ -205,7 +205,7 @@ def cpu_leg(p, f, sols: dict):
             continue
         fx = prob.rhs()
         cxx, cyy, vv = oracle.problem_coefficients(prob)
-        uex = spectral.exact_solve(fx, cxx, cyy, float(vv))
+        uex = spectral.exact_solve(fx, cxx, cyy, vv)
         ref[key] = {"reference": "exact spectral solution (Fourier x Fourier x DCT-II)",
                     "rel_err": {k: rel_err(u, uex) for k, u in sols.pop(key).items()}}
         del fx, uex
@@ -213,7 +213,7 @@ def cpu_leg(p, f, sols: dict):
         errs = []
         for prob, u in zip(workloads.batched(), sols.pop("batched")):
             cxx, cyy, vv = oracle.problem_coefficients(prob)
-            errs.append(rel_err(u, spectral.exact_solve(prob.rhs(), cxx, cyy, float(vv))))
+            errs.append(rel_err(u, spectral.exact_solve(prob.rhs(), cxx, cyy, vv)))
         ref["batched"] = {"reference": "exact spectral solution of each problem",
                           "rel_err_max": max(errs), "rel_err_median": float(np.median(errs))}
     ref["seconds"] = round(time.perf_counter() - t0, 1)
@@ -397,6 +397,37 @@ def bench_paper_shaped(tpmg, torch):
                      "ms_per_iter": round(best / max(r["iters"], 1), 4)}
     out["paper_k20x"] = {"mg_iters": 8, "ms_per_vcycle": 88.8, "cg_iters": 59, "ms_per_cg_iter": 29.7}
     op.close()
+    return out
+
+
+def bench_robustness(tpmg, torch):
+    """The robustness study of Sec. 5.2 on the paper's 512^2 x 128 grid: nu_CFL = 2 omega / h from
+    0.84 to 840, multigrid V(1,1) (rho = 2/3, epsilon = 1e-5) with 5, 7 and 10 levels and the coarse
+    smoothing steps the paper needed, and line-preconditioned CG, native FP64: cycles or iterations
+    and device ms of each solve."""
+    out = {"settings": "V(1,1), rho 2/3, tol 1e-5, native FP64; CG tol 1e-5"}
+    for nu in workloads.ROBUSTNESS_CFL:
+        row = {}
+        for L in workloads.ROBUSTNESS_LEVELS:
+            p = workloads.paper_shaped(nu_cfl=nu, nlevels=L)
+            nc = workloads.robustness_coarse_steps(L, nu)
+            op = tpmg.Operator.from_problem(p, nlevels=L)
+            f = torch.from_numpy(p.rhs()).cuda()
+            u = torch.zeros_like(f)
+            prm = tpmg.default_params(prec=tpmg.F64, tol=1e-5, max_iter=300, nu_pre=1, nu_post=1, n_coarse=nc,
+                                      rho=2.0 / 3.0, zero_guess=1)
+            ms = []
+            for _ in range(2):
+                r = tpmg.mg_solve(op.op, prm, f, u, p.n)
+                ms.append(r["ms"])
+            row[f"mg_{L}_levels"] = {"iters": r["iters"], "converged": r["converged"], "ms": round(min(ms), 3),
+                                     "coarse_steps": nc}
+            if L == workloads.ROBUSTNESS_LEVELS[0]:
+                r = tpmg.cg_solve(op.op, tpmg.default_params(prec=tpmg.F64, tol=1e-5, max_iter=20000, zero_guess=1),
+                                  f, u, p.n)
+                row["cg"] = {"iters": r["iters"], "converged": r["converged"], "ms": round(r["ms"], 3)}
+            op.close()
+        out[f"cfl_{nu:g}"] = row
     return out
 
 
@@ -695,6 +726,7 @@ def run_ours(args, rank, world, dist):
     variants["batched_64"] = bench_batched(tpmg, torch, sols)
     variants["mixed_1024x1024x128"] = bench_mixed(tpmg, torch, sols)
     variants["paper_shaped_512x512x128"] = bench_paper_shaped(tpmg, torch)
+    variants["robustness_512x512x128"] = bench_robustness(tpmg, torch)
     variants["learned_2048x2048x64"] = bench_learned(tpmg, torch, sols)
 
     cpu, errors = None, None

@@ -29,12 +29,16 @@ def eigenvalues_plane(nx: int, ny: int, nz: int, cx: float, cy: float, v: float,
     return 1.0 + 4.0 * cx * sx[None, :] + 4.0 * cy * sy[:, None] + 4.0 * v * sz
 
 
-def exact_solve(f: np.ndarray, cx: float, cy: float, v: float, workers: int = -1) -> np.ndarray:
-    """u = A^{-1} f for a constant v; f has shape (nz, ny, nx), x fastest. `workers` host threads
+def exact_solve(f: np.ndarray, cx: float, cy: float, v, workers: int = -1) -> np.ndarray:
+    """u = A^{-1} f for a constant v (a number, or a field of equal values); f has shape
+    (nz, ny, nx), x fastest. `workers` host threads
     run the transforms (-1: all cores). Peak memory is about three copies of f."""
     f = np.asarray(f, dtype=np.float64)
     nz, ny, nx = f.shape
-    v = float(np.asarray(v).ravel()[0]) if np.ndim(v) else float(v)
+    va = np.asarray(v, dtype=np.float64)
+    if va.size > 1 and not np.all(va == va.ravel()[0]):
+        raise ValueError("exact_solve needs a constant vertical coefficient")
+    v = float(va.ravel()[0])
     g = scipy.fft.dct(f, type=2, norm="ortho", axis=0, workers=workers)  # vertical modes m
     for m in range(nz):  # one plane at a time keeps the complex spectrum to one plane
         F = scipy.fft.rfft2(g[m], workers=workers)

@@ -103,11 +103,32 @@ def learned_target(nx: int = 2048, nz: int = 64) -> Problem:
                    1e3, levels_to_8(nx, nx), 0, "uniform")
 
 
-def paper_shaped(nx: int = 512, nz: int = 128, lambda2: float = 1e3) -> Problem:
-    """Paper-shaped variant: omega = 4.2 h (nu_CFL = 8.4, Eq. (4)), so kappa ~ 142 (Eq. (7))."""
+def paper_shaped(nx: int = 512, nz: int = 128, lambda2: float = 1e3, nu_cfl: float = 8.4,
+                 nlevels: int | None = None) -> Problem:
+    """Paper-shaped variant: omega = nu_CFL h / 2 with the horizontal CFL number nu_CFL = 2 omega / h
+    of Sec. 5.2 (8.4 by default, i.e. omega = 4.2 h, Eq. (4)), so kappa ~ 1 + 2 nu_CFL^2 (Eq. (7):
+    142 at 8.4); N(0,1) right-hand side from seed 0."""
     h = 1.0 / nx
-    return Problem(f"paper_shaped_{nx}x{nx}x{nz}", nx, nx, nz, (4.2 * h) ** 2, h, h, 1.0 / nz,
-                   lambda2, levels_to_8(nx, nx), 0, "normal")
+    name = f"paper_shaped_{nx}x{nx}x{nz}" + ("" if nu_cfl == 8.4 else f"_cfl{nu_cfl:g}")
+    return Problem(name, nx, nx, nz, (0.5 * nu_cfl * h) ** 2, h, h, 1.0 / nz,
+                   lambda2, levels_to_8(nx, nx) if nlevels is None else nlevels, 0, "normal")
+
+
+# The robustness study of Sec. 5.2 (512^2 x 128 in the paper): nu_CFL from 0.84 to 840 with 5, 7 and
+# 10 multigrid levels; the number of smoothing steps on the coarsest level grows with nu_CFL as the
+# paper reports it needed (10 levels: 2 throughout; 7 levels: 5 at 84, 15 at 840; 5 levels: 30 at
+# 84, 150 at 840; 2 up to 16.8).
+ROBUSTNESS_CFL = (0.84, 8.4, 84.0, 840.0)
+ROBUSTNESS_LEVELS = (5, 7, 10)
+
+
+def robustness_coarse_steps(nlevels: int, nu_cfl: float) -> int:
+    """Smoothing steps on the coarsest level for the robustness study (Sec. 5.2)."""
+    if nu_cfl <= 16.8 or nlevels >= 10:
+        return 2
+    table = {7: {84.0: 5, 840.0: 15}, 5: {84.0: 30, 840.0: 150}}
+    row = table.get(nlevels, table[5] if nlevels < 7 else table[7])
+    return row[min(row, key=lambda c: abs(c - nu_cfl))]
 
 
 def batched(nprob: int = 64, seed: int = 0) -> list[Problem]:

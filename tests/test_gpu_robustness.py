@@ -1,0 +1,61 @@
+"""The robustness study of Sec. 5.2 at a size the oracle finishes quickly: the horizontal CFL number
+nu_CFL = 2 omega / h from 0.84 to 840 with the paper's smoothing settings (V(1,1), rho = 2/3,
+epsilon = 1e-5) on a 128^2 x 32 grid with 5, 7 and 8 levels -- the paper's 5- and 7-level
+hierarchies level for level (the horizontal coupling of level l, and so the conditioning of the
+coarsest problem, depends only on nu_CFL and the number of coarsenings), and its 10-level hierarchy
+down to a 1 x 1 coarsest level -- with the coarse smoothing steps the paper needed there. The native FP64 and double-word solves take the oracle's number of cycles and their iterates
+agree with the oracle's to 1e-10; line-preconditioned CG (small CFL numbers, where it stays short)
+takes the oracle's iteration count to within one."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1402_3545_gb300 import tpmg, workloads
+
+pytestmark = pytest.mark.gpu
+
+NX, NZ = 128, 32
+LEVELS = {5: 5, 7: 7, 10: 8}  # the paper's levels on 512^2 -> levels here (10: coarsest 1 x 1)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+@pytest.mark.parametrize("nu", workloads.ROBUSTNESS_CFL)
+@pytest.mark.parametrize("paper_levels", sorted(LEVELS))
+def test_multigrid_across_cfl_numbers_matches_oracle(nu, paper_levels):
+    L = LEVELS[paper_levels]
+    nc = workloads.robustness_coarse_steps(paper_levels, nu)
+    p = workloads.paper_shaped(NX, NZ, nu_cfl=nu, nlevels=L)
+    f = p.rhs()
+    cx, cy, v = oracle.problem_coefficients(p)
+    u_ref, it_ref, _, conv = oracle.mg_solve(f, cx, cy, v, L, tol=1e-5, max_iter=200, nu_pre=1, nu_post=1,
+                                             n_coarse=nc, rho=2.0 / 3.0)
+    assert conv
+    op = tpmg.Operator.from_problem(p, nlevels=L)
+    fd = torch.from_numpy(f).cuda()
+    for prec in (tpmg.F64, tpmg.DW):
+        u = torch.zeros_like(fd)
+        prm = tpmg.default_params(prec=prec, tol=1e-5, max_iter=200, nu_pre=1, nu_post=1, n_coarse=nc,
+                                  rho=2.0 / 3.0, zero_guess=1)
+        res = tpmg.mg_solve(op.op, prm, fd, u, p.n)
+        assert res["iters"] == it_ref, (prec, res["iters"], it_ref)
+        assert _rel(u.cpu().numpy(), u_ref) < 1e-10, prec
+    op.close()
+
+
+@pytest.mark.parametrize("nu", [0.84, 8.4])
+def test_cg_across_cfl_numbers_matches_oracle(nu):
+    p = workloads.paper_shaped(NX, NZ, nu_cfl=nu, nlevels=1)
+    f = p.rhs()
+    cx, cy, v = oracle.problem_coefficients(p)
+    _, it_ref, _, conv = oracle.cg_solve(f, cx, cy, v, tol=1e-5, max_iter=2000)
+    assert conv
+    op = tpmg.Operator.from_problem(p, nlevels=1)
+    fd = torch.from_numpy(f).cuda()
+    u = torch.zeros_like(fd)
+    res = tpmg.cg_solve(op.op, tpmg.default_params(prec=tpmg.F64, tol=1e-5, max_iter=2000, zero_guess=1), fd, u, p.n)
+    assert res["converged"] and abs(res["iters"] - it_ref) <= 1, (res["iters"], it_ref)
+    op.close()
