@@ -71,6 +71,91 @@ def test_forward_matches_oracle(shape, cin):
     net.close()
 
 
+def _layers(params, cin):
+    """(W, b) of the four layers from the flat parameters (W[co][ci][tap], tap = (dz, dy, dx))."""
+    q = np.asarray(params, dtype=np.float64)
+    out, o = [], 0
+    for ci, co in ((cin, 16), (16, 16), (16, 16), (16, 1)):
+        out.append((q[o:o + co * ci * 27].reshape(co, ci, 3, 3, 3), q[o + co * ci * 27:o + co * ci * 27 + co]))
+        o += co * ci * 27 + co
+    return out
+
+
+def _forward_bf16_storage(params, x, cin):
+    """The network with the GPU's storage: the oracle's layers (oracle.conv3d, FP64 sums) on
+    BF16-rounded weights and input, every hidden activation rounded to BF16 after its ReLU, the
+    output kept. Returns the output and the stored activations [x, a1, a2, a3]."""
+    acts = [bf16(x)]
+    for li, (W, b) in enumerate(_layers(weights_bf16(params, cin), cin)):
+        y = oracle.conv3d(acts[-1], W, b, relu=li < 3)
+        if li < 3:
+            acts.append(bf16(y))
+    return y[0], acts
+
+
+# Layer-by-layer tolerances. With the GPU's BF16 storage reproduced, what remains is the FP32
+# accumulation of each output's 27 * 16 = 432 products (relative ~sqrt(432) * 2^-24 ~ 1.2e-6, times a
+# cancellation factor of up to ~10) and, where that difference straddles a BF16 rounding boundary,
+# a stored value one BF16 ulp (2^-8 relative) away: a fraction ~1e-5 / 2^-8 ~ 3e-3 of the values, so
+# ~sqrt(3e-3) * 2^-8 ~ 2e-4 relative per stored layer, ~4e-4 after three. Forward: 1e-3. Gradients
+# go through five stored layers and parameter sums over every cell with cancellation: 1e-2. A slip in
+# one layer's indexing, taps or channels is an O(1) error at either tolerance.
+FWD_TOL, GRAD_TOL = 1e-3, 1e-2
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("cin", [1, 2])
+def test_forward_matches_oracle_layers_with_bf16_storage(shape, cin):
+    p = random_params(cin, seed=30 + cin)
+    x = np.random.default_rng(31).standard_normal((cin,) + shape)
+    # the layer composition itself, without rounding, is the oracle's network
+    plain = x
+    for li, (W, b) in enumerate(_layers(weights_bf16(p, cin), cin)):
+        plain = oracle.conv3d(plain, W, b, relu=li < 3)
+    assert rel(plain[0], oracle.nn_forward(weights_bf16(p, cin), x)) < 1e-13
+    net = tpmg.Network(cin, p)
+    y = host(net.forward(channels_last(x), shape)).reshape(shape)
+    ref, _ = _forward_bf16_storage(p, x, cin)
+    assert rel(y, ref) < FWD_TOL, rel(y, ref)
+    net.close()
+
+
+@pytest.mark.parametrize("shape", SHAPES[:2], ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("cin", [1, 2])
+def test_gradient_matches_oracle_layers_with_bf16_storage(shape, cin):
+    """Backpropagation as the kernels store it: the output gradient 2 (y - t) / n in FP32, every
+    hidden data gradient (the ReLU mask times the transposed convolution of the next layer's) rounded
+    to BF16; each layer's parameter gradient is the oracle's (oracle.conv3d_backward) on the stored
+    input activations and the stored output gradient. Compared per weight and bias block."""
+    p = random_params(cin, seed=40 + cin)
+    rng = np.random.default_rng(41)
+    x = rng.standard_normal((cin,) + shape)
+    target = rng.standard_normal(shape).astype(np.float32).astype(np.float64)
+    y, acts = _forward_bf16_storage(p, x, cin)
+    n = y.size
+    layers = _layers(weights_bf16(p, cin), cin)
+    d = (2.0 * (y - target) / n)[None]  # gradient of the output, (1, nz, ny, nx)
+    grads = [None] * 4
+    for li in (3, 2, 1, 0):
+        W, _ = layers[li]
+        dx, dW, db = oracle.conv3d_backward(acts[li], W, d, want_dx=li > 0)
+        grads[li] = (dW, db)
+        if li > 0:
+            d = bf16(np.where(acts[li] > 0, dx, 0.0))
+    net = tpmg.Network(cin, p)
+    loss, grad = net.loss_grad(channels_last(x), torch.from_numpy(target.astype(np.float32).ravel()).cuda(), shape)
+    loss, grad = float(host(loss)[0]), host(grad)
+    assert abs(loss - np.mean((y - target) ** 2)) < FWD_TOL * loss
+    o = 0
+    for li, (ci, co) in enumerate(((cin, 16), (16, 16), (16, 16), (16, 1))):
+        dW, db = grads[li]
+        for size, ref, what in ((co * ci * 27, dW.ravel(), "W"), (co, db, "b")):
+            g = grad[o:o + size]
+            assert rel(g, ref) < GRAD_TOL, (what, li + 1, rel(g, ref))
+            o += size
+    net.close()
+
+
 @pytest.mark.parametrize("cin", [1, 2])
 def test_affine_network_is_exact(cin):
     """alpha * bf16(x0) + beta (+ gamma relu(bf16(x1))) to FP32 accuracy: the hidden layers only
