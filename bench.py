@@ -629,26 +629,30 @@ def run_ours(args, rank, world, dist):
     sols["mid_headline_u"] = sols["mid"]["f64"]
 
     # dominant kernel: the finest-level native FP64 Smooth (4 of the 5 fine-level sweeps of each
-    # cycle), bound by the FP64 pipe: FP64 flops over its CUDA-event launch time, against twice the
-    # FP64 multiply-add rate measured on this GPU in this process (a multiply-add is 2 flops)
+    # cycle), bound by the FP64 pipe, which issues multiply-adds, adds and multiplies at one rate:
+    # FP64 instructions per second over its CUDA-event launch time, against the FP64 instruction
+    # rate measured on this GPU in this process (tpmg_measure_alu_rate)
     peaks, peak_kind = measured_peaks()
     traffic = read_traffic()
     fma_rate, _ = tpmg.measure_alu_rate(tpmg.ALU_FP64_FMA)
     add_rate, _ = tpmg.measure_alu_rate(tpmg.ALU_FP64_ADD)
     t_s64 = tpmg.time_kernel(op.op, tpmg.F64, tpmg.K_SMOOTH, reps=20)
     v64 = tuned["f64"][-1] if tuned["f64"] else None
-    ach = SMOOTH_F64_FLOPS * n / (t_s64 * 1e-3) / 1e12
-    peak64 = 2.0 * fma_rate / 1e12
+    ach = SMOOTH_F64_INSTR * n / (t_s64 * 1e-3) / 1e12
+    peak64 = min(fma_rate, add_rate) / 1e12
     tr = traffic.get(("smooth", "f64", int(v64) if v64 is not None else -1, "mid_512x512x128"))
-    roofline = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak64, 4), "unit": "TFLOP/s",
+    roofline = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak64, 4), "unit": "T FP64 op/s",
                 "frac": round(ach / peak64, 4), "traffic": tr[0] if tr else None,
                 "traffic_source": (f"ncu capture: {tr[1]}" if tr else None),
                 "kernel": f"finest-level native FP64 Smooth (tile variant {v64})",
-                "peak_source": ("measured in this run: FP64 multiply-add rate of tpmg_measure_alu_rate x 2 "
-                                f"({fma_rate / 1e12:.4f} T FMA/s; FP64 add {add_rate / 1e12:.4f} T/s)"),
-                "flops_per_cell": SMOOTH_F64_FLOPS, "instructions_per_cell": SMOOTH_F64_INSTR,
-                "pipe_frac": round(SMOOTH_F64_INSTR * n / (t_s64 * 1e-3) / fma_rate, 4),
-                "ms_per_launch": round(t_s64, 4), "flops_per_launch": SMOOTH_F64_FLOPS * n,
+                "peak_source": ("measured in this run: FP64 instruction rate of tpmg_measure_alu_rate "
+                                f"(multiply-add {fma_rate / 1e12:.4f}, add {add_rate / 1e12:.4f} T/s)"),
+                "op": "one FP64 arithmetic instruction (multiply-add, add or multiply: the same rate)",
+                "ops_per_cell": SMOOTH_F64_INSTR, "ops_per_launch": SMOOTH_F64_INSTR * n,
+                "ms_per_launch": round(t_s64, 4),
+                "flops": {"per_cell": SMOOTH_F64_FLOPS, "achieved_tflops": round(SMOOTH_F64_FLOPS * n / (t_s64 * 1e-3) / 1e12, 4),
+                          "peak_tflops": round(2 * fma_rate / 1e12, 4),
+                          "frac": round(SMOOTH_F64_FLOPS * n / (t_s64 * 1e-3) / (2 * fma_rate), 4)},
                 "share_of_solve": round((4 * iters[-1] + 1) * t_s64 / ms_per_step, 3),
                 "hbm_frac_same_launch": round(3 * 8 * n / (t_s64 * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
                 "hbm_peak_source": peak_kind}
