@@ -58,7 +58,11 @@ def test_checkpoint_round_trip(trained, tmp_path):
 
 def test_ablation_with_and_without_the_network(trained):
     """Same right-hand side, flexible CG with the V-cycle alone and with the learned stage: both
-    converge, the trained corrections are kept, and the iteration count does not grow."""
+    converge and the trained corrections are kept, and the measured gain is the one the bound of
+    tests/test_learned_stage_bound.py allows: a corrector with the network's 9^3 receptive field can
+    remove at most a few per cent of the error a V-cycle leaves, so the iteration count stays within
+    one of the V-cycle-only count, while the network does remove most of its input residual (held-out
+    residual loss below 0.5) and leaves the held-out error where it was (error ratio 0.9 .. 1.1)."""
     net, _, _, _, _, _ = trained
     p = workloads.Problem("ablation", 128, 128, 32, CFG.omega2, CFG.h, CFG.h, CFG.hz, 1e3,
                           learned.levels_full(128, 128), 3, "uniform")
@@ -68,4 +72,6 @@ def test_ablation_with_and_without_the_network(trained):
           f"{b['nn_accepted']} corrections kept")
     assert a["converged"] and b["converged"]
     assert b["nn_accepted"] > 0
-    assert b["iters"] <= a["iters"] + 1
+    assert abs(b["iters"] - a["iters"]) <= 1
+    _, _, _, _, after, _ = trained
+    assert after["residual"] < 0.5 and 0.9 < after["error"] < 1.1, after
