@@ -1623,7 +1623,10 @@ static tpmg_status build_batch(BatchCache* bc, const tpmg_params* prm) {
             ld.v = op->v32[l];
             ld.finv = (const float*)op->finv[1][l];
             ld.fw = (const float*)op->fw[1][l];
+            ld.k1 = sweep_k<PolF32>(op->cx[l], op->cy[l], 1.0);
+            ld.krho = sweep_k<PolF32>(op->cx[l], op->cy[l], prm->rho);
         }
+        pd.kD = sweep_k<PolDW>(op->cx[L], op->cy[L], 1.0);
         pd.uD = (float2*)op->hier[2].u[L];
         pd.fD = (const float2*)op->hier[2].f[L];
         pd.vD = op->vdw[L];

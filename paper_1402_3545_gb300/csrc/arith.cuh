@@ -154,6 +154,8 @@ struct PolF64 {
     __device__ __forceinline__ static void sts(S* p, size_t i, R x) { p[i] = x; }
     __device__ __forceinline__ static R rnd(R x) { return x; }
     __device__ __forceinline__ static R cst(double x) { return x; }
+    // the same conversion on the host, for constants handed to kernels ready-made
+    static R hcst(double x) { return x; }
     __device__ __forceinline__ static double to_d(R x) { return x; }
     __device__ __forceinline__ static R zero() { return 0.0; }
     __device__ __forceinline__ static R add(R a, R b) { return a + b; }
@@ -187,6 +189,7 @@ struct PolF32 {
     __device__ __forceinline__ static void sts(S* p, size_t i, R x) { p[i] = x; }
     __device__ __forceinline__ static R rnd(R x) { return x; }
     __device__ __forceinline__ static R cst(double x) { return (float)x; }
+    static R hcst(double x) { return (float)x; }  // round to nearest, as on the device
     __device__ __forceinline__ static double to_d(R x) { return (double)x; }
     __device__ __forceinline__ static R zero() { return 0.0f; }
     __device__ __forceinline__ static R add(R a, R b) { return a + b; }
@@ -231,6 +234,11 @@ struct PolDW {
     __device__ __forceinline__ static R cst(double x) {
         float h = __double2float_rn(x);
         return dw{h, __double2float_rn(x - (double)h)};
+    }
+    // the same split on the host (x - h is exact in double; both roundings to nearest)
+    static R hcst(double x) {
+        const float h = (float)x;
+        return dw{h, (float)(x - (double)h)};
     }
     __device__ __forceinline__ static double to_d(R x) { return (double)x.hi + (double)x.lo; }
     __device__ __forceinline__ static R zero() { return dw{0.0f, 0.0f}; }

@@ -91,8 +91,8 @@ __device__ void t_sweep(const BLevelDesc& L, float rho, const float* __restrict_
     const size_t pl = (size_t)nx * ny, c = (size_t)t.j * nx + t.i;
     const size_t cw = (size_t)t.j * nx + bwrap(t.i - 1, nx), ce = (size_t)t.j * nx + bwrap(t.i + 1, nx);
     const size_t cs = (size_t)bwrap(t.j - 1, ny) * nx + t.i, cn = (size_t)bwrap(t.j + 1, ny) * nx + t.i;
-    const float cx = (float)L.cx, cy = (float)L.cy, vv = __ldg(L.v + c);
-    const float dh = (float)(1.0 + 2.0 * L.cx + 2.0 * L.cy), dh1 = dh + vv, dh2 = dh1 + vv;
+    const float cx = L.k1.cx, cy = L.k1.cy, vv = __ldg(L.v + c);  // converted on the host
+    const float dh = L.k1.dh, dh1 = dh + vv, dh2 = dh1 + vv;
     float um = 0.f, uc = (MODE != 2) ? __ldg(u + c) : 0.f, d_prev = 0.f;
     float fnext = __ldg(f + c);
     #pragma unroll 2
@@ -221,8 +221,8 @@ __device__ double t_outres(const BProbDesc& pb, int i0, int j0) {
         const size_t pl = (size_t)nx * ny, c = (size_t)t.j * nx + t.i;
         const size_t cw = (size_t)t.j * nx + bwrap(t.i - 1, nx), ce = (size_t)t.j * nx + bwrap(t.i + 1, nx);
         const size_t cs = (size_t)bwrap(t.j - 1, ny) * nx + t.i, cn = (size_t)bwrap(t.j + 1, ny) * nx + t.i;
-        const R cx = P::cst(L.cx), cy = P::cst(L.cy), vv = P::ld(pb.vD, c);
-        const R dh = P::cst(1.0 + 2.0 * L.cx + 2.0 * L.cy), dh1 = P::add(dh, vv), dh2 = P::add(dh1, vv);
+        const R cx = pb.kD.cx, cy = pb.kD.cy, vv = P::ld(pb.vD, c);  // converted on the host
+        const R dh = pb.kD.dh, dh1 = P::add(dh, vv), dh2 = P::add(dh1, vv);
         R um = P::zero(), uc = P::ld_plain(pb.uD, c);
         for (int k = 0; k < nz; ++k) {
             const size_t b = (size_t)k * pl;
@@ -395,30 +395,30 @@ __global__ void __launch_bounds__(32 * BTY, 4) k_batched(BatchDesc d) {
                             LD.fac_percol = 0;
                             LD.variant = -1;
                             const double s = sweep_x2_tiles<PolDW, PolF32, BTY, BPD, MODE_RESIDUAL, 0>(
-                                LD, 1.0, pb.uD, pb.fD, pb.r32, true, loc, loc + 1, 1, nullptr, bsmem);
+                                LD, pb.kD, pb.uD, pb.fD, pb.r32, true, loc, loc + 1, 1, nullptr, bsmem);
                             if (threadIdx.x == 0 && threadIdx.y == 0) d.partials[pb.part_base + loc] = s;
                             break;
                         }
                         case BT_LS0:
                             sweep_x2_tiles<PolF32, PolF32, BTY, BPD, MODE_LINESOLVE, HINT_ALL>(
-                                lv32(pb.lev[tk.level]), d.rho, (const float*)tk.b, nullptr, (float*)tk.out, false, loc,
+                                lv32(pb.lev[tk.level]), pb.lev[tk.level].krho, (const float*)tk.b, nullptr, (float*)tk.out, false, loc,
                                 loc + 1, 1, stack, bsmem);
                             break;
                         case BT_SMOOTH:
                             sweep_x2_tiles<PolF32, PolF32, BTY, BPD, MODE_SMOOTH, HINT_ALL>(
-                                lv32(pb.lev[tk.level]), d.rho, (const float*)tk.a, (const float*)tk.b, (float*)tk.out,
+                                lv32(pb.lev[tk.level]), pb.lev[tk.level].krho, (const float*)tk.a, (const float*)tk.b, (float*)tk.out,
                                 false, loc, loc + 1, 1, stack, bsmem);
                             break;
                         case BT_RESID:
                             sweep_x2_tiles<PolF32, PolF32, BTY, BPD, MODE_RESIDUAL, 0>(
-                                lv32(pb.lev[tk.level]), 1.0, (const float*)tk.a, (const float*)tk.b, (float*)tk.out,
+                                lv32(pb.lev[tk.level]), pb.lev[tk.level].k1, (const float*)tk.a, (const float*)tk.b, (float*)tk.out,
                                 false, loc, loc + 1, 1, nullptr, bsmem);
                             break;
                         case BT_RRS: {
-                            const XRestrict<PolF32> xr{lv32(pb.lev[tk.level - 1]), d.rho, (float*)tk.out,
-                                                       (float*)tk.out2};
+                            const XRestrict<PolF32> xr{lv32(pb.lev[tk.level - 1]), pb.lev[tk.level - 1].krho.coef,
+                                                       0.25f, (float*)tk.out, (float*)tk.out2};
                             sweep_x2_tiles<PolF32, PolF32, BTY, BPD, MODE_RESTRICT, 0>(
-                                lv32(pb.lev[tk.level]), 1.0, (const float*)tk.a, (const float*)tk.b, nullptr, false,
+                                lv32(pb.lev[tk.level]), pb.lev[tk.level].k1, (const float*)tk.a, (const float*)tk.b, nullptr, false,
                                 loc, loc + 1, 1, stack, bsmem, &xr);
                             break;
                         }

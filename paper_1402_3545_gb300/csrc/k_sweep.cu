@@ -97,7 +97,7 @@ void launch_factor_k0(const Lv<P>& L, const typename P::S* finv, const typename 
 // the scratch stays resident in L2 and shared memory holds only the rings; d'_k is written with
 // plain stores in the forward sweep and streamed back through the backward ring.
 template <class P, class PO, int TY, int PD, int MODE, bool GS>
-__global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, const typename P::S* __restrict__ u,
+__global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, SweepK<P> K, const typename P::S* __restrict__ u,
                                                       const typename P::S* __restrict__ f,
                                                       typename PO::S* __restrict__ out, double* partials,
                                                       const int* done) {
@@ -187,12 +187,11 @@ __global__ void __launch_bounds__(32 * TY) k_sweep_pp(Lv<P> L, double coef, cons
         for (int s = 0; s < PD; ++s) issue_plane(s, s);
 
         const R vv = P::ld(L.v, c);
-        const R cx = P::cst(L.cx), cy = P::cst(L.cy);
-        const R dh = P::cst(1.0 + 2.0 * L.cx + 2.0 * L.cy);
+        const R cx = K.cx, cy = K.cy, dh = K.dh;
         const R dh1 = P::add(dh, vv), dh2 = P::add(dh1, vv);
-        const bool iso = L.cx == L.cy;  // square cells: one product for the four horizontal neighbours
+        const bool iso = K.iso != 0;  // square cells: one product for the four horizontal neighbours
         const bool want_norm = partials != nullptr;
-        const R cf = P::cst(coef);
+        const R cf = K.coef;
         R um = vzero, uc = vzero, d_prev = vzero;
         int slot = 0;
         const int ctr = (ty + 1) * 34 + tx + 1;
@@ -339,7 +338,7 @@ static int run_sweep_pp(const Lv<P>& L, double coef, const typename P::S* u, con
         if (nb > ntiles) nb = ntiles;
         grd = dim3(nb, 1);
     }
-    kern<<<grd, blk, smem, s>>>(L, coef, u, f, out, partials, done);
+    kern<<<grd, blk, smem, s>>>(L, sweep_k<P>(L.cx, L.cy, coef), u, f, out, partials, done);
     note_launch();
     return (int)(grd.x * grd.y);
 }
@@ -347,7 +346,7 @@ static int run_sweep_pp(const Lv<P>& L, double coef, const typename P::S* u, con
 // ---------------------------------------------------------------- two columns per thread
 // The body is sweep_x2_tiles (sweep_x2.cuh), shared with the batched persistent kernel.
 template <class P, class PO, int TY, int PD, int MODE, int MINB = 1, int HINT = 0>
-__global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef, const typename P::S* __restrict__ u,
+__global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, SweepK<P> K, const typename P::S* __restrict__ u,
                                                       const typename P::S* __restrict__ f,
                                                       typename PO::S* __restrict__ out, double* partials,
                                                       const int* done) {
@@ -357,7 +356,7 @@ __global__ void __launch_bounds__(32 * TY, MINB) k_sweep_x2(Lv<P> L, double coef
                               ? reinterpret_cast<typename P::S*>(L.gstack) + (size_t)blockIdx.x * L.nz * 2 * 32 * TY
                               : nullptr;
     const int ntiles = (L.nx / 64) * (L.ny / TY);
-    const double sm = sweep_x2_tiles<P, PO, TY, PD, MODE, HINT>(L, coef, u, f, out, partials != nullptr, blockIdx.x,
+    const double sm = sweep_x2_tiles<P, PO, TY, PD, MODE, HINT>(L, K, u, f, out, partials != nullptr, blockIdx.x,
                                                                  ntiles, gridDim.x, slot, smem_raw);
     if (partials && threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.x] = sm;
 }
@@ -396,7 +395,8 @@ static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, con
     const int nb = sweep_x2_grid<P, PO, TY, PD, MODE, MINB, HINT>(L, u, f, out, cap);
     if (nb < 0) return -1;
     const size_t smem = sweep_x2_smem<P, TY, PD, MODE>();
-    k_sweep_x2<P, PO, TY, PD, MODE, MINB, HINT><<<nb, dim3(32, TY), smem, s>>>(L, coef, u, f, out, partials, done);
+    k_sweep_x2<P, PO, TY, PD, MODE, MINB, HINT><<<nb, dim3(32, TY), smem, s>>>(L, sweep_k<P>(L.cx, L.cy, coef), u, f,
+                                                                             out, partials, done);
     note_launch();
     return nb;
 }
@@ -408,14 +408,14 @@ static int run_sweep_x2(const Lv<P>& L, double coef, const typename P::S* u, con
 // per fine cell for the two kernels. The arithmetic is that of the separate kernels, operation for
 // operation, so the results are the same bit for bit.
 template <class P, int PD>
-__global__ void __launch_bounds__(64) k_residual_restrict_x2(Lv<P> L, XRestrict<P> xr,
+__global__ void __launch_bounds__(64) k_residual_restrict_x2(Lv<P> L, SweepK<P> K, XRestrict<P> xr,
                                                                const typename P::S* __restrict__ u,
                                                                const typename P::S* __restrict__ f, const int* done) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (done && *(volatile const int*)done) return;
     typename P::S* slot = reinterpret_cast<typename P::S*>(L.gstack) + (size_t)blockIdx.x * L.nz * 2 * 32 * 2;
     const int ntiles = (L.nx / 64) * (L.ny / 2);
-    sweep_x2_tiles<P, P, 2, PD, MODE_RESTRICT, 0>(L, 1.0, u, f, nullptr, false, blockIdx.x, ntiles, gridDim.x, slot,
+    sweep_x2_tiles<P, P, 2, PD, MODE_RESTRICT, 0>(L, K, u, f, nullptr, false, blockIdx.x, ntiles, gridDim.x, slot,
                                                  smem_raw, &xr);
 }
 
@@ -442,8 +442,8 @@ int launch_residual_restrict(const Lv<P>& L, const Lv<P>& Lc, double rho, const 
     const int slots = num_sms() * GS_BLOCKS_PER_SM * GS_MAX_NT / (2 * 32 * 2);
     if (nb > slots) nb = slots;
     if (nb > ntiles) nb = ntiles;
-    XRestrict<P> xr{Lc, rho, fc, uc};
-    kern<<<nb, dim3(32, 2), smem, s>>>(L, xr, u, f, done);
+    XRestrict<P> xr{Lc, P::hcst(rho), P::hcst(0.25), fc, uc};
+    kern<<<nb, dim3(32, 2), smem, s>>>(L, sweep_k<P>(L.cx, L.cy, 1.0), xr, u, f, done);
     note_launch();
     return nb;
 }

@@ -108,6 +108,27 @@ struct Lv {
     void* gstack = nullptr;
 };
 
+// A sweep's constants in the policy's arithmetic type: cx, cy, the horizontal part of the diagonal
+// 1 + 2 cx + 2 cy and the sweep's coefficient (rho, or 1), converted from double on the host. On this
+// part the FP64 pipe that a device-side conversion (and the double arithmetic of the diagonal) runs on
+// issues about one warp-instruction per 19 cycles per SM, so doing it per tile in an FP32 or
+// double-word kernel made every warp queue on that pipe at each tile start.
+template <class P>
+struct SweepK {
+    typename P::R cx, cy, dh, coef;
+    int iso;  // cx == cy: square cells, one product for the four horizontal neighbours
+};
+template <class P>
+inline SweepK<P> sweep_k(double cx, double cy, double coef) {
+    SweepK<P> k;
+    k.cx = P::hcst(cx);
+    k.cy = P::hcst(cy);
+    k.dh = P::hcst(1.0 + 2.0 * cx + 2.0 * cy);
+    k.coef = P::hcst(coef);
+    k.iso = cx == cy;
+    return k;
+}
+
 // persistent sweep variants: at most GS_BLOCKS_PER_SM blocks per SM, each covering at most GS_MAX_NT
 // columns, own a stack slot of the scratch
 static constexpr int GS_BLOCKS_PER_SM = 16;
@@ -310,6 +331,7 @@ struct BLevelDesc {  // FP32 view of one level of one problem
     const float* v;
     const float* finv;
     const float* fw;
+    SweepK<PolF32> k1, krho;  // the level's sweep constants with coefficient 1 and rho
 };
 struct BProbDesc {
     int L, nz;
@@ -317,6 +339,7 @@ struct BProbDesc {
     float2* uD;         // double-word finest iterate
     const float2* fD;   // double-word finest right-hand side
     const float2* vD;   // double-word finest v per column
+    SweepK<PolDW> kD;   // double-word constants of the finest level (coefficient 1)
     float* r32;         // FP32 right-hand side of the inner cycle (finest level)
     int part_base;      // first partial-sum slot of this problem's outer residual norm
     int fine_tiles;     // tiles of the outer residual (= its partial sums)

@@ -46,7 +46,8 @@ __host__ __device__ constexpr bool x2_slot(int mode) { return mode != MODE_RESID
 template <class P>
 struct XRestrict {
     Lv<P> Lc;
-    double rho;
+    typename P::R rho;      // converted on the host (P::hcst)
+    typename P::R quarter;  // 1/4, likewise
     typename P::S* fc;
     typename P::S* uc;
 };
@@ -67,13 +68,14 @@ constexpr int HINT_STREAM = 1, HINT_KEEP = 2, HINT_DISCARD = 4, HINT_ALL = 7;
 // per-thread load, store and cp.async moves a 16-byte pair (8 bytes in FP32), and the two
 // independent Thomas recurrences interleave. gstack is this block's scratch slot of nz x 64 TY
 // values (unused in residual and apply modes; the coarse columns' stack in restrict mode); smem_raw
-// its dynamic shared memory (sweep_x2_smem bytes). Every thread of the block must call it
-// (barriers). Shared ring per slot: u rows of stride UW = 68 (pad, left halo, 64 columns, right
+// its dynamic shared memory (sweep_x2_smem bytes); K the level's constants and the mode's
+// coefficient (rho for Smooth, the line solve's scale, 1 otherwise). Every thread of the block must
+// call it (barriers). Shared ring per slot: u rows of stride UW = 68 (pad, left halo, 64 columns, right
 // halo, pad), rows j0-1 .. j0+TY; f pairs; 1/m_k pairs (restrict mode: the coarse columns' 1/m_k,
 // then a two-plane buffer of the odd rows' pair sums). xr: the coarse level and outputs of restrict
 // mode (unused otherwise). Requires nx % 64 == 0, ny % TY == 0 and 16-byte aligned fields.
 template <class P, class PO, int TY, int PD, int MODE, int HINT = 0>
-__device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, const typename P::S* __restrict__ u,
+__device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, const SweepK<P>& K, const typename P::S* __restrict__ u,
                                                  const typename P::S* __restrict__ f,
                                                  typename PO::S* __restrict__ out, bool want_norm, int tile0,
                                                  int tile_end, int tile_step, typename P::S* gstack,
@@ -111,7 +113,7 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
     const S* rhs = (MODE == MODE_LINESOLVE) ? u : f;
     const R vzero = P::zero();
     typename P::Acc acc = 0, cmp = 0;
-    const bool iso = L.cx == L.cy;
+    const bool iso = K.iso != 0;
     const int k0 = L.fac_k0;
     unsigned long long pol_first = 0, pol_last = 0;
     if constexpr (HINT != 0) {
@@ -188,8 +190,7 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
             cw0 = P::ld(L.fw, r);
             cw1 = P::ld(L.fw, r + 1);
         }
-        const R cx = P::cst(L.cx), cy = P::cst(L.cy), cf = P::cst(coef);
-        const R dh = P::cst(1.0 + 2.0 * L.cx + 2.0 * L.cy);
+        const R cx = K.cx, cy = K.cy, cf = K.coef, dh = K.dh;
         const R dh1a = P::add(dh, v0), dh2a = P::add(dh1a, v0);
         const R dh1b = P::add(dh, v1), dh2b = P::add(dh1b, v1);
         R um0 = vzero, um1 = vzero, uc0 = vzero, uc1 = vzero, dp0 = vzero, dp1 = vzero;
@@ -302,7 +303,7 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
             if constexpr (RESTR) {
                 if (even) {
                     // f_c = 1/4 (even row pair + odd row pair), then the coarse forward elimination
-                    const R fk = P::mul(P::cst(0.25), P::add(qv, P::ld_plain(xs, (k & 1) * 32 * CR + ci)));
+                    const R fk = P::mul(xr->quarter, P::add(qv, P::ld_plain(xs, (k & 1) * 32 * CR + ci)));
                     P::st(xr->fc, (size_t)k * plc + cc, fk);
                     R ic;
                     if (xr->Lc.fac_percol && k >= xr->Lc.fac_k0 && k <= nz - 2)
@@ -406,7 +407,7 @@ __device__ __forceinline__ double sweep_x2_tiles(const Lv<P>& L, double coef, co
                     cp_commit();
                 };
                 for (int s = 0; s < PD; ++s) issue_back(nz - 1 - s, s);
-                const R rho = P::cst(xr->rho);
+                const R rho = xr->rho;
                 R xn = vzero;
                 slot = 0;
                 for (int k = nz - 1; k >= 0; --k) {
