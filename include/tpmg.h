@@ -367,6 +367,46 @@ tpmg_status tpmg_residual_norm_noalloc(int nx, int ny, int nz, double cx, double
                                        void* stream);
 const char* tpmg_noalloc_last_error(void);
 
+/* ---------------------------------------------------------------- the cubed-sphere panel operator
+ * The paper's own operator: Eq. (1) (Sec. 2.1) discretised by cell-centred finite volumes on one
+ * gnomonic cubed-sphere panel (Sec. 2.1.1: homogeneous Dirichlet on the panel boundary, Neumann at
+ * r = 1 and r = 1 + H), in the factorised form of Eq. (14):
+ *   A_{T,T'} = alpha_{TT'} I,   A_T = |T| diag(a) - alpha_T I + |T| tridiag(-(b + c), b, c),
+ * with |T| the cell's area on the unit sphere (exact), alpha_{TT'} = -omega2 |e| / d for each face
+ * (|e| the edge's great-circle length, d the great-circle distance of the cell centres; a face on the
+ * panel boundary couples to a ghost value of 0), alpha_T their sum, and the radial vectors of nz
+ * cells on [1, 1 + H]: a_k = (r_{k+1/2}^3 - r_{k-1/2}^3) / (3 h_z), b_k = -omega2 lambda2
+ * r_{k-1/2}^2 / h_z^2, c_k = -omega2 lambda2 r_{k+1/2}^2 / h_z^2 (b_0 = c_{nz-1} = 0), h_z = H / nz.
+ * The equations are integrated over the cells. Coarse levels rediscretise the same panel (Sec. 3.1).
+ * The panel [-extent, extent]^2 of cube-face coordinates (extent 1: a whole cube face) maps to the
+ * sphere by (X, Y, 1) / sqrt(1 + X^2 + Y^2). Native FP64 only.
+ *
+ * tpmg_mg_solve on a panel operator (prm->prec must be TPMG_F64) runs Algorithm 1 with these kernels:
+ * RestrictSmooth sums the 2 x 2 children's residuals (the integrated residual of the coarse cell),
+ * Prolongate is bilinear in the logical grid with a ghost value of 0 beyond the panel. Fields are
+ * DEVICE doubles, nz*ny*nx per level, x fastest. The unit entry points below run one kernel on level
+ * `level` (1 = coarsest) on the caller's stream; norm_out (DEVICE double or NULL) receives
+ * ||f - A u||. Errors: TPMG_ERR_ARG (not a panel operator, level out of range, NULL field). */
+tpmg_status tpmg_create_panel_operator(const tpmg_grid* g, double omega2, double lambda2, double H,
+                                       double extent, tpmg_op** out);
+/* the geometry of level `level` as computed by the library: HOST arrays |T| (ny*nx), x-face
+ * coefficients (ny*(nx+1), index j*(nx+1) + i for the face between cells i-1 and i) and y-face
+ * coefficients ((ny+1)*nx, index j*nx + i for the face between rows j-1 and j); any may be NULL */
+tpmg_status tpmg_panel_level_geometry(const tpmg_op* op, int level, double* area, double* ax, double* ay);
+tpmg_status tpmg_panel_apply_A(tpmg_op* op, int level, const double* x, double* y, void* stream);
+/* x = M^{-1} b, M the column blocks A_T (vertical line relaxation, Sec. 2.2) */
+tpmg_status tpmg_panel_line_solve(tpmg_op* op, int level, const double* b, double* x, void* stream);
+/* u_out = u + rho M^{-1}(f - A u) (Eq. (11)); u_out must not overlap u */
+tpmg_status tpmg_panel_smooth(tpmg_op* op, int level, double rho, const double* u, const double* f,
+                              double* u_out, double* norm_out, void* stream);
+tpmg_status tpmg_panel_residual(tpmg_op* op, int level, const double* u, const double* f, double* r,
+                                double* norm_out, void* stream);
+/* f_c = R r_fine (sum of the children), u_c = rho M_c^{-1} f_c on the coarse level `level` */
+tpmg_status tpmg_panel_restrict_smooth(tpmg_op* op, int level, double rho, const double* r_fine, double* f_c,
+                                       double* u_c, void* stream);
+/* u_f += P u_c with u_f on level `level` and u_c on level - 1 */
+tpmg_status tpmg_panel_prolongate(tpmg_op* op, int level, const double* u_c, double* u_f, void* stream);
+
 /* Batched solve: nprob independent problems (each its own operator, all on one device, no operator
  * twice) solved together by one cooperative persistent kernel -- the mixed-precision iterative
  * refinement of tpmg_mg_solve (prm->prec must be TPMG_MIXED) with the steps of every problem's

@@ -29,7 +29,8 @@ _P = ctypes.c_void_p
 
 def build(force: bool = False) -> str:
     """Compile the C oracle into oracle/liboracle.so with the host gcc (no -march flags)."""
-    srcs = [_SRC] + [os.path.join(_HERE, s) for s in ("nn_oracle.c",) if os.path.exists(os.path.join(_HERE, s))]
+    srcs = [_SRC] + [os.path.join(_HERE, s) for s in ("nn_oracle.c", "panel_oracle.c")
+                     if os.path.exists(os.path.join(_HERE, s))]
     newest = max(os.path.getmtime(s) for s in srcs)
     import platform
     stamp = _LIB + ".host"

@@ -10,12 +10,15 @@
 #include <math.h>
 #include <string.h>
 
+#include <cmath>
+
 #include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
 
 #include "kernels.cuh"
+#include "panel.cuh"
 #include "tpmg.h"
 
 using namespace tpmg;
@@ -101,6 +104,11 @@ struct tpmg_op {
     void* fcgbuf[3] = {};      // flexible CG scratch vectors (double-word)
     void* hio[3] = {};         // host-buffer solves: device f, u (finest level) and a transpose buffer
     cudaEvent_t hev[4] = {};   // host-buffer solves: start, solve start, solve end, end
+    // the cubed-sphere panel operator (tpmg_create_panel_operator; native FP64 only)
+    int panel = 0;
+    double* pgeo[MAXL + 1][3] = {};  // per level: |T|, x-face and y-face coefficients
+    double* prad[3] = {};            // radial E = a - b - c, B = -b, C = -c
+    double* pfac[MAXL + 1][3] = {};  // per level: Thomas factors 1/m, forward and backward multipliers
 };
 
 // ---------------------------------------------------------------- helpers
@@ -818,6 +826,13 @@ tpmg_status tpmg_destroy_operator(tpmg_op* op) {
     for (int t = 0; t < 3; ++t) dfree(op->hio[t]);
     for (int t = 0; t < 4; ++t)
         if (op->hev[t]) cudaEventDestroy(op->hev[t]);
+    for (int t = 0; t < 3; ++t) {
+        dfree((void*&)op->prad[t]);
+        for (int l = 0; l <= MAXL; ++l) {
+            dfree((void*&)op->pgeo[l][t]);
+            dfree((void*&)op->pfac[l][t]);
+        }
+    }
     delete op;
     return TPMG_OK;
 }
@@ -1130,6 +1145,9 @@ void tpmg_default_params(tpmg_params* p) {
     p->coarse_bf16 = 0;
 }
 
+static tpmg_status panel_mg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, void* u, tpmg_info* info,
+                                  void* stream);
+
 // The initial iterate: the caller's u, converted to the solve's storage, or zero without reading u.
 static tpmg_status init_u_dw(size_t n, const tpmg_params* prm, const void* u, float2* uD, cudaStream_t s) {
     if (prm->zero_guess) CK(cudaMemsetAsync(uD, 0, n * sizeof(float2), s));
@@ -1146,6 +1164,7 @@ tpmg_status tpmg_mg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, vo
                           void* stream) {
     TRY(check_params(op, prm));
     if (!f || !u) return set_err(TPMG_ERR_ARG, "NULL field");
+    if (op->panel) return panel_mg_solve(op, prm, f, u, info, stream);
     cudaStream_t s = (cudaStream_t)stream;
     const int L = op->g.L;
     const size_t n = lvl_cells(op, L);
@@ -2239,4 +2258,329 @@ extern "C" tpmg_status tpmg_fcg_solve(tpmg_op* op, tpmg_nn* nn, const float* aux
     if (hs->nonfinite) return set_err(TPMG_ERR_NONFINITE, "non-finite value in flexible CG");
     if (!hs->converged) return set_err(TPMG_ERR_NOT_CONVERGED, "max_iter reached");
     return TPMG_OK;
+}
+
+// ================================================================ the cubed-sphere panel operator
+// Eq. (1) on one gnomonic cubed-sphere panel (Sec. 2.1.1: cell-centred finite volumes, homogeneous
+// Dirichlet on the panel boundary, Neumann at the bottom and top) in the factorised form of Eq. (14).
+// The host computes the geometry of every level (the rediscretised panel, Sec. 3.1) and the radial
+// vectors once; k_panel.cu holds the kernels.
+
+namespace {
+
+struct V3 {
+    double x, y, z;
+};
+// the cube-face point (X, Y, 1) projected onto the unit sphere
+V3 gnomonic_point(double X, double Y) {
+    const double r = std::sqrt(1.0 + X * X + Y * Y);
+    return V3{X / r, Y / r, 1.0 / r};
+}
+// great-circle distance of two unit vectors (the atan2 form keeps short arcs accurate)
+double great_arc(const V3& p, const V3& q) {
+    const double cx = p.y * q.z - p.z * q.y, cy = p.z * q.x - p.x * q.z, cz = p.x * q.y - p.y * q.x;
+    return std::atan2(std::sqrt(cx * cx + cy * cy + cz * cz), p.x * q.x + p.y * q.y + p.z * q.z);
+}
+// antiderivative of the spherical area element (1 + X^2 + Y^2)^(-3/2) dX dY of the gnomonic map
+double gnomonic_area_prim(double X, double Y) { return std::atan(X * Y / std::sqrt(1.0 + X * X + Y * Y)); }
+
+// |T| (ny x nx), x-face coefficients (ny x (nx+1)) and y-face coefficients ((ny+1) x nx) of an
+// nx x ny grid on the panel [-ext, ext]^2: alpha = -omega^2 |e| / d, |e| the edge's great-circle
+// length, d the great-circle distance of the two cell centres (the images of the coordinate
+// midpoints; beyond the boundary the centre of the ghost cell of the extended grid).
+void panel_level_geometry(int nx, int ny, double omega2, double ext, std::vector<double>& area,
+                          std::vector<double>& ax, std::vector<double>& ay) {
+    auto xs = [&](int i) { return -ext + 2.0 * ext * i / nx; };  // corner coordinates
+    auto ys = [&](int j) { return -ext + 2.0 * ext * j / ny; };
+    auto xc = [&](int i) { return -ext + 2.0 * ext * (i + 0.5) / nx; };  // centres, i = -1 .. nx
+    auto yc = [&](int j) { return -ext + 2.0 * ext * (j + 0.5) / ny; };
+    area.assign((size_t)nx * ny, 0.0);
+    ax.assign((size_t)ny * (nx + 1), 0.0);
+    ay.assign((size_t)(ny + 1) * nx, 0.0);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+            area[(size_t)j * nx + i] = gnomonic_area_prim(xs(i + 1), ys(j + 1)) - gnomonic_area_prim(xs(i), ys(j + 1)) -
+                                       gnomonic_area_prim(xs(i + 1), ys(j)) + gnomonic_area_prim(xs(i), ys(j));
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i <= nx; ++i) {
+            const double e = great_arc(gnomonic_point(xs(i), ys(j)), gnomonic_point(xs(i), ys(j + 1)));
+            const double d = great_arc(gnomonic_point(xc(i - 1), yc(j)), gnomonic_point(xc(i), yc(j)));
+            ax[(size_t)j * (nx + 1) + i] = -omega2 * e / d;
+        }
+    for (int j = 0; j <= ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            const double e = great_arc(gnomonic_point(xs(i), ys(j)), gnomonic_point(xs(i + 1), ys(j)));
+            const double d = great_arc(gnomonic_point(xc(i), yc(j - 1)), gnomonic_point(xc(i), yc(j)));
+            ay[(size_t)j * nx + i] = -omega2 * e / d;
+        }
+}
+
+}  // namespace
+
+static PanelLv panel_view(const tpmg_op* op, int l) {
+    PanelLv L;
+    L.nx = op->g.lnx[l];
+    L.ny = op->g.lny[l];
+    L.nz = op->g.nz;
+    L.area = op->pgeo[l][0];
+    L.ax = op->pgeo[l][1];
+    L.ay = op->pgeo[l][2];
+    L.E = op->prad[0];
+    L.B = op->prad[1];
+    L.C = op->prad[2];
+    L.inv = op->pfac[l][0];
+    L.fl = op->pfac[l][1];
+    L.fw = op->pfac[l][2];
+    return L;
+}
+
+// the FP64 hierarchy of a panel operator (u, u', f, r per level; the finest u, f are the caller's)
+static tpmg_status panel_ensure_hier(tpmg_op* op) {
+    Hier& h = op->hier[0];
+    if (h.ready) return ensure_common(op);
+    const int L = op->g.L;
+    for (int l = 1; l <= L; ++l) {
+        const size_t bytes = lvl_cells(op, l) * sizeof(double);
+        TRY(dalloc(&h.ub[l], bytes));
+        TRY(dalloc(&h.r[l], bytes));
+        if (l < L) {
+            TRY(dalloc(&h.u[l], bytes));
+            TRY(dalloc(&h.f[l], bytes));
+        }
+    }
+    h.ready = true;
+    return ensure_common(op);
+}
+
+extern "C" tpmg_status tpmg_create_panel_operator(const tpmg_grid* g, double omega2, double lambda2, double H,
+                                                  double extent, tpmg_op** out) {
+    if (!g || !out) return set_err(TPMG_ERR_ARG, "NULL grid or output pointer");
+    *out = nullptr;
+    if (!(omega2 > 0.0) || !(lambda2 >= 0.0) || !(H > 0.0) || !(extent > 0.0 && extent <= 1.0))
+        return set_err(TPMG_ERR_ARG, "omega2 > 0, lambda2 >= 0, H > 0 and 0 < extent <= 1 required");
+    tpmg_op* op = new tpmg_op();
+    for (int p = 0; p < 3; ++p)
+        for (int l = 0; l <= MAXL; ++l) {
+            op->variant[p][l] = -1;
+            op->fac_k0[p][l] = 1 << 30;
+        }
+    op->g = *g;
+    op->panel = 1;
+    op->omega2 = omega2;
+    cudaGetDevice(&op->device);
+    const int L = g->L, nz = g->nz;
+    tpmg_status st = TPMG_OK;
+    auto fail = [&](tpmg_status s2) {
+        tpmg_destroy_operator(op);
+        return s2;
+    };
+    // radial vectors of r in [1, 1 + H] with nz cells: a_k = (r_{k+1/2}^3 - r_{k-1/2}^3) / (3 h_z),
+    // B_k = omega^2 lambda^2 r_{k-1/2}^2 / h_z^2 (0 at k = 0), C_k = B_{k+1} (0 at the top)
+    const double hz = H / nz;
+    std::vector<double> E(nz), B(nz), C(nz);
+    auto rface = [&](int k) { return 1.0 + H * k / nz; };
+    for (int k = 0; k < nz; ++k) B[k] = k == 0 ? 0.0 : omega2 * lambda2 * rface(k) * rface(k) / (hz * hz);
+    for (int k = 0; k < nz; ++k) {
+        C[k] = k + 1 < nz ? B[k + 1] : 0.0;
+        const double a = (std::pow(rface(k + 1), 3) - std::pow(rface(k), 3)) / (3.0 * hz);
+        E[k] = a + B[k] + C[k];
+    }
+    const std::vector<double>* rad[3] = {&E, &B, &C};
+    for (int t = 0; t < 3; ++t) {
+        if ((st = dalloc((void**)&op->prad[t], nz * sizeof(double))) != TPMG_OK) return fail(st);
+        if (cudaMemcpy(op->prad[t], rad[t]->data(), nz * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(set_err(TPMG_ERR_CUDA, "copy of the radial vectors failed"));
+    }
+    for (int l = L; l >= 1; --l) {
+        const int nx = g->lnx[l], ny = g->lny[l];
+        std::vector<double> geo[3];
+        panel_level_geometry(nx, ny, omega2, extent, geo[0], geo[1], geo[2]);
+        for (int t = 0; t < 3; ++t) {
+            if ((st = dalloc((void**)&op->pgeo[l][t], geo[t].size() * sizeof(double))) != TPMG_OK) return fail(st);
+            if (cudaMemcpy(op->pgeo[l][t], geo[t].data(), geo[t].size() * sizeof(double), cudaMemcpyHostToDevice) !=
+                cudaSuccess)
+                return fail(set_err(TPMG_ERR_CUDA, "copy of the panel geometry failed"));
+        }
+        for (int t = 0; t < 3; ++t)
+            if ((st = dalloc((void**)&op->pfac[l][t], lvl_cells(op, l) * sizeof(double))) != TPMG_OK) return fail(st);
+        launch_panel_factors(panel_view(op, l), op->pfac[l][0], op->pfac[l][1], op->pfac[l][2], 0);
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(set_err(TPMG_ERR_CUDA, "panel setup kernels failed"));
+    if (cudaStreamCreateWithFlags(&op->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&op->ev0) != cudaSuccess || cudaEventCreate(&op->ev1) != cudaSuccess)
+        return fail(set_err(TPMG_ERR_CUDA, "stream/event creation failed"));
+    *out = op;
+    return TPMG_OK;
+}
+
+extern "C" tpmg_status tpmg_panel_level_geometry(const tpmg_op* op, int level, double* area, double* ax, double* ay) {
+    TRY(check_level(op, level));
+    if (!op->panel) return set_err(TPMG_ERR_ARG, "not a panel operator");
+    const size_t nx = op->g.lnx[level], ny = op->g.lny[level];
+    const size_t sz[3] = {nx * ny, ny * (nx + 1), (ny + 1) * nx};
+    double* dst[3] = {area, ax, ay};
+    for (int t = 0; t < 3; ++t)
+        if (dst[t]) CK(cudaMemcpy(dst[t], op->pgeo[level][t], sz[t] * sizeof(double), cudaMemcpyDeviceToHost));
+    return TPMG_OK;
+}
+
+static tpmg_status panel_unit_check(tpmg_op* op, int level) {
+    TRY(check_level(op, level));
+    if (!op->panel) return set_err(TPMG_ERR_ARG, "not a panel operator (tpmg_create_panel_operator)");
+    return panel_ensure_hier(op);
+}
+
+extern "C" tpmg_status tpmg_panel_apply_A(tpmg_op* op, int level, const double* x, double* y, void* stream) {
+    TRY(panel_unit_check(op, level));
+    if (!x || !y) return set_err(TPMG_ERR_ARG, "NULL field");
+    launch_panel_sweep(PANEL_APPLY, panel_view(op, level), 1.0, x, nullptr, y, nullptr, nullptr, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+extern "C" tpmg_status tpmg_panel_line_solve(tpmg_op* op, int level, const double* b, double* x, void* stream) {
+    TRY(panel_unit_check(op, level));
+    if (!b || !x) return set_err(TPMG_ERR_ARG, "NULL field");
+    launch_panel_sweep(PANEL_LINESOLVE, panel_view(op, level), 1.0, b, nullptr, x, nullptr, nullptr,
+                       (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+extern "C" tpmg_status tpmg_panel_smooth(tpmg_op* op, int level, double rho, const double* u, const double* f,
+                                         double* u_out, double* norm_out, void* stream) {
+    TRY(panel_unit_check(op, level));
+    if (!u || !f || !u_out) return set_err(TPMG_ERR_ARG, "NULL field");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int np = launch_panel_sweep(PANEL_SMOOTH, panel_view(op, level), rho, u, f, u_out,
+                                      norm_out ? op->partials : nullptr, nullptr, s);
+    if (norm_out) launch_finalize_norm(op->partials, np, FIN_STORE, op->sc, nullptr, norm_out, s);
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+extern "C" tpmg_status tpmg_panel_residual(tpmg_op* op, int level, const double* u, const double* f, double* r,
+                                           double* norm_out, void* stream) {
+    TRY(panel_unit_check(op, level));
+    if (!u || !f || !r) return set_err(TPMG_ERR_ARG, "NULL field");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int np = launch_panel_sweep(PANEL_RESIDUAL, panel_view(op, level), 1.0, u, f, r,
+                                      norm_out ? op->partials : nullptr, nullptr, s);
+    if (norm_out) launch_finalize_norm(op->partials, np, FIN_STORE, op->sc, nullptr, norm_out, s);
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+extern "C" tpmg_status tpmg_panel_restrict_smooth(tpmg_op* op, int level, double rho, const double* r_fine,
+                                                  double* f_c, double* u_c, void* stream) {
+    TRY(panel_unit_check(op, level));
+    if (level >= op->g.L) return set_err(TPMG_ERR_ARG, "the coarse level must be below the finest");
+    if (!r_fine || !f_c || !u_c) return set_err(TPMG_ERR_ARG, "NULL field");
+    launch_panel_restrict_smooth(panel_view(op, level), rho, r_fine, f_c, u_c, nullptr, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+extern "C" tpmg_status tpmg_panel_prolongate(tpmg_op* op, int level, const double* u_c, double* u_f, void* stream) {
+    TRY(panel_unit_check(op, level));
+    if (level < 2) return set_err(TPMG_ERR_ARG, "the fine level must be above the coarsest");
+    if (!u_c || !u_f) return set_err(TPMG_ERR_ARG, "NULL field");
+    launch_panel_prolongate(op->g.lnx[level - 1], op->g.lny[level - 1], op->g.nz, u_c, u_f, nullptr,
+                            (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return TPMG_OK;
+}
+
+// One V-cycle of Algorithm 1 on the panel hierarchy after the finest level's first smoothing step,
+// as Cycle does for the flat box (RestrictSmooth opening every coarse level, nu_pre - 1 further
+// pre-smoothing steps, the residual, the recursion, the prolongation, nu_post post-smoothing steps;
+// n_coarse steps in all on the coarsest level).
+struct PanelCycle {
+    tpmg_op* op;
+    const tpmg_params* prm;
+    cudaStream_t s;
+    const int* done;
+    const double* fL;
+    void smooth(int l, double*& cur, double*& oth, const double* f) {
+        launch_panel_sweep(PANEL_SMOOTH, panel_view(op, l), prm->rho, cur, f, oth, nullptr, done, s);
+        double* t = cur;
+        cur = oth;
+        oth = t;
+    }
+    double* coarse(int l) {
+        Hier& h = op->hier[0];
+        double* cur = (double*)h.u[l];
+        double* oth = (double*)h.ub[l];
+        const double* f = (const double*)h.f[l];
+        launch_panel_restrict_smooth(panel_view(op, l), prm->rho, (const double*)h.r[l + 1], (double*)h.f[l], cur,
+                                     done, s);
+        if (l == 1) {
+            for (int t = 1; t < prm->n_coarse; ++t) smooth(l, cur, oth, f);
+            return cur;
+        }
+        for (int t = 1; t < prm->nu_pre; ++t) smooth(l, cur, oth, f);
+        return below(l, cur, oth, f);
+    }
+    // residual of level l, the coarser levels, prolongation and post-smoothing on level l
+    double* below(int l, double* cur, double* oth, const double* f) {
+        Hier& h = op->hier[0];
+        launch_panel_sweep(PANEL_RESIDUAL, panel_view(op, l), 1.0, cur, f, (double*)h.r[l], nullptr, done, s);
+        const double* uc = coarse(l - 1);
+        launch_panel_prolongate(op->g.lnx[l - 1], op->g.lny[l - 1], op->g.nz, uc, cur, done, s);
+        for (int t = 0; t < prm->nu_post; ++t) smooth(l, cur, oth, f);
+        return cur;
+    }
+    double* rest(double* cur, double* oth) {
+        const int L = op->g.L;
+        if (L == 1) {
+            for (int t = 1; t < prm->n_coarse; ++t) smooth(L, cur, oth, fL);
+            return cur;
+        }
+        for (int t = 1; t < prm->nu_pre; ++t) smooth(L, cur, oth, fL);
+        return below(L, cur, oth, fL);
+    }
+};
+
+static tpmg_status panel_mg_loop(tpmg_op* op, const tpmg_params* prm, double* A, const double* fL, cudaStream_t s) {
+    const int L = op->g.L;
+    const int* done = &op->sc->done;
+    double* B = (double*)op->hier[0].ub[L];
+    const size_t nfine = lvl_cells(op, L);
+    const PanelLv LL = panel_view(op, L);
+    launch_scalars_init(op->sc, prm->tol, prm->max_iter, s);
+    const int nparts = launch_panel_sweep(PANEL_SMOOTH, LL, prm->rho, A, fL, B, op->partials, done, s);
+    launch_finalize_norm(op->partials, nparts, FIN_MG_INIT, op->sc, op->history, nullptr, s);
+    CK(cudaGetLastError());
+    TRY(read_scalars(op, s));
+    auto body = [&](cudaStream_t st) {
+        PanelCycle c{op, prm, st, done, fL};
+        double* cur = c.rest(B, A);
+        if (cur != A) launch_copy<PolF64>(nfine, cur, A, done, st);
+        const int np = launch_panel_sweep(PANEL_SMOOTH, LL, prm->rho, A, fL, B, op->partials, done, st);
+        launch_finalize_norm(op->partials, np, FIN_MG_CYCLE, op->sc, op->history, nullptr, st);
+    };
+    std::vector<const void*> key = {A, fL, B, op->history, (const void*)(size_t)prm->nu_pre,
+                                    (const void*)(size_t)prm->nu_post, (const void*)(size_t)prm->n_coarse,
+                                    (const void*)(size_t)(prm->rho * 1e12)};
+    int guard = 0;
+    while (!op->sc_host->done && guard++ <= prm->max_iter + 1) {
+        TRY(run_iteration(op, 7, key, prm->use_graph != 0, s, body));
+        TRY(read_scalars(op, s));
+    }
+    return TPMG_OK;
+}
+
+static tpmg_status panel_mg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, void* u, tpmg_info* info,
+                                  void* stream) {
+    if (prm->prec != TPMG_F64) return set_err(TPMG_ERR_ARG, "the panel operator runs in native FP64 (TPMG_F64)");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = lvl_cells(op, op->g.L);
+    TRY(panel_ensure_hier(op));
+    TRY(ensure_history(op, prm->max_iter + 2));
+    CK(cudaEventRecord(op->ev0, s));
+    TRY(init_u(n, sizeof(double), prm, u, s));
+    TRY(panel_mg_loop(op, prm, (double*)u, (const double*)f, s));
+    CK(cudaEventRecord(op->ev1, s));
+    CK(cudaGetLastError());
+    return finish_info(op, info, s);
 }

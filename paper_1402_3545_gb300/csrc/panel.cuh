@@ -1,0 +1,40 @@
+// panel.cuh -- the cubed-sphere panel operator's level view and launchers (k_panel.cu), used by the
+// C-ABI layer. Native FP64.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace tpmg {
+
+// One multigrid level of the panel operator (Eq. (14)) as the kernels see it: nx x ny columns of
+// nz cells, x fastest. Geometry: area[j*nx + i] = |T|; ax[j*(nx+1) + i] the coefficient alpha of
+// the x-face between cells i-1 and i of row j (i = 0 and nx: the panel boundary); ay[j*nx + i] that
+// of the y-face between rows j-1 and j (j = 0..ny). Radial vectors (nz each, shared by the levels):
+// E = a - b - c, B = -b, C = -c with B[0] = C[nz-1] = 0 and C[k] = B[k+1]. Thomas factors per cell:
+// inv = 1/m_k, fl = |T| B_k / m_k, fw = |T| C_k / m_k.
+struct PanelLv {
+    int nx, ny, nz;
+    const double* area;
+    const double* ax;
+    const double* ay;
+    const double* E;
+    const double* B;
+    const double* C;
+    const double* inv;
+    const double* fl;
+    const double* fw;
+};
+
+enum { PANEL_SMOOTH = 0, PANEL_RESIDUAL = 1, PANEL_LINESOLVE = 2, PANEL_APPLY = 3 };
+
+void launch_panel_factors(const PanelLv& L, double* inv, double* fl, double* fw, cudaStream_t s);
+// mode PANEL_*: Smooth (coef = rho) and Residual write partial sums of ||f - A u||^2 when partials is
+// non-null; the line solve takes its right-hand side in u and scales by coef. Returns the number of
+// thread blocks (= partial sums written).
+int launch_panel_sweep(int mode, const PanelLv& L, double coef, const double* u, const double* f, double* out,
+                       double* partials, const int* done, cudaStream_t s);
+void launch_panel_restrict_smooth(const PanelLv& Lc, double rho, const double* rf, double* fc, double* uc,
+                                  const int* done, cudaStream_t s);
+void launch_panel_prolongate(int nxc, int nyc, int nz, const double* uc, double* uf, const int* done, cudaStream_t s);
+
+}  // namespace tpmg

@@ -76,6 +76,14 @@ _SIGNATURES = {
     "tpmg_default_params": [ctypes.POINTER(Params)],
     "tpmg_mg_solve": [_P, ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Info), _P],
     "tpmg_mg_solve_host": [_P, ctypes.POINTER(Params), _I, _P, _P, ctypes.POINTER(Info), _P, _P],
+    "tpmg_create_panel_operator": [_P, _D, _D, _D, _D, ctypes.POINTER(_P)],
+    "tpmg_panel_level_geometry": [_P, _I, _P, _P, _P],
+    "tpmg_panel_apply_A": [_P, _I, _P, _P, _P],
+    "tpmg_panel_line_solve": [_P, _I, _P, _P, _P],
+    "tpmg_panel_smooth": [_P, _I, _D, _P, _P, _P, _P, _P],
+    "tpmg_panel_residual": [_P, _I, _P, _P, _P, _P, _P],
+    "tpmg_panel_restrict_smooth": [_P, _I, _D, _P, _P, _P, _P],
+    "tpmg_panel_prolongate": [_P, _I, _P, _P, _P],
     "tpmg_vcycle": [_P, ctypes.POINTER(Params), _P, _P, _P],
     "tpmg_cg_solve": [_P, ctypes.POINTER(Params), _P, _P, ctypes.POINTER(Info), _P],
     "tpmg_mg_solve_batched": [_I, _P, ctypes.POINTER(Params), _P, _P, _P, _P],
@@ -604,6 +612,89 @@ def set_variant(op, prec, level, variant) -> None:
 
 
 # ---------------------------------------------------------------- convenience owner object
+# ---------------------------------------------------------------- the cubed-sphere panel operator
+def create_panel_operator(g: int, omega2: float, lambda2: float, H: float, extent: float = 1.0):
+    h = _P()
+    _check(load().tpmg_create_panel_operator(g, omega2, lambda2, H, extent, ctypes.byref(h)), "create_panel_operator")
+    return h.value
+
+
+def panel_level_geometry(op, level, nx, ny):
+    """(|T| (ny, nx), x-face coefficients (ny, nx + 1), y-face coefficients (ny + 1, nx)) as the
+    library computed them."""
+    import numpy as np
+    area, ax, ay = np.empty((ny, nx)), np.empty((ny, nx + 1)), np.empty((ny + 1, nx))
+    _check(load().tpmg_panel_level_geometry(op, level, area.ctypes.data_as(_P), ax.ctypes.data_as(_P),
+                                            ay.ctypes.data_as(_P)), "panel_level_geometry")
+    return area, ax, ay
+
+
+def panel_apply_A(op, level, x, y, n, stream=None):
+    _check(load().tpmg_panel_apply_A(op, level, _field(x, F64, n, "x"), _field(y, F64, n, "y"), _stream(stream)),
+           "panel_apply_A")
+
+
+def panel_line_solve(op, level, b, x, n, stream=None):
+    _check(load().tpmg_panel_line_solve(op, level, _field(b, F64, n, "b"), _field(x, F64, n, "x"), _stream(stream)),
+           "panel_line_solve")
+
+
+def panel_smooth(op, level, rho, u, f, u_out, n, norm_out=None, stream=None):
+    _check(load().tpmg_panel_smooth(op, level, rho, _field(u, F64, n, "u"), _field(f, F64, n, "f"),
+                                    _field(u_out, F64, n, "u_out"), _scalar_out(norm_out), _stream(stream)),
+           "panel_smooth")
+
+
+def panel_residual(op, level, u, f, r, n, norm_out=None, stream=None):
+    _check(load().tpmg_panel_residual(op, level, _field(u, F64, n, "u"), _field(f, F64, n, "f"),
+                                      _field(r, F64, n, "r"), _scalar_out(norm_out), _stream(stream)),
+           "panel_residual")
+
+
+def panel_restrict_smooth(op, level, rho, r_fine, f_c, u_c, n_fine, n_coarse, stream=None):
+    _check(load().tpmg_panel_restrict_smooth(op, level, rho, _field(r_fine, F64, n_fine, "r_fine"),
+                                             _field(f_c, F64, n_coarse, "f_c"), _field(u_c, F64, n_coarse, "u_c"),
+                                             _stream(stream)), "panel_restrict_smooth")
+
+
+def panel_prolongate(op, level, u_c, u_f, n_coarse, n_fine, stream=None):
+    _check(load().tpmg_panel_prolongate(op, level, _field(u_c, F64, n_coarse, "u_c"), _field(u_f, F64, n_fine, "u_f"),
+                                        _stream(stream)), "panel_prolongate")
+
+
+class PanelOperator:
+    """Owns a grid and a cubed-sphere panel operator (native FP64)."""
+
+    def __init__(self, nx, ny, nz, omega2, lambda2, H, extent=1.0, nlevels=0):
+        self.grid = create_grid(nx, ny, nz, nlevels)
+        self.op = None
+        self.op = create_panel_operator(self.grid, omega2, lambda2, H, extent)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.L = grid_nlevels(self.grid)
+
+    def level_shape(self, level):
+        nx, ny = grid_level_size(self.grid, level)
+        return (self.nz, ny, nx)
+
+    def level_n(self, level):
+        a, b, c = self.level_shape(level)
+        return a * b * c
+
+    def close(self):
+        if self.op:
+            destroy_operator(self.op)
+            self.op = None
+        if self.grid:
+            destroy_grid(self.grid)
+            self.grid = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Operator:
     """Owns a grid and an operator built from a workloads.Problem-like description."""
 

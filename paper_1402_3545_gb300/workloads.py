@@ -131,6 +131,43 @@ def robustness_coarse_steps(nlevels: int, nu_cfl: float) -> int:
     return row[min(row, key=lambda c: abs(c - nu_cfl))]
 
 
+@dataclasses.dataclass
+class PanelProblem:
+    """The paper's own problem, Eq. (1) on one gnomonic cubed-sphere panel (Sec. 2.1.1): nx x ny
+    cells on the panel, nz on r in [1, 1 + H], omega^2, lambda^2, the panel's half-width in cube-face
+    coordinates (1: a whole cube face)."""
+
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    omega2: float
+    lambda2: float
+    H: float
+    extent: float
+    nlevels: int
+    seed: int
+    rhs_kind: str
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def rhs(self) -> np.ndarray:
+        return make_rhs(self.nx, self.ny, self.nz, self.seed, self.rhs_kind)
+
+
+def panel(nx: int = 512, nz: int = 128, nu_cfl: float = 8.4, nlevels: int = 5) -> PanelProblem:
+    """The paper's single-GPU configuration on its own operator: an nx x nx panel (mean angular cell
+    width h = (pi/2) / nx), omega = nu_CFL h / 2 (Eq. (4), nu_CFL = 8.4), lambda^2 = 1 (the limit of
+    lambda(h) at high resolution, Sec. 2.1; the table of the companion paper is not available), an
+    atmosphere 10 km deep on the earth's 6371 km radius (H = 10/6371), 5 levels, N(0,1) right-hand
+    side from seed 0."""
+    h = 0.5 * np.pi / nx
+    return PanelProblem(f"panel_{nx}x{nx}x{nz}", nx, nx, nz, (0.5 * nu_cfl * h) ** 2, 1.0, 10.0 / 6371.0, 1.0,
+                        nlevels, 0, "normal")
+
+
 def batched(nprob: int = 64, seed: int = 0) -> list[Problem]:
     """Batched: sizes drawn uniformly from {64,128,256,512}^2 x {32,64,128} (seed 0), lambda^2
     log-uniform in [1e2, 1e4], problem b's uniform[-1,1] RHS from seed 1000 + b. Horizontal cells are
