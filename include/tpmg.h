@@ -381,6 +381,8 @@ const char* tpmg_noalloc_last_error(void);
  * The panel [-extent, extent]^2 of cube-face coordinates (extent 1: a whole cube face) maps to the
  * sphere by (X, Y, 1) / sqrt(1 + X^2 + Y^2). Native FP64 only.
  *
+ * tpmg_cg_solve on a panel operator (TPMG_F64) runs line-preconditioned CG with the fused SpMV and
+ * Tridiag kernels of Sec. 3.1 on the panel stencil.
  * tpmg_mg_solve on a panel operator (prm->prec must be TPMG_F64) runs Algorithm 1 with these kernels:
  * RestrictSmooth sums the 2 x 2 children's residuals (the integrated residual of the coarse cell),
  * Prolongate is bilinear in the logical grid with a ghost value of 0 beyond the panel. Fields are

@@ -1147,6 +1147,8 @@ void tpmg_default_params(tpmg_params* p) {
 
 static tpmg_status panel_mg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, void* u, tpmg_info* info,
                                   void* stream);
+static tpmg_status panel_cg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, void* u, tpmg_info* info,
+                                  void* stream);
 
 // The initial iterate: the caller's u, converted to the solve's storage, or zero without reading u.
 static tpmg_status init_u_dw(size_t n, const tpmg_params* prm, const void* u, float2* uD, cudaStream_t s) {
@@ -1457,6 +1459,7 @@ tpmg_status tpmg_cg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, vo
                           void* stream) {
     TRY(check_params(op, prm));
     if (!f || !u) return set_err(TPMG_ERR_ARG, "NULL field");
+    if (op->panel) return panel_cg_solve(op, prm, f, u, info, stream);
     cudaStream_t s = (cudaStream_t)stream;
     const int L = op->g.L;
     const size_t n = lvl_cells(op, L);
@@ -2580,6 +2583,53 @@ static tpmg_status panel_mg_solve(tpmg_op* op, const tpmg_params* prm, const voi
     CK(cudaEventRecord(op->ev0, s));
     TRY(init_u(n, sizeof(double), prm, u, s));
     TRY(panel_mg_loop(op, prm, (double*)u, (const double*)f, s));
+    CK(cudaEventRecord(op->ev1, s));
+    CK(cudaGetLastError());
+    return finish_info(op, info, s);
+}
+
+// Line-preconditioned CG on the panel (Sec. 2.2) with the fused SpMV and Tridiag kernels of Sec. 3.1,
+// the same iteration and device-side scalars as the flat-box CG.
+static tpmg_status panel_cg_solve(tpmg_op* op, const tpmg_params* prm, const void* fv, void* uv, tpmg_info* info,
+                                  void* stream) {
+    if (prm->prec != TPMG_F64) return set_err(TPMG_ERR_ARG, "the panel operator runs in native FP64 (TPMG_F64)");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = op->g.L;
+    const size_t n = lvl_cells(op, L);
+    TRY(panel_ensure_hier(op));
+    TRY(ensure_history(op, prm->max_iter + 2));
+    for (int t = 0; t < 4; ++t) TRY(dalloc(&op->cgbuf[0][t], n * sizeof(double)));
+    double* u = (double*)uv;
+    const double* f = (const double*)fv;
+    double* r = (double*)op->cgbuf[0][0];
+    double* z = (double*)op->cgbuf[0][1];
+    double* p = (double*)op->cgbuf[0][2];
+    double* q = (double*)op->cgbuf[0][3];
+    const PanelLv LL = panel_view(op, L);
+    const int nb = panel_blocks(LL.nx, LL.ny);
+    CK(cudaEventRecord(op->ev0, s));
+    TRY(init_u(n, sizeof(double), prm, u, s));
+    launch_scalars_init(op->sc, prm->tol, prm->max_iter, s);
+    launch_panel_sweep(PANEL_RESIDUAL, LL, 1.0, u, f, r, nullptr, nullptr, s);
+    CK(cudaMemsetAsync(p, 0, n * sizeof(double), s));
+    CK(cudaMemsetAsync(q, 0, n * sizeof(double), s));
+    launch_panel_cg_tridiag(LL, op->sc, r, q, z, op->partials, s);  // alpha = 0: z = M^{-1} r
+    launch_cg_beta(op->partials, nb, 1, op->sc, op->history, s);
+    CK(cudaGetLastError());
+    TRY(read_scalars(op, s));
+    auto body = [&](cudaStream_t st) {
+        launch_panel_cg_spmv(LL, op->sc, u, p, z, q, op->partials, st);
+        launch_cg_alpha(op->partials, nb, op->sc, st);
+        launch_panel_cg_tridiag(LL, op->sc, r, q, z, op->partials, st);
+        launch_cg_beta(op->partials, nb, 0, op->sc, op->history, st);
+    };
+    std::vector<const void*> key = {u, f, r, op->history};
+    int guard = 0;
+    while (!op->sc_host->done && guard++ <= prm->max_iter + 1) {
+        TRY(run_iteration(op, 4, key, prm->use_graph != 0, s, body));  // a panel operator runs no flat CG
+        TRY(read_scalars(op, s));
+    }
+    launch_cg_finish<PolF64>(n, op->sc, u, p, s);
     CK(cudaEventRecord(op->ev1, s));
     CK(cudaGetLastError());
     return finish_info(op, info, s);

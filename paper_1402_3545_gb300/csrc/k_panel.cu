@@ -198,7 +198,95 @@ __global__ void __launch_bounds__(128) k_panel_prolongate(int nxc, int nyc, int 
     }
 }
 
+// ---------------------------------------------------------------- fused CG kernels (Sec. 3.1)
+// SpMV: u += alpha p; p = z + beta p; q = A z + beta q; sigma = <p, q> (alpha, beta from the previous
+// iteration in the device scalars; the u update lags one iteration, as in the flat-box CG)
+__global__ void __launch_bounds__(128) k_panel_cg_spmv(PanelLv L, const Scalars* __restrict__ sc, double* u,
+                                                       double* p, const double* __restrict__ z, double* q,
+                                                       double* partials) {
+    if (*(volatile const int*)&sc->done) return;
+    const PCol c = panel_col(L);
+    const size_t pl = (size_t)L.nx * L.ny;
+    const double alpha = sc->alpha, beta = sc->beta;
+    double acc = 0.0;
+    if (c.act) {
+        double zm = 0.0, zc = __ldg(z + c.c), tb = 0.0;
+        for (int k = 0; k < L.nz; ++k) {
+            const size_t b = (size_t)k * pl, id = b + c.c;
+            const double tc = (k + 1 < L.nz) ? c.area * __ldg(L.B + k + 1) : 0.0;
+            const double zp = (k + 1 < L.nz) ? __ldg(z + id + pl) : 0.0;
+            const double az = panel_Au(L, c, z, b, k, zc, zm, zp, tb, tc);
+            const double po = p[id];
+            u[id] = fma(alpha, po, u[id]);
+            const double pn = fma(beta, po, zc);
+            const double qn = fma(beta, q[id], az);
+            p[id] = pn;
+            q[id] = qn;
+            acc = fma(pn, qn, acc);
+            zm = zc;
+            zc = zp;
+            tb = tc;
+        }
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+// Tridiag: r -= alpha q; z = M^{-1} r; partial sums of <r, r> (first nparts slots) and <r, z> (next)
+__global__ void __launch_bounds__(128) k_panel_cg_tridiag(PanelLv L, const Scalars* __restrict__ sc, double* r,
+                                                          const double* __restrict__ q, double* z, double* partials,
+                                                          int nparts) {
+    if (*(volatile const int*)&sc->done) return;
+    const PCol c = panel_col(L);
+    const size_t pl = (size_t)L.nx * L.ny;
+    const double alpha = sc->alpha;
+    double rr = 0.0, rz = 0.0;
+    if (c.act) {
+        double dp = 0.0;
+        for (int k = 0; k < L.nz; ++k) {
+            const size_t id = (size_t)k * pl + c.c;
+            const double rk = fma(-alpha, __ldg(q + id), r[id]);
+            r[id] = rk;
+            rr = fma(rk, rk, rr);
+            dp = fma(__ldg(L.fl + id), dp, rk * __ldg(L.inv + id));
+            z[id] = dp;
+        }
+        double x = 0.0;
+        for (int k = L.nz - 1; k >= 0; --k) {
+            const size_t id = (size_t)k * pl + c.c;
+            x = fma(__ldg(L.fw + id), x, z[id]);
+            z[id] = x;
+            rz = fma(r[id], x, rz);
+        }
+    }
+    const double s1 = block_sum(rr);
+    __syncthreads();
+    const double s2 = block_sum(rz);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        partials[blockIdx.y * gridDim.x + blockIdx.x] = s1;
+        partials[nparts + blockIdx.y * gridDim.x + blockIdx.x] = s2;
+    }
+}
+
 static dim3 panel_grid(int nx, int ny) { return dim3((nx + 31) / 32, (ny + 3) / 4); }
+
+int panel_blocks(int nx, int ny) {
+    const dim3 g = panel_grid(nx, ny);
+    return (int)(g.x * g.y);
+}
+
+void launch_panel_cg_spmv(const PanelLv& L, const Scalars* sc, double* u, double* p, const double* z, double* q,
+                          double* partials, cudaStream_t s) {
+    k_panel_cg_spmv<<<panel_grid(L.nx, L.ny), dim3(32, 4), 0, s>>>(L, sc, u, p, z, q, partials);
+    note_launch();
+}
+
+void launch_panel_cg_tridiag(const PanelLv& L, const Scalars* sc, double* r, const double* q, double* z,
+                             double* partials, cudaStream_t s) {
+    k_panel_cg_tridiag<<<panel_grid(L.nx, L.ny), dim3(32, 4), 0, s>>>(L, sc, r, q, z, partials,
+                                                                        panel_blocks(L.nx, L.ny));
+    note_launch();
+}
 
 void launch_panel_factors(const PanelLv& L, double* inv, double* fl, double* fw, cudaStream_t s) {
     k_panel_factors<<<panel_grid(L.nx, L.ny), dim3(32, 4), 0, s>>>(L, inv, fl, fw);

@@ -36,5 +36,13 @@ int launch_panel_sweep(int mode, const PanelLv& L, double coef, const double* u,
 void launch_panel_restrict_smooth(const PanelLv& Lc, double rho, const double* rf, double* fc, double* uc,
                                   const int* done, cudaStream_t s);
 void launch_panel_prolongate(int nxc, int nyc, int nz, const double* uc, double* uf, const int* done, cudaStream_t s);
+// fused CG kernels on the finest level (Sec. 3.1): SpMV writes one partial sum of <p, q> per block,
+// Tridiag those of <r, r> and then of <r, z> (panel_blocks(nx, ny) each)
+struct Scalars;
+int panel_blocks(int nx, int ny);
+void launch_panel_cg_spmv(const PanelLv& L, const Scalars* sc, double* u, double* p, const double* z, double* q,
+                          double* partials, cudaStream_t s);
+void launch_panel_cg_tridiag(const PanelLv& L, const Scalars* sc, double* r, const double* q, double* z,
+                             double* partials, cudaStream_t s);
 
 }  // namespace tpmg
