@@ -59,7 +59,7 @@ def parse_args():
                     help="precision of the --solve-only solves")
     ap.add_argument("--kernel-only", choices=["smooth", "residual", "restrict_smooth", "residual_restrict",
                                               "prolongate", "line_solve", "apply_A", "cg_spmv", "cg_tridiag",
-                                              "nn_forward", "alu_rate", "transpose"],
+                                              "nn_forward", "alu_rate", "transpose", "panel_smooth"],
                     help="launch only this finest-level kernel a few times (tile variant --variant, "
                          "no autotuning): the command a per-kernel ncu capture runs; alu_rate prints "
                          "the measured FP64 and FP32 arithmetic rates")
@@ -561,6 +561,25 @@ def run_kernel_only(args):
         print(json.dumps({"kernel": "nn_forward", "voxels": nvox, "ms_per_forward": round(ms, 4),
                           "tflops": round(nn_flops_per_voxel(2) * nvox / (ms * 1e-3) / 1e12, 2)}), flush=True)
         net.close()
+        return
+    if args.kernel_only == "panel_smooth":
+        # the finest-level Smooth of the cubed-sphere panel operator (512^2 x 128, native FP64)
+        pp = workloads.panel()
+        pop = tpmg.PanelOperator(pp.nx, pp.ny, pp.nz, pp.omega2, pp.lambda2, pp.H, pp.extent, nlevels=pp.nlevels)
+        f = torch.from_numpy(pp.rhs()).cuda().reshape(-1)
+        u = torch.zeros_like(f)
+        uo = torch.empty_like(f)
+        tpmg.panel_smooth(pop.op, pop.L, 2.0 / 3.0, u, f, uo, pp.n)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(max(args.steps, 1)):
+            tpmg.panel_smooth(pop.op, pop.L, 2.0 / 3.0, f, f, uo, pp.n)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel": "panel_smooth", "workload": pp.name,
+                          "ms_per_launch": round(e0.elapsed_time(e1) / max(args.steps, 1), 4)}), flush=True)
+        pop.close()
         return
     p = workloads.mid()
     op = tpmg.Operator.from_problem(p)
