@@ -343,6 +343,14 @@ static tpmg_status check_level(const tpmg_op* op, int level) {
     if (level < 1 || level > op->g.L) return set_err(TPMG_ERR_ARG, "level out of range");
     return TPMG_OK;
 }
+// entry points written for the flat box refuse a cubed-sphere panel operator (its own entry points
+// are tpmg_panel_*; tpmg_mg_solve, tpmg_cg_solve and tpmg_mg_solve_host serve both)
+static tpmg_status flat_only(const tpmg_op* op) {
+    if (op && op->panel)
+        return set_err(TPMG_ERR_ARG, "a panel operator: use tpmg_panel_* or tpmg_mg_solve / tpmg_cg_solve");
+    return TPMG_OK;
+}
+
 static int pid_of(tpmg_precision p) { return p == TPMG_F64 ? 0 : (p == TPMG_F32 ? 1 : 2); }
 
 // ---------------------------------------------------------------- the V-cycle (Algorithm 1)
@@ -838,6 +846,7 @@ tpmg_status tpmg_destroy_operator(tpmg_op* op) {
 }
 
 tpmg_status tpmg_op_reserve(tpmg_op* op, tpmg_precision prec) {
+    TRY(flat_only(op));
     if (!op) return set_err(TPMG_ERR_ARG, "NULL operator");
     switch (prec) {
         case TPMG_F64: TRY(ensure_hier(op, 0, false)); TRY(ensure_cg(op, 0)); break;
@@ -852,6 +861,7 @@ tpmg_status tpmg_op_reserve(tpmg_op* op, tpmg_precision prec) {
 }
 
 tpmg_status tpmg_op_level_coefficients(const tpmg_op* op, int level, double* cx, double* cy, double* v_host) {
+    TRY(flat_only(op));
     TRY(check_level(op, level));
     if (cx) *cx = op->cx[level];
     if (cy) *cy = op->cy[level];
@@ -906,6 +916,7 @@ static tpmg_status prep_unit(tpmg_op* op, tpmg_precision prec) {
 extern "C" {
 
 tpmg_status tpmg_apply_A(tpmg_op* op, int level, tpmg_precision prec, const void* x, void* y, void* stream) {
+    TRY(flat_only(op));
     TRY(check_level(op, level));
     if (prec == TPMG_DW && level < op->lsw_dw) prec = TPMG_F64;  // see DW_KAPPA_MAX
     if (!x || !y) return set_err(TPMG_ERR_ARG, "NULL field");
@@ -923,6 +934,7 @@ tpmg_status tpmg_apply_A(tpmg_op* op, int level, tpmg_precision prec, const void
 }
 
 tpmg_status tpmg_line_solve(tpmg_op* op, int level, tpmg_precision prec, const void* b, void* x, void* stream) {
+    TRY(flat_only(op));
     TRY(check_level(op, level));
     if (prec == TPMG_DW && level < op->lsw_dw) prec = TPMG_F64;  // see DW_KAPPA_MAX
     if (!x || !b) return set_err(TPMG_ERR_ARG, "NULL field");
@@ -941,6 +953,7 @@ tpmg_status tpmg_line_solve(tpmg_op* op, int level, tpmg_precision prec, const v
 
 tpmg_status tpmg_smooth(tpmg_op* op, int level, tpmg_precision prec, double rho, const void* u,
                         const void* f, void* u_out, double* norm_out, void* stream) {
+    TRY(flat_only(op));
     TRY(check_level(op, level));
     if (prec == TPMG_DW && level < op->lsw_dw) prec = TPMG_F64;  // see DW_KAPPA_MAX
     if (!u || !f || !u_out) return set_err(TPMG_ERR_ARG, "NULL field");
@@ -962,6 +975,7 @@ tpmg_status tpmg_smooth(tpmg_op* op, int level, tpmg_precision prec, double rho,
 
 tpmg_status tpmg_residual(tpmg_op* op, int level, tpmg_precision prec, const void* u, const void* f,
                           void* r, double* norm_out, void* stream) {
+    TRY(flat_only(op));
     TRY(check_level(op, level));
     if (prec == TPMG_DW && level < op->lsw_dw) prec = TPMG_F64;  // see DW_KAPPA_MAX
     if (!u || !f || !r) return set_err(TPMG_ERR_ARG, "NULL field");
@@ -983,6 +997,7 @@ tpmg_status tpmg_residual(tpmg_op* op, int level, tpmg_precision prec, const voi
 
 tpmg_status tpmg_restrict_smooth(tpmg_op* op, int level, tpmg_precision prec, double rho, const void* r_fine,
                                  void* f_c, void* u_c, void* stream) {
+    TRY(flat_only(op));
     TRY(check_level(op, level));
     if (prec == TPMG_DW && level < op->lsw_dw) prec = TPMG_F64;  // see DW_KAPPA_MAX
     if (level >= op->g.L) return set_err(TPMG_ERR_ARG, "restrict_smooth needs a coarse level < L");
@@ -1005,6 +1020,7 @@ tpmg_status tpmg_restrict_smooth(tpmg_op* op, int level, tpmg_precision prec, do
 tpmg_status tpmg_residual_restrict_smooth(tpmg_op* op, int level, tpmg_precision prec, double rho,
                                           const void* u_fine, const void* f_fine, void* f_c, void* u_c,
                                           void* stream) {
+    TRY(flat_only(op));
     TRY(check_level(op, level));
     if (level >= op->g.L) return set_err(TPMG_ERR_ARG, "residual_restrict_smooth needs a coarse level < L");
     if (!u_fine || !f_fine || !f_c || !u_c) return set_err(TPMG_ERR_ARG, "NULL field");
@@ -1050,6 +1066,7 @@ tpmg_status tpmg_set_allocator(tpmg_alloc_fn alloc_fn, tpmg_free_fn free_fn, voi
 }
 
 tpmg_status tpmg_set_fusion(tpmg_op* op, int enable) {
+    TRY(flat_only(op));
     if (!op) return set_err(TPMG_ERR_ARG, "NULL operator");
     const int on = enable != 0;
     if (op->fuse_restrict != on) {
@@ -1061,6 +1078,7 @@ tpmg_status tpmg_set_fusion(tpmg_op* op, int enable) {
 }
 
 tpmg_status tpmg_prolongate(tpmg_op* op, int level, tpmg_precision prec, const void* u_c, void* u_f, void* stream) {
+    TRY(flat_only(op));
     TRY(check_level(op, level));
     if (prec == TPMG_DW && level - 1 < op->lsw_dw) prec = TPMG_F64;
     if (level <= 1) return set_err(TPMG_ERR_ARG, "prolongate needs a fine level > 1");
@@ -1080,6 +1098,7 @@ tpmg_status tpmg_prolongate(tpmg_op* op, int level, tpmg_precision prec, const v
 
 tpmg_status tpmg_cg_fused_spmv(tpmg_op* op, tpmg_precision prec, double alpha, double beta, void* u, void* p,
                                const void* z, void* q, double* sigma_out, void* stream) {
+    TRY(flat_only(op));
     if (!op) return set_err(TPMG_ERR_ARG, "NULL operator");
     if (prec == TPMG_DW && op->lsw_dw > op->g.L) prec = TPMG_F64;
     if (!u || !p || !z || !q || !sigma_out) return set_err(TPMG_ERR_ARG, "NULL argument");
@@ -1106,6 +1125,7 @@ tpmg_status tpmg_cg_fused_spmv(tpmg_op* op, tpmg_precision prec, double alpha, d
 
 tpmg_status tpmg_cg_fused_tridiag(tpmg_op* op, tpmg_precision prec, double alpha, void* r, const void* q, void* z,
                                   double* rr_out, double* rz_out, void* stream) {
+    TRY(flat_only(op));
     if (!op) return set_err(TPMG_ERR_ARG, "NULL operator");
     if (prec == TPMG_DW && op->lsw_dw > op->g.L) prec = TPMG_F64;
     if (!r || !q || !z || !rr_out || !rz_out) return set_err(TPMG_ERR_ARG, "NULL argument");
@@ -1285,6 +1305,7 @@ tpmg_status tpmg_mg_solve_host(tpmg_op* op, const tpmg_params* prm, int layout, 
 }
 
 tpmg_status tpmg_vcycle(tpmg_op* op, const tpmg_params* prm, const void* f, void* u, void* stream) {
+    TRY(flat_only(op));
     TRY(check_params(op, prm));
     if (!f || !u) return set_err(TPMG_ERR_ARG, "NULL field");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1336,6 +1357,7 @@ tpmg_status tpmg_vcycle(tpmg_op* op, const tpmg_params* prm, const void* f, void
 unsigned long long tpmg_kernel_launches(void) { return launch_counter(); }
 
 tpmg_status tpmg_set_variant(tpmg_op* op, tpmg_precision prec, int level, int variant) {
+    TRY(flat_only(op));
     TRY(check_level(op, level));
     if (prec != TPMG_F64 && prec != TPMG_F32 && prec != TPMG_DW) return set_err(TPMG_ERR_ARG, "bad precision");
     if (variant < 0 || variant >= TPMG_NUM_VARIANTS) return set_err(TPMG_ERR_ARG, "bad variant");
@@ -1347,6 +1369,7 @@ tpmg_status tpmg_set_variant(tpmg_op* op, tpmg_precision prec, int level, int va
 }
 
 tpmg_status tpmg_autotune(tpmg_op* op, tpmg_precision prec, int reps, int* variants_out, void* stream) {
+    TRY(flat_only(op));
     if (!op || reps < 1) return set_err(TPMG_ERR_ARG, "NULL operator or reps < 1");
     if (prec != TPMG_F64 && prec != TPMG_F32 && prec != TPMG_DW) return set_err(TPMG_ERR_ARG, "bad precision");
     const int pid = pid_of(prec);
@@ -1391,6 +1414,7 @@ tpmg_status tpmg_autotune(tpmg_op* op, tpmg_precision prec, int reps, int* varia
 
 tpmg_status tpmg_time_kernel(tpmg_op* op, tpmg_precision prec, tpmg_kernel k, int reps, double* ms,
                              void* stream) {
+    TRY(flat_only(op));
     if (!op || !ms || reps < 1) return set_err(TPMG_ERR_ARG, "NULL operator/output or reps < 1");
     if (prec != TPMG_F64 && prec != TPMG_F32 && prec != TPMG_DW)
         return set_err(TPMG_ERR_ARG, "precision must be TPMG_F64, TPMG_F32 or TPMG_DW");
@@ -1740,6 +1764,7 @@ extern "C" tpmg_status tpmg_mg_solve_batched(int nprob, tpmg_op* const* ops, con
     const int dev = ops[0]->device;
     for (int b = 0; b < nprob; ++b) {
         if (!ops[b] || !f[b] || !u[b]) return set_err(TPMG_ERR_ARG, "NULL operator or field");
+        TRY(flat_only(ops[b]));
         if (ops[b]->device != dev) return set_err(TPMG_ERR_ARG, "all operators must live on one device");
         for (int c = 0; c < b; ++c)
             if (ops[c] == ops[b]) return set_err(TPMG_ERR_ARG, "an operator appears twice in the batch");
@@ -2056,6 +2081,7 @@ tpmg_status tpmg_nn_train_step(tpmg_nn* nn, int nx, int ny, int nz, const float*
 // r = channel 0 of x; its gradient w.r.t. the output is -2 D^{-1} A (r - A D^{-1} NN(x)) / n.
 tpmg_status tpmg_nn_loss_grad_residual(tpmg_nn* nn, tpmg_op* op, const float* x, double* loss_out, float* grad_out,
                                        void* stream) {
+    TRY(flat_only(op));
     if (!nn || !op || !x || !loss_out) return set_err(TPMG_ERR_ARG, "NULL argument");
     const int L = op->g.L, nx = op->g.nx, ny = op->g.ny, nz = op->g.nz;
     TRY(nn_check_shape(nx, ny, nz));
@@ -2121,6 +2147,7 @@ __global__ void k_bf16_to_f32(size_t n, const __nv_bfloat16* __restrict__ a, flo
 extern "C" tpmg_status tpmg_nn_make_pair(tpmg_op* op, int cin, const double* r, const double* u_star,
                                          const double* u_k, const float* aux, float* x_out, float* target_out,
                                          void* stream) {
+    TRY(flat_only(op));
     if (!op || (cin != 1 && cin != 2) || !r || !x_out || (cin == 2 && !aux) || (target_out && (!u_star || !u_k)))
         return set_err(TPMG_ERR_ARG, "bad arguments");
     const int L = op->g.L, nx = op->g.nx, ny = op->g.ny, nz = op->g.nz;
@@ -2159,6 +2186,7 @@ static tpmg_status read_fcg(tpmg_op* op, cudaStream_t s) {
 // correction, kept only when it lowers the residual.
 extern "C" tpmg_status tpmg_fcg_solve(tpmg_op* op, tpmg_nn* nn, const float* aux, const tpmg_params* prm,
                                       const double* f, double* u, tpmg_info* info, int* nn_accepted, void* stream) {
+    TRY(flat_only(op));
     TRY(check_params(op, prm));
     if (!f || !u) return set_err(TPMG_ERR_ARG, "NULL field");
     const int L = op->g.L;

@@ -143,6 +143,22 @@ def test_panel_refuses_other_precisions():
     op.close()
 
 
+def test_flat_entry_points_refuse_a_panel_operator():
+    """The flat-box entry points need the flat operator's buffers: given a panel operator they return
+    TPMG_ERR_ARG instead of touching memory the panel operator does not have."""
+    op, _ = _pair(64, 64, 4, 2)
+    n = op.level_n(2)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    for call in (lambda: tpmg.apply_A(op.op, 2, tpmg.F64, x, x.clone(), n),
+                 lambda: tpmg.smooth(op.op, 2, tpmg.F64, 0.8, x, x, x.clone(), n),
+                 lambda: tpmg.autotune(op.op, tpmg.F64, op.L),
+                 lambda: tpmg.time_kernel(op.op, tpmg.F64, tpmg.K_SMOOTH)):
+        with pytest.raises(tpmg.TpmgError) as e:
+            call()
+        assert e.value.status == tpmg.ERR_ARG
+    op.close()
+
+
 def test_paper_configuration_full_size():
     """512^2 x 128 on a whole cube face, the paper's solver settings: the GPU's cycles and iterate
     equal the oracle's (all host threads), and the residual recomputed by the oracle meets epsilon."""
