@@ -379,11 +379,14 @@ const char* tpmg_noalloc_last_error(void);
  * r_{k-1/2}^2 / h_z^2, c_k = -omega2 lambda2 r_{k+1/2}^2 / h_z^2 (b_0 = c_{nz-1} = 0), h_z = H / nz.
  * The equations are integrated over the cells. Coarse levels rediscretise the same panel (Sec. 3.1).
  * The panel [-extent, extent]^2 of cube-face coordinates (extent 1: a whole cube face) maps to the
- * sphere by (X, Y, 1) / sqrt(1 + X^2 + Y^2). Native FP64 only.
+ * sphere by (X, Y, 1) / sqrt(1 + X^2 + Y^2). The unit entry points and CG are native FP64.
  *
  * tpmg_cg_solve on a panel operator (TPMG_F64) runs line-preconditioned CG with the fused SpMV and
  * Tridiag kernels of Sec. 3.1 on the panel stencil.
- * tpmg_mg_solve on a panel operator (prm->prec must be TPMG_F64) runs Algorithm 1 with these kernels:
+ * tpmg_mg_solve on a panel operator runs Algorithm 1 in native FP64 (prm->prec TPMG_F64) or as
+ * iterative refinement (TPMG_MIXED): outer residual r = f - A u in FP64, one FP32 V-cycle on A e = r
+ * (geometry and Thomas factors rounded once from the FP64 ones), u += e in FP64, until the FP64
+ * residual meets prm->tol. Other precisions return TPMG_ERR_ARG. The cycle's kernels:
  * RestrictSmooth sums the 2 x 2 children's residuals (the integrated residual of the coarse cell),
  * Prolongate is bilinear in the logical grid with a ghost value of 0 beyond the panel. Fields are
  * DEVICE doubles, nz*ny*nx per level, x fastest. The unit entry points below run one kernel on level

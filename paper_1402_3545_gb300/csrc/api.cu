@@ -109,6 +109,9 @@ struct tpmg_op {
     double* pgeo[MAXL + 1][3] = {};  // per level: |T|, x-face and y-face coefficients
     double* prad[3] = {};            // radial E = a - b - c, B = -b, C = -c
     double* pfac[MAXL + 1][3] = {};  // per level: Thomas factors 1/m, forward and backward multipliers
+    float* pgeo32[MAXL + 1][3] = {};  // FP32 copies for the mixed solve's inner V-cycles
+    float* prad32[3] = {};
+    float* pfac32[MAXL + 1][3] = {};
 };
 
 // ---------------------------------------------------------------- helpers
@@ -836,9 +839,12 @@ tpmg_status tpmg_destroy_operator(tpmg_op* op) {
         if (op->hev[t]) cudaEventDestroy(op->hev[t]);
     for (int t = 0; t < 3; ++t) {
         dfree((void*&)op->prad[t]);
+        dfree((void*&)op->prad32[t]);
         for (int l = 0; l <= MAXL; ++l) {
             dfree((void*&)op->pgeo[l][t]);
             dfree((void*&)op->pfac[l][t]);
+            dfree((void*&)op->pgeo32[l][t]);
+            dfree((void*&)op->pfac32[l][t]);
         }
     }
     delete op;
@@ -2464,7 +2470,7 @@ static tpmg_status panel_unit_check(tpmg_op* op, int level) {
 extern "C" tpmg_status tpmg_panel_apply_A(tpmg_op* op, int level, const double* x, double* y, void* stream) {
     TRY(panel_unit_check(op, level));
     if (!x || !y) return set_err(TPMG_ERR_ARG, "NULL field");
-    launch_panel_sweep(PANEL_APPLY, panel_view(op, level), 1.0, x, nullptr, y, nullptr, nullptr, (cudaStream_t)stream);
+    launch_panel_sweep<double>(PANEL_APPLY, panel_view(op, level), 1.0, x, nullptr, y, nullptr, nullptr, (cudaStream_t)stream);
     CK(cudaGetLastError());
     return TPMG_OK;
 }
@@ -2472,7 +2478,7 @@ extern "C" tpmg_status tpmg_panel_apply_A(tpmg_op* op, int level, const double* 
 extern "C" tpmg_status tpmg_panel_line_solve(tpmg_op* op, int level, const double* b, double* x, void* stream) {
     TRY(panel_unit_check(op, level));
     if (!b || !x) return set_err(TPMG_ERR_ARG, "NULL field");
-    launch_panel_sweep(PANEL_LINESOLVE, panel_view(op, level), 1.0, b, nullptr, x, nullptr, nullptr,
+    launch_panel_sweep<double>(PANEL_LINESOLVE, panel_view(op, level), 1.0, b, nullptr, x, nullptr, nullptr,
                        (cudaStream_t)stream);
     CK(cudaGetLastError());
     return TPMG_OK;
@@ -2483,7 +2489,7 @@ extern "C" tpmg_status tpmg_panel_smooth(tpmg_op* op, int level, double rho, con
     TRY(panel_unit_check(op, level));
     if (!u || !f || !u_out) return set_err(TPMG_ERR_ARG, "NULL field");
     cudaStream_t s = (cudaStream_t)stream;
-    const int np = launch_panel_sweep(PANEL_SMOOTH, panel_view(op, level), rho, u, f, u_out,
+    const int np = launch_panel_sweep<double>(PANEL_SMOOTH, panel_view(op, level), rho, u, f, u_out,
                                       norm_out ? op->partials : nullptr, nullptr, s);
     if (norm_out) launch_finalize_norm(op->partials, np, FIN_STORE, op->sc, nullptr, norm_out, s);
     CK(cudaGetLastError());
@@ -2495,7 +2501,7 @@ extern "C" tpmg_status tpmg_panel_residual(tpmg_op* op, int level, const double*
     TRY(panel_unit_check(op, level));
     if (!u || !f || !r) return set_err(TPMG_ERR_ARG, "NULL field");
     cudaStream_t s = (cudaStream_t)stream;
-    const int np = launch_panel_sweep(PANEL_RESIDUAL, panel_view(op, level), 1.0, u, f, r,
+    const int np = launch_panel_sweep<double>(PANEL_RESIDUAL, panel_view(op, level), 1.0, u, f, r,
                                       norm_out ? op->partials : nullptr, nullptr, s);
     if (norm_out) launch_finalize_norm(op->partials, np, FIN_STORE, op->sc, nullptr, norm_out, s);
     CK(cudaGetLastError());
@@ -2522,29 +2528,89 @@ extern "C" tpmg_status tpmg_panel_prolongate(tpmg_op* op, int level, const doubl
     return TPMG_OK;
 }
 
-// One V-cycle of Algorithm 1 on the panel hierarchy after the finest level's first smoothing step,
-// as Cycle does for the flat box (RestrictSmooth opening every coarse level, nu_pre - 1 further
-// pre-smoothing steps, the residual, the recursion, the prolongation, nu_post post-smoothing steps;
-// n_coarse steps in all on the coarsest level).
+static PanelLvT<float> panel_view32(const tpmg_op* op, int l) {
+    PanelLvT<float> L;
+    L.nx = op->g.lnx[l];
+    L.ny = op->g.lny[l];
+    L.nz = op->g.nz;
+    L.area = op->pgeo32[l][0];
+    L.ax = op->pgeo32[l][1];
+    L.ay = op->pgeo32[l][2];
+    L.E = op->prad32[0];
+    L.B = op->prad32[1];
+    L.C = op->prad32[2];
+    L.inv = op->pfac32[l][0];
+    L.fl = op->pfac32[l][1];
+    L.fw = op->pfac32[l][2];
+    return L;
+}
+template <class T>
+static PanelLvT<T> panel_view_t(const tpmg_op* op, int l);
+template <>
+PanelLvT<double> panel_view_t<double>(const tpmg_op* op, int l) {
+    return panel_view(op, l);
+}
+template <>
+PanelLvT<float> panel_view_t<float>(const tpmg_op* op, int l) {
+    return panel_view32(op, l);
+}
+
+// FP32 copies of the geometry, radial vectors and Thomas factors (rounded from the FP64 ones) and the
+// FP32 hierarchy, for the mixed-precision solve's inner V-cycles
+static tpmg_status panel_ensure_f32(tpmg_op* op, cudaStream_t s) {
+    Hier& h = op->hier[1];
+    if (h.ready) return TPMG_OK;
+    const int L = op->g.L, nz = op->g.nz;
+    for (int t = 0; t < 3; ++t) {
+        TRY(dalloc((void**)&op->prad32[t], nz * sizeof(float)));
+        launch_f64_to_f32(nz, op->prad[t], op->prad32[t], s);
+    }
+    for (int l = 1; l <= L; ++l) {
+        const size_t nx = op->g.lnx[l], ny = op->g.lny[l], n = lvl_cells(op, l);
+        const size_t gsz[3] = {nx * ny, ny * (nx + 1), (ny + 1) * nx};
+        for (int t = 0; t < 3; ++t) {
+            TRY(dalloc((void**)&op->pgeo32[l][t], gsz[t] * sizeof(float)));
+            launch_f64_to_f32(gsz[t], op->pgeo[l][t], op->pgeo32[l][t], s);
+            TRY(dalloc((void**)&op->pfac32[l][t], n * sizeof(float)));
+            launch_f64_to_f32(n, op->pfac[l][t], op->pfac32[l][t], s);
+        }
+        const size_t bytes = n * sizeof(float);
+        TRY(dalloc(&h.u[l], bytes));
+        TRY(dalloc(&h.ub[l], bytes));
+        TRY(dalloc(&h.f[l], bytes));
+        TRY(dalloc(&h.r[l], bytes));
+    }
+    CK(cudaGetLastError());
+    h.ready = true;
+    return TPMG_OK;
+}
+
+// One V-cycle of Algorithm 1 on the panel hierarchy of value type T (FP64: op->hier[0]; FP32, the
+// mixed solve's inner cycle: op->hier[1]) after the finest level's first smoothing step, as Cycle
+// does for the flat box (RestrictSmooth opening every coarse level, nu_pre - 1 further pre-smoothing
+// steps, the residual, the recursion, the prolongation, nu_post post-smoothing steps; n_coarse steps
+// in all on the coarsest level).
+template <class T>
 struct PanelCycle {
     tpmg_op* op;
     const tpmg_params* prm;
     cudaStream_t s;
     const int* done;
-    const double* fL;
-    void smooth(int l, double*& cur, double*& oth, const double* f) {
-        launch_panel_sweep(PANEL_SMOOTH, panel_view(op, l), prm->rho, cur, f, oth, nullptr, done, s);
-        double* t = cur;
+    const T* fL;
+    Hier& hier() { return op->hier[sizeof(T) == 8 ? 0 : 1]; }
+    void smooth(int l, T*& cur, T*& oth, const T* f) {
+        launch_panel_sweep<T>(PANEL_SMOOTH, panel_view_t<T>(op, l), prm->rho, cur, f, oth, nullptr, done, s);
+        T* t = cur;
         cur = oth;
         oth = t;
     }
-    double* coarse(int l) {
-        Hier& h = op->hier[0];
-        double* cur = (double*)h.u[l];
-        double* oth = (double*)h.ub[l];
-        const double* f = (const double*)h.f[l];
-        launch_panel_restrict_smooth(panel_view(op, l), prm->rho, (const double*)h.r[l + 1], (double*)h.f[l], cur,
-                                     done, s);
+    T* coarse(int l) {
+        Hier& h = hier();
+        T* cur = (T*)h.u[l];
+        T* oth = (T*)h.ub[l];
+        const T* f = (const T*)h.f[l];
+        launch_panel_restrict_smooth<T>(panel_view_t<T>(op, l), prm->rho, (const T*)h.r[l + 1], (T*)h.f[l], cur, done,
+                                        s);
         if (l == 1) {
             for (int t = 1; t < prm->n_coarse; ++t) smooth(l, cur, oth, f);
             return cur;
@@ -2553,15 +2619,15 @@ struct PanelCycle {
         return below(l, cur, oth, f);
     }
     // residual of level l, the coarser levels, prolongation and post-smoothing on level l
-    double* below(int l, double* cur, double* oth, const double* f) {
-        Hier& h = op->hier[0];
-        launch_panel_sweep(PANEL_RESIDUAL, panel_view(op, l), 1.0, cur, f, (double*)h.r[l], nullptr, done, s);
-        const double* uc = coarse(l - 1);
-        launch_panel_prolongate(op->g.lnx[l - 1], op->g.lny[l - 1], op->g.nz, uc, cur, done, s);
+    T* below(int l, T* cur, T* oth, const T* f) {
+        Hier& h = hier();
+        launch_panel_sweep<T>(PANEL_RESIDUAL, panel_view_t<T>(op, l), 1.0, cur, f, (T*)h.r[l], nullptr, done, s);
+        const T* uc = coarse(l - 1);
+        launch_panel_prolongate<T>(op->g.lnx[l - 1], op->g.lny[l - 1], op->g.nz, uc, cur, done, s);
         for (int t = 0; t < prm->nu_post; ++t) smooth(l, cur, oth, f);
         return cur;
     }
-    double* rest(double* cur, double* oth) {
+    T* rest(T* cur, T* oth) {
         const int L = op->g.L;
         if (L == 1) {
             for (int t = 1; t < prm->n_coarse; ++t) smooth(L, cur, oth, fL);
@@ -2579,15 +2645,15 @@ static tpmg_status panel_mg_loop(tpmg_op* op, const tpmg_params* prm, double* A,
     const size_t nfine = lvl_cells(op, L);
     const PanelLv LL = panel_view(op, L);
     launch_scalars_init(op->sc, prm->tol, prm->max_iter, s);
-    const int nparts = launch_panel_sweep(PANEL_SMOOTH, LL, prm->rho, A, fL, B, op->partials, done, s);
+    const int nparts = launch_panel_sweep<double>(PANEL_SMOOTH, LL, prm->rho, A, fL, B, op->partials, done, s);
     launch_finalize_norm(op->partials, nparts, FIN_MG_INIT, op->sc, op->history, nullptr, s);
     CK(cudaGetLastError());
     TRY(read_scalars(op, s));
     auto body = [&](cudaStream_t st) {
-        PanelCycle c{op, prm, st, done, fL};
+        PanelCycle<double> c{op, prm, st, done, fL};
         double* cur = c.rest(B, A);
         if (cur != A) launch_copy<PolF64>(nfine, cur, A, done, st);
-        const int np = launch_panel_sweep(PANEL_SMOOTH, LL, prm->rho, A, fL, B, op->partials, done, st);
+        const int np = launch_panel_sweep<double>(PANEL_SMOOTH, LL, prm->rho, A, fL, B, op->partials, done, st);
         launch_finalize_norm(op->partials, np, FIN_MG_CYCLE, op->sc, op->history, nullptr, st);
     };
     std::vector<const void*> key = {A, fL, B, op->history, (const void*)(size_t)prm->nu_pre,
@@ -2601,16 +2667,59 @@ static tpmg_status panel_mg_loop(tpmg_op* op, const tpmg_params* prm, double* A,
     return TPMG_OK;
 }
 
+// Mixed precision on the panel: iterative refinement with the outer residual r = f - A u in native
+// FP64 (stored FP32), one FP32 V-cycle for A e = r from e = 0, u += e in FP64, until Eq. (10) holds.
+static tpmg_status panel_mixed_loop(tpmg_op* op, const tpmg_params* prm, double* u, const double* f, cudaStream_t s) {
+    const int L = op->g.L;
+    const int* done = &op->sc->done;
+    Hier& h32 = op->hier[1];
+    float* e = (float*)h32.u[L];
+    float* eb = (float*)h32.ub[L];
+    float* r32 = (float*)h32.f[L];
+    const size_t nfine = lvl_cells(op, L);
+    const PanelLv LD = panel_view(op, L);
+    const PanelLvT<float> L32 = panel_view32(op, L);
+    launch_scalars_init(op->sc, prm->tol, prm->max_iter, s);
+    const int nparts = launch_panel_residual_to_f32(LD, u, f, r32, op->partials, done, s);
+    launch_finalize_norm(op->partials, nparts, FIN_MG_INIT, op->sc, op->history, nullptr, s);
+    CK(cudaGetLastError());
+    TRY(read_scalars(op, s));
+    auto body = [&](cudaStream_t st) {
+        // first smoothing step from e = 0: e = rho M^{-1} r
+        launch_panel_sweep<float>(PANEL_LINESOLVE, L32, prm->rho, r32, nullptr, e, nullptr, done, st);
+        PanelCycle<float> c{op, prm, st, done, r32};
+        const float* cur = c.rest(e, eb);
+        launch_correct<PolF64>(nfine, u, cur, done, st);
+        const int np = launch_panel_residual_to_f32(LD, u, f, r32, op->partials, done, st);
+        launch_finalize_norm(op->partials, np, FIN_MG_CYCLE, op->sc, op->history, nullptr, st);
+    };
+    std::vector<const void*> key = {u, f, e, op->history, (const void*)(size_t)prm->nu_pre,
+                                    (const void*)(size_t)prm->nu_post, (const void*)(size_t)prm->n_coarse,
+                                    (const void*)(size_t)(prm->rho * 1e12)};
+    int guard = 0;
+    while (!op->sc_host->done && guard++ <= prm->max_iter + 1) {
+        TRY(run_iteration(op, 3, key, prm->use_graph != 0, s, body));  // a panel operator runs no flat mixed solve
+        TRY(read_scalars(op, s));
+    }
+    return TPMG_OK;
+}
+
 static tpmg_status panel_mg_solve(tpmg_op* op, const tpmg_params* prm, const void* f, void* u, tpmg_info* info,
                                   void* stream) {
-    if (prm->prec != TPMG_F64) return set_err(TPMG_ERR_ARG, "the panel operator runs in native FP64 (TPMG_F64)");
+    if (prm->prec != TPMG_F64 && prm->prec != TPMG_MIXED)
+        return set_err(TPMG_ERR_ARG, "the panel operator runs in native FP64 (TPMG_F64) or mixed (TPMG_MIXED)");
+    if (prm->coarse_bf16) return set_err(TPMG_ERR_ARG, "coarse_bf16 is a flat-box measurement");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = lvl_cells(op, op->g.L);
     TRY(panel_ensure_hier(op));
+    if (prm->prec == TPMG_MIXED) TRY(panel_ensure_f32(op, s));
     TRY(ensure_history(op, prm->max_iter + 2));
     CK(cudaEventRecord(op->ev0, s));
     TRY(init_u(n, sizeof(double), prm, u, s));
-    TRY(panel_mg_loop(op, prm, (double*)u, (const double*)f, s));
+    if (prm->prec == TPMG_MIXED)
+        TRY(panel_mixed_loop(op, prm, (double*)u, (const double*)f, s));
+    else
+        TRY(panel_mg_loop(op, prm, (double*)u, (const double*)f, s));
     CK(cudaEventRecord(op->ev1, s));
     CK(cudaGetLastError());
     return finish_info(op, info, s);
@@ -2638,7 +2747,7 @@ static tpmg_status panel_cg_solve(tpmg_op* op, const tpmg_params* prm, const voi
     CK(cudaEventRecord(op->ev0, s));
     TRY(init_u(n, sizeof(double), prm, u, s));
     launch_scalars_init(op->sc, prm->tol, prm->max_iter, s);
-    launch_panel_sweep(PANEL_RESIDUAL, LL, 1.0, u, f, r, nullptr, nullptr, s);
+    launch_panel_sweep<double>(PANEL_RESIDUAL, LL, 1.0, u, f, r, nullptr, nullptr, s);
     CK(cudaMemsetAsync(p, 0, n * sizeof(double), s));
     CK(cudaMemsetAsync(q, 0, n * sizeof(double), s));
     launch_panel_cg_tridiag(LL, op->sc, r, q, z, op->partials, s);  // alpha = 0: z = M^{-1} r

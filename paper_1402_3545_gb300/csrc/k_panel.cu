@@ -25,15 +25,17 @@ namespace tpmg {
 
 namespace {
 
+template <class T>
 struct PCol {
     int i, j;
     bool act, hw, he, hs, hn;  // in range; which horizontal neighbours lie on the panel
     size_t c;
-    double area, aw, ae, as, an, at;
+    T area, aw, ae, as, an, at;
 };
 
-__device__ __forceinline__ PCol panel_col(const PanelLv& L) {
-    PCol q;
+template <class T>
+__device__ __forceinline__ PCol<T> panel_col(const PanelLvT<T>& L) {
+    PCol<T> q;
     q.i = blockIdx.x * blockDim.x + threadIdx.x;
     q.j = blockIdx.y * blockDim.y + threadIdx.y;
     q.act = q.i < L.nx && q.j < L.ny;
@@ -54,13 +56,14 @@ __device__ __forceinline__ PCol panel_col(const PanelLv& L) {
 
 // (A u)_{T,k} given the centre value, its vertical neighbours (0 beyond the column) and
 // |T| B_k, |T| C_k; the horizontal neighbours of plane k are read here (0 beyond the panel)
-__device__ __forceinline__ double panel_Au(const PanelLv& L, const PCol& q, const double* __restrict__ x, size_t b,
-                                          int k, double uc, double um, double up, double tb, double tc) {
-    const double xw = q.hw ? __ldg(x + b + q.c - 1) : 0.0;
-    const double xe = q.he ? __ldg(x + b + q.c + 1) : 0.0;
-    const double xs = q.hs ? __ldg(x + b + q.c - L.nx) : 0.0;
-    const double xn = q.hn ? __ldg(x + b + q.c + L.nx) : 0.0;
-    double s = fma(q.area, __ldg(L.E + k), -q.at) * uc;  // the diagonal
+template <class T>
+__device__ __forceinline__ T panel_Au(const PanelLvT<T>& L, const PCol<T>& q, const T* __restrict__ x, size_t b, int k,
+                                     T uc, T um, T up, T tb, T tc) {
+    const T xw = q.hw ? __ldg(x + b + q.c - 1) : T(0);
+    const T xe = q.he ? __ldg(x + b + q.c + 1) : T(0);
+    const T xs = q.hs ? __ldg(x + b + q.c - L.nx) : T(0);
+    const T xn = q.hn ? __ldg(x + b + q.c + L.nx) : T(0);
+    T s = fma(q.area, __ldg(L.E + k), -q.at) * uc;  // the diagonal
     s = fma(q.aw, xw, s);
     s = fma(q.ae, xe, s);
     s = fma(q.as, xs, s);
@@ -76,7 +79,7 @@ __device__ __forceinline__ double panel_Au(const PanelLv& L, const PCol& q, cons
 // C_{k-1} = B_k); stored 1/m_k, |T| B_k / m_k and |T| C_k / m_k.
 __global__ void __launch_bounds__(128) k_panel_factors(PanelLv L, double* __restrict__ inv, double* __restrict__ fl,
                                                        double* __restrict__ fw) {
-    const PCol q = panel_col(L);
+    const PCol<double> q = panel_col(L);
     if (!q.act) return;
     const size_t pl = (size_t)L.nx * L.ny;
     double m_prev = 1.0;
@@ -93,29 +96,31 @@ __global__ void __launch_bounds__(128) k_panel_factors(PanelLv L, double* __rest
 }
 
 // MODE 0 Smooth: out = u + coef M^{-1} (f - A u) (Eq. (11)), partial sums of ||f - A u||^2
-// MODE 1 Residual: out = f - A u, partial sums of ||f - A u||^2
+// MODE 1 Residual: out = f - A u (stored in TO: the FP64 outer residual of the mixed solve is stored
+//        in FP32), partial sums of ||f - A u||^2
 // MODE 2 line solve: out = coef M^{-1} u (u is the right-hand side)
 // MODE 3 apply: out = A u
-template <int MODE>
-__global__ void __launch_bounds__(128) k_panel_sweep(PanelLv L, double coef, const double* __restrict__ u,
-                                                     const double* __restrict__ f, double* out, double* partials,
+// T is the arithmetic (double or float); the norm's partial sums are accumulated in T.
+template <int MODE, class T, class TO>
+__global__ void __launch_bounds__(128) k_panel_sweep(PanelLvT<T> L, T coef, const T* __restrict__ u,
+                                                     const T* __restrict__ f, TO* out, double* partials,
                                                      const int* done) {
     if (done && *(volatile const int*)done) return;
-    const PCol q = panel_col(L);
+    const PCol<T> q = panel_col(L);
     const size_t pl = (size_t)L.nx * L.ny;
     const int nz = L.nz;
-    double acc = 0.0;
+    T acc = 0;
     if (q.act) {
-        double um = 0.0, uc = (MODE != 2) ? __ldg(u + q.c) : 0.0, dp = 0.0;
-        double tb = 0.0;  // |T| B_k (B_0 = 0); |T| C_k = |T| B_{k+1} is carried to the next plane
+        T um = 0, uc = (MODE != 2) ? __ldg(u + q.c) : T(0), dp = 0;
+        T tb = 0;  // |T| B_k (B_0 = 0); |T| C_k = |T| B_{k+1} is carried to the next plane
 #pragma unroll 2
         for (int k = 0; k < nz; ++k) {
             const size_t b = (size_t)k * pl;
-            const double tc = (k + 1 < nz) ? q.area * __ldg(L.B + k + 1) : 0.0;
-            double r;
+            const T tc = (k + 1 < nz) ? q.area * __ldg(L.B + k + 1) : T(0);
+            T r;
             if (MODE != 2) {
-                const double up = (k + 1 < nz) ? __ldg(u + b + pl + q.c) : 0.0;
-                const double au = panel_Au(L, q, u, b, k, uc, um, up, tb, tc);
+                const T up = (k + 1 < nz) ? __ldg(u + b + pl + q.c) : T(0);
+                const T au = panel_Au(L, q, u, b, k, uc, um, up, tb, tc);
                 r = (MODE == 3) ? au : __ldg(f + b + q.c) - au;
                 um = uc;
                 uc = up;
@@ -129,44 +134,45 @@ __global__ void __launch_bounds__(128) k_panel_sweep(PanelLv L, double coef, con
                 dp = fma(__ldg(L.fl + b + q.c), dp, r * __ldg(L.inv + b + q.c));  // forward elimination
                 out[b + q.c] = dp;  // the output field holds d'_k until the back substitution
             } else {
-                out[b + q.c] = r;
+                out[b + q.c] = (TO)r;
             }
             tb = tc;
         }
         if (MODE == 0 || MODE == 2) {
-            double x = 0.0;
+            T x = 0;
             for (int k = nz - 1; k >= 0; --k) {
                 const size_t id = (size_t)k * pl + q.c;
-                x = fma(__ldg(L.fw + id), x, out[id]);
+                x = fma(__ldg(L.fw + id), x, (T)out[id]);
                 out[id] = (MODE == 0) ? fma(coef, x, __ldg(u + id)) : coef * x;
             }
         }
     }
     if ((MODE == 0 || MODE == 1) && partials) {
-        const double s = block_sum(acc);
+        const double s = block_sum((double)acc);
         if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
     }
 }
 
 // RestrictSmooth onto level Lc: f_c = sum of the 2 x 2 children's residuals r_f (the equations are
 // integrated over the cells), u_c = rho M_c^{-1} f_c (the first smoothing step from zero).
-__global__ void __launch_bounds__(128) k_panel_restrict_smooth(PanelLv Lc, double rho, const double* __restrict__ rf,
-                                                               double* __restrict__ fc, double* uc, const int* done) {
+template <class T>
+__global__ void __launch_bounds__(128) k_panel_restrict_smooth(PanelLvT<T> Lc, T rho, const T* __restrict__ rf,
+                                                               T* __restrict__ fc, T* uc, const int* done) {
     if (done && *(volatile const int*)done) return;
-    const PCol q = panel_col(Lc);
+    const PCol<T> q = panel_col(Lc);
     if (!q.act) return;
     const size_t plc = (size_t)Lc.nx * Lc.ny, nxf = 2 * (size_t)Lc.nx, plf = 4 * plc;
     const size_t f0 = (size_t)(2 * q.j) * nxf + 2 * q.i;
-    double dp = 0.0;
+    T dp = 0;
     for (int k = 0; k < Lc.nz; ++k) {
-        const double* r = rf + (size_t)k * plf + f0;
-        const double s = (__ldg(r) + __ldg(r + 1)) + (__ldg(r + nxf) + __ldg(r + nxf + 1));
+        const T* r = rf + (size_t)k * plf + f0;
+        const T s = (__ldg(r) + __ldg(r + 1)) + (__ldg(r + nxf) + __ldg(r + nxf + 1));
         const size_t id = (size_t)k * plc + q.c;
         fc[id] = s;
         dp = fma(__ldg(Lc.fl + id), dp, s * __ldg(Lc.inv + id));
         uc[id] = dp;
     }
-    double x = 0.0;
+    T x = 0;
     for (int k = Lc.nz - 1; k >= 0; --k) {
         const size_t id = (size_t)k * plc + q.c;
         x = fma(__ldg(Lc.fw + id), x, uc[id]);
@@ -176,8 +182,9 @@ __global__ void __launch_bounds__(128) k_panel_restrict_smooth(PanelLv Lc, doubl
 
 // u_f += P u_c: bilinear in the logical grid (weights 3/4 and 1/4 per direction), a coarse
 // neighbour beyond the panel boundary contributing 0. One thread per fine column.
-__global__ void __launch_bounds__(128) k_panel_prolongate(int nxc, int nyc, int nz, const double* __restrict__ uc,
-                                                          double* __restrict__ uf, const int* done) {
+template <class T>
+__global__ void __launch_bounds__(128) k_panel_prolongate(int nxc, int nyc, int nz, const T* __restrict__ uc,
+                                                          T* __restrict__ uf, const int* done) {
     if (done && *(volatile const int*)done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     const int nxf = 2 * nxc, nyf = 2 * nyc;
@@ -189,11 +196,11 @@ __global__ void __launch_bounds__(128) k_panel_prolongate(int nxc, int nyc, int 
     const size_t c0 = (size_t)J * nxc + I, cx = (size_t)J * nxc + I2, cy = (size_t)J2 * nxc + I,
                  cxy = (size_t)J2 * nxc + I2, fo = (size_t)j * nxf + i;
     for (int k = 0; k < nz; ++k) {
-        const double* p = uc + (size_t)k * plc;
-        double v = 0.5625 * __ldg(p + c0);
-        if (in2) v = fma(0.1875, __ldg(p + cx), v);
-        if (jn2) v = fma(0.1875, __ldg(p + cy), v);
-        if (in2 && jn2) v = fma(0.0625, __ldg(p + cxy), v);
+        const T* p = uc + (size_t)k * plc;
+        T v = T(0.5625) * __ldg(p + c0);
+        if (in2) v = fma(T(0.1875), __ldg(p + cx), v);
+        if (jn2) v = fma(T(0.1875), __ldg(p + cy), v);
+        if (in2 && jn2) v = fma(T(0.0625), __ldg(p + cxy), v);
         uf[(size_t)k * plf + fo] += v;
     }
 }
@@ -205,7 +212,7 @@ __global__ void __launch_bounds__(128) k_panel_cg_spmv(PanelLv L, const Scalars*
                                                        double* p, const double* __restrict__ z, double* q,
                                                        double* partials) {
     if (*(volatile const int*)&sc->done) return;
-    const PCol c = panel_col(L);
+    const PCol<double> c = panel_col(L);
     const size_t pl = (size_t)L.nx * L.ny;
     const double alpha = sc->alpha, beta = sc->beta;
     double acc = 0.0;
@@ -237,7 +244,7 @@ __global__ void __launch_bounds__(128) k_panel_cg_tridiag(PanelLv L, const Scala
                                                           const double* __restrict__ q, double* z, double* partials,
                                                           int nparts) {
     if (*(volatile const int*)&sc->done) return;
-    const PCol c = panel_col(L);
+    const PCol<double> c = panel_col(L);
     const size_t pl = (size_t)L.nx * L.ny;
     const double alpha = sc->alpha;
     double rr = 0.0, rz = 0.0;
@@ -293,28 +300,49 @@ void launch_panel_factors(const PanelLv& L, double* inv, double* fl, double* fw,
     note_launch();
 }
 
-int launch_panel_sweep(int mode, const PanelLv& L, double coef, const double* u, const double* f, double* out,
-                       double* partials, const int* done, cudaStream_t s) {
+template <class T>
+int launch_panel_sweep(int mode, const PanelLvT<T>& L, double coef, const T* u, const T* f, T* out, double* partials,
+                       const int* done, cudaStream_t s) {
     const dim3 g = panel_grid(L.nx, L.ny), b(32, 4);
+    const T c = (T)coef;
     switch (mode) {
-        case PANEL_SMOOTH: k_panel_sweep<0><<<g, b, 0, s>>>(L, coef, u, f, out, partials, done); break;
-        case PANEL_RESIDUAL: k_panel_sweep<1><<<g, b, 0, s>>>(L, coef, u, f, out, partials, done); break;
-        case PANEL_LINESOLVE: k_panel_sweep<2><<<g, b, 0, s>>>(L, coef, u, f, out, nullptr, done); break;
-        default: k_panel_sweep<3><<<g, b, 0, s>>>(L, coef, u, f, out, nullptr, done); break;
+        case PANEL_SMOOTH: k_panel_sweep<0, T, T><<<g, b, 0, s>>>(L, c, u, f, out, partials, done); break;
+        case PANEL_RESIDUAL: k_panel_sweep<1, T, T><<<g, b, 0, s>>>(L, c, u, f, out, partials, done); break;
+        case PANEL_LINESOLVE: k_panel_sweep<2, T, T><<<g, b, 0, s>>>(L, c, u, f, out, nullptr, done); break;
+        default: k_panel_sweep<3, T, T><<<g, b, 0, s>>>(L, c, u, f, out, nullptr, done); break;
     }
     note_launch();
     return (int)(g.x * g.y);
 }
 
-void launch_panel_restrict_smooth(const PanelLv& Lc, double rho, const double* rf, double* fc, double* uc,
-                                  const int* done, cudaStream_t s) {
-    k_panel_restrict_smooth<<<panel_grid(Lc.nx, Lc.ny), dim3(32, 4), 0, s>>>(Lc, rho, rf, fc, uc, done);
+int launch_panel_residual_to_f32(const PanelLv& L, const double* u, const double* f, float* r, double* partials,
+                                 const int* done, cudaStream_t s) {
+    const dim3 g = panel_grid(L.nx, L.ny);
+    k_panel_sweep<1, double, float><<<g, dim3(32, 4), 0, s>>>(L, 1.0, u, f, r, partials, done);
+    note_launch();
+    return (int)(g.x * g.y);
+}
+
+template <class T>
+void launch_panel_restrict_smooth(const PanelLvT<T>& Lc, double rho, const T* rf, T* fc, T* uc, const int* done,
+                                  cudaStream_t s) {
+    k_panel_restrict_smooth<T><<<panel_grid(Lc.nx, Lc.ny), dim3(32, 4), 0, s>>>(Lc, (T)rho, rf, fc, uc, done);
     note_launch();
 }
 
-void launch_panel_prolongate(int nxc, int nyc, int nz, const double* uc, double* uf, const int* done, cudaStream_t s) {
-    k_panel_prolongate<<<panel_grid(2 * nxc, 2 * nyc), dim3(32, 4), 0, s>>>(nxc, nyc, nz, uc, uf, done);
+template <class T>
+void launch_panel_prolongate(int nxc, int nyc, int nz, const T* uc, T* uf, const int* done, cudaStream_t s) {
+    k_panel_prolongate<T><<<panel_grid(2 * nxc, 2 * nyc), dim3(32, 4), 0, s>>>(nxc, nyc, nz, uc, uf, done);
     note_launch();
 }
+
+#define TPMG_PANEL_INST(T)                                                                                       \
+    template int launch_panel_sweep<T>(int, const PanelLvT<T>&, double, const T*, const T*, T*, double*, const int*, \
+                                       cudaStream_t);                                                            \
+    template void launch_panel_restrict_smooth<T>(const PanelLvT<T>&, double, const T*, T*, T*, const int*,        \
+                                                  cudaStream_t);                                                  \
+    template void launch_panel_prolongate<T>(int, int, int, const T*, T*, const int*, cudaStream_t);
+TPMG_PANEL_INST(double)
+TPMG_PANEL_INST(float)
 
 }  // namespace tpmg

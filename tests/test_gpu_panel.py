@@ -143,6 +143,36 @@ def test_panel_refuses_other_precisions():
     op.close()
 
 
+@pytest.mark.parametrize("tol", [1e-6, 1e-10])
+def test_mixed_precision_solve(tol):
+    """Iterative refinement on the panel: FP64 outer residual, FP32 V-cycles. The residual of its
+    solution, recomputed by the oracle, meets the tolerance; at 1e-10 the solution is within 1e-6 of
+    the oracle's multigrid solve to 1e-12 (the final-solution bound); the cycle count stays within two
+    of the FP64 multigrid's (the inner cycle is the same iteration in FP32)."""
+    nx, ny, nz, L = 128, 96, 32, 4
+    op, ref = _pair(nx, ny, nz, L)
+    f = np.random.default_rng(13).standard_normal((nz, ny, nx))
+    fd = dev(f).reshape(-1)
+    u = torch.zeros(f.size, dtype=torch.float64, device="cuda")
+    prm = dict(tol=tol, max_iter=80, nu_pre=1, nu_post=1, rho=2.0 / 3.0, zero_guess=1)
+    res = tpmg.mg_solve(op.op, tpmg.default_params(prec=tpmg.MIXED, **prm), fd, u, f.size)
+    assert res["converged"], res
+    uh = host(u).reshape(f.shape)
+    assert np.linalg.norm(ref.residual(uh, f)) / np.linalg.norm(f) < tol * 1.01
+    u64 = torch.zeros_like(u)
+    r64 = tpmg.mg_solve(op.op, tpmg.default_params(prec=tpmg.F64, **prm), fd, u64, f.size)
+    assert abs(res["iters"] - r64["iters"]) <= 2, (res["iters"], r64["iters"])
+    if tol <= 1e-10:
+        before = oracle.set_threads(0)
+        oracle.set_threads(64)
+        try:
+            u_star, _, _, _ = ref.mg_solve(f, tol=1e-12, max_iter=200, nu_pre=1, nu_post=1, rho=2.0 / 3.0)
+        finally:
+            oracle.set_threads(before)
+        assert rel(uh, u_star) < 1e-6
+    op.close()
+
+
 def test_flat_entry_points_refuse_a_panel_operator():
     """The flat-box entry points need the flat operator's buffers: given a panel operator they return
     TPMG_ERR_ARG instead of touching memory the panel operator does not have."""
