@@ -264,16 +264,20 @@ tpmg_status tpmg_measure_alu_rate(int which, int reps, double* ops_per_s, double
 /* ---------------------------------------------------------------- autotuning
  * The plane-pipelined Smooth has TPMG_NUM_VARIANTS variants: tile shapes (columns per block x ring
  * depth) with the Thomas stack in shared memory (0-2), persistent ones with the stack in global
- * scratch (3, 4), and persistent ones with two columns per thread that steer L2 residency of the
- * stack with eviction hints (5-7). A level that was never tuned or set takes variant 6 (double-word;
- * 5 in FP32) where it applies (nx % 64 == 0), else variant 3 (native FP64: variant 0).
+ * scratch (3, 4), persistent ones with two columns per thread that steer L2 residency of the stack
+ * with eviction hints (5-7), and, in FP32 only, one warp per tile of 128 x 1 or 128 x 2 columns with
+ * four columns per thread and the Thomas factors 1/m_k formed in registers (8-11: one-row tiles;
+ * one-row tiles run as overlapping forward/backward stages; two-row tiles; one-row tiles with a
+ * shallower ring). A level that was never tuned or set takes, in FP32, variant 8 where the level
+ * fits one tile per resident warp (nx % 128 == 0), else 5; double-word takes 6 where nx % 64 == 0;
+ * otherwise variant 3 (native FP64: variant 0). Variants 8-11 in other precisions run the default.
  * tpmg_autotune times each of them `reps` times on every level of precision `prec` (on the
  * operator's workspace, CUDA events on `stream`) and keeps the fastest per level; if variants_out
  * is not NULL it receives the choice of level l in variants_out[l] (host array of L+1 ints).
  * tpmg_set_variant sets one level's choice (e.g. from a saved tuning table). Both invalidate the
  * operator's cached CUDA graphs. Variants change the schedule, not the per-cell arithmetic (only the
  * grouping of the residual norm's partial sums differs). */
-#define TPMG_NUM_VARIANTS 8
+#define TPMG_NUM_VARIANTS 12
 tpmg_status tpmg_autotune(tpmg_op* op, tpmg_precision prec, int reps, int* variants_out, void* stream);
 tpmg_status tpmg_set_variant(tpmg_op* op, tpmg_precision prec, int level, int variant);
 

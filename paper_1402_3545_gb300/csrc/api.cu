@@ -1385,6 +1385,7 @@ tpmg_status tpmg_autotune(tpmg_op* op, tpmg_precision prec, int reps, int* varia
         double best = 1e300;
         int best_v = 0;
         for (int v = 0; v < TPMG_NUM_VARIANTS; ++v) {
+            if (v >= 8 && pid != 1) continue;  // the four-column tiles are FP32 only
             op->variant[pid][l] = v;
             auto run = [&](auto tag) {
                 typedef decltype(tag) P;

@@ -36,7 +36,11 @@ __global__ void k_factors(Lv<P> L, typename P::S* __restrict__ finv, typename P:
     R inv_prev = P::zero();
     for (int k = 0; k < L.nz; ++k) {
         R diag = (L.nz == 1) ? dh : ((k == 0 || k == L.nz - 1) ? dh1 : dh2);
-        R m = (k == 0) ? diag : P::sub(diag, P::mul(vv2, inv_prev));
+        R m;
+        if constexpr (P::id == 1)  // FP32: one rounding, as the four-column sweep forms it in registers
+            m = (k == 0) ? diag : fmaf(-vv2, inv_prev, diag);
+        else
+            m = (k == 0) ? diag : P::sub(diag, P::mul(vv2, inv_prev));
         R inv = P::rcp(m);
         const size_t id = percol ? (size_t)k * pl + c : (size_t)k;
         P::st(finv, id, inv);
@@ -474,7 +478,13 @@ template <class P>
 static int smooth_dispatch(const Lv<P>& L, double rho, const typename P::S* u, const typename P::S* f,
                            typename P::S* uo, double* partials, const int* done, cudaStream_t s) {
     int v = L.variant;
-    if (v < 0 || v >= TPMG_NUM_VARIANTS) {
+    if constexpr (std::is_same<P, PolF32>::value) {  // one tile of 128 x 2 columns per warp where the level takes it
+        if ((v < 0 || v >= TPMG_NUM_VARIANTS || v >= 8) && L.gstack) {
+            const int nb = launch_smooth_x4(L, rho, u, f, uo, partials, done, s, v >= 8 && v < TPMG_NUM_VARIANTS ? v - 8 : 0);
+            if (nb >= 0) return nb;
+        }
+    }
+    if (v < 0 || v >= TPMG_NUM_VARIANTS || v >= 8) {
         v = 0;
         if (L.gstack && P::id != 0) {  // native FP64 is bound by its slow pipe: one column per thread
             const int nb = P::id == 1
@@ -547,6 +557,12 @@ int launch_apply_A_x2(const Lv<P>& L, const typename P::S* x, typename P::S* y, 
 template <class P>
 int launch_line_solve_pp(const Lv<P>& L, const typename P::S* b, typename P::S* x, double scale, const int* done,
                          cudaStream_t s) {
+    if constexpr (std::is_same<P, PolF32>::value) {
+        if (L.gstack) {
+            const int nb = launch_line_solve_x4(L, b, x, scale, done, s);
+            if (nb >= 0) return nb;
+        }
+    }
     // two columns per thread with the stack in the L2-steered scratch where the level allows it
     if (L.gstack && P::id != 0) {
         const int nb = run_sweep_x2<P, P, 2, 4, MODE_LINESOLVE, 1, HINT_ALL>(L, scale, b, nullptr, x, nullptr, done, s, 8);

@@ -218,6 +218,12 @@ int launch_residual_pp(const Lv<P>& L, const typename P::S* u, const typename P:
 template <class P>
 int launch_line_solve_pp(const Lv<P>& L, const typename P::S* b, typename P::S* x, double scale, const int* done,
                          cudaStream_t s);
+// FP32 Smooth and line solve with one tile of 128 x 2 columns per warp (k_sweep4.cu): nx % 128 == 0,
+// ny even, 16-byte aligned fields and the level's scratch and factors, else -1; config picks the
+// ring depth and blocks per SM (0 the default)
+int launch_smooth_x4(const Lv<PolF32>& L, double rho, const float* u, const float* f, float* uo, double* partials,
+                     const int* done, cudaStream_t s, int config);
+int launch_line_solve_x4(const Lv<PolF32>& L, const float* b, float* x, double scale, const int* done, cudaStream_t s);
 // y = A x by the two-column sweep (nx % 64 == 0, 16-byte aligned fields), else -1
 template <class P>
 int launch_apply_A_x2(const Lv<P>& L, const typename P::S* x, typename P::S* y, cudaStream_t s);

@@ -596,7 +596,7 @@ def measure_alu_rate(which: int, reps: int = 3) -> tuple[float, float]:
     return rate.value, ms.value
 
 
-NUM_VARIANTS = 8
+NUM_VARIANTS = 12
 
 
 def autotune(op, prec, nlevels, reps=5, stream=None) -> list[int]:
