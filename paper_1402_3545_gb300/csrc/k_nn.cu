@@ -491,7 +491,7 @@ static void conv16(const NNBufs& b, const __nv_bfloat16* in, const __nv_bfloat16
 // per thread, keeps the input planes k-1, k, k+1 (one-cell halo) in a 4-slot ring and the weights
 // in shared memory as FP32, so every input value is read from memory once per tile and the weight
 // reads are shared-memory broadcasts. (The two-channel first layer and the last layer run on the
-// tensor cores: k_first_tc, k_last_tc.)
+// tensor cores: k_first_tc2, k_last_proj.)
 static constexpr int TCELLS = TXC * TYC;  // 128 cells per tile plane
 
 // thin input (C = 1 or 2 channels, bf16): plane kk of the tile into ring slot (kk + 1) & 3
@@ -605,11 +605,20 @@ __global__ void __launch_bounds__(128) k_first_z(const __nv_bfloat16* __restrict
 // ---------------------------------------------------------------- thin layers on the tensor cores
 // First layer (2 -> 16) as one implicit GEMM per 16 cells: K = 27 taps x 2 channels, padded to 64
 // (4 k16 blocks of 8 taps); an A fragment register holds the 2 channels of one cell and tap (one
-// 32-bit shared load), the B fragments (the weights) stay in registers for the whole kernel.
-__global__ void __launch_bounds__(128) k_first_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ W,
-                                                  const float* __restrict__ bias, __nv_bfloat16* __restrict__ out, int nx,
-                                                  int ny, int nz) {
-    __shared__ __align__(16) __nv_bfloat16 ring[4 * PLANE_CELLS * 2];
+// 32-bit shared load), the B fragments (the weights) stay in registers for the whole kernel. The
+// input planes arrive through a 6-slot cp.async ring (planes k+2 .. k+4 in flight while plane k is
+// computed; planes beyond the z ends are zeros), and the output tile is staged in shared memory, so
+// it leaves in coalesced 16-byte stores instead of 4-byte pieces of 32-byte cells.
+static constexpr int FP_SLOTS = 6;
+static constexpr int FP_PLANE = PLANE_CELLS * 2;  // bf16 values of one halo plane (2 channels)
+__device__ __forceinline__ void cp4nn(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa_nn(dst)), "l"(src));
+}
+__global__ void __launch_bounds__(128) k_first_tc2(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ W,
+                                                   const float* __restrict__ bias, __nv_bfloat16* __restrict__ out, int nx,
+                                                   int ny, int nz) {
+    __shared__ __align__(16) __nv_bfloat16 ring[FP_SLOTS * FP_PLANE];
+    __shared__ __align__(16) __nv_bfloat16 stage[TCELLS * 16];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, t = lane & 3, t2 = 2 * t;
     // B fragments: k = 2 j + ci within block kb <-> tap 8 kb + j; column n = output channel
@@ -631,13 +640,26 @@ __global__ void __launch_bounds__(128) k_first_tc(const __nv_bfloat16* __restric
     const float bc0 = __ldg(bias + t2), bc1 = __ldg(bias + t2 + 1), bc8 = __ldg(bias + t2 + 8), bc9 = __ldg(bias + t2 + 9);
     const int tiles_x = nx / TXC, ntiles = tiles_x * (ny / TYC);
     const int yw = warp >> 1, xw = (warp & 1) * 32;
+    // plane kk (-1 <= kk) of the tile's halo into slot (kk + 1) % FP_SLOTS, one group per plane
+    auto issue = [&](int x0, int y0, int kk) {
+        __nv_bfloat16* P = ring + ((kk + 1) % FP_SLOTS) * FP_PLANE;
+        for (int q = tid; q < PLANE_CELLS; q += 128) {
+            if (kk >= 0 && kk < nz) {
+                const int i = nwrap(x0 - 1 + q % HX, nx), j = nwrap(y0 - 1 + q / HX, ny);
+                cp4nn(P + 2 * q, in + (((size_t)kk * ny + j) * nx + i) * 2);
+            } else {
+                *reinterpret_cast<uint32_t*>(P + 2 * q) = 0u;
+            }
+        }
+        cp_commit_nn();
+    };
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int x0 = (tile % tiles_x) * TXC, y0 = (tile / tiles_x) * TYC;
-        __syncthreads();
-        load_thin<2>(in, ring, nx, ny, nz, x0, y0, -1);
-        load_thin<2>(in, ring, nx, ny, nz, x0, y0, 0);
+        __syncthreads();  // the previous tile's ring and output stage are no longer read
+        for (int kk = -1; kk <= 3; ++kk) issue(x0, y0, kk);
         for (int k = 0; k < nz; ++k) {
-            load_thin<2>(in, ring, nx, ny, nz, x0, y0, k + 1);
+            issue(x0, y0, k + 4);
+            cp_wait_nn<3>();  // planes k-1, k, k+1 have landed
             __syncthreads();
             float c[2][2][4];
 #pragma unroll
@@ -653,7 +675,7 @@ __global__ void __launch_bounds__(128) k_first_tc(const __nv_bfloat16* __restric
                 for (int r = 0; r < 2; ++r) {  // r = 0: taps 8 kb + t, r = 1: taps 8 kb + t + 4
                     const int tap = 8 * kb + t + 4 * r;
                     const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-                    const uint32_t* P = reinterpret_cast<const uint32_t*>(ring + ((k + dz) & 3) * (PLANE_CELLS * 2));
+                    const uint32_t* P = reinterpret_cast<const uint32_t*>(ring + ((k + dz) % FP_SLOTS) * FP_PLANE);
 #pragma unroll
                     for (int m = 0; m < 2; ++m) {
                         const int cell = (yw + dy) * HX + xw + 16 * m + g + dx;
@@ -663,90 +685,126 @@ __global__ void __launch_bounds__(128) k_first_tc(const __nv_bfloat16* __restric
                 }
 #pragma unroll
                 for (int m = 0; m < 2; ++m) {
-                    // fragment order: a0 (row g, k 2t), a1 (row g+8, k 2t), a2 (row g, k 2t+8), a3 (row g+8, k 2t+8)
                     mma16816(c[m][0], a[m][0], a[m][1], a[m][2], a[m][3], bf[kb][0][0], bf[kb][0][1]);
                     mma16816(c[m][1], a[m][0], a[m][1], a[m][2], a[m][3], bf[kb][1][0], bf[kb][1][1]);
                 }
             }
-            const int y = y0 + yw;
 #pragma unroll
             for (int m = 0; m < 2; ++m)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const size_t p = ((size_t)k * ny + y) * nx + x0 + xw + 16 * m + g + 8 * h;
-                    *reinterpret_cast<__nv_bfloat162*>(out + p * 16 + t2) =
+                    const int cell = yw * TXC + xw + 16 * m + g + 8 * h;
+                    *reinterpret_cast<__nv_bfloat162*>(stage + cell * 16 + t2) =
                         __floats2bfloat162_rn(fmaxf(c[m][0][2 * h] + bc0, 0.f), fmaxf(c[m][0][2 * h + 1] + bc1, 0.f));
-                    *reinterpret_cast<__nv_bfloat162*>(out + p * 16 + t2 + 8) =
+                    *reinterpret_cast<__nv_bfloat162*>(stage + cell * 16 + t2 + 8) =
                         __floats2bfloat162_rn(fmaxf(c[m][1][2 * h] + bc8, 0.f), fmaxf(c[m][1][2 * h + 1] + bc9, 0.f));
                 }
-            __syncthreads();
+            __syncthreads();  // the output tile is staged; the ring's planes k-1 .. k+1 are read
+            for (int q = tid; q < TCELLS * 2; q += 128) {
+                const int cell = q >> 1, half = q & 1;
+                const size_t p = ((size_t)k * ny + y0 + cell / TXC) * nx + x0 + cell % TXC;
+                *reinterpret_cast<uint4*>(out + p * 16 + half * 8) = *reinterpret_cast<const uint4*>(stage + cell * 16 + half * 8);
+            }
         }
+        cp_wait_nn<0>();
     }
 }
 
-// Last layer (16 -> 1) on the tensor cores: per tap one m16n8k16 MMA with the activations as A
-// (ldmatrix from the swizzled plane ring) and W4[:, tap] as the only non-zero column of B.
-__global__ void __launch_bounds__(128) k_last_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ W,
-                                                 const float* __restrict__ bias, float* __restrict__ out, int nx, int ny,
-                                                 int nz) {
+// Last layer (16 -> 1) by in-plane tap projections: out[v] = b + sum over (dy, dx) of
+// Q_{dy,dx}[v + (dy-1, dx-1)] with Q_{dy,dx}[c] = sum over dz and ci of W4[ci][dz,dy,dx] a_{k-1+dz}[c][ci].
+// Per output plane k one small GEMM on the tensor cores forms Q for every cell of the tile's 66 x 4
+// halo (M = 16 cells, K = 48: the three planes k-1 .. k+1 x 16 channels, N = the 9 in-plane taps
+// padded to 16); Q goes to shared memory tap-major and each thread sums its cell's 9 shifted
+// values. Against one MMA per tap with a single non-zero B column (the earlier form) this is 102
+// instead of 216 MMAs per plane of a 128-cell tile, with 9 shared stores and loads per cell; the
+// activation planes arrive through a 5-slot cp.async ring (planes beyond the z ends are zeros).
+static constexpr int LP_CELLS = 272;  // 66 x 4 halo cells padded to 17 m16 tiles
+static constexpr int LP_PS = 276;     // tap-row stride of Q (conflict-free stores and gathers)
+static constexpr int LP_SLOTS = 5;    // planes k-1 .. k+1 read, k+2 and k+3 in flight
+static constexpr size_t LP_SMEM = (size_t)LP_SLOTS * LP_CELLS * 32 + (size_t)9 * LP_PS * 4;
+
+__global__ void __launch_bounds__(128) k_last_proj(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ W,
+                                                   const float* __restrict__ bias, float* __restrict__ out, int nx,
+                                                   int ny, int nz) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint2* bt = reinterpret_cast<uint2*>(smem);  // [tap][lane] B fragments
-    unsigned char* ring = smem + 27 * 32 * 8;
+    unsigned char* ring = smem;
+    float* Q = reinterpret_cast<float*>(smem + (size_t)LP_SLOTS * LP_CELLS * 32);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = lane >> 2, t2 = (lane & 3) * 2;
-    for (int q = tid; q < 27 * 32; q += blockDim.x) {
-        const int tap = q / 32, ln = q % 32, lg = ln >> 2, lt = (ln & 3) * 2;
-        __nv_bfloat162 b0 = __floats2bfloat162_rn(0.f, 0.f), b1 = b0;
-        if (lg == 0) {  // column n = 0 is the output channel
-            b0.x = W[lt * 27 + tap];
-            b0.y = W[(lt + 1) * 27 + tap];
-            b1.x = W[(lt + 8) * 27 + tap];
-            b1.y = W[(lt + 9) * 27 + tap];
+    // B fragments of W4 for k-block dz (16 channels) and n-tile nt: column n = dy*3 + dx (< 9)
+    uint32_t bf[3][2][2];
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const int n = g + 8 * nt, tap = dz * 9 + n;
+            __nv_bfloat162 b0 = __floats2bfloat162_rn(0.f, 0.f), b1 = b0;
+            if (n < 9) {
+                b0.x = W[t2 * 27 + tap];
+                b0.y = W[(t2 + 1) * 27 + tap];
+                b1.x = W[(t2 + 8) * 27 + tap];
+                b1.y = W[(t2 + 9) * 27 + tap];
+            }
+            bf[dz][nt][0] = *reinterpret_cast<uint32_t*>(&b0);
+            bf[dz][nt][1] = *reinterpret_cast<uint32_t*>(&b1);
         }
-        bt[q] = make_uint2(*reinterpret_cast<uint32_t*>(&b0), *reinterpret_cast<uint32_t*>(&b1));
-    }
     const float b4 = __ldg(bias);
     const int tiles_x = nx / TXC, ntiles = tiles_x * (ny / TYC);
-    const int yw = warp >> 1, xw = (warp & 1) * 32;
-    const int ar = lane & 15, acol = (lane >> 4) * 8;
+    const int tx = tid & 63, ty = tid >> 6;  // this thread's output cell of the 64 x 2 tile
+    const int ar = lane & 15, ah = lane >> 4;
+    // plane kk (-1 <= kk) of the tile's halo into ring slot (kk + 1) % LP_SLOTS: 16-byte halves of the
+    // swizzled cell rows by cp.async, zeros beyond the z ends; one group per plane
+    auto issue = [&](int x0, int y0, int kk) {
+        unsigned char* S = ring + ((kk + 1) % LP_SLOTS) * (LP_CELLS * 32);
+        for (int q = tid; q < PLANE_CELLS * 2; q += 128) {
+            const int v = q >> 1, half = q & 1;
+            if (kk >= 0 && kk < nz) {
+                const int i = nwrap(x0 - 1 + v % HX, nx), j = nwrap(y0 - 1 + v / HX, ny);
+                cp16(S + swz(v, half), in + (((size_t)kk * ny + j) * nx + i) * 16 + half * 8);
+            } else {
+                *reinterpret_cast<uint4*>(S + swz(v, half)) = make_uint4(0, 0, 0, 0);
+            }
+        }
+        cp_commit_nn();
+    };
+    const size_t pl = (size_t)nx * ny;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int x0 = (tile % tiles_x) * TXC, y0 = (tile / tiles_x) * TYC;
-        __syncthreads();
-        load_wide(in, ring, nx, ny, nz, x0, y0, -1);
-        load_wide(in, ring, nx, ny, nz, x0, y0, 0);
-        load_wide(in, ring, nx, ny, nz, x0, y0, 1);
+        __syncthreads();  // the previous tile's ring and projections are no longer read
+        for (int kk = -1; kk <= LP_SLOTS - 3; ++kk) issue(x0, y0, kk);
+        const size_t orow = (size_t)(y0 + ty) * nx + x0 + tx;
         for (int k = 0; k < nz; ++k) {
-            load_wide(in, ring, nx, ny, nz, x0, y0, k + 2);
-            cp_wait_nn<1>();
-            __syncthreads();
-            float c[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-#pragma unroll 1
-            for (int dz = 0; dz < 3; ++dz) {
-                const unsigned char* H = ring + ((k + dz) & 3) * PLANE_BYTES;
+            issue(x0, y0, k + LP_SLOTS - 2);
+            cp_wait_nn<LP_SLOTS - 3>();  // planes k-1, k, k+1 have landed
+            __syncthreads();             // ... for every thread; the last gather is done
+            for (int mt = warp; mt < LP_CELLS / 16; mt += 4) {
+                float c[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
-                for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                    for (int dx = 0; dx < 3; ++dx) {
-                        const int tap = (dz * 3 + dy) * 3 + dx;
-                        const uint2 b = bt[tap * 32 + lane];
-#pragma unroll
-                        for (int m = 0; m < 2; ++m) {
-                            uint32_t a0, a1, a2, a3;
-                            ldm_x4(saddr(H + swz((yw + dy) * HX + xw + 16 * m + ar + dx, acol >> 3)), a0, a1, a2, a3);
-                            mma16816(c[m], a0, a1, a2, a3, b.x, b.y);
-                        }
-                    }
-            }
-            if (t2 == 0) {  // lanes holding output column 0: cells g and g + 8
-                const int y = y0 + yw;
-#pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    const size_t p = ((size_t)k * ny + y) * nx + x0 + xw + 16 * m + g;
-                    out[p] = c[m][0] + b4;
-                    out[p + 8] = c[m][2] + b4;
+                for (int dz = 0; dz < 3; ++dz) {  // plane k-1+dz sits in slot (k + dz) % LP_SLOTS
+                    const unsigned char* S = ring + ((k + dz) % LP_SLOTS) * (LP_CELLS * 32);
+                    uint32_t a0, a1, a2, a3;
+                    ldm_x4(saddr(S + swz(mt * 16 + ar, ah)), a0, a1, a2, a3);
+                    mma16816(c[0], a0, a1, a2, a3, bf[dz][0][0], bf[dz][0][1]);
+                    mma16816(c[1], a0, a1, a2, a3, bf[dz][1][0], bf[dz][1][1]);
+                }
+                const int cell = mt * 16 + g;
+                // n-tile 0 holds taps t2, t2+1; n-tile 1 tap 8 + t2 (only tap 8 is used)
+                Q[t2 * LP_PS + cell] = c[0][0];
+                Q[t2 * LP_PS + cell + 8] = c[0][2];
+                Q[(t2 + 1) * LP_PS + cell] = c[0][1];
+                Q[(t2 + 1) * LP_PS + cell + 8] = c[0][3];
+                if (t2 == 0) {
+                    Q[8 * LP_PS + cell] = c[1][0];
+                    Q[8 * LP_PS + cell + 8] = c[1][2];
                 }
             }
-            __syncthreads();
+            __syncthreads();  // the plane's projections are complete
+            float s = 0.f;
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) s += Q[(dy * 3 + dx) * LP_PS + (ty + dy) * HX + tx + dx];
+            out[(size_t)k * pl + orow] = s + b4;
         }
         cp_wait_nn<0>();
     }
@@ -1144,6 +1202,20 @@ void nn_prepare_weights(const NNBufs& b, cudaStream_t s) {
 
 static unsigned blocks_for(size_t n) { return (unsigned)((n + 255) / 256); }
 
+// persistent grid of a 128-thread thin-layer kernel over the 64 x 2 tiles: the blocks the SMs hold
+// at once (so no block waits for another to finish all its tiles), at most one per tile
+template <class K>
+static int resident_grid(K kern, size_t smem, int nx, int ny) {
+    int nsm = 0, dev = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, smem);
+    if (occ < 1) occ = 1;
+    const int ntiles = (nx / TXC) * (ny / TYC);
+    const int nb = nsm * occ;
+    return nb < ntiles ? nb : ntiles;
+}
+
 void nn_forward(const NNBufs& b, int nx, int ny, int nz, const __nv_bfloat16* x, float* out, cudaStream_t s) {
     const size_t n = (size_t)nx * ny * nz;
     const float* b1 = b.params + 16 * b.cin * 27;
@@ -1152,11 +1224,16 @@ void nn_forward(const NNBufs& b, int nx, int ny, int nz, const __nv_bfloat16* x,
     const float* b4 = b3 + 16 + 16 * 27;
     const int gt = thin_grid(nx, ny, 1 << 30);
     if (b.cin == 1) k_first_z<1><<<gt, 128, 0, s>>>(x, b.w1, b1, b.a1, nx, ny, nz);
-    else k_first_tc<<<gt, 128, 0, s>>>(x, b.w1, b1, b.a1, nx, ny, nz);
+    else k_first_tc2<<<resident_grid(k_first_tc2, 0, nx, ny), 128, 0, s>>>(x, b.w1, b1, b.a1, nx, ny, nz);
     note_launch();
     conv16<EPI_RELU>(b, b.a1, b.w2f, b2, nullptr, b.a2, nx, ny, nz, s);
     conv16<EPI_RELU>(b, b.a2, b.w3f, b3, nullptr, b.a3, nx, ny, nz, s);
-    k_last_tc<<<gt, 128, 27 * 32 * 8 + 4 * PLANE_BYTES, s>>>(b.a3, b.w4, b4, out, nx, ny, nz);
+    static bool lp_attr = false;
+    if (!lp_attr) {
+        cudaFuncSetAttribute(k_last_proj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LP_SMEM);
+        lp_attr = true;
+    }
+    k_last_proj<<<resident_grid(k_last_proj, LP_SMEM, nx, ny), 128, LP_SMEM, s>>>(b.a3, b.w4, b4, out, nx, ny, nz);
     note_launch();
 }
 
