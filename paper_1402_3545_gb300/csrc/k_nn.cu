@@ -213,34 +213,17 @@ static int conv16z_grid(int nx, int ny) {
     return nb < ntiles ? nb : ntiles;
 }
 
-// ---------------------------------------------------------------- 16 -> 16 on tcgen05
-// The same implicit GEMM on the fifth-generation tensor cores: per output row of TCX = 128
-// consecutive x cells (M = 128) and tap, one tcgen05.mma (kind::f16, BF16 in, FP32 accumulate in
-// tensor memory) with K = 16 input channels and N = 16 output channels; 27 MMAs per row. A block
-// of 128 TR threads owns TR rows and marches them in z: it keeps the planes k-1 .. k+3 of the
-// (TR + 2) x 130 halo rows in a 5-slot shared-memory ring (cp.async), one thread issues the MMAs of
-// plane k into one of two TMEM accumulator groups, and all threads drain the other group (tcgen05.ld,
-// bias + ReLU or the backward mask, BF16 store) for plane k-1 meanwhile. Operands are in the
-// canonical no-swizzle K-major layout: 16-byte rows of 8 channels, 8 cells (or output channels) per
-// 128-byte core matrix; for tap (dz, dy, dx) and tile row r the A operand is the halo row of plane
-// k-1+dz, row r+dy, starting dx cells in (a 16-byte aligned view, so no copy per tap).
+// ---------------------------------------------------------------- 16 -> 16 on tcgen05: common parts
+// Tiles of TR rows of TCX = 128 consecutive x cells (M = 128 per MMA); a halo plane of the tile is
+// TR + 2 rows of 130 cells in shared memory, in the canonical no-swizzle K-major layout of the MMA
+// operands: per row the two 8-channel K halves one after the other, 16-byte rows of 8 channels, 8
+// cells per 128-byte core matrix, so the A operand of a tap's shift dx is the halo row viewed from
+// cell dx (a 16-byte aligned view, no copy).
 static constexpr int TCX = 128;                     // cells per tile row
 static constexpr int TC_ROWC = TCX + 2;             // halo row cells
 static constexpr int TC_HALF = TC_ROWC * 16;        // bytes of one K half of a halo row
 static constexpr int TC_ROWB = 2 * TC_HALF;         // bytes of one halo row (both K halves)
-static constexpr int TC_WB = 27 * 512;              // weights: per tap [K half][16 co][8 ci]
-static constexpr int TC_SLOTS = 5;                  // planes k-1 .. k+3 in flight
 static constexpr long long TC_SPIN = 1LL << 26;     // bound of every mbarrier wait
-// per tile row three independent accumulator chains of 9 MMAs (one per dz, 16 FP32 columns
-// each), summed in the epilogue; two groups in flight (double buffer)
-static constexpr int TC_ACC = 3;
-template <int TR>
-struct TcShape {
-    static constexpr int PLANEB = (TR + 2) * TC_ROWB;            // one halo plane
-    static constexpr int SMEM = TC_WB + TC_SLOTS * PLANEB;
-    static constexpr int GROUP_COLS = 16 * TC_ACC * TR;          // TMEM columns per group
-    static constexpr int TMEM_COLS = 2 * GROUP_COLS <= 64 ? 64 : (2 * GROUP_COLS <= 128 ? 128 : 256);
-};
 
 __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     // start address >> 4 (bits 0-13), leading (K) byte offset >> 4 (16-29), stride (M/N) byte
@@ -248,9 +231,6 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_
     return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
-// kind::f16 instruction descriptor: D FP32 (bit 4), A and B BF16 (bits 7, 10), both K-major,
-// N >> 3 at bit 17, M >> 4 at bit 24
-static constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
     for (long long it = 0; it < TC_SPIN; ++it) {
@@ -265,26 +245,92 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
+// kind::f16 instruction descriptors below: D FP32 (bit 4), A and B BF16 (bits 7, 10), both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24
+
+// bounded wait on an mbarrier phase that also returns (false) once *abort is set
+__device__ __forceinline__ bool ws_wait(uint32_t mbar, uint32_t parity, const volatile int* abort) {
+    for (long long it = 0; it < TC_SPIN; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 255) == 255 && *abort) return false;
+    }
+    return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+// ---------------------------------------------------------------- 16 -> 16 on tcgen05, rolling planes
+// The implicit GEMM with MMAs of N = 144. A tcgen05.mma with M = 128 and K = 16 whose operands come
+// fresh from shared memory costs about the same up to N = 144 (measured: 69 cycles at N = 16, 48
+// and 96, 72 at 144, 128 at 256), so each MMA should produce 144 output columns. One input view --
+// plane p, halo row h, shift dx -- feeds nine outputs: rows h-2, h-1, h (taps dy = 2, 1, 0) of output
+// planes p+1, p, p-1 (taps dz = 0, 1, 2). The accumulators of three consecutive output planes live
+// in tensor memory by residue q = plane mod 3, row-major: column 48 (r + 2) + 16 q + channel for
+// tile row r in -2 .. TR+1 (rows outside the tile collect unused sums), so the nine outputs of a view
+// are 144 contiguous columns; B holds the nine taps' 16 x 16 weights in that order, rotated with p
+// mod 3 (3 rotations x 3 shifts = 9 matrices). Per input plane: 3 (TR + 2) MMAs; after them output
+// plane p-1 is complete and the input plane is never read again. Roles:
+//   producer warps (4): copy each input plane into a ring of SLOTS planes with cp.async, each
+//     thread's copies followed by cp.async.mbarrier.arrive on the slot's `full` mbarrier;
+//   one MMA thread: per input plane waits for it (`full`) and for the epilogue to have zeroed the
+//     residue block the plane opens (`acce` of the previous step), issues the MMAs, commits to `accf`
+//     and releases the plane's slot (`empty`, by tcgen05.commit);
+//   epilogue warps (4 per tile row): per input plane p drain output plane p-1 (and, after the
+//     tile's last plane, plane nz-1), zero the drained residue blocks (after the last plane all three),
+//     arrive on `acce`, then bias + ReLU (or the backward mask) into a BF16 staging tile in shared
+//     memory that one thread writes out by bulk copies (TMA), one per tile row.
+// The z padding needs no planes: the planes beyond the ends contribute nothing. Every wait is bounded
+// and also gives up once another role has given up (a shared abort flag), which raises the error flag.
+static constexpr int RL_NPROD = 128;
+static constexpr int RL_BB = 144 * 32;  // one B matrix: [K half][144 rows][8 ci]
+static constexpr int RL_WB = 9 * RL_BB;
+static constexpr uint32_t RL_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((144u >> 3) << 17) | ((128u >> 4) << 24);
+template <int TR>
+struct RlShape {
+    static constexpr int NEPI = 128 * TR;
+    static constexpr int NT = NEPI + 32 + RL_NPROD;
+    static constexpr int PLANEB = (TR + 2) * TC_ROWB;
+    static constexpr int SLOTS = 4;
+    static constexpr int STAGE = TR * TCX * 32;  // one output plane of the tile in BF16, rows of 4 KB
+    static constexpr int SMEM = RL_WB + SLOTS * PLANEB + 2 * STAGE;
+    static constexpr int WIN_COLS = 48 * (TR + 4);
+    static constexpr int TMEM_COLS = 512;
+};
+
 template <int EPI, int TR>
-__global__ void __launch_bounds__(128 * TR) k_conv16_tc(const __nv_bfloat16* __restrict__ in,
-                                                        const __nv_bfloat16* __restrict__ Wt,
-                                                        const float* __restrict__ bias,
-                                                        const __nv_bfloat16* __restrict__ mask,
-                                                        __nv_bfloat16* __restrict__ out, int nx, int ny, int nz, int* err) {
-    typedef TcShape<TR> SH;
-    constexpr int NT = 128 * TR;
+__global__ void __launch_bounds__(RlShape<TR>::NT) k_conv16_roll(const __nv_bfloat16* __restrict__ in,
+                                                                 const __nv_bfloat16* __restrict__ Wt,
+                                                                 const float* __restrict__ bias,
+                                                                 const __nv_bfloat16* __restrict__ mask,
+                                                                 __nv_bfloat16* __restrict__ out, int nx, int ny,
+                                                                 int nz, int* err) {
+    typedef RlShape<TR> SH;
+    static_assert(SH::WIN_COLS <= SH::TMEM_COLS, "the window of three planes fits the tensor memory");
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t full[RlShape<TR>::SLOTS], empty[RlShape<TR>::SLOTS], accf, acce;
     __shared__ uint32_t tmem_base;
     __shared__ float bsh[16];
+    __shared__ volatile int abort;
     unsigned char* Ws = smem;
-    unsigned char* ring = smem + TC_WB;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int erow = warp >> 2, ecell = (warp & 3) * 32 + (tid & 31);  // epilogue: tile row, cell
-    // weights Wt[tap][co][ci] -> per tap [ci / 8][co][ci % 8]
-    for (int q = tid; q < 27 * 32; q += NT) {
-        const int tap = q >> 5, co = (q >> 1) & 15, h = q & 1;
-        *reinterpret_cast<uint4*>(Ws + tap * 512 + h * 256 + co * 16) =
+    unsigned char* ring = smem + RL_WB;
+    unsigned char* stage = ring + SH::SLOTS * SH::PLANEB;  // two output staging buffers
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // B matrix (rotation rot, shift dx), row 48 j + 16 q + co: tap dy = 2 - j, dz = (rot + 1 - q) mod 3
+    for (int e = tid; e < 9 * 9 * 32; e += SH::NT) {
+        const int mtx = e / 288, blk = (e / 32) % 9, co = (e >> 1) & 15, h = e & 1;
+        const int rot = mtx / 3, dx = mtx % 3, j = blk / 3, qq = blk % 3;
+        const int dy = 2 - j, dz = (rot + 4 - qq) % 3, tap = (dz * 3 + dy) * 3 + dx;
+        *reinterpret_cast<uint4*>(Ws + mtx * RL_BB + h * (RL_BB / 2) + (blk * 16 + co) * 16) =
             __ldg(reinterpret_cast<const uint4*>(Wt + (tap * 16 + co) * 16 + h * 8));
     }
     if (warp == 0) {
@@ -294,155 +340,216 @@ __global__ void __launch_bounds__(128 * TR) k_conv16_tc(const __nv_bfloat16* __r
     }
     if (tid < 16) bsh[tid] = (EPI == EPI_RELU) ? __ldg(bias + tid) : 0.f;
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mbar[1])));
+        for (int s = 0; s < SH::SLOTS; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&full[s])), "n"(RL_NPROD));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty[s])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&accf)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&acce)), "n"(SH::NEPI / 32));
+        abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("fence.proxy.async.shared::cta;");  // the weights, written by plain stores, for the MMAs
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
-
+    // the epilogue warp of tile row r zeroes, in residue block q, its 32 lanes in the columns of row r
+    // and of its share of the rows outside the tile (-2, -1, TR, TR+1)
+    auto zero_block = [&](int q) {
+        const uint32_t base = tmem + 16 * q + ((uint32_t)((warp & 3) * 32) << 16);
+        const int r = warp >> 2;
+        const uint32_t z = 0;
+        auto zero16 = [&](int rr) {  // tile row rr in -2 .. TR+1
+            asm volatile(
+                "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(
+                    base + 48 * (rr + 2)),
+                "r"(z)
+                : "memory");
+        };
+        zero16(r);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (i % TR == r) zero16(i < 2 ? i - 2 : TR + i - 2);
+    };
+    if (tid < SH::NEPI) {  // the window starts at zero; afterwards each block is zeroed as it is drained
+        zero_block(0);
+        zero_block(1);
+        zero_block(2);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
     const int tiles_x = nx / TCX, ntiles = tiles_x * (ny / TR);
-    unsigned step = 0;  // MMA groups issued by this block: accumulator step & 1, parity (step >> 1) & 1
     bool ok = true;
-    // drain the accumulators of MMA group g (plane kk of the current tile) into the output
-    auto epilogue = [&](unsigned g, int kk, int x0, int y0) -> bool {
-        if (!tc_wait(saddr(&mbar[g & 1]), (g >> 1) & 1)) return false;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        float v[16];
+    unsigned step = 0;  // input planes handled by the block (MMA thread and epilogue alike)
+    if (tid >= SH::NEPI + 32) {
+        // ---- producers: input plane q of the block's sequence into slot q % SLOTS
+        const int ptid = tid - (SH::NEPI + 32);
+        constexpr int NCH = (TR + 2) * TC_ROWC * 2, CPT = (NCH + RL_NPROD - 1) / RL_NPROD;
+        int q = 0;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
+            int ch_dst[CPT];
+            size_t ch_src[CPT];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = 0.f;
+            for (int c = 0; c < CPT; ++c) {
+                const int qq = ptid + RL_NPROD * c;
+                const int hh = qq & 1, cc = (qq >> 1) % TC_ROWC, rr = (qq >> 1) / TC_ROWC;
+                ch_dst[c] = qq < NCH ? rr * TC_ROWB + hh * TC_HALF + cc * 16 : -1;
+                ch_src[c] = ((size_t)nwrap(y0 - 1 + rr, ny) * nx + nwrap(x0 - 1 + cc, nx)) * 16 + hh * 8;
+            }
+            for (int p = 0; p < nz; ++p, ++q) {
+                const int slot = q % SH::SLOTS;
+                if (q >= SH::SLOTS && !ws_wait(saddr(&empty[slot]), ((q / SH::SLOTS) - 1) & 1, &abort)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* P = ring + slot * SH::PLANEB;
+                const __nv_bfloat16* src = in + (size_t)p * ny * nx * 16;
 #pragma unroll
-        for (int a = 0; a < TC_ACC; ++a) {
+                for (int c = 0; c < CPT; ++c)
+                    if (ch_dst[c] >= 0) cp16(P + ch_dst[c], src + ch_src[c]);
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(saddr(&full[slot])) : "memory");
+            }
+        }
+        cp_wait_nn<0>();
+    } else if (warp == SH::NEPI / 32) {
+        // ---- MMA thread: one step per input plane
+        if (lane == 0) {
+            const uint64_t dw0 = tc_desc(saddr(Ws), RL_BB / 2, 128);
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                for (int p = 0; p < nz; ++p) {
+                    const int slot = step % SH::SLOTS;
+                    if (!ws_wait(saddr(&full[slot]), (step / SH::SLOTS) & 1, &abort) ||
+                        (step >= 1 && !ws_wait(saddr(&acce), (step - 1) & 1, &abort))) {
+                        ok = false;
+                        break;
+                    }
+                    // the plane's copies, observed through the barrier, ordered before the tensor
+                    // core's reads; the zeroed window before its writes
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint64_t dp = tc_desc(saddr(ring + slot * SH::PLANEB), TC_HALF, 128);
+                    const int rot = p % 3;
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const uint64_t db = dw0 + (uint64_t)(((rot * 3 + dx) * RL_BB) >> 4);
+#pragma unroll
+                        for (int h = 0; h < TR + 2; ++h) {  // halo row h feeds rows h-2 .. h of three planes
+                            const uint64_t da = dp + (uint64_t)(((h * TC_ROWB) + dx * 16) >> 4);
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + 48 * h),
+                                "l"(da), "l"(db), "r"(RL_IDESC), "r"(1));
+                        }
+                    }
+                    tc_commit(saddr(&accf));
+                    tc_commit(saddr(&empty[slot]));  // the input plane has no later reader
+                    ++step;
+                }
+            }
+            // no MMA may be in flight when the tensor memory is freed (a bounded wait, abort or not)
+            if (step > 0) tc_wait(saddr(&accf), (step - 1) & 1);
+        }
+    } else {
+        // ---- epilogue: thread (erow, ecell) owns one cell of the tile rows
+        const int erow = warp >> 2, ecell = (warp & 3) * 32 + lane;
+        const uint32_t tq = tmem + 48 * (erow + 2) + ((uint32_t)((warp & 3) * 32) << 16);
+        auto load16 = [&](int q, float (&v)[16]) {
             uint32_t r[16];
-            const uint32_t ta = tmem + (g & 1) * SH::GROUP_COLS + (erow * TC_ACC + a) * 16 +
-                                ((uint32_t)((warp & 3) * 32) << 16);
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                : "r"(ta));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
+                : "r"(tq + 16 * q));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int c = 0; c < 16; ++c) v[c] += __uint_as_float(r[c]);
-        }
-        const size_t p = ((size_t)kk * ny + y0 + erow) * nx + x0 + ecell;
-        if (EPI == EPI_RELU) {
-#pragma unroll
-            for (int c = 0; c < 16; ++c) v[c] = fmaxf(v[c] + bsh[c], 0.f);
-        } else {
-            const uint4 m0 = __ldg(reinterpret_cast<const uint4*>(mask + p * 16));
-            const uint4 m1 = __ldg(reinterpret_cast<const uint4*>(mask + p * 16 + 8));
-            const __nv_bfloat16* mk0 = reinterpret_cast<const __nv_bfloat16*>(&m0);
-            const __nv_bfloat16* mk1 = reinterpret_cast<const __nv_bfloat16*>(&m1);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                if (!(__bfloat162float(mk0[c]) > 0.f)) v[c] = 0.f;
-                if (!(__bfloat162float(mk1[c]) > 0.f)) v[c + 8] = 0.f;
-            }
-        }
-        uint4 o0, o1;
-        __nv_bfloat162* h0 = reinterpret_cast<__nv_bfloat162*>(&o0);
-        __nv_bfloat162* h1 = reinterpret_cast<__nv_bfloat162*>(&o1);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            h0[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
-            h1[c] = __floats2bfloat162_rn(v[8 + 2 * c], v[8 + 2 * c + 1]);
-        }
-        *reinterpret_cast<uint4*>(out + p * 16) = o0;
-        *reinterpret_cast<uint4*>(out + p * 16 + 8) = o1;
-        return true;
-    };
-
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
-        // this thread's 16-byte chunks of a halo plane: slot offset and in-plane source, the same for
-        // every plane of the tile
-        constexpr int NCH = (TR + 2) * TC_ROWC * 2, CPT = (NCH + NT - 1) / NT;
-        int ch_dst[CPT];
-        size_t ch_src[CPT];
-#pragma unroll
-        for (int j = 0; j < CPT; ++j) {
-            const int q = tid + NT * j;
-            const int h = q & 1, c = (q >> 1) % TC_ROWC, rr = (q >> 1) / TC_ROWC;
-            ch_dst[j] = q < NCH ? rr * TC_ROWB + h * TC_HALF + c * 16 : -1;
-            ch_src[j] = ((size_t)nwrap(y0 - 1 + rr, ny) * nx + nwrap(x0 - 1 + c, nx)) * 16 + h * 8;
-        }
-        // plane kk into ring slot (kk + 1) % TC_SLOTS; the z padding planes -1 and nz are zeros,
-        // later ones are never read (an empty group)
-        auto load_plane = [&](int kk) {
-            unsigned char* P = ring + ((kk + 1) % TC_SLOTS) * SH::PLANEB;
-            const bool real = kk >= 0 && kk < nz, pad = kk == -1 || kk == nz;
-            const __nv_bfloat16* src = in + (size_t)(real ? kk : 0) * ny * nx * 16;
-#pragma unroll
-            for (int j = 0; j < CPT; ++j) {
-                if (ch_dst[j] < 0) continue;
-                if (real) cp16(P + ch_dst[j], src + ch_src[j]);
-                else if (pad) *reinterpret_cast<uint4*>(P + ch_dst[j]) = make_uint4(0, 0, 0, 0);
-            }
-            cp_commit_nn();
+            for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
         };
-        __syncthreads();  // the previous tile's ring is no longer read
-        load_plane(-1);
-        load_plane(0);
-        load_plane(1);
-        load_plane(2);
-        for (int k = 0; k < nz; ++k) {
-            cp_wait_nn<1>();                                 // planes up to k+1 (this thread's copies)
-            asm volatile("fence.proxy.async.shared::cta;");  // ... visible to the tensor core
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncthreads();
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            if (tid == 0) {
-                const uint32_t dt = tmem + (step & 1) * SH::GROUP_COLS;
-                // descriptors of tap (dz, dy, dx), row r: the start-address field (bits 0-13,
-                // address >> 4) of the plane's descriptor advanced by the view's offset in the slot
-                uint64_t dplane[3];
+        // output plane o of the tile: BF16 cells into staging buffer `nemit & 1`, then one bulk copy
+        // (TMA) per tile row from the buffer to global memory, issued by epilogue thread 0; a buffer
+        // is rewritten once the copy issued from it two emits earlier has read it
+        unsigned nemit = 0;
+        auto emit = [&](int o, int x0, int y0, float (&v)[16]) {
+            const size_t pidx = ((size_t)o * ny + y0 + erow) * nx + x0 + ecell;
+            if (EPI == EPI_RELU) {
 #pragma unroll
-                for (int dz = 0; dz < 3; ++dz)
-                    dplane[dz] = tc_desc(saddr(ring + ((k + dz) % TC_SLOTS) * SH::PLANEB), TC_HALF, 128);
-                const uint64_t dw0 = tc_desc(saddr(Ws), 256, 128);
+                for (int c = 0; c < 16; ++c) v[c] = fmaxf(v[c] + bsh[c], 0.f);
+            } else {
+                const uint4 m0 = __ldg(reinterpret_cast<const uint4*>(mask + pidx * 16));
+                const uint4 m1 = __ldg(reinterpret_cast<const uint4*>(mask + pidx * 16 + 8));
+                const __nv_bfloat16* mk0 = reinterpret_cast<const __nv_bfloat16*>(&m0);
+                const __nv_bfloat16* mk1 = reinterpret_cast<const __nv_bfloat16*>(&m1);
 #pragma unroll
-                for (int i = 0; i < 27; ++i) {  // the three chains interleaved
-                    const int dz = i % 3, tap = dz * 9 + i / 3, dy = (tap / 3) % 3, dx = tap % 3;
-                    const uint64_t db = dw0 + (uint64_t)((tap * 512) >> 4);
-#pragma unroll
-                    for (int r = 0; r < TR; ++r) {
-                        const uint64_t da = dplane[dz] + (uint64_t)((((dy + r) * TC_ROWB) + dx * 16) >> 4);
-                        asm volatile(
-                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                                dt + (r * TC_ACC + dz) * 16),
-                            "l"(da), "l"(db), "r"(TC_IDESC), "r"(tap % 9));
-                    }
+                for (int c = 0; c < 8; ++c) {
+                    if (!(__bfloat162float(mk0[c]) > 0.f)) v[c] = 0.f;
+                    if (!(__bfloat162float(mk1[c]) > 0.f)) v[c + 8] = 0.f;
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    saddr(&mbar[step & 1])));
             }
-            // plane k+3 into the slot of plane k-2, whose last readers (group step-1) must be done;
-            // then drain group step-1 (plane k-1)
-            if (k > 0 && !tc_wait(saddr(&mbar[(step - 1) & 1]), ((step - 1) >> 1) & 1)) {
-                ok = false;
-                break;
+            uint4 o0, o1;
+            __nv_bfloat162* h0 = reinterpret_cast<__nv_bfloat162*>(&o0);
+            __nv_bfloat162* h1 = reinterpret_cast<__nv_bfloat162*>(&o1);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                h0[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
+                h1[c] = __floats2bfloat162_rn(v[8 + 2 * c], v[8 + 2 * c + 1]);
             }
-            load_plane(k + 3);
-            if (k > 0 && !epilogue(step - 1, k - 1, x0, y0)) {
-                ok = false;
-                break;
+            unsigned char* B = stage + (nemit & 1) * SH::STAGE;
+            if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(SH::NEPI) : "memory");  // the buffer's last copy has read it
+            *reinterpret_cast<uint4*>(B + (erow * TCX + ecell) * 32) = o0;
+            *reinterpret_cast<uint4*>(B + (erow * TCX + ecell) * 32 + 16) = o1;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the stores, for the bulk copy
+            asm volatile("bar.sync 1, %0;" ::"n"(SH::NEPI) : "memory");
+            if (tid == 0) {
+#pragma unroll
+                for (int r = 0; r < TR; ++r)
+                    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
+                                     out + (((size_t)o * ny + y0 + r) * nx + x0) * 16),
+                                 "r"(saddr(B + r * TCX * 32)), "n"(TCX * 32)
+                                 : "memory");
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             }
-            ++step;
+            ++nemit;
+        };
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
+            for (int p = 0; p < nz; ++p) {
+                if (!ws_wait(saddr(&accf), step & 1, &abort)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const bool last = p == nz - 1;
+                float va[16], vb[16];
+                if (p >= 1) load16((p - 1) % 3, va);  // output plane p-1 is complete
+                if (last) load16((nz - 1) % 3, vb);   // ... and after the last input plane, plane nz-1
+                // zero what was drained (after the tile's last plane the whole window, including the
+                // block of the plane beyond the end), so the next plane's MMAs may accumulate
+                if (last) {
+                    zero_block(0);
+                    zero_block(1);
+                    zero_block(2);
+                } else {
+                    zero_block((p + 2) % 3);
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(saddr(&acce));
+                if (p >= 1) emit(p - 1, x0, y0, va);
+                if (last) emit(nz - 1, x0, y0, vb);
+                ++step;
+            }
         }
-        if (ok && !epilogue(step - 1, nz - 1, x0, y0)) ok = false;
-        asm volatile("tcgen05.fence::before_thread_sync;");
+        if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the output has been written
     }
     if (!ok) {
+        abort = 1;
         atomicExch(err, 1);
-        // the MMAs in flight may still complete: give them the bounded wait before the TMEM is freed
-        tc_wait(saddr(&mbar[(step - 1) & 1]), ((step - 1) >> 1) & 1);
     }
-    cp_wait_nn<0>();
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -450,34 +557,33 @@ __global__ void __launch_bounds__(128 * TR) k_conv16_tc(const __nv_bfloat16* __r
 }
 
 template <int TR>
-static int conv16_tc_grid(int nx, int ny) {
-    typedef TcShape<TR> SH;
-    static int per_sm = 0, nsm = 0;
-    if (per_sm == 0) {
-        cudaFuncSetAttribute(k_conv16_tc<EPI_RELU, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM);
-        cudaFuncSetAttribute(k_conv16_tc<EPI_MASK, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM);
-        int dev = 0, smem_sm = 0;
+static int conv16_roll_grid(int nx, int ny) {
+    typedef RlShape<TR> SH;
+    static int nsm = 0;
+    if (nsm == 0) {
+        cudaFuncSetAttribute(k_conv16_roll<EPI_RELU, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM);
+        cudaFuncSetAttribute(k_conv16_roll<EPI_MASK, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM);
+        int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        // blocks per SM by shared memory (1 KB per block reserved by the system) and by TMEM
-        per_sm = smem_sm / (SH::SMEM + 1024);
-        if (per_sm > 512 / SH::TMEM_COLS) per_sm = 512 / SH::TMEM_COLS;  // tcgen05.alloc never waits
-        if (per_sm < 1) per_sm = 1;
     }
+    // one block per SM: the window takes the whole tensor memory (tcgen05.alloc never waits)
     const int ntiles = (nx / TCX) * (ny / TR);
-    const int nb = per_sm * nsm;
-    return nb < ntiles ? nb : ntiles;
+    return nsm < ntiles ? nsm : ntiles;
 }
 
-// one 16 -> 16 layer: the tcgen05 kernel (two rows per block; the network's shapes have even ny)
+// one 16 -> 16 layer: the rolling-plane tcgen05 kernel (tiles of four rows, two where ny % 4 == 2)
 // when nx is a multiple of 128, else the mma.sync one
 template <int EPI>
 static void conv16(const NNBufs& b, const __nv_bfloat16* in, const __nv_bfloat16* W, const float* bias,
                    const __nv_bfloat16* mask, __nv_bfloat16* out, int nx, int ny, int nz, cudaStream_t s) {
     if (nx % TCX == 0 && ny % 2 == 0) {
-        k_conv16_tc<EPI, 2><<<conv16_tc_grid<2>(nx, ny), 256, TcShape<2>::SMEM, s>>>(in, W, bias, mask, out, nx, ny, nz,
-                                                                                   b.err);
+        if (ny % 4 == 0)
+            k_conv16_roll<EPI, 4><<<conv16_roll_grid<4>(nx, ny), RlShape<4>::NT, RlShape<4>::SMEM, s>>>(
+                in, W, bias, mask, out, nx, ny, nz, b.err);
+        else
+            k_conv16_roll<EPI, 2><<<conv16_roll_grid<2>(nx, ny), RlShape<2>::NT, RlShape<2>::SMEM, s>>>(
+                in, W, bias, mask, out, nx, ny, nz, b.err);
     } else {
         const size_t smemz = W_BYTES + 4 * PLANE_BYTES;
         k_conv16z<EPI, CONV_MT><<<conv16z_grid(nx, ny), 256 / CONV_MT, smemz, s>>>(in, W, bias, mask, out, nx, ny, nz);

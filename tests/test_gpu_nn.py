@@ -103,7 +103,9 @@ def _forward_bf16_storage(params, x, cin):
 FWD_TOL, GRAD_TOL = 1e-3, 1e-2
 
 
-@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+# (3, 700, 128): 350 tiles of 128 x 2 cells for the tensor-core 16 -> 16 layers, more than the SMs
+# hold blocks, so some blocks carry their plane ring and accumulators from one tile into the next
+@pytest.mark.parametrize("shape", SHAPES + [(3, 700, 128)], ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("cin", [1, 2])
 def test_forward_matches_oracle_layers_with_bf16_storage(shape, cin):
     p = random_params(cin, seed=30 + cin)
