@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <cmath>
+#include <cstdint>
 
 #include <mutex>
 #include <string>
@@ -2127,14 +2128,35 @@ tpmg_status tpmg_nn_train_step_residual(tpmg_nn* nn, tpmg_op* op, const float* x
 
 }  // extern "C"
 
-__global__ void k_nn_input_f32(size_t n, int cin, const float* __restrict__ x, __nv_bfloat16* __restrict__ xb) {
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n * cin; t += (size_t)gridDim.x * blockDim.x)
-        xb[t] = __float2bfloat16_rn(x[t]);
+// the FP32 input rounded to BF16 (round to nearest even), four values per thread and step where the
+// buffer allows 16-byte loads, one at a time otherwise
+__global__ void k_nn_input_f32(size_t m, const float* __restrict__ x, __nv_bfloat16* __restrict__ xb) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if ((m & 3) == 0 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)xb & 7) == 0) {
+        for (size_t t = t0; t < m / 4; t += stride) {
+            const float4 v = __ldcs(reinterpret_cast<const float4*>(x) + t);
+            __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+            uint2 o;
+            o.x = *reinterpret_cast<uint32_t*>(&lo);
+            o.y = *reinterpret_cast<uint32_t*>(&hi);
+            reinterpret_cast<uint2*>(xb)[t] = o;
+        }
+    } else {
+        for (size_t t = t0; t < m; t += stride) xb[t] = __float2bfloat16_rn(x[t]);
+    }
 }
 static tpmg_status nn_load_input(tpmg_nn* nn, size_t n, const float* x, cudaStream_t s) {
-    size_t blocks = (n * nn->b.cin + 255) / 256;
-    if (blocks > 4096) blocks = 4096;
-    k_nn_input_f32<<<(unsigned)blocks, 256, 0, s>>>(n, nn->b.cin, x, nn->b.x);
+    const size_t m = n * nn->b.cin;
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    size_t blocks = (m / 4 + 255) / 256;
+    if (blocks > (size_t)nsm * 8) blocks = (size_t)nsm * 8;  // eight 256-thread blocks per SM, grid-stride
+    if (blocks < 1) blocks = 1;
+    k_nn_input_f32<<<(unsigned)blocks, 256, 0, s>>>(m, x, nn->b.x);
     note_launch();
     return TPMG_OK;
 }

@@ -270,41 +270,47 @@ __device__ __forceinline__ void tc_commit(uint32_t mbar) {
 }
 
 // ---------------------------------------------------------------- 16 -> 16 on tcgen05, rolling planes
-// The implicit GEMM with MMAs of N = 144. A tcgen05.mma with M = 128 and K = 16 whose operands come
-// fresh from shared memory costs about the same up to N = 144 (measured: 69 cycles at N = 16, 48
-// and 96, 72 at 144, 128 at 256), so each MMA should produce 144 output columns. One input view --
-// plane p, halo row h, shift dx -- feeds nine outputs: rows h-2, h-1, h (taps dy = 2, 1, 0) of output
-// planes p+1, p, p-1 (taps dz = 0, 1, 2). The accumulators of three consecutive output planes live
-// in tensor memory by residue q = plane mod 3, row-major: column 48 (r + 2) + 16 q + channel for
-// tile row r in -2 .. TR+1 (rows outside the tile collect unused sums), so the nine outputs of a view
-// are 144 contiguous columns; B holds the nine taps' 16 x 16 weights in that order, rotated with p
-// mod 3 (3 rotations x 3 shifts = 9 matrices). Per input plane: 3 (TR + 2) MMAs; after them output
-// plane p-1 is complete and the input plane is never read again. Roles:
-//   producer warps (4): copy each input plane into a ring of SLOTS planes with cp.async, each
+// The implicit GEMM with MMAs of up to N = 144. A tcgen05.mma with M = 128 and K = 16 whose operands
+// come fresh from shared memory costs about the same up to N = 144 (measured: 69 cycles at N = 16,
+// 48 and 96, 72 at 144, 128 at 256), so each MMA should produce many output columns. One input view
+// -- plane p, halo row h, shift dx -- feeds nine outputs: rows h-2, h-1, h (taps dy = 2, 1, 0) of
+// output planes p+1, p, p-1 (taps dz = 0, 1, 2). The accumulators of three consecutive output planes
+// live in tensor memory by residue q = plane mod 3, row-major: column 48 r + 16 q + channel for tile
+// row r, so the outputs of a view inside the tile are contiguous columns (N = 144 for the inner
+// rows, 96 or 48 for the two halo rows at each end, whose other outputs lie outside the tile); B holds
+// the nine taps' weights in that order, rotated with p mod 3 (3 rotations x 3 shifts = 9 matrices),
+// and a narrower MMA reads the rows of B it needs. Per input plane 3 (TR + 2) MMAs; after them output
+// plane p-1 is complete and the input plane is never read again, so the z padding needs no planes.
+// A block works on two tiles at once, plane by plane in turn, each with its own window of 48 TR
+// columns: the MMAs of one tile run while the epilogue drains the other's window. Roles:
+//   producer warps (4): copy the input planes into a ring of SLOTS planes with cp.async, each
 //     thread's copies followed by cp.async.mbarrier.arrive on the slot's `full` mbarrier;
 //   one MMA thread: per input plane waits for it (`full`) and for the epilogue to have zeroed the
-//     residue block the plane opens (`acce` of the previous step), issues the MMAs, commits to `accf`
-//     and releases the plane's slot (`empty`, by tcgen05.commit);
-//   epilogue warps (4 per tile row): per input plane p drain output plane p-1 (and, after the
-//     tile's last plane, plane nz-1), zero the drained residue blocks (after the last plane all three),
-//     arrive on `acce`, then bias + ReLU (or the backward mask) into a BF16 staging tile in shared
-//     memory that one thread writes out by bulk copies (TMA), one per tile row.
-// The z padding needs no planes: the planes beyond the ends contribute nothing. Every wait is bounded
-// and also gives up once another role has given up (a shared abort flag), which raises the error flag.
+//     residue block it opens in its tile's window (`acce` of that window), issues the MMAs, commits
+//     to the window's `accf` and releases the plane's slot (`empty`, by tcgen05.commit);
+//   epilogue warps (4 per tile row): per input plane p drain output plane p-1 of the tile (and,
+//     after the tile's last plane, plane nz-1), zero the drained residue blocks (after the last plane
+//     all three), arrive on `acce`, then bias + ReLU (or the backward mask) into the warp's BF16
+//     staging buffer, which the warp's lane 0 writes out by a bulk copy (TMA) of its 32 cells.
+// Every wait is bounded and also gives up once another role has given up (a shared abort flag), which
+// raises the error flag.
 static constexpr int RL_NPROD = 128;
 static constexpr int RL_BB = 144 * 32;  // one B matrix: [K half][144 rows][8 ci]
 static constexpr int RL_WB = 9 * RL_BB;
-static constexpr uint32_t RL_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((144u >> 3) << 17) | ((128u >> 4) << 24);
+__host__ __device__ constexpr uint32_t rl_idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
 template <int TR>
 struct RlShape {
     static constexpr int NEPI = 128 * TR;
     static constexpr int NT = NEPI + 32 + RL_NPROD;
     static constexpr int PLANEB = (TR + 2) * TC_ROWB;
-    static constexpr int SLOTS = 4;
+    static constexpr int SLOTS = 6;              // input planes in flight or waiting for the tensor core
     static constexpr int STAGE = TR * TCX * 32;  // one output plane of the tile in BF16, rows of 4 KB
     static constexpr int SMEM = RL_WB + SLOTS * PLANEB + 2 * STAGE;
-    static constexpr int WIN_COLS = 48 * (TR + 4);
-    static constexpr int TMEM_COLS = 512;
+    static constexpr int WIN_COLS = 48 * TR;     // one tile's window of three output planes
+    static constexpr int TMEM_COLS = 2 * WIN_COLS <= 256 ? 256 : 512;
+    static_assert(TR >= 2 && 2 * WIN_COLS <= 512, "two windows in the tensor memory");
 };
 
 template <int EPI, int TR>
@@ -315,9 +321,8 @@ __global__ void __launch_bounds__(RlShape<TR>::NT) k_conv16_roll(const __nv_bflo
                                                                  __nv_bfloat16* __restrict__ out, int nx, int ny,
                                                                  int nz, int* err) {
     typedef RlShape<TR> SH;
-    static_assert(SH::WIN_COLS <= SH::TMEM_COLS, "the window of three planes fits the tensor memory");
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t full[RlShape<TR>::SLOTS], empty[RlShape<TR>::SLOTS], accf, acce;
+    __shared__ __align__(8) uint64_t full[RlShape<TR>::SLOTS], empty[RlShape<TR>::SLOTS], accf[2], acce[2];
     __shared__ uint32_t tmem_base;
     __shared__ float bsh[16];
     __shared__ volatile int abort;
@@ -344,8 +349,10 @@ __global__ void __launch_bounds__(RlShape<TR>::NT) k_conv16_roll(const __nv_bflo
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&full[s])), "n"(RL_NPROD));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty[s])));
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&accf)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&acce)), "n"(SH::NEPI / 32));
+        for (int w = 0; w < 2; ++w) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&accf[w])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&acce[w])), "n"(SH::NEPI / 32));
+        }
         abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -354,123 +361,136 @@ __global__ void __launch_bounds__(RlShape<TR>::NT) k_conv16_roll(const __nv_bflo
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
-    // the epilogue warp of tile row r zeroes, in residue block q, its 32 lanes in the columns of row r
-    // and of its share of the rows outside the tile (-2, -1, TR, TR+1)
-    auto zero_block = [&](int q) {
-        const uint32_t base = tmem + 16 * q + ((uint32_t)((warp & 3) * 32) << 16);
-        const int r = warp >> 2;
+    // the epilogue warp of tile row r zeroes its 32 lanes of row r in residue block q of window w
+    auto zero_block = [&](int w, int q) {
         const uint32_t z = 0;
-        auto zero16 = [&](int rr) {  // tile row rr in -2 .. TR+1
-            asm volatile(
-                "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(
-                    base + 48 * (rr + 2)),
-                "r"(z)
-                : "memory");
-        };
-        zero16(r);
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (i % TR == r) zero16(i < 2 ? i - 2 : TR + i - 2);
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(
+                tmem + w * SH::WIN_COLS + 48 * (warp >> 2) + 16 * q + ((uint32_t)((warp & 3) * 32) << 16)),
+            "r"(z)
+            : "memory");
     };
-    if (tid < SH::NEPI) {  // the window starts at zero; afterwards each block is zeroed as it is drained
-        zero_block(0);
-        zero_block(1);
-        zero_block(2);
+    if (tid < SH::NEPI) {  // the windows start at zero; afterwards a block is zeroed as it is drained
+        for (int w = 0; w < 2; ++w)
+            for (int q = 0; q < 3; ++q) zero_block(w, q);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const int tiles_x = nx / TCX, ntiles = tiles_x * (ny / TR);
+    const int G = (int)gridDim.x;
     bool ok = true;
-    unsigned step = 0;  // input planes handled by the block (MMA thread and epilogue alike)
+    // the block's tiles in pairs (t, t + G), t = blockIdx.x + 2 G i; a pair runs its planes in turn
+    // (tile 0 of the pair, tile 1, next plane ...); a pair whose second tile does not exist runs alone
     if (tid >= SH::NEPI + 32) {
-        // ---- producers: input plane q of the block's sequence into slot q % SLOTS
+        // ---- producers: the pair's planes in turn into slot q % SLOTS of the ring
         const int ptid = tid - (SH::NEPI + 32);
         constexpr int NCH = (TR + 2) * TC_ROWC * 2, CPT = (NCH + RL_NPROD - 1) / RL_NPROD;
+        int ch_dst[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const int qq = ptid + RL_NPROD * c;
+            ch_dst[c] = qq < NCH ? ((qq >> 1) / TC_ROWC) * TC_ROWB + (qq & 1) * TC_HALF + ((qq >> 1) % TC_ROWC) * 16 : -1;
+        }
         int q = 0;
-        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-            const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
-            int ch_dst[CPT];
-            size_t ch_src[CPT];
+        for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += 2 * G) {
+            const int nt = t0 + G < ntiles ? 2 : 1;
+            uint32_t src[2][CPT];  // element offsets within a plane (the caller keeps a plane below 2^32)
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) {
-                const int qq = ptid + RL_NPROD * c;
-                const int hh = qq & 1, cc = (qq >> 1) % TC_ROWC, rr = (qq >> 1) / TC_ROWC;
-                ch_dst[c] = qq < NCH ? rr * TC_ROWB + hh * TC_HALF + cc * 16 : -1;
-                ch_src[c] = ((size_t)nwrap(y0 - 1 + rr, ny) * nx + nwrap(x0 - 1 + cc, nx)) * 16 + hh * 8;
-            }
-            for (int p = 0; p < nz; ++p, ++q) {
-                const int slot = q % SH::SLOTS;
-                if (q >= SH::SLOTS && !ws_wait(saddr(&empty[slot]), ((q / SH::SLOTS) - 1) & 1, &abort)) {
-                    ok = false;
-                    break;
+            for (int w = 0; w < 2; ++w) {
+                const int tile = w < nt ? t0 + w * G : t0;
+                const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) {
+                    const int qq = ptid + RL_NPROD * c;
+                    const int hh = qq & 1, cc = (qq >> 1) % TC_ROWC, rr = (qq >> 1) / TC_ROWC;
+                    src[w][c] = ((uint32_t)nwrap(y0 - 1 + rr, ny) * nx + nwrap(x0 - 1 + cc, nx)) * 16 + hh * 8;
                 }
-                unsigned char* P = ring + slot * SH::PLANEB;
-                const __nv_bfloat16* src = in + (size_t)p * ny * nx * 16;
+            }
+            for (int p = 0; p < nz && ok; ++p) {
+                for (int w = 0; w < nt; ++w, ++q) {
+                    const int slot = q % SH::SLOTS;
+                    if (q >= SH::SLOTS && !ws_wait(saddr(&empty[slot]), ((q / SH::SLOTS) - 1) & 1, &abort)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char* P = ring + slot * SH::PLANEB;
+                    const __nv_bfloat16* base = in + (size_t)p * ny * nx * 16;
 #pragma unroll
-                for (int c = 0; c < CPT; ++c)
-                    if (ch_dst[c] >= 0) cp16(P + ch_dst[c], src + ch_src[c]);
-                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(saddr(&full[slot])) : "memory");
+                    for (int c = 0; c < CPT; ++c)
+                        if (ch_dst[c] >= 0) cp16(P + ch_dst[c], base + src[w][c]);
+                    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(saddr(&full[slot]))
+                                 : "memory");
+                }
             }
         }
         cp_wait_nn<0>();
     } else if (warp == SH::NEPI / 32) {
-        // ---- MMA thread: one step per input plane
+        // ---- MMA thread: one step per input plane of a tile, into that tile's window
         if (lane == 0) {
             const uint64_t dw0 = tc_desc(saddr(Ws), RL_BB / 2, 128);
-            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-                for (int p = 0; p < nz; ++p) {
-                    const int slot = step % SH::SLOTS;
-                    if (!ws_wait(saddr(&full[slot]), (step / SH::SLOTS) & 1, &abort) ||
-                        (step >= 1 && !ws_wait(saddr(&acce), (step - 1) & 1, &abort))) {
-                        ok = false;
-                        break;
-                    }
-                    // the plane's copies, observed through the barrier, ordered before the tensor
-                    // core's reads; the zeroed window before its writes
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint64_t dp = tc_desc(saddr(ring + slot * SH::PLANEB), TC_HALF, 128);
-                    const int rot = p % 3;
-#pragma unroll
-                    for (int dx = 0; dx < 3; ++dx) {
-                        const uint64_t db = dw0 + (uint64_t)(((rot * 3 + dx) * RL_BB) >> 4);
-#pragma unroll
-                        for (int h = 0; h < TR + 2; ++h) {  // halo row h feeds rows h-2 .. h of three planes
-                            const uint64_t da = dp + (uint64_t)(((h * TC_ROWB) + dx * 16) >> 4);
-                            asm volatile(
-                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + 48 * h),
-                                "l"(da), "l"(db), "r"(RL_IDESC), "r"(1));
+            unsigned s = 0, cnt[2] = {0, 0};
+            for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += 2 * G) {
+                const int nt = t0 + G < ntiles ? 2 : 1;
+                for (int p = 0; p < nz && ok; ++p) {
+                    for (int w = 0; w < nt; ++w, ++s) {
+                        const int slot = s % SH::SLOTS;
+                        if (!ws_wait(saddr(&full[slot]), (s / SH::SLOTS) & 1, &abort) ||
+                            (cnt[w] >= 1 && !ws_wait(saddr(&acce[w]), (cnt[w] - 1) & 1, &abort))) {
+                            ok = false;
+                            break;
                         }
+                        // the plane's copies, observed through the barrier, ordered before the tensor
+                        // core's reads; the zeroed window before its writes
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        const uint64_t dp = tc_desc(saddr(ring + slot * SH::PLANEB), TC_HALF, 128);
+                        const uint32_t win = tmem + w * SH::WIN_COLS;
+                        const int rot = p % 3;
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const uint32_t bmat = (rot * 3 + dx) * RL_BB;
+#pragma unroll
+                            for (int h = 0; h < TR + 2; ++h) {
+                                // halo row h feeds tile rows h-2+j for j in [jlo, jhi]
+                                const int jlo = h < 2 ? 2 - h : 0, jhi = h > TR - 1 ? TR + 1 - h : 2;
+                                const uint64_t da = dp + (uint64_t)(((h * TC_ROWB) + dx * 16) >> 4);
+                                const uint64_t db = dw0 + (uint64_t)((bmat + 48 * jlo * 16) >> 4);
+                                asm volatile(
+                                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                        win + 48 * (h - 2 + jlo)),
+                                    "l"(da), "l"(db), "r"(rl_idesc(48 * (jhi - jlo + 1))), "r"(1));
+                            }
+                        }
+                        tc_commit(saddr(&accf[w]));
+                        tc_commit(saddr(&empty[slot]));  // the input plane has no later reader
+                        ++cnt[w];
                     }
-                    tc_commit(saddr(&accf));
-                    tc_commit(saddr(&empty[slot]));  // the input plane has no later reader
-                    ++step;
                 }
             }
             // no MMA may be in flight when the tensor memory is freed (a bounded wait, abort or not)
-            if (step > 0) tc_wait(saddr(&accf), (step - 1) & 1);
+            for (int w = 0; w < 2; ++w)
+                if (cnt[w] > 0) tc_wait(saddr(&accf[w]), (cnt[w] - 1) & 1);
         }
     } else {
         // ---- epilogue: thread (erow, ecell) owns one cell of the tile rows
         const int erow = warp >> 2, ecell = (warp & 3) * 32 + lane;
-        const uint32_t tq = tmem + 48 * (erow + 2) + ((uint32_t)((warp & 3) * 32) << 16);
-        auto load16 = [&](int q, float (&v)[16]) {
+        auto load16 = [&](int w, int q, float (&v)[16]) {
             uint32_t r[16];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                : "r"(tq + 16 * q));
+                : "r"(tmem + w * SH::WIN_COLS + 48 * erow + 16 * q + ((uint32_t)((warp & 3) * 32) << 16)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
         };
-        // output plane o of the tile: BF16 cells into staging buffer `nemit & 1`, then one bulk copy
-        // (TMA) per tile row from the buffer to global memory, issued by epilogue thread 0; a buffer
-        // is rewritten once the copy issued from it two emits earlier has read it
+        // output plane o of a tile: the warp's 32 cells (1 KB of BF16) into its staging buffer
+        // `nemit & 1`, then one bulk copy (TMA) of them to global memory issued by the warp's lane 0;
+        // a buffer is rewritten once the copy issued from it two emits earlier has read it
         unsigned nemit = 0;
         auto emit = [&](int o, int x0, int y0, float (&v)[16]) {
             const size_t pidx = ((size_t)o * ny + y0 + erow) * nx + x0 + ecell;
@@ -496,55 +516,57 @@ __global__ void __launch_bounds__(RlShape<TR>::NT) k_conv16_roll(const __nv_bflo
                 h0[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
                 h1[c] = __floats2bfloat162_rn(v[8 + 2 * c], v[8 + 2 * c + 1]);
             }
-            unsigned char* B = stage + (nemit & 1) * SH::STAGE;
-            if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-            asm volatile("bar.sync 1, %0;" ::"n"(SH::NEPI) : "memory");  // the buffer's last copy has read it
-            *reinterpret_cast<uint4*>(B + (erow * TCX + ecell) * 32) = o0;
-            *reinterpret_cast<uint4*>(B + (erow * TCX + ecell) * 32 + 16) = o1;
+            unsigned char* B = stage + (nemit & 1) * SH::STAGE + warp * 1024;
+            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            __syncwarp();  // the buffer's last copy has read it
+            *reinterpret_cast<uint4*>(B + lane * 32) = o0;
+            *reinterpret_cast<uint4*>(B + lane * 32 + 16) = o1;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the stores, for the bulk copy
-            asm volatile("bar.sync 1, %0;" ::"n"(SH::NEPI) : "memory");
-            if (tid == 0) {
-#pragma unroll
-                for (int r = 0; r < TR; ++r)
-                    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
-                                     out + (((size_t)o * ny + y0 + r) * nx + x0) * 16),
-                                 "r"(saddr(B + r * TCX * 32)), "n"(TCX * 32)
-                                 : "memory");
+            __syncwarp();
+            if (lane == 0) {
+                asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], 1024;" ::"l"(out + (pidx - lane) * 16),
+                             "r"(saddr(B))
+                             : "memory");
                 asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             }
             ++nemit;
         };
-        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-            const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
-            for (int p = 0; p < nz; ++p) {
-                if (!ws_wait(saddr(&accf), step & 1, &abort)) {
-                    ok = false;
-                    break;
+        unsigned cnt[2] = {0, 0};
+        for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += 2 * G) {
+            const int nt = t0 + G < ntiles ? 2 : 1;
+            for (int p = 0; p < nz && ok; ++p) {
+                for (int w = 0; w < nt; ++w) {
+                    const int tile = t0 + w * G;
+                    const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
+                    if (!ws_wait(saddr(&accf[w]), cnt[w] & 1, &abort)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const bool last = p == nz - 1;
+                    float va[16], vb[16];
+                    if (p >= 1) load16(w, (p - 1) % 3, va);  // output plane p-1 is complete
+                    if (last) load16(w, (nz - 1) % 3, vb);   // ... and after the last plane, plane nz-1
+                    // zero what was drained (after the tile's last plane the whole window, including the
+                    // block of the plane beyond the end), so the tile's next MMAs may accumulate
+                    if (last) {
+                        zero_block(w, 0);
+                        zero_block(w, 1);
+                        zero_block(w, 2);
+                    } else {
+                        zero_block(w, (p + 2) % 3);
+                    }
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(saddr(&acce[w]));
+                    if (p >= 1) emit(p - 1, x0, y0, va);
+                    if (last) emit(nz - 1, x0, y0, vb);
+                    ++cnt[w];
                 }
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const bool last = p == nz - 1;
-                float va[16], vb[16];
-                if (p >= 1) load16((p - 1) % 3, va);  // output plane p-1 is complete
-                if (last) load16((nz - 1) % 3, vb);   // ... and after the last input plane, plane nz-1
-                // zero what was drained (after the tile's last plane the whole window, including the
-                // block of the plane beyond the end), so the next plane's MMAs may accumulate
-                if (last) {
-                    zero_block(0);
-                    zero_block(1);
-                    zero_block(2);
-                } else {
-                    zero_block((p + 2) % 3);
-                }
-                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(saddr(&acce));
-                if (p >= 1) emit(p - 1, x0, y0, va);
-                if (last) emit(nz - 1, x0, y0, vb);
-                ++step;
             }
         }
-        if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the output has been written
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the output has been written
     }
     if (!ok) {
         abort = 1;
@@ -577,7 +599,7 @@ static int conv16_roll_grid(int nx, int ny) {
 template <int EPI>
 static void conv16(const NNBufs& b, const __nv_bfloat16* in, const __nv_bfloat16* W, const float* bias,
                    const __nv_bfloat16* mask, __nv_bfloat16* out, int nx, int ny, int nz, cudaStream_t s) {
-    if (nx % TCX == 0 && ny % 2 == 0) {
+    if (nx % TCX == 0 && ny % 2 == 0 && (size_t)nx * ny * 16 < ((size_t)1 << 32)) {
         if (ny % 4 == 0)
             k_conv16_roll<EPI, 4><<<conv16_roll_grid<4>(nx, ny), RlShape<4>::NT, RlShape<4>::SMEM, s>>>(
                 in, W, bias, mask, out, nx, ny, nz, b.err);
@@ -914,6 +936,306 @@ __global__ void __launch_bounds__(128) k_last_proj(const __nv_bfloat16* __restri
         }
         cp_wait_nn<0>();
     }
+}
+
+// ---------------------------------------------------------------- last layer (16 -> 1) on tcgen05
+// The rolling scheme of k_conv16_roll for one output channel: the view (input plane p, halo row h,
+// shift dx) feeds rows h-2 .. h of output planes p+1, p, p-1, nine single-channel outputs, so one MMA
+// of N = 16 (M = 128 cells, K = 16 channels; B columns 9 .. 15 zero) covers them. Each halo row h has
+// its own 16 accumulator columns at 16 h (column 3 j + q: tile row h-2+j, residue q = plane mod 3), so
+// output row r of a plane sums column 3 j + q of the blocks of rows r+2-j (j = 0, 1, 2). Per input
+// plane 3 (TR + 2) MMAs; then output plane p-1 is complete. The epilogue warps (one per lane quarter,
+// a thread owns one cell of every tile row) load the whole window of their lanes (all loads in
+// flight, one wait), add each row's three columns, zero the drained residue's columns (all after the
+// tile's last plane), store it back, hand it back and store the outputs (+ bias) in FP32. Two windows
+// of 16 (TR + 2) columns take a pair of tiles plane by plane in turn, so the tensor core fills one
+// while the epilogue drains the other. Producers and the bounded waits as in k_conv16_roll.
+static constexpr int LR_NPROD = 64;
+static constexpr int LR_BB = 16 * 32;  // one B matrix: [K half][16 rows][8 ci]
+static constexpr int LR_WB = 9 * LR_BB;
+static constexpr uint32_t LR_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+template <int TR>
+struct LrShape {
+    static constexpr int NT = 128 + 32 + LR_NPROD;  // epilogue warps, the MMA warp, the producers
+    static constexpr int PLANEB = (TR + 2) * TC_ROWB;
+    static constexpr int SLOTS = 4;
+    static constexpr int SMEM = LR_WB + SLOTS * PLANEB;
+    static constexpr int WIN_COLS = 16 * (TR + 2);  // one block of 16 columns per halo row
+    static constexpr int TMEM_COLS = 2 * WIN_COLS <= 128 ? 128 : 256;
+    static_assert(2 * WIN_COLS <= TMEM_COLS, "two windows");
+};
+
+template <int TR>
+__global__ void __launch_bounds__(LrShape<TR>::NT, 2) k_last_roll(const __nv_bfloat16* __restrict__ in,
+                                                               const __nv_bfloat16* __restrict__ W,
+                                                               const float* __restrict__ bias,
+                                                               float* __restrict__ out, int nx, int ny, int nz,
+                                                               int* err) {
+    typedef LrShape<TR> SH;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[LrShape<TR>::SLOTS], empty[LrShape<TR>::SLOTS], accf[2], acce[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort;
+    unsigned char* Ws = smem;
+    unsigned char* ring = smem + LR_WB;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // B matrix (rotation rot, shift dx): row n = 3 j + q (n < 9) is tap dy = 2 - j, dz = (rot + 1 - q)
+    // mod 3 of W4[ci][tap]; rows 9 .. 15 zero
+    for (int e = tid; e < 9 * 16 * 16; e += SH::NT) {
+        const int mtx = e / 256, n = (e / 16) % 16, ci = e % 16;
+        const int rot = mtx / 3, dx = mtx % 3, j = n / 3, qq = n % 3;
+        float w = 0.f;
+        if (n < 9) {
+            const int dy = 2 - j, dz = (rot + 4 - qq) % 3;
+            w = __bfloat162float(W[ci * 27 + (dz * 3 + dy) * 3 + dx]);
+        }
+        *reinterpret_cast<__nv_bfloat16*>(Ws + mtx * LR_BB + (ci >> 3) * (LR_BB / 2) + n * 16 + (ci & 7) * 2) =
+            __float2bfloat16_rn(w);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
+                     "n"(SH::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < SH::SLOTS; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&full[s])), "n"(LR_NPROD));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty[s])));
+        }
+        for (int w = 0; w < 2; ++w) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&accf[w])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(saddr(&acce[w])));
+        }
+        abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    const float b4 = __ldg(bias);
+    const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // an epilogue warp's lane quarter
+    auto ld16 = [&](int blk, uint32_t (&r)[16]) {  // the caller waits (tcgen05.wait::ld) before use
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(tlane + 16 * blk));
+    };
+    auto st16 = [&](int blk, const uint32_t (&r)[16]) {
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+                tlane + 16 * blk),
+            "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+            "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+            : "memory");
+    };
+    if (tid < 128) {  // both windows start at zero
+        uint32_t z[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) z[c] = 0;
+#pragma unroll
+        for (int h = 0; h < 2 * (TR + 2); ++h) st16(h, z);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int tiles_x = nx / TCX, ntiles = tiles_x * (ny / TR);
+    const int G = (int)gridDim.x;
+    bool ok = true;
+    // tiles in pairs (t, t + G) as in k_conv16_roll: while the epilogue drains one tile's window the
+    // tensor core accumulates into the other's
+    if (tid >= 128 + 32) {
+        // ---- producers: the pair's planes in turn into slot q % SLOTS of the ring
+        const int ptid = tid - (128 + 32);
+        constexpr int NCH = (TR + 2) * TC_ROWC * 2, CPT = (NCH + LR_NPROD - 1) / LR_NPROD;
+        int ch_dst[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            const int qq = ptid + LR_NPROD * c;
+            ch_dst[c] = qq < NCH ? ((qq >> 1) / TC_ROWC) * TC_ROWB + (qq & 1) * TC_HALF + ((qq >> 1) % TC_ROWC) * 16 : -1;
+        }
+        int q = 0;
+        for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += 2 * G) {
+            const int nt = t0 + G < ntiles ? 2 : 1;
+            uint32_t src[2][CPT];  // element offsets within a plane (the caller keeps a plane below 2^32)
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                const int tile = w < nt ? t0 + w * G : t0;
+                const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) {
+                    const int qq = ptid + LR_NPROD * c;
+                    const int hh = qq & 1, cc = (qq >> 1) % TC_ROWC, rr = (qq >> 1) / TC_ROWC;
+                    src[w][c] = ((uint32_t)nwrap(y0 - 1 + rr, ny) * nx + nwrap(x0 - 1 + cc, nx)) * 16 + hh * 8;
+                }
+            }
+            for (int p = 0; p < nz && ok; ++p) {
+                for (int w = 0; w < nt; ++w, ++q) {
+                    const int slot = q % SH::SLOTS;
+                    if (q >= SH::SLOTS && !ws_wait(saddr(&empty[slot]), ((q / SH::SLOTS) - 1) & 1, &abort)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char* P = ring + slot * SH::PLANEB;
+                    const __nv_bfloat16* base = in + (size_t)p * ny * nx * 16;
+#pragma unroll
+                    for (int c = 0; c < CPT; ++c)
+                        if (ch_dst[c] >= 0) cp16(P + ch_dst[c], base + src[w][c]);
+                    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(saddr(&full[slot]))
+                                 : "memory");
+                }
+            }
+        }
+        cp_wait_nn<0>();
+    } else if (warp == 4) {
+        // ---- MMA thread: one step per input plane of a tile, into that tile's window
+        if (lane == 0) {
+            const uint64_t dw0 = tc_desc(saddr(Ws), LR_BB / 2, 128);
+            unsigned s = 0, cnt[2] = {0, 0};
+            for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += 2 * G) {
+                const int nt = t0 + G < ntiles ? 2 : 1;
+                for (int p = 0; p < nz && ok; ++p) {
+                    for (int w = 0; w < nt; ++w, ++s) {
+                        const int slot = s % SH::SLOTS;
+                        if (!ws_wait(saddr(&full[slot]), (s / SH::SLOTS) & 1, &abort) ||
+                            (cnt[w] >= 1 && !ws_wait(saddr(&acce[w]), (cnt[w] - 1) & 1, &abort))) {
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        const uint64_t dp = tc_desc(saddr(ring + slot * SH::PLANEB), TC_HALF, 128);
+                        const uint32_t win = tmem + w * SH::WIN_COLS;
+                        const int rot = p % 3;
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const uint64_t db = dw0 + (uint64_t)(((rot * 3 + dx) * LR_BB) >> 4);
+#pragma unroll
+                            for (int h = 0; h < TR + 2; ++h) {
+                                const uint64_t da = dp + (uint64_t)(((h * TC_ROWB) + dx * 16) >> 4);
+                                asm volatile(
+                                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(win + 16 * h),
+                                    "l"(da), "l"(db), "r"(LR_IDESC), "r"(1));
+                            }
+                        }
+                        tc_commit(saddr(&accf[w]));
+                        tc_commit(saddr(&empty[slot]));
+                        ++cnt[w];
+                    }
+                }
+            }
+            for (int w = 0; w < 2; ++w)
+                if (cnt[w] > 0) tc_wait(saddr(&accf[w]), (cnt[w] - 1) & 1);
+        }
+    } else {
+        // ---- epilogue warps 0 .. 3: the thread owns cell `cell` of every tile row
+        const int cell = (warp & 3) * 32 + lane;
+        unsigned cnt[2] = {0, 0};
+        for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += 2 * G) {
+            const int nt = t0 + G < ntiles ? 2 : 1;
+            for (int p = 0; p < nz && ok; ++p) {
+                for (int w = 0; w < nt; ++w) {
+                    const int tile = t0 + w * G;
+                    const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
+                    if (!ws_wait(saddr(&accf[w]), cnt[w] & 1, &abort)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const bool last = p == nz - 1;
+                    const int qa = (p + 2) % 3;   // residue of output plane p-1: drained (p >= 1) and zeroed
+                    const int qb = (nz - 1) % 3;  // residue of output plane nz-1, drained after the last plane
+                    float oa[TR], ob[TR];
+#pragma unroll
+                    for (int r = 0; r < TR; ++r) oa[r] = ob[r] = 0.f;
+                    // the window of this lane in two halves, each half's loads in flight at once
+                    constexpr int HH = (TR + 2) / 2;
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                    uint32_t vv[HH][16];
+#pragma unroll
+                    for (int i = 0; i < HH; ++i) ld16(w * (TR + 2) + g * HH + i, vv[i]);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int i = 0; i < HH; ++i) {
+                        const int h = g * HH + i;
+                        uint32_t (&v)[16] = vv[i];
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            const int r = h - 2 + j;
+                            if (r < 0 || r >= TR) continue;
+                            const float a0 = __uint_as_float(v[3 * j]), a1 = __uint_as_float(v[3 * j + 1]),
+                                        a2 = __uint_as_float(v[3 * j + 2]);
+                            oa[r] += qa == 0 ? a0 : (qa == 1 ? a1 : a2);
+                            ob[r] += qb == 0 ? a0 : (qb == 1 ? a1 : a2);
+                        }
+#pragma unroll
+                        for (int c = 0; c < 9; ++c)
+                            if (last || c % 3 == qa) v[c] = 0;
+                        st16(w * (TR + 2) + h, v);
+                    }
+                    }
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(saddr(&acce[w]));
+#pragma unroll
+                    for (int r = 0; r < TR; ++r) {
+                        const size_t row = (size_t)(y0 + r) * nx + x0 + cell;
+                        if (p >= 1) out[(size_t)(p - 1) * nx * ny + row] = oa[r] + b4;
+                        if (last) out[(size_t)(nz - 1) * nx * ny + row] = ob[r] + b4;
+                    }
+                    ++cnt[w];
+                }
+            }
+        }
+    }
+    if (!ok) {
+        abort = 1;
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(SH::TMEM_COLS));
+}
+
+template <int TR>
+static int last_roll_grid(int nx, int ny) {
+    typedef LrShape<TR> SH;
+    static int per_sm = 0, nsm = 0;
+    if (per_sm == 0) {
+        cudaFuncSetAttribute(k_last_roll<TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM);
+        cudaFuncSetAttribute(k_last_roll<TR>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        int dev = 0, occ = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        // blocks per SM from the register file, shared memory and thread slots (the occupancy query
+        // answers one for this kernel where the launch holds two)
+        cudaFuncAttributes fa;
+        cudaFuncGetAttributes(&fa, k_last_roll<TR>);
+        int regs_sm = 0, smem_sm = 0, resv = 0, thr_sm = 0;
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+        const int warps = (SH::NT + 31) / 32, regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+        const int by_regs = regs_sm / (warps * regs_warp);
+        const int by_smem = smem_sm / (int)(SH::SMEM + fa.sharedSizeBytes + resv);
+        const int by_thr = thr_sm / SH::NT;
+        occ = by_regs < by_smem ? by_regs : by_smem;
+        if (by_thr < occ) occ = by_thr;
+        per_sm = occ;
+        if (per_sm > 512 / SH::TMEM_COLS) per_sm = 512 / SH::TMEM_COLS;  // tcgen05.alloc never waits
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int ntiles = (nx / TCX) * (ny / TR);
+    const int nb = per_sm * nsm;
+    return nb < ntiles ? nb : ntiles;
 }
 
 // partial weight gradient of the first layer: dW1[co][ci][tap] = sum_p d1[p][co] x[p + d(tap)][ci].
@@ -1334,12 +1656,17 @@ void nn_forward(const NNBufs& b, int nx, int ny, int nz, const __nv_bfloat16* x,
     note_launch();
     conv16<EPI_RELU>(b, b.a1, b.w2f, b2, nullptr, b.a2, nx, ny, nz, s);
     conv16<EPI_RELU>(b, b.a2, b.w3f, b3, nullptr, b.a3, nx, ny, nz, s);
-    static bool lp_attr = false;
-    if (!lp_attr) {
-        cudaFuncSetAttribute(k_last_proj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LP_SMEM);
-        lp_attr = true;
+    if (nx % TCX == 0 && ny % 4 == 0 && (size_t)nx * ny * 16 < ((size_t)1 << 32)) {
+        k_last_roll<4><<<last_roll_grid<4>(nx, ny), LrShape<4>::NT, LrShape<4>::SMEM, s>>>(b.a3, b.w4, b4, out, nx, ny,
+                                                                                        nz, b.err);
+    } else {
+        static bool lp_attr = false;
+        if (!lp_attr) {
+            cudaFuncSetAttribute(k_last_proj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LP_SMEM);
+            lp_attr = true;
+        }
+        k_last_proj<<<resident_grid(k_last_proj, LP_SMEM, nx, ny), 128, LP_SMEM, s>>>(b.a3, b.w4, b4, out, nx, ny, nz);
     }
-    k_last_proj<<<resident_grid(k_last_proj, LP_SMEM, nx, ny), 128, LP_SMEM, s>>>(b.a3, b.w4, b4, out, nx, ny, nz);
     note_launch();
 }
 
