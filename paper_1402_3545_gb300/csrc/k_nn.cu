@@ -76,6 +76,9 @@ __device__ __forceinline__ unsigned sa_nn(const void* p) { return (unsigned)__cv
 __device__ __forceinline__ void cp16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa_nn(dst)), "l"(src));
 }
+__device__ __forceinline__ void cp4nn(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa_nn(dst)), "l"(src));
+}
 __device__ __forceinline__ void cp_commit_nn() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_wait_nn() {
@@ -300,43 +303,78 @@ static constexpr int RL_WB = 9 * RL_BB;
 __host__ __device__ constexpr uint32_t rl_idesc(int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
 }
-template <int TR>
+template <int TR, bool FIRST = false>
 struct RlShape {
     static constexpr int NEPI = 128 * TR;
     static constexpr int NT = NEPI + 32 + RL_NPROD;
-    static constexpr int PLANEB = (TR + 2) * TC_ROWB;
-    static constexpr int SLOTS = 6;              // input planes in flight or waiting for the tensor core
+    // weights: nine B matrices (rotation, dx); the first layer folds dx into K: three (rotation)
+    static constexpr int WB = FIRST ? 3 * RL_BB : RL_WB;
+    // one halo row of the A ring: 130 cells x 16 channels (both K halves), or for the first layer the
+    // 128 cells of an operand row (K half 0: dx x 2 channels, K half 1 zero)
+    static constexpr int ROWB = FIRST ? 2 * TCX * 16 : TC_ROWB;
+    static constexpr int PLANEB = (TR + 2) * ROWB;
+    static constexpr int SLOTS = FIRST ? 3 : (TR == 4 ? 6 : 3);  // operand planes in flight or waiting
+                                                                  // (two rows: three, two blocks per SM)
+    // first layer: raw halo rows (130 cells x 2 BF16 channels, 12 bytes of padding on either side,
+    // the 128 interior cells 16-byte aligned) in a ring of RAW planes
+    static constexpr int RAWROW = 32 + TCX * 4;
+    static constexpr int RAW = FIRST ? 8 : 0;
+    static constexpr int RAWB = (TR + 2) * RAWROW;
     static constexpr int STAGE = TR * TCX * 32;  // one output plane of the tile in BF16, rows of 4 KB
-    static constexpr int SMEM = RL_WB + SLOTS * PLANEB + 2 * STAGE;
+    // output staging buffers per epilogue warp: up to NSTG of a warp's 1 KB bulk stores are in flight,
+    // which is what hides the write latency
+    static constexpr int NSTG = 2;
+    static constexpr int SMEM = WB + SLOTS * PLANEB + RAW * RAWB + NSTG * STAGE;
     static constexpr int WIN_COLS = 48 * TR;     // one tile's window of three output planes
     static constexpr int TMEM_COLS = 2 * WIN_COLS <= 256 ? 256 : 512;
     static_assert(TR >= 2 && 2 * WIN_COLS <= 512, "two windows in the tensor memory");
 };
 
-template <int EPI, int TR>
-__global__ void __launch_bounds__(RlShape<TR>::NT) k_conv16_roll(const __nv_bfloat16* __restrict__ in,
+template <int EPI, int TR, bool FIRST = false>
+__global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __nv_bfloat16* __restrict__ in,
                                                                  const __nv_bfloat16* __restrict__ Wt,
                                                                  const float* __restrict__ bias,
                                                                  const __nv_bfloat16* __restrict__ mask,
                                                                  __nv_bfloat16* __restrict__ out, int nx, int ny,
                                                                  int nz, int* err) {
-    typedef RlShape<TR> SH;
+    typedef RlShape<TR, FIRST> SH;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t full[RlShape<TR>::SLOTS], empty[RlShape<TR>::SLOTS], accf[2], acce[2];
+    __shared__ __align__(8) uint64_t full[SH::SLOTS], empty[SH::SLOTS], accf[2], acce[2];
     __shared__ uint32_t tmem_base;
     __shared__ float bsh[16];
     __shared__ volatile int abort;
+    __shared__ volatile int pstat[2];  // first layer: the producers' verdict on step q, slot q & 1
     unsigned char* Ws = smem;
-    unsigned char* ring = smem + RL_WB;
-    unsigned char* stage = ring + SH::SLOTS * SH::PLANEB;  // two output staging buffers
+    unsigned char* ring = smem + SH::WB;
+    unsigned char* raw = ring + SH::SLOTS * SH::PLANEB;  // first layer only
+    unsigned char* stage = raw + SH::RAW * SH::RAWB;     // NSTG output staging buffers
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // B matrix (rotation rot, shift dx), row 48 j + 16 q + co: tap dy = 2 - j, dz = (rot + 1 - q) mod 3
-    for (int e = tid; e < 9 * 9 * 32; e += SH::NT) {
-        const int mtx = e / 288, blk = (e / 32) % 9, co = (e >> 1) & 15, h = e & 1;
-        const int rot = mtx / 3, dx = mtx % 3, j = blk / 3, qq = blk % 3;
-        const int dy = 2 - j, dz = (rot + 4 - qq) % 3, tap = (dz * 3 + dy) * 3 + dx;
-        *reinterpret_cast<uint4*>(Ws + mtx * RL_BB + h * (RL_BB / 2) + (blk * 16 + co) * 16) =
-            __ldg(reinterpret_cast<const uint4*>(Wt + (tap * 16 + co) * 16 + h * 8));
+    if constexpr (FIRST) {
+        // B matrix (rotation rot), row 48 j + 16 q + co, K index 2 dx + ci (K 6 .. 15 zero): tap
+        // dy = 2 - j, dz = (rot + 1 - q) mod 3 of W1[co][ci][tap]
+        for (int e = tid; e < 3 * 144 * 16; e += SH::NT) {
+            const int rot = e / 2304, n = (e >> 4) % 144, k = e & 15;
+            const int j = n / 48, qq = (n / 16) % 3, co = n & 15;
+            float wv = 0.f;
+            if (k < 6) {
+                const int dx = k >> 1, ci = k & 1, dy = 2 - j, dz = (rot + 4 - qq) % 3;
+                wv = __bfloat162float(Wt[(co * 2 + ci) * 27 + (dz * 3 + dy) * 3 + dx]);
+            }
+            *reinterpret_cast<__nv_bfloat16*>(Ws + rot * RL_BB + (k >> 3) * (RL_BB / 2) + n * 16 + (k & 7) * 2) =
+                __float2bfloat16_rn(wv);
+        }
+        // the operand ring starts at zero; its K half 1 is never written again
+        for (int i = tid; i < SH::SLOTS * SH::PLANEB / 16; i += SH::NT)
+            reinterpret_cast<uint4*>(ring)[i] = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+        // B matrix (rotation rot, shift dx), row 48 j + 16 q + co: tap dy = 2 - j, dz = (rot + 1 - q) mod 3
+        for (int e = tid; e < 9 * 9 * 32; e += SH::NT) {
+            const int mtx = e / 288, blk = (e / 32) % 9, co = (e >> 1) & 15, h = e & 1;
+            const int rot = mtx / 3, dx = mtx % 3, j = blk / 3, qq = blk % 3;
+            const int dy = 2 - j, dz = (rot + 4 - qq) % 3, tap = (dz * 3 + dy) * 3 + dx;
+            *reinterpret_cast<uint4*>(Ws + mtx * RL_BB + h * (RL_BB / 2) + (blk * 16 + co) * 16) =
+                __ldg(reinterpret_cast<const uint4*>(Wt + (tap * 16 + co) * 16 + h * 8));
+        }
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
@@ -384,48 +422,118 @@ __global__ void __launch_bounds__(RlShape<TR>::NT) k_conv16_roll(const __nv_bflo
     // the block's tiles in pairs (t, t + G), t = blockIdx.x + 2 G i; a pair runs its planes in turn
     // (tile 0 of the pair, tile 1, next plane ...); a pair whose second tile does not exist runs alone
     if (tid >= SH::NEPI + 32) {
-        // ---- producers: the pair's planes in turn into slot q % SLOTS of the ring
-        const int ptid = tid - (SH::NEPI + 32);
-        constexpr int NCH = (TR + 2) * TC_ROWC * 2, CPT = (NCH + RL_NPROD - 1) / RL_NPROD;
-        int ch_dst[CPT];
+        if constexpr (FIRST) {
+            // ---- producers, first layer: the pair's planes in turn. A plane's halo rows (130 cells x 2
+            // BF16 channels) arrive by cp.async in a ring of RAW planes, DQ steps ahead; then each
+            // producer writes the operand row of its cell: K = (dx, ci) for the shifts dx = 0 .. 2, the
+            // three 4-byte channel pairs of cells x-1 .. x+1 side by side
+            constexpr int CPR = TCX * 4 / 16 + 2;  // copies per halo row: 32 of 16 bytes, two halo cells
+            constexpr int NCH = (TR + 2) * CPR, CPT = (NCH + RL_NPROD - 1) / RL_NPROD;
+            constexpr int DQ = SH::RAW - 2;  // a raw slot is refilled two steps after it was read
+            const int ptid = tid - (SH::NEPI + 32);
+            int it0 = blockIdx.x, ip = 0, iw = 0, iq = 0;  // the next step to copy: pair, plane, tile
+            auto issue = [&]() {
+                if (it0 < ntiles) {
+                    const int tile = it0 + iw * G;
+                    const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
+                    unsigned char* R = raw + (iq % SH::RAW) * SH::RAWB;
+                    const __nv_bfloat16* base = in + (size_t)ip * ny * nx * 2;
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-            const int qq = ptid + RL_NPROD * c;
-            ch_dst[c] = qq < NCH ? ((qq >> 1) / TC_ROWC) * TC_ROWB + (qq & 1) * TC_HALF + ((qq >> 1) % TC_ROWC) * 16 : -1;
-        }
-        int q = 0;
-        for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += 2 * G) {
-            const int nt = t0 + G < ntiles ? 2 : 1;
-            uint32_t src[2][CPT];  // element offsets within a plane (the caller keeps a plane below 2^32)
-#pragma unroll
-            for (int w = 0; w < 2; ++w) {
-                const int tile = w < nt ? t0 + w * G : t0;
-                const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
-#pragma unroll
-                for (int c = 0; c < CPT; ++c) {
-                    const int qq = ptid + RL_NPROD * c;
-                    const int hh = qq & 1, cc = (qq >> 1) % TC_ROWC, rr = (qq >> 1) / TC_ROWC;
-                    src[w][c] = ((uint32_t)nwrap(y0 - 1 + rr, ny) * nx + nwrap(x0 - 1 + cc, nx)) * 16 + hh * 8;
-                }
-            }
-            for (int p = 0; p < nz && ok; ++p) {
-                for (int w = 0; w < nt; ++w, ++q) {
-                    const int slot = q % SH::SLOTS;
-                    if (q >= SH::SLOTS && !ws_wait(saddr(&empty[slot]), ((q / SH::SLOTS) - 1) & 1, &abort)) {
-                        ok = false;
-                        break;
+                    for (int c = 0; c < CPT; ++c) {
+                        const int qq = ptid + RL_NPROD * c;
+                        if (qq < NCH) {
+                            const int rr = qq / CPR, k = qq % CPR;
+                            const size_t row = (size_t)nwrap(y0 - 1 + rr, ny) * nx;
+                            unsigned char* d = R + rr * SH::RAWROW;
+                            if (k < CPR - 2) cp16(d + 16 + 16 * k, base + (row + x0) * 2 + 8 * k);
+                            else if (k == CPR - 2) cp4nn(d + 12, base + (row + nwrap(x0 - 1, nx)) * 2);
+                            else cp4nn(d + 16 + TCX * 4, base + (row + nwrap(x0 + TCX, nx)) * 2);
+                        }
                     }
-                    unsigned char* P = ring + slot * SH::PLANEB;
-                    const __nv_bfloat16* base = in + (size_t)p * ny * nx * 16;
+                    ++iq;
+                    const int nt = it0 + G < ntiles ? 2 : 1;
+                    if (++iw == nt) {
+                        iw = 0;
+                        if (++ip == nz) {
+                            ip = 0;
+                            it0 += 2 * G;
+                        }
+                    }
+                }
+                cp_commit_nn();  // one group per step, empty past the block's last step
+            };
+            int nsteps = 0;
+            for (int t0 = blockIdx.x; t0 < ntiles; t0 += 2 * G) nsteps += nz * (t0 + G < ntiles ? 2 : 1);
+            for (int i = 0; i < DQ; ++i) issue();
+            for (int q = 0; q < nsteps; ++q) {
+                issue();              // step q + DQ
+                cp_wait_nn<DQ>();     // this thread's copies of step q have landed
+                const int slot = q % SH::SLOTS;
+                // one thread waits for the operand slot; the barrier hands its verdict (and, with the
+                // other producers' copies, the whole raw plane) to all, so that all leave together
+                if (ptid == 0)
+                    pstat[q & 1] =
+                        (q < SH::SLOTS || ws_wait(saddr(&empty[slot]), ((q / SH::SLOTS) - 1) & 1, &abort)) ? 1 : 0;
+                asm volatile("bar.sync 1, %0;" ::"n"(RL_NPROD) : "memory");
+                if (!pstat[q & 1]) {
+                    ok = false;
+                    break;
+                }
+                const unsigned char* R = raw + (q % SH::RAW) * SH::RAWB;
+                unsigned char* A = ring + slot * SH::PLANEB;
 #pragma unroll
-                    for (int c = 0; c < CPT; ++c)
-                        if (ch_dst[c] >= 0) cp16(P + ch_dst[c], base + src[w][c]);
-                    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(saddr(&full[slot]))
-                                 : "memory");
+                for (int h = 0; h < TR + 2; ++h) {
+                    const uint32_t* r = reinterpret_cast<const uint32_t*>(R + h * SH::RAWROW + 12) + ptid;
+                    *reinterpret_cast<uint4*>(A + h * SH::ROWB + ptid * 16) = make_uint4(r[0], r[1], r[2], 0u);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the operand, for the MMAs
+                mbar_arrive(saddr(&full[slot]));
+            }
+            cp_wait_nn<0>();
+        } else {
+            // ---- producers: the pair's planes in turn into slot q % SLOTS of the ring
+            const int ptid = tid - (SH::NEPI + 32);
+            constexpr int NCH = (TR + 2) * TC_ROWC * 2, CPT = (NCH + RL_NPROD - 1) / RL_NPROD;
+            int ch_dst[CPT];
+    #pragma unroll
+            for (int c = 0; c < CPT; ++c) {
+                const int qq = ptid + RL_NPROD * c;
+                ch_dst[c] = qq < NCH ? ((qq >> 1) / TC_ROWC) * TC_ROWB + (qq & 1) * TC_HALF + ((qq >> 1) % TC_ROWC) * 16 : -1;
+            }
+            int q = 0;
+            for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += 2 * G) {
+                const int nt = t0 + G < ntiles ? 2 : 1;
+                uint32_t src[2][CPT];  // element offsets within a plane (the caller keeps a plane below 2^32)
+    #pragma unroll
+                for (int w = 0; w < 2; ++w) {
+                    const int tile = w < nt ? t0 + w * G : t0;
+                    const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
+    #pragma unroll
+                    for (int c = 0; c < CPT; ++c) {
+                        const int qq = ptid + RL_NPROD * c;
+                        const int hh = qq & 1, cc = (qq >> 1) % TC_ROWC, rr = (qq >> 1) / TC_ROWC;
+                        src[w][c] = ((uint32_t)nwrap(y0 - 1 + rr, ny) * nx + nwrap(x0 - 1 + cc, nx)) * 16 + hh * 8;
+                    }
+                }
+                for (int p = 0; p < nz && ok; ++p) {
+                    for (int w = 0; w < nt; ++w, ++q) {
+                        const int slot = q % SH::SLOTS;
+                        if (q >= SH::SLOTS && !ws_wait(saddr(&empty[slot]), ((q / SH::SLOTS) - 1) & 1, &abort)) {
+                            ok = false;
+                            break;
+                        }
+                        unsigned char* P = ring + slot * SH::PLANEB;
+                        const __nv_bfloat16* base = in + (size_t)p * ny * nx * 16;
+    #pragma unroll
+                        for (int c = 0; c < CPT; ++c)
+                            if (ch_dst[c] >= 0) cp16(P + ch_dst[c], base + src[w][c]);
+                        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(saddr(&full[slot]))
+                                     : "memory");
+                    }
                 }
             }
+            cp_wait_nn<0>();
         }
-        cp_wait_nn<0>();
     } else if (warp == SH::NEPI / 32) {
         // ---- MMA thread: one step per input plane of a tile, into that tile's window
         if (lane == 0) {
@@ -445,23 +553,38 @@ __global__ void __launch_bounds__(RlShape<TR>::NT) k_conv16_roll(const __nv_bflo
                         // core's reads; the zeroed window before its writes
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         asm volatile("tcgen05.fence::after_thread_sync;");
-                        const uint64_t dp = tc_desc(saddr(ring + slot * SH::PLANEB), TC_HALF, 128);
+                        const uint64_t dp = tc_desc(saddr(ring + slot * SH::PLANEB), FIRST ? TCX * 16 : TC_HALF, 128);
                         const uint32_t win = tmem + w * SH::WIN_COLS;
                         const int rot = p % 3;
-#pragma unroll
-                        for (int dx = 0; dx < 3; ++dx) {
-                            const uint32_t bmat = (rot * 3 + dx) * RL_BB;
+                        if constexpr (FIRST) {
+                            // one MMA per halo row: K spans the three shifts
 #pragma unroll
                             for (int h = 0; h < TR + 2; ++h) {
-                                // halo row h feeds tile rows h-2+j for j in [jlo, jhi]
                                 const int jlo = h < 2 ? 2 - h : 0, jhi = h > TR - 1 ? TR + 1 - h : 2;
-                                const uint64_t da = dp + (uint64_t)(((h * TC_ROWB) + dx * 16) >> 4);
-                                const uint64_t db = dw0 + (uint64_t)((bmat + 48 * jlo * 16) >> 4);
+                                const uint64_t da = dp + (uint64_t)((h * SH::ROWB) >> 4);
+                                const uint64_t db = dw0 + (uint64_t)((rot * RL_BB + 48 * jlo * 16) >> 4);
                                 asm volatile(
                                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
                                         win + 48 * (h - 2 + jlo)),
                                     "l"(da), "l"(db), "r"(rl_idesc(48 * (jhi - jlo + 1))), "r"(1));
+                            }
+                        } else {
+#pragma unroll
+                            for (int dx = 0; dx < 3; ++dx) {
+                                const uint32_t bmat = (rot * 3 + dx) * RL_BB;
+#pragma unroll
+                                for (int h = 0; h < TR + 2; ++h) {
+                                    // halo row h feeds tile rows h-2+j for j in [jlo, jhi]
+                                    const int jlo = h < 2 ? 2 - h : 0, jhi = h > TR - 1 ? TR + 1 - h : 2;
+                                    const uint64_t da = dp + (uint64_t)(((h * TC_ROWB) + dx * 16) >> 4);
+                                    const uint64_t db = dw0 + (uint64_t)((bmat + 48 * jlo * 16) >> 4);
+                                    asm volatile(
+                                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                            win + 48 * (h - 2 + jlo)),
+                                        "l"(da), "l"(db), "r"(rl_idesc(48 * (jhi - jlo + 1))), "r"(1));
+                                }
                             }
                         }
                         tc_commit(saddr(&accf[w]));
@@ -489,8 +612,8 @@ __global__ void __launch_bounds__(RlShape<TR>::NT) k_conv16_roll(const __nv_bflo
             for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
         };
         // output plane o of a tile: the warp's 32 cells (1 KB of BF16) into its staging buffer
-        // `nemit & 1`, then one bulk copy (TMA) of them to global memory issued by the warp's lane 0;
-        // a buffer is rewritten once the copy issued from it two emits earlier has read it
+        // `nemit % NSTG`, then one bulk copy (TMA) of them to global memory issued by the warp's lane 0;
+        // a buffer is rewritten once the copy issued from it NSTG emits earlier has read it
         unsigned nemit = 0;
         auto emit = [&](int o, int x0, int y0, float (&v)[16]) {
             const size_t pidx = ((size_t)o * ny + y0 + erow) * nx + x0 + ecell;
@@ -516,8 +639,8 @@ __global__ void __launch_bounds__(RlShape<TR>::NT) k_conv16_roll(const __nv_bflo
                 h0[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
                 h1[c] = __floats2bfloat162_rn(v[8 + 2 * c], v[8 + 2 * c + 1]);
             }
-            unsigned char* B = stage + (nemit & 1) * SH::STAGE + warp * 1024;
-            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            unsigned char* B = stage + (nemit % SH::NSTG) * SH::STAGE + warp * 1024;
+            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(SH::NSTG - 1) : "memory");
             __syncwarp();  // the buffer's last copy has read it
             *reinterpret_cast<uint4*>(B + lane * 32) = o0;
             *reinterpret_cast<uint4*>(B + lane * 32 + 16) = o1;
@@ -578,20 +701,49 @@ __global__ void __launch_bounds__(RlShape<TR>::NT) k_conv16_roll(const __nv_bflo
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(SH::TMEM_COLS));
 }
 
-template <int TR>
+// Blocks of a kernel that fit on one SM by its registers, shared memory and thread slots (the
+// occupancy query answers one for the tensor-memory kernels here where a launch holds two), capped
+// by the tensor memory: 512 columns per SM, and tcgen05.alloc of a block beyond them would wait.
+static int blocks_per_sm(const void* fn, int nt, int smem, int tmem_cols) {
+    int dev = 0, regs_sm = 0, smem_sm = 0, resv = 0, thr_sm = 0;
+    cudaGetDevice(&dev);
+    cudaFuncAttributes fa;
+    cudaFuncGetAttributes(&fa, fn);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    const int warps = (nt + 31) / 32, regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    int k = regs_sm / (warps * regs_warp);
+    const int by_smem = smem_sm / (smem + (int)fa.sharedSizeBytes + resv), by_thr = thr_sm / nt;
+    if (by_smem < k) k = by_smem;
+    if (by_thr < k) k = by_thr;
+    if (k > 512 / tmem_cols) k = 512 / tmem_cols;
+    return k < 1 ? 1 : k;
+}
+
+template <int TR, bool FIRST = false>
 static int conv16_roll_grid(int nx, int ny) {
-    typedef RlShape<TR> SH;
-    static int nsm = 0;
+    typedef RlShape<TR, FIRST> SH;
+    static int nsm = 0, per_sm = 0;
     if (nsm == 0) {
-        cudaFuncSetAttribute(k_conv16_roll<EPI_RELU, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM);
-        cudaFuncSetAttribute(k_conv16_roll<EPI_MASK, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM);
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const void* fr = (const void*)k_conv16_roll<EPI_RELU, TR, FIRST>;
+        cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM);
+        cudaFuncSetAttribute(fr, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        per_sm = blocks_per_sm(fr, SH::NT, SH::SMEM, SH::TMEM_COLS);
+        if constexpr (!FIRST) {  // the masked variant (backward pass) shares the grid
+            const void* fm = (const void*)k_conv16_roll<EPI_MASK, TR, FIRST>;
+            cudaFuncSetAttribute(fm, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM);
+            cudaFuncSetAttribute(fm, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            const int b = blocks_per_sm(fm, SH::NT, SH::SMEM, SH::TMEM_COLS);
+            if (b < per_sm) per_sm = b;
+        }
     }
-    // one block per SM: the window takes the whole tensor memory (tcgen05.alloc never waits)
-    const int ntiles = (nx / TCX) * (ny / TR);
-    return nsm < ntiles ? nsm : ntiles;
+    const int ntiles = (nx / TCX) * (ny / TR), nb = per_sm * nsm;
+    return nb < ntiles ? nb : ntiles;
 }
 
 // one 16 -> 16 layer: the rolling-plane tcgen05 kernel (tiles of four rows, two where ny % 4 == 2)
@@ -739,9 +891,6 @@ __global__ void __launch_bounds__(128) k_first_z(const __nv_bfloat16* __restrict
 // it leaves in coalesced 16-byte stores instead of 4-byte pieces of 32-byte cells.
 static constexpr int FP_SLOTS = 6;
 static constexpr int FP_PLANE = PLANE_CELLS * 2;  // bf16 values of one halo plane (2 channels)
-__device__ __forceinline__ void cp4nn(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa_nn(dst)), "l"(src));
-}
 __global__ void __launch_bounds__(128) k_first_tc2(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ W,
                                                    const float* __restrict__ bias, __nv_bfloat16* __restrict__ out, int nx,
                                                    int ny, int nz) {
@@ -1211,27 +1360,10 @@ static int last_roll_grid(int nx, int ny) {
     if (per_sm == 0) {
         cudaFuncSetAttribute(k_last_roll<TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM);
         cudaFuncSetAttribute(k_last_roll<TR>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        int dev = 0, occ = 0;
+        int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        // blocks per SM from the register file, shared memory and thread slots (the occupancy query
-        // answers one for this kernel where the launch holds two)
-        cudaFuncAttributes fa;
-        cudaFuncGetAttributes(&fa, k_last_roll<TR>);
-        int regs_sm = 0, smem_sm = 0, resv = 0, thr_sm = 0;
-        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
-        const int warps = (SH::NT + 31) / 32, regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
-        const int by_regs = regs_sm / (warps * regs_warp);
-        const int by_smem = smem_sm / (int)(SH::SMEM + fa.sharedSizeBytes + resv);
-        const int by_thr = thr_sm / SH::NT;
-        occ = by_regs < by_smem ? by_regs : by_smem;
-        if (by_thr < occ) occ = by_thr;
-        per_sm = occ;
-        if (per_sm > 512 / SH::TMEM_COLS) per_sm = 512 / SH::TMEM_COLS;  // tcgen05.alloc never waits
-        if (per_sm < 1) per_sm = 1;
+        per_sm = blocks_per_sm((const void*)k_last_roll<TR>, SH::NT, SH::SMEM, SH::TMEM_COLS);
     }
     const int ntiles = (nx / TCX) * (ny / TR);
     const int nb = per_sm * nsm;
@@ -1652,6 +1784,9 @@ void nn_forward(const NNBufs& b, int nx, int ny, int nz, const __nv_bfloat16* x,
     const float* b4 = b3 + 16 + 16 * 27;
     const int gt = thin_grid(nx, ny, 1 << 30);
     if (b.cin == 1) k_first_z<1><<<gt, 128, 0, s>>>(x, b.w1, b1, b.a1, nx, ny, nz);
+    else if (nx % TCX == 0 && ny % 4 == 0)
+        k_conv16_roll<EPI_RELU, 4, true><<<conv16_roll_grid<4, true>(nx, ny), RlShape<4, true>::NT, RlShape<4, true>::SMEM,
+                                           s>>>(x, b.w1, b1, nullptr, b.a1, nx, ny, nz, b.err);
     else k_first_tc2<<<resident_grid(k_first_tc2, 0, nx, ny), 128, 0, s>>>(x, b.w1, b1, b.a1, nx, ny, nz);
     note_launch();
     conv16<EPI_RELU>(b, b.a1, b.w2f, b2, nullptr, b.a2, nx, ny, nz, s);
