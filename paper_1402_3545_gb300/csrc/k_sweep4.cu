@@ -1,11 +1,12 @@
-// k_sweep4.cu -- the FP32 line smoother (Eq. 11) and line solve (Eq. 9) with one tile of 128 x 2
-// columns per warp, four columns x two rows per thread.
+// k_sweep4.cu -- the FP32 line smoother (Eq. 11) and line solve (Eq. 9) with one tile of 128 x ROWS
+// columns per warp (ROWS = 1 or 2), four columns x ROWS rows per thread.
 //
-// Per plane a thread copies its own 16-byte pieces of the u rows j0-1 .. j0+2 and of the right-hand
-// side rows j0, j0+1 into its part of the warp's ring and later reads only those, so no block or
-// warp barrier orders the ring; the x-neighbours across thread boundaries come from the adjacent
-// lanes by shuffles (lanes 0 and 31 copy the tile's periodic edge values). Eight cells share every
-// per-plane cost (copies, addresses, ring bookkeeping) that the two-column sweep spends on two, and
+// Per plane a thread copies its own 16-byte pieces of the u rows j0-1 .. j0+ROWS and of the
+// right-hand side rows j0 .. j0+ROWS-1 into its part of the warp's ring and later reads only those,
+// so no block or warp barrier orders the ring; the x-neighbours across thread boundaries come from
+// the adjacent lanes by shuffles (lanes 0 and 31 copy the tile's periodic edge values). Four or eight
+// cells share every per-plane cost (copies, addresses, ring bookkeeping) that the two-column sweep
+// spends on two, and
 // the planes go in pairs: the two planes' residuals are independent, so their loads and arithmetic
 // interleave (a warp has few neighbours on its scheduler to hide latencies behind).
 //

@@ -1,4 +1,4 @@
-"""The FP32 Smooth and line solve with one 128 x 2 tile per warp (four columns x two rows per thread,
+"""The FP32 Smooth and line solve with one 128 x ROWS tile per warp (four columns x ROWS rows per thread,
 Thomas factors 1/m_k formed in registers): the same per-cell arithmetic as the two-column sweep, so
 the smoothed field equals variant 5's bit for bit -- on one-tile and many-wave grids, nz from 1 to
 128, lambda^2 varying by column (per-cell factors, converged range) or constant (shared table) --
