@@ -103,9 +103,15 @@ def _forward_bf16_storage(params, x, cin):
 FWD_TOL, GRAD_TOL = 1e-3, 1e-2
 
 
-# (3, 700, 128): 350 tiles of 128 x 2 cells for the tensor-core 16 -> 16 layers, more than the SMs
-# hold blocks, so some blocks carry their plane ring and accumulators from one tile into the next
-@pytest.mark.parametrize("shape", SHAPES + [(3, 700, 128)], ids=lambda s: "x".join(map(str, s)))
+# Shapes with nx % 128 = 0 and ny % 4 = 0 run every layer on the tensor-memory kernels with tiles of
+# 4 x 128 cells. (3, 700, 128): 175 tiles, more than the blocks, so blocks take tile pairs and some a
+# lone last tile; (1, 4, 128) and (2, 8, 256): one and two planes (the output plane completes after
+# the last input plane; halo cells wrap to the tile's own other edge); (4, 12, 384): three tile
+# columns, three tile rows.
+ROLL_SHAPES = [(3, 700, 128), (1, 4, 128), (2, 8, 256), (4, 12, 384)]
+
+
+@pytest.mark.parametrize("shape", SHAPES + ROLL_SHAPES, ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("cin", [1, 2])
 def test_forward_matches_oracle_layers_with_bf16_storage(shape, cin):
     p = random_params(cin, seed=30 + cin)
@@ -122,7 +128,7 @@ def test_forward_matches_oracle_layers_with_bf16_storage(shape, cin):
     net.close()
 
 
-@pytest.mark.parametrize("shape", SHAPES[:2], ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("shape", SHAPES[:2] + [(3, 8, 128)], ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("cin", [1, 2])
 def test_gradient_matches_oracle_layers_with_bf16_storage(shape, cin):
     """Backpropagation as the kernels store it: the output gradient 2 (y - t) / n in FP32, every
