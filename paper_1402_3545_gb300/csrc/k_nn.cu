@@ -305,29 +305,36 @@ __host__ __device__ constexpr uint32_t rl_idesc(int n) {
 }
 template <int TR, bool FIRST = false>
 struct RlShape {
-    static constexpr int NEPI = 128 * TR;
-    static constexpr int NT = NEPI + 32 + RL_NPROD;
+    // epilogue: one warp per lane quarter and row group, ERW row groups; a thread drains rows
+    // erow, erow + ERW, ... (RPT of them)
+    static constexpr int ERW = TR < 4 ? TR : 4;
+    static constexpr int RPT = TR / ERW;
+    static constexpr int NEPI = 128 * ERW;
+    static constexpr int NPROD = RL_NPROD;  // producer threads (the full barrier's arrival count)
+    static constexpr int NT = NEPI + 32 + NPROD;
     // weights: nine B matrices (rotation, dx); the first layer folds dx into K: three (rotation)
     static constexpr int WB = FIRST ? 3 * RL_BB : RL_WB;
     // one halo row of the A ring: 130 cells x 16 channels (both K halves), or for the first layer the
     // 128 cells of an operand row (K half 0: dx x 2 channels, K half 1 zero)
     static constexpr int ROWB = FIRST ? 2 * TCX * 16 : TC_ROWB;
     static constexpr int PLANEB = (TR + 2) * ROWB;
-    static constexpr int SLOTS = FIRST ? 3 : (TR == 4 ? 6 : 3);  // operand planes in flight or waiting
-                                                                  // (two rows: three, two blocks per SM)
+    // operand planes in flight or waiting (two rows: three, so that two blocks share an SM)
+    static constexpr int SLOTS = FIRST ? 3 : (TR == 4 ? 6 : 3);
     // first layer: raw halo rows (130 cells x 2 BF16 channels, 12 bytes of padding on either side,
     // the 128 interior cells 16-byte aligned) in a ring of RAW planes
     static constexpr int RAWROW = 32 + TCX * 4;
     static constexpr int RAW = FIRST ? 8 : 0;
     static constexpr int RAWB = (TR + 2) * RAWROW;
-    static constexpr int STAGE = TR * TCX * 32;  // one output plane of the tile in BF16, rows of 4 KB
+    static constexpr int STAGE = NEPI * 32;  // 1 KB of BF16 output per epilogue warp
     // output staging buffers per epilogue warp: up to NSTG of a warp's 1 KB bulk stores are in flight,
     // which is what hides the write latency
     static constexpr int NSTG = 2;
     static constexpr int SMEM = WB + SLOTS * PLANEB + RAW * RAWB + NSTG * STAGE;
     static constexpr int WIN_COLS = 48 * TR;     // one tile's window of three output planes
-    static constexpr int TMEM_COLS = 2 * WIN_COLS <= 256 ? 256 : 512;
-    static_assert(TR >= 2 && 2 * WIN_COLS <= 512, "two windows in the tensor memory");
+    // two windows (a pair of tiles in turn) where the tensor memory holds them, else one
+    static constexpr int NWIN = 2 * WIN_COLS <= 512 ? 2 : 1;
+    static constexpr int TMEM_COLS = NWIN * WIN_COLS <= 256 ? 256 : 512;
+    static_assert(TR >= 2 && TR % ERW == 0 && NWIN * WIN_COLS <= 512 && (!FIRST || NWIN == 2), "windows");
 };
 
 template <int EPI, int TR, bool FIRST = false>
@@ -384,7 +391,7 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
     if (tid < 16) bsh[tid] = (EPI == EPI_RELU) ? __ldg(bias + tid) : 0.f;
     if (tid == 0) {
         for (int s = 0; s < SH::SLOTS; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&full[s])), "n"(RL_NPROD));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&full[s])), "n"(SH::NPROD));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty[s])));
         }
         for (int w = 0; w < 2; ++w) {
@@ -399,18 +406,19 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
-    // the epilogue warp of tile row r zeroes its 32 lanes of row r in residue block q of window w
-    auto zero_block = [&](int w, int q) {
+    // an epilogue warp zeroes its 32 lanes of tile row `row` in residue block q of window w
+    auto zero_block = [&](int w, int q, int row) {
         const uint32_t z = 0;
         asm volatile(
             "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(
-                tmem + w * SH::WIN_COLS + 48 * (warp >> 2) + 16 * q + ((uint32_t)((warp & 3) * 32) << 16)),
+                tmem + w * SH::WIN_COLS + 48 * row + 16 * q + ((uint32_t)((warp & 3) * 32) << 16)),
             "r"(z)
             : "memory");
     };
     if (tid < SH::NEPI) {  // the windows start at zero; afterwards a block is zeroed as it is drained
-        for (int w = 0; w < 2; ++w)
-            for (int q = 0; q < 3; ++q) zero_block(w, q);
+        for (int w = 0; w < SH::NWIN; ++w)
+            for (int rr = 0; rr < SH::RPT; ++rr)
+                for (int q = 0; q < 3; ++q) zero_block(w, q, (warp >> 2) + SH::ERW * rr);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -493,24 +501,24 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
         } else {
             // ---- producers: the pair's planes in turn into slot q % SLOTS of the ring
             const int ptid = tid - (SH::NEPI + 32);
-            constexpr int NCH = (TR + 2) * TC_ROWC * 2, CPT = (NCH + RL_NPROD - 1) / RL_NPROD;
+            constexpr int NCH = (TR + 2) * TC_ROWC * 2, CPT = (NCH + SH::NPROD - 1) / SH::NPROD;
             int ch_dst[CPT];
-    #pragma unroll
+#pragma unroll
             for (int c = 0; c < CPT; ++c) {
-                const int qq = ptid + RL_NPROD * c;
+                const int qq = ptid + SH::NPROD * c;
                 ch_dst[c] = qq < NCH ? ((qq >> 1) / TC_ROWC) * TC_ROWB + (qq & 1) * TC_HALF + ((qq >> 1) % TC_ROWC) * 16 : -1;
             }
             int q = 0;
-            for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += 2 * G) {
-                const int nt = t0 + G < ntiles ? 2 : 1;
-                uint32_t src[2][CPT];  // element offsets within a plane (the caller keeps a plane below 2^32)
-    #pragma unroll
-                for (int w = 0; w < 2; ++w) {
+            for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += SH::NWIN * G) {
+                const int nt = SH::NWIN == 2 && t0 + G < ntiles ? 2 : 1;
+                uint32_t src[SH::NWIN][CPT];  // element offsets within a plane (the caller keeps a plane below 2^32)
+#pragma unroll
+                for (int w = 0; w < SH::NWIN; ++w) {
                     const int tile = w < nt ? t0 + w * G : t0;
                     const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
-    #pragma unroll
+#pragma unroll
                     for (int c = 0; c < CPT; ++c) {
-                        const int qq = ptid + RL_NPROD * c;
+                        const int qq = ptid + SH::NPROD * c;
                         const int hh = qq & 1, cc = (qq >> 1) % TC_ROWC, rr = (qq >> 1) / TC_ROWC;
                         src[w][c] = ((uint32_t)nwrap(y0 - 1 + rr, ny) * nx + nwrap(x0 - 1 + cc, nx)) * 16 + hh * 8;
                     }
@@ -524,7 +532,7 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
                         }
                         unsigned char* P = ring + slot * SH::PLANEB;
                         const __nv_bfloat16* base = in + (size_t)p * ny * nx * 16;
-    #pragma unroll
+#pragma unroll
                         for (int c = 0; c < CPT; ++c)
                             if (ch_dst[c] >= 0) cp16(P + ch_dst[c], base + src[w][c]);
                         asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(saddr(&full[slot]))
@@ -539,8 +547,8 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
         if (lane == 0) {
             const uint64_t dw0 = tc_desc(saddr(Ws), RL_BB / 2, 128);
             unsigned s = 0, cnt[2] = {0, 0};
-            for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += 2 * G) {
-                const int nt = t0 + G < ntiles ? 2 : 1;
+            for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += SH::NWIN * G) {
+                const int nt = SH::NWIN == 2 && t0 + G < ntiles ? 2 : 1;
                 for (int p = 0; p < nz && ok; ++p) {
                     for (int w = 0; w < nt; ++w, ++s) {
                         const int slot = s % SH::SLOTS;
@@ -598,46 +606,53 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
                 if (cnt[w] > 0) tc_wait(saddr(&accf[w]), (cnt[w] - 1) & 1);
         }
     } else {
-        // ---- epilogue: thread (erow, ecell) owns one cell of the tile rows
+        // ---- epilogue: thread (erow, ecell) owns one cell of tile rows erow, erow + ERW, ...
         const int erow = warp >> 2, ecell = (warp & 3) * 32 + lane;
-        auto load16 = [&](int w, int q, float (&v)[16]) {
+        auto load16 = [&](int w, int q, int row, float (&v)[16]) {
             uint32_t r[16];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                : "r"(tmem + w * SH::WIN_COLS + 48 * erow + 16 * q + ((uint32_t)((warp & 3) * 32) << 16)));
+                : "r"(tmem + w * SH::WIN_COLS + 48 * row + 16 * q + ((uint32_t)((warp & 3) * 32) << 16)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
         };
-        // output plane o of a tile: the warp's 32 cells (1 KB of BF16) into its staging buffer
-        // `nemit % NSTG`, then one bulk copy (TMA) of them to global memory issued by the warp's lane 0;
-        // a buffer is rewritten once the copy issued from it NSTG emits earlier has read it
-        unsigned nemit = 0;
-        auto emit = [&](int o, int x0, int y0, float (&v)[16]) {
-            const size_t pidx = ((size_t)o * ny + y0 + erow) * nx + x0 + ecell;
+        // a cell's 16 channels for output, rounded to BF16 and packed (forward: bias and ReLU first);
+        // done before the window is handed back, so that a thread holds 8 registers per row, not 16
+        auto pack = [&](float (&v)[16], uint4& o0, uint4& o1) {
             if (EPI == EPI_RELU) {
 #pragma unroll
                 for (int c = 0; c < 16; ++c) v[c] = fmaxf(v[c] + bsh[c], 0.f);
-            } else {
-                const uint4 m0 = __ldg(reinterpret_cast<const uint4*>(mask + pidx * 16));
-                const uint4 m1 = __ldg(reinterpret_cast<const uint4*>(mask + pidx * 16 + 8));
-                const __nv_bfloat16* mk0 = reinterpret_cast<const __nv_bfloat16*>(&m0);
-                const __nv_bfloat16* mk1 = reinterpret_cast<const __nv_bfloat16*>(&m1);
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    if (!(__bfloat162float(mk0[c]) > 0.f)) v[c] = 0.f;
-                    if (!(__bfloat162float(mk1[c]) > 0.f)) v[c + 8] = 0.f;
-                }
             }
-            uint4 o0, o1;
             __nv_bfloat162* h0 = reinterpret_cast<__nv_bfloat162*>(&o0);
             __nv_bfloat162* h1 = reinterpret_cast<__nv_bfloat162*>(&o1);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 h0[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
                 h1[c] = __floats2bfloat162_rn(v[8 + 2 * c], v[8 + 2 * c + 1]);
+            }
+        };
+        // output plane o of a tile: (data gradient: the ReLU mask, zeroing the rounded values, which
+        // gives the bits of zeroing before the rounding) the warp's 32 cells (1 KB of BF16) into its
+        // staging buffer `nemit % NSTG`, then one bulk copy (TMA) of them to global memory issued by the
+        // warp's lane 0; a buffer is rewritten once the copy issued from it NSTG emits earlier has read it
+        unsigned nemit = 0;
+        auto emit = [&](int o, int x0, int y0, int row, uint4 o0, uint4 o1) {
+            const size_t pidx = ((size_t)o * ny + y0 + row) * nx + x0 + ecell;
+            if (EPI == EPI_MASK) {
+                const uint4 m0 = __ldg(reinterpret_cast<const uint4*>(mask + pidx * 16));
+                const uint4 m1 = __ldg(reinterpret_cast<const uint4*>(mask + pidx * 16 + 8));
+                const __nv_bfloat16* mk0 = reinterpret_cast<const __nv_bfloat16*>(&m0);
+                const __nv_bfloat16* mk1 = reinterpret_cast<const __nv_bfloat16*>(&m1);
+                __nv_bfloat16* b0 = reinterpret_cast<__nv_bfloat16*>(&o0);
+                __nv_bfloat16* b1 = reinterpret_cast<__nv_bfloat16*>(&o1);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    if (!(__bfloat162float(mk0[c]) > 0.f)) b0[c] = __float2bfloat16_rn(0.f);
+                    if (!(__bfloat162float(mk1[c]) > 0.f)) b1[c] = __float2bfloat16_rn(0.f);
+                }
             }
             unsigned char* B = stage + (nemit % SH::NSTG) * SH::STAGE + warp * 1024;
             if (lane == 0) asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(SH::NSTG - 1) : "memory");
@@ -655,8 +670,8 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
             ++nemit;
         };
         unsigned cnt[2] = {0, 0};
-        for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += 2 * G) {
-            const int nt = t0 + G < ntiles ? 2 : 1;
+        for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += SH::NWIN * G) {
+            const int nt = SH::NWIN == 2 && t0 + G < ntiles ? 2 : 1;
             for (int p = 0; p < nz && ok; ++p) {
                 for (int w = 0; w < nt; ++w) {
                     const int tile = t0 + w * G;
@@ -666,25 +681,52 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const bool last = p == nz - 1;
-                    float va[16], vb[16];
-                    if (p >= 1) load16(w, (p - 1) % 3, va);  // output plane p-1 is complete
-                    if (last) load16(w, (nz - 1) % 3, vb);   // ... and after the last plane, plane nz-1
-                    // zero what was drained (after the tile's last plane the whole window, including the
-                    // block of the plane beyond the end), so the tile's next MMAs may accumulate
-                    if (last) {
-                        zero_block(w, 0);
-                        zero_block(w, 1);
-                        zero_block(w, 2);
+                    if (p < nz - 1) {
+                        // output plane p-1 is complete: drain it from every row of the thread and zero
+                        // its block, so that the tile's next MMAs may accumulate there; hand the window
+                        // back before the (slower) output stores
+                        uint4 oa[SH::RPT][2];
+#pragma unroll
+                        for (int rr = 0; rr < SH::RPT; ++rr) {
+                            if (p >= 1) {
+                                float v[16];
+                                load16(w, (p - 1) % 3, erow + SH::ERW * rr, v);
+                                pack(v, oa[rr][0], oa[rr][1]);
+                            }
+                            zero_block(w, (p + 2) % 3, erow + SH::ERW * rr);
+                        }
+                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                        asm volatile("tcgen05.fence::before_thread_sync;");
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(saddr(&acce[w]));
+                        if (p >= 1)
+#pragma unroll
+                            for (int rr = 0; rr < SH::RPT; ++rr) emit(p - 1, x0, y0, erow + SH::ERW * rr, oa[rr][0], oa[rr][1]);
                     } else {
-                        zero_block(w, (p + 2) % 3);
+                        // the tile's last plane: output planes p-1 and nz-1, then the whole window zeroed
+                        // (including the block of the plane beyond the end)
+#pragma unroll
+                        for (int rr = 0; rr < SH::RPT; ++rr) {
+                            const int row = erow + SH::ERW * rr;
+                            float va[16], vb[16];
+                            uint4 a0, a1, b0, b1;
+                            if (p >= 1) {
+                                load16(w, (p - 1) % 3, row, va);
+                                pack(va, a0, a1);
+                            }
+                            load16(w, (nz - 1) % 3, row, vb);
+                            pack(vb, b0, b1);
+                            zero_block(w, 0, row);
+                            zero_block(w, 1, row);
+                            zero_block(w, 2, row);
+                            if (p >= 1) emit(p - 1, x0, y0, row, a0, a1);
+                            emit(nz - 1, x0, y0, row, b0, b1);
+                        }
+                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                        asm volatile("tcgen05.fence::before_thread_sync;");
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(saddr(&acce[w]));
                     }
-                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                    asm volatile("tcgen05.fence::before_thread_sync;");
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(saddr(&acce[w]));
-                    if (p >= 1) emit(p - 1, x0, y0, va);
-                    if (last) emit(nz - 1, x0, y0, vb);
                     ++cnt[w];
                 }
             }
@@ -751,8 +793,18 @@ static int conv16_roll_grid(int nx, int ny) {
 template <int EPI>
 static void conv16(const NNBufs& b, const __nv_bfloat16* in, const __nv_bfloat16* W, const float* bias,
                    const __nv_bfloat16* mask, __nv_bfloat16* out, int nx, int ny, int nz, cudaStream_t s) {
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
     if (nx % TCX == 0 && ny % 2 == 0 && (size_t)nx * ny * 16 < ((size_t)1 << 32)) {
-        if (ny % 4 == 0)
+        // 8-row tiles (fewer MMAs per row, one window) where they still give every SM a tile
+        if (ny % 8 == 0 && (nx / TCX) * (ny / 8) >= nsm)
+            k_conv16_roll<EPI, 8><<<conv16_roll_grid<8>(nx, ny), RlShape<8>::NT, RlShape<8>::SMEM, s>>>(
+                in, W, bias, mask, out, nx, ny, nz, b.err);
+        else if (ny % 4 == 0)
             k_conv16_roll<EPI, 4><<<conv16_roll_grid<4>(nx, ny), RlShape<4>::NT, RlShape<4>::SMEM, s>>>(
                 in, W, bias, mask, out, nx, ny, nz, b.err);
         else
