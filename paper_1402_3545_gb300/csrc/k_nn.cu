@@ -790,15 +790,20 @@ static int conv16_roll_grid(int nx, int ny) {
 
 // one 16 -> 16 layer: the rolling-plane tcgen05 kernel (tiles of four rows, two where ny % 4 == 2)
 // when nx is a multiple of 128, else the mma.sync one
-template <int EPI>
-static void conv16(const NNBufs& b, const __nv_bfloat16* in, const __nv_bfloat16* W, const float* bias,
-                   const __nv_bfloat16* mask, __nv_bfloat16* out, int nx, int ny, int nz, cudaStream_t s) {
+static int sm_count() {
     static int nsm = 0;
     if (nsm == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     }
+    return nsm;
+}
+
+template <int EPI>
+static void conv16(const NNBufs& b, const __nv_bfloat16* in, const __nv_bfloat16* W, const float* bias,
+                   const __nv_bfloat16* mask, __nv_bfloat16* out, int nx, int ny, int nz, cudaStream_t s) {
+    const int nsm = sm_count();
     if (nx % TCX == 0 && ny % 2 == 0 && (size_t)nx * ny * 16 < ((size_t)1 << 32)) {
         // 8-row tiles (fewer MMAs per row, one window) where they still give every SM a tile
         if (ny % 8 == 0 && (nx / TCX) * (ny / 8) >= nsm)
@@ -1159,11 +1164,13 @@ template <int TR>
 struct LrShape {
     static constexpr int NT = 128 + 32 + LR_NPROD;  // epilogue warps, the MMA warp, the producers
     static constexpr int PLANEB = (TR + 2) * TC_ROWB;
-    static constexpr int SLOTS = 4;
+    static constexpr int SLOTS = TR >= 8 ? 2 : 4;   // two blocks share an SM
     static constexpr int SMEM = LR_WB + SLOTS * PLANEB;
     static constexpr int WIN_COLS = 16 * (TR + 2);  // one block of 16 columns per halo row
-    static constexpr int TMEM_COLS = 2 * WIN_COLS <= 128 ? 128 : 256;
-    static_assert(2 * WIN_COLS <= TMEM_COLS, "two windows");
+    // two windows (a pair of tiles in turn) where two blocks per SM still fit the tensor memory
+    static constexpr int NWIN = 2 * WIN_COLS <= 256 ? 2 : 1;
+    static constexpr int TMEM_COLS = NWIN * WIN_COLS <= 128 ? 128 : 256;
+    static_assert(NWIN * WIN_COLS <= TMEM_COLS, "windows");
 };
 
 template <int TR>
@@ -1232,12 +1239,12 @@ __global__ void __launch_bounds__(LrShape<TR>::NT, 2) k_last_roll(const __nv_bfl
             "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
             : "memory");
     };
-    if (tid < 128) {  // both windows start at zero
+    if (tid < 128) {  // the windows start at zero
         uint32_t z[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) z[c] = 0;
 #pragma unroll
-        for (int h = 0; h < 2 * (TR + 2); ++h) st16(h, z);
+        for (int h = 0; h < SH::NWIN * (TR + 2); ++h) st16(h, z);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1259,11 +1266,11 @@ __global__ void __launch_bounds__(LrShape<TR>::NT, 2) k_last_roll(const __nv_bfl
             ch_dst[c] = qq < NCH ? ((qq >> 1) / TC_ROWC) * TC_ROWB + (qq & 1) * TC_HALF + ((qq >> 1) % TC_ROWC) * 16 : -1;
         }
         int q = 0;
-        for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += 2 * G) {
-            const int nt = t0 + G < ntiles ? 2 : 1;
-            uint32_t src[2][CPT];  // element offsets within a plane (the caller keeps a plane below 2^32)
+        for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += SH::NWIN * G) {
+            const int nt = SH::NWIN == 2 && t0 + G < ntiles ? 2 : 1;
+            uint32_t src[SH::NWIN][CPT];  // element offsets within a plane (the caller keeps a plane below 2^32)
 #pragma unroll
-            for (int w = 0; w < 2; ++w) {
+            for (int w = 0; w < SH::NWIN; ++w) {
                 const int tile = w < nt ? t0 + w * G : t0;
                 const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
 #pragma unroll
@@ -1296,8 +1303,8 @@ __global__ void __launch_bounds__(LrShape<TR>::NT, 2) k_last_roll(const __nv_bfl
         if (lane == 0) {
             const uint64_t dw0 = tc_desc(saddr(Ws), LR_BB / 2, 128);
             unsigned s = 0, cnt[2] = {0, 0};
-            for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += 2 * G) {
-                const int nt = t0 + G < ntiles ? 2 : 1;
+            for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += SH::NWIN * G) {
+                const int nt = SH::NWIN == 2 && t0 + G < ntiles ? 2 : 1;
                 for (int p = 0; p < nz && ok; ++p) {
                     for (int w = 0; w < nt; ++w, ++s) {
                         const int slot = s % SH::SLOTS;
@@ -1336,8 +1343,8 @@ __global__ void __launch_bounds__(LrShape<TR>::NT, 2) k_last_roll(const __nv_bfl
         // ---- epilogue warps 0 .. 3: the thread owns cell `cell` of every tile row
         const int cell = (warp & 3) * 32 + lane;
         unsigned cnt[2] = {0, 0};
-        for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += 2 * G) {
-            const int nt = t0 + G < ntiles ? 2 : 1;
+        for (int t0 = blockIdx.x; t0 < ntiles && ok; t0 += SH::NWIN * G) {
+            const int nt = SH::NWIN == 2 && t0 + G < ntiles ? 2 : 1;
             for (int p = 0; p < nz && ok; ++p) {
                 for (int w = 0; w < nt; ++w) {
                     const int tile = t0 + w * G;
@@ -1353,17 +1360,19 @@ __global__ void __launch_bounds__(LrShape<TR>::NT, 2) k_last_roll(const __nv_bfl
                     float oa[TR], ob[TR];
 #pragma unroll
                     for (int r = 0; r < TR; ++r) oa[r] = ob[r] = 0.f;
-                    // the window of this lane in two halves, each half's loads in flight at once
-                    constexpr int HH = (TR + 2) / 2;
+                    // the window of this lane in groups of three blocks, each group's loads in flight at once
+                    constexpr int HH = 3, NG = (TR + 2 + HH - 1) / HH;
 #pragma unroll
-                    for (int g = 0; g < 2; ++g) {
+                    for (int g = 0; g < NG; ++g) {
                     uint32_t vv[HH][16];
 #pragma unroll
-                    for (int i = 0; i < HH; ++i) ld16(w * (TR + 2) + g * HH + i, vv[i]);
+                    for (int i = 0; i < HH; ++i)
+                        if (g * HH + i < TR + 2) ld16(w * (TR + 2) + g * HH + i, vv[i]);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                     for (int i = 0; i < HH; ++i) {
                         const int h = g * HH + i;
+                        if (h >= TR + 2) continue;
                         uint32_t (&v)[16] = vv[i];
 #pragma unroll
                         for (int j = 0; j < 3; ++j) {
@@ -1843,7 +1852,11 @@ void nn_forward(const NNBufs& b, int nx, int ny, int nz, const __nv_bfloat16* x,
     note_launch();
     conv16<EPI_RELU>(b, b.a1, b.w2f, b2, nullptr, b.a2, nx, ny, nz, s);
     conv16<EPI_RELU>(b, b.a2, b.w3f, b3, nullptr, b.a3, nx, ny, nz, s);
-    if (nx % TCX == 0 && ny % 4 == 0 && (size_t)nx * ny * 16 < ((size_t)1 << 32)) {
+    if (nx % TCX == 0 && ny % 8 == 0 && (size_t)nx * ny * 16 < ((size_t)1 << 32) &&
+        (nx / TCX) * (ny / 8) >= 2 * sm_count()) {  // 8-row tiles where they fill two blocks per SM
+        k_last_roll<8><<<last_roll_grid<8>(nx, ny), LrShape<8>::NT, LrShape<8>::SMEM, s>>>(b.a3, b.w4, b4, out, nx, ny,
+                                                                                        nz, b.err);
+    } else if (nx % TCX == 0 && ny % 4 == 0 && (size_t)nx * ny * 16 < ((size_t)1 << 32)) {
         k_last_roll<4><<<last_roll_grid<4>(nx, ny), LrShape<4>::NT, LrShape<4>::SMEM, s>>>(b.a3, b.w4, b4, out, nx, ny,
                                                                                         nz, b.err);
     } else {

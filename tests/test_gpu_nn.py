@@ -104,12 +104,13 @@ FWD_TOL, GRAD_TOL = 1e-3, 1e-2
 
 
 # Shapes with nx % 128 = 0 and ny % 4 = 0 run every layer on the tensor-memory kernels (the 16 -> 16
-# layers with tiles of 8 x 128 cells where ny % 8 = 0, else 4 x 128). (3, 700, 128): 175 tiles of 4
-# rows, more than the blocks, so blocks take tile pairs and some a lone last tile; (2, 1224, 128):
-# 153 tiles of 8 rows, one block runs two; (1, 4, 128) and (2, 8, 256): one and two planes (the
-# output plane completes after the last input plane; halo cells wrap to the tile's own other edge);
-# (4, 12, 384): three tile columns, three tile rows.
-ROLL_SHAPES = [(3, 700, 128), (2, 1224, 128), (1, 4, 128), (2, 8, 256), (4, 12, 384)]
+# and last layers with tiles of 8 x 128 cells where ny % 8 = 0 and there are enough tiles to fill the
+# SMs, else 4 x 128). (3, 700, 128): 175 tiles of 4 rows, more than the blocks, so blocks take tile
+# pairs and some a lone last tile; (2, 2440, 128): 305 tiles of 8 rows (the last layer too, two
+# blocks per SM), so some blocks run more than one; (1, 4, 128) and (2, 8, 256): one and two planes
+# (the output plane completes after the last input plane; halo cells wrap to the tile's own other
+# edge); (4, 12, 384): three tile columns, three tile rows.
+ROLL_SHAPES = [(3, 700, 128), (2, 2440, 128), (1, 4, 128), (2, 8, 256), (4, 12, 384)]
 
 
 @pytest.mark.parametrize("shape", SHAPES + ROLL_SHAPES, ids=lambda s: "x".join(map(str, s)))
