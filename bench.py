@@ -65,6 +65,7 @@ def parse_args():
                          "the measured FP64 and FP32 arithmetic rates")
     ap.add_argument("--variant", type=int, default=3)
     ap.add_argument("--nn-nx", type=int, default=256, help="horizontal size of the nn_forward kernel-only grid")
+    ap.add_argument("--nn-ny", type=int, default=0, help="its y size (default: the x size)")
     ap.add_argument("--precision", choices=["dw", "f32", "f64"], default="dw")
     return ap.parse_args()
 
@@ -554,10 +555,10 @@ def run_kernel_only(args):
         print(json.dumps(out), flush=True)
         return
     if args.kernel_only == "nn_forward":
-        # the learned stage's forward pass on one nn_nx^2 x 64 grid (256: a training crop of 4.2 M
-        # voxels; 2048: the inference grid of the learned workload)
+        # the learned stage's forward pass on one nn_ny x nn_nx x 64 grid (256^2: a training crop of
+        # 4.2 M voxels; 2048^2: the inference grid of the learned workload)
         from paper_1402_3545_gb300 import learned
-        shape = (64, args.nn_nx, args.nn_nx)
+        shape = (64, args.nn_ny or args.nn_nx, args.nn_nx)
         nvox = shape[0] * shape[1] * shape[2]
         net = tpmg.Network(2, learned.init_params(2, 0))
         x = torch.randn(nvox * 2, device="cuda", dtype=torch.float32, generator=torch.Generator("cuda").manual_seed(0))

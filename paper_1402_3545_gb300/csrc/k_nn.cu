@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
             // producer writes the operand row of its cell: K = (dx, ci) for the shifts dx = 0 .. 2, the
             // three 4-byte channel pairs of cells x-1 .. x+1 side by side
             constexpr int CPR = TCX * 4 / 16 + 2;  // copies per halo row: 32 of 16 bytes, two halo cells
-            constexpr int NCH = (TR + 2) * CPR, CPT = (NCH + RL_NPROD - 1) / RL_NPROD;
+            constexpr int NCH = (TR + 2) * CPR, CPT = (NCH + SH::NPROD - 1) / SH::NPROD;
             constexpr int DQ = SH::RAW - 2;  // a raw slot is refilled two steps after it was read
             const int ptid = tid - (SH::NEPI + 32);
             int it0 = blockIdx.x, ip = 0, iw = 0, iq = 0;  // the next step to copy: pair, plane, tile
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
                     const __nv_bfloat16* base = in + (size_t)ip * ny * nx * 2;
 #pragma unroll
                     for (int c = 0; c < CPT; ++c) {
-                        const int qq = ptid + RL_NPROD * c;
+                        const int qq = ptid + SH::NPROD * c;
                         if (qq < NCH) {
                             const int rr = qq / CPR, k = qq % CPR;
                             const size_t row = (size_t)nwrap(y0 - 1 + rr, ny) * nx;
@@ -482,17 +482,19 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
                 if (ptid == 0)
                     pstat[q & 1] =
                         (q < SH::SLOTS || ws_wait(saddr(&empty[slot]), ((q / SH::SLOTS) - 1) & 1, &abort)) ? 1 : 0;
-                asm volatile("bar.sync 1, %0;" ::"n"(RL_NPROD) : "memory");
+                asm volatile("bar.sync 1, %0;" ::"n"(SH::NPROD) : "memory");
                 if (!pstat[q & 1]) {
                     ok = false;
                     break;
                 }
                 const unsigned char* R = raw + (q % SH::RAW) * SH::RAWB;
                 unsigned char* A = ring + slot * SH::PLANEB;
+                constexpr int HS = SH::NPROD / TCX;  // producers per cell: rows h0, h0 + HS, ...
+                const int cell = ptid % TCX, h0 = ptid / TCX;
 #pragma unroll
-                for (int h = 0; h < TR + 2; ++h) {
-                    const uint32_t* r = reinterpret_cast<const uint32_t*>(R + h * SH::RAWROW + 12) + ptid;
-                    *reinterpret_cast<uint4*>(A + h * SH::ROWB + ptid * 16) = make_uint4(r[0], r[1], r[2], 0u);
+                for (int h = h0; h < TR + 2; h += HS) {
+                    const uint32_t* r = reinterpret_cast<const uint32_t*>(R + h * SH::RAWROW + 12) + cell;
+                    *reinterpret_cast<uint4*>(A + h * SH::ROWB + cell * 16) = make_uint4(r[0], r[1], r[2], 0u);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the operand, for the MMAs
                 mbar_arrive(saddr(&full[slot]));
