@@ -334,7 +334,7 @@ struct RlShape {
     // two windows (a pair of tiles in turn) where the tensor memory holds them, else one
     static constexpr int NWIN = 2 * WIN_COLS <= 512 ? 2 : 1;
     static constexpr int TMEM_COLS = NWIN * WIN_COLS <= 256 ? 256 : 512;
-    static_assert(TR >= 2 && TR % ERW == 0 && NWIN * WIN_COLS <= 512 && (!FIRST || NWIN == 2), "windows");
+    static_assert(TR >= 2 && TR % ERW == 0 && NWIN * WIN_COLS <= 512, "windows");
 };
 
 template <int EPI, int TR, bool FIRST = false>
@@ -459,19 +459,20 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
                         }
                     }
                     ++iq;
-                    const int nt = it0 + G < ntiles ? 2 : 1;
+                    const int nt = SH::NWIN == 2 && it0 + G < ntiles ? 2 : 1;
                     if (++iw == nt) {
                         iw = 0;
                         if (++ip == nz) {
                             ip = 0;
-                            it0 += 2 * G;
+                            it0 += SH::NWIN * G;
                         }
                     }
                 }
                 cp_commit_nn();  // one group per step, empty past the block's last step
             };
             int nsteps = 0;
-            for (int t0 = blockIdx.x; t0 < ntiles; t0 += 2 * G) nsteps += nz * (t0 + G < ntiles ? 2 : 1);
+            for (int t0 = blockIdx.x; t0 < ntiles; t0 += SH::NWIN * G)
+                nsteps += nz * (SH::NWIN == 2 && t0 + G < ntiles ? 2 : 1);
             for (int i = 0; i < DQ; ++i) issue();
             for (int q = 0; q < nsteps; ++q) {
                 issue();              // step q + DQ
@@ -1847,6 +1848,9 @@ void nn_forward(const NNBufs& b, int nx, int ny, int nz, const __nv_bfloat16* x,
     const float* b4 = b3 + 16 + 16 * 27;
     const int gt = thin_grid(nx, ny, 1 << 30);
     if (b.cin == 1) k_first_z<1><<<gt, 128, 0, s>>>(x, b.w1, b1, b.a1, nx, ny, nz);
+    else if (nx % TCX == 0 && ny % 8 == 0 && (nx / TCX) * (ny / 8) >= sm_count())  // 8-row tiles fill the SMs
+        k_conv16_roll<EPI_RELU, 8, true><<<conv16_roll_grid<8, true>(nx, ny), RlShape<8, true>::NT, RlShape<8, true>::SMEM,
+                                           s>>>(x, b.w1, b1, nullptr, b.a1, nx, ny, nz, b.err);
     else if (nx % TCX == 0 && ny % 4 == 0)
         k_conv16_roll<EPI_RELU, 4, true><<<conv16_roll_grid<4, true>(nx, ny), RlShape<4, true>::NT, RlShape<4, true>::SMEM,
                                            s>>>(x, b.w1, b1, nullptr, b.a1, nx, ny, nz, b.err);
