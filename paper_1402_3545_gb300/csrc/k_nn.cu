@@ -555,6 +555,10 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
                 for (int p = 0; p < nz && ok; ++p) {
                     for (int w = 0; w < nt; ++w, ++s) {
                         const int slot = s % SH::SLOTS;
+                        // one window with two rows per epilogue thread: the epilogue hands the drained
+                        // rows 0 .. ERW-1 back on acce[0] and the rest on acce[1], so that the views of
+                        // the first rows go in while the last rows drain
+                        constexpr bool SPLIT = SH::NWIN == 1 && SH::RPT == 2;
                         if (!ws_wait(saddr(&full[slot]), (s / SH::SLOTS) & 1, &abort) ||
                             (cnt[w] >= 1 && !ws_wait(saddr(&acce[w]), (cnt[w] - 1) & 1, &abort))) {
                             ok = false;
@@ -567,36 +571,44 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
                         const uint64_t dp = tc_desc(saddr(ring + slot * SH::PLANEB), FIRST ? TCX * 16 : TC_HALF, 128);
                         const uint32_t win = tmem + w * SH::WIN_COLS;
                         const int rot = p % 3;
-                        if constexpr (FIRST) {
-                            // one MMA per halo row: K spans the three shifts
+                        // the views of halo rows hlo .. hhi-1 (halo row h feeds tile rows h-2+j, j in [jlo, jhi])
+                        auto views = [&](int hlo, int hhi) {
 #pragma unroll
-                            for (int h = 0; h < TR + 2; ++h) {
+                            for (int h = hlo; h < hhi; ++h) {
                                 const int jlo = h < 2 ? 2 - h : 0, jhi = h > TR - 1 ? TR + 1 - h : 2;
-                                const uint64_t da = dp + (uint64_t)((h * SH::ROWB) >> 4);
-                                const uint64_t db = dw0 + (uint64_t)((rot * RL_BB + 48 * jlo * 16) >> 4);
-                                asm volatile(
-                                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                                        win + 48 * (h - 2 + jlo)),
-                                    "l"(da), "l"(db), "r"(rl_idesc(48 * (jhi - jlo + 1))), "r"(1));
-                            }
-                        } else {
-#pragma unroll
-                            for (int dx = 0; dx < 3; ++dx) {
-                                const uint32_t bmat = (rot * 3 + dx) * RL_BB;
-#pragma unroll
-                                for (int h = 0; h < TR + 2; ++h) {
-                                    // halo row h feeds tile rows h-2+j for j in [jlo, jhi]
-                                    const int jlo = h < 2 ? 2 - h : 0, jhi = h > TR - 1 ? TR + 1 - h : 2;
-                                    const uint64_t da = dp + (uint64_t)(((h * TC_ROWB) + dx * 16) >> 4);
-                                    const uint64_t db = dw0 + (uint64_t)((bmat + 48 * jlo * 16) >> 4);
+                                const uint32_t d = win + 48 * (h - 2 + jlo), idesc = rl_idesc(48 * (jhi - jlo + 1));
+                                if constexpr (FIRST) {  // one MMA per halo row: K spans the three shifts
+                                    const uint64_t da = dp + (uint64_t)((h * SH::ROWB) >> 4);
+                                    const uint64_t db = dw0 + (uint64_t)((rot * RL_BB + 48 * jlo * 16) >> 4);
                                     asm volatile(
                                         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                                            win + 48 * (h - 2 + jlo)),
-                                        "l"(da), "l"(db), "r"(rl_idesc(48 * (jhi - jlo + 1))), "r"(1));
+                                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                                        "l"(da), "l"(db), "r"(idesc), "r"(1));
+                                } else {
+#pragma unroll
+                                    for (int dx = 0; dx < 3; ++dx) {
+                                        const uint64_t da = dp + (uint64_t)(((h * TC_ROWB) + dx * 16) >> 4);
+                                        const uint64_t db = dw0 + (uint64_t)((((rot * 3 + dx) * RL_BB) + 48 * jlo * 16) >> 4);
+                                        asm volatile(
+                                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                                            "l"(da), "l"(db), "r"(idesc), "r"(1));
+                                    }
                                 }
                             }
+                        };
+                        if constexpr (SPLIT) {
+                            views(0, SH::ERW);  // tile rows up to ERW-1 (acce[0], waited above)
+                            if (cnt[w] >= 1 && !ws_wait(saddr(&acce[1]), (cnt[w] - 1) & 1, &abort)) {
+                                tc_commit(saddr(&accf[w]));  // the final wait covers the MMAs issued
+                                ++cnt[w];
+                                ok = false;
+                                break;
+                            }
+                            asm volatile("tcgen05.fence::after_thread_sync;");
+                            views(SH::ERW, TR + 2);
+                        } else {
+                            views(0, TR + 2);
                         }
                         tc_commit(saddr(&accf[w]));
                         tc_commit(saddr(&empty[slot]));  // the input plane has no later reader
@@ -611,6 +623,7 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
     } else {
         // ---- epilogue: thread (erow, ecell) owns one cell of tile rows erow, erow + ERW, ...
         const int erow = warp >> 2, ecell = (warp & 3) * 32 + lane;
+        constexpr bool SPLIT = SH::NWIN == 1 && SH::RPT == 2;  // rows handed back in two groups
         auto load16 = [&](int w, int q, int row, float (&v)[16]) {
             uint32_t r[16];
             asm volatile(
@@ -697,11 +710,13 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
                                 pack(v, oa[rr][0], oa[rr][1]);
                             }
                             zero_block(w, (p + 2) % 3, erow + SH::ERW * rr);
+                            if (SPLIT || rr == SH::RPT - 1) {  // rows handed back by groups (see the MMA thread)
+                                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                                asm volatile("tcgen05.fence::before_thread_sync;");
+                                __syncwarp();
+                                if (lane == 0) mbar_arrive(saddr(&acce[SPLIT ? rr : w]));
+                            }
                         }
-                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                        asm volatile("tcgen05.fence::before_thread_sync;");
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(saddr(&acce[w]));
                         if (p >= 1)
 #pragma unroll
                             for (int rr = 0; rr < SH::RPT; ++rr) emit(p - 1, x0, y0, erow + SH::ERW * rr, oa[rr][0], oa[rr][1]);
@@ -728,7 +743,10 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
                         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                         asm volatile("tcgen05.fence::before_thread_sync;");
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(saddr(&acce[w]));
+                        if (lane == 0) {
+                            mbar_arrive(saddr(&acce[w]));
+                            if (SPLIT) mbar_arrive(saddr(&acce[1]));
+                        }
                     }
                     ++cnt[w];
                 }
