@@ -1202,7 +1202,11 @@ __global__ void __launch_bounds__(LrShape<TR>::NT, 2) k_last_roll(const __nv_bfl
                                                                int* err) {
     typedef LrShape<TR> SH;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t full[LrShape<TR>::SLOTS], empty[LrShape<TR>::SLOTS], accf[2], acce[2];
+    // acce: per window, or with one window per group of three drained blocks (SPLIT)
+    __shared__ __align__(8) uint64_t full[LrShape<TR>::SLOTS], empty[LrShape<TR>::SLOTS], accf[2], acce[4];
+    constexpr int HH = 3, NG = (TR + 2 + HH - 1) / HH;  // the window's blocks in groups of three
+    constexpr bool SPLIT = SH::NWIN == 1;
+    static_assert(NG <= 4, "handover barriers");
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort;
     unsigned char* Ws = smem;
@@ -1231,10 +1235,8 @@ __global__ void __launch_bounds__(LrShape<TR>::NT, 2) k_last_roll(const __nv_bfl
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&full[s])), "n"(LR_NPROD));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty[s])));
         }
-        for (int w = 0; w < 2; ++w) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&accf[w])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(saddr(&acce[w])));
-        }
+        for (int w = 0; w < 2; ++w) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&accf[w])));
+        for (int g = 0; g < 4; ++g) asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(saddr(&acce[g])));
         abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -1339,17 +1341,38 @@ __global__ void __launch_bounds__(LrShape<TR>::NT, 2) k_last_roll(const __nv_bfl
                         const uint64_t dp = tc_desc(saddr(ring + slot * SH::PLANEB), TC_HALF, 128);
                         const uint32_t win = tmem + w * SH::WIN_COLS;
                         const int rot = p % 3;
+                        // the views of halo rows hlo .. hhi-1 (block h of the window each)
+                        auto views = [&](int hlo, int hhi) {
 #pragma unroll
-                        for (int dx = 0; dx < 3; ++dx) {
-                            const uint64_t db = dw0 + (uint64_t)(((rot * 3 + dx) * LR_BB) >> 4);
+                            for (int h = hlo; h < hhi; ++h)
 #pragma unroll
-                            for (int h = 0; h < TR + 2; ++h) {
-                                const uint64_t da = dp + (uint64_t)(((h * TC_ROWB) + dx * 16) >> 4);
-                                asm volatile(
-                                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(win + 16 * h),
-                                    "l"(da), "l"(db), "r"(LR_IDESC), "r"(1));
+                                for (int dx = 0; dx < 3; ++dx) {
+                                    const uint64_t db = dw0 + (uint64_t)(((rot * 3 + dx) * LR_BB) >> 4);
+                                    const uint64_t da = dp + (uint64_t)(((h * TC_ROWB) + dx * 16) >> 4);
+                                    asm volatile(
+                                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(win + 16 * h),
+                                        "l"(da), "l"(db), "r"(LR_IDESC), "r"(1));
+                                }
+                        };
+                        if constexpr (SPLIT) {  // each group of blocks as soon as the epilogue has zeroed it
+                            views(0, HH);  // group 0 (acce[0], waited above)
+                            bool okg = true;
+#pragma unroll
+                            for (int g = 1; g < NG; ++g) {
+                                if (okg && cnt[w] >= 1 && !ws_wait(saddr(&acce[g]), (cnt[w] - 1) & 1, &abort)) okg = false;
+                                if (!okg) break;
+                                asm volatile("tcgen05.fence::after_thread_sync;");
+                                views(g * HH, (g + 1) * HH < TR + 2 ? (g + 1) * HH : TR + 2);
                             }
+                            if (!okg) {
+                                tc_commit(saddr(&accf[w]));  // the final wait covers the MMAs issued
+                                ++cnt[w];
+                                ok = false;
+                                break;
+                            }
+                        } else {
+                            views(0, TR + 2);
                         }
                         tc_commit(saddr(&accf[w]));
                         tc_commit(saddr(&empty[slot]));
@@ -1381,8 +1404,8 @@ __global__ void __launch_bounds__(LrShape<TR>::NT, 2) k_last_roll(const __nv_bfl
                     float oa[TR], ob[TR];
 #pragma unroll
                     for (int r = 0; r < TR; ++r) oa[r] = ob[r] = 0.f;
-                    // the window of this lane in groups of three blocks, each group's loads in flight at once
-                    constexpr int HH = 3, NG = (TR + 2 + HH - 1) / HH;
+                    // the window of this lane in groups of three blocks, each group's loads in flight at once;
+                    // with one window each group is handed back once zeroed
 #pragma unroll
                     for (int g = 0; g < NG; ++g) {
                     uint32_t vv[HH][16];
@@ -1409,11 +1432,13 @@ __global__ void __launch_bounds__(LrShape<TR>::NT, 2) k_last_roll(const __nv_bfl
                             if (last || c % 3 == qa) v[c] = 0;
                         st16(w * (TR + 2) + h, v);
                     }
+                    if (SPLIT || g == NG - 1) {
+                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                        asm volatile("tcgen05.fence::before_thread_sync;");
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(saddr(&acce[SPLIT ? g : w]));
                     }
-                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                    asm volatile("tcgen05.fence::before_thread_sync;");
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(saddr(&acce[w]));
+                    }
 #pragma unroll
                     for (int r = 0; r < TR; ++r) {
                         const size_t row = (size_t)(y0 + r) * nx + x0 + cell;
