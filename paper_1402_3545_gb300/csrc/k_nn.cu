@@ -692,7 +692,8 @@ __global__ void __launch_bounds__(RlShape<TR, FIRST>::NT) k_conv16_roll(const __
                 for (int w = 0; w < nt; ++w) {
                     const int tile = t0 + w * G;
                     const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
-                    if (!ws_wait(saddr(&accf[w]), cnt[w] & 1, &abort)) {
+                    // the warp agrees on the bounded wait's outcome, so that it leaves or goes on as one
+                    if (!__all_sync(0xffffffffu, ws_wait(saddr(&accf[w]), cnt[w] & 1, &abort))) {
                         ok = false;
                         break;
                     }
@@ -1393,7 +1394,8 @@ __global__ void __launch_bounds__(LrShape<TR>::NT, 2) k_last_roll(const __nv_bfl
                 for (int w = 0; w < nt; ++w) {
                     const int tile = t0 + w * G;
                     const int x0 = (tile % tiles_x) * TCX, y0 = (tile / tiles_x) * TR;
-                    if (!ws_wait(saddr(&accf[w]), cnt[w] & 1, &abort)) {
+                    // the warp agrees on the bounded wait's outcome, so that it leaves or goes on as one
+                    if (!__all_sync(0xffffffffu, ws_wait(saddr(&accf[w]), cnt[w] & 1, &abort))) {
                         ok = false;
                         break;
                     }
