@@ -4,12 +4,12 @@
 //
 // Activations are channels-last BF16 (16 channels = 32 bytes per cell, cell index (k*ny + j)*nx + i);
 // weights are BF16 copies of FP32 master parameters; all sums accumulate in FP32.
-// The 16 -> 16 layers are implicit GEMMs on the tensor cores: a block computes tiles of 64 x 2
-// cells, plane after plane; each warp owns 16 consecutive cells (the M = 16 rows of
-// mma.m16n8k16), the K dimension runs over the 27 taps x 16 input channels, N = 16 output channels
-// (two n8 tiles). The 27 x 16 x 16 weights and the input planes with their one-cell halo (66 x 4
-// cells) are staged in shared memory and fed to the MMAs with ldmatrix. The same kernel computes
-// the data gradient of the backward pass with flipped, transposed weights and a ReLU-mask epilogue. The weight
+// Where nx is a multiple of 128 (and ny of 4), every layer is an implicit GEMM on the fifth-generation
+// tensor cores (tcgen05, accumulators in tensor memory) in one rolling scheme over the z planes:
+// k_conv16_roll (the 16 -> 16 layers, their data gradient, and the 2 -> 16 first layer) and
+// k_last_roll (16 -> 1). Other shapes use mma.sync kernels: k_conv16z (16 -> 16: tiles of 64 x 2
+// cells, each warp 16 consecutive cells as the M = 16 rows of mma.m16n8k16, K over the 27 taps x 16
+// input channels, operands by ldmatrix), k_first_z / k_first_tc2 and k_last_proj. The weight
 // gradients of the 16 -> 16 layers are tensor-core GEMMs too (cells are the K dimension).
 #include <cuda_bf16.h>
 
@@ -284,16 +284,22 @@ __device__ __forceinline__ void tc_commit(uint32_t mbar) {
 // the nine taps' weights in that order, rotated with p mod 3 (3 rotations x 3 shifts = 9 matrices),
 // and a narrower MMA reads the rows of B it needs. Per input plane 3 (TR + 2) MMAs; after them output
 // plane p-1 is complete and the input plane is never read again, so the z padding needs no planes.
-// A block works on two tiles at once, plane by plane in turn, each with its own window of 48 TR
-// columns: the MMAs of one tile run while the epilogue drains the other's window. Roles:
+// Tiles of TR = 4 rows: a block works on two tiles at once, plane by plane in turn, each with its own
+// window of 48 TR columns, so the MMAs of one tile run while the epilogue drains the other's window.
+// Tiles of TR = 8 rows (fewer MMAs per row; one window of 384 columns): the epilogue hands rows 0-3
+// and 4-7 back on separate barriers, and the MMA thread issues the views of the first rows while the
+// others drain. The first layer (FIRST) folds the three shifts into K (2 channels x 3 shifts = 6 of
+// K = 16): one MMA per halo row. Roles:
 //   producer warps (4): copy the input planes into a ring of SLOTS planes with cp.async, each
-//     thread's copies followed by cp.async.mbarrier.arrive on the slot's `full` mbarrier;
+//     thread's copies followed by cp.async.mbarrier.arrive on the slot's `full` mbarrier (first
+//     layer: raw rows into a ring of their own, then each producer writes its cell's operand rows);
 //   one MMA thread: per input plane waits for it (`full`) and for the epilogue to have zeroed the
 //     residue block it opens in its tile's window (`acce` of that window), issues the MMAs, commits
 //     to the window's `accf` and releases the plane's slot (`empty`, by tcgen05.commit);
-//   epilogue warps (4 per tile row): per input plane p drain output plane p-1 of the tile (and,
-//     after the tile's last plane, plane nz-1), zero the drained residue blocks (after the last plane
-//     all three), arrive on `acce`, then bias + ReLU (or the backward mask) into the warp's BF16
+//   epilogue warps (4 per group of tile rows, TR / 4 rows per thread): per input plane p drain output
+//     plane p-1 of the tile (and, after the tile's last plane, plane nz-1), round it to BF16 (bias +
+//     ReLU first in the forward pass), zero the drained residue blocks (after the last plane all
+//     three), arrive on `acce`, then (with the backward pass's ReLU mask) write the warp's BF16
 //     staging buffer, which the warp's lane 0 writes out by a bulk copy (TMA) of its 32 cells.
 // Every wait is bounded and also gives up once another role has given up (a shared abort flag), which
 // raises the error flag.
@@ -810,8 +816,8 @@ static int conv16_roll_grid(int nx, int ny) {
     return nb < ntiles ? nb : ntiles;
 }
 
-// one 16 -> 16 layer: the rolling-plane tcgen05 kernel (tiles of four rows, two where ny % 4 == 2)
-// when nx is a multiple of 128, else the mma.sync one
+// one 16 -> 16 layer: the rolling-plane tcgen05 kernel when nx is a multiple of 128 (tiles of eight
+// rows where they give every SM one, else four, two where ny % 4 == 2), else the mma.sync one
 static int sm_count() {
     static int nsm = 0;
     if (nsm == 0) {
@@ -1175,9 +1181,10 @@ __global__ void __launch_bounds__(128) k_last_proj(const __nv_bfloat16* __restri
 // plane 3 (TR + 2) MMAs; then output plane p-1 is complete. The epilogue warps (one per lane quarter,
 // a thread owns one cell of every tile row) load the whole window of their lanes (all loads in
 // flight, one wait), add each row's three columns, zero the drained residue's columns (all after the
-// tile's last plane), store it back, hand it back and store the outputs (+ bias) in FP32. Two windows
-// of 16 (TR + 2) columns take a pair of tiles plane by plane in turn, so the tensor core fills one
-// while the epilogue drains the other. Producers and the bounded waits as in k_conv16_roll.
+// tile's last plane), store it back, hand it back and store the outputs (+ bias) in FP32. With TR = 4
+// two windows of 16 (TR + 2) columns take a pair of tiles plane by plane in turn, so the tensor core
+// fills one while the epilogue drains the other; with TR = 8 one window, handed back in groups of
+// three blocks. Two blocks per SM. Producers and the bounded waits as in k_conv16_roll.
 static constexpr int LR_NPROD = 64;
 static constexpr int LR_BB = 16 * 32;  // one B matrix: [K half][16 rows][8 ci]
 static constexpr int LR_WB = 9 * LR_BB;
