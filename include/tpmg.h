@@ -287,8 +287,9 @@ tpmg_status tpmg_set_variant(tpmg_op* op, tpmg_precision prec, int level, int va
  * Architecture: cin (1 or 2) -> 16 -> 16 -> 16 -> 1 channels, 3x3x3 kernels, ReLU after the first
  * three layers, periodic padding in x and y and zero padding in z (the problem's boundaries).
  * Parameters: tpmg_nn_nparams(cin) floats, flat W1 b1 W2 b2 W3 b3 W4 b4 with W[co][ci][dz][dy][dx].
- * Inference and training run in BF16 with FP32 accumulation (the 16 -> 16 layers and their weight
- * gradients on the tensor cores); FP32 master weights; Adam (lr given, beta 0.9/0.999, eps 1e-8).
+ * Inference and training run in BF16 with FP32 accumulation on the tensor cores (all four layers of
+ * the forward pass where nx % 128 == 0 and ny % 4 == 0, the 16 -> 16 layers and their gradients
+ * otherwise); FP32 master weights; Adam (lr given, beta 0.9/0.999, eps 1e-8).
  * Network inputs x are DEVICE fp32, channels-last (cin values per cell, cell index (k*ny+j)*nx+i);
  * outputs and targets DEVICE fp32 (one value per cell). Grids need nx % 64 == 0 and ny % 2 == 0. */
 typedef struct tpmg_nn tpmg_nn;
