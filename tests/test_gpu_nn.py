@@ -307,3 +307,33 @@ def test_params_round_trip_and_zero_default():
     net.set_params(p)
     assert np.array_equal(net.get_params(), p)
     net.close()
+
+
+def test_forward_full_size_sampled():
+    """The forward pass at the learned workload's inference size, 2048^2 x 64 (every layer on 8-row
+    tiles, several tiles per block, as the bench times it), against the oracle on sampled cells. An
+    output depends on the input within 4 cells (four 3x3x3 layers), so the oracle evaluates each
+    sampled cell on the 9^3 crop around it, wrapped in x and y and clipped at the z ends (where the
+    network zero-pads): crop cells near the crop's own edges see wrong neighbours, but their errors
+    move one cell inwards per layer and do not reach the centre in four. The samples include the
+    volume's faces and corners and the edges of the 8 x 128 tiles."""
+    nz, ny, nx, cin = 64, 2048, 2048, 2
+    p = random_params(cin, seed=77)
+    rng = np.random.default_rng(78)
+    xl = rng.standard_normal((nz, ny, nx, cin), dtype=np.float32)  # channels-last, as the kernels read it
+    net = tpmg.Network(cin, p)
+    y = net.forward(torch.from_numpy(xl.reshape(-1)).cuda(), (nz, ny, nx))
+    cells = [(0, 0, 0), (nz - 1, ny - 1, nx - 1), (0, ny - 1, 0), (nz - 1, 0, nx - 1), (1, 7, 127), (2, 8, 128),
+             (31, 1023, 1024), (32, 1024, 1023), (62, 2047, 128), (63, 8, 2047)]
+    cells += [tuple(int(v) for v in rng.integers(0, (nz, ny, nx))) for _ in range(30)]
+    idx = torch.tensor([(k * ny + j) * nx + i for k, j, i in cells], device="cuda")
+    got = y[idx].double().cpu().numpy()
+    ref = np.empty(len(cells))
+    for s, (k, j, i) in enumerate(cells):
+        zlo, zhi = max(0, k - 4), min(nz, k + 5)
+        crop = xl[zlo:zhi][:, np.arange(j - 4, j + 5) % ny][:, :, np.arange(i - 4, i + 5) % nx]
+        yc, _ = _forward_bf16_storage(p, np.moveaxis(crop, -1, 0).astype(np.float64), cin)
+        ref[s] = yc[k - zlo, 4, 4]
+    assert rel(got, ref) < FWD_TOL, rel(got, ref)
+    assert np.max(np.abs(got - ref)) < 1e-2 * np.max(np.abs(ref))
+    net.close()
